@@ -1,0 +1,463 @@
+"""Oracle for the server-side hot path of the private database query (PDQ):
+Mask followed by the SIMD-aware homomorphic compression Comp, plus the
+client-side Decomp and the plaintext closed form that pins the result.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Paper anchors:
+* Answer = Match -> Mask -> Comp, with the Match output v reused as the index
+  vector (Alg. 7, Sec. 4.2.2).  Match depends on the query and is not given in
+  the paper; the client's encrypted 0/1 index vector stands in for it.
+* The compression matrix C[j][i] = i^j, j = 1..s (Eq. 1); Comp returns
+  ctxt(Cv) and ctxt(Cd) (Alg. 5 and Alg. 7).
+* SIMD form: u = [v; d] packed with row masks and Rot_col (Remark in
+  Sec. 5.2), Pegasus-style diagonal matrix-vector product with baby-step /
+  giant-step rotations on both rows at once, blocks summed before a single
+  rotate-and-sum (Sec. 5.2).
+* Decomp: Dec, Newton's identity (Lem. 1, Alg. 1 step 1), strip the factors
+  of X and find the roots (Alg. 1 step 2), solve the Vandermonde system on
+  the recovered columns (Alg. 4), scatter (Alg. 6).
+
+Readings where the paper is silent (all mirrored by the GPU library):
+* s' = 2^ceil(log2 s) rows of C (the diagonal method needs s' | N/2).
+* The paper requires t > n (Eq. 1 remark).  Records are split into groups of
+  G_sz = N*floor((t-1)/N) consecutive records; group gamma uses nodes
+  alpha(i) = (i mod G_sz) + 1, and its (w, e) block sits in output ciphertext
+  floor(gamma/(m/s')) at slot offset (gamma mod (m/s'))*s'.  With one group
+  this is exactly the paper's C.
+* The row masks of the u-packing remark are folded into the Mask plaintexts:
+  (v.DB).[1;0] = v.(DB.[1;0]) (same slots, one multiplicative level less).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import ring
+from .bfv import (Params, ct_add, decrypt, encode, lift, mod_up_all, pt_mul, qlimbs,
+                  rotate, rotate_hoisted, encrypt)
+
+
+# ------------------------------------------------------------------ plan ----
+
+@dataclass(frozen=True)
+class Plan:
+    n: int          # records
+    s: int          # sparsity bound
+    s_prime: int    # padded compressed length per row
+    B: int          # baby steps
+    J: int          # index-vector ciphertexts
+    H: int          # half-blocks (u ciphertexts) = 2J
+    G_sz: int       # records per group
+    hpg: int        # half-blocks per group
+    G: int          # groups
+    per_out: int    # groups per output ciphertext = m / s'
+    n_out: int      # output ciphertexts
+
+    @property
+    def giants(self) -> int:
+        return self.s_prime // self.B
+
+
+def make_plan(par: Params, n: int, s: int, B: int | None = None) -> Plan:
+    if n < 1 or s < 1:
+        raise ValueError("n and s must be positive")
+    s_prime = 1 << math.ceil(math.log2(s))
+    if s_prime > par.m or s_prime >= par.t:
+        raise ValueError("sparsity too large for the ring")
+    if B is None:
+        B = 1 << math.ceil(math.log2(s_prime) / 2)
+    if B < 1 or s_prime % B:
+        raise ValueError("B must divide s'")
+    J = -(-n // par.N)
+    H = 2 * J
+    G_sz = par.N * ((par.t - 1) // par.N)
+    hpg = G_sz // par.m
+    G = -(-H // hpg)
+    per_out = par.m // s_prime
+    n_out = -(-G // per_out)
+    return Plan(n, s, s_prime, B, J, H, G_sz, hpg, G, per_out, n_out)
+
+
+def galois_elements(par: Params, plan: Plan) -> list[int]:
+    """Every automorphism the schedule uses, ascending."""
+    ks = {par.galois_col}
+    ks.update(par.galois_rot(a) for a in range(1, plan.B))
+    ks.update(par.galois_rot(g * plan.B) for g in range(1, plan.giants))
+    l = plan.s_prime
+    while l < par.m:
+        ks.add(par.galois_rot(l))
+        l *= 2
+    return sorted(ks)
+
+
+# ---------------------------------------------------------------- layout ----
+
+def record_slots(par: Params, values, j: int) -> np.ndarray:
+    """Slots of ciphertext j: record i = j*N + rho*m + c sits at row rho,
+    column c (slot index rho*m + c); records past the end are 0."""
+    out = np.zeros(par.N, dtype=np.uint64)
+    chunk = np.asarray(values[j * par.N:(j + 1) * par.N], dtype=np.uint64)
+    out[:chunk.size] = chunk
+    return out
+
+
+def encrypt_index(par: Params, sk, v, plan: Plan, a, e) -> list[np.ndarray]:
+    """Query: the client encrypts its 0/1 index vector, N records per
+    ciphertext.  a: [J][L][N], e: [J][N] supplied randomness."""
+    return [encrypt(par, sk, encode(par, record_slots(par, v, j)), a[j], e[j])
+            for j in range(plan.J)]
+
+
+def row_mask_slots(par: Params, rho: int) -> np.ndarray:
+    s = np.zeros(par.N, dtype=np.uint64)
+    s[rho * par.m:(rho + 1) * par.m] = 1
+    return s
+
+
+def lifted_pt(par: Params, slots) -> np.ndarray:
+    return lift(par, encode(par, slots), par.q)
+
+
+# ------------------------------------------------------------------ Mask ----
+
+def mask(par: Params, v_cts, db, plan: Plan) -> list[np.ndarray]:
+    """Mask with the row split folded in (4 ciphertexts per index ciphertext):
+    vT = v.[1;0], vB = v.[0;1], dT = v.(DB.[1;0]), dB = v.(DB.[0;1])."""
+    top = row_mask_slots(par, 0)
+    bot = row_mask_slots(par, 1)
+    pt_top, pt_bot = lifted_pt(par, top), lifted_pt(par, bot)
+    out = []
+    for j in range(plan.J):
+        dbs = record_slots(par, db, j)
+        out.append(pt_mul(par, v_cts[j], pt_top))
+        out.append(pt_mul(par, v_cts[j], pt_bot))
+        out.append(pt_mul(par, v_cts[j], lifted_pt(par, dbs * top)))
+        out.append(pt_mul(par, v_cts[j], lifted_pt(par, dbs * bot)))
+    return out
+
+
+# ------------------------------------------------------------------ Comp ----
+
+def pack(par: Params, masked, keys, plan: Plan) -> list[np.ndarray]:
+    """u_{2j} = vT_j + Rot_col(dT_j), u_{2j+1} = Rot_col(vB_j) + dB_j, so that
+    u_h = [v_h; d_h] for half-block h (u-packing remark, Sec. 5.2)."""
+    kc = par.galois_col
+    u = []
+    for j in range(plan.J):
+        vT, vB, dT, dB = masked[4 * j:4 * j + 4]
+        u.append(ct_add(par, vT, rotate(par, dT, kc, keys[kc])))
+        u.append(ct_add(par, rotate(par, vB, kc, keys[kc]), dB))
+    return u
+
+
+def node_row(par: Params, plan: Plan, h: int) -> np.ndarray:
+    """alpha(i) = (i mod G_sz) + 1 for the m records i = h*m + x of half-block h."""
+    x = np.arange(par.m, dtype=np.int64)
+    return ((h * par.m + x) % plan.G_sz + 1).astype(np.uint64)
+
+
+def powmod_vec(base: np.ndarray, exp: np.ndarray, t: int) -> np.ndarray:
+    """Element-wise base^exp mod t (t < 2^31), square and multiply."""
+    r = np.ones_like(base, dtype=np.uint64)
+    b = base.astype(np.uint64) % np.uint64(t)
+    e = exp.astype(np.int64).copy()
+    while (e > 0).any():
+        odd = (e & 1) == 1
+        r = np.where(odd, r * b % np.uint64(t), r)
+        b = b * b % np.uint64(t)
+        e >>= 1
+    return r
+
+
+def diagonal_slots(par: Params, plan: Plan, h: int, k: int) -> np.ndarray:
+    """k-th extended diagonal of the block of C acting on half-block h, the
+    same on both rows (C "encoded twice", Sec. 5.2):
+      D_{h,k}[c] = alpha(h*m + ((c + k) mod m))^{(c mod s') + 1}  mod t."""
+    m = par.m
+    c = np.arange(m)
+    nodes = node_row(par, plan, h)[(c + k) % m]
+    row = powmod_vec(nodes, (c % plan.s_prime) + 1, par.t)
+    return np.concatenate([row, row])
+
+
+def rot_slots(par: Params, slots, r: int) -> np.ndarray:
+    """Rot(.; r) on both rows: [v_1..v_m] -> [v_{1+r}, ..., v_r] (Sec. 5.1)."""
+    s = np.asarray(slots).reshape(2, par.m)
+    return np.roll(s, -r, axis=1).reshape(-1)
+
+
+def ring_dot(par: Params, pts, cts) -> np.ndarray:
+    """sum_i pts[i] * cts[i] in R_Q (plaintext-ciphertext products, summed).
+    Each product is a negacyclic product limb by limb; it is computed through
+    the oracle's transform as INTT(sum_i NTT(pt_i) .* NTT(ct_i)), which equals
+    the sum of the individual products because the transform is linear."""
+    L, N = par.L, par.N
+    acc = np.zeros((2, L, N), dtype=np.uint64)
+    for pt, ct in zip(pts, cts):
+        for i in range(L):
+            q, psi = par.q[i], par.psi[i]
+            fp = ring.ntt_forward(pt[i], q, psi)
+            for p in range(2):
+                fc = ring.ntt_forward(ct[p][i], q, psi)
+                acc[p][i] = ring.vec_add(acc[p][i], ring.vec_mul(fp, fc, q), q)
+    for p in range(2):
+        for i in range(L):
+            acc[p][i] = ring.ntt_inverse(acc[p][i], par.q[i], par.psi[i])
+    return acc
+
+
+def group_halfblocks(plan: Plan, gamma: int) -> range:
+    return range(gamma * plan.hpg, min((gamma + 1) * plan.hpg, plan.H))
+
+
+def baby_steps(par: Params, u, keys, plan: Plan):
+    """R[h][a] = Rot_row(u_h; a), a = 0..B-1, the digits of c1 raised once per
+    u_h and shared by all its rotations."""
+    R = []
+    for uh in u:
+        raised = mod_up_all(par, uh[1])
+        row = [uh]
+        for a in range(1, plan.B):
+            k = par.galois_rot(a)
+            row.append(rotate_hoisted(par, uh, raised, k, keys[k]))
+        R.append(row)
+    return R
+
+
+def giant_accumulators(par: Params, R, plan: Plan):
+    """acc[gamma][g] = sum_{h in gamma} sum_{a<B} Rot(D_{h,gB+a}; -gB) . Rot(u_h; a)."""
+    acc = []
+    for gamma in range(plan.G):
+        row = []
+        for g in range(plan.giants):
+            pts, cts = [], []
+            for h in group_halfblocks(plan, gamma):
+                for a in range(plan.B):
+                    d = rot_slots(par, diagonal_slots(par, plan, h, g * plan.B + a),
+                                  -g * plan.B)
+                    pts.append(lifted_pt(par, d))
+                    cts.append(R[h][a])
+            row.append(ring_dot(par, pts, cts))
+        acc.append(row)
+    return acc
+
+
+def giant_steps(par: Params, acc, keys, plan: Plan):
+    """y_gamma = sum_g Rot(acc[gamma][g]; gB)  (Rot(.; 0) is the identity)."""
+    ys = []
+    for gamma in range(plan.G):
+        y = acc[gamma][0]
+        for g in range(1, plan.giants):
+            k = par.galois_rot(g * plan.B)
+            y = ct_add(par, y, rotate(par, acc[gamma][g], k, keys[k]))
+        ys.append(y)
+    return ys
+
+
+def rotate_and_sum(par: Params, y, keys, plan: Plan):
+    """y <- y + Rot(y; s' 2^l) for l = 0 .. log2(m/s') - 1 (once, after the
+    blocks were summed, Sec. 5.2)."""
+    l = plan.s_prime
+    while l < par.m:
+        k = par.galois_rot(l)
+        y = ct_add(par, y, rotate(par, y, k, keys[k]))
+        l *= 2
+    return y
+
+
+def group_mask_slots(par: Params, plan: Plan, o: int) -> np.ndarray:
+    s = np.zeros(par.N, dtype=np.uint64)
+    for rho in range(2):
+        s[rho * par.m + o * plan.s_prime: rho * par.m + (o + 1) * plan.s_prime] = 1
+    return s
+
+
+def combine_groups(par: Params, ys, plan: Plan):
+    """One group: the result as is (its block repeats every s' slots).
+    Several groups: Out_c = sum_{gamma in c} M_{gamma mod (m/s')} . y_gamma."""
+    if plan.G == 1:
+        return [ys[0]]
+    outs = []
+    for c in range(plan.n_out):
+        gs = range(c * plan.per_out, min((c + 1) * plan.per_out, plan.G))
+        pts = [lifted_pt(par, group_mask_slots(par, plan, g - c * plan.per_out)) for g in gs]
+        outs.append(ring_dot(par, pts, [ys[g] for g in gs]))
+    return outs
+
+
+def comp(par: Params, masked, keys, plan: Plan) -> list[np.ndarray]:
+    """Comp of Alg. 7 in SIMD form: returns the output ciphertexts holding
+    ctxt(Cv) in row 0 and ctxt(Cd) in row 1."""
+    u = pack(par, masked, keys, plan)
+    R = baby_steps(par, u, keys, plan)
+    acc = giant_accumulators(par, R, plan)
+    ys = giant_steps(par, acc, keys, plan)
+    ys = [rotate_and_sum(par, y, keys, plan) for y in ys]
+    return combine_groups(par, ys, plan)
+
+
+def answer(par: Params, v_cts, db, keys, plan: Plan) -> list[np.ndarray]:
+    """Server side of the query: Mask then Comp (Alg. 7 without Match)."""
+    return comp(par, mask(par, v_cts, db, plan), keys, plan)
+
+
+# ------------------------------------------------------- closed form ------
+
+def closed_form(par: Params, plan: Plan, v, db):
+    """The plaintext result: per group gamma, for k = 1..s'
+      w_k = sum_{i in gamma} alpha(i)^k v_i,   e_k = sum_{i in gamma} alpha(i)^k v_i DB_i  (mod t)
+    i.e. C v and C d with d = v.DB (Eq. 1, Alg. 7).  Returns [G][2][s']."""
+    t = np.uint64(par.t)
+    v = np.asarray(v, dtype=np.uint64)
+    d = v * np.asarray(db, dtype=np.uint64) % t
+    out = np.zeros((plan.G, 2, plan.s_prime), dtype=np.uint64)
+    n = v.size
+    for gamma in range(plan.G):
+        lo = gamma * plan.G_sz
+        hi = min(lo + plan.G_sz, n)
+        if lo >= hi:
+            continue
+        alpha = (np.arange(lo, hi, dtype=np.int64) % plan.G_sz + 1).astype(np.uint64)
+        pw = np.ones_like(alpha)
+        vv, dd = v[lo:hi], d[lo:hi]
+        for k in range(plan.s_prime):
+            pw = pw * alpha % t
+            out[gamma, 0, k] = int((pw * vv % t).sum() % t)
+            out[gamma, 1, k] = int((pw * dd % t).sum() % t)
+    return out
+
+
+def expected_slots(par: Params, plan: Plan, v, db) -> list[np.ndarray]:
+    """Decrypted slots every output ciphertext must hold."""
+    blocks = closed_form(par, plan, v, db)
+    outs = []
+    for c in range(plan.n_out):
+        s = np.zeros(par.N, dtype=np.uint64)
+        if plan.G == 1:
+            for o in range(plan.per_out):
+                for rho in range(2):
+                    base = rho * par.m + o * plan.s_prime
+                    s[base:base + plan.s_prime] = blocks[0, rho]
+        else:
+            for gamma in range(c * plan.per_out, min((c + 1) * plan.per_out, plan.G)):
+                o = gamma - c * plan.per_out
+                for rho in range(2):
+                    base = rho * par.m + o * plan.s_prime
+                    s[base:base + plan.s_prime] = blocks[gamma, rho]
+        outs.append(s)
+    return outs
+
+
+# ---------------------------------------------------------------- Decomp ----
+
+class DecodeError(Exception):
+    pass
+
+
+def newton_coefficients(w, t: int) -> list[int]:
+    """Alg. 1 step 1: a_0 = 1, a_k = k^{-1} sum_{i=1}^{k} (-1)^{i-1} a_{k-i} w_i
+    (mod t), from the power sums w_1..w_s (Lem. 1)."""
+    s = len(w)
+    a = [1]
+    for k in range(1, s + 1):
+        acc = 0
+        for i in range(1, k + 1):
+            term = a[k - i] * int(w[i - 1])
+            acc += term if i % 2 == 1 else -term
+        a.append(acc * pow(k, -1, t) % t)
+    return a
+
+
+def f_from_coefficients(a, t: int) -> list[int]:
+    """f(X) = sum_{k=0}^{s} (-1)^k a_k X^{s-k}; returned lowest degree first."""
+    s = len(a) - 1
+    f = [0] * (s + 1)
+    for k in range(s + 1):
+        f[s - k] = (a[k] if k % 2 == 0 else -a[k]) % t
+    return f
+
+
+def strip_x(f) -> list[int]:
+    """Divide by X while X divides f (Alg. 1 step 2)."""
+    i = 0
+    while i < len(f) - 1 and f[i] == 0:
+        i += 1
+    return list(f[i:])
+
+
+def roots_bruteforce(g, lo: int, hi: int, t: int) -> list[int]:
+    """All x in [lo, hi] with g(x) = 0 mod t, by evaluating g everywhere."""
+    x = np.arange(lo, hi + 1, dtype=np.uint64)
+    acc = np.zeros_like(x)
+    tt = np.uint64(t)
+    for c in reversed(g):
+        acc = (acc * x + np.uint64(c)) % tt
+    return [int(r) for r in x[acc == 0]]
+
+
+def solve_mod(A, b, t: int):
+    """Gaussian elimination mod t for a square nonsingular system."""
+    n = len(A)
+    M = [[int(A[i][j]) % t for j in range(n)] + [int(b[i]) % t] for i in range(n)]
+    for col in range(n):
+        piv = next((r for r in range(col, n) if M[r][col]), None)
+        if piv is None:
+            raise DecodeError("singular system")
+        M[col], M[piv] = M[piv], M[col]
+        inv = pow(M[col][col], -1, t)
+        M[col] = [x * inv % t for x in M[col]]
+        for r in range(n):
+            if r != col and M[r][col]:
+                f = M[r][col]
+                M[r] = [(x - f * y) % t for x, y in zip(M[r], M[col])]
+    return [M[i][n] for i in range(n)]
+
+
+def reconst_idx(w, t: int, max_node: int) -> list[int]:
+    """Alg. 1: the nodes whose power sums are w."""
+    g = strip_x(f_from_coefficients(newton_coefficients(w, t), t))
+    deg = len(g) - 1
+    if deg == 0:
+        return []
+    roots = roots_bruteforce(g, 1, max_node, t)
+    if len(roots) != deg:
+        raise DecodeError(f"found {len(roots)} roots for degree {deg}")
+    return roots
+
+
+def reconst(e, nodes, t: int) -> list[int]:
+    """Alg. 4: solve C_hat x = e on the recovered columns (rows 1..l square,
+    the remaining rows must agree)."""
+    l = len(nodes)
+    if l == 0:
+        if any(int(x) % t for x in e):
+            raise DecodeError("nonzero values without indices")
+        return []
+    A = [[pow(a, j + 1, t) for a in nodes] for j in range(l)]
+    x = solve_mod(A, [int(v) for v in e[:l]], t)
+    for j in range(l, len(e)):
+        if sum(pow(a, j + 1, t) * xi for a, xi in zip(nodes, x)) % t != int(e[j]) % t:
+            raise DecodeError("inconsistent compressed values")
+    return x
+
+
+def decomp_slots(par: Params, plan: Plan, out_slots) -> list[tuple[int, int]]:
+    """Alg. 6 on decrypted output slots: sorted (record index, value) pairs."""
+    res = []
+    for gamma in range(plan.G):
+        c, o = divmod(gamma, plan.per_out) if plan.G > 1 else (0, 0)
+        s = out_slots[c]
+        w = s[o * plan.s_prime:(o + 1) * plan.s_prime]
+        e = s[par.m + o * plan.s_prime: par.m + (o + 1) * plan.s_prime]
+        nodes = reconst_idx(w, par.t, plan.G_sz)
+        vals = reconst(e, nodes, par.t)
+        res.extend((gamma * plan.G_sz + a - 1, int(x)) for a, x in zip(nodes, vals))
+    return sorted(res)
+
+
+def decomp(par: Params, sk, plan: Plan, outs) -> list[tuple[int, int]]:
+    """Client-side Recover: decrypt the answer, then decompress."""
+    return decomp_slots(par, plan, [decrypt(par, sk, ct) for ct in outs])

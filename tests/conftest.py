@@ -1,0 +1,13 @@
+"""Shared pytest setup: the `gpu` marker and import paths."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line(
+        "markers", "gpu: needs a CUDA GPU and the compiled library (sm_103a)")
+    config.addinivalue_line("markers", "slow: long CPU-side oracle run")

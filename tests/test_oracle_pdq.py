@@ -1,0 +1,202 @@
+"""Pins for the oracle's Mask / Comp / Decomp (no GPU).
+
+The Comp ciphertext is not unique, so its slots are pinned: they must decrypt
+to C v and C d computed straight from Eq. 1 with Python integers.  The
+diagonal (Pegasus) algebra is pinned in the clear against an explicit matrix
+product, Newton's identity against brute-force elementary symmetric
+polynomials, and Decomp by exhaustive enumeration on tiny inputs."""
+import itertools
+import random
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import bfv, pdq
+
+
+def build(cfg_name, seed=None):
+    cfg = W.CONFIGS[cfg_name]
+    par = bfv.Params.from_config(cfg)
+    qi = W.draw_query(cfg, seed)
+    plan = pdq.make_plan(par, cfg.n, cfg.s)
+    ks = pdq.galois_elements(par, plan)
+    kr = W.rotation_key_randomness(par.ext, par.N, len(par.digits), ks, cfg.seed)
+    keys = {k: bfv.rotation_key(par, qi.sk, k, *kr[k]) for k in ks}
+    a, e = W.encryption_randomness(par.q, par.N, plan.J, cfg.seed)
+    v_cts = pdq.encrypt_index(par, qi.sk, qi.v, plan, a, e)
+    return cfg, par, qi, plan, keys, v_cts
+
+
+def matrix_C(s_prime, nodes, t):
+    """Eq. 1: C[j][i] = nodes[i]^(j+1) mod t."""
+    return [[pow(int(a), j + 1, t) for a in nodes] for j in range(s_prime)]
+
+
+def test_plan_shapes_match_cost_model():
+    # (config) -> (s', B, J, half-blocks, groups, outputs, #galois)
+    want = {"c1": (16, 4, 1, 2, 1, 1, 14), "c2": (64, 8, 8, 16, 1, 1, 21),
+            "c3": (256, 16, 32, 64, 16, 1, 37)}
+    for name, w in want.items():
+        cfg = W.CONFIGS[name]
+        par = bfv.Params.from_config(cfg)
+        plan = pdq.make_plan(par, cfg.n, cfg.s)
+        got = (plan.s_prime, plan.B, plan.J, plan.H, plan.G, plan.n_out,
+               len(pdq.galois_elements(par, plan)))
+        assert got == w, name
+
+
+def test_paper_single_ciphertext_answer():
+    """Sec. 6 (footnote on communication): with N = 2^13 and t = 65537 the
+    answer is one ciphertext unless s exceeds N/2 = 4096 slots per row."""
+    par = bfv.Params(13, 65537, 54, 2, 1, 2)
+    for n in (1 << 13, 1 << 14, 1 << 15, 1 << 16):
+        for s in (8, 16, 32, 64, 128):
+            assert pdq.make_plan(par, n, s).n_out == 1
+    assert pdq.make_plan(par, 1 << 14, 4096).n_out == 1
+    with pytest.raises(ValueError):
+        pdq.make_plan(par, 1 << 14, 4097)
+
+
+@pytest.mark.parametrize("cfg_name", ["tiny", "tiny2", "grouped", "small"])
+def test_closed_form_is_matrix_C(cfg_name):
+    cfg = W.CONFIGS[cfg_name]
+    par = bfv.Params.from_config(cfg)
+    qi = W.draw_query(cfg)
+    plan = pdq.make_plan(par, cfg.n, cfg.s)
+    cf = pdq.closed_form(par, plan, qi.v, qi.db)
+    t = par.t
+    for gamma in range(plan.G):
+        lo, hi = gamma * plan.G_sz, min((gamma + 1) * plan.G_sz, cfg.n)
+        nodes = list(range(1, hi - lo + 1))
+        C = matrix_C(plan.s_prime, nodes, t)
+        v = [int(x) for x in qi.v[lo:hi]]
+        d = [int(x) * int(y) % t for x, y in zip(qi.v[lo:hi], qi.db[lo:hi])]
+        assert cf[gamma, 0].tolist() == [sum(c * x for c, x in zip(row, v)) % t for row in C]
+        assert cf[gamma, 1].tolist() == [sum(c * x for c, x in zip(row, d)) % t for row in C]
+
+
+@pytest.mark.parametrize("cfg_name", ["tiny", "grouped"])
+def test_diagonal_bsgs_in_the_clear(cfg_name):
+    """The extended diagonals, baby/giant split and rotate-and-sum reproduce
+    C u in the clear (Sec. 5.2), for every half-block and group."""
+    cfg = W.CONFIGS[cfg_name]
+    par = bfv.Params.from_config(cfg)
+    plan = pdq.make_plan(par, cfg.n, cfg.s)
+    t, m, sp, B = par.t, par.m, plan.s_prime, plan.B
+    rng = np.random.default_rng(5)
+    u = [rng.integers(0, t, size=par.N, dtype=np.uint64) for _ in range(plan.H)]
+    for gamma in range(plan.G):
+        y = np.zeros(par.N, dtype=np.uint64)
+        for g in range(plan.giants):
+            acc = np.zeros(par.N, dtype=np.uint64)
+            for h in pdq.group_halfblocks(plan, gamma):
+                for a in range(B):
+                    d = pdq.rot_slots(par, pdq.diagonal_slots(par, plan, h, g * B + a), -g * B)
+                    acc = (acc + d * pdq.rot_slots(par, u[h], a)) % t
+            y = (y + pdq.rot_slots(par, acc, g * B)) % t
+        l = sp
+        while l < m:
+            y = (y + pdq.rot_slots(par, y, l)) % t
+            l *= 2
+        # explicit product with the group's block of C, both rows
+        for rho in range(2):
+            want = [0] * sp
+            for h in pdq.group_halfblocks(plan, gamma):
+                for x in range(m):
+                    node = (h * m + x) % plan.G_sz + 1
+                    val = int(u[h][rho * m + x])
+                    for j in range(sp):
+                        want[j] = (want[j] + pow(node, j + 1, t) * val) % t
+            row = y[rho * m:(rho + 1) * m]
+            for o in range(m // sp):
+                assert row[o * sp:(o + 1) * sp].tolist() == want
+
+
+@pytest.mark.parametrize("cfg_name", ["tiny", "tiny2"])
+def test_mask_and_pack_decrypt(cfg_name):
+    cfg, par, qi, plan, keys, v_cts = build(cfg_name)
+    masked = pdq.mask(par, v_cts, qi.db, plan)
+    t = par.t
+    for j in range(plan.J):
+        v = pdq.record_slots(par, qi.v, j)
+        d = v * pdq.record_slots(par, qi.db, j) % t
+        top, bot = pdq.row_mask_slots(par, 0), pdq.row_mask_slots(par, 1)
+        want = [v * top, v * bot, d * top, d * bot]
+        for idx in range(4):
+            assert np.array_equal(bfv.decrypt(par, qi.sk, masked[4 * j + idx]), want[idx])
+    u = pdq.pack(par, masked, keys, plan)
+    for h in range(plan.H):
+        rec = np.arange(h * par.m, (h + 1) * par.m)
+        vh = np.zeros(par.m, dtype=np.uint64)
+        dh = np.zeros(par.m, dtype=np.uint64)
+        ok = rec < cfg.n
+        vh[ok] = qi.v[rec[ok]]
+        dh[ok] = qi.v[rec[ok]].astype(np.uint64) * qi.db[rec[ok]] % t
+        assert np.array_equal(bfv.decrypt(par, qi.sk, u[h]), np.concatenate([vh, dh]))
+
+
+@pytest.mark.parametrize("cfg_name", ["tiny", "tiny2", "grouped", "small", "c1"])
+def test_answer_decrypts_to_closed_form_and_decompresses(cfg_name):
+    cfg, par, qi, plan, keys, v_cts = build(cfg_name)
+    outs = pdq.answer(par, v_cts, qi.db, keys, plan)
+    assert len(outs) == plan.n_out
+    exp = pdq.expected_slots(par, plan, qi.v, qi.db)
+    for ct, want in zip(outs, exp):
+        assert np.array_equal(bfv.decrypt(par, qi.sk, ct), want)
+        assert bfv.noise_budget_bits(par, qi.sk, ct) > 10
+    got = pdq.decomp(par, qi.sk, plan, outs)
+    assert got == [(int(i), int(qi.db[i])) for i in qi.positions]
+
+
+def test_newton_against_elementary_symmetric_bruteforce():
+    t = 65537
+    rnd = random.Random(4)
+    for size in range(0, 9):
+        xs = rnd.sample(range(1, 2000), size)
+        s = 12
+        w = [sum(pow(x, k, t) for x in xs) % t for k in range(1, s + 1)]
+        a = pdq.newton_coefficients(w, t)
+        for k in range(s + 1):
+            ek = sum(np.prod([x for x in c], dtype=object) for c in itertools.combinations(xs, k)) \
+                if k <= size else 0
+            assert a[k] == int(ek) % t
+        f = pdq.f_from_coefficients(a, t)          # prod over the multiset (X - x) X^{s-size}
+        for x in xs + [0]:
+            assert sum(c * pow(x, i, t) for i, c in enumerate(f)) % t == 0
+        assert sorted(pdq.reconst_idx(w, t, 2000)) == sorted(xs)
+
+
+def test_decomp_exhaustive_tiny():
+    """Every s-sparse (v, d) with s <= 3 on n = 16 records decodes uniquely
+    (records may hold the value 0)."""
+    t, n, sp = 257, 16, 4
+    rnd = random.Random(5)
+    for size in range(0, 4):
+        for idx in itertools.combinations(range(n), size):
+            vals = [rnd.randrange(t) for _ in idx]
+            nodes = [i + 1 for i in idx]
+            w = [sum(pow(a, j + 1, t) for a in nodes) % t for j in range(sp)]
+            e = [sum(pow(a, j + 1, t) * x for a, x in zip(nodes, vals)) % t for j in range(sp)]
+            got_nodes = pdq.reconst_idx(w, t, n)
+            assert got_nodes == nodes
+            assert pdq.reconst(e, got_nodes, t) == vals
+
+
+def test_decomp_single_match_closed_form():
+    """s' = 1: the index is w_1 and the value e_1 / w_1."""
+    t = 65537
+    for node, val in [(1, 0), (7, 5), (65536, 65536), (300, 12)]:
+        w = [node % t]
+        e = [node * val % t]
+        assert pdq.reconst_idx(w, t, 65536) == [node]
+        assert pdq.reconst(e, [node], t) == [val * 1 % t]
+
+
+def test_decomp_detects_overflow():
+    """More matches than s' do not decode to a wrong answer silently."""
+    t, sp = 65537, 4
+    nodes = [3, 10, 77, 1000, 5000, 12345]
+    w = [sum(pow(a, j + 1, t) for a in nodes) % t for j in range(sp)]
+    with pytest.raises(pdq.DecodeError):
+        pdq.reconst_idx(w, t, 65536)
