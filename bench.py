@@ -1,0 +1,350 @@
+"""Benchmark: Mask+Comp queries/s and p50/p99 latency of the private database
+query answer at N = 2^15 (8 x 60-bit ciphertext primes + 2 special primes, 4
+key-switching digits), n = 2^20 records, s = 256 clustered matches: one query
+per step on one GPU, database plaintexts, diagonals and rotation keys
+resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pdq|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank answers its own
+queries (replicas; the method has no cross-GPU exchange), rank 0 prints.
+``--impl reference`` times the CPU oracle on the host cores instead (a
+bounded sample per step, see ``oracle_sample``).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mask+Comp queries/sec and p50/p99 latency at N=2^15, batched vs plain"
+WORKLOAD = "c3"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pdq", choices=["pdq", "reference"])
+    ap.add_argument("--config", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+def config_dict(cfg, extra=None):
+    d = {"workload": f"{cfg.name}: plain single query, BFV N=2^{cfg.log_n}, t={cfg.t}, "
+                     f"{cfg.L}x{cfg.prime_bits}-bit + {cfg.K} special primes (dnum={cfg.dnum}), "
+                     f"n={cfg.n} records, s={cfg.s} {cfg.pattern} matches",
+         "N": cfg.N, "n": cfg.n, "s": cfg.s, "L": cfg.L, "K": cfg.K, "dnum": cfg.dnum,
+         "t": cfg.t, "queries_per_step": 1, "mode": "plain (one query at a time)",
+         "l2": "inputs larger than L2 (2 GiB of diagonals, 128 MiB query, 128 MiB database, "
+               "740 MiB keys read per query)"}
+    d.update(extra or {})
+    return d
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------- CPU oracle sample --
+
+def oracle_sample(cfg, budget_s: float = 20.0) -> dict:
+    """Time the CPU oracle on a bounded sample of the workload and scale it to
+    one query with the schedule's operation counts: one full key switch, one
+    hoisted raise, one hoisted rotation, a plaintext-ciphertext product (Mask)
+    and multiply-accumulate products (diagonal MAC) at full size."""
+    import numpy as np
+    import workloads as W
+    from oracle import bfv, pdq as opdq
+
+    par = bfv.Params.from_config(cfg)
+    plan = opdq.make_plan(par, cfg.n, cfg.s)
+    sk = W.draw_ternary(par.N, W.rng_for(cfg.seed, 3))
+    a, e = W.encryption_randomness(par.q, par.N, 1, cfg.seed)
+    ct = bfv.encrypt(par, sk, bfv.encode(par, np.arange(par.N) % par.t), a[0], e[0])
+    k = par.galois_rot(1)
+    kr = W.rotation_key_randomness(par.ext, par.N, len(par.digits), [k], cfg.seed)
+    key = bfv.rotation_key(par, sk, k, *kr[k])
+    pt = opdq.lifted_pt(par, np.arange(par.N) % par.t)
+    t0 = time.perf_counter()
+    raised = bfv.mod_up_all(par, ct[1])
+    t_raise = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bfv.rotate_hoisted(par, ct, raised, k, key)
+    t_apply = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bfv.pt_mul(par, ct, pt)
+    t_ptmul = time.perf_counter() - t0
+    nmac = 4
+    t0 = time.perf_counter()
+    opdq.ring_dot(par, [pt] * nmac, [ct] * nmac)
+    t_mac = (time.perf_counter() - t0) / nmac
+    n_full_ks = plan.H + plan.G * (plan.giants - 1) + plan.G * int(np.log2(par.m // plan.s_prime))
+    n_raise_hoisted = plan.H if plan.B > 1 else 0
+    n_apply_hoisted = plan.H * (plan.B - 1)
+    n_mac = plan.H * plan.B * plan.giants
+    n_mask = 4 * plan.J
+    per_query = (n_full_ks * (t_raise + t_apply) + n_raise_hoisted * t_raise
+                 + n_apply_hoisted * t_apply + n_mac * t_mac + n_mask * t_ptmul)
+    sampled = t_raise + t_apply + t_ptmul + nmac * t_mac
+    return {"value": 1.0 / per_query, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle timed on one full-size key-switch raise ({t_raise:.2f} s), one "
+                       f"rotation ({t_apply:.2f} s), one Mask product ({t_ptmul:.2f} s) and "
+                       f"{nmac} diagonal MAC products ({t_mac:.2f} s each), scaled by the "
+                       f"schedule's counts per query ({n_full_ks} full key switches, "
+                       f"{n_raise_hoisted} hoisted raises, {n_apply_hoisted} hoisted rotations, "
+                       f"{n_mac} MAC products, {n_mask} Mask products) = {per_query:.0f} s "
+                       f"per query; {sampled:.1f} s sampled, single thread"),
+            "seconds_per_query": per_query}
+
+
+def run_reference(args, cfg, rank: int):
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(cfg)
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(cfg)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * wall / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64 (exact modular integers)",
+            "data": "synthetic", "config": config_dict(cfg),
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm --
+
+def run_gpu(args, cfg, rank: int, world: int):
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2408_17063_gb300 import build, pdq
+
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    ctx = pdq.Context.from_config(cfg)
+    q = W.draw_query(cfg, cfg.seed + rank)
+    plan = ctx.plan(cfg.n, cfg.s)
+    galois = ctx.plan_galois(plan)
+    sk = ctx.secret_prepare(torch.from_numpy(q.sk))
+    N = ctx.N
+    # rotation keys, database, diagonals: resident
+    keys = ctx._u64(len(galois) * ctx.key_elems)
+    kv = keys.view(len(galois), -1)
+    kr = W.rotation_key_randomness(ctx.moduli, N, ctx.ndigits, galois, cfg.seed + rank)
+    for i, k in enumerate(galois):
+        a, e = kr[k]
+        ctx.rotkey_gen(sk, k, torch.from_numpy(a.view(np.int64)).cuda(),
+                       torch.from_numpy(e).cuda(), out=kv[i])
+    db = ctx.db_encode(torch.from_numpy(q.db.astype(np.int32)).cuda())
+    consts = ctx.plan_constants(plan)
+    # the query: encrypted index vector
+    a, e = W.encryption_randomness(ctx.moduli[:ctx.L], N, plan.J, cfg.seed + rank)
+    v = np.zeros(plan.J * N, dtype=np.int32)
+    v[:cfg.n] = q.v
+    v_cts = ctx.encrypt(sk, torch.from_numpy(v).cuda(), torch.from_numpy(a.view(np.int64)).cuda(),
+                        torch.from_numpy(e).cuda())
+    ws = ctx.answer_workspace(plan)
+    out = ctx._u64(plan.n_out * ctx.ct_elems)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+
+    def step():
+        ctx.answer(plan, v_cts, db, keys, galois, consts, ws=ws, out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness of what is timed: decrypt and decompress the answer
+    slots = ctx.decrypt(sk, out).cpu().numpy()
+    got = ctx.decomp(plan, slots)
+    truth = [(int(i), int(q.db[i])) for i in q.positions]
+    if got != truth:
+        raise SystemExit("benchmark answer does not decompress to the query result")
+
+    clocks = ClockSampler(local)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.profile_enable(True)
+    launches0 = pdq.pdq_launch_count()
+    clocks.start()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = pdq.pdq_launch_count() - launches0
+    clk = clocks.stop()
+    stages = ctx.profile_read()
+    ctx.profile_enable(False)
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # end to end through the host-buffer entry point (pinned host buffers,
+    # coefficient form, copies inside the timed region)
+    vc = v_cts.clone()
+    ctx.ntt_inverse(vc, 2 * plan.J, ctx.L)
+    v_host = vc.cpu().pin_memory()
+    del vc
+    out_host = torch.empty(plan.n_out * ctx.ct_elems, dtype=torch.int64).pin_memory()
+    ws_host = ctx.answer_host_workspace(plan)
+    del ws
+    for _ in range(2):
+        ctx.answer_host(plan, v_host, db, keys, galois, consts, out_host, ws=ws_host, stream=stream)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.answer_host(plan, v_host, db, keys, galois, consts, out_host, ws=ws_host, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": "queries/s",
+           "h2d_bytes_per_step": v_host.numel() * 8, "d2h_bytes_per_step": out_host.numel() * 8,
+           "steps": args.e2e_steps, "entry_point": "pdq_answer_host"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    # roofline of the diagonal multiply-accumulate kernel (one launch per query)
+    mac_ms, mac_calls = stages["mac"]
+    mac_ms_per = mac_ms / max(1, mac_calls)
+    L, E = ctx.L, ctx.E
+    mac_bytes = 8 * N * L * (plan.H * plan.B * 2 + plan.hclass * plan.giants * plan.B
+                             + plan.G * plan.giants * 2)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = mac_bytes / (mac_ms_per / 1000.0) / 1e9
+    roofline = {"kernel": "k_diag_mac", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "bytes_per_launch": mac_bytes, "ms_per_launch": mac_ms_per,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s"}
+    ms_sorted = sorted(per)
+    p50 = statistics.median(per)
+    p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]
+    line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64 (exact modular integers)", "data": "synthetic",
+            "config": config_dict(cfg, {"parallelism": f"replicas x{world}"}),
+            "latency_ms": {"p50": p50, "p99": p99, "min": ms_sorted[0], "max": ms_sorted[-1]},
+            "stages_ms_per_query": {k: v[0] / max(1, args.steps) for k, v in stages.items()},
+            "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps,
+            "clocks": clk, "e2e": e2e, "roofline": roofline}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in oracle_sample(cfg).items()
+                                if k != "seconds_per_query"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    import workloads as W
+    cfg = W.CONFIGS[args.config]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, cfg, rank)
+        return
+    run_gpu(args, cfg, rank, world)
+
+
+if __name__ == "__main__":
+    main()

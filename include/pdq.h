@@ -1,0 +1,273 @@
+/*
+ * pdq.h -- C ABI of the GB300 library for the server-side hot path of the
+ * HE-based private database query of "SIMD-Aware Homomorphic Compression and
+ * Application to Private Database Query" (arXiv 2408.17063).
+ *
+ * The path is Answer = Mask -> Comp (Alg. 7): the client's encrypted 0/1
+ * index vector v (the output of Match) is multiplied slot-wise with the
+ * database, and the masked ciphertexts are compressed by the homomorphic
+ * matrix-vector product with the power-sum matrix C[j][i] = i^j (Eq. 1) in
+ * the SIMD form of Sec. 5.2: u = [v; d] packing, Pegasus diagonals with
+ * baby-step/giant-step rotations on both rows, blocks summed before one
+ * rotate-and-sum.  The client decompresses with Newton's identity, root
+ * finding and a Vandermonde solve (Alg. 1, 4, 6).
+ *
+ * Notation: N is the ring dimension (the paper's n), n the number of records
+ * (the paper's N), t the plaintext prime (the paper's p), m = N/2 slots per
+ * row, s' = 2^ceil(log2 s) the compressed length per row.
+ *
+ * Conventions for every call:
+ *  - Return value: PDQ_OK (0) or an error code; pdq_last_error() gives a
+ *    message for the calling thread.  No call throws across the ABI.
+ *  - "dev" pointers are CUDA device pointers, "host" pointers host memory.
+ *    The caller owns every buffer it passes; the library never frees them.
+ *    The context owns only its own tables (allocated in pdq_ctx_create).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued asynchronously on it unless a call says otherwise; buffers must
+ *    stay valid until the stream reaches that point.
+ *  - Residues are uint64 in [0, q).  A polynomial over the ciphertext primes
+ *    is [L][N] (limb-major); over the extended basis [L+K][N] (the L
+ *    ciphertext primes first, then the K special primes).  A ciphertext is
+ *    [2][L][N]; J ciphertexts are contiguous, [J][2][L][N].  Device-side
+ *    ciphertexts, keys and plaintexts are in the library's transform
+ *    (evaluation) domain ("NTT form"); pdq_ntt_inverse gives coefficient
+ *    form, which is what is compared with other implementations.
+ *  - Slots of one plaintext are [N] uint32 with slot (row rho, column c) at
+ *    index rho*m + c; record i of a database sits in ciphertext floor(i/N),
+ *    slot i mod N.
+ */
+#ifndef PDQ_H
+#define PDQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PDQ_OK 0
+#define PDQ_E_PARAM 1    /* invalid argument or unsupported size */
+#define PDQ_E_NOMEM 2    /* workspace too small or allocation failed */
+#define PDQ_E_CUDA 3     /* CUDA runtime error (message has the detail) */
+#define PDQ_E_DECODE 4   /* Decomp found no consistent sparse answer */
+#define PDQ_E_KEY 5      /* a needed rotation key is missing */
+
+#define PDQ_MAX_MODULI 40
+
+typedef struct pdq_ctx pdq_ctx;
+
+/* Parameter set (Sec. 5.1: ring X^N+1 with N a power of two, t = 1 mod 2N). */
+typedef struct {
+    uint32_t log_n;       /* N = 2^log_n, 3 <= log_n <= 16 */
+    uint32_t prime_bits;  /* every RNS prime is < 2^prime_bits (<= 60) */
+    uint32_t L;           /* ciphertext primes */
+    uint32_t K;           /* special primes for hybrid key switching */
+    uint32_t dnum;        /* key-switching digits: ceil(L / ceil(L/dnum)) */
+    uint32_t reserved;
+    uint64_t t;           /* plaintext prime, t = 1 mod 2N, t < 2^31 */
+} pdq_params;
+
+typedef struct {
+    uint32_t N, L, K, ndigits;
+    uint64_t t;
+    uint64_t zeta;                      /* slot root mod t */
+    uint64_t moduli[PDQ_MAX_MODULI];    /* q_0..q_{L-1}, p_0..p_{K-1} */
+    uint64_t psi[PDQ_MAX_MODULI];       /* transform root (order 2N) per
+                                           modulus; index L+K is t (= zeta) */
+} pdq_info;
+
+/* Layout of one query's compression (Sec. 5.2 with the readings below).
+ * Records are split into groups of G_sz = N*floor((t-1)/N) consecutive
+ * records so that the nodes 1..G_sz of Eq. 1 stay distinct mod t (the paper
+ * assumes t > n); group gamma's (Cv, Cd) block lands in output ciphertext
+ * floor(gamma/per_out) at slot offset (gamma mod per_out)*s'. */
+typedef struct {
+    uint64_t n;          /* records */
+    uint32_t s;          /* sparsity bound (matches per group) */
+    uint32_t s_prime;    /* 2^ceil(log2 s) */
+    uint32_t B;          /* baby steps (divides s') */
+    uint32_t giants;     /* s'/B */
+    uint32_t J;          /* index-vector ciphertexts ceil(n/N) */
+    uint32_t H;          /* half-blocks = u ciphertexts = 2J */
+    uint32_t G_sz;       /* records per group */
+    uint32_t hpg;        /* half-blocks per group */
+    uint32_t G;          /* groups */
+    uint32_t hclass;     /* distinct diagonal sets = min(hpg, H) */
+    uint32_t per_out;    /* groups per output ciphertext = m/s' */
+    uint32_t n_out;      /* output ciphertexts */
+} pdq_plan;
+
+/* ---------------------------------------------------------------- context */
+
+/* Build the prime chain, transform tables, slot permutation and key-switching
+ * constants on the current device.  Synchronous.  *out is owned by the
+ * caller and released with pdq_ctx_destroy.  Errors: PDQ_E_PARAM for
+ * unsupported sizes, PDQ_E_NOMEM / PDQ_E_CUDA on device failures. */
+int pdq_ctx_create(const pdq_params* params, pdq_ctx** out);
+int pdq_ctx_destroy(pdq_ctx* ctx);
+int pdq_ctx_info(const pdq_ctx* ctx, pdq_info* info);
+const char* pdq_last_error(void);
+
+/* ------------------------------------------------------------- transforms
+ * Negacyclic transform of polynomials in Z_q[X]/(X^N+1) (the ring of
+ * Sec. 5.1), in place on `count` groups of `nlimbs` limbs: group g, limb l is
+ * at data + g*stride + l*N (uint64 elements) and uses extended-basis modulus
+ * limb0 + l (index L+K is the plaintext prime t).  dev data. */
+int pdq_ntt_forward(const pdq_ctx* ctx, uint64_t* data, uint32_t count, uint32_t nlimbs,
+                    uint32_t limb0, uint64_t stride, void* stream);
+int pdq_ntt_inverse(const pdq_ctx* ctx, uint64_t* data, uint32_t count, uint32_t nlimbs,
+                    uint32_t limb0, uint64_t stride, void* stream);
+
+/* ------------------------------------------------------- encode / keys
+ * Encode `count` slot vectors (dev [count][N] uint32, values < t) into
+ * NTT-form plaintexts over the first nlimbs extended-basis primes (dev
+ * pt_out [count][nlimbs][N]): interpolation mod t at the slot roots
+ * (Sec. 5.1), centred lift to (-t/2, t/2], forward transform. */
+int pdq_encode(const pdq_ctx* ctx, const uint32_t* slots, uint32_t count, uint32_t nlimbs,
+               uint64_t* pt_out, void* stream);
+
+/* Ternary secret (dev [N] int8 in {-1,0,1}) -> NTT form over the extended
+ * basis (dev sk_out [L+K][N]). */
+int pdq_secret_prepare(const pdq_ctx* ctx, const int8_t* s, uint64_t* sk_out, void* stream);
+
+/* Symmetric BFV encryption of `count` slot vectors (HE Enc, Sec. 2.2):
+ * c1 = a, c0 = -a*s + e + floor(Q/t)*m.  The caller supplies the
+ * randomness: a = dev [count][L][N] uniform residues in coefficient form,
+ * e = dev [count][N] small integers.  ct_out: dev [count][2][L][N]. */
+int pdq_encrypt(const pdq_ctx* ctx, const uint64_t* sk, const uint32_t* slots, uint32_t count,
+                const uint64_t* a, const int32_t* e, uint64_t* ct_out, void* stream);
+
+/* Hybrid key-switching key from sigma_k(s) to s for the Galois element
+ * `galois` (k odd, < 2N; Rot_row(.; r) is k = 3^r, Rot_col is k = 2N-1):
+ * per digit beta, b = -a*s + e + [q_i in beta] * P * sigma_k(s).  a: dev
+ * [ndigits][L+K][N] uniform coefficient form, e: dev [ndigits][N].
+ * key_out: dev [ndigits][2][L+K][N] NTT form. */
+int pdq_rotkey_gen(const pdq_ctx* ctx, const uint64_t* sk, uint64_t galois, const uint64_t* a,
+                   const int32_t* e, uint64_t* key_out, void* stream);
+
+/* HE Dec + decode (Sec. 2.2, Alg. 6 first line): m = round(t [c0 + c1 s]_Q / Q)
+ * mod t, then the slot values.  ct: dev [count][2][L][N]; slots_out: dev
+ * [count][N] uint32.  Needs a workspace of pdq_decrypt_workspace_bytes. */
+size_t pdq_decrypt_workspace_bytes(const pdq_ctx* ctx, uint32_t count);
+int pdq_decrypt(const pdq_ctx* ctx, const uint64_t* sk, const uint64_t* ct, uint32_t count,
+                uint32_t* slots_out, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------- homomorphic rotation
+ * ct_out[i] = sigma_k(ct_in[i]) followed by hybrid key switching with `key`
+ * (the key for `galois`), for i < count (Rot_row / Rot_col of Sec. 5.1).
+ * The raised digits of c1 are computed before the automorphism.  ct_in and
+ * ct_out: dev [count][2][L][N], may not overlap.  Workspace:
+ * pdq_rotate_workspace_bytes(count). */
+size_t pdq_rotate_workspace_bytes(const pdq_ctx* ctx, uint32_t count);
+int pdq_rotate(const pdq_ctx* ctx, const uint64_t* ct_in, uint32_t count, uint64_t galois,
+               const uint64_t* key, uint64_t* ct_out, void* ws, size_t ws_bytes, void* stream);
+
+/* ----------------------------------------------------------------- plans
+ * Fill the layout for n records and sparsity s; B = 0 picks
+ * 2^ceil(log2(s')/2).  Errors: PDQ_E_PARAM if s' > N/2, s' >= t or B does
+ * not divide s'. */
+int pdq_plan_make(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B, pdq_plan* plan);
+
+/* The Galois elements of every rotation the plan uses, ascending (host
+ * out[cap]); *count receives how many there are.  The key buffer passed to
+ * pdq_comp holds one key per element in this order. */
+int pdq_plan_galois(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out, uint32_t cap,
+                    uint32_t* count);
+
+/* Query-independent constants of a plan: the extended diagonals
+ *   D_{h,k}[c] = alpha(h m + ((c+k) mod m))^{(c mod s')+1} mod t,
+ * alpha(i) = (i mod G_sz) + 1, rotated by -gB for k = gB + a, encoded on both
+ * rows (Sec. 5.2: "encoding C twice"), for the hclass distinct half-block
+ * classes; then the group masks.  dev out of pdq_plan_constants_bytes. */
+size_t pdq_plan_constants_bytes(const pdq_ctx* ctx, const pdq_plan* plan);
+int pdq_plan_constants_build(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out,
+                             void* stream);
+
+/* Database plaintexts: for each index ciphertext j, DB_j . [1;0] and
+ * DB_j . [0;1] (the row masks of the u-packing remark of Sec. 5.2 folded
+ * into the database), NTT form.  values: dev [n] uint32 (< t).  db_out: dev
+ * [J][2][L][N] (pdq_db_bytes). */
+size_t pdq_db_bytes(const pdq_ctx* ctx, uint64_t n);
+int pdq_db_encode(const pdq_ctx* ctx, const uint32_t* values, uint64_t n, uint64_t* db_out,
+                  void* stream);
+
+/* ------------------------------------------------------------ hot path
+ * Mask (Alg. 7 step 2, with the row split of the u-packing remark): for each
+ * index ciphertext j, vT = v_j.[1;0], vB = v_j.[0;1], dT = v_j.(DB_j.[1;0]),
+ * dB = v_j.(DB_j.[0;1]).  v_cts: dev [J][2][L][N]; db from pdq_db_encode;
+ * masked_out: dev [J][4][2][L][N]. */
+int pdq_mask(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
+             const uint64_t* db, uint64_t* masked_out, void* stream);
+
+/* Comp (Alg. 7 step 3 in the SIMD form of Sec. 5.2): pack u_h = [v_h; d_h]
+ * with Rot_col, baby-step rotations of every u_h, diagonal multiply-
+ * accumulate per group and giant step, giant-step rotations, rotate-and-sum,
+ * group masks.  masked: dev output of pdq_mask; keys: dev, one key per
+ * element of pdq_plan_galois in that order ([nkeys][ndigits][2][L+K][N]);
+ * galois: host [nkeys]; consts from pdq_plan_constants_build.  out: dev
+ * [n_out][2][L][N], row 0 of group gamma's block = Cv, row 1 = Cd.
+ * Workspace: pdq_comp_workspace_bytes; too small -> PDQ_E_NOMEM. */
+size_t pdq_comp_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan);
+int pdq_comp(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* masked,
+             const uint64_t* keys, const uint64_t* galois, uint32_t nkeys,
+             const uint64_t* consts, uint64_t* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Answer = Mask then Comp on device buffers (Alg. 7 without Match).
+ * Workspace: pdq_answer_workspace_bytes (holds the masked ciphertexts too). */
+size_t pdq_answer_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan);
+int pdq_answer(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
+               const uint64_t* db, const uint64_t* keys, const uint64_t* galois,
+               uint32_t nkeys, const uint64_t* consts, uint64_t* out, void* ws,
+               size_t ws_bytes, void* stream);
+
+/* Answer with host buffers, end to end: copies the query ciphertexts (host
+ * [J][2][L][N], coefficient form) to the device, transforms them, runs
+ * Mask and Comp, transforms the answer back and copies it to out_host
+ * ([n_out][2][L][N], coefficient form).  Synchronises `stream` before
+ * returning.  Host buffers should be pinned for full copy bandwidth.
+ * Workspace: pdq_answer_host_workspace_bytes (device). */
+size_t pdq_answer_host_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan);
+int pdq_answer_host(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_host,
+                    const uint64_t* db, const uint64_t* keys, const uint64_t* galois,
+                    uint32_t nkeys, const uint64_t* consts, uint64_t* out_host, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- Decomp
+ * Client-side Decomp (Alg. 6) on decrypted answer slots (host [n_out][N]
+ * uint32): per group, Newton's identity on w (Alg. 1 step 1), strip the
+ * factors of X and find the roots among the nodes 1..G_sz (Alg. 1 step 2),
+ * solve the Vandermonde system on the recovered columns (Alg. 4) and check
+ * the remaining rows.  Writes up to cap (record index, value) pairs sorted by
+ * index to idx_out / val_out (host) and the total to *count.  Errors:
+ * PDQ_E_DECODE if a group's power sums are not those of at most s' nodes or
+ * the values are inconsistent, PDQ_E_NOMEM if cap is too small.  Host only,
+ * synchronous. */
+int pdq_decomp(const pdq_ctx* ctx, const pdq_plan* plan, const uint32_t* slots,
+               uint64_t* idx_out, uint32_t* val_out, uint64_t cap, uint64_t* count);
+
+/* -------------------------------------------------------- instrumentation
+ * Not part of the paper's method: counters for measuring the library.
+ * pdq_launch_count: kernels this library has launched in this process.
+ * pdq_profile_enable: when on, pdq_answer / pdq_comp record a CUDA event on
+ * their stream at every stage boundary (stages PDQ_STAGE_*); enabling resets
+ * the record.  pdq_profile_read waits for the recorded events, writes per
+ * stage the summed milliseconds (ms[nstages]) and call counts (calls, may be
+ * NULL), and clears the record. */
+#define PDQ_STAGE_MASK 0
+#define PDQ_STAGE_PACK 1
+#define PDQ_STAGE_BABY 2
+#define PDQ_STAGE_MAC 3
+#define PDQ_STAGE_GIANT 4
+#define PDQ_STAGE_ROTSUM 5
+#define PDQ_STAGE_COMBINE 6
+#define PDQ_NSTAGES 7
+unsigned long long pdq_launch_count(void);
+int pdq_profile_enable(pdq_ctx* ctx, int enable);
+int pdq_profile_read(pdq_ctx* ctx, float* ms, uint32_t* calls, uint32_t nstages);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDQ_H */

@@ -1,0 +1,406 @@
+// Comp and Answer (Alg. 7) in the SIMD form of Sec. 5.2, plus the C ABI
+// entry points of the library's device-side calls.
+//
+// Schedule (every key switch raises the digits of c1 before the
+// automorphism; additions are exact, so their order is free):
+//   1. pack   u_{2j} = vT_j + Rot_col(dT_j),  u_{2j+1} = Rot_col(vB_j) + dB_j
+//   2. baby   R[h][a] = Rot(u_h; a), a < B, digits of u_h raised once
+//   3. MAC    acc[gamma][g] = sum_{h in gamma} sum_a Rot(D_{h,gB+a}; -gB) . R[h][a]
+//   4. giant  y_gamma = sum_g Rot(acc[gamma][g]; gB)
+//   5. sum    y <- y + Rot(y; s' 2^l), l = 0 .. log2(m/s') - 1
+//   6. groups out_c = sum_o M_o . y_{c per_out + o}   (one group: out = y)
+#include <algorithm>
+#include <cstring>
+
+#include "pdq_internal.h"
+#include "pdq_ops.h"
+
+namespace pdq {
+
+namespace {
+
+const Ctx& C(const pdq_ctx* p) { return *reinterpret_cast<const Ctx*>(p); }
+
+u64 ct_elems(const Ctx& c) { return 2ull * c.L * c.N; }
+
+u32 ceil_log2(u64 x) {
+    u32 r = 0;
+    while ((1ull << r) < x) ++r;
+    return r;
+}
+
+int plan_make(const Ctx& c, u64 n, u32 s, u32 B, pdq_plan* pl) {
+    if (n == 0 || s == 0) return fail(PDQ_E_PARAM, "plan: n and s must be positive");
+    std::memset(pl, 0, sizeof(*pl));
+    const u64 sp = 1ull << ceil_log2(s);
+    if (sp > c.m || sp >= c.t) return fail(PDQ_E_PARAM, "plan: sparsity too large for the ring");
+    if (B == 0) B = 1u << ((ceil_log2(sp) + 1) / 2);
+    if (sp % B != 0 || B > 128) return fail(PDQ_E_PARAM, "plan: B must divide s' and be at most 128");
+    const u64 J = (n + c.N - 1) / c.N;
+    if (J > (1u << 20)) return fail(PDQ_E_PARAM, "plan: too many records");
+    const u64 G_sz = (u64)c.N * ((c.t - 1) / c.N);
+    const u64 hpg = G_sz / c.m;
+    const u64 H = 2 * J;
+    const u64 G = (H + hpg - 1) / hpg;
+    const u64 per_out = c.m / sp;
+    pl->n = n;
+    pl->s = s;
+    pl->s_prime = (u32)sp;
+    pl->B = B;
+    pl->giants = (u32)(sp / B);
+    pl->J = (u32)J;
+    pl->H = (u32)H;
+    pl->G_sz = (u32)G_sz;
+    pl->hpg = (u32)hpg;
+    pl->G = (u32)G;
+    pl->hclass = (u32)std::min(hpg, H);
+    pl->per_out = (u32)per_out;
+    pl->n_out = (u32)((G + per_out - 1) / per_out);
+    if (pl->giants > 32) return fail(PDQ_E_PARAM, "plan: at most 32 giant steps (choose a larger B)");
+    return PDQ_OK;
+}
+
+u64 galois_rot(const Ctx& c, long long r) {
+    const long long m = c.m;
+    long long rr = ((r % m) + m) % m;
+    return host_powmod(3, (u64)rr, 2ull * c.N);
+}
+
+std::vector<u64> plan_galois(const Ctx& c, const pdq_plan& pl) {
+    std::vector<u64> ks;
+    ks.push_back(2ull * c.N - 1);
+    for (u32 a = 1; a < pl.B; ++a) ks.push_back(galois_rot(c, a));
+    for (u32 g = 1; g < pl.giants; ++g) ks.push_back(galois_rot(c, (long long)g * pl.B));
+    for (u64 l = pl.s_prime; l < c.m; l *= 2) ks.push_back(galois_rot(c, (long long)l));
+    std::sort(ks.begin(), ks.end());
+    ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+    return ks;
+}
+
+bool valid_plan(const Ctx& c, const pdq_plan* pl) {
+    if (!pl) return false;
+    pdq_plan chk;
+    if (plan_make(c, pl->n, pl->s, pl->B, &chk) != PDQ_OK) return false;
+    return std::memcmp(&chk, pl, sizeof(chk)) == 0;
+}
+
+struct Keys {
+    const u64* base;
+    const u64* galois;
+    u32 n;
+    u64 keysz;
+    const u64* find(u64 k) const {
+        for (u32 i = 0; i < n; ++i)
+            if (galois[i] == k) return base + (u64)i * keysz;
+        return nullptr;
+    }
+};
+
+size_t comp_ws_bytes(const Ctx& c, const pdq_plan& pl) {
+    const u64 cts = ct_elems(c);
+    const u64 R = (u64)pl.H * pl.B * cts;
+    const u64 acc = (u64)pl.G * pl.giants * cts;
+    const u64 ys = 2ull * pl.G * cts;
+    const u32 cnt = std::max(pl.H, pl.G);
+    return (R + acc + ys) * sizeof(u64) + raise_ws(c, cnt) + apply_ws(c, cnt);
+}
+
+int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& keys,
+             const u64* consts, u64* out, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (ws_bytes < comp_ws_bytes(c, pl)) return fail(PDQ_E_NOMEM, "comp: workspace too small");
+    const long long cts = (long long)ct_elems(c);
+    const u32 H = pl.H, B = pl.B, G = pl.G, GI = pl.giants;
+    u64* R = reinterpret_cast<u64*>(ws);
+    u64* acc = R + (u64)H * B * cts;
+    u64* Y0 = acc + (u64)G * GI * cts;
+    u64* Y1 = Y0 + (u64)G * cts;
+    u64* rws = Y1 + (u64)G * cts;
+    u64* aws = rws + raise_ws(c, std::max(H, G)) / sizeof(u64);
+    const u64* Dg = consts;
+    const u64* masks = consts + (u64)pl.hclass * GI * B * c.L * c.N;
+
+    auto key_for = [&](u64 k, const u64** kp) -> int {
+        *kp = keys.find(k);
+        if (!*kp) return fail(PDQ_E_KEY, "comp: missing rotation key for Galois element " + std::to_string(k));
+        return PDQ_OK;
+    };
+    const CtSet none{};
+    u64* D = nullptr;
+
+    // 1. pack: i = 2j + which; which 0: dT_j (+vT_j), which 1: vB_j (+dB_j)
+    prof_mark(c, PDQ_STAGE_PACK, st);
+    {
+        CtSet in;  in.base = masked + 2 * cts;  in.outer = 4 * cts;  in.per = 2;  in.inner = -cts;
+        CtSet add; add.base = masked;           add.outer = 4 * cts; add.per = 2; add.inner = 3 * cts;
+        CtSet o;   o.base = R;                  o.outer = 2LL * B * cts; o.per = 2; o.inner = (long long)B * cts;
+        const u64* kp;
+        PDQ_TRY(key_for(2ull * c.N - 1, &kp));
+        PDQ_TRY(ks_raise(c, in, H, rws, &D, st));
+        PDQ_TRY(ks_apply(c, D, in, H, (u32)(2ull * c.N - 1), kp, o, add, aws, st));
+    }
+    // 2. baby steps, hoisted
+    prof_mark(c, PDQ_STAGE_BABY, st);
+    const CtSet u = ct_set(R, (long long)B * cts);
+    if (B > 1) PDQ_TRY(ks_raise(c, u, H, rws, &D, st));
+    for (u32 a = 1; a < B; ++a) {
+        const u64 k = galois_rot(c, a);
+        const u64* kp;
+        PDQ_TRY(key_for(k, &kp));
+        PDQ_TRY(ks_apply(c, D, u, H, (u32)k, kp, ct_set(R + (u64)a * cts, (long long)B * cts), none,
+                         aws, st));
+    }
+    // 3. diagonal multiply-accumulate
+    prof_mark(c, PDQ_STAGE_MAC, st);
+    PDQ_TRY(diag_mac(c, pl, R, Dg, acc, st));
+    // 4. giant steps: y_gamma accumulates in acc[gamma][0]
+    prof_mark(c, PDQ_STAGE_GIANT, st);
+    const CtSet y0 = ct_set(acc, (long long)GI * cts);
+    for (u32 g = 1; g < GI; ++g) {
+        const u64 k = galois_rot(c, (long long)g * B);
+        const u64* kp;
+        PDQ_TRY(key_for(k, &kp));
+        const CtSet in = ct_set(acc + (u64)g * cts, (long long)GI * cts);
+        PDQ_TRY(ks_raise(c, in, G, rws, &D, st));
+        PDQ_TRY(ks_apply(c, D, in, G, (u32)k, kp, y0, y0, aws, st));
+    }
+    PDQ_TRY(gather_rows(y0, 0, G, (u64)cts, Y0, (u64)cts, st));
+    // 5. rotate-and-sum, ping-pong between Y0 and Y1
+    prof_mark(c, PDQ_STAGE_ROTSUM, st);
+    u64* ycur = Y0;
+    u64* ynext = Y1;
+    for (u64 l = pl.s_prime; l < c.m; l *= 2) {
+        const u64 k = galois_rot(c, (long long)l);
+        const u64* kp;
+        PDQ_TRY(key_for(k, &kp));
+        const CtSet yin = ct_set(ycur, cts);
+        PDQ_TRY(ks_raise(c, yin, G, rws, &D, st));
+        PDQ_TRY(ks_apply(c, D, yin, G, (u32)k, kp, ct_set(ynext, cts), yin, aws, st));
+        std::swap(ycur, ynext);
+    }
+    // 6. output
+    prof_mark(c, PDQ_STAGE_COMBINE, st);
+    if (G == 1) {
+        if (cudaMemcpyAsync(out, ycur, (size_t)cts * sizeof(u64), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return fail(PDQ_E_CUDA, "comp: output copy failed");
+    } else {
+        PDQ_TRY(group_combine(c, pl, ycur, masks, out, st));
+    }
+    prof_mark(c, -1, st);
+    return PDQ_OK;
+}
+
+}  // namespace
+
+}  // namespace pdq
+
+using namespace pdq;
+
+#define PDQ_CHECK_CTX(ctx) \
+    if (!(ctx)) return fail(PDQ_E_PARAM, "null context")
+
+extern "C" {
+
+int pdq_ntt_forward(const pdq_ctx* ctx, uint64_t* data, uint32_t count, uint32_t nlimbs,
+                    uint32_t limb0, uint64_t stride, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    return ntt_forward(C(ctx), data, count, nlimbs, limb0, stride, (cudaStream_t)stream);
+}
+
+int pdq_ntt_inverse(const pdq_ctx* ctx, uint64_t* data, uint32_t count, uint32_t nlimbs,
+                    uint32_t limb0, uint64_t stride, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    return ntt_inverse(C(ctx), data, count, nlimbs, limb0, stride, (cudaStream_t)stream);
+}
+
+int pdq_encode(const pdq_ctx* ctx, const uint32_t* slots, uint32_t count, uint32_t nlimbs,
+               uint64_t* pt_out, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    return encode_slots(C(ctx), slots, count, nlimbs, pt_out, (cudaStream_t)stream);
+}
+
+int pdq_secret_prepare(const pdq_ctx* ctx, const int8_t* s, uint64_t* sk_out, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    return secret_prepare(C(ctx), s, sk_out, (cudaStream_t)stream);
+}
+
+int pdq_encrypt(const pdq_ctx* ctx, const uint64_t* sk, const uint32_t* slots, uint32_t count,
+                const uint64_t* a, const int32_t* e, uint64_t* ct_out, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    return encrypt(C(ctx), sk, slots, count, a, e, ct_out, (cudaStream_t)stream);
+}
+
+int pdq_rotkey_gen(const pdq_ctx* ctx, const uint64_t* sk, uint64_t galois, const uint64_t* a,
+                   const int32_t* e, uint64_t* key_out, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    return rotkey_gen(C(ctx), sk, galois, a, e, key_out, (cudaStream_t)stream);
+}
+
+size_t pdq_decrypt_workspace_bytes(const pdq_ctx* ctx, uint32_t count) {
+    return ctx ? decrypt_ws(C(ctx), count) : 0;
+}
+
+int pdq_decrypt(const pdq_ctx* ctx, const uint64_t* sk, const uint64_t* ct, uint32_t count,
+                uint32_t* slots_out, void* ws, size_t ws_bytes, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    if (ws_bytes < decrypt_ws(C(ctx), count)) return fail(PDQ_E_NOMEM, "decrypt: workspace too small");
+    return decrypt(C(ctx), sk, ct, count, slots_out, reinterpret_cast<u64*>(ws), (cudaStream_t)stream);
+}
+
+size_t pdq_rotate_workspace_bytes(const pdq_ctx* ctx, uint32_t count) {
+    return ctx ? raise_ws(C(ctx), count) + apply_ws(C(ctx), count) : 0;
+}
+
+int pdq_rotate(const pdq_ctx* ctx, const uint64_t* ct_in, uint32_t count, uint64_t galois,
+               const uint64_t* key, uint64_t* ct_out, void* ws, size_t ws_bytes, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    const Ctx& c = C(ctx);
+    if (count == 0) return PDQ_OK;
+    if (galois % 2 == 0 || galois >= 2ull * c.N) return fail(PDQ_E_PARAM, "rotate: bad Galois element");
+    if (ws_bytes < pdq_rotate_workspace_bytes(ctx, count)) return fail(PDQ_E_NOMEM, "rotate: workspace too small");
+    const long long cts = (long long)ct_elems(c);
+    u64* rws = reinterpret_cast<u64*>(ws);
+    u64* aws = rws + raise_ws(c, count) / sizeof(u64);
+    u64* D = nullptr;
+    const CtSet in = ct_set(ct_in, cts);
+    PDQ_TRY(ks_raise(c, in, count, rws, &D, (cudaStream_t)stream));
+    return ks_apply(c, D, in, count, (u32)galois, key, ct_set(ct_out, cts), CtSet{}, aws,
+                    (cudaStream_t)stream);
+}
+
+int pdq_plan_make(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B, pdq_plan* plan) {
+    PDQ_CHECK_CTX(ctx);
+    if (!plan) return fail(PDQ_E_PARAM, "null plan");
+    return plan_make(C(ctx), n, s, B, plan);
+}
+
+int pdq_plan_galois(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out, uint32_t cap,
+                    uint32_t* count) {
+    PDQ_CHECK_CTX(ctx);
+    if (!valid_plan(C(ctx), plan) || !count) return fail(PDQ_E_PARAM, "plan_galois: invalid plan");
+    auto ks = plan_galois(C(ctx), *plan);
+    *count = (uint32_t)ks.size();
+    if (out) {
+        if (cap < ks.size()) return fail(PDQ_E_NOMEM, "plan_galois: output too small");
+        std::copy(ks.begin(), ks.end(), out);
+    }
+    return PDQ_OK;
+}
+
+size_t pdq_plan_constants_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {
+    if (!ctx || !valid_plan(C(ctx), plan)) return 0;
+    const Ctx& c = C(ctx);
+    const u64 pts = (u64)plan->hclass * plan->giants * plan->B + (plan->G > 1 ? plan->per_out : 0);
+    return pts * c.L * c.N * sizeof(u64);
+}
+
+int pdq_plan_constants_build(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out,
+                             void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    const Ctx& c = C(ctx);
+    if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "plan_constants_build: invalid plan");
+    PDQ_TRY(build_diagonals(c, *plan, out, (cudaStream_t)stream));
+    if (plan->G > 1) {
+        u64* masks = out + (u64)plan->hclass * plan->giants * plan->B * c.L * c.N;
+        PDQ_TRY(build_group_masks(c, *plan, masks, (cudaStream_t)stream));
+    }
+    return PDQ_OK;
+}
+
+size_t pdq_db_bytes(const pdq_ctx* ctx, uint64_t n) {
+    if (!ctx) return 0;
+    const Ctx& c = C(ctx);
+    const u64 J = (n + c.N - 1) / c.N;
+    return J * ct_elems(c) * sizeof(u64);
+}
+
+int pdq_db_encode(const pdq_ctx* ctx, const uint32_t* values, uint64_t n, uint64_t* db_out,
+                  void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    const Ctx& c = C(ctx);
+    if (n == 0) return fail(PDQ_E_PARAM, "db_encode: empty database");
+    const u64 J = (n + c.N - 1) / c.N;
+    return build_db(c, values, n, (u32)J, db_out, (cudaStream_t)stream);
+}
+
+int pdq_mask(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts, const uint64_t* db,
+             uint64_t* masked_out, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    if (!valid_plan(C(ctx), plan)) return fail(PDQ_E_PARAM, "mask: invalid plan");
+    return mask(C(ctx), plan->J, v_cts, db, masked_out, (cudaStream_t)stream);
+}
+
+size_t pdq_comp_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {
+    if (!ctx || !valid_plan(C(ctx), plan)) return 0;
+    return comp_ws_bytes(C(ctx), *plan);
+}
+
+int pdq_comp(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* masked,
+             const uint64_t* keys, const uint64_t* galois, uint32_t nkeys,
+             const uint64_t* consts, uint64_t* out, void* ws, size_t ws_bytes, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    const Ctx& c = C(ctx);
+    if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "comp: invalid plan");
+    if (!masked || !keys || !galois || !consts || !out || !ws) return fail(PDQ_E_PARAM, "comp: null buffer");
+    Keys k{keys, galois, nkeys, (u64)c.ndigits * 2 * (c.L + c.K) * c.N};
+    return comp_run(c, *plan, masked, k, consts, out, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+size_t pdq_answer_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {
+    if (!ctx || !valid_plan(C(ctx), plan)) return 0;
+    const Ctx& c = C(ctx);
+    return (size_t)plan->J * 4 * ct_elems(c) * sizeof(u64) + comp_ws_bytes(c, *plan);
+}
+
+int pdq_answer(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
+               const uint64_t* db, const uint64_t* keys, const uint64_t* galois,
+               uint32_t nkeys, const uint64_t* consts, uint64_t* out, void* ws,
+               size_t ws_bytes, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    const Ctx& c = C(ctx);
+    if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "answer: invalid plan");
+    if (ws_bytes < pdq_answer_workspace_bytes(ctx, plan)) return fail(PDQ_E_NOMEM, "answer: workspace too small");
+    u64* masked = reinterpret_cast<u64*>(ws);
+    const size_t mbytes = (size_t)plan->J * 4 * ct_elems(c) * sizeof(u64);
+    prof_mark(c, PDQ_STAGE_MASK, (cudaStream_t)stream);
+    PDQ_TRY(mask(c, plan->J, v_cts, db, masked, (cudaStream_t)stream));
+    Keys k{keys, galois, nkeys, (u64)c.ndigits * 2 * (c.L + c.K) * c.N};
+    return comp_run(c, *plan, masked, k, consts, out, reinterpret_cast<char*>(ws) + mbytes,
+                    ws_bytes - mbytes, (cudaStream_t)stream);
+}
+
+size_t pdq_answer_host_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {
+    if (!ctx || !valid_plan(C(ctx), plan)) return 0;
+    const Ctx& c = C(ctx);
+    return ((size_t)plan->J + plan->n_out) * ct_elems(c) * sizeof(u64) +
+           pdq_answer_workspace_bytes(ctx, plan);
+}
+
+int pdq_answer_host(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_host,
+                    const uint64_t* db, const uint64_t* keys, const uint64_t* galois,
+                    uint32_t nkeys, const uint64_t* consts, uint64_t* out_host, void* ws,
+                    size_t ws_bytes, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    const Ctx& c = C(ctx);
+    if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "answer_host: invalid plan");
+    if (!v_host || !out_host) return fail(PDQ_E_PARAM, "answer_host: null host buffer");
+    if (ws_bytes < pdq_answer_host_workspace_bytes(ctx, plan)) return fail(PDQ_E_NOMEM, "answer_host: workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    const u64 cts = ct_elems(c);
+    u64* v = reinterpret_cast<u64*>(ws);
+    u64* o = v + (u64)plan->J * cts;
+    char* rest = reinterpret_cast<char*>(o + (u64)plan->n_out * cts);
+    const size_t vbytes = (size_t)plan->J * cts * sizeof(u64);
+    const size_t obytes = (size_t)plan->n_out * cts * sizeof(u64);
+    if (cudaMemcpyAsync(v, v_host, vbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(PDQ_E_CUDA, "answer_host: upload failed");
+    PDQ_TRY(ntt_forward(c, v, 2 * plan->J, c.L, 0, (u64)c.L * c.N, st));
+    PDQ_TRY(pdq_answer(ctx, plan, v, db, keys, galois, nkeys, consts, o, rest,
+                       ws_bytes - vbytes - obytes, stream));
+    PDQ_TRY(ntt_inverse(c, o, 2 * plan->n_out, c.L, 0, (u64)c.L * c.N, st));
+    if (cudaMemcpyAsync(out_host, o, obytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return fail(PDQ_E_CUDA, "answer_host: download failed");
+    if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("answer_host");
+    return PDQ_OK;
+}
+
+}  // extern "C"

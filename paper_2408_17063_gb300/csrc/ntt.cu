@@ -1,0 +1,254 @@
+// Negacyclic number-theoretic transform over 60-bit primes for sm_103a.
+//
+// The forward transform maps a(X) in Z_q[X]/(X^N+1) to its values at the
+// odd powers of a primitive 2N-th root psi, stored in bit-reversed order
+// (position k holds a(psi^{2 brv(k) + 1})); the inverse undoes it.  Both use
+// the merged-twiddle radix-2 formulation: Cooley-Tukey butterflies forward,
+// Gentleman-Sande butterflies inverse, Shoup multiplication by
+// precomputed twiddles and Harvey's lazy ranges ([0,4q) forward, [0,2q)
+// inverse), with N^{-1} folded into the last inverse level.  Outputs are
+// canonical residues.
+//
+// Work decomposition: for log N <= 11 one CTA transforms one polynomial in
+// shared memory.  Larger rings split the log N levels into a column phase
+// (levels 0..S1-1: independent length-2^S1 transforms over elements spaced
+// 2^9 apart) and a row phase (levels S1..logN-1: independent contiguous
+// length-2^9 transforms), each CTA holding a 2048-element tile (16 KB) of
+// consecutive columns or rows so that every global access is coalesced.
+// Inside a tile, each thread runs up to three levels on eight elements in
+// registers between shared-memory exchanges.
+#include "pdq_internal.h"
+
+namespace pdq {
+
+namespace {
+
+constexpr u32 kTile = 2048;       // elements per CTA tile
+constexpr u32 kRowBits = 9;       // row length 2^9 in the two-phase split
+constexpr u32 kThreads = 256;
+
+struct NttArgs {
+    u64* data;
+    u64 stride;        // elements between consecutive groups
+    u32 nlimbs;        // limbs per group
+    u32 limb0;         // modulus index of the first limb
+    const Mod* mods;
+    const u64* tw;     // [nmod][N] twiddles (forward or inverse)
+    const u64* tws;    // Shoup companions
+    const u64* ninv4;  // [nmod][4]
+    u32 logN;
+    u32 S1;            // levels done by the column phase (0: single phase)
+    u32 logC;          // log2(sub-transforms per CTA)
+    u32 last;          // 1: this phase writes canonical output
+};
+
+__device__ __forceinline__ void bf_fwd(u64& x, u64& y, u64 w, u64 wp, u64 q) {
+    u64 a = csub(x, 2 * q);
+    u64 t = mul_shoup_lazy(y, w, wp, q);
+    x = a + t;
+    y = a - t + 2 * q;
+}
+
+__device__ __forceinline__ void bf_inv(u64& x, u64& y, u64 w, u64 wp, u64 q) {
+    u64 a = x, b = y;
+    x = csub(a + b, 2 * q);
+    y = mul_shoup_lazy(a - b + 2 * q, w, wp, q);
+}
+
+template <bool FWD, int S, bool COLS>
+struct Phase {
+    static constexpr u32 GS = 1u << S;
+
+    u64* sm;
+    const NttArgs& a;
+    u64 q;
+    const u64* tw;
+    const u64* tws;
+    u64 n0, n0s, n1, n1s;  // N^-1 and psi^-1 N^-1 (with Shoup) for level 0
+    u32 sub0, st0, S2, C;
+
+    __device__ __forceinline__ u64 gidx(u32 c, u32 l) const {
+        return COLS ? (((u64)l) << S2) + sub0 + c : (((u64)(sub0 + c)) << S2) + l;
+    }
+    __device__ __forceinline__ u32 sidx(u32 c, u32 l) const {
+        return COLS ? (l << a.logC) + c : c * GS + l;
+    }
+
+    // One pass over the R local levels whose pair bits are lb .. lb+R-1.
+    template <int R>
+    __device__ __forceinline__ void pass(u32 lb) const {
+        constexpr u32 NE = 1u << R;
+        const u32 items = (C * GS) >> R;
+        const u32 lowmask = (1u << lb) - 1;
+        for (u32 w = threadIdx.x; w < items; w += blockDim.x) {
+            u32 c, fixed;
+            if (COLS) {
+                c = w & (C - 1);
+                fixed = w >> a.logC;
+            } else {
+                fixed = w & ((GS >> R) - 1);
+                c = w >> (S - R);
+            }
+            const u32 lbase = (fixed & lowmask) | ((fixed >> lb) << (lb + R));
+            u64 x[NE];
+#pragma unroll
+            for (u32 k = 0; k < NE; ++k) x[k] = sm[sidx(c, lbase | (k << lb))];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const u32 kb = FWD ? (u32)(R - 1 - r) : (u32)r;
+                const u32 half = 1u << kb;
+                const u32 st = st0 + (S - 1 - (lb + kb));   // global level
+#pragma unroll
+                for (u32 k = 0; k < NE; ++k) {
+                    if (k & half) continue;
+                    const u64 j = gidx(c, lbase | (k << lb));
+                    const u32 ti = (1u << st) + (u32)(j >> (a.logN - st));
+                    if (FWD) {
+                        bf_fwd(x[k], x[k | half], __ldg(tw + ti), __ldg(tws + ti), q);
+                    } else if (st == 0) {
+                        u64 xa = x[k], xb = x[k | half];
+                        x[k] = mul_shoup_lazy(xa + xb, n0, n0s, q);
+                        x[k | half] = mul_shoup_lazy(xa - xb + 2 * q, n1, n1s, q);
+                    } else {
+                        bf_inv(x[k], x[k | half], __ldg(tw + ti), __ldg(tws + ti), q);
+                    }
+                }
+            }
+#pragma unroll
+            for (u32 k = 0; k < NE; ++k) sm[sidx(c, lbase | (k << lb))] = x[k];
+        }
+        __syncthreads();
+    }
+
+    __device__ __forceinline__ void run() const {
+        if (FWD) {
+            int top = S;
+            while (top > 0) {
+                const int r = top >= 3 ? 3 : top;
+                const u32 lb = (u32)(top - r);
+                if (r == 3) pass<3>(lb); else if (r == 2) pass<2>(lb); else pass<1>(lb);
+                top -= r;
+            }
+        } else {
+            int lo = 0;
+            while (lo < S) {
+                const int r = (S - lo) >= 3 ? 3 : (S - lo);
+                if (r == 3) pass<3>((u32)lo); else if (r == 2) pass<2>((u32)lo); else pass<1>((u32)lo);
+                lo += r;
+            }
+        }
+    }
+};
+
+template <bool FWD, int S, bool COLS>
+__global__ void __launch_bounds__(kThreads) ntt_phase_kernel(NttArgs a) {
+    __shared__ u64 sm[kTile];
+    const u32 p = blockIdx.x;
+    const u32 grp = p / a.nlimbs, limb = p % a.nlimbs;
+    const u32 mi = a.limb0 + limb;
+    const u64 N = 1ull << a.logN;
+    u64* base = a.data + (u64)grp * a.stride + (u64)limb * N;
+
+    Phase<FWD, S, COLS> ph{sm, a};
+    ph.q = a.mods[mi].q;
+    ph.tw = a.tw + (u64)mi * N;
+    ph.tws = a.tws + (u64)mi * N;
+    ph.n0 = a.ninv4[4 * mi + 0];
+    ph.n0s = a.ninv4[4 * mi + 1];
+    ph.n1 = a.ninv4[4 * mi + 2];
+    ph.n1s = a.ninv4[4 * mi + 3];
+    ph.C = 1u << a.logC;
+    ph.sub0 = blockIdx.y * ph.C;
+    ph.st0 = COLS ? 0 : a.S1;
+    ph.S2 = a.logN - a.S1;
+    if (COLS) ph.S2 = a.logN - S;
+
+    constexpr u32 GS = 1u << S;
+    const u32 T = ph.C * GS;
+    for (u32 e = threadIdx.x; e < T; e += blockDim.x) {
+        u32 c, l;
+        if (COLS) { l = e >> a.logC; c = e & (ph.C - 1); }
+        else { c = e >> S; l = e & (GS - 1); }
+        sm[ph.sidx(c, l)] = base[ph.gidx(c, l)];
+    }
+    __syncthreads();
+    ph.run();
+    const u64 q = ph.q;
+    for (u32 e = threadIdx.x; e < T; e += blockDim.x) {
+        u32 c, l;
+        if (COLS) { l = e >> a.logC; c = e & (ph.C - 1); }
+        else { c = e >> S; l = e & (GS - 1); }
+        u64 v = sm[ph.sidx(c, l)];
+        if (a.last) v = FWD ? csub(csub(v, 2 * q), q) : csub(v, q);
+        base[ph.gidx(c, l)] = v;
+    }
+}
+
+template <bool FWD, bool COLS>
+int launch_phase(int S, dim3 grid, u32 threads, const NttArgs& a, cudaStream_t st) {
+    switch (S) {
+#define PDQ_CASE(s) case s: ntt_phase_kernel<FWD, s, COLS><<<grid, threads, 0, st>>>(a); break;
+        PDQ_CASE(1) PDQ_CASE(2) PDQ_CASE(3) PDQ_CASE(4) PDQ_CASE(5) PDQ_CASE(6)
+        PDQ_CASE(7) PDQ_CASE(8) PDQ_CASE(9) PDQ_CASE(10) PDQ_CASE(11)
+#undef PDQ_CASE
+        default: return fail(PDQ_E_PARAM, "ntt: unsupported phase size");
+    }
+    return launched("ntt_phase_kernel");
+}
+
+template <bool FWD>
+int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
+            cudaStream_t st) {
+    if (count == 0 || nlimbs == 0) return PDQ_OK;
+    if (limb0 + nlimbs > c.nmod) return fail(PDQ_E_PARAM, "ntt: limb range out of bounds");
+    const u64 polys = (u64)count * nlimbs;
+    if (polys > 0x7fffffffULL) return fail(PDQ_E_PARAM, "ntt: too many polynomials");
+    NttArgs a{};
+    a.data = data;
+    a.stride = stride;
+    a.nlimbs = nlimbs;
+    a.limb0 = limb0;
+    a.mods = c.d_mods;
+    a.tw = FWD ? c.d_fw : c.d_iw;
+    a.tws = FWD ? c.d_fw_shoup : c.d_iw_shoup;
+    a.ninv4 = c.d_ninv;
+    a.logN = c.log_n;
+    if (c.log_n <= 11) {
+        a.S1 = 0;
+        a.logC = 0;
+        a.last = 1;
+        u32 threads = c.N / 8 < 32 ? 32 : (c.N / 8 > kThreads ? kThreads : c.N / 8);
+        return launch_phase<FWD, false>((int)c.log_n, dim3((u32)polys, 1), threads, a, st);
+    }
+    const u32 S1 = c.log_n - kRowBits;
+    a.S1 = S1;
+    NttArgs cols = a, rows = a;
+    cols.logC = 11 - S1;                       // 2^S1 * C = 2048
+    rows.logC = 11 - kRowBits;                 // 4 rows of 512
+    const dim3 gcols((u32)polys, (1u << kRowBits) >> cols.logC);
+    const dim3 grows((u32)polys, (1u << S1) >> rows.logC);
+    if (FWD) {
+        cols.last = 0;
+        rows.last = 1;
+        PDQ_TRY((launch_phase<FWD, true>((int)S1, gcols, kThreads, cols, st)));
+        return launch_phase<FWD, false>((int)kRowBits, grows, kThreads, rows, st);
+    }
+    rows.last = 0;
+    cols.last = 1;
+    PDQ_TRY((launch_phase<FWD, false>((int)kRowBits, grows, kThreads, rows, st)));
+    return launch_phase<FWD, true>((int)S1, gcols, kThreads, cols, st);
+}
+
+}  // namespace
+
+int ntt_forward(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
+                cudaStream_t st) {
+    return ntt_run<true>(c, data, count, nlimbs, limb0, stride, st);
+}
+
+int ntt_inverse(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
+                cudaStream_t st) {
+    return ntt_run<false>(c, data, count, nlimbs, limb0, stride, st);
+}
+
+}  // namespace pdq

@@ -1,0 +1,162 @@
+// Internal declarations of the PDQ library (not part of the C ABI).
+//
+// Residues are uint64 in [0, q) with every prime q < 2^60, so lazy values up
+// to 4q fit in 62 bits and sums of up to 2^7 products of two residues fit in
+// an unsigned 128-bit accumulator.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pdq.h"
+
+namespace pdq {
+
+using u64 = uint64_t;
+using u32 = uint32_t;
+using u128 = unsigned __int128;
+
+// ---------------------------------------------------------------- errors ----
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_check(const char* where);  // PDQ_OK or PDQ_E_CUDA with the message
+int launched(const char* where);    // counts one kernel launch, then cuda_check
+
+#define PDQ_TRY(expr)                   \
+    do {                                \
+        int _rc = (expr);               \
+        if (_rc != PDQ_OK) return _rc;  \
+    } while (0)
+
+// ------------------------------------------------------- modulus constants --
+// One prime with the constants every kernel needs.
+struct Mod {
+    u64 q;
+    u64 ratio;       // floor(2^64 / q)
+    u64 r64;         // 2^64 mod q
+    u64 r64_shoup;   // floor(r64 * 2^64 / q)
+};
+
+// ------------------------------------------------------------ device math --
+__host__ __device__ __forceinline__ u64 mulhi64(u64 a, u64 b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (u64)(((u128)a * b) >> 64);
+#endif
+}
+
+// w * x mod q in [0, 2q) with wp = floor(w 2^64 / q), any x < 2^64 (Shoup).
+__host__ __device__ __forceinline__ u64 mul_shoup_lazy(u64 x, u64 w, u64 wp, u64 q) {
+    return x * w - mulhi64(x, wp) * q;
+}
+
+__host__ __device__ __forceinline__ u64 csub(u64 x, u64 q) { return x >= q ? x - q : x; }
+
+// x mod q for any x < 2^64, via the estimate floor(x * floor(2^64/q) / 2^64).
+__host__ __device__ __forceinline__ u64 reduce64(u64 x, const Mod& m) {
+    return csub(x - mulhi64(x, m.ratio) * m.q, m.q);
+}
+
+// (hi * 2^64 + lo) mod q for any 128-bit value: hi * (2^64 mod q) by Shoup,
+// lo by the single-word estimate, then two conditional subtractions.
+__host__ __device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const Mod& m) {
+    u64 a = mul_shoup_lazy(hi, m.r64, m.r64_shoup, m.q);      // [0, 2q)
+    u64 b = lo - mulhi64(lo, m.ratio) * m.q;                  // [0, 2q)
+    u64 s = a + b;                                            // [0, 4q)
+    s = csub(s, 2 * m.q);
+    return csub(s, m.q);
+}
+
+__host__ __device__ __forceinline__ u64 mulmod(u64 a, u64 b, const Mod& m) {
+    u64 lo = a * b;
+    u64 hi = mulhi64(a, b);
+    return reduce128(hi, lo, m);
+}
+
+__host__ __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
+__host__ __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// 128-bit accumulator: (hi, lo) += a * b.
+__host__ __device__ __forceinline__ void mac128(u64& hi, u64& lo, u64 a, u64 b) {
+    u64 plo = a * b;
+    u64 phi = mulhi64(a, b);
+    lo += plo;
+    hi += phi + (lo < plo ? 1 : 0);
+}
+
+// --------------------------------------------------------------- context ----
+struct Ctx {
+    u32 log_n = 0, N = 0, m = 0;
+    u64 t = 0;
+    u32 L = 0, K = 0, dnum = 0, alpha = 0, ndigits = 0, bits = 0;
+    u32 nmod = 0;                 // L + K + 1 (the last is t)
+    std::vector<u64> mods;        // q_0..q_{L-1}, p_0..p_{K-1}, t
+    std::vector<Mod> hmods;
+    u64 zeta = 0;                 // slot root mod t
+    std::vector<u64> psi;         // transform root per modulus
+    // device tables, each [nmod][N] unless noted
+    Mod* d_mods = nullptr;        // [nmod]
+    u64* d_fw = nullptr;          // forward twiddles psi^{brv(i)}
+    u64* d_fw_shoup = nullptr;
+    u64* d_iw = nullptr;          // inverse twiddles psi^{-brv(i)}
+    u64* d_iw_shoup = nullptr;
+    u64* d_ninv = nullptr;        // [nmod][4]: N^-1, shoup, N^-1 * iw[1], shoup
+    u32* d_slot_pos = nullptr;    // [N] transform position of slot rho*m + c
+    u64* d_rowmask = nullptr;     // [2][L][N] NTT-form plaintexts [1;0], [0;1]
+    // key-switching constants
+    // ModUp, digit beta: for i in digit, hat_inv (Q_b/q_i)^-1 mod q_i + shoup;
+    // for every ext prime r: (Q_b/q_i) mod r.   Layout:
+    u64* d_up_hatinv = nullptr;   // [L] (q_i's own digit), value
+    u64* d_up_hatinv_shoup = nullptr;
+    u64* d_up_hatmod = nullptr;   // [L][L+K]: (Q_{digit(i)}/q_i) mod r
+    // ModDown: (P/p_k)^-1 mod p_k (+shoup); (P/p_k) mod q_i; P^-1 mod q_i (+shoup)
+    u64* d_dn_hatinv = nullptr;   // [K]
+    u64* d_dn_hatinv_shoup = nullptr;
+    u64* d_dn_hatmod = nullptr;   // [K][L]
+    u64* d_dn_pinv = nullptr;     // [L]
+    u64* d_dn_pinv_shoup = nullptr;
+    // P mod q_i (keygen), Delta mod q_i (encryption)
+    std::vector<u64> P_mod_q, delta_mod_q;
+    u64* d_P_mod_q = nullptr;
+    u64* d_delta_mod_q = nullptr;
+    // decryption: per q_i, omega_i = (Q/q_i)^-1 mod q_i (+shoup), and
+    // t * b / q_i split for rounding is done with 128-bit arithmetic.
+    u64* d_dec_omega = nullptr;
+    u64* d_dec_omega_shoup = nullptr;
+    std::vector<std::vector<u32>> digit_limbs;   // limbs of each digit
+    // stage profiling: events recorded on the caller's stream when enabled
+    struct Prof {
+        bool on = false;
+        std::vector<cudaEvent_t> ev;
+        std::vector<int> stage;
+        size_t used = 0;
+    };
+    mutable Prof prof;
+};
+
+// Record a stage boundary (stage < 0 closes the current stage) when
+// profiling is enabled on the context.
+void prof_mark(const Ctx& c, int stage, cudaStream_t st);
+
+// ---------------------------------------------------------- host helpers ---
+u64 host_powmod(u64 a, u64 e, u64 q);
+u64 host_invmod(u64 a, u64 q);
+u64 shoup_of(u64 w, u64 q);
+Mod make_mod(u64 q);
+bool host_is_prime(u64 n);
+u32 bitrev(u32 x, u32 bits);
+
+// ------------------------------------------------------------- transforms --
+// Forward / inverse negacyclic transform of `count` groups of `nlimbs` limbs,
+// group g limb l at data + g*stride + l*N, modulus index limb0 + l.
+int ntt_forward(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
+                cudaStream_t st);
+int ntt_inverse(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
+                cudaStream_t st);
+
+}  // namespace pdq

@@ -1,0 +1,68 @@
+// Launchers of the element-wise kernels (ops.cu), used by the Comp
+// orchestration (comp.cu) and the C ABI.
+#pragma once
+
+#include "pdq_internal.h"
+
+namespace pdq {
+
+// A strided set of ciphertexts: ciphertext i starts at
+// base + (i / per) * outer + (i % per) * inner  (uint64 elements).
+struct CtSet {
+    const u64* base = nullptr;
+    long long outer = 0;
+    u32 per = 1;
+    long long inner = 0;
+
+    __host__ __device__ __forceinline__ u64* at(u64 i) const {
+        return const_cast<u64*>(base) + (long long)(i / per) * outer + (long long)(i % per) * inner;
+    }
+};
+
+inline CtSet ct_set(const u64* base, long long stride) {
+    CtSet s;
+    s.base = base;
+    s.outer = stride;
+    return s;
+}
+
+struct DigitBounds {
+    u32 lo[32];
+    u32 hi[32];
+};
+
+int encode_finish(const Ctx& c, u64* out, u32 count, u32 nlimbs, cudaStream_t st);
+int encode_slots(const Ctx& c, const u32* slots, u32 count, u32 nlimbs, u64* out, cudaStream_t st);
+int build_diagonals(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st);
+int build_group_masks(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st);
+int build_db(const Ctx& c, const u32* values, u64 n, u32 J, u64* out, cudaStream_t st);
+int secret_prepare(const Ctx& c, const int8_t* s, u64* out, cudaStream_t st);
+int encrypt(const Ctx& c, const u64* sk, const u32* slots, u32 count, const u64* a,
+            const int32_t* e, u64* ct, cudaStream_t st);
+int rotkey_gen(const Ctx& c, const u64* sk, u64 galois, const u64* a, const int32_t* e, u64* key,
+               cudaStream_t st);
+size_t decrypt_ws(const Ctx& c, u32 count);
+int decrypt(const Ctx& c, const u64* sk, const u64* ct, u32 count, u32* slots, u64* ws,
+            cudaStream_t st);
+int mask(const Ctx& c, u32 J, const u64* v, const u64* db, u64* out, cudaStream_t st);
+
+// Hybrid key switching, split so that the raised digits of c1 can be shared
+// by every rotation of the same ciphertexts (hoisting):
+//   ks_raise: D[i][beta] = raise of digit beta of c1(in[i]) to Q u P (NTT form)
+//   ks_apply: out[i] = sigma_k(c0) + ModDown(sum_beta sigma_k(D[i][beta]) * key[beta][0]),
+//             ModDown(sum_beta sigma_k(D[i][beta]) * key[beta][1])   (+ add[i])
+size_t raise_ws(const Ctx& c, u32 cnt);   // holds D (returned) and a scratch copy of c1
+size_t apply_ws(const Ctx& c, u32 cnt);
+int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t st);
+int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u64* key,
+             CtSet out, CtSet add, u64* ws, cudaStream_t st);
+
+int gather_rows(CtSet src, long long src_off, u32 cnt, u64 len, u64* dst, u64 dst_stride,
+                cudaStream_t st);
+int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc,
+             cudaStream_t st);
+int ct_add(const Ctx& c, CtSet y, CtSet x, u32 cnt, cudaStream_t st);
+int group_combine(const Ctx& c, const pdq_plan& pl, const u64* y, const u64* masks, u64* out,
+                  cudaStream_t st);
+
+}  // namespace pdq

@@ -1,0 +1,360 @@
+"""Python binding of the PDQ C ABI (include/pdq.h).
+
+Argument marshalling only: every function forwards to the entry point of the
+same name in ``_lib/libpdq.so``; tensors are passed as device pointers and
+sizes.  PyTorch supplies device memory and streams.  There is no fallback:
+if the compiled library is missing, loading raises.
+
+The ``Context`` class bundles a ``pdq_ctx`` with its parameters and offers
+the same calls with workspace allocation from PyTorch's caching allocator.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libpdq.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pdq.h")
+
+PDQ_OK, PDQ_E_PARAM, PDQ_E_NOMEM, PDQ_E_CUDA, PDQ_E_DECODE, PDQ_E_KEY = 0, 1, 2, 3, 4, 5
+MAX_MODULI = 40
+
+
+class PdqError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pdq error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_uint32), ("prime_bits", ctypes.c_uint32),
+                ("L", ctypes.c_uint32), ("K", ctypes.c_uint32), ("dnum", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("t", ctypes.c_uint64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("K", ctypes.c_uint32),
+                ("ndigits", ctypes.c_uint32), ("t", ctypes.c_uint64), ("zeta", ctypes.c_uint64),
+                ("moduli", ctypes.c_uint64 * MAX_MODULI), ("psi", ctypes.c_uint64 * MAX_MODULI)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64)] + [(f, ctypes.c_uint32) for f in (
+        "s", "s_prime", "B", "giants", "J", "H", "G_sz", "hpg", "G", "hclass", "per_out",
+        "n_out")]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_U32 = ctypes.c_uint32
+_U64 = ctypes.c_uint64
+_SZ = ctypes.c_size_t
+_I = ctypes.c_int
+
+_SIGS = {
+    "pdq_ctx_create": (_I, [ctypes.POINTER(Params), ctypes.POINTER(_P)]),
+    "pdq_ctx_destroy": (_I, [_P]),
+    "pdq_ctx_info": (_I, [_P, ctypes.POINTER(Info)]),
+    "pdq_last_error": (ctypes.c_char_p, []),
+    "pdq_ntt_forward": (_I, [_P, _P, _U32, _U32, _U32, _U64, _P]),
+    "pdq_ntt_inverse": (_I, [_P, _P, _U32, _U32, _U32, _U64, _P]),
+    "pdq_encode": (_I, [_P, _P, _U32, _U32, _P, _P]),
+    "pdq_secret_prepare": (_I, [_P, _P, _P, _P]),
+    "pdq_encrypt": (_I, [_P, _P, _P, _U32, _P, _P, _P, _P]),
+    "pdq_rotkey_gen": (_I, [_P, _P, _U64, _P, _P, _P, _P]),
+    "pdq_decrypt_workspace_bytes": (_SZ, [_P, _U32]),
+    "pdq_decrypt": (_I, [_P, _P, _P, _U32, _P, _P, _SZ, _P]),
+    "pdq_rotate_workspace_bytes": (_SZ, [_P, _U32]),
+    "pdq_rotate": (_I, [_P, _P, _U32, _U64, _P, _P, _P, _SZ, _P]),
+    "pdq_plan_make": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
+    "pdq_plan_galois": (_I, [_P, ctypes.POINTER(Plan), _P, _U32, ctypes.POINTER(_U32)]),
+    "pdq_plan_constants_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
+    "pdq_plan_constants_build": (_I, [_P, ctypes.POINTER(Plan), _P, _P]),
+    "pdq_db_bytes": (_SZ, [_P, _U64]),
+    "pdq_db_encode": (_I, [_P, _P, _U64, _P, _P]),
+    "pdq_mask": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _P]),
+    "pdq_comp_workspace_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
+    "pdq_comp": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _U32, _P, _P, _P, _SZ, _P]),
+    "pdq_answer_workspace_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
+    "pdq_answer": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _P, _U32, _P, _P, _P, _SZ, _P]),
+    "pdq_answer_host_workspace_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
+    "pdq_answer_host": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _P, _U32, _P, _P, _P, _SZ,
+                             _P]),
+    "pdq_decomp": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _U64, ctypes.POINTER(_U64)]),
+    "pdq_launch_count": (ctypes.c_ulonglong, []),
+    "pdq_profile_enable": (_I, [_P, _I]),
+    "pdq_profile_read": (_I, [_P, _P, _P, _U32]),
+}
+
+STAGES = ["mask", "pack", "baby", "mac", "giant", "rotsum", "combine"]
+
+
+def pdq_launch_count() -> int:
+    return int(load().pdq_launch_count())
+
+_lib = None
+
+
+def header_symbols() -> list[str]:
+    """Every entry point declared in include/pdq.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(pdq_[a-z0-9_]+)\s*\(", text)))
+
+
+def load() -> ctypes.CDLL:
+    """Load libpdq.so (built by paper_2408_17063_gb300.build); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2408_17063_gb300.build.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != PDQ_OK:
+        raise PdqError(rc, load().pdq_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.is_contiguous(), "tensors passed to the C ABI must be contiguous"
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    return int(t)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Context:
+    """A parameter set on the current CUDA device (owns a pdq_ctx)."""
+
+    def __init__(self, log_n: int, t: int, prime_bits: int, L: int, K: int, dnum: int):
+        lib = load()
+        p = Params(log_n, prime_bits, L, K, dnum, 0, t)
+        h = _P()
+        _check(lib.pdq_ctx_create(ctypes.byref(p), ctypes.byref(h)))
+        self.h = h
+        info = Info()
+        _check(lib.pdq_ctx_info(h, ctypes.byref(info)))
+        self.N, self.L, self.K, self.ndigits = info.N, info.L, info.K, info.ndigits
+        self.t, self.zeta = info.t, info.zeta
+        self.m = self.N // 2
+        self.E = self.L + self.K
+        self.moduli = [int(info.moduli[i]) for i in range(self.E)]
+        self.psi = [int(info.psi[i]) for i in range(self.E + 1)]
+        self.log_n = log_n
+
+    @classmethod
+    def from_config(cls, cfg) -> "Context":
+        return cls(cfg.log_n, cfg.t, cfg.prime_bits, cfg.L, cfg.K, cfg.dnum)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pdq_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # sizes
+    @property
+    def ct_elems(self) -> int:
+        return 2 * self.L * self.N
+
+    @property
+    def key_elems(self) -> int:
+        return self.ndigits * 2 * self.E * self.N
+
+    def _u64(self, n: int, device="cuda") -> torch.Tensor:
+        # 64-bit residues travel as int64 tensors (same bits; torch has few uint64 ops)
+        return torch.empty(int(n), dtype=torch.int64, device=device)
+
+    def _ws(self, nbytes: int) -> torch.Tensor:
+        return torch.empty(max(int(nbytes), 8), dtype=torch.uint8, device="cuda")
+
+    # transforms
+    def ntt_forward(self, data, count, nlimbs, limb0=0, stride=None, stream=None):
+        stride = nlimbs * self.N if stride is None else stride
+        _check(load().pdq_ntt_forward(self.h, _ptr(data), count, nlimbs, limb0, stride,
+                                      _stream(stream)))
+
+    def ntt_inverse(self, data, count, nlimbs, limb0=0, stride=None, stream=None):
+        stride = nlimbs * self.N if stride is None else stride
+        _check(load().pdq_ntt_inverse(self.h, _ptr(data), count, nlimbs, limb0, stride,
+                                      _stream(stream)))
+
+    # client-side helpers
+    def encode(self, slots: torch.Tensor, nlimbs=None, stream=None) -> torch.Tensor:
+        slots = slots.to(device="cuda", dtype=torch.int32).contiguous()
+        count = slots.numel() // self.N
+        nlimbs = self.L if nlimbs is None else nlimbs
+        out = self._u64(count * nlimbs * self.N)
+        _check(load().pdq_encode(self.h, _ptr(slots), count, nlimbs, _ptr(out), _stream(stream)))
+        return out.view(count, nlimbs, self.N)
+
+    def secret_prepare(self, s: torch.Tensor, stream=None) -> torch.Tensor:
+        s = s.to(device="cuda", dtype=torch.int8).contiguous()
+        out = self._u64(self.E * self.N)
+        _check(load().pdq_secret_prepare(self.h, _ptr(s), _ptr(out), _stream(stream)))
+        return out.view(self.E, self.N)
+
+    def encrypt(self, sk, slots, a, e, stream=None) -> torch.Tensor:
+        slots = slots.to(device="cuda", dtype=torch.int32).contiguous()
+        count = slots.numel() // self.N
+        a = a.to(device="cuda").contiguous()
+        e = e.to(device="cuda", dtype=torch.int32).contiguous()
+        out = self._u64(count * self.ct_elems)
+        _check(load().pdq_encrypt(self.h, _ptr(sk), _ptr(slots), count, _ptr(a), _ptr(e),
+                                  _ptr(out), _stream(stream)))
+        return out.view(count, 2, self.L, self.N)
+
+    def rotkey_gen(self, sk, galois: int, a, e, out=None, stream=None) -> torch.Tensor:
+        a = a.to(device="cuda").contiguous()
+        e = e.to(device="cuda", dtype=torch.int32).contiguous()
+        out = self._u64(self.key_elems) if out is None else out
+        _check(load().pdq_rotkey_gen(self.h, _ptr(sk), galois, _ptr(a), _ptr(e), _ptr(out),
+                                     _stream(stream)))
+        return out.view(self.ndigits, 2, self.E, self.N)
+
+    def decrypt(self, sk, ct, stream=None) -> torch.Tensor:
+        count = ct.numel() // self.ct_elems
+        out = torch.empty(count * self.N, dtype=torch.int32, device="cuda")
+        lib = load()
+        ws = self._ws(lib.pdq_decrypt_workspace_bytes(self.h, count))
+        _check(lib.pdq_decrypt(self.h, _ptr(sk), _ptr(ct), count, _ptr(out), _ptr(ws),
+                               ws.numel(), _stream(stream)))
+        return out.view(count, self.N)
+
+    def rotate(self, ct, galois: int, key, stream=None) -> torch.Tensor:
+        count = ct.numel() // self.ct_elems
+        lib = load()
+        ws = self._ws(lib.pdq_rotate_workspace_bytes(self.h, count))
+        out = torch.empty_like(ct)
+        _check(lib.pdq_rotate(self.h, _ptr(ct), count, galois, _ptr(key), _ptr(out), _ptr(ws),
+                              ws.numel(), _stream(stream)))
+        return out
+
+    # plans
+    def plan(self, n: int, s: int, B: int = 0) -> Plan:
+        pl = Plan()
+        _check(load().pdq_plan_make(self.h, n, s, B, ctypes.byref(pl)))
+        return pl
+
+    def plan_galois(self, plan: Plan) -> list[int]:
+        lib = load()
+        cnt = _U32()
+        _check(lib.pdq_plan_galois(self.h, ctypes.byref(plan), None, 0, ctypes.byref(cnt)))
+        arr = (ctypes.c_uint64 * cnt.value)()
+        _check(lib.pdq_plan_galois(self.h, ctypes.byref(plan), ctypes.cast(arr, _P), cnt.value,
+                                   ctypes.byref(cnt)))
+        return [int(x) for x in arr]
+
+    def plan_constants(self, plan: Plan, stream=None) -> torch.Tensor:
+        lib = load()
+        nbytes = lib.pdq_plan_constants_bytes(self.h, ctypes.byref(plan))
+        out = self._u64(nbytes // 8)
+        _check(lib.pdq_plan_constants_build(self.h, ctypes.byref(plan), _ptr(out),
+                                            _stream(stream)))
+        return out
+
+    def db_encode(self, values, stream=None) -> torch.Tensor:
+        values = values.to(device="cuda", dtype=torch.int32).contiguous()
+        n = values.numel()
+        lib = load()
+        out = self._u64(lib.pdq_db_bytes(self.h, n) // 8)
+        _check(lib.pdq_db_encode(self.h, _ptr(values), n, _ptr(out), _stream(stream)))
+        return out
+
+    # hot path
+    def mask(self, plan: Plan, v_cts, db, stream=None) -> torch.Tensor:
+        out = self._u64(plan.J * 4 * self.ct_elems)
+        _check(load().pdq_mask(self.h, ctypes.byref(plan), _ptr(v_cts), _ptr(db), _ptr(out),
+                               _stream(stream)))
+        return out.view(plan.J * 4, 2, self.L, self.N)
+
+    def comp_workspace(self, plan: Plan) -> torch.Tensor:
+        return self._ws(load().pdq_comp_workspace_bytes(self.h, ctypes.byref(plan)))
+
+    def answer_workspace(self, plan: Plan) -> torch.Tensor:
+        return self._ws(load().pdq_answer_workspace_bytes(self.h, ctypes.byref(plan)))
+
+    def comp(self, plan: Plan, masked, keys, galois, consts, ws=None, out=None, stream=None):
+        ws = self.comp_workspace(plan) if ws is None else ws
+        out = self._u64(plan.n_out * self.ct_elems) if out is None else out
+        gal = (ctypes.c_uint64 * len(galois))(*galois)
+        _check(load().pdq_comp(self.h, ctypes.byref(plan), _ptr(masked), _ptr(keys),
+                               ctypes.cast(gal, _P), len(galois), _ptr(consts), _ptr(out),
+                               _ptr(ws), ws.numel(), _stream(stream)))
+        return out.view(plan.n_out, 2, self.L, self.N)
+
+    def answer(self, plan: Plan, v_cts, db, keys, galois, consts, ws=None, out=None,
+               stream=None):
+        ws = self.answer_workspace(plan) if ws is None else ws
+        out = self._u64(plan.n_out * self.ct_elems) if out is None else out
+        gal = (ctypes.c_uint64 * len(galois))(*galois)
+        _check(load().pdq_answer(self.h, ctypes.byref(plan), _ptr(v_cts), _ptr(db), _ptr(keys),
+                                 ctypes.cast(gal, _P), len(galois), _ptr(consts), _ptr(out),
+                                 _ptr(ws), ws.numel(), _stream(stream)))
+        return out.view(plan.n_out, 2, self.L, self.N)
+
+    def answer_host_workspace(self, plan: Plan) -> torch.Tensor:
+        return self._ws(load().pdq_answer_host_workspace_bytes(self.h, ctypes.byref(plan)))
+
+    def answer_host(self, plan: Plan, v_host, db, keys, galois, consts, out_host, ws=None,
+                    stream=None):
+        """v_host / out_host: host tensors (pinned for full bandwidth), coefficient form."""
+        ws = self.answer_host_workspace(plan) if ws is None else ws
+        gal = (ctypes.c_uint64 * len(galois))(*galois)
+        _check(load().pdq_answer_host(self.h, ctypes.byref(plan), _ptr(v_host), _ptr(db),
+                                      _ptr(keys), ctypes.cast(gal, _P), len(galois), _ptr(consts),
+                                      _ptr(out_host), _ptr(ws), ws.numel(), _stream(stream)))
+        return out_host
+
+    def profile_enable(self, on: bool = True):
+        _check(load().pdq_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        """Summed milliseconds and call counts per stage since enabling."""
+        ms = (ctypes.c_float * len(STAGES))()
+        calls = (ctypes.c_uint32 * len(STAGES))()
+        _check(load().pdq_profile_read(self.h, ctypes.cast(ms, _P), ctypes.cast(calls, _P),
+                                       len(STAGES)))
+        return {name: (float(ms[i]), int(calls[i])) for i, name in enumerate(STAGES)}
+
+    def decomp(self, plan: Plan, slots) -> list[tuple[int, int]]:
+        """slots: [n_out][N] decrypted answer (host or device); returns sorted
+        (record index, value) pairs."""
+        s = np.ascontiguousarray(torch.as_tensor(slots).cpu().numpy().astype(np.uint32))
+        cap = max(1, plan.G * plan.s_prime)
+        idx = np.zeros(cap, dtype=np.uint64)
+        val = np.zeros(cap, dtype=np.uint32)
+        cnt = _U64()
+        _check(load().pdq_decomp(self.h, ctypes.byref(plan), _ptr(s), _ptr(idx), _ptr(val), cap,
+                                 ctypes.byref(cnt)))
+        n = cnt.value
+        return [(int(i), int(v)) for i, v in zip(idx[:n], val[:n])]
