@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--n", type=int, default=0, help="override the record count")
+    ap.add_argument("--s", type=int, default=0, help="override the sparsity")
     return ap.parse_args()
 
 
@@ -71,7 +73,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -186,6 +188,35 @@ def run_reference(args, cfg, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def run_e2e(args, ctx, plan, v_cts, db, keys, galois, consts, ws, stream, dist, world):
+    """queries/s through pdq_answer_host: H2D of the query, Mask+Comp, D2H of
+    the answer inside the timed region (pinned host buffers)."""
+    import torch
+    vc = v_cts.clone()
+    ctx.ntt_inverse(vc, 2 * plan.J, ctx.L)
+    v_host = vc.cpu().pin_memory()
+    del vc
+    out_host = torch.empty(plan.n_out * ctx.ct_elems, dtype=torch.int64).pin_memory()
+    ws_host = ctx.answer_host_workspace(plan)
+    for _ in range(2):
+        ctx.answer_host(plan, v_host, db, keys, galois, consts, out_host, ws=ws_host, stream=stream)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.answer_host(plan, v_host, db, keys, galois, consts, out_host, ws=ws_host, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": "queries/s",
+           "h2d_bytes_per_step": v_host.numel() * 8, "d2h_bytes_per_step": out_host.numel() * 8,
+           "steps": args.e2e_steps, "entry_point": "pdq_answer_host"}
+    return e2e
+
+
 # ------------------------------------------------------------------ GPU arm --
 
 def run_gpu(args, cfg, rank: int, world: int):
@@ -250,11 +281,13 @@ def run_gpu(args, cfg, rank: int, world: int):
     ctx.profile_enable(True)
     launches0 = pdq.pdq_launch_count()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")
     ev[0].record(stream)
     for i in range(args.steps):
         step()
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = pdq.pdq_launch_count() - launches0
     clk = clocks.stop()
     stages = ctx.profile_read()
@@ -269,34 +302,16 @@ def run_gpu(args, cfg, rank: int, world: int):
 
     # end to end through the host-buffer entry point (pinned host buffers,
     # coefficient form, copies inside the timed region)
-    vc = v_cts.clone()
-    ctx.ntt_inverse(vc, 2 * plan.J, ctx.L)
-    v_host = vc.cpu().pin_memory()
-    del vc
-    out_host = torch.empty(plan.n_out * ctx.ct_elems, dtype=torch.int64).pin_memory()
-    ws_host = ctx.answer_host_workspace(plan)
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(args, ctx, plan, v_cts, db, keys, galois, consts, ws, stream, dist, world)
     del ws
-    for _ in range(2):
-        ctx.answer_host(plan, v_host, db, keys, galois, consts, out_host, ws=ws_host, stream=stream)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        ctx.answer_host(plan, v_host, db, keys, galois, consts, out_host, ws=ws_host, stream=stream)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": "queries/s",
-           "h2d_bytes_per_step": v_host.numel() * 8, "d2h_bytes_per_step": out_host.numel() * 8,
-           "steps": args.e2e_steps, "entry_point": "pdq_answer_host"}
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
+
     # roofline of the diagonal multiply-accumulate kernel (one launch per query)
     mac_ms, mac_calls = stages["mac"]
     mac_ms_per = mac_ms / max(1, mac_calls)
@@ -336,8 +351,11 @@ def run_gpu(args, cfg, rank: int, world: int):
 
 def main():
     args = parse()
+    import dataclasses
     import workloads as W
     cfg = W.CONFIGS[args.config]
+    if args.n or args.s:
+        cfg = dataclasses.replace(cfg, n=args.n or cfg.n, s=args.s or cfg.s)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
