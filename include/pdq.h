@@ -246,6 +246,25 @@ int pdq_answer_host(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_
 int pdq_decomp(const pdq_ctx* ctx, const pdq_plan* plan, const uint32_t* slots,
                uint64_t* idx_out, uint32_t* val_out, uint64_t cap, uint64_t* count);
 
+/* ------------------------------------------------- rotation without alloc
+ * The paper has no counterpart to this call: it exists for callers that
+ * cannot allocate device memory where they rotate (an external memory
+ * manager owns every byte, a hard device-memory budget, or a serving loop
+ * that must not risk an allocation synchronising the device).
+ * Same result as pdq_rotate (bit for bit), but the key-switching scratch is
+ * a fixed array of pdq_rotate_noalloc_max_bytes() bytes (32 MiB) that the
+ * library reserves on every GPU that loads it, until the process exits; the
+ * call itself allocates nothing.  The first call on a device looks up that
+ * array's address (once per device), so make it before any stream capture.
+ * Calls share the array: two calls that overlap on the GPU race.  Every
+ * scratch byte is written before it is read, so nothing needs clearing.
+ * Errors: PDQ_E_PARAM if `count` ciphertexts need more scratch than the
+ * array holds (pdq_rotate_workspace_bytes(count) > the maximum), PDQ_E_CUDA
+ * if the address look-up fails. */
+size_t pdq_rotate_noalloc_max_bytes(void);
+int pdq_rotate_noalloc(const pdq_ctx* ctx, const uint64_t* ct_in, uint32_t count,
+                       uint64_t galois, const uint64_t* key, uint64_t* ct_out, void* stream);
+
 /* -------------------------------------------------------- instrumentation
  * Not part of the paper's method: counters for measuring the library.
  * pdq_launch_count: kernels this library has launched in this process.

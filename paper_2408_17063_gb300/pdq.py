@@ -89,6 +89,8 @@ _SIGS = {
                              _P]),
     "pdq_decomp": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _U64, ctypes.POINTER(_U64)]),
     "pdq_launch_count": (ctypes.c_ulonglong, []),
+    "pdq_rotate_noalloc_max_bytes": (_SZ, []),
+    "pdq_rotate_noalloc": (_I, [_P, _P, _U32, _U64, _P, _P, _P]),
     "pdq_profile_enable": (_I, [_P, _I]),
     "pdq_profile_read": (_I, [_P, _P, _P, _U32]),
 }
@@ -257,6 +259,15 @@ class Context:
         out = torch.empty_like(ct)
         _check(lib.pdq_rotate(self.h, _ptr(ct), count, galois, _ptr(key), _ptr(out), _ptr(ws),
                               ws.numel(), _stream(stream)))
+        return out
+
+    def rotate_noalloc(self, ct, galois: int, key, out=None, stream=None) -> torch.Tensor:
+        """pdq_rotate without a workspace: the library's fixed device scratch
+        is used (no allocation inside the call; `out` may be preallocated)."""
+        count = ct.numel() // self.ct_elems
+        out = torch.empty_like(ct) if out is None else out
+        _check(load().pdq_rotate_noalloc(self.h, _ptr(ct), count, galois, _ptr(key), _ptr(out),
+                                         _stream(stream)))
         return out
 
     # plans
