@@ -151,7 +151,7 @@ static int upload(T** dst, const std::vector<T>& src) {
 
 static void free_ctx(Ctx* c) {
     if (!c) return;
-    void* ptrs[] = {c->d_mods, c->d_fw, c->d_fw_shoup, c->d_iw, c->d_iw_shoup, c->d_ninv,
+    void* ptrs[] = {c->d_mods, c->d_fw2, c->d_iw2, c->d_ninv,
                     c->d_slot_pos, c->d_rowmask, c->d_up_hatinv, c->d_up_hatinv_shoup,
                     c->d_up_hatmod, c->d_dn_hatinv, c->d_dn_hatinv_shoup, c->d_dn_hatmod,
                     c->d_dn_pinv, c->d_dn_pinv_shoup, c->d_P_mod_q, c->d_delta_mod_q,
@@ -250,10 +250,15 @@ static int build_ctx(const pdq_params& p, Ctx* c) {
         ninv[4 * mi + 3] = shoup_of(n1, q);
     }
     PDQ_TRY(upload(&c->d_mods, c->hmods));
-    PDQ_TRY(upload(&c->d_fw, fw));
-    PDQ_TRY(upload(&c->d_fw_shoup, fws));
-    PDQ_TRY(upload(&c->d_iw, iw));
-    PDQ_TRY(upload(&c->d_iw_shoup, iws));
+    std::vector<u64> fw2(2 * (size_t)nm * N), iw2(2 * (size_t)nm * N);
+    for (size_t i = 0; i < (size_t)nm * N; ++i) {
+        fw2[2 * i] = fw[i];
+        fw2[2 * i + 1] = fws[i];
+        iw2[2 * i] = iw[i];
+        iw2[2 * i + 1] = iws[i];
+    }
+    PDQ_TRY(upload(&c->d_fw2, fw2));
+    PDQ_TRY(upload(&c->d_iw2, iw2));
     PDQ_TRY(upload(&c->d_ninv, ninv));
 
     // slot position in the transform output: slot (rho, c) is the value at

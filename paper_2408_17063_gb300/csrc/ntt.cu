@@ -33,8 +33,7 @@ struct NttArgs {
     u32 nlimbs;        // limbs per group
     u32 limb0;         // modulus index of the first limb
     const Mod* mods;
-    const u64* tw;     // [nmod][N] twiddles (forward or inverse)
-    const u64* tws;    // Shoup companions
+    const ulonglong2* tw;  // [nmod][N] (twiddle, Shoup companion), forward or inverse
     const u64* ninv4;  // [nmod][4]
     u32 logN;
     u32 S1;            // levels done by the column phase (0: single phase)
@@ -43,16 +42,27 @@ struct NttArgs {
 };
 
 __device__ __forceinline__ void bf_fwd(u64& x, u64& y, u64 w, u64 wp, u64 q) {
-    u64 a = csub(x, 2 * q);
-    u64 t = mul_shoup_lazy(y, w, wp, q);
+    const u64 a = csub(x, 2 * q);
+    const u64 t = mul_shoup_lazy(y, w, wp, q);
     x = a + t;
     y = a - t + 2 * q;
 }
 
 __device__ __forceinline__ void bf_inv(u64& x, u64& y, u64 w, u64 wp, u64 q) {
-    u64 a = x, b = y;
+    const u64 a = x, b = y;
     x = csub(a + b, 2 * q);
     y = mul_shoup_lazy(a - b + 2 * q, w, wp, q);
+}
+
+// Shared-memory word of element l of sub-transform c.  Column tiles hold
+// rows of C >= 16 consecutive columns (conflict-free as is); row tiles get
+// one pad word every 8 so that the strided accesses of the low passes hit
+// distinct banks.
+template <int S, bool COLS>
+__device__ __forceinline__ u32 smem_index(u32 c, u32 l, u32 logC) {
+    if (COLS) return (l << logC) + c;
+    const u32 w = (c << S) + l;
+    return w + (w >> 3);
 }
 
 template <bool FWD, int S, bool COLS>
@@ -60,62 +70,67 @@ struct Phase {
     static constexpr u32 GS = 1u << S;
 
     u64* sm;
-    const NttArgs& a;
+    const ulonglong2* tw;
     u64 q;
-    const u64* tw;
-    const u64* tws;
     u64 n0, n0s, n1, n1s;  // N^-1 and psi^-1 N^-1 (with Shoup) for level 0
-    u32 sub0, st0, S2, C;
+    u32 logN, logC, C, sub0, S2;
 
-    __device__ __forceinline__ u64 gidx(u32 c, u32 l) const {
-        return COLS ? (((u64)l) << S2) + sub0 + c : (((u64)(sub0 + c)) << S2) + l;
-    }
-    __device__ __forceinline__ u32 sidx(u32 c, u32 l) const {
-        return COLS ? (l << a.logC) + c : c * GS + l;
+    // global index of element l of sub-transform c
+    __device__ __forceinline__ u32 gidx(u32 c, u32 l) const {
+        return COLS ? (l << S2) + sub0 + c : ((sub0 + c) << S) + l;
     }
 
-    // One pass over the R local levels whose pair bits are lb .. lb+R-1.
+    // One pass over the R local levels whose pair bits are lb .. lb+R-1:
+    // every thread item holds the 2^R elements that these levels combine.
     template <int R>
     __device__ __forceinline__ void pass(u32 lb) const {
         constexpr u32 NE = 1u << R;
         const u32 items = (C * GS) >> R;
         const u32 lowmask = (1u << lb) - 1;
+        const u32 gsh = lb + (COLS ? S2 : 0u);   // global position of pass bit 0
         for (u32 w = threadIdx.x; w < items; w += blockDim.x) {
             u32 c, fixed;
             if (COLS) {
                 c = w & (C - 1);
-                fixed = w >> a.logC;
+                fixed = w >> logC;
             } else {
                 fixed = w & ((GS >> R) - 1);
                 c = w >> (S - R);
             }
             const u32 lbase = (fixed & lowmask) | ((fixed >> lb) << (lb + R));
+            const u32 jbase = gidx(c, lbase);
             u64 x[NE];
 #pragma unroll
-            for (u32 k = 0; k < NE; ++k) x[k] = sm[sidx(c, lbase | (k << lb))];
+            for (u32 k = 0; k < NE; ++k) x[k] = sm[smem_index<S, COLS>(c, lbase | (k << lb), logC)];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const u32 kb = FWD ? (u32)(R - 1 - r) : (u32)r;
-                const u32 half = 1u << kb;
-                const u32 st = st0 + (S - 1 - (lb + kb));   // global level
+                const int kb = FWD ? R - 1 - r : r;          // pair bit inside the item
+                const u32 P = gsh + kb;                      // pair bit in the global index
+                const u32 st = logN - 1 - P;                 // radix-2 level
+                const u32 ti0 = (1u << st) + (jbase >> (P + 1));
 #pragma unroll
-                for (u32 k = 0; k < NE; ++k) {
-                    if (k & half) continue;
-                    const u64 j = gidx(c, lbase | (k << lb));
-                    const u32 ti = (1u << st) + (u32)(j >> (a.logN - st));
-                    if (FWD) {
-                        bf_fwd(x[k], x[k | half], __ldg(tw + ti), __ldg(tws + ti), q);
-                    } else if (st == 0) {
-                        u64 xa = x[k], xb = x[k | half];
-                        x[k] = mul_shoup_lazy(xa + xb, n0, n0s, q);
-                        x[k | half] = mul_shoup_lazy(xa - xb + 2 * q, n1, n1s, q);
+                for (int id = 0; id < (int)(NE >> (kb + 1)); ++id) {
+                    if (!FWD && st == 0) {
+#pragma unroll
+                        for (int low = 0; low < (1 << kb); ++low) {
+                            const int k = (id << (kb + 1)) | low;
+                            const u64 xa = x[k], xb = x[k + (1 << kb)];
+                            x[k] = mul_shoup_lazy(xa + xb, n0, n0s, q);
+                            x[k + (1 << kb)] = mul_shoup_lazy(xa - xb + 2 * q, n1, n1s, q);
+                        }
                     } else {
-                        bf_inv(x[k], x[k | half], __ldg(tw + ti), __ldg(tws + ti), q);
+                        const ulonglong2 wv = __ldg(tw + ti0 + id);
+#pragma unroll
+                        for (int low = 0; low < (1 << kb); ++low) {
+                            const int k = (id << (kb + 1)) | low;
+                            if (FWD) bf_fwd(x[k], x[k + (1 << kb)], wv.x, wv.y, q);
+                            else bf_inv(x[k], x[k + (1 << kb)], wv.x, wv.y, q);
+                        }
                     }
                 }
             }
 #pragma unroll
-            for (u32 k = 0; k < NE; ++k) sm[sidx(c, lbase | (k << lb))] = x[k];
+            for (u32 k = 0; k < NE; ++k) sm[smem_index<S, COLS>(c, lbase | (k << lb), logC)] = x[k];
         }
         __syncthreads();
     }
@@ -141,27 +156,27 @@ struct Phase {
 };
 
 template <bool FWD, int S, bool COLS>
-__global__ void __launch_bounds__(kThreads) ntt_phase_kernel(NttArgs a) {
-    __shared__ u64 sm[kTile];
+__global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
+    __shared__ u64 sm[kTile + kTile / 8];
     const u32 p = blockIdx.x;
-    const u32 grp = p / a.nlimbs, limb = p % a.nlimbs;
+    const u32 grp = p / a.nlimbs, limb = p - grp * a.nlimbs;
     const u32 mi = a.limb0 + limb;
-    const u64 N = 1ull << a.logN;
+    const u32 N = 1u << a.logN;
     u64* base = a.data + (u64)grp * a.stride + (u64)limb * N;
 
-    Phase<FWD, S, COLS> ph{sm, a};
+    Phase<FWD, S, COLS> ph;
+    ph.sm = sm;
     ph.q = a.mods[mi].q;
     ph.tw = a.tw + (u64)mi * N;
-    ph.tws = a.tws + (u64)mi * N;
     ph.n0 = a.ninv4[4 * mi + 0];
     ph.n0s = a.ninv4[4 * mi + 1];
     ph.n1 = a.ninv4[4 * mi + 2];
     ph.n1s = a.ninv4[4 * mi + 3];
+    ph.logN = a.logN;
+    ph.logC = a.logC;
     ph.C = 1u << a.logC;
-    ph.sub0 = blockIdx.y * ph.C;
-    ph.st0 = COLS ? 0 : a.S1;
-    ph.S2 = a.logN - a.S1;
-    if (COLS) ph.S2 = a.logN - S;
+    ph.sub0 = blockIdx.y << a.logC;
+    ph.S2 = a.logN - S;               // column phase: stride of the column elements
 
     constexpr u32 GS = 1u << S;
     const u32 T = ph.C * GS;
@@ -169,7 +184,7 @@ __global__ void __launch_bounds__(kThreads) ntt_phase_kernel(NttArgs a) {
         u32 c, l;
         if (COLS) { l = e >> a.logC; c = e & (ph.C - 1); }
         else { c = e >> S; l = e & (GS - 1); }
-        sm[ph.sidx(c, l)] = base[ph.gidx(c, l)];
+        sm[smem_index<S, COLS>(c, l, a.logC)] = base[ph.gidx(c, l)];
     }
     __syncthreads();
     ph.run();
@@ -178,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) ntt_phase_kernel(NttArgs a) {
         u32 c, l;
         if (COLS) { l = e >> a.logC; c = e & (ph.C - 1); }
         else { c = e >> S; l = e & (GS - 1); }
-        u64 v = sm[ph.sidx(c, l)];
+        u64 v = sm[smem_index<S, COLS>(c, l, a.logC)];
         if (a.last) v = FWD ? csub(csub(v, 2 * q), q) : csub(v, q);
         base[ph.gidx(c, l)] = v;
     }
@@ -209,8 +224,7 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
     a.nlimbs = nlimbs;
     a.limb0 = limb0;
     a.mods = c.d_mods;
-    a.tw = FWD ? c.d_fw : c.d_iw;
-    a.tws = FWD ? c.d_fw_shoup : c.d_iw_shoup;
+    a.tw = reinterpret_cast<const ulonglong2*>(FWD ? c.d_fw2 : c.d_iw2);
     a.ninv4 = c.d_ninv;
     a.logN = c.log_n;
     if (c.log_n <= 11) {

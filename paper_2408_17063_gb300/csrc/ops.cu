@@ -6,6 +6,10 @@
 // All kernels read and write canonical residues.  Products of two residues
 // are formed as 128-bit values and reduced once (reduce128), or summed
 // unreduced in a 128-bit accumulator first when several products meet.
+// Launch shape: a 2-D (or 3-D) grid whose x dimension walks the N (or L*N,
+// E*N) positions of one polynomial block in 256-thread CTAs and whose y/z
+// dimensions enumerate ciphertexts, limbs or digits, so that every index is
+// a shift or a mask of 32-bit values.
 #include "pdq_internal.h"
 #include "pdq_ops.h"
 
@@ -15,446 +19,468 @@ namespace {
 
 constexpr u32 kBlock = 256;
 
-inline dim3 grid_for(u64 total) {
-    u64 b = (total + kBlock - 1) / kBlock;
-    if (b > (1u << 20)) b = 1u << 20;
-    if (b == 0) b = 1;
-    return dim3((u32)b);
+inline dim3 grid2(u64 xlen, u32 y, u32 z = 1) {
+    return dim3((u32)((xlen + kBlock - 1) / kBlock), y, z);
+}
+
+inline int check_y(u64 y, const char* what) {
+    if (y == 0 || y > 65535) return fail(PDQ_E_PARAM, std::string(what) + ": batch size out of range");
+    return PDQ_OK;
 }
 
 // Position holding a(psi^{e k}) for the position x that holds a(psi^e):
-// sigma_k in the bit-reversed evaluation domain.
+// sigma_k in the bit-reversed evaluation domain.  Aligned tiles of 2^i
+// consecutive positions map onto aligned tiles (k is odd), so warps gather
+// from one contiguous 256-byte span.
 __device__ __forceinline__ u32 auto_index(u32 x, u32 k, u32 logN) {
     const u32 twoN_mask = (2u << logN) - 1;
     const u32 e = 2 * (__brev(x) >> (32 - logN)) + 1;
-    const u32 e2 = (u32)(((u64)e * k) & twoN_mask);
+    const u32 e2 = (e * k) & twoN_mask;
     return __brev((e2 - 1) >> 1) >> (32 - logN);
 }
 
 // ------------------------------------------------------------- encoding ----
 
-__global__ void k_scatter_slots(const u32* __restrict__ slots, u32 count, u32 N, u64 lstride,
+// out[c][0][pos[idx]] = slots[c][idx] mod t
+__global__ void k_scatter_slots(const u32* __restrict__ slots, u32 logN, u64 lstride,
                                 const u32* __restrict__ pos, u64 t, u64* __restrict__ out) {
-    const u64 total = (u64)count * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / N, idx = i % N;
-        out[c * lstride + pos[idx]] = slots[i] % t;
-    }
+    const u32 idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (1u << logN)) return;
+    const u32 c = blockIdx.y;
+    out[c * lstride + pos[idx]] = slots[((u64)c << logN) + idx] % t;
 }
 
-__global__ void k_lift(u64* __restrict__ out, u32 count, u32 N, u32 nlimbs,
-                       const Mod* __restrict__ mods, u64 t) {
-    const u64 total = (u64)count * N;
+// centred lift of limb 0 (mod t) to limbs 0..nlimbs-1 (limb 0 written last)
+__global__ void k_lift(u64* __restrict__ out, u32 logN, u32 nlimbs, const Mod* __restrict__ mods,
+                       u64 t) {
+    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (1u << logN)) return;
+    u64* base = out + (((u64)blockIdx.y * nlimbs) << logN) + x;
+    const u64 v = base[0];
     const u64 half = (t - 1) / 2;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / N, x = i % N;
-        u64* base = out + c * nlimbs * (u64)N + x;
-        const u64 v = base[0];
-        for (int l = (int)nlimbs - 1; l >= 0; --l) {
-            const u64 q = mods[l].q;
-            base[(u64)l * N] = v > half ? q - (t - v) : v;
-        }
+    for (int l = (int)nlimbs - 1; l >= 0; --l) {
+        const u64 q = mods[l].q;
+        base[(u64)l << logN] = v > half ? q - (t - v) : v;
     }
 }
 
-// diagonal slot values, rotated by -gB, scattered to transform positions
-__global__ void k_diag_slots(u64* __restrict__ out, u32 hclass, u32 giants, u32 B, u32 s_prime,
-                             u32 m, u32 N, u32 L, const u32* __restrict__ pos, u64 t) {
-    const u64 total = (u64)hclass * giants * B * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 pt = i / N;
-        const u32 idx = (u32)(i % N);
-        const u32 a = (u32)(pt % B);
-        const u32 g = (u32)((pt / B) % giants);
-        const u32 cls = (u32)(pt / ((u64)B * giants));
-        const u32 col = idx % m;
-        const u32 k = g * B + a;
-        const u32 cp = (col + m - (g * B) % m) % m;        // Rot(.; -gB)
-        const u64 node = (u64)cls * m + (cp + k) % m + 1;
-        u32 e = cp % s_prime + 1;
-        u64 r = 1, b = node % t;
-        while (e) {
-            if (e & 1) r = r * b % t;
-            b = b * b % t;
-            e >>= 1;
-        }
-        out[pt * (u64)L * N + pos[idx]] = r;
+// Diagonal slot values D_{h,gB+a} rotated by -gB (both rows), scattered to
+// transform positions; one plaintext (cls, g, a) per grid row.
+__global__ void k_diag_slots(u64* __restrict__ out, u32 giants, u32 B, u32 s_prime, u32 logN,
+                             u32 L, const u32* __restrict__ pos, u64 t) {
+    const u32 idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 N = 1u << logN, m = N / 2;
+    if (idx >= N) return;
+    const u32 pt = blockIdx.y;
+    const u32 a = pt % B;
+    const u32 g = (pt / B) % giants;
+    const u32 cls = pt / (B * giants);
+    const u32 col = idx & (m - 1);
+    const u32 k = g * B + a;
+    const u32 cp = (col + m - (g * B) % m) & (m - 1);        // Rot(.; -gB)
+    const u64 node = (u64)cls * m + ((cp + k) & (m - 1)) + 1;
+    u32 e = (cp & (s_prime - 1)) + 1;
+    u64 r = 1, b = node % t;
+    while (e) {
+        if (e & 1) r = r * b % t;
+        b = b * b % t;
+        e >>= 1;
     }
+    out[(((u64)pt * L) << logN) + pos[idx]] = r;
 }
 
-// database plaintexts: for ciphertext j, [DB.[1;0], DB.[0;1]]
-__global__ void k_db_slots(u64* __restrict__ out, const u32* __restrict__ values, u64 n, u32 J,
-                           u32 m, u32 N, u32 L, const u32* __restrict__ pos, u64 t) {
-    const u64 total = (u64)J * 2 * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 pt = i / N;               // j*2 + half
-        const u32 idx = (u32)(i % N);
-        const u64 j = pt / 2, half = pt % 2;
-        const u64 rec = j * N + idx;
-        const bool row_ok = (idx >= m) == (half == 1);
-        const u64 v = (row_ok && rec < n) ? (u64)values[rec] % t : 0;
-        out[pt * (u64)L * N + pos[idx]] = v;
-    }
+// database plaintexts: row pt = 2j + half holds DB_j.[1;0] (half 0) or DB_j.[0;1]
+__global__ void k_db_slots(u64* __restrict__ out, const u32* __restrict__ values, u64 n, u32 logN,
+                           u32 L, const u32* __restrict__ pos, u64 t) {
+    const u32 idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 N = 1u << logN, m = N / 2;
+    if (idx >= N) return;
+    const u32 pt = blockIdx.y;
+    const u64 j = pt >> 1;
+    const u32 half = pt & 1;
+    const u64 rec = (j << logN) + idx;
+    const bool row_ok = (idx >= m) == (half == 1);
+    const u64 v = (row_ok && rec < n) ? (u64)values[rec] % t : 0;
+    out[(((u64)pt * L) << logN) + pos[idx]] = v;
 }
 
 // group mask o: ones at slots [o s', (o+1) s') of both rows
-__global__ void k_groupmask_slots(u64* __restrict__ out, u32 per_out, u32 s_prime, u32 m, u32 N,
-                                  u32 L, const u32* __restrict__ pos) {
-    const u64 total = (u64)per_out * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 o = i / N;
-        const u32 idx = (u32)(i % N);
-        const u32 col = idx % m;
-        out[o * (u64)L * N + pos[idx]] = (col / s_prime == o) ? 1 : 0;
-    }
+__global__ void k_groupmask_slots(u64* __restrict__ out, u32 s_prime, u32 logN, u32 L,
+                                  const u32* __restrict__ pos) {
+    const u32 idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 N = 1u << logN, m = N / 2;
+    if (idx >= N) return;
+    const u32 o = blockIdx.y;
+    const u32 col = idx & (m - 1);
+    out[(((u64)o * L) << logN) + pos[idx]] = (col / s_prime == o) ? 1 : 0;
 }
 
 // ------------------------------------------------------- keys / encryption -
 
-__global__ void k_signed_to_rns(const int8_t* __restrict__ s, u32 N, u32 nl,
-                                const Mod* __restrict__ mods, u64* __restrict__ out) {
-    const u64 total = (u64)nl * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u32 l = (u32)(i / N), x = (u32)(i % N);
-        const int v = s[x];
-        const u64 q = mods[l].q;
-        out[i] = v < 0 ? q - (u64)(-v) : (u64)v;
-    }
+// out[l][x] = s[x] mod (prime l), s small signed
+template <class T>
+__global__ void k_signed_to_rns(const T* __restrict__ s, u32 logN, const Mod* __restrict__ mods,
+                                u64* __restrict__ out) {
+    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (1u << logN)) return;
+    const u32 l = blockIdx.y;
+    const long long v = s[x];
+    const u64 q = mods[l].q;
+    out[((u64)l << logN) + x] = v < 0 ? q - (u64)(-v) : (u64)v;
 }
 
-// c0 = e + Delta * m (coefficient form); m read from limb 0 of c1's slot
-__global__ void k_enc_c0(u64* __restrict__ ct, const int32_t* __restrict__ e, u32 count, u32 N,
-                         u32 L, const Mod* __restrict__ mods, const u64* __restrict__ delta) {
-    const u64 total = (u64)count * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / N, x = i % N;
-        u64* c0 = ct + c * 2 * L * (u64)N;
-        const u64 m = c0[(u64)L * N + x];         // c1 limb 0 holds m mod t
-        const int ev = e[i];
-        for (u32 l = 0; l < L; ++l) {
-            const Mod md = mods[l];
-            const u64 ee = ev < 0 ? md.q - (u64)(-ev) : (u64)ev;
-            c0[(u64)l * N + x] = addmod(mulmod(m, delta[l], md), ee, md.q);
-        }
+// c0 = e + Delta * m (coefficient form); m read from limb 0 of c1
+__global__ void k_enc_c0(u64* __restrict__ ct, const int32_t* __restrict__ e, u32 logN, u32 L,
+                         const Mod* __restrict__ mods, const u64* __restrict__ delta) {
+    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (1u << logN)) return;
+    const u32 c = blockIdx.y;
+    u64* c0 = ct + (((u64)c * 2 * L) << logN);
+    const u64 m = c0[((u64)L << logN) + x];
+    const int ev = e[((u64)c << logN) + x];
+    for (u32 l = 0; l < L; ++l) {
+        const Mod md = mods[l];
+        const u64 ee = ev < 0 ? md.q - (u64)(-ev) : (u64)ev;
+        c0[((u64)l << logN) + x] = addmod(mulmod(m, delta[l], md), ee, md.q);
     }
 }
 
 __global__ void k_copy_rows(u64* __restrict__ dst, u64 dst_stride, const u64* __restrict__ src,
-                            u64 src_stride, u32 count, u64 len) {
-    const u64 total = (u64)count * len;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / len, x = i % len;
-        dst[c * dst_stride + x] = src[c * src_stride + x];
-    }
+                            u64 src_stride, u32 len) {
+    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= len) return;
+    const u32 c = blockIdx.y;
+    dst[c * dst_stride + x] = src[c * src_stride + x];
 }
 
 // c0 -= c1 * s (NTT form)
-__global__ void k_enc_finish(u64* __restrict__ ct, const u64* __restrict__ sk, u32 count, u32 N,
-                             u32 L, const Mod* __restrict__ mods) {
-    const u64 total = (u64)count * L * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / ((u64)L * N), r = i % ((u64)L * N);
-        const u32 l = (u32)(r / N);
-        const Mod md = mods[l];
-        u64* c0 = ct + c * 2 * L * (u64)N;
-        const u64 as = mulmod(c0[(u64)L * N + r], sk[r], md);
-        c0[r] = submod(c0[r], as, md.q);
-    }
+__global__ void k_enc_finish(u64* __restrict__ ct, const u64* __restrict__ sk, u32 logN, u32 L,
+                             const Mod* __restrict__ mods) {
+    const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (L << logN)) return;
+    const Mod md = mods[r >> logN];
+    u64* c0 = ct + (((u64)blockIdx.y * 2 * L) << logN);
+    const u64 as = mulmod(c0[((u64)L << logN) + r], sk[r], md);
+    c0[r] = submod(c0[r], as, md.q);
 }
 
 // key: b = b(e) - a*s + [l in digit] P sigma_k(s), all NTT form
-__global__ void k_key_finish(u64* __restrict__ key, const u64* __restrict__ sk, u32 nd, u32 E,
-                             u32 N, u32 logN, u32 galois, const Mod* __restrict__ mods,
+__global__ void k_key_finish(u64* __restrict__ key, const u64* __restrict__ sk, u32 E, u32 logN,
+                             u32 galois, const Mod* __restrict__ mods,
                              const u64* __restrict__ Pmodq, DigitBounds db) {
-    const u64 total = (u64)nd * E * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u32 b = (u32)(i / ((u64)E * N));
-        const u64 r = i % ((u64)E * N);
-        const u32 l = (u32)(r / N), x = (u32)(r % N);
-        const Mod md = mods[l];
-        u64* kb = key + (u64)b * 2 * E * N;
-        const u64 av = kb[(u64)E * N + r];
-        u64 v = submod(kb[r], mulmod(av, sk[r], md), md.q);
-        if (l >= db.lo[b] && l < db.hi[b]) {
-            const u64 sv = sk[(u64)l * N + auto_index(x, galois, logN)];
-            v = addmod(v, mulmod(sv, Pmodq[l], md), md.q);
-        }
-        kb[r] = v;
+    const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (E << logN)) return;
+    const u32 b = blockIdx.y;
+    const u32 l = r >> logN, x = r & ((1u << logN) - 1);
+    const Mod md = mods[l];
+    u64* kb = key + (((u64)b * 2 * E) << logN);
+    const u64 av = kb[((u64)E << logN) + r];
+    u64 v = submod(kb[r], mulmod(av, sk[r], md), md.q);
+    if (l >= db.lo[b] && l < db.hi[b]) {
+        const u64 sv = sk[((u64)l << logN) + auto_index(x, galois, logN)];
+        v = addmod(v, mulmod(sv, Pmodq[l], md), md.q);
     }
+    kb[r] = v;
 }
 
 // decryption: x = c0 + c1 s (NTT form) into ws
-__global__ void k_dec_inner(const u64* __restrict__ ct, const u64* __restrict__ sk, u32 count,
-                            u32 N, u32 L, const Mod* __restrict__ mods, u64* __restrict__ out) {
-    const u64 total = (u64)count * L * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / ((u64)L * N), r = i % ((u64)L * N);
-        const Mod md = mods[r / N];
-        const u64* c0 = ct + c * 2 * L * (u64)N;
-        out[i] = addmod(c0[r], mulmod(c0[(u64)L * N + r], sk[r], md), md.q);
-    }
+__global__ void k_dec_inner(const u64* __restrict__ ct, const u64* __restrict__ sk, u32 logN,
+                            u32 L, const Mod* __restrict__ mods, u64* __restrict__ out) {
+    const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (L << logN)) return;
+    const Mod md = mods[r >> logN];
+    const u64* c0 = ct + (((u64)blockIdx.y * 2 * L) << logN);
+    out[(((u64)blockIdx.y * L) << logN) + r] =
+        addmod(c0[r], mulmod(c0[((u64)L << logN) + r], sk[r], md), md.q);
 }
 
-// m = round(sum_i [x_i omega_i]_{q_i} t / q_i) mod t, written to limb 0 of
-// a [count][1][N] buffer (mod t)
-__global__ void k_dec_round(const u64* __restrict__ x, u32 count, u32 N, u32 L,
+// m = round(sum_i [x_i omega_i]_{q_i} t / q_i) mod t  (x in coefficient form)
+__global__ void k_dec_round(const u64* __restrict__ x, u32 logN, u32 L,
                             const Mod* __restrict__ mods, const u64* __restrict__ om,
                             const u64* __restrict__ oms, u64 t, u64* __restrict__ out) {
-    const u64 total = (u64)count * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / N, xi = i % N;
-        u64 ip = 0;        // integer part (mod t accumulation, < L t)
-        u128 fr = 0;       // fractional part, 64-bit fixed point
-        for (u32 l = 0; l < L; ++l) {
-            const u64 q = mods[l].q;
-            const u64 v = x[(c * L + l) * (u64)N + xi];
-            const u64 b = csub(mul_shoup_lazy(v, om[l], oms[l], q), q);
-            const u128 bt = (u128)b * t;
-            const u64 quo = (u64)(bt / q);
-            const u64 rem = (u64)(bt % q);
-            ip += quo % t;
-            fr += (u128)(u64)(((u128)rem << 64) / q);
-        }
-        const u64 whole = (u64)(fr >> 64);
-        const u64 lo = (u64)fr;
-        const u64 r = (ip + whole + (lo >> 63)) % t;
-        out[i] = r;
+    const u32 xi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (xi >= (1u << logN)) return;
+    const u64 c = blockIdx.y;
+    u64 ip = 0;        // integer part
+    u128 fr = 0;       // fractional part, 64-bit fixed point
+    for (u32 l = 0; l < L; ++l) {
+        const u64 q = mods[l].q;
+        const u64 v = x[((c * L + l) << logN) + xi];
+        const u64 b = csub(mul_shoup_lazy(v, om[l], oms[l], q), q);
+        const u128 bt = (u128)b * t;
+        const u64 quo = (u64)(bt / q);
+        const u64 rem = (u64)(bt % q);
+        ip += quo % t;
+        fr += (u128)(u64)(((u128)rem << 64) / q);
     }
+    const u64 whole = (u64)(fr >> 64);
+    const u64 lo = (u64)fr;
+    out[(c << logN) + xi] = (ip + whole + (lo >> 63)) % t;
 }
 
-__global__ void k_gather_slots(const u64* __restrict__ in, u32 count, u32 N,
-                               const u32* __restrict__ pos, u32* __restrict__ slots) {
-    const u64 total = (u64)count * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / N, idx = i % N;
-        slots[i] = (u32)in[c * N + pos[idx]];
-    }
+__global__ void k_gather_slots(const u64* __restrict__ in, u32 logN, const u32* __restrict__ pos,
+                               u32* __restrict__ slots) {
+    const u32 idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (1u << logN)) return;
+    const u64 c = blockIdx.y;
+    slots[(c << logN) + idx] = (u32)in[(c << logN) + pos[idx]];
 }
 
 // ------------------------------------------------------------------ Mask ----
 
 // out[j] = (v.[1;0], v.[0;1], v.(DB.[1;0]), v.(DB.[0;1]))
 __global__ void k_mask(const u64* __restrict__ v, const u64* __restrict__ db,
-                       const u64* __restrict__ rowmask, u32 J, u32 L, u32 N,
+                       const u64* __restrict__ rowmask, u32 L, u32 logN,
                        const Mod* __restrict__ mods, u64* __restrict__ out) {
-    const u64 LN = (u64)L * N;
-    const u64 total = (u64)J * LN;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 j = i / LN, r = i % LN;
-        const Mod md = mods[r / N];
-        const u64 v0 = v[j * 2 * LN + r], v1 = v[j * 2 * LN + LN + r];
-        const u64 pt[4] = {rowmask[r], rowmask[LN + r], db[j * 2 * LN + r], db[j * 2 * LN + LN + r]};
-        u64* o = out + j * 8 * LN;
+    const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 LN = (u64)L << logN;
+    if (r >= LN) return;
+    const u64 j = blockIdx.y;
+    const Mod md = mods[r >> logN];
+    const u64 v0 = v[j * 2 * LN + r], v1 = v[j * 2 * LN + LN + r];
+    const u64 pt[4] = {rowmask[r], rowmask[LN + r], db[j * 2 * LN + r], db[j * 2 * LN + LN + r]};
+    u64* o = out + j * 8 * LN;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            o[(2 * k) * LN + r] = mulmod(v0, pt[k], md);
-            o[(2 * k + 1) * LN + r] = mulmod(v1, pt[k], md);
-        }
+    for (int k = 0; k < 4; ++k) {
+        o[(2 * k) * LN + r] = mulmod(v0, pt[k], md);
+        o[(2 * k + 1) * LN + r] = mulmod(v1, pt[k], md);
     }
 }
 
 // ---------------------------------------------------------- key switching --
 
-// Raise every digit of c1 (coefficient form X [cnt][L][N]) to the extended
-// basis: D[ct][beta][r] for r outside the digit (coefficient form, to be
-// transformed), and for r inside the digit the NTT-form c1 limb is copied.
-__global__ void k_modup(const u64* __restrict__ X, CtSet c1ntt, u32 cnt, u32 N, u32 L, u32 E,
-                        u32 nd, u32 alpha, const Mod* __restrict__ mods,
-                        const u64* __restrict__ hinv, const u64* __restrict__ hinvs,
-                        const u64* __restrict__ hmod, u64* __restrict__ D) {
-    const u64 total = (u64)cnt * nd * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 ct = i / ((u64)nd * N);
-        const u32 b = (u32)((i / N) % nd);
-        const u32 x = (u32)(i % N);
-        const u32 lo = b * alpha, hi = min(lo + alpha, L);
-        u64 y[8];
-        const u64* Xc = X + ct * (u64)L * N;
-        for (u32 l = lo; l < hi; ++l) {
-            const u64 q = mods[l].q;
-            y[l - lo] = csub(mul_shoup_lazy(Xc[(u64)l * N + x], hinv[l], hinvs[l], q), q);
+// Raise digit b = blockIdx.y of c1 (coefficient form X [cnt][L][N]) of
+// ciphertext blockIdx.z to the extended basis: D[ct][b][r] for r outside
+// the digit (coefficient form, transformed afterwards); inside the digit
+// the NTT-form c1 limb is copied.
+__global__ void k_modup(const u64* __restrict__ X, CtSet c1ntt, u32 logN, u32 L, u32 E,
+                        u32 alpha, const Mod* __restrict__ mods, const u64* __restrict__ hinv,
+                        const u64* __restrict__ hinvs, const u64* __restrict__ hmod,
+                        u64* __restrict__ D) {
+    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (1u << logN)) return;
+    const u32 b = blockIdx.y, nd = gridDim.y;
+    const u64 ct = blockIdx.z;
+    const u32 lo = b * alpha, hi = min(lo + alpha, L);
+    u64 y[8];
+    const u64* Xc = X + ((ct * L) << logN);
+    for (u32 l = lo; l < hi; ++l) {
+        const u64 q = mods[l].q;
+        y[l - lo] = csub(mul_shoup_lazy(Xc[((u64)l << logN) + x], hinv[l], hinvs[l], q), q);
+    }
+    u64* Dc = D + (((ct * nd + b) * E) << logN);
+    const u64* src = c1ntt.at(ct) + ((u64)L << logN);    // c1 of the input (NTT form)
+    for (u32 r = 0; r < E; ++r) {
+        if (r >= lo && r < hi) {
+            Dc[((u64)r << logN) + x] = src[((u64)r << logN) + x];
+            continue;
         }
-        u64* Dc = D + (ct * nd + b) * (u64)E * N;
-        const u64* src = c1ntt.at(ct) + (u64)L * N;    // c1 of the input (NTT form)
-        for (u32 r = 0; r < E; ++r) {
-            if (r >= lo && r < hi) {
-                Dc[(u64)r * N + x] = src[(u64)r * N + x];
-                continue;
-            }
-            const Mod md = mods[r];
-            u64 ah = 0, al = 0;
-            for (u32 l = lo; l < hi; ++l) mac128(ah, al, y[l - lo], hmod[(u64)l * E + r]);
-            Dc[(u64)r * N + x] = reduce128(ah, al, md);
-        }
+        u64 ah = 0, al = 0;
+        for (u32 l = lo; l < hi; ++l) mac128(ah, al, y[l - lo], hmod[(u64)l * E + r]);
+        Dc[((u64)r << logN) + x] = reduce128(ah, al, mods[r]);
     }
 }
 
 // A[ct][p][r][x] = sum_beta D[ct][beta][r][sigma(x)] * key[beta][p][r][x]
-__global__ void k_ks_inner(const u64* __restrict__ D, const u64* __restrict__ key, u32 cnt, u32 N,
-                           u32 logN, u32 E, u32 nd, u32 galois, const Mod* __restrict__ mods,
+__global__ void k_ks_inner(const u64* __restrict__ D, const u64* __restrict__ key, u32 logN,
+                           u32 E, u32 nd, u32 galois, const Mod* __restrict__ mods,
                            u64* __restrict__ A) {
-    const u64 EN = (u64)E * N;
-    const u64 total = (u64)cnt * EN;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 ct = i / EN, r = i % EN;
-        const u32 l = (u32)(r / N), x = (u32)(r % N);
-        const u32 sx = auto_index(x, galois, logN);
-        u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
-        for (u32 b = 0; b < nd; ++b) {
-            const u64 d = D[(ct * nd + b) * EN + (u64)l * N + sx];
-            mac128(h0, l0, d, key[(u64)b * 2 * EN + r]);
-            mac128(h1, l1, d, key[(u64)b * 2 * EN + EN + r]);
-        }
-        const Mod md = mods[l];
-        A[ct * 2 * EN + r] = reduce128(h0, l0, md);
-        A[ct * 2 * EN + EN + r] = reduce128(h1, l1, md);
+    const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 EN = (u64)E << logN;
+    if (r >= EN) return;
+    const u64 ct = blockIdx.y;
+    const u32 l = r >> logN, x = r & ((1u << logN) - 1);
+    const u32 sr = (l << logN) + auto_index(x, galois, logN);
+    u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+    const u64* Dc = D + ct * nd * EN;
+    for (u32 b = 0; b < nd; ++b) {
+        const u64 d = Dc[b * EN + sr];
+        mac128(h0, l0, d, key[b * 2 * EN + r]);
+        mac128(h1, l1, d, key[b * 2 * EN + EN + r]);
     }
+    const Mod md = mods[l];
+    A[ct * 2 * EN + r] = reduce128(h0, l0, md);
+    A[ct * 2 * EN + EN + r] = reduce128(h1, l1, md);
 }
 
-// Conv[ct][p][i] = sum_k [y_k (P/p_k)^-1]_{p_k} (P/p_k) mod q_i from the
-// special limbs of A (coefficient form)
-__global__ void k_moddown_conv(const u64* __restrict__ A, u32 cnt, u32 N, u32 L, u32 K,
+// Conv[cp][i] = sum_k [y_k (P/p_k)^-1]_{p_k} (P/p_k) mod q_i from the special
+// limbs of A (coefficient form); cp = blockIdx.y = ct*2 + p
+__global__ void k_moddown_conv(const u64* __restrict__ A, u32 logN, u32 L, u32 K,
                                const Mod* __restrict__ mods, const u64* __restrict__ hinv,
                                const u64* __restrict__ hinvs, const u64* __restrict__ hmod,
                                u64* __restrict__ Cv) {
+    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (1u << logN)) return;
     const u32 E = L + K;
-    const u64 total = (u64)cnt * 2 * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 cp = i / N;      // ct*2 + p
-        const u32 x = (u32)(i % N);
-        const u64* a = A + cp * (u64)E * N;
-        u64 y[8];
-        for (u32 k = 0; k < K; ++k) {
-            const u64 pk = mods[L + k].q;
-            y[k] = csub(mul_shoup_lazy(a[(u64)(L + k) * N + x], hinv[k], hinvs[k], pk), pk);
-        }
-        u64* o = Cv + cp * (u64)L * N;
-        for (u32 l = 0; l < L; ++l) {
-            u64 ah = 0, al = 0;
-            for (u32 k = 0; k < K; ++k) mac128(ah, al, y[k], hmod[(u64)k * L + l]);
-            o[(u64)l * N + x] = reduce128(ah, al, mods[l]);
-        }
+    const u64 cp = blockIdx.y;
+    const u64* a = A + ((cp * E) << logN);
+    u64 y[8];
+    for (u32 k = 0; k < K; ++k) {
+        const u64 pk = mods[L + k].q;
+        y[k] = csub(mul_shoup_lazy(a[((u64)(L + k) << logN) + x], hinv[k], hinvs[k], pk), pk);
+    }
+    u64* o = Cv + ((cp * L) << logN);
+    for (u32 l = 0; l < L; ++l) {
+        u64 ah = 0, al = 0;
+        for (u32 k = 0; k < K; ++k) mac128(ah, al, y[k], hmod[(u64)k * L + l]);
+        o[((u64)l << logN) + x] = reduce128(ah, al, mods[l]);
     }
 }
 
 // out = (A - Conv) * P^-1 (+ sigma(c0) for p = 0) (+ addend), NTT form
 __global__ void k_moddown_final(const u64* __restrict__ A, const u64* __restrict__ Cv,
-                                CtSet in, CtSet out, CtSet add, u32 cnt, u32 N, u32 logN, u32 L,
-                                u32 K, u32 galois, const Mod* __restrict__ mods,
+                                CtSet in, CtSet out, CtSet add, u32 logN, u32 L, u32 K,
+                                u32 galois, const Mod* __restrict__ mods,
                                 const u64* __restrict__ pinv, const u64* __restrict__ pinvs) {
+    const u32 rr = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 LN = L << logN;
+    if (rr >= 2 * LN) return;
+    const u64 ct = blockIdx.y;
     const u32 E = L + K;
-    const u64 LN = (u64)L * N;
-    const u64 total = (u64)cnt * 2 * LN;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 ct = i / (2 * LN);
-        const u64 rr = i % (2 * LN);
-        const u32 p = (u32)(rr / LN);
-        const u64 r = rr % LN;
-        const u32 l = (u32)(r / N), x = (u32)(r % N);
-        const u64 q = mods[l].q;
-        const u64 a = A[(ct * 2 + p) * (u64)E * N + r];
-        const u64 cv = Cv[(ct * 2 + p) * LN + r];
-        u64 v = csub(mul_shoup_lazy(submod(a, cv, q), pinv[l], pinvs[l], q), q);
-        if (p == 0) v = addmod(v, in.at(ct)[(u64)l * N + auto_index(x, galois, logN)], q);
-        if (add.base) v = addmod(v, add.at(ct)[rr], q);
-        out.at(ct)[rr] = v;
-    }
+    const u32 p = rr >= LN ? 1 : 0;
+    const u32 r = rr - p * LN;
+    const u32 l = r >> logN, x = r & ((1u << logN) - 1);
+    const u64 q = mods[l].q;
+    const u64 a = A[(((ct * 2 + p) * E) << logN) + r];
+    const u64 cv = Cv[(ct * 2 + p) * LN + r];
+    u64 v = csub(mul_shoup_lazy(submod(a, cv, q), pinv[l], pinvs[l], q), q);
+    if (p == 0) v = addmod(v, in.at(ct)[((u64)l << logN) + auto_index(x, galois, logN)], q);
+    if (add.base) v = addmod(v, add.at(ct)[rr], q);
+    out.at(ct)[rr] = v;
 }
 
 // ----------------------------------------------------------- Comp kernels --
 
-// acc[gamma][g][p] = sum_{hh} sum_{a<B} Dg[cls(h)][g][a] * R[h][a][p], h = gamma*hpg + hh
-template <int GI>
-__global__ void k_diag_mac(const u64* __restrict__ R, const u64* __restrict__ Dg, u32 G, u32 hpg,
-                           u32 H, u32 B, u32 L, u32 N, const Mod* __restrict__ mods,
-                           u64* __restrict__ acc) {
-    const u64 LN = (u64)L * N;
-    const u64 total = (u64)G * 2 * LN;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 r = i % LN;
-        const u32 p = (u32)((i / LN) % 2);
-        const u32 gamma = (u32)(i / (2 * LN));
-        u64 ah[GI], al[GI];
+// Diagonal multiply-accumulate (the Pegasus inner sum):
+//   acc[gamma][g][p][l][x] = sum_{hh} sum_{a<B} Dg[hh][g][a][l][x] * R[gamma hpg + hh][a][p][l][x]
+// One CTA owns limb l = blockIdx.y and X consecutive positions.  Thread
+// (xi, gs, ct) handles position x0 + xi, giant indices gs*GT .. gs*GT+GT-1
+// and the (gamma, p) combinations 2ct, 2ct+1 of its z-slice (both
+// polynomials of one group when CPT = 2, so every diagonal value read from
+// shared memory feeds two products).  The diagonal tile
+// Dg[hh][:][a0:a0+Bc][l][x0:x0+X] is staged in shared memory once per CTA and
+// reused by every combination, so each diagonal value leaves DRAM once per
+// z-slice.  Sums are 128-bit (4 registers each, hence GT*CPT <= 16), folded
+// back to a residue before 255 products could overflow them.
+template <int GT, int CPT>
+__global__ void __launch_bounds__(512) k_diag_mac(const u64* __restrict__ R,
+                                                  const u64* __restrict__ Dg, u32 G, u32 hpg,
+                                                  u32 H, u32 B, u32 Bc, u32 GI, u32 L, u32 logN,
+                                                  u32 logX, u32 logGS, u32 combos_per_cta,
+                                                  const Mod* __restrict__ mods,
+                                                  u64* __restrict__ acc) {
+    extern __shared__ u64 Ds[];
+    const u32 X = 1u << logX;
+    const u32 l = blockIdx.y;
+    const u32 x0 = blockIdx.x << logX;
+    const u32 xi = threadIdx.x & (X - 1);
+    const u32 gs = (threadIdx.x >> logX) & ((1u << logGS) - 1);
+    const u32 ct = threadIdx.x >> (logX + logGS);
+    const u32 combo0 = blockIdx.z * combos_per_cta + ct * CPT;
+    const u64 LN = (u64)L << logN;
+    const u64 pos = ((u64)l << logN) + x0 + xi;
+    const Mod md = mods[l];
+    const u32 hpg_eff = min(hpg, H);
+    const u32 g0 = gs * GT;
+
+    const u32 gam0 = combo0 >> 1, p0 = combo0 & 1;
+    const u32 gam1 = (combo0 + CPT - 1) >> 1, p1 = (combo0 + CPT - 1) & 1;
+    const bool ok0 = gam0 < G, ok1 = CPT == 2 && gam1 < G;
+
+    // accumulators of the two combinations as separate one-dimensional
+    // arrays so that they stay in registers
+    u64 ah0[GT], al0[GT], ah1[GT], al1[GT];
 #pragma unroll
-        for (int g = 0; g < GI; ++g) { ah[g] = 0; al[g] = 0; }
-        const u32 h0 = gamma * hpg;
-        const u32 h1 = min(h0 + hpg, H);
-        const Mod md = mods[r / N];
-        u32 terms = 0;   // products since the last fold (each < 2^120; 255 of them fit)
-        for (u32 h = h0; h < h1; ++h) {
-            if (terms + B > 255) {
+    for (int g = 0; g < GT; ++g) { ah0[g] = 0; al0[g] = 0; ah1[g] = 0; al1[g] = 0; }
+    u32 terms = 0;
+
+    const u32 tile = GI * Bc * X;
+    for (u32 hh = 0; hh < hpg_eff; ++hh) {
+        for (u32 a0 = 0; a0 < B; a0 += Bc) {
+            __syncthreads();
+            for (u32 e = threadIdx.x; e < tile; e += blockDim.x) {
+                const u32 xx = e & (X - 1);
+                const u32 row = e >> logX;          // g * Bc + ai
+                const u32 g = row / Bc, ai = row - g * Bc;
+                Ds[e] = Dg[((u64)(hh * GI + g) * B + a0 + ai) * LN + ((u64)l << logN) + x0 + xx];
+            }
+            __syncthreads();
+            if (terms + Bc > 255) {
 #pragma unroll
-                for (int g = 0; g < GI; ++g) { al[g] = reduce128(ah[g], al[g], md); ah[g] = 0; }
+                for (int g = 0; g < GT; ++g) {
+                    al0[g] = reduce128(ah0[g], al0[g], md); ah0[g] = 0;
+                    if (CPT == 2) { al1[g] = reduce128(ah1[g], al1[g], md); ah1[g] = 0; }
+                }
                 terms = 0;
             }
-            terms += B;
-            const u32 cls = h % hpg;
-            const u64* Rh = R + (u64)h * B * 2 * LN + (u64)p * LN + r;
-            const u64* Dh = Dg + (u64)cls * GI * B * LN + r;
-            for (u32 a = 0; a < B; ++a) {
-                const u64 rv = Rh[(u64)a * 2 * LN];
+            terms += Bc;
+            const u32 h0 = gam0 * hpg + hh, h1 = gam1 * hpg + hh;
+            const bool act0 = ok0 && h0 < H, act1 = ok1 && h1 < H;
+            const u64* Rp0 = R + ((u64)h0 * B + a0) * 2 * LN + p0 * LN + pos;
+            const u64* Rp1 = R + ((u64)h1 * B + a0) * 2 * LN + p1 * LN + pos;
+            const u64* dbase = Ds + (u64)g0 * Bc * X + xi;
+            for (u32 ai = 0; ai < Bc; ++ai) {
+                const u64 r0 = act0 ? Rp0[(u64)ai * 2 * LN] : 0;
+                const u64 r1 = act1 ? Rp1[(u64)ai * 2 * LN] : 0;
+                const u64* drow = dbase + ai * X;
 #pragma unroll
-                for (int g = 0; g < GI; ++g) mac128(ah[g], al[g], Dh[((u64)g * B + a) * LN], rv);
+                for (int g = 0; g < GT; ++g) {
+                    const u64 d = drow[(u64)g * Bc * X];
+                    mac128(ah0[g], al0[g], d, r0);
+                    if (CPT == 2) mac128(ah1[g], al1[g], d, r1);
+                }
             }
         }
-        u64* o = acc + (u64)gamma * GI * 2 * LN + (u64)p * LN + r;
+    }
+    if (ok0) {
+        u64* o = acc + (((u64)gam0 * GI + g0) * 2 + p0) * LN + pos;
 #pragma unroll
-        for (int g = 0; g < GI; ++g) o[(u64)g * 2 * LN] = reduce128(ah[g], al[g], md);
+        for (int g = 0; g < GT; ++g) o[(u64)g * 2 * LN] = reduce128(ah0[g], al0[g], md);
+    }
+    if (ok1) {
+        u64* o = acc + (((u64)gam1 * GI + g0) * 2 + p1) * LN + pos;
+#pragma unroll
+        for (int g = 0; g < GT; ++g) o[(u64)g * 2 * LN] = reduce128(ah1[g], al1[g], md);
     }
 }
 
-// y[cnt] += x[cnt] (ciphertexts)
-__global__ void k_ct_add(CtSet y, CtSet x, u32 cnt, u32 L, u32 N, const Mod* __restrict__ mods) {
-    const u64 LN = (u64)L * N;
-    const u64 total = (u64)cnt * 2 * LN;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / (2 * LN), r = i % (2 * LN);
-        const u64 q = mods[(r % LN) / N].q;
-        u64* yp = y.at(c);
-        yp[r] = addmod(yp[r], x.at(c)[r], q);
-    }
+// y[ct] += x[ct] (ciphertexts)
+__global__ void k_ct_add(CtSet y, CtSet x, u32 L, u32 logN, const Mod* __restrict__ mods) {
+    const u32 rr = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 LN = L << logN;
+    if (rr >= 2 * LN) return;
+    const u64 c = blockIdx.y;
+    const u64 q = mods[(rr >= LN ? rr - LN : rr) >> logN].q;
+    u64* yp = y.at(c);
+    yp[rr] = addmod(yp[rr], x.at(c)[rr], q);
 }
 
-// out[c] = sum_{o} M_o * y[c*per_out + o]
+// out[c] = sum_o M_o * y[c per_out + o]
 __global__ void k_group_combine(const u64* __restrict__ y, const u64* __restrict__ masks, u32 G,
-                                u32 per_out, u32 n_out, u32 L, u32 N, const Mod* __restrict__ mods,
+                                u32 per_out, u32 L, u32 logN, const Mod* __restrict__ mods,
                                 u64* __restrict__ out) {
-    const u64 LN = (u64)L * N;
-    const u64 total = (u64)n_out * 2 * LN;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / (2 * LN), rr = i % (2 * LN);
-        const u64 r = rr % LN;
-        const Mod md = mods[r / N];
-        u64 ah = 0, al = 0;
-        for (u32 o = 0; o < per_out; ++o) {
-            const u64 gamma = c * per_out + o;
-            if (gamma >= G) break;
-            if ((o & 127) == 127) { al = reduce128(ah, al, md); ah = 0; }
-            mac128(ah, al, masks[(u64)o * LN + r], y[gamma * 2 * LN + rr]);
-        }
-        out[i] = reduce128(ah, al, md);
+    const u32 rr = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 LN = L << logN;
+    if (rr >= 2 * LN) return;
+    const u64 c = blockIdx.y;
+    const u32 r = rr >= LN ? rr - LN : rr;
+    const Mod md = mods[r >> logN];
+    u64 ah = 0, al = 0;
+    for (u32 o = 0; o < per_out; ++o) {
+        const u64 gamma = c * per_out + o;
+        if (gamma >= G) break;
+        if ((o & 127) == 127) { al = reduce128(ah, al, md); ah = 0; }
+        mac128(ah, al, masks[(u64)o * LN + r], y[gamma * 2 * LN + rr]);
     }
+    out[c * 2 * LN + rr] = reduce128(ah, al, md);
+}
+
+__global__ void k_gather_set(CtSet src, long long off, u64 len, u64* __restrict__ dst,
+                             u64 dst_stride) {
+    const u64 x = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= len) return;
+    const u64 c = blockIdx.y;
+    dst[c * dst_stride + x] = src.at(c)[off + (long long)x];
 }
 
 }  // namespace
@@ -463,8 +489,9 @@ __global__ void k_group_combine(const u64* __restrict__ y, const u64* __restrict
 
 int encode_finish(const Ctx& c, u64* out, u32 count, u32 nlimbs, cudaStream_t st) {
     const u64 N = c.N;
+    PDQ_TRY(check_y(count, "encode"));
     PDQ_TRY(ntt_inverse(c, out, count, 1, c.nmod - 1, (u64)nlimbs * N, st));
-    k_lift<<<grid_for((u64)count * N), kBlock, 0, st>>>(out, count, c.N, nlimbs, c.d_mods, c.t);
+    k_lift<<<grid2(N, count), kBlock, 0, st>>>(out, c.log_n, nlimbs, c.d_mods, c.t);
     PDQ_TRY(launched("k_lift"));
     return ntt_forward(c, out, count, nlimbs, 0, (u64)nlimbs * N, st);
 }
@@ -473,37 +500,41 @@ int encode_slots(const Ctx& c, const u32* slots, u32 count, u32 nlimbs, u64* out
                  cudaStream_t st) {
     if (count == 0) return PDQ_OK;
     if (nlimbs < 1 || nlimbs > c.L + c.K) return fail(PDQ_E_PARAM, "encode: bad limb count");
-    k_scatter_slots<<<grid_for((u64)count * c.N), kBlock, 0, st>>>(
-        slots, count, c.N, (u64)nlimbs * c.N, c.d_slot_pos, c.t, out);
+    PDQ_TRY(check_y(count, "encode"));
+    k_scatter_slots<<<grid2(c.N, count), kBlock, 0, st>>>(slots, c.log_n, (u64)nlimbs * c.N,
+                                                          c.d_slot_pos, c.t, out);
     PDQ_TRY(launched("k_scatter_slots"));
     return encode_finish(c, out, count, nlimbs, st);
 }
 
 int build_diagonals(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st) {
     const u32 count = pl.hclass * pl.giants * pl.B;
-    k_diag_slots<<<grid_for((u64)count * c.N), kBlock, 0, st>>>(
-        out, pl.hclass, pl.giants, pl.B, pl.s_prime, c.m, c.N, c.L, c.d_slot_pos, c.t);
+    PDQ_TRY(check_y(count, "diagonals"));
+    k_diag_slots<<<grid2(c.N, count), kBlock, 0, st>>>(out, pl.giants, pl.B, pl.s_prime, c.log_n,
+                                                       c.L, c.d_slot_pos, c.t);
     PDQ_TRY(launched("k_diag_slots"));
     return encode_finish(c, out, count, c.L, st);
 }
 
 int build_group_masks(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st) {
-    k_groupmask_slots<<<grid_for((u64)pl.per_out * c.N), kBlock, 0, st>>>(
-        out, pl.per_out, pl.s_prime, c.m, c.N, c.L, c.d_slot_pos);
+    PDQ_TRY(check_y(pl.per_out, "group masks"));
+    k_groupmask_slots<<<grid2(c.N, pl.per_out), kBlock, 0, st>>>(out, pl.s_prime, c.log_n, c.L,
+                                                                 c.d_slot_pos);
     PDQ_TRY(launched("k_groupmask_slots"));
     return encode_finish(c, out, pl.per_out, c.L, st);
 }
 
 int build_db(const Ctx& c, const u32* values, u64 n, u32 J, u64* out, cudaStream_t st) {
-    k_db_slots<<<grid_for((u64)J * 2 * c.N), kBlock, 0, st>>>(out, values, n, J, c.m, c.N, c.L,
-                                                               c.d_slot_pos, c.t);
+    PDQ_TRY(check_y(2ull * J, "database"));
+    k_db_slots<<<grid2(c.N, 2 * J), kBlock, 0, st>>>(out, values, n, c.log_n, c.L, c.d_slot_pos,
+                                                     c.t);
     PDQ_TRY(launched("k_db_slots"));
     return encode_finish(c, out, 2 * J, c.L, st);
 }
 
 int secret_prepare(const Ctx& c, const int8_t* s, u64* out, cudaStream_t st) {
     const u32 E = c.L + c.K;
-    k_signed_to_rns<<<grid_for((u64)E * c.N), kBlock, 0, st>>>(s, c.N, E, c.d_mods, out);
+    k_signed_to_rns<int8_t><<<grid2(c.N, E), kBlock, 0, st>>>(s, c.log_n, c.d_mods, out);
     PDQ_TRY(launched("k_signed_to_rns"));
     return ntt_forward(c, out, 1, E, 0, (u64)E * c.N, st);
 }
@@ -511,49 +542,26 @@ int secret_prepare(const Ctx& c, const int8_t* s, u64* out, cudaStream_t st) {
 int encrypt(const Ctx& c, const u64* sk, const u32* slots, u32 count, const u64* a,
             const int32_t* e, u64* ct, cudaStream_t st) {
     if (count == 0) return PDQ_OK;
+    PDQ_TRY(check_y(count, "encrypt"));
     const u64 N = c.N, L = c.L, LN = L * N;
     // m mod t (coefficient form) into limb 0 of each c1
-    k_scatter_slots<<<grid_for((u64)count * N), kBlock, 0, st>>>(slots, count, c.N, 2 * LN,
-                                                                 c.d_slot_pos, c.t, ct + LN);
+    k_scatter_slots<<<grid2(N, count), kBlock, 0, st>>>(slots, c.log_n, 2 * LN, c.d_slot_pos, c.t,
+                                                        ct + LN);
     PDQ_TRY(launched("k_scatter_slots"));
     PDQ_TRY(ntt_inverse(c, ct + LN, count, 1, c.nmod - 1, 2 * LN, st));
-    k_enc_c0<<<grid_for((u64)count * N), kBlock, 0, st>>>(ct, e, count, c.N, c.L, c.d_mods,
-                                                          c.d_delta_mod_q);
+    k_enc_c0<<<grid2(N, count), kBlock, 0, st>>>(ct, e, c.log_n, c.L, c.d_mods, c.d_delta_mod_q);
     PDQ_TRY(launched("k_enc_c0"));
-    k_copy_rows<<<grid_for((u64)count * LN), kBlock, 0, st>>>(ct + LN, 2 * LN, a, LN, count, LN);
+    k_copy_rows<<<grid2(LN, count), kBlock, 0, st>>>(ct + LN, 2 * LN, a, LN, (u32)LN);
     PDQ_TRY(launched("k_copy_rows"));
     PDQ_TRY(ntt_forward(c, ct, 2 * count, c.L, 0, LN, st));
-    k_enc_finish<<<grid_for((u64)count * LN), kBlock, 0, st>>>(ct, sk, count, c.N, c.L, c.d_mods);
+    k_enc_finish<<<grid2(LN, count), kBlock, 0, st>>>(ct, sk, c.log_n, c.L, c.d_mods);
     return launched("k_enc_finish");
 }
 
-namespace {
-__global__ void k_signed32_to_rns(const int32_t* __restrict__ e, u32 N, u32 nl,
-                                  const Mod* __restrict__ mods, u64* __restrict__ out) {
-    const u64 total = (u64)nl * N;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u32 l = (u32)(i / N), x = (u32)(i % N);
-        const long long v = e[x];
-        const u64 q = mods[l].q;
-        out[i] = v < 0 ? q - (u64)(-v) : (u64)v;
-    }
-}
-
-__global__ void k_gather_set(CtSet src, long long off, u32 cnt, u64 len, u64* __restrict__ dst,
-                             u64 dst_stride) {
-    const u64 total = (u64)cnt * len;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 c = i / len, x = i % len;
-        dst[c * dst_stride + x] = src.at(c)[off + (long long)x];
-    }
-}
-}  // namespace
-
 int gather_rows(CtSet src, long long src_off, u32 cnt, u64 len, u64* dst, u64 dst_stride,
                 cudaStream_t st) {
-    k_gather_set<<<grid_for((u64)cnt * len), kBlock, 0, st>>>(src, src_off, cnt, len, dst, dst_stride);
+    PDQ_TRY(check_y(cnt, "gather"));
+    k_gather_set<<<grid2(len, cnt), kBlock, 0, st>>>(src, src_off, len, dst, dst_stride);
     return launched("k_gather_set");
 }
 
@@ -564,12 +572,12 @@ int rotkey_gen(const Ctx& c, const u64* sk, u64 galois, const u64* a, const int3
     if (galois % 2 == 0 || galois >= 2ull * c.N) return fail(PDQ_E_PARAM, "galois element must be odd and < 2N");
     if (nd > 32) return fail(PDQ_E_PARAM, "at most 32 digits");
     // a into the second half of every digit, e (as residues) into the first
-    k_copy_rows<<<grid_for((u64)nd * EN), kBlock, 0, st>>>(key + EN, 2 * EN, a, EN, nd, EN);
+    k_copy_rows<<<grid2(EN, nd), kBlock, 0, st>>>(key + EN, 2 * EN, a, EN, (u32)EN);
     PDQ_TRY(launched("k_copy_rows"));
     for (u32 b = 0; b < nd; ++b) {
-        k_signed32_to_rns<<<grid_for(EN), kBlock, 0, st>>>(e + (u64)b * c.N, c.N, E, c.d_mods,
-                                                           key + (u64)b * 2 * EN);
-        PDQ_TRY(launched("k_signed32_to_rns"));
+        k_signed_to_rns<int32_t><<<grid2(c.N, E), kBlock, 0, st>>>(e + (u64)b * c.N, c.log_n,
+                                                                   c.d_mods, key + (u64)b * 2 * EN);
+        PDQ_TRY(launched("k_signed_to_rns"));
     }
     PDQ_TRY(ntt_forward(c, key, 2 * nd, E, 0, EN, st));
     DigitBounds db{};
@@ -577,8 +585,8 @@ int rotkey_gen(const Ctx& c, const u64* sk, u64 galois, const u64* a, const int3
         db.lo[b] = c.digit_limbs[b].front();
         db.hi[b] = c.digit_limbs[b].back() + 1;
     }
-    k_key_finish<<<grid_for((u64)nd * EN), kBlock, 0, st>>>(key, sk, nd, E, c.N, c.log_n,
-                                                            (u32)galois, c.d_mods, c.d_P_mod_q, db);
+    k_key_finish<<<grid2(EN, nd), kBlock, 0, st>>>(key, sk, E, c.log_n, (u32)galois, c.d_mods,
+                                                   c.d_P_mod_q, db);
     return launched("k_key_finish");
 }
 
@@ -587,23 +595,25 @@ size_t decrypt_ws(const Ctx& c, u32 count) { return (size_t)count * (c.L + 1) * 
 int decrypt(const Ctx& c, const u64* sk, const u64* ct, u32 count, u32* slots, u64* ws,
             cudaStream_t st) {
     if (count == 0) return PDQ_OK;
+    PDQ_TRY(check_y(count, "decrypt"));
     const u64 LN = (u64)c.L * c.N;
     u64* x = ws;
     u64* m = ws + count * LN;
-    k_dec_inner<<<grid_for(count * LN), kBlock, 0, st>>>(ct, sk, count, c.N, c.L, c.d_mods, x);
+    k_dec_inner<<<grid2(LN, count), kBlock, 0, st>>>(ct, sk, c.log_n, c.L, c.d_mods, x);
     PDQ_TRY(launched("k_dec_inner"));
     PDQ_TRY(ntt_inverse(c, x, count, c.L, 0, LN, st));
-    k_dec_round<<<grid_for((u64)count * c.N), kBlock, 0, st>>>(
-        x, count, c.N, c.L, c.d_mods, c.d_dec_omega, c.d_dec_omega_shoup, c.t, m);
+    k_dec_round<<<grid2(c.N, count), kBlock, 0, st>>>(x, c.log_n, c.L, c.d_mods, c.d_dec_omega,
+                                                      c.d_dec_omega_shoup, c.t, m);
     PDQ_TRY(launched("k_dec_round"));
     PDQ_TRY(ntt_forward(c, m, count, 1, c.nmod - 1, c.N, st));
-    k_gather_slots<<<grid_for((u64)count * c.N), kBlock, 0, st>>>(m, count, c.N, c.d_slot_pos, slots);
+    k_gather_slots<<<grid2(c.N, count), kBlock, 0, st>>>(m, c.log_n, c.d_slot_pos, slots);
     return launched("k_gather_slots");
 }
 
 int mask(const Ctx& c, u32 J, const u64* v, const u64* db, u64* out, cudaStream_t st) {
-    k_mask<<<grid_for((u64)J * c.L * c.N), kBlock, 0, st>>>(v, db, c.d_rowmask, J, c.L, c.N,
-                                                             c.d_mods, out);
+    PDQ_TRY(check_y(J, "mask"));
+    k_mask<<<grid2((u64)c.L * c.N, J), kBlock, 0, st>>>(v, db, c.d_rowmask, c.L, c.log_n, c.d_mods,
+                                                        out);
     return launched("k_mask");
 }
 
@@ -616,14 +626,15 @@ size_t raise_ws(const Ctx& c, u32 cnt) {
 
 int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t st) {
     const u64 N = c.N, L = c.L, E = c.L + c.K, nd = c.ndigits;
+    PDQ_TRY(check_y(cnt, "key switch"));
     u64* X = ws;
     u64* D = ws + cnt * L * N;
     // c1 of every ciphertext -> X, then coefficient form
     PDQ_TRY(gather_rows(in, (long long)(L * N), cnt, L * N, X, L * N, st));
     PDQ_TRY(ntt_inverse(c, X, cnt, c.L, 0, L * N, st));
-    k_modup<<<grid_for((u64)cnt * nd * N), kBlock, 0, st>>>(
-        X, in, cnt, c.N, c.L, (u32)E, (u32)nd, c.alpha, c.d_mods, c.d_up_hatinv,
-        c.d_up_hatinv_shoup, c.d_up_hatmod, D);
+    k_modup<<<dim3((c.N + kBlock - 1) / kBlock, (u32)nd, cnt), kBlock, 0, st>>>(
+        X, in, c.log_n, c.L, (u32)E, c.alpha, c.d_mods, c.d_up_hatinv, c.d_up_hatinv_shoup,
+        c.d_up_hatmod, D);
     PDQ_TRY(launched("k_modup"));
     for (u32 b = 0; b < nd; ++b) {
         const u32 lo = c.digit_limbs[b].front(), hi = c.digit_limbs[b].back() + 1;
@@ -643,43 +654,111 @@ size_t apply_ws(const Ctx& c, u32 cnt) {
 int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u64* key,
              CtSet out, CtSet add, u64* ws, cudaStream_t st) {
     const u64 N = c.N, L = c.L, K = c.K, E = L + K;
+    PDQ_TRY(check_y(2ull * cnt, "key switch"));
     u64* A = ws;
     u64* Cv = ws + cnt * 2 * E * N;
-    k_ks_inner<<<grid_for((u64)cnt * E * N), kBlock, 0, st>>>(D, key, cnt, c.N, c.log_n, (u32)E,
-                                                              c.ndigits, galois, c.d_mods, A);
+    k_ks_inner<<<grid2(E * N, cnt), kBlock, 0, st>>>(D, key, c.log_n, (u32)E, c.ndigits, galois,
+                                                     c.d_mods, A);
     PDQ_TRY(launched("k_ks_inner"));
     PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
-    k_moddown_conv<<<grid_for((u64)cnt * 2 * N), kBlock, 0, st>>>(
-        A, cnt, c.N, c.L, c.K, c.d_mods, c.d_dn_hatinv, c.d_dn_hatinv_shoup, c.d_dn_hatmod, Cv);
+    k_moddown_conv<<<grid2(N, 2 * cnt), kBlock, 0, st>>>(A, c.log_n, c.L, c.K, c.d_mods,
+                                                         c.d_dn_hatinv, c.d_dn_hatinv_shoup,
+                                                         c.d_dn_hatmod, Cv);
     PDQ_TRY(launched("k_moddown_conv"));
     PDQ_TRY(ntt_forward(c, Cv, 2 * cnt, c.L, 0, L * N, st));
-    k_moddown_final<<<grid_for((u64)cnt * 2 * L * N), kBlock, 0, st>>>(
-        A, Cv, in, out, add, cnt, c.N, c.log_n, c.L, c.K, galois, c.d_mods, c.d_dn_pinv,
-        c.d_dn_pinv_shoup);
+    k_moddown_final<<<grid2(2 * L * N, cnt), kBlock, 0, st>>>(A, Cv, in, out, add, c.log_n, c.L,
+                                                              c.K, galois, c.d_mods, c.d_dn_pinv,
+                                                              c.d_dn_pinv_shoup);
     return launched("k_moddown_final");
 }
 
-int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc,
-             cudaStream_t st) {
-    const dim3 grid = grid_for((u64)pl.G * 2 * c.L * c.N);
-    switch (pl.giants) {
-#define PDQ_GI(n) case n: k_diag_mac<n><<<grid, kBlock, 0, st>>>(R, Dg, pl.G, pl.hpg, pl.H, pl.B, c.L, c.N, c.d_mods, acc); break;
-        PDQ_GI(1) PDQ_GI(2) PDQ_GI(4) PDQ_GI(8) PDQ_GI(16) PDQ_GI(32)
-#undef PDQ_GI
-        default: return fail(PDQ_E_PARAM, "diag_mac: giant-step count must be a power of two <= 32");
+namespace {
+
+struct MacShape {
+    u32 GT, CPT, logGS, logX, Bc, zslices, combos_per_cta, threads;
+    size_t smem;
+};
+
+u32 log2u(u32 x) {
+    u32 r = 0;
+    while ((1u << (r + 1)) <= x) ++r;
+    return r;
+}
+
+// Launch shape of k_diag_mac: 8 giant indices and both polynomials of one
+// group per thread (fewer when the plan has fewer), up to 16 thread rows of
+// groups per CTA (more groups go to further z-slices), X positions so that a
+// CTA has up to 512 threads, and an a-chunk Bc that keeps the staged
+// diagonal tile within 64 KB of shared memory.
+MacShape mac_shape(const pdq_plan& pl, u32 logN) {
+    MacShape s{};
+    const u32 GI = pl.giants, combos = 2 * pl.G;
+    s.CPT = 2;
+    s.GT = GI < 8 ? GI : 8;
+    const u32 GS = GI / s.GT;
+    s.logGS = log2u(GS);
+    u32 ct = combos / s.CPT;
+    const u32 ct_max = 512 / (GS * 16) > 0 ? 512 / (GS * 16) : 1;
+    if (ct > ct_max) ct = 1u << log2u(ct_max);
+    s.combos_per_cta = ct * s.CPT;
+    s.zslices = (combos + s.combos_per_cta - 1) / s.combos_per_cta;
+    u32 logX = 4;
+    while (((ct * GS) << (logX + 1)) <= 512 && logX < 8) ++logX;
+    if (logX > logN) logX = logN;
+    u32 Bc = pl.B;
+    while ((size_t)GI * Bc * (1u << logX) * 8 > (64u << 10)) {
+        if (Bc > 1) Bc /= 2; else --logX;
     }
+    s.logX = logX;
+    s.Bc = Bc;
+    s.threads = (ct * GS) << logX;
+    s.smem = (size_t)GI * Bc * (1u << logX) * 8;
+    return s;
+}
+
+template <int GT>
+int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R, const u64* Dg,
+               u64* acc, cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(k_diag_mac<GT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 64 << 10) != cudaSuccess)
+            return cuda_check("k_diag_mac attribute");
+        configured = true;
+    }
+    const dim3 grid(c.N >> s.logX, c.L, s.zslices);
+    k_diag_mac<GT, 2><<<grid, s.threads, s.smem, st>>>(R, Dg, pl.G, pl.hpg, pl.H, pl.B, s.Bc,
+                                                       pl.giants, c.L, c.log_n, s.logX, s.logGS,
+                                                       s.combos_per_cta, c.d_mods, acc);
     return launched("k_diag_mac");
 }
 
+}  // namespace
+
+int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc,
+             cudaStream_t st) {
+    const MacShape s = mac_shape(pl, c.log_n);
+    if (s.zslices > 65535) return fail(PDQ_E_PARAM, "diag_mac: too many groups");
+    switch (s.GT) {
+        case 1: return launch_mac<1>(c, pl, s, R, Dg, acc, st);
+        case 2: return launch_mac<2>(c, pl, s, R, Dg, acc, st);
+        case 4: return launch_mac<4>(c, pl, s, R, Dg, acc, st);
+        case 8: return launch_mac<8>(c, pl, s, R, Dg, acc, st);
+        default: return fail(PDQ_E_PARAM, "diag_mac: giant-step count must be a power of two");
+    }
+}
+
 int ct_add(const Ctx& c, CtSet y, CtSet x, u32 cnt, cudaStream_t st) {
-    k_ct_add<<<grid_for((u64)cnt * 2 * c.L * c.N), kBlock, 0, st>>>(y, x, cnt, c.L, c.N, c.d_mods);
+    PDQ_TRY(check_y(cnt, "ct_add"));
+    k_ct_add<<<grid2(2ull * c.L * c.N, cnt), kBlock, 0, st>>>(y, x, c.L, c.log_n, c.d_mods);
     return launched("k_ct_add");
 }
 
 int group_combine(const Ctx& c, const pdq_plan& pl, const u64* y, const u64* masks, u64* out,
                   cudaStream_t st) {
-    k_group_combine<<<grid_for((u64)pl.n_out * 2 * c.L * c.N), kBlock, 0, st>>>(
-        y, masks, pl.G, pl.per_out, pl.n_out, c.L, c.N, c.d_mods, out);
+    PDQ_TRY(check_y(pl.n_out, "group_combine"));
+    k_group_combine<<<grid2(2ull * c.L * c.N, pl.n_out), kBlock, 0, st>>>(
+        y, masks, pl.G, pl.per_out, c.L, c.log_n, c.d_mods, out);
     return launched("k_group_combine");
 }
 

@@ -101,10 +101,8 @@ struct Ctx {
     std::vector<u64> psi;         // transform root per modulus
     // device tables, each [nmod][N] unless noted
     Mod* d_mods = nullptr;        // [nmod]
-    u64* d_fw = nullptr;          // forward twiddles psi^{brv(i)}
-    u64* d_fw_shoup = nullptr;
-    u64* d_iw = nullptr;          // inverse twiddles psi^{-brv(i)}
-    u64* d_iw_shoup = nullptr;
+    u64* d_fw2 = nullptr;         // [nmod][N][2] forward twiddles psi^{brv(i)} + Shoup
+    u64* d_iw2 = nullptr;         // [nmod][N][2] inverse twiddles psi^{-brv(i)} + Shoup
     u64* d_ninv = nullptr;        // [nmod][4]: N^-1, shoup, N^-1 * iw[1], shoup
     u32* d_slot_pos = nullptr;    // [N] transform position of slot rho*m + c
     u64* d_rowmask = nullptr;     // [2][L][N] NTT-form plaintexts [1;0], [0;1]
