@@ -40,6 +40,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--n", type=int, default=0, help="override the record count")
     ap.add_argument("--s", type=int, default=0, help="override the sparsity")
+    ap.add_argument("--mix", type=int, default=64, help="queries of the batched/served mix (0: skip)")
+    ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--rates", default="50,200,1000", help="served arrival rates, queries/s")
+    ap.add_argument("--served-requests", type=int, default=192)
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="served HBM budget")
     return ap.parse_args()
 
 
@@ -217,6 +222,190 @@ def run_e2e(args, ctx, plan, v_cts, db, keys, galois, consts, ws, stream, dist, 
     return e2e
 
 
+
+# ------------------------------------------------------ batched / served ----
+
+class Mix:
+    """The batched workload: independent queries with mixed ring dimension,
+    record count and sparsity, each with its own key set; one resident
+    database of 2^20 records (values uniform in [0, 2^16)) per ring size;
+    diagonal constants shared by queries with the same plan."""
+
+    def __init__(self, nq: int, lanes: int):
+        import numpy as np
+        import torch
+        import workloads as W
+        from paper_2408_17063_gb300 import pdq
+
+        self.pdq = pdq
+        self.specs = W.batched_mix(nq)
+        self.lanes = lanes
+        self.ctx, self.db, self.dbvals = {}, {}, {}
+        for ln in sorted({q.log_n for q in self.specs}):
+            ctx = pdq.Context(**W.RING_PARAMS[ln])
+            vals = W.rng_for(0xDB, ln).integers(0, 1 << 16, size=1 << 20).astype(np.uint32)
+            self.ctx[ln] = ctx
+            self.dbvals[ln] = vals
+            self.db[ln] = ctx.db_encode(torch.from_numpy(vals.astype(np.int32)).cuda())
+        consts = {}
+        self.items = []
+        for q in self.specs:
+            ctx = self.ctx[q.log_n]
+            plan = ctx.plan(q.n, q.s)
+            key = (q.log_n, plan.s_prime, plan.B, plan.hclass, plan.G > 1)
+            if key not in consts:
+                consts[key] = ctx.plan_constants(plan)
+            pos = W.draw_matches_uniform(q.n, q.s, W.rng_for(q.seed, 2))
+            sk = ctx.secret_prepare(torch.from_numpy(W.draw_ternary(ctx.N, W.rng_for(q.seed, 3))))
+            galois = ctx.plan_galois(plan)
+            keys = ctx._u64(len(galois) * ctx.key_elems)
+            kv = keys.view(len(galois), -1)
+            kr = W.rotation_key_randomness(ctx.moduli, ctx.N, ctx.ndigits, galois, q.seed)
+            for i, k in enumerate(galois):
+                a, e = kr[k]
+                ctx.rotkey_gen(sk, k, torch.from_numpy(a.view(np.int64)).cuda(),
+                               torch.from_numpy(e).cuda(), out=kv[i])
+            v = np.zeros(plan.J * ctx.N, dtype=np.int32)
+            v[pos] = 1
+            a, e = W.encryption_randomness(ctx.moduli[:ctx.L], ctx.N, plan.J, q.seed)
+            v_cts = ctx.encrypt(sk, torch.from_numpy(v).cuda(),
+                                torch.from_numpy(a.view(np.int64)).cuda(), torch.from_numpy(e).cuda())
+            truth = [(int(i), int(self.dbvals[q.log_n][i])) for i in pos]
+            self.items.append(dict(spec=q, ctx=ctx, plan=plan, galois=galois, keys=keys,
+                                   consts=consts[key], v_cts=v_cts, sk=sk, truth=truth))
+            torch.cuda.synchronize()
+        self.n_consts = len(consts)
+
+    def handle(self, it, out=None):
+        ctx = it["ctx"]
+        out = ctx._u64(it["plan"].n_out * ctx.ct_elems) if out is None else out
+        return ctx.query(it["plan"], it["v_cts"], self.db[it["spec"].log_n], it["keys"],
+                         it["galois"], it["consts"], out)
+
+    def ws_bytes(self, it):
+        return self.pdq.load().pdq_answer_workspace_bytes(it["ctx"].h, it["plan"])
+
+    def check(self, it, out) -> bool:
+        ctx = it["ctx"]
+        slots = ctx.decrypt(it["sk"], out.view(it["plan"].n_out, 2, ctx.L, ctx.N)).cpu().numpy()
+        return ctx.decomp(it["plan"], slots) == it["truth"]
+
+
+def run_batched(args, mix) -> dict:
+    """All queries of the mix: one pdq_answer_batch per ring size on its own
+    stream (lanes per context), captured in CUDA graphs and replayed, against
+    the plain path (the same queries one at a time on one stream)."""
+    import torch
+    by_ring = {}
+    for it in mix.items:
+        by_ring.setdefault(it["spec"].log_n, []).append(it)
+    handles = {ln: [mix.handle(it) for it in its] for ln, its in by_ring.items()}
+    lane_ws = {}
+    for ln, its in by_ring.items():
+        need = [0] * args.lanes
+        for i, it in enumerate(its):
+            need[i % args.lanes] = max(need[i % args.lanes], mix.ws_bytes(it))
+        lane_ws[ln] = [torch.empty(max(b, 8), dtype=torch.uint8, device="cuda") for b in need]
+    streams = {ln: torch.cuda.Stream() for ln in by_ring}
+    for ln in by_ring:
+        streams[ln].wait_stream(torch.cuda.current_stream())
+
+    def launch_all():
+        for ln in by_ring:
+            mix.ctx[ln].answer_batch(handles[ln], lane_ws[ln], stream=streams[ln])
+
+    launch_all()
+    torch.cuda.synchronize()
+    ok = all(mix.check(it, h.out) for ln in by_ring for it, h in zip(by_ring[ln], handles[ln]))
+    graphs = {}
+    for ln in by_ring:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=streams[ln]):
+            mix.ctx[ln].answer_batch(handles[ln], lane_ws[ln], stream=streams[ln])
+        graphs[ln] = g
+    torch.cuda.synchronize()
+
+    def replay():
+        for ln, g in graphs.items():
+            with torch.cuda.stream(streams[ln]):
+                g.replay()
+
+    for _ in range(2):
+        replay()
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        replay()
+    torch.cuda.synchronize()
+    t_graph = (time.perf_counter() - t0) / reps
+    ok = ok and all(mix.check(it, h.out) for ln in by_ring for it, h in zip(by_ring[ln], handles[ln]))
+    # plain: one query at a time on one stream, no graph
+    ws_plain = {ln: torch.empty(max(max(mix.ws_bytes(it) for it in its), 8), dtype=torch.uint8,
+                                device="cuda") for ln, its in by_ring.items()}
+    outs = [mix.handle(it) for it in mix.items]
+
+    def plain():
+        for it, h in zip(mix.items, outs):
+            it["ctx"].answer(it["plan"], it["v_cts"], mix.db[it["spec"].log_n], it["keys"],
+                             it["galois"], it["consts"], ws=ws_plain[it["spec"].log_n], out=h.out)
+
+    plain()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain()
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    nq = len(mix.items)
+    return {"queries": nq, "rings": {str(1 << ln): len(v) for ln, v in by_ring.items()},
+            "lanes_per_ring": args.lanes, "cuda_graph": True, "distinct_plan_constants": mix.n_consts,
+            "batched_qps": nq / t_graph, "plain_qps": nq / t_plain,
+            "batched_ms_per_batch": 1000 * t_graph, "plain_ms_per_batch": 1000 * t_plain,
+            "speedup": t_plain / t_graph, "all_decompress_exactly": bool(ok),
+            "mix": "64 queries, N uniform in {2^13, 2^14, 2^15}, log2 n uniform in 12..20, "
+                   "s uniform in [1, min(1024, n/16)], own key set per query"}
+
+
+def run_served(args, mix) -> list:
+    """Poisson arrivals of the mix against resident databases and keys; the
+    continuous-batching server admits requests by the HBM budget."""
+    import numpy as np
+    import torch
+    import workloads as W
+    pdq = mix.pdq
+    free, total = torch.cuda.mem_get_info()
+    resident = torch.cuda.memory_allocated()
+    budget = int(args.budget_gb * (1 << 30))
+    arena_bytes = max(budget - resident, 1 << 30)
+    arena_bytes = min(arena_bytes, free - (4 << 30))
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
+    out = []
+    for r_i, rate in enumerate(float(x) for x in args.rates.split(",") if x):
+        nreq = args.served_requests
+        arrivals = W.poisson_arrivals(rate, nreq, 0x5E + r_i)
+        order = [mix.items[i % len(mix.items)] for i in range(nreq)]
+        handles = [mix.handle(it) for it in order]
+        srv = pdq.Server(arena, lanes=8)
+        tickets = []
+        t0 = time.perf_counter()
+        for ta, h in zip(arrivals, handles):
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(h))
+        srv.drain()
+        infos = [srv.status(t) for t in tickets]
+        srv.close()
+        lat = np.array([(i.t_done_ns - i.t_submit_ns) / 1e6 for i in infos])
+        span = (max(i.t_done_ns for i in infos) - min(i.t_submit_ns for i in infos)) / 1e9
+        ok = all(i.status == 0 for i in infos)
+        exact = all(mix.check(it, h.out) for it, h in list(zip(order, handles))[:16])
+        out.append({"rate_qps": rate, "requests": nreq, "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)), "served_qps": nreq / span,
+                    "all_ok": bool(ok), "first16_decompress_exactly": bool(exact)})
+    del arena
+    return out
+
 # ------------------------------------------------------------------ GPU arm --
 
 def run_gpu(args, cfg, rank: int, world: int):
@@ -341,6 +530,12 @@ def run_gpu(args, cfg, rank: int, world: int):
             "stages_ms_per_query": {k: v[0] / max(1, args.steps) for k, v in stages.items()},
             "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps,
             "clocks": clk, "e2e": e2e, "roofline": roofline}
+    if args.mix > 0:
+        del v_cts, keys, db, consts, out
+        torch.cuda.empty_cache()
+        mix = Mix(args.mix, args.lanes)
+        line["batched"] = run_batched(args, mix)
+        line["served"] = run_served(args, mix)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in oracle_sample(cfg).items()
                                 if k != "seconds_per_query"}

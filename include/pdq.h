@@ -52,6 +52,8 @@ extern "C" {
 #define PDQ_E_CUDA 3     /* CUDA runtime error (message has the detail) */
 #define PDQ_E_DECODE 4   /* Decomp found no consistent sparse answer */
 #define PDQ_E_KEY 5      /* a needed rotation key is missing */
+#define PDQ_E_TIMEOUT 6  /* a wait ran out */
+#define PDQ_E_BUSY 7     /* the server's queue is full */
 
 #define PDQ_MAX_MODULI 40
 
@@ -232,6 +234,60 @@ int pdq_answer_host(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_
                     const uint64_t* db, const uint64_t* keys, const uint64_t* galois,
                     uint32_t nkeys, const uint64_t* consts, uint64_t* out_host, void* ws,
                     size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------ batches, serving
+ * One query of a batch or of the server: the buffers of pdq_answer.  plan
+ * and galois are host pointers, the rest device pointers. */
+typedef struct {
+    const pdq_plan* plan;
+    const uint64_t* v_cts;    /* dev [J][2][L][N] encrypted index vector */
+    const uint64_t* db;       /* dev pdq_db_encode output (>= n records) */
+    const uint64_t* keys;     /* dev keys, one per element of galois */
+    const uint64_t* galois;   /* host [nkeys] */
+    uint32_t nkeys;
+    uint32_t reserved;
+    const uint64_t* consts;   /* dev pdq_plan_constants_build output */
+    uint64_t* out;            /* dev [n_out][2][L][N] answer */
+} pdq_query;
+
+/* Answer nq queries of one parameter set (Alg. 7 per query).  Query i runs
+ * on lane i mod lanes, a stream owned by the context, with workspace
+ * lane_ws[i mod lanes] (dev, lane_ws_bytes[...] >= pdq_answer_workspace_bytes
+ * of every query of that lane); queries of one lane run in order, lanes run
+ * concurrently.  The lanes fork from `stream` and join back into it (events
+ * only), so the whole batch can be captured into a CUDA graph on `stream`.
+ * Stage profiling is suspended during the call.  1 <= lanes <= 32. */
+int pdq_answer_batch(const pdq_ctx* ctx, const pdq_query* queries, uint32_t nq,
+                     void* const* lane_ws, const size_t* lane_ws_bytes, uint32_t lanes,
+                     void* stream);
+
+/* Continuous-batching server.  `arena` (dev, arena_bytes) is the device
+ * memory the server may use for workspaces: a request is admitted when one
+ * of the `lanes` worker threads is idle and the arena has room for its
+ * workspace (first fit), in arrival order; it then runs on that worker's
+ * stream, concurrently with the other admitted requests.  max_queue (0 =
+ * unbounded) caps the number of waiting requests (PDQ_E_BUSY beyond).  A
+ * request whose workspace exceeds the whole arena is refused with
+ * PDQ_E_NOMEM.  The caller keeps every buffer of a request alive until it is
+ * done and must not enable stage profiling while a server runs.  Times are
+ * host steady-clock nanoseconds. */
+typedef struct pdq_server pdq_server;
+#define PDQ_REQ_QUEUED 0
+#define PDQ_REQ_RUNNING 1
+#define PDQ_REQ_DONE 2
+typedef struct {
+    int32_t state;           /* PDQ_REQ_* */
+    int32_t status;          /* result code once done */
+    uint64_t t_submit_ns, t_start_ns, t_done_ns;
+} pdq_ticket_info;
+int pdq_server_create(void* arena, size_t arena_bytes, uint32_t lanes, uint32_t max_queue,
+                      pdq_server** out);
+int pdq_server_submit(pdq_server* srv, const pdq_ctx* ctx, const pdq_query* q,
+                      uint64_t* ticket);
+int pdq_server_status(pdq_server* srv, uint64_t ticket, pdq_ticket_info* info);
+int pdq_server_wait(pdq_server* srv, uint64_t ticket, uint32_t timeout_ms);
+int pdq_server_drain(pdq_server* srv, uint32_t timeout_ms);
+int pdq_server_destroy(pdq_server* srv);
 
 /* ---------------------------------------------------------------- Decomp
  * Client-side Decomp (Alg. 6) on decrypted answer slots (host [n_out][N]

@@ -55,14 +55,16 @@ __device__ __forceinline__ void bf_inv(u64& x, u64& y, u64 w, u64 wp, u64 q) {
 }
 
 // Shared-memory word of element l of sub-transform c.  Column tiles hold
-// rows of C >= 16 consecutive columns (conflict-free as is); row tiles get
-// one pad word every 8 so that the strided accesses of the low passes hit
-// distinct banks.
+// rows of C >= 16 consecutive columns (conflict-free as is).  Row tiles XOR
+// bits 3..6 of the word index into bits 0..3: a bijection inside every
+// aligned run of 16 words that makes the contiguous accesses and the
+// stride-8 and stride-64 accesses of the register passes all hit distinct
+// banks.
 template <int S, bool COLS>
 __device__ __forceinline__ u32 smem_index(u32 c, u32 l, u32 logC) {
     if (COLS) return (l << logC) + c;
     const u32 w = (c << S) + l;
-    return w + (w >> 3);
+    return w ^ ((w >> 3) & 15);
 }
 
 template <bool FWD, int S, bool COLS>
@@ -157,7 +159,7 @@ struct Phase {
 
 template <bool FWD, int S, bool COLS>
 __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
-    __shared__ u64 sm[kTile + kTile / 8];
+    __shared__ __align__(16) u64 sm[kTile];
     const u32 p = blockIdx.x;
     const u32 grp = p / a.nlimbs, limb = p - grp * a.nlimbs;
     const u32 mi = a.limb0 + limb;
@@ -180,22 +182,33 @@ __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
 
     constexpr u32 GS = 1u << S;
     const u32 T = ph.C * GS;
-    for (u32 e = threadIdx.x; e < T; e += blockDim.x) {
+    // adjacent element pairs are adjacent in global memory (C >= 2 columns,
+    // or rows of >= 2 elements) and in shared memory (the row swizzle keeps
+    // aligned pairs together, possibly swapped), so tiles move with 16-byte
+    // accesses on both sides
+    for (u32 e = 2 * threadIdx.x; e < T; e += 2 * blockDim.x) {
         u32 c, l;
         if (COLS) { l = e >> a.logC; c = e & (ph.C - 1); }
         else { c = e >> S; l = e & (GS - 1); }
-        sm[smem_index<S, COLS>(c, l, a.logC)] = base[ph.gidx(c, l)];
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(base + ph.gidx(c, l));
+        const u32 w = smem_index<S, COLS>(c, l, a.logC);
+        *reinterpret_cast<ulonglong2*>(sm + (w & ~1u)) = (w & 1) ? make_ulonglong2(v.y, v.x) : v;
     }
     __syncthreads();
     ph.run();
     const u64 q = ph.q;
-    for (u32 e = threadIdx.x; e < T; e += blockDim.x) {
+    for (u32 e = 2 * threadIdx.x; e < T; e += 2 * blockDim.x) {
         u32 c, l;
         if (COLS) { l = e >> a.logC; c = e & (ph.C - 1); }
         else { c = e >> S; l = e & (GS - 1); }
-        u64 v = sm[smem_index<S, COLS>(c, l, a.logC)];
-        if (a.last) v = FWD ? csub(csub(v, 2 * q), q) : csub(v, q);
-        base[ph.gidx(c, l)] = v;
+        const u32 w = smem_index<S, COLS>(c, l, a.logC);
+        const ulonglong2 sv = *reinterpret_cast<const ulonglong2*>(sm + (w & ~1u));
+        u64 v0 = (w & 1) ? sv.y : sv.x, v1 = (w & 1) ? sv.x : sv.y;
+        if (a.last) {
+            v0 = FWD ? csub(csub(v0, 2 * q), q) : csub(v0, q);
+            v1 = FWD ? csub(csub(v1, 2 * q), q) : csub(v1, q);
+        }
+        *reinterpret_cast<ulonglong2*>(base + ph.gidx(c, l)) = make_ulonglong2(v0, v1);
     }
 }
 

@@ -282,25 +282,36 @@ __global__ void k_modup(const u64* __restrict__ X, CtSet c1ntt, u32 logN, u32 L,
 }
 
 // A[ct][p][r][x] = sum_beta D[ct][beta][r][sigma(x)] * key[beta][p][r][x]
+// Two adjacent positions per thread (16-byte loads and stores): sigma maps
+// the aligned pair {x, x+1} onto an aligned pair, possibly swapped.
 __global__ void k_ks_inner(const u64* __restrict__ D, const u64* __restrict__ key, u32 logN,
                            u32 E, u32 nd, u32 galois, const Mod* __restrict__ mods,
                            u64* __restrict__ A) {
-    const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const u64 EN = (u64)E << logN;
     if (r >= EN) return;
     const u64 ct = blockIdx.y;
     const u32 l = r >> logN, x = r & ((1u << logN) - 1);
-    const u32 sr = (l << logN) + auto_index(x, galois, logN);
-    u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+    const u32 sx = auto_index(x, galois, logN);
+    const bool swap = (sx & 1) != 0;                 // sigma(x) odd -> sigma(x+1) = sigma(x) - 1
+    const u32 sr = (l << logN) + (sx & ~1u);
+    u64 h0a = 0, l0a = 0, h1a = 0, l1a = 0, h0b = 0, l0b = 0, h1b = 0, l1b = 0;
     const u64* Dc = D + ct * nd * EN;
     for (u32 b = 0; b < nd; ++b) {
-        const u64 d = Dc[b * EN + sr];
-        mac128(h0, l0, d, key[b * 2 * EN + r]);
-        mac128(h1, l1, d, key[b * 2 * EN + EN + r]);
+        const ulonglong2 dv = *reinterpret_cast<const ulonglong2*>(Dc + b * EN + sr);
+        const u64 da = swap ? dv.y : dv.x, db = swap ? dv.x : dv.y;
+        const ulonglong2 k0 = __ldg(reinterpret_cast<const ulonglong2*>(key + b * 2 * EN + r));
+        const ulonglong2 k1 = __ldg(reinterpret_cast<const ulonglong2*>(key + b * 2 * EN + EN + r));
+        mac128(h0a, l0a, da, k0.x);
+        mac128(h0b, l0b, db, k0.y);
+        mac128(h1a, l1a, da, k1.x);
+        mac128(h1b, l1b, db, k1.y);
     }
     const Mod md = mods[l];
-    A[ct * 2 * EN + r] = reduce128(h0, l0, md);
-    A[ct * 2 * EN + EN + r] = reduce128(h1, l1, md);
+    *reinterpret_cast<ulonglong2*>(A + ct * 2 * EN + r) =
+        make_ulonglong2(reduce128(h0a, l0a, md), reduce128(h0b, l0b, md));
+    *reinterpret_cast<ulonglong2*>(A + ct * 2 * EN + EN + r) =
+        make_ulonglong2(reduce128(h1a, l1a, md), reduce128(h1b, l1b, md));
 }
 
 // Conv[cp][i] = sum_k [y_k (P/p_k)^-1]_{p_k} (P/p_k) mod q_i from the special
@@ -353,94 +364,188 @@ __global__ void k_moddown_final(const u64* __restrict__ A, const u64* __restrict
 
 // Diagonal multiply-accumulate (the Pegasus inner sum):
 //   acc[gamma][g][p][l][x] = sum_{hh} sum_{a<B} Dg[hh][g][a][l][x] * R[gamma hpg + hh][a][p][l][x]
-// One CTA owns limb l = blockIdx.y and X consecutive positions.  Thread
-// (xi, gs, ct) handles position x0 + xi, giant indices gs*GT .. gs*GT+GT-1
-// and the (gamma, p) combinations 2ct, 2ct+1 of its z-slice (both
-// polynomials of one group when CPT = 2, so every diagonal value read from
-// shared memory feeds two products).  The diagonal tile
-// Dg[hh][:][a0:a0+Bc][l][x0:x0+X] is staged in shared memory once per CTA and
-// reused by every combination, so each diagonal value leaves DRAM once per
-// z-slice.  Sums are 128-bit (4 registers each, hence GT*CPT <= 16), folded
-// back to a residue before 255 products could overflow them.
-template <int GT, int CPT>
+//
+// Arithmetic: residues are < 2^60, split into 30-bit halves v = v0 + v1 2^30;
+// a product then is four 32x32->64-bit multiply-adds into four 64-bit partial
+// sums (S0 = sum a0 b0, S1a = sum a0 b1, S1b = sum a1 b0, S2 = sum a1 b1), each
+// term < 2^60, so 15 terms fit; the sums are folded back to one residue
+// (S0 + (S1a + S1b) 2^30 + S2 2^60 mod q) every 14 terms and at the end.
+//
+// Work split: one CTA owns limb l = blockIdx.y and X consecutive positions;
+// thread (xi, gs, ct) handles position x0 + xi, giant indices gs*GT ..
+// gs*GT+GT-1 and the combinations (gamma, p) = 2ct, 2ct+1 of its z-slice.
+// Per step (hh, a-chunk) the CTA stages the diagonal tile
+// Dg[hh][:][a0:a0+Bc][l][x0:x0+X] and the rotated-ciphertext tile
+// R[gamma hpg + hh][a0:a0+Bc][p][l][x0:x0+X] of all its combinations in
+// shared memory with asynchronous 16-byte copies, double-buffered so that
+// the next step's copies overlap this step's arithmetic; each diagonal value
+// leaves DRAM once per z-slice and each rotated value once.
+struct Acc30 {
+    u64 s0, s1a, s1b, s2;
+};
+
+__device__ __forceinline__ void mac30(Acc30& A, u32 a0, u32 a1, u32 b0, u32 b1) {
+    asm("mad.wide.u32 %0, %4, %6, %0;\n\t"
+        "mad.wide.u32 %1, %4, %7, %1;\n\t"
+        "mad.wide.u32 %2, %5, %6, %2;\n\t"
+        "mad.wide.u32 %3, %5, %7, %3;"
+        : "+l"(A.s0), "+l"(A.s1a), "+l"(A.s1b), "+l"(A.s2)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+}
+
+struct Fold30 {
+    Mod md;
+    u64 c30, c30s, c60, c60s;   // 2^30 and 2^60 mod q with Shoup companions
+};
+
+__device__ __forceinline__ u64 fold30(const Acc30& A, const Fold30& f) {
+    const u64 q = f.md.q;
+    u64 v = A.s0 - mulhi64(A.s0, f.md.ratio) * q;                  // [0, 2q)
+    v += mul_shoup_lazy(A.s1a, f.c30, f.c30s, q);                   // [0, 4q)
+    v += mul_shoup_lazy(A.s1b, f.c30, f.c30s, q);                   // [0, 6q)
+    v += mul_shoup_lazy(A.s2, f.c60, f.c60s, q);                    // [0, 8q) < 2^63
+    return reduce64(v, f.md);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+    const u32 s = (u32)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
+                 "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <int GT>
 __global__ void __launch_bounds__(512) k_diag_mac(const u64* __restrict__ R,
                                                   const u64* __restrict__ Dg, u32 G, u32 hpg,
                                                   u32 H, u32 B, u32 Bc, u32 GI, u32 L, u32 logN,
                                                   u32 logX, u32 logGS, u32 combos_per_cta,
+                                                  u32 tiles_per_cta, u32 logGI, u32 logBc,
                                                   const Mod* __restrict__ mods,
+                                                  const u64* __restrict__ c30tab,
                                                   u64* __restrict__ acc) {
-    extern __shared__ u64 Ds[];
+    extern __shared__ __align__(16) u64 smem[];
     const u32 X = 1u << logX;
     const u32 l = blockIdx.y;
-    const u32 x0 = blockIdx.x << logX;
     const u32 xi = threadIdx.x & (X - 1);
     const u32 gs = (threadIdx.x >> logX) & ((1u << logGS) - 1);
     const u32 ct = threadIdx.x >> (logX + logGS);
-    const u32 combo0 = blockIdx.z * combos_per_cta + ct * CPT;
+    const u32 cbase = blockIdx.z * combos_per_cta;      // first combination of the z-slice
     const u64 LN = (u64)L << logN;
-    const u64 pos = ((u64)l << logN) + x0 + xi;
-    const Mod md = mods[l];
     const u32 hpg_eff = min(hpg, H);
     const u32 g0 = gs * GT;
 
-    const u32 gam0 = combo0 >> 1, p0 = combo0 & 1;
-    const u32 gam1 = (combo0 + CPT - 1) >> 1, p1 = (combo0 + CPT - 1) & 1;
-    const bool ok0 = gam0 < G, ok1 = CPT == 2 && gam1 < G;
+    Fold30 f;
+    f.md = mods[l];
+    f.c30 = c30tab[4 * l + 0];
+    f.c30s = c30tab[4 * l + 1];
+    f.c60 = c30tab[4 * l + 2];
+    f.c60s = c30tab[4 * l + 3];
 
-    // accumulators of the two combinations as separate one-dimensional
-    // arrays so that they stay in registers
-    u64 ah0[GT], al0[GT], ah1[GT], al1[GT];
+    // Tiles in shared memory, rows of X positions padded to Xp = X + 2 words
+    // (16-byte aligned rows, and the giant-index groups of a warp land in
+    // different bank halves): diagonals as [a][g][x], rotated operands as
+    // [combination][a][x].
+    const u32 Xp = X + 2;
+    const u32 drows = GI * Bc, rrows = combos_per_cta * Bc;
+    const u32 dtile = drows * Xp, rtile = rrows * Xp;
+    u64* Dsm[2] = {smem, smem + dtile + rtile};
+    u64* Rsm[2] = {smem + dtile, smem + 2 * dtile + rtile};
+
+    const u32 c0 = 2 * ct, c1 = 2 * ct + 1;        // combinations of this thread (in slice)
+    const u32 gam0 = (cbase + c0) >> 1, gam1 = (cbase + c1) >> 1;
+    const bool ok0 = gam0 < G, ok1 = gam1 < G;
+
+    const u32 achunks = B >> logBc;
+    const u32 spt = hpg_eff * achunks;             // steps per position tile
+    const u32 steps = spt * tiles_per_cta;
+    const u32 tile0 = blockIdx.x * tiles_per_cta;
+    const u32 pairs_per_row = X >> 1;
+
+    // copies of global step `st` (tile st / spt, step st % spt) into buffer `buf`
+    auto issue = [&](u32 st, u32 buf) {
+        const u32 tt = st / spt, sst = st - tt * spt;
+        const u32 hh = sst / achunks, a0 = (sst - hh * achunks) << logBc;
+        const u64 lx0 = ((u64)l << logN) + ((u64)(tile0 + tt) << logX);
+        u64* D = Dsm[buf];
+        for (u32 e = threadIdx.x; e < drows * pairs_per_row; e += blockDim.x) {
+            const u32 row = e >> (logX - 1), xx = (e & (pairs_per_row - 1)) * 2;
+            const u32 ai = row >> logGI, g = row & (GI - 1);
+            cp_async16(D + row * Xp + xx,
+                       Dg + ((u64)(hh * GI + g) * B + a0 + ai) * LN + lx0 + xx, true);
+        }
+        u64* Rt = Rsm[buf];
+        for (u32 e = threadIdx.x; e < rrows * pairs_per_row; e += blockDim.x) {
+            const u32 row = e >> (logX - 1), xx = (e & (pairs_per_row - 1)) * 2;
+            const u32 cb = row >> logBc, ai = row & (Bc - 1);
+            const u32 combo = cbase + cb;
+            const u32 gam = combo >> 1, p = combo & 1;
+            const u32 h = gam * hpg + hh;
+            const bool valid = gam < G && h < H;
+            const u64* src = R + (((u64)(valid ? h : 0) * B + a0 + ai) * 2 + p) * LN + lx0 + xx;
+            cp_async16(Rt + row * Xp + xx, src, valid);
+        }
+        cp_async_commit();
+    };
+
+    Acc30 A0[GT], A1[GT];
 #pragma unroll
-    for (int g = 0; g < GT; ++g) { ah0[g] = 0; al0[g] = 0; ah1[g] = 0; al1[g] = 0; }
+    for (int g = 0; g < GT; ++g) { A0[g] = Acc30{0, 0, 0, 0}; A1[g] = Acc30{0, 0, 0, 0}; }
     u32 terms = 0;
 
-    const u32 tile = GI * Bc * X;
-    for (u32 hh = 0; hh < hpg_eff; ++hh) {
-        for (u32 a0 = 0; a0 < B; a0 += Bc) {
-            __syncthreads();
-            for (u32 e = threadIdx.x; e < tile; e += blockDim.x) {
-                const u32 xx = e & (X - 1);
-                const u32 row = e >> logX;          // g * Bc + ai
-                const u32 g = row / Bc, ai = row - g * Bc;
-                Ds[e] = Dg[((u64)(hh * GI + g) * B + a0 + ai) * LN + ((u64)l << logN) + x0 + xx];
-            }
-            __syncthreads();
-            if (terms + Bc > 255) {
+    issue(0, 0);
+    for (u32 st = 0; st < steps; ++st) {
+        const u32 buf = st & 1;
+        if (st + 1 < steps) {
+            issue(st + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const u64* D = Dsm[buf] + g0 * Xp + xi;
+        const u64* Rt0 = Rsm[buf] + c0 * Bc * Xp + xi;
+        const u64* Rt1 = Rsm[buf] + c1 * Bc * Xp + xi;
+        for (u32 ai = 0; ai < Bc; ++ai) {
+            if (terms == 14) {
 #pragma unroll
                 for (int g = 0; g < GT; ++g) {
-                    al0[g] = reduce128(ah0[g], al0[g], md); ah0[g] = 0;
-                    if (CPT == 2) { al1[g] = reduce128(ah1[g], al1[g], md); ah1[g] = 0; }
+                    A0[g] = Acc30{fold30(A0[g], f), 0, 0, 0};
+                    A1[g] = Acc30{fold30(A1[g], f), 0, 0, 0};
                 }
-                terms = 0;
+                terms = 1;
             }
-            terms += Bc;
-            const u32 h0 = gam0 * hpg + hh, h1 = gam1 * hpg + hh;
-            const bool act0 = ok0 && h0 < H, act1 = ok1 && h1 < H;
-            const u64* Rp0 = R + ((u64)h0 * B + a0) * 2 * LN + p0 * LN + pos;
-            const u64* Rp1 = R + ((u64)h1 * B + a0) * 2 * LN + p1 * LN + pos;
-            const u64* dbase = Ds + (u64)g0 * Bc * X + xi;
-            for (u32 ai = 0; ai < Bc; ++ai) {
-                const u64 r0 = act0 ? Rp0[(u64)ai * 2 * LN] : 0;
-                const u64 r1 = act1 ? Rp1[(u64)ai * 2 * LN] : 0;
-                const u64* drow = dbase + ai * X;
+            ++terms;
+            const u64 r0 = Rt0[ai * Xp], r1 = Rt1[ai * Xp];
+            const u32 r00 = (u32)r0 & 0x3fffffffu, r01 = (u32)(r0 >> 30);
+            const u32 r10 = (u32)r1 & 0x3fffffffu, r11 = (u32)(r1 >> 30);
 #pragma unroll
-                for (int g = 0; g < GT; ++g) {
-                    const u64 d = drow[(u64)g * Bc * X];
-                    mac128(ah0[g], al0[g], d, r0);
-                    if (CPT == 2) mac128(ah1[g], al1[g], d, r1);
-                }
+            for (int g = 0; g < GT; ++g) {
+                const u64 d = D[(ai * GI + g) * Xp];
+                const u32 d0 = (u32)d & 0x3fffffffu, d1 = (u32)(d >> 30);
+                mac30(A0[g], r00, r01, d0, d1);
+                mac30(A1[g], r10, r11, d0, d1);
             }
         }
-    }
-    if (ok0) {
-        u64* o = acc + (((u64)gam0 * GI + g0) * 2 + p0) * LN + pos;
+        const u32 tt = st / spt;
+        if (st - tt * spt == spt - 1) {            // last step of this position tile
+            const u64 pos = ((u64)l << logN) + ((u64)(tile0 + tt) << logX) + xi;
+            if (ok0) {
+                u64* o = acc + (((u64)gam0 * GI + g0) * 2 + ((cbase + c0) & 1)) * LN + pos;
 #pragma unroll
-        for (int g = 0; g < GT; ++g) o[(u64)g * 2 * LN] = reduce128(ah0[g], al0[g], md);
-    }
-    if (ok1) {
-        u64* o = acc + (((u64)gam1 * GI + g0) * 2 + p1) * LN + pos;
+                for (int g = 0; g < GT; ++g) o[(u64)g * 2 * LN] = fold30(A0[g], f);
+            }
+            if (ok1) {
+                u64* o = acc + (((u64)gam1 * GI + g0) * 2 + ((cbase + c1) & 1)) * LN + pos;
 #pragma unroll
-        for (int g = 0; g < GT; ++g) o[(u64)g * 2 * LN] = reduce128(ah1[g], al1[g], md);
+                for (int g = 0; g < GT; ++g) o[(u64)g * 2 * LN] = fold30(A1[g], f);
+            }
+#pragma unroll
+            for (int g = 0; g < GT; ++g) { A0[g] = Acc30{0, 0, 0, 0}; A1[g] = Acc30{0, 0, 0, 0}; }
+            terms = 0;
+        }
+        __syncthreads();                 // buffer `buf` is refilled by the next issue
     }
 }
 
@@ -657,8 +762,8 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
     PDQ_TRY(check_y(2ull * cnt, "key switch"));
     u64* A = ws;
     u64* Cv = ws + cnt * 2 * E * N;
-    k_ks_inner<<<grid2(E * N, cnt), kBlock, 0, st>>>(D, key, c.log_n, (u32)E, c.ndigits, galois,
-                                                     c.d_mods, A);
+    k_ks_inner<<<grid2(E * N / 2, cnt), kBlock, 0, st>>>(D, key, c.log_n, (u32)E, c.ndigits,
+                                                         galois, c.d_mods, A);
     PDQ_TRY(launched("k_ks_inner"));
     PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
     k_moddown_conv<<<grid2(N, 2 * cnt), kBlock, 0, st>>>(A, c.log_n, c.L, c.K, c.d_mods,
@@ -675,7 +780,7 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
 namespace {
 
 struct MacShape {
-    u32 GT, CPT, logGS, logX, Bc, zslices, combos_per_cta, threads;
+    u32 GT, logGS, logX, Bc, zslices, combos_per_cta, threads, tiles_per_cta;
     size_t smem;
 };
 
@@ -685,34 +790,41 @@ u32 log2u(u32 x) {
     return r;
 }
 
-// Launch shape of k_diag_mac: 8 giant indices and both polynomials of one
-// group per thread (fewer when the plan has fewer), up to 16 thread rows of
-// groups per CTA (more groups go to further z-slices), X positions so that a
-// CTA has up to 512 threads, and an a-chunk Bc that keeps the staged
-// diagonal tile within 64 KB of shared memory.
+// Launch shape of k_diag_mac: up to 4 giant indices and both polynomials of
+// one group per thread, up to 16 groups per CTA (more go to further
+// z-slices), X >= 2 positions so that a CTA has up to 512 threads, and an
+// a-chunk Bc that keeps the two staged (diagonal + rotated) tiles within
+// 160 KB of shared memory.
 MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     MacShape s{};
     const u32 GI = pl.giants, combos = 2 * pl.G;
-    s.CPT = 2;
-    s.GT = GI < 8 ? GI : 8;
+    s.GT = GI < 4 ? GI : 4;
     const u32 GS = GI / s.GT;
     s.logGS = log2u(GS);
-    u32 ct = combos / s.CPT;
-    const u32 ct_max = 512 / (GS * 16) > 0 ? 512 / (GS * 16) : 1;
+    u32 ct = combos / 2;
+    u32 ct_max = 512 / (GS * 2);
+    if (ct_max > 16) ct_max = 16;
     if (ct > ct_max) ct = 1u << log2u(ct_max);
-    s.combos_per_cta = ct * s.CPT;
+    s.combos_per_cta = ct * 2;
     s.zslices = (combos + s.combos_per_cta - 1) / s.combos_per_cta;
-    u32 logX = 4;
+    u32 logX = 1;
     while (((ct * GS) << (logX + 1)) <= 512 && logX < 8) ++logX;
     if (logX > logN) logX = logN;
     u32 Bc = pl.B;
-    while ((size_t)GI * Bc * (1u << logX) * 8 > (64u << 10)) {
-        if (Bc > 1) Bc /= 2; else --logX;
+    auto bytes = [&](u32 bc, u32 lx) {
+        return 2 * (size_t)(GI + s.combos_per_cta) * bc * ((1u << lx) + 2) * 8;
+    };
+    while (bytes(Bc, logX) > (160u << 10)) {
+        if (Bc > 1) Bc /= 2; else if (logX > 1) --logX; else break;
     }
     s.logX = logX;
     s.Bc = Bc;
     s.threads = (ct * GS) << logX;
-    s.smem = (size_t)GI * Bc * (1u << logX) * 8;
+    s.smem = bytes(Bc, logX);
+    // several position tiles per CTA so that the copy pipeline runs long
+    const u32 tiles = 1u << (logN - logX);
+    s.tiles_per_cta = 1;
+    while (s.tiles_per_cta < 8 && tiles / (s.tiles_per_cta * 2) >= 64) s.tiles_per_cta *= 2;
     return s;
 }
 
@@ -721,15 +833,17 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
                u64* acc, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
-        if (cudaFuncSetAttribute(k_diag_mac<GT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 64 << 10) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_diag_mac<GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 160 << 10) != cudaSuccess)
             return cuda_check("k_diag_mac attribute");
         configured = true;
     }
-    const dim3 grid(c.N >> s.logX, c.L, s.zslices);
-    k_diag_mac<GT, 2><<<grid, s.threads, s.smem, st>>>(R, Dg, pl.G, pl.hpg, pl.H, pl.B, s.Bc,
-                                                       pl.giants, c.L, c.log_n, s.logX, s.logGS,
-                                                       s.combos_per_cta, c.d_mods, acc);
+    const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, c.L, s.zslices);
+    k_diag_mac<GT><<<grid, s.threads, s.smem, st>>>(R, Dg, pl.G, pl.hpg, pl.H, pl.B, s.Bc,
+                                                    pl.giants, c.L, c.log_n, s.logX, s.logGS,
+                                                    s.combos_per_cta, s.tiles_per_cta,
+                                                    log2u(pl.giants), log2u(s.Bc), c.d_mods,
+                                                    c.d_c30, acc);
     return launched("k_diag_mac");
 }
 
@@ -739,11 +853,11 @@ int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64*
              cudaStream_t st) {
     const MacShape s = mac_shape(pl, c.log_n);
     if (s.zslices > 65535) return fail(PDQ_E_PARAM, "diag_mac: too many groups");
+    if (s.logX < 1 || s.smem > (160u << 10)) return fail(PDQ_E_PARAM, "diag_mac: plan too large for one tile");
     switch (s.GT) {
         case 1: return launch_mac<1>(c, pl, s, R, Dg, acc, st);
         case 2: return launch_mac<2>(c, pl, s, R, Dg, acc, st);
         case 4: return launch_mac<4>(c, pl, s, R, Dg, acc, st);
-        case 8: return launch_mac<8>(c, pl, s, R, Dg, acc, st);
         default: return fail(PDQ_E_PARAM, "diag_mac: giant-step count must be a power of two");
     }
 }

@@ -7,6 +7,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -81,12 +82,19 @@ __host__ __device__ __forceinline__ u64 mulmod(u64 a, u64 b, const Mod& m) {
 __host__ __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
 __host__ __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
 
-// 128-bit accumulator: (hi, lo) += a * b.
+// 128-bit accumulator: (hi, lo) += a * b, one carry chain.
 __host__ __device__ __forceinline__ void mac128(u64& hi, u64& lo, u64 a, u64 b) {
+#ifdef __CUDA_ARCH__
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(lo), "+l"(hi)
+        : "l"(a), "l"(b));
+#else
     u64 plo = a * b;
     u64 phi = mulhi64(a, b);
     lo += plo;
     hi += phi + (lo < plo ? 1 : 0);
+#endif
 }
 
 // --------------------------------------------------------------- context ----
@@ -124,6 +132,7 @@ struct Ctx {
     u64* d_delta_mod_q = nullptr;
     // decryption: per q_i, omega_i = (Q/q_i)^-1 mod q_i (+shoup), and
     // t * b / q_i split for rounding is done with 128-bit arithmetic.
+    u64* d_c30 = nullptr;         // [nmod][4]: 2^30, Shoup, 2^60, Shoup (mod q)
     u64* d_dec_omega = nullptr;
     u64* d_dec_omega_shoup = nullptr;
     std::vector<std::vector<u32>> digit_limbs;   // limbs of each digit
@@ -135,7 +144,17 @@ struct Ctx {
         size_t used = 0;
     };
     mutable Prof prof;
+    // streams of pdq_answer_batch, created on first use
+    struct Lanes {
+        std::vector<cudaStream_t> streams;
+        std::vector<cudaEvent_t> joins;
+        cudaEvent_t fork = nullptr;
+    };
+    mutable Lanes lanes;
+    mutable std::mutex lanes_mu;
 };
+
+void lanes_release(Ctx* c);
 
 // Record a stage boundary (stage < 0 closes the current stage) when
 // profiling is enabled on the context.

@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(HERE, "_lib", "libpdq.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pdq.h")
 
 PDQ_OK, PDQ_E_PARAM, PDQ_E_NOMEM, PDQ_E_CUDA, PDQ_E_DECODE, PDQ_E_KEY = 0, 1, 2, 3, 4, 5
+PDQ_E_TIMEOUT, PDQ_E_BUSY = 6, 7
+PDQ_REQ_QUEUED, PDQ_REQ_RUNNING, PDQ_REQ_DONE = 0, 1, 2
 MAX_MODULI = 40
 
 
@@ -50,6 +52,19 @@ class Plan(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Query(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("v_cts", ctypes.c_void_p), ("db", ctypes.c_void_p),
+                ("keys", ctypes.c_void_p), ("galois", ctypes.c_void_p),
+                ("nkeys", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("consts", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("t_submit_ns", ctypes.c_uint64), ("t_start_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64)]
 
 
 _P = ctypes.c_void_p
@@ -89,6 +104,13 @@ _SIGS = {
                              _P]),
     "pdq_decomp": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _U64, ctypes.POINTER(_U64)]),
     "pdq_launch_count": (ctypes.c_ulonglong, []),
+    "pdq_answer_batch": (_I, [_P, ctypes.POINTER(Query), _U32, _P, _P, _U32, _P]),
+    "pdq_server_create": (_I, [_P, _SZ, _U32, _U32, ctypes.POINTER(_P)]),
+    "pdq_server_submit": (_I, [_P, _P, ctypes.POINTER(Query), ctypes.POINTER(_U64)]),
+    "pdq_server_status": (_I, [_P, _U64, ctypes.POINTER(TicketInfo)]),
+    "pdq_server_wait": (_I, [_P, _U64, _U32]),
+    "pdq_server_drain": (_I, [_P, _U32]),
+    "pdq_server_destroy": (_I, [_P]),
     "pdq_rotate_noalloc_max_bytes": (_SZ, []),
     "pdq_rotate_noalloc": (_I, [_P, _P, _U32, _U64, _P, _P, _P]),
     "pdq_profile_enable": (_I, [_P, _I]),
@@ -346,6 +368,18 @@ class Context:
                                       _ptr(out_host), _ptr(ws), ws.numel(), _stream(stream)))
         return out_host
 
+    def query(self, plan: Plan, v_cts, db, keys, galois, consts, out) -> "QueryHandle":
+        """Bundle one query's buffers for pdq_answer_batch / the server."""
+        return QueryHandle(self, plan, v_cts, db, keys, galois, consts, out)
+
+    def answer_batch(self, handles, lane_ws, stream=None):
+        """pdq_answer_batch over QueryHandles; lane_ws: list of workspaces."""
+        qs = (Query * len(handles))(*[h.struct for h in handles])
+        ws = (ctypes.c_void_p * len(lane_ws))(*[_ptr(w) for w in lane_ws])
+        nb = (ctypes.c_size_t * len(lane_ws))(*[w.numel() for w in lane_ws])
+        _check(load().pdq_answer_batch(self.h, qs, len(handles), ctypes.cast(ws, _P),
+                                       ctypes.cast(nb, _P), len(lane_ws), _stream(stream)))
+
     def profile_enable(self, on: bool = True):
         _check(load().pdq_profile_enable(self.h, 1 if on else 0))
 
@@ -369,3 +403,58 @@ class Context:
                                  ctypes.byref(cnt)))
         n = cnt.value
         return [(int(i), int(v)) for i, v in zip(idx[:n], val[:n])]
+
+
+class QueryHandle:
+    """Keeps a query's plan, Galois list and tensors alive with its pdq_query."""
+
+    def __init__(self, ctx: Context, plan: Plan, v_cts, db, keys, galois, consts, out):
+        self.ctx, self.plan = ctx, plan
+        self.tensors = (v_cts, db, keys, consts, out)
+        self.galois = (ctypes.c_uint64 * len(galois))(*galois)
+        self.struct = Query(ctypes.cast(ctypes.pointer(plan), _P).value, _ptr(v_cts), _ptr(db),
+                            _ptr(keys), ctypes.cast(self.galois, _P).value, len(galois), 0,
+                            _ptr(consts), _ptr(out))
+        self.out = out
+
+
+class Server:
+    """pdq_server: continuous batching over `lanes` worker streams with the
+    workspaces carved out of `arena` (a device tensor = the HBM budget)."""
+
+    def __init__(self, arena: torch.Tensor, lanes: int = 4, max_queue: int = 0):
+        self.arena = arena
+        h = _P()
+        _check(load().pdq_server_create(_ptr(arena), arena.numel() * arena.element_size(), lanes,
+                                        max_queue, ctypes.byref(h)))
+        self.h = h
+        self.pending = {}
+
+    def submit(self, handle: QueryHandle) -> int:
+        t = _U64()
+        _check(load().pdq_server_submit(self.h, handle.ctx.h, ctypes.byref(handle.struct),
+                                        ctypes.byref(t)))
+        self.pending[t.value] = handle
+        return t.value
+
+    def status(self, ticket: int) -> TicketInfo:
+        info = TicketInfo()
+        _check(load().pdq_server_status(self.h, ticket, ctypes.byref(info)))
+        return info
+
+    def wait(self, ticket: int, timeout_ms: int = 600000):
+        _check(load().pdq_server_wait(self.h, ticket, timeout_ms))
+
+    def drain(self, timeout_ms: int = 600000):
+        _check(load().pdq_server_drain(self.h, timeout_ms))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pdq_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -42,7 +42,7 @@ class Setup:
     """Oracle and GPU state for one configuration with identical randomness."""
 
     def __init__(self, cfg_name: str, seed: int | None = None, s: int | None = None,
-                 n: int | None = None, B: int = 0, pattern: str | None = None):
+                 n: int | None = None, B: int = 0, pattern: str | None = None, ctx=None):
         pdq = library()
         cfg = W.CONFIGS[cfg_name]
         if s is not None or n is not None or pattern is not None:
@@ -51,7 +51,7 @@ class Setup:
                                       pattern=pattern or cfg.pattern)
         self.cfg = cfg
         self.par = bfv.Params.from_config(cfg)
-        self.ctx = pdq.Context.from_config(cfg)
+        self.ctx = pdq.Context.from_config(cfg) if ctx is None else ctx
         self.q = W.draw_query(cfg, seed)
         self.seed = cfg.seed if seed is None else seed
         self.oplan = opdq.make_plan(self.par, cfg.n, cfg.s, B or None)
@@ -93,3 +93,9 @@ class Setup:
     def answer(self):
         return self.ctx.answer(self.plan, self.v_cts, self.db, self.keys, self.galois,
                                self.consts)
+
+    def handle(self, out=None):
+        """A pdq_query over this setup's buffers (new output buffer)."""
+        out = self.ctx._u64(self.plan.n_out * self.ctx.ct_elems) if out is None else out
+        return self.ctx.query(self.plan, self.v_cts, self.db, self.keys, self.galois,
+                              self.consts, out)

@@ -176,3 +176,40 @@ def rotation_key_randomness(moduli_ext, N: int, digits: int, galois_elts, seed: 
         out[int(k)] = (a, e)
     return out
 
+
+
+# Parameter sets of the mixed-ring workloads, by log2 N (the N = 2^14 chain
+# is this implementation's choice: 4 x 60-bit + 2 special primes, 2 digits).
+RING_PARAMS = {
+    13: dict(log_n=13, t=65537, prime_bits=60, L=3, K=1, dnum=3),
+    14: dict(log_n=14, t=65537, prime_bits=60, L=4, K=2, dnum=2),
+    15: dict(log_n=15, t=65537, prime_bits=60, L=8, K=2, dnum=4),
+}
+
+
+@dataclasses.dataclass(frozen=True)
+class MixQuery:
+    log_n: int      # ring dimension 2^log_n
+    n: int          # records
+    s: int          # matches
+    seed: int
+
+
+def batched_mix(count: int = 64, base_seed: int = 0xB0) -> list[MixQuery]:
+    """Independent queries of the batched / served workloads: ring dimension
+    uniform over {2^13, 2^14, 2^15}, log2 n uniform over the integers 12..20,
+    s uniform in [1, min(1024, n/16)], query q seeded with base_seed + q."""
+    out = []
+    for q in range(count):
+        rng = rng_for(base_seed + q, 0)
+        log_n = int(rng.integers(13, 16))
+        n = 1 << int(rng.integers(12, 21))
+        s = int(rng.integers(1, min(1024, n // 16) + 1))
+        out.append(MixQuery(log_n, n, s, base_seed + q))
+    return out
+
+
+def poisson_arrivals(rate_per_s: float, count: int, seed: int) -> np.ndarray:
+    """Arrival times (seconds from 0) of a Poisson process."""
+    rng = rng_for(seed, 7)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=count))
