@@ -387,6 +387,40 @@ def rotate_hoisted(par: Params, ct, raised, k: int, key) -> np.ndarray:
     return np.stack([c0, c1])
 
 
+def rotate_ext(par: Params, ct, raised, k: int, key) -> np.ndarray:
+    """The rotation of rotate_hoisted before its ModDown, kept in the
+    extended basis Q u P: (P sigma_k(c0) + A0, A1), [2][L+K][N].  P sigma_k(c0)
+    is 0 modulo the special primes."""
+    el = extlimbs(par)
+    A0 = np.zeros((par.L + par.K, par.N), dtype=np.uint64)
+    A1 = np.zeros_like(A0)
+    for b_idx, _ in enumerate(par.digits):
+        d = poly_automorphism(par, raised[b_idx], k, el)
+        A0 = poly_add(par, A0, poly_mul(par, d, key[b_idx][0], el), el)
+        A1 = poly_add(par, A1, poly_mul(par, d, key[b_idx][1], el), el)
+    pc0 = times_P(par, poly_automorphism(par, ct[0], k, qlimbs(par)))
+    return np.stack([poly_add(par, A0, pc0, el), A1])
+
+
+def times_P(par: Params, x) -> np.ndarray:
+    """P x over the extended basis for x over Q ([L][N] -> [L+K][N]); the
+    special-prime limbs are 0."""
+    out = np.zeros((par.L + par.K, par.N), dtype=np.uint64)
+    for i, qi in enumerate(par.q):
+        out[i] = ring.vec_scale(x[i], par.P % qi, qi)
+    return out
+
+
+def ct_times_P(par: Params, ct) -> np.ndarray:
+    """A ciphertext over Q lifted to Q u P as (P c0, P c1)."""
+    return np.stack([times_P(par, ct[0]), times_P(par, ct[1])])
+
+
+def ct_mod_down(par: Params, ct_ext) -> np.ndarray:
+    """ModDown of both polynomials of an extended-basis ciphertext."""
+    return np.stack([mod_down(par, ct_ext[0]), mod_down(par, ct_ext[1])])
+
+
 def rotate(par: Params, ct, k: int, key) -> np.ndarray:
     """Homomorphic automorphism sigma_k (Rot_row for k = 3^r, Rot_col for
     k = 2N-1), Sec. 5.1."""

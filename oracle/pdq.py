@@ -27,6 +27,10 @@ Readings where the paper is silent (all mirrored by the GPU library):
   this is exactly the paper's C.
 * The row masks of the u-packing remark are folded into the Mask plaintexts:
   (v.DB).[1;0] = v.(DB.[1;0]) (same slots, one multiplicative level less).
+* Key switching is placed for speed without changing any slot: the baby-step
+  rotations stay in the extended basis Q u P (no ModDown), the diagonal
+  products are summed there and each accumulator is lowered once; the
+  giant-step rotations of a group are summed in Q u P and lowered once.
 """
 from __future__ import annotations
 
@@ -36,8 +40,8 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import ring
-from .bfv import (Params, ct_add, decrypt, encode, lift, mod_up_all, pt_mul, qlimbs,
-                  rotate, rotate_hoisted, encrypt)
+from .bfv import (Params, ct_add, ct_mod_down, ct_times_P, decrypt, encode, encrypt, lift,
+                  mod_up_all, poly_add, pt_mul, rotate, rotate_ext)
 
 
 # ------------------------------------------------------------------ plan ----
@@ -214,21 +218,42 @@ def group_halfblocks(plan: Plan, gamma: int) -> range:
 
 
 def baby_steps(par: Params, u, keys, plan: Plan):
-    """R[h][a] = Rot_row(u_h; a), a = 0..B-1, the digits of c1 raised once per
-    u_h and shared by all its rotations."""
+    """R[h][a] = Rot_row(u_h; a) for a = 0..B-1, kept in the extended basis
+    Q u P before its ModDown (a = 0: (P c0, P c1)); the digits of c1 are
+    raised once per u_h and shared by all its rotations."""
     R = []
     for uh in u:
         raised = mod_up_all(par, uh[1])
-        row = [uh]
+        row = [ct_times_P(par, uh)]
         for a in range(1, plan.B):
             k = par.galois_rot(a)
-            row.append(rotate_hoisted(par, uh, raised, k, keys[k]))
+            row.append(rotate_ext(par, uh, raised, k, keys[k]))
         R.append(row)
     return R
 
 
+def ring_dot_ext(par: Params, pts, cts) -> np.ndarray:
+    """ring_dot over the extended basis: sum_i pts[i] * cts[i] in R_{QP}
+    (pts [L+K][N], cts [2][L+K][N]), through the oracle's transform."""
+    E, N = par.L + par.K, par.N
+    acc = np.zeros((2, E, N), dtype=np.uint64)
+    for pt, ct in zip(pts, cts):
+        for i in range(E):
+            q, psi = par.ext[i], par.psi[i]
+            fp = ring.ntt_forward(pt[i], q, psi)
+            for p in range(2):
+                fc = ring.ntt_forward(ct[p][i], q, psi)
+                acc[p][i] = ring.vec_add(acc[p][i], ring.vec_mul(fp, fc, q), q)
+    for p in range(2):
+        for i in range(E):
+            acc[p][i] = ring.ntt_inverse(acc[p][i], par.ext[i], par.psi[i])
+    return acc
+
+
 def giant_accumulators(par: Params, R, plan: Plan):
-    """acc[gamma][g] = sum_{h in gamma} sum_{a<B} Rot(D_{h,gB+a}; -gB) . Rot(u_h; a)."""
+    """acc[gamma][g] = ModDown( sum_{h in gamma} sum_{a<B} Rot(D_{h,gB+a}; -gB) . R[h][a] ),
+    the products summed over Q u P (diagonals lifted to every prime) and
+    lowered to Q once per accumulator."""
     acc = []
     for gamma in range(plan.G):
         row = []
@@ -238,22 +263,26 @@ def giant_accumulators(par: Params, R, plan: Plan):
                 for a in range(plan.B):
                     d = rot_slots(par, diagonal_slots(par, plan, h, g * plan.B + a),
                                   -g * plan.B)
-                    pts.append(lifted_pt(par, d))
+                    pts.append(lift(par, encode(par, d), par.ext))
                     cts.append(R[h][a])
-            row.append(ring_dot(par, pts, cts))
+            row.append(ct_mod_down(par, ring_dot_ext(par, pts, cts)))
         acc.append(row)
     return acc
 
 
 def giant_steps(par: Params, acc, keys, plan: Plan):
-    """y_gamma = sum_g Rot(acc[gamma][g]; gB)  (Rot(.; 0) is the identity)."""
+    """y_gamma = ModDown( (P acc[gamma][0]) + sum_{g>=1} Rot(acc[gamma][g]; gB) ),
+    each giant rotation kept in Q u P and the sum lowered to Q once."""
+    el = list(range(par.L + par.K))
     ys = []
     for gamma in range(plan.G):
-        y = acc[gamma][0]
+        y = ct_times_P(par, acc[gamma][0])
         for g in range(1, plan.giants):
             k = par.galois_rot(g * plan.B)
-            y = ct_add(par, y, rotate(par, acc[gamma][g], k, keys[k]))
-        ys.append(y)
+            ct = acc[gamma][g]
+            r = rotate_ext(par, ct, mod_up_all(par, ct[1]), k, keys[k])
+            y = np.stack([poly_add(par, y[0], r[0], el), poly_add(par, y[1], r[1], el)])
+        ys.append(ct_mod_down(par, y))
     return ys
 
 

@@ -11,6 +11,7 @@
 //   6. groups out_c = sum_o M_o . y_{c per_out + o}   (one group: out = y)
 #include <algorithm>
 #include <cstring>
+#include <initializer_list>
 
 #include "pdq_internal.h"
 #include "pdq_ops.h"
@@ -97,27 +98,35 @@ struct Keys {
 };
 
 size_t comp_ws_bytes(const Ctx& c, const pdq_plan& pl) {
-    const u64 cts = ct_elems(c);
-    const u64 R = (u64)pl.H * pl.B * cts;
-    const u64 acc = (u64)pl.G * pl.giants * cts;
-    const u64 ys = 2ull * pl.G * cts;
+    const u64 cts = ct_elems(c), ects = 2ull * (c.L + c.K) * c.N;
+    const u64 U = (u64)pl.H * cts;                       // packed u_h over Q
+    const u64 Rx = (u64)pl.H * pl.B * ects;              // baby steps over Q u P
+    const u64 accx = (u64)pl.G * pl.giants * ects;       // accumulators over Q u P
+    const u64 acc = (u64)pl.G * pl.giants * cts;         // ... lowered to Q
+    const u64 yx = (u64)pl.G * ects;                     // giant-step sums over Q u P
+    const u64 ys = 2ull * pl.G * cts;                    // rotate-and-sum ping-pong
     const u32 cnt = std::max(pl.H, pl.G);
-    return (R + acc + ys) * sizeof(u64) + raise_ws(c, cnt) + apply_ws(c, cnt);
+    const size_t scratch = std::max({apply_ws(c, cnt), mod_down_ws(c, pl.G * pl.giants)});
+    return (U + Rx + accx + acc + yx + ys) * sizeof(u64) + raise_ws(c, cnt) + scratch;
 }
 
 int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& keys,
              const u64* consts, u64* out, void* ws, size_t ws_bytes, cudaStream_t st) {
     if (ws_bytes < comp_ws_bytes(c, pl)) return fail(PDQ_E_NOMEM, "comp: workspace too small");
     const long long cts = (long long)ct_elems(c);
+    const long long ects = 2LL * (c.L + c.K) * c.N;
     const u32 H = pl.H, B = pl.B, G = pl.G, GI = pl.giants;
-    u64* R = reinterpret_cast<u64*>(ws);
-    u64* acc = R + (u64)H * B * cts;
-    u64* Y0 = acc + (u64)G * GI * cts;
+    u64* U = reinterpret_cast<u64*>(ws);
+    u64* Rx = U + (u64)H * cts;
+    u64* accx = Rx + (u64)H * B * ects;
+    u64* acc = accx + (u64)G * GI * ects;
+    u64* yx = acc + (u64)G * GI * cts;
+    u64* Y0 = yx + (u64)G * ects;
     u64* Y1 = Y0 + (u64)G * cts;
     u64* rws = Y1 + (u64)G * cts;
     u64* aws = rws + raise_ws(c, std::max(H, G)) / sizeof(u64);
     const u64* Dg = consts;
-    const u64* masks = consts + (u64)pl.hclass * GI * B * c.L * c.N;
+    const u64* masks = consts + (u64)pl.hclass * GI * B * (c.L + c.K) * c.N;
 
     auto key_for = [&](u64 k, const u64** kp) -> int {
         *kp = keys.find(k);
@@ -132,38 +141,39 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     {
         CtSet in;  in.base = masked + 2 * cts;  in.outer = 4 * cts;  in.per = 2;  in.inner = -cts;
         CtSet add; add.base = masked;           add.outer = 4 * cts; add.per = 2; add.inner = 3 * cts;
-        CtSet o;   o.base = R;                  o.outer = 2LL * B * cts; o.per = 2; o.inner = (long long)B * cts;
         const u64* kp;
         PDQ_TRY(key_for(2ull * c.N - 1, &kp));
         PDQ_TRY(ks_raise(c, in, H, rws, &D, st));
-        PDQ_TRY(ks_apply(c, D, in, H, (u32)(2ull * c.N - 1), kp, o, add, aws, st));
+        PDQ_TRY(ks_apply(c, D, in, H, (u32)(2ull * c.N - 1), kp, ct_set(U, cts), add, aws, st));
     }
-    // 2. baby steps, hoisted
+    // 2. baby steps in the extended basis, the digits of every u_h raised once
     prof_mark(c, PDQ_STAGE_BABY, st);
-    const CtSet u = ct_set(R, (long long)B * cts);
+    const CtSet u = ct_set(U, cts);
+    PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * ects), st));
     if (B > 1) PDQ_TRY(ks_raise(c, u, H, rws, &D, st));
     for (u32 a = 1; a < B; ++a) {
         const u64 k = galois_rot(c, a);
         const u64* kp;
         PDQ_TRY(key_for(k, &kp));
-        PDQ_TRY(ks_apply(c, D, u, H, (u32)k, kp, ct_set(R + (u64)a * cts, (long long)B * cts), none,
-                         aws, st));
+        PDQ_TRY(ks_apply_ext(c, D, u, H, (u32)k, kp, ct_set(Rx + (u64)a * ects, (long long)B * ects),
+                             false, st));
     }
-    // 3. diagonal multiply-accumulate
+    // 3. diagonal multiply-accumulate over Q u P, one ModDown per accumulator
     prof_mark(c, PDQ_STAGE_MAC, st);
-    PDQ_TRY(diag_mac(c, pl, R, Dg, acc, st));
-    // 4. giant steps: y_gamma accumulates in acc[gamma][0]
+    PDQ_TRY(diag_mac(c, pl, Rx, Dg, accx, st));
+    PDQ_TRY(mod_down_batch(c, accx, G * GI, ct_set(acc, cts), aws, st));
+    // 4. giant steps: sum over Q u P, one ModDown per group
     prof_mark(c, PDQ_STAGE_GIANT, st);
-    const CtSet y0 = ct_set(acc, (long long)GI * cts);
+    PDQ_TRY(times_P(c, ct_set(acc, (long long)GI * cts), G, ct_set(yx, ects), st));
     for (u32 g = 1; g < GI; ++g) {
         const u64 k = galois_rot(c, (long long)g * B);
         const u64* kp;
         PDQ_TRY(key_for(k, &kp));
         const CtSet in = ct_set(acc + (u64)g * cts, (long long)GI * cts);
         PDQ_TRY(ks_raise(c, in, G, rws, &D, st));
-        PDQ_TRY(ks_apply(c, D, in, G, (u32)k, kp, y0, y0, aws, st));
+        PDQ_TRY(ks_apply_ext(c, D, in, G, (u32)k, kp, ct_set(yx, ects), true, st));
     }
-    PDQ_TRY(gather_rows(y0, 0, G, (u64)cts, Y0, (u64)cts, st));
+    PDQ_TRY(mod_down_batch(c, yx, G, ct_set(Y0, cts), aws, st));
     // 5. rotate-and-sum, ping-pong between Y0 and Y1
     prof_mark(c, PDQ_STAGE_ROTSUM, st);
     u64* ycur = Y0;
@@ -186,6 +196,7 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
         PDQ_TRY(group_combine(c, pl, ycur, masks, out, st));
     }
     prof_mark(c, -1, st);
+    (void)none;
     return PDQ_OK;
 }
 
@@ -289,8 +300,9 @@ int pdq_plan_galois(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out, uin
 size_t pdq_plan_constants_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {
     if (!ctx || !valid_plan(C(ctx), plan)) return 0;
     const Ctx& c = C(ctx);
-    const u64 pts = (u64)plan->hclass * plan->giants * plan->B + (plan->G > 1 ? plan->per_out : 0);
-    return pts * c.L * c.N * sizeof(u64);
+    const u64 diag = (u64)plan->hclass * plan->giants * plan->B * (c.L + c.K);
+    const u64 masks = plan->G > 1 ? (u64)plan->per_out * c.L : 0;
+    return (diag + masks) * c.N * sizeof(u64);
 }
 
 int pdq_plan_constants_build(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out,
@@ -300,7 +312,7 @@ int pdq_plan_constants_build(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t*
     if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "plan_constants_build: invalid plan");
     PDQ_TRY(build_diagonals(c, *plan, out, (cudaStream_t)stream));
     if (plan->G > 1) {
-        u64* masks = out + (u64)plan->hclass * plan->giants * plan->B * c.L * c.N;
+        u64* masks = out + (u64)plan->hclass * plan->giants * plan->B * (c.L + c.K) * c.N;
         PDQ_TRY(build_group_masks(c, *plan, masks, (cudaStream_t)stream));
     }
     return PDQ_OK;

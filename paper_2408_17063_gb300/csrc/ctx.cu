@@ -153,8 +153,9 @@ static void free_ctx(Ctx* c) {
     if (!c) return;
     void* ptrs[] = {c->d_mods, c->d_fw2, c->d_iw2, c->d_ninv,
                     c->d_slot_pos, c->d_rowmask, c->d_up_hatinv, c->d_up_hatinv_shoup,
-                    c->d_up_hatmod, c->d_dn_hatinv, c->d_dn_hatinv_shoup, c->d_dn_hatmod,
-                    c->d_dn_pinv, c->d_dn_pinv_shoup, c->d_P_mod_q, c->d_delta_mod_q,
+                    c->d_up_hatmod, c->d_up_hatmod_shoup, c->d_dn_hatinv,
+                    c->d_dn_hatinv_shoup, c->d_dn_hatmod, c->d_dn_hatmod_shoup,
+                    c->d_dn_pinv, c->d_dn_pinv_shoup, c->d_P_mod_q, c->d_P_mod_q_shoup, c->d_delta_mod_q,
                     c->d_dec_omega, c->d_dec_omega_shoup, c->d_c30};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -307,6 +308,11 @@ static int build_ctx(const pdq_params& p, Ctx* c) {
     PDQ_TRY(upload(&c->d_up_hatinv, up_inv));
     PDQ_TRY(upload(&c->d_up_hatinv_shoup, up_inv_s));
     PDQ_TRY(upload(&c->d_up_hatmod, up_mod));
+    std::vector<u64> up_mod_s(up_mod.size());
+    for (u32 i = 0; i < L; ++i)
+        for (u32 r = 0; r < E; ++r)
+            up_mod_s[(size_t)i * E + r] = shoup_of(up_mod[(size_t)i * E + r], c->mods[r]);
+    PDQ_TRY(upload(&c->d_up_hatmod_shoup, up_mod_s));
 
     // ModDown constants
     std::vector<u64> dn_inv(K), dn_inv_s(K), dn_mod((size_t)K * L), pinv(L), pinv_s(L);
@@ -337,9 +343,17 @@ static int build_ctx(const pdq_params& p, Ctx* c) {
     PDQ_TRY(upload(&c->d_dn_hatinv, dn_inv));
     PDQ_TRY(upload(&c->d_dn_hatinv_shoup, dn_inv_s));
     PDQ_TRY(upload(&c->d_dn_hatmod, dn_mod));
+    std::vector<u64> dn_mod_s(dn_mod.size());
+    for (u32 k = 0; k < K; ++k)
+        for (u32 i = 0; i < L; ++i)
+            dn_mod_s[(size_t)k * L + i] = shoup_of(dn_mod[(size_t)k * L + i], c->mods[i]);
+    PDQ_TRY(upload(&c->d_dn_hatmod_shoup, dn_mod_s));
     PDQ_TRY(upload(&c->d_dn_pinv, pinv));
     PDQ_TRY(upload(&c->d_dn_pinv_shoup, pinv_s));
     PDQ_TRY(upload(&c->d_P_mod_q, c->P_mod_q));
+    std::vector<u64> pq_s(L);
+    for (u32 i = 0; i < L; ++i) pq_s[i] = shoup_of(c->P_mod_q[i], c->mods[i]);
+    PDQ_TRY(upload(&c->d_P_mod_q_shoup, pq_s));
 
     // Delta = floor(Q/t): Q = t*Delta + (Q mod t) and Q = 0 mod q_i, so
     // Delta = -(Q mod t) * t^{-1} mod q_i.

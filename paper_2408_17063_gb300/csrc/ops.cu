@@ -256,7 +256,7 @@ __global__ void k_mask(const u64* __restrict__ v, const u64* __restrict__ db,
 __global__ void k_modup(const u64* __restrict__ X, CtSet c1ntt, u32 logN, u32 L, u32 E,
                         u32 alpha, const Mod* __restrict__ mods, const u64* __restrict__ hinv,
                         const u64* __restrict__ hinvs, const u64* __restrict__ hmod,
-                        u64* __restrict__ D) {
+                        const u64* __restrict__ hmods, u64* __restrict__ D) {
     const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= (1u << logN)) return;
     const u32 b = blockIdx.y, nd = gridDim.y;
@@ -275,9 +275,13 @@ __global__ void k_modup(const u64* __restrict__ X, CtSet c1ntt, u32 logN, u32 L,
             Dc[((u64)r << logN) + x] = src[((u64)r << logN) + x];
             continue;
         }
-        u64 ah = 0, al = 0;
-        for (u32 l = lo; l < hi; ++l) mac128(ah, al, y[l - lo], hmod[(u64)l * E + r]);
-        Dc[((u64)r << logN) + x] = reduce128(ah, al, mods[r]);
+        // products by the constants (Q_b/q_i) mod r, Shoup: each in [0, 2r),
+        // at most 8 of them, so the sum stays below 2^64
+        const Mod md = mods[r];
+        u64 sum = 0;
+        for (u32 l = lo; l < hi; ++l)
+            sum += mul_shoup_lazy(y[l - lo], hmod[(u64)l * E + r], hmods[(u64)l * E + r], md.q);
+        Dc[((u64)r << logN) + x] = reduce64(sum, md);
     }
 }
 
@@ -314,12 +318,81 @@ __global__ void k_ks_inner(const u64* __restrict__ D, const u64* __restrict__ ke
         make_ulonglong2(reduce128(h1a, l1a, md), reduce128(h1b, l1b, md));
 }
 
+// The rotation before its ModDown, in the extended basis: for output
+// ciphertext ct, limb r < E, position x (two positions per thread)
+//   out[ct][0][r] (+)= sum_beta D[ct][beta][r][s(x)] key[beta][0][r][x] + [r < L] P c0[ct][r][s(x)]
+//   out[ct][1][r] (+)= sum_beta D[ct][beta][r][s(x)] key[beta][1][r][x]
+// with s = sigma_k; `accumulate` adds into out instead of overwriting it.
+__global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict__ key, u32 logN,
+                               u32 E, u32 L, u32 nd, u32 galois, const Mod* __restrict__ mods,
+                               CtSet c0src, const u64* __restrict__ Pq,
+                               const u64* __restrict__ Pqs, CtSet out, u32 accumulate) {
+    const u32 r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const u64 EN = (u64)E << logN;
+    if (r >= EN) return;
+    const u64 ct = blockIdx.y;
+    const u32 l = r >> logN, x = r & ((1u << logN) - 1);
+    const u32 sx = auto_index(x, galois, logN);
+    const bool swap = (sx & 1) != 0;
+    const u32 sr = (l << logN) + (sx & ~1u);
+    u64 h0a = 0, l0a = 0, h1a = 0, l1a = 0, h0b = 0, l0b = 0, h1b = 0, l1b = 0;
+    const u64* Dc = D + ct * nd * EN;
+    for (u32 b = 0; b < nd; ++b) {
+        const ulonglong2 dv = *reinterpret_cast<const ulonglong2*>(Dc + b * EN + sr);
+        const u64 da = swap ? dv.y : dv.x, db = swap ? dv.x : dv.y;
+        const ulonglong2 k0 = __ldg(reinterpret_cast<const ulonglong2*>(key + b * 2 * EN + r));
+        const ulonglong2 k1 = __ldg(reinterpret_cast<const ulonglong2*>(key + b * 2 * EN + EN + r));
+        mac128(h0a, l0a, da, k0.x);
+        mac128(h0b, l0b, db, k0.y);
+        mac128(h1a, l1a, da, k1.x);
+        mac128(h1b, l1b, db, k1.y);
+    }
+    const Mod md = mods[l];
+    u64 a0 = reduce128(h0a, l0a, md), b0 = reduce128(h0b, l0b, md);
+    u64 a1 = reduce128(h1a, l1a, md), b1 = reduce128(h1b, l1b, md);
+    if (l < L) {
+        const ulonglong2 cv = *reinterpret_cast<const ulonglong2*>(c0src.at(ct) + sr);
+        const u64 ca = swap ? cv.y : cv.x, cb = swap ? cv.x : cv.y;
+        a0 = addmod(a0, csub(mul_shoup_lazy(ca, Pq[l], Pqs[l], md.q), md.q), md.q);
+        b0 = addmod(b0, csub(mul_shoup_lazy(cb, Pq[l], Pqs[l], md.q), md.q), md.q);
+    }
+    ulonglong2* o0 = reinterpret_cast<ulonglong2*>(out.at(ct) + r);
+    ulonglong2* o1 = reinterpret_cast<ulonglong2*>(out.at(ct) + EN + r);
+    if (accumulate) {
+        const ulonglong2 p0 = *o0, p1 = *o1;
+        a0 = addmod(a0, p0.x, md.q);
+        b0 = addmod(b0, p0.y, md.q);
+        a1 = addmod(a1, p1.x, md.q);
+        b1 = addmod(b1, p1.y, md.q);
+    }
+    *o0 = make_ulonglong2(a0, b0);
+    *o1 = make_ulonglong2(a1, b1);
+}
+
+// (P c0, P c1) over Q u P from a ciphertext over Q (special limbs 0)
+__global__ void k_times_P(CtSet in, u32 logN, u32 L, u32 E, const Mod* __restrict__ mods,
+                          const u64* __restrict__ Pq, const u64* __restrict__ Pqs, CtSet out) {
+    const u32 rr = blockIdx.x * blockDim.x + threadIdx.x;     // over [2][E][N]
+    const u32 EN = E << logN;
+    if (rr >= 2 * EN) return;
+    const u64 ct = blockIdx.y;
+    const u32 p = rr >= EN ? 1 : 0;
+    const u32 r = rr - p * EN;
+    const u32 l = r >> logN;
+    u64 v = 0;
+    if (l < L) {
+        const u64 q = mods[l].q;
+        v = csub(mul_shoup_lazy(in.at(ct)[(u64)p * (L << logN) + r], Pq[l], Pqs[l], q), q);
+    }
+    out.at(ct)[rr] = v;
+}
+
 // Conv[cp][i] = sum_k [y_k (P/p_k)^-1]_{p_k} (P/p_k) mod q_i from the special
 // limbs of A (coefficient form); cp = blockIdx.y = ct*2 + p
 __global__ void k_moddown_conv(const u64* __restrict__ A, u32 logN, u32 L, u32 K,
                                const Mod* __restrict__ mods, const u64* __restrict__ hinv,
                                const u64* __restrict__ hinvs, const u64* __restrict__ hmod,
-                               u64* __restrict__ Cv) {
+                               const u64* __restrict__ hmods, u64* __restrict__ Cv) {
     const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= (1u << logN)) return;
     const u32 E = L + K;
@@ -332,9 +405,11 @@ __global__ void k_moddown_conv(const u64* __restrict__ A, u32 logN, u32 L, u32 K
     }
     u64* o = Cv + ((cp * L) << logN);
     for (u32 l = 0; l < L; ++l) {
-        u64 ah = 0, al = 0;
-        for (u32 k = 0; k < K; ++k) mac128(ah, al, y[k], hmod[(u64)k * L + l]);
-        o[((u64)l << logN) + x] = reduce128(ah, al, mods[l]);
+        const Mod md = mods[l];
+        u64 sum = 0;
+        for (u32 k = 0; k < K; ++k)
+            sum += mul_shoup_lazy(y[k], hmod[(u64)k * L + l], hmods[(u64)k * L + l], md.q);
+        o[((u64)l << logN) + x] = reduce64(sum, md);
     }
 }
 
@@ -355,7 +430,7 @@ __global__ void k_moddown_final(const u64* __restrict__ A, const u64* __restrict
     const u64 a = A[(((ct * 2 + p) * E) << logN) + r];
     const u64 cv = Cv[(ct * 2 + p) * LN + r];
     u64 v = csub(mul_shoup_lazy(submod(a, cv, q), pinv[l], pinvs[l], q), q);
-    if (p == 0) v = addmod(v, in.at(ct)[((u64)l << logN) + auto_index(x, galois, logN)], q);
+    if (p == 0 && in.base) v = addmod(v, in.at(ct)[((u64)l << logN) + auto_index(x, galois, logN)], q);
     if (add.base) v = addmod(v, add.at(ct)[rr], q);
     out.at(ct)[rr] = v;
 }
@@ -613,12 +688,13 @@ int encode_slots(const Ctx& c, const u32* slots, u32 count, u32 nlimbs, u64* out
 }
 
 int build_diagonals(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st) {
-    const u32 count = pl.hclass * pl.giants * pl.B;
+    // over every prime of Q u P: the products are taken in the extended basis
+    const u32 count = pl.hclass * pl.giants * pl.B, E = c.L + c.K;
     PDQ_TRY(check_y(count, "diagonals"));
     k_diag_slots<<<grid2(c.N, count), kBlock, 0, st>>>(out, pl.giants, pl.B, pl.s_prime, c.log_n,
-                                                       c.L, c.d_slot_pos, c.t);
+                                                       E, c.d_slot_pos, c.t);
     PDQ_TRY(launched("k_diag_slots"));
-    return encode_finish(c, out, count, c.L, st);
+    return encode_finish(c, out, count, E, st);
 }
 
 int build_group_masks(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st) {
@@ -739,7 +815,7 @@ int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t
     PDQ_TRY(ntt_inverse(c, X, cnt, c.L, 0, L * N, st));
     k_modup<<<dim3((c.N + kBlock - 1) / kBlock, (u32)nd, cnt), kBlock, 0, st>>>(
         X, in, c.log_n, c.L, (u32)E, c.alpha, c.d_mods, c.d_up_hatinv, c.d_up_hatinv_shoup,
-        c.d_up_hatmod, D);
+        c.d_up_hatmod, c.d_up_hatmod_shoup, D);
     PDQ_TRY(launched("k_modup"));
     for (u32 b = 0; b < nd; ++b) {
         const u32 lo = c.digit_limbs[b].front(), hi = c.digit_limbs[b].back() + 1;
@@ -768,11 +844,47 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
     PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
     k_moddown_conv<<<grid2(N, 2 * cnt), kBlock, 0, st>>>(A, c.log_n, c.L, c.K, c.d_mods,
                                                          c.d_dn_hatinv, c.d_dn_hatinv_shoup,
-                                                         c.d_dn_hatmod, Cv);
+                                                         c.d_dn_hatmod, c.d_dn_hatmod_shoup, Cv);
     PDQ_TRY(launched("k_moddown_conv"));
     PDQ_TRY(ntt_forward(c, Cv, 2 * cnt, c.L, 0, L * N, st));
     k_moddown_final<<<grid2(2 * L * N, cnt), kBlock, 0, st>>>(A, Cv, in, out, add, c.log_n, c.L,
                                                               c.K, galois, c.d_mods, c.d_dn_pinv,
+                                                              c.d_dn_pinv_shoup);
+    return launched("k_moddown_final");
+}
+
+int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, const u64* key,
+                 CtSet out, bool accumulate, cudaStream_t st) {
+    const u64 N = c.N, E = c.L + c.K;
+    PDQ_TRY(check_y(cnt, "key switch"));
+    k_ks_inner_ext<<<grid2(E * N / 2, cnt), kBlock, 0, st>>>(
+        D, key, c.log_n, (u32)E, c.L, c.ndigits, galois, c.d_mods, c0src, c.d_P_mod_q,
+        c.d_P_mod_q_shoup, out, accumulate ? 1u : 0u);
+    return launched("k_ks_inner_ext");
+}
+
+int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, cudaStream_t st) {
+    const u64 E = c.L + c.K;
+    PDQ_TRY(check_y(cnt, "times_P"));
+    k_times_P<<<grid2(2 * E * c.N, cnt), kBlock, 0, st>>>(in, c.log_n, c.L, (u32)E, c.d_mods,
+                                                         c.d_P_mod_q, c.d_P_mod_q_shoup, out);
+    return launched("k_times_P");
+}
+
+size_t mod_down_ws(const Ctx& c, u32 cnt) { return (size_t)cnt * 2 * c.L * c.N * sizeof(u64); }
+
+int mod_down_batch(const Ctx& c, u64* A, u32 cnt, CtSet out, u64* ws, cudaStream_t st) {
+    const u64 N = c.N, L = c.L, E = c.L + c.K;
+    PDQ_TRY(check_y(2ull * cnt, "mod_down"));
+    u64* Cv = ws;
+    PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
+    k_moddown_conv<<<grid2(N, 2 * cnt), kBlock, 0, st>>>(A, c.log_n, c.L, c.K, c.d_mods,
+                                                         c.d_dn_hatinv, c.d_dn_hatinv_shoup,
+                                                         c.d_dn_hatmod, c.d_dn_hatmod_shoup, Cv);
+    PDQ_TRY(launched("k_moddown_conv"));
+    PDQ_TRY(ntt_forward(c, Cv, 2 * cnt, c.L, 0, L * N, st));
+    k_moddown_final<<<grid2(2 * L * N, cnt), kBlock, 0, st>>>(A, Cv, CtSet{}, out, CtSet{}, c.log_n,
+                                                              c.L, c.K, 0, c.d_mods, c.d_dn_pinv,
                                                               c.d_dn_pinv_shoup);
     return launched("k_moddown_final");
 }
@@ -838,9 +950,10 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
             return cuda_check("k_diag_mac attribute");
         configured = true;
     }
-    const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, c.L, s.zslices);
+    const u32 E = c.L + c.K;
+    const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, E, s.zslices);
     k_diag_mac<GT><<<grid, s.threads, s.smem, st>>>(R, Dg, pl.G, pl.hpg, pl.H, pl.B, s.Bc,
-                                                    pl.giants, c.L, c.log_n, s.logX, s.logGS,
+                                                    pl.giants, E, c.log_n, s.logX, s.logGS,
                                                     s.combos_per_cta, s.tiles_per_cta,
                                                     log2u(pl.giants), log2u(s.Bc), c.d_mods,
                                                     c.d_c30, acc);

@@ -120,15 +120,18 @@ struct Ctx {
     u64* d_up_hatinv = nullptr;   // [L] (q_i's own digit), value
     u64* d_up_hatinv_shoup = nullptr;
     u64* d_up_hatmod = nullptr;   // [L][L+K]: (Q_{digit(i)}/q_i) mod r
+    u64* d_up_hatmod_shoup = nullptr;
     // ModDown: (P/p_k)^-1 mod p_k (+shoup); (P/p_k) mod q_i; P^-1 mod q_i (+shoup)
     u64* d_dn_hatinv = nullptr;   // [K]
     u64* d_dn_hatinv_shoup = nullptr;
     u64* d_dn_hatmod = nullptr;   // [K][L]
+    u64* d_dn_hatmod_shoup = nullptr;
     u64* d_dn_pinv = nullptr;     // [L]
     u64* d_dn_pinv_shoup = nullptr;
     // P mod q_i (keygen), Delta mod q_i (encryption)
     std::vector<u64> P_mod_q, delta_mod_q;
     u64* d_P_mod_q = nullptr;
+    u64* d_P_mod_q_shoup = nullptr;
     u64* d_delta_mod_q = nullptr;
     // decryption: per q_i, omega_i = (Q/q_i)^-1 mod q_i (+shoup), and
     // t * b / q_i split for rounding is done with 128-bit arithmetic.

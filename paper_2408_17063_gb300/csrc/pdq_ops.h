@@ -57,6 +57,17 @@ int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t
 int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u64* key,
              CtSet out, CtSet add, u64* ws, cudaStream_t st);
 
+// Extended-basis rotation (no ModDown): out (+)= (P sigma(c0) + A0, A1) over
+// Q u P, out ciphertexts [2][L+K][N]
+int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, const u64* key,
+                 CtSet out, bool accumulate, cudaStream_t st);
+// (P c0, P c1) over Q u P
+int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, cudaStream_t st);
+// ModDown of cnt extended-basis ciphertexts A ([cnt][2][L+K][N], special limbs
+// clobbered) into out (Q basis)
+size_t mod_down_ws(const Ctx& c, u32 cnt);
+int mod_down_batch(const Ctx& c, u64* A, u32 cnt, CtSet out, u64* ws, cudaStream_t st);
+
 int gather_rows(CtSet src, long long src_off, u32 cnt, u64 len, u64* dst, u64 dst_stride,
                 cudaStream_t st);
 int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc,

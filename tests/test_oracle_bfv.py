@@ -212,3 +212,21 @@ def test_plaintext_product_decrypts(tiny2):
     ct = bfv.encrypt(par, sk, bfv.encode(par, x), a[0], e[0])
     out = bfv.pt_mul(par, ct, bfv.lift(par, bfv.encode(par, y), par.q))
     assert np.array_equal(bfv.decrypt(par, sk, out), x * y % par.t)
+
+
+@pytest.mark.parametrize("cfg", ["tiny", "tiny2"])
+def test_extended_rotation_lowers_to_the_rotation(cfg):
+    """Keeping a rotation in Q u P and lowering it later gives the same bits:
+    ModDown(P sigma(c0) + A0) = sigma(c0) + ModDown(A0) because P sigma(c0)
+    vanishes modulo the special primes; and ModDown(P x) = x."""
+    par = bfv.Params.from_config(W.CONFIGS[cfg])
+    sk = _key_material(par, 21)
+    a, e = W.encryption_randomness(par.q, par.N, 1, seed=21)
+    slots = W.rng_for(22).integers(0, par.t, size=par.N, dtype=np.uint64)
+    ct = bfv.encrypt(par, sk, bfv.encode(par, slots), a[0], e[0])
+    k = par.galois_rot(2)
+    kr = W.rotation_key_randomness(par.ext, par.N, len(par.digits), [k], seed=23)
+    key = bfv.rotation_key(par, sk, k, *kr[k])
+    ext = bfv.rotate_ext(par, ct, bfv.mod_up_all(par, ct[1]), k, key)
+    assert np.array_equal(bfv.ct_mod_down(par, ext), bfv.rotate(par, ct, k, key))
+    assert np.array_equal(bfv.ct_mod_down(par, bfv.ct_times_P(par, ct)), ct)
