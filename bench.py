@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--n", type=int, default=0, help="override the record count")
+    ap.add_argument("--L", type=int, default=0, help="override the ciphertext primes")
+    ap.add_argument("--K", type=int, default=0, help="override the special primes")
+    ap.add_argument("--dnum", type=int, default=0, help="override the key-switching digits")
     ap.add_argument("--s", type=int, default=0, help="override the sparsity")
     ap.add_argument("--mix", type=int, default=64, help="queries of the batched/served mix (0: skip)")
     ap.add_argument("--lanes", type=int, default=4)
@@ -58,6 +61,24 @@ def config_dict(cfg, extra=None):
                "740 MiB keys read per query)"}
     d.update(extra or {})
     return d
+
+
+# ------------------------------------------------------------- replicas -----
+
+def max_over_ranks(value: float, dist=None, device="cuda") -> float:
+    """The slowest rank's value (each rank answers its own queries; the job
+    takes as long as its slowest replica)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(total_ms: float, steps: int, world: int, queries_per_step: int = 1) -> float:
+    """Whole-job queries/s: all ranks' queries over the slowest rank's time."""
+    return world * steps * queries_per_step / (total_ms / 1000.0)
 
 
 # ------------------------------------------------------------------ clocks --
@@ -211,11 +232,7 @@ def run_e2e(args, ctx, plan, v_cts, db, keys, galois, consts, ws, stream, dist, 
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         ctx.answer_host(plan, v_host, db, keys, galois, consts, out_host, ws=ws_host, stream=stream)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     e2e = {"value": world * args.e2e_steps / e2e_s, "unit": "queries/s",
            "h2d_bytes_per_step": v_host.numel() * 8, "d2h_bytes_per_step": out_host.numel() * 8,
            "steps": args.e2e_steps, "entry_point": "pdq_answer_host"}
@@ -482,12 +499,8 @@ def run_gpu(args, cfg, rank: int, world: int):
     stages = ctx.profile_read()
     ctx.profile_enable(False)
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dist)
+    value = job_throughput(total_ms, args.steps, world)
 
     # end to end through the host-buffer entry point (pinned host buffers,
     # coefficient form, copies inside the timed region)
@@ -549,8 +562,9 @@ def main():
     import dataclasses
     import workloads as W
     cfg = W.CONFIGS[args.config]
-    if args.n or args.s:
-        cfg = dataclasses.replace(cfg, n=args.n or cfg.n, s=args.s or cfg.s)
+    if args.n or args.s or args.L or args.K or args.dnum:
+        cfg = dataclasses.replace(cfg, n=args.n or cfg.n, s=args.s or cfg.s, L=args.L or cfg.L,
+                                  K=args.K or cfg.K, dnum=args.dnum or cfg.dnum)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

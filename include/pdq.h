@@ -180,8 +180,10 @@ int pdq_plan_galois(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out, uin
 /* Query-independent constants of a plan: the extended diagonals
  *   D_{h,k}[c] = alpha(h m + ((c+k) mod m))^{(c mod s')+1} mod t,
  * alpha(i) = (i mod G_sz) + 1, rotated by -gB for k = gB + a, encoded on both
- * rows (Sec. 5.2: "encoding C twice"), for the hclass distinct half-block
- * classes; then the group masks.  dev out of pdq_plan_constants_bytes. */
+ * rows (Sec. 5.2: "encoding C twice") over every prime of Q u P, for the
+ * hclass distinct half-block classes; then the group masks.  The layout is
+ * internal to the library (the diagonals are stored in the operand format of
+ * its multiply-accumulate).  dev out of pdq_plan_constants_bytes. */
 size_t pdq_plan_constants_bytes(const pdq_ctx* ctx, const pdq_plan* plan);
 int pdq_plan_constants_build(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out,
                              void* stream);

@@ -149,14 +149,16 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     // 2. baby steps in the extended basis, the digits of every u_h raised once
     prof_mark(c, PDQ_STAGE_BABY, st);
     const CtSet u = ct_set(U, cts);
-    PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * ects), st));
-    if (B > 1) PDQ_TRY(ks_raise(c, u, H, rws, &D, st));
-    for (u32 a = 1; a < B; ++a) {
-        const u64 k = galois_rot(c, a);
-        const u64* kp;
-        PDQ_TRY(key_for(k, &kp));
-        PDQ_TRY(ks_apply_ext(c, D, u, H, (u32)k, kp, ct_set(Rx + (u64)a * ects, (long long)B * ects),
-                             false, st));
+    PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * ects), true, st));
+    if (B > 1) {
+        PDQ_TRY(ks_raise(c, u, H, rws, &D, st));
+        std::vector<u64> koff(B, 0);
+        for (u32 a = 1; a < B; ++a) {
+            const u64* kp;
+            PDQ_TRY(key_for(galois_rot(c, a), &kp));
+            koff[a] = (u64)(kp - keys.base);
+        }
+        PDQ_TRY(baby_steps_ext(c, D, u, H, B, keys.base, koff, Rx, st));
     }
     // 3. diagonal multiply-accumulate over Q u P, one ModDown per accumulator
     prof_mark(c, PDQ_STAGE_MAC, st);
@@ -164,14 +166,14 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     PDQ_TRY(mod_down_batch(c, accx, G * GI, ct_set(acc, cts), aws, st));
     // 4. giant steps: sum over Q u P, one ModDown per group
     prof_mark(c, PDQ_STAGE_GIANT, st);
-    PDQ_TRY(times_P(c, ct_set(acc, (long long)GI * cts), G, ct_set(yx, ects), st));
+    PDQ_TRY(times_P(c, ct_set(acc, (long long)GI * cts), G, ct_set(yx, ects), false, st));
     for (u32 g = 1; g < GI; ++g) {
         const u64 k = galois_rot(c, (long long)g * B);
         const u64* kp;
         PDQ_TRY(key_for(k, &kp));
         const CtSet in = ct_set(acc + (u64)g * cts, (long long)GI * cts);
         PDQ_TRY(ks_raise(c, in, G, rws, &D, st));
-        PDQ_TRY(ks_apply_ext(c, D, in, G, (u32)k, kp, ct_set(yx, ects), true, st));
+        PDQ_TRY(ks_apply_ext(c, D, in, G, (u32)k, kp, ct_set(yx, ects), true, false, st));
     }
     PDQ_TRY(mod_down_batch(c, yx, G, ct_set(Y0, cts), aws, st));
     // 5. rotate-and-sum, ping-pong between Y0 and Y1

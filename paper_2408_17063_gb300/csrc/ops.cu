@@ -39,6 +39,9 @@ __device__ __forceinline__ u32 auto_index(u32 x, u32 k, u32 logN) {
     return __brev((e2 - 1) >> 1) >> (32 - logN);
 }
 
+// v -> v0 | v1 << 32 with v = v0 + v1 2^30 (the operand layout of k_diag_mac)
+__device__ __forceinline__ u64 split30(u64 v) { return (v & 0x3fffffffull) | ((v >> 30) << 32); }
+
 // ------------------------------------------------------------- encoding ----
 
 // out[c][0][pos[idx]] = slots[c][idx] mod t
@@ -326,7 +329,8 @@ __global__ void k_ks_inner(const u64* __restrict__ D, const u64* __restrict__ ke
 __global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict__ key, u32 logN,
                                u32 E, u32 L, u32 nd, u32 galois, const Mod* __restrict__ mods,
                                CtSet c0src, const u64* __restrict__ Pq,
-                               const u64* __restrict__ Pqs, CtSet out, u32 accumulate) {
+                               const u64* __restrict__ Pqs, CtSet out, u32 accumulate,
+                               u32 split) {
     const u32 r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const u64 EN = (u64)E << logN;
     if (r >= EN) return;
@@ -365,13 +369,90 @@ __global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict_
         a1 = addmod(a1, p1.x, md.q);
         b1 = addmod(b1, p1.y, md.q);
     }
+    if (split) {
+        a0 = split30(a0); b0 = split30(b0); a1 = split30(a1); b1 = split30(b1);
+    }
     *o0 = make_ulonglong2(a0, b0);
     *o1 = make_ulonglong2(a1, b1);
 }
 
+// All hoisted baby-step rotations a = 1..B-1 of H ciphertexts in one launch,
+// in the extended basis (the rotation before its ModDown), written in the
+// split operand layout of the multiply-accumulate:
+//   R[h][a][0][r][x] = sum_beta D[h][beta][r][s(x)] key_a[beta][0][r][x] + [r < L] P c0_h[r][s(x)]
+//   R[h][a][1][r][x] = sum_beta D[h][beta][r][s(x)] key_a[beta][1][r][x],   s = sigma_{3^a}.
+// A CTA owns the aligned input tile Y = [y0, y0+T) of limb r for HC
+// ciphertexts: it stages their raised digits (and c0) at Y in shared memory
+// once; sigma_{3^a} maps the aligned output tile X_a = sigma^{-1}(Y) onto Y,
+// so for every a it reads the key tile at X_a, computes all outputs of X_a
+// and writes them as contiguous runs.
+struct BabyParams {
+    u32 k[128];       // Galois element of Rot(.; a)
+    u32 kinv[128];    // its inverse mod 2N
+    u64 koff[128];    // element offset of key a in the key buffer
+};
+
+template <int T, int HC, int CPT>
+__global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
+        const u64* __restrict__ D, CtSet u, const u64* __restrict__ keys, u32 H, u32 B, u32 logN,
+        u32 E, u32 L, u32 nd, const Mod* __restrict__ mods, const u64* __restrict__ Pq,
+        const u64* __restrict__ Pqs, u64* __restrict__ Rx, const BabyParams bp) {
+    extern __shared__ __align__(16) u64 sm[];
+    u64* Ds = sm;                       // [HC][nd][T]
+    u64* Cs = Ds + HC * nd * T;         // [HC][T]
+    u64* Ks = Cs + HC * T;              // [nd][2][T]
+    const u32 y0 = blockIdx.x * T, r = blockIdx.y, h0 = blockIdx.z * HC;
+    const u64 EN = (u64)E << logN;
+    const u32 nthreads = T * HC / CPT;
+    for (u32 e = threadIdx.x; e < HC * nd * T; e += nthreads) {
+        const u32 yy = e % T, rest = e / T, b = rest % nd, ct = rest / nd;
+        const u32 h = h0 + ct;
+        Ds[e] = h < H ? D[((u64)h * nd + b) * EN + ((u64)r << logN) + y0 + yy] : 0;
+    }
+    if (r < L) {
+        for (u32 e = threadIdx.x; e < HC * T; e += nthreads) {
+            const u32 yy = e % T, ct = e / T, h = h0 + ct;
+            Cs[e] = h < H ? u.at(h)[((u64)r << logN) + y0 + yy] : 0;
+        }
+    }
+    const Mod md = mods[r];
+    const u64 P = r < L ? Pq[r] : 0, Ps = r < L ? Pqs[r] : 0;
+    const u32 xi = threadIdx.x % T, hg = threadIdx.x / T;
+    for (u32 a = 1; a < B; ++a) {
+        const u32 x0 = auto_index(y0, bp.kinv[a], logN) & ~(T - 1);
+        __syncthreads();                // Ds/Cs ready; previous Ks consumed
+        const u64* key = keys + bp.koff[a];
+        for (u32 e = threadIdx.x; e < nd * 2 * T; e += nthreads) {
+            const u32 xx = e % T, bp2 = e / T;            // bp2 = beta * 2 + p
+            Ks[e] = key[(u64)bp2 * EN + ((u64)r << logN) + x0 + xx];
+        }
+        __syncthreads();
+        const u32 x = x0 + xi;
+        const u32 y = auto_index(x, bp.k[a], logN) - y0;  // in [0, T)
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            const u32 ct = hg * CPT + i, h = h0 + ct;
+            if (h >= H) continue;
+            u64 h0a = 0, l0a = 0, h1a = 0, l1a = 0;
+            for (u32 b = 0; b < nd; ++b) {
+                const u64 d = Ds[(ct * nd + b) * T + y];
+                mac128(h0a, l0a, d, Ks[(b * 2) * T + xi]);
+                mac128(h1a, l1a, d, Ks[(b * 2 + 1) * T + xi]);
+            }
+            u64 v0 = reduce128(h0a, l0a, md);
+            const u64 v1 = reduce128(h1a, l1a, md);
+            if (r < L) v0 = addmod(v0, csub(mul_shoup_lazy(Cs[ct * T + y], P, Ps, md.q), md.q), md.q);
+            u64* o = Rx + (((u64)h * B + a) * 2) * EN + ((u64)r << logN) + x;
+            o[0] = split30(v0);
+            o[EN] = split30(v1);
+        }
+    }
+}
+
 // (P c0, P c1) over Q u P from a ciphertext over Q (special limbs 0)
 __global__ void k_times_P(CtSet in, u32 logN, u32 L, u32 E, const Mod* __restrict__ mods,
-                          const u64* __restrict__ Pq, const u64* __restrict__ Pqs, CtSet out) {
+                          const u64* __restrict__ Pq, const u64* __restrict__ Pqs, CtSet out,
+                          u32 split) {
     const u32 rr = blockIdx.x * blockDim.x + threadIdx.x;     // over [2][E][N]
     const u32 EN = E << logN;
     if (rr >= 2 * EN) return;
@@ -384,7 +465,7 @@ __global__ void k_times_P(CtSet in, u32 logN, u32 L, u32 E, const Mod* __restric
         const u64 q = mods[l].q;
         v = csub(mul_shoup_lazy(in.at(ct)[(u64)p * (L << logN) + r], Pq[l], Pqs[l], q), q);
     }
-    out.at(ct)[rr] = v;
+    out.at(ct)[rr] = split ? split30(v) : v;
 }
 
 // Conv[cp][i] = sum_k [y_k (P/p_k)^-1]_{p_k} (P/p_k) mod q_i from the special
@@ -440,11 +521,12 @@ __global__ void k_moddown_final(const u64* __restrict__ A, const u64* __restrict
 // Diagonal multiply-accumulate (the Pegasus inner sum):
 //   acc[gamma][g][p][l][x] = sum_{hh} sum_{a<B} Dg[hh][g][a][l][x] * R[gamma hpg + hh][a][p][l][x]
 //
-// Arithmetic: residues are < 2^60, split into 30-bit halves v = v0 + v1 2^30;
+// Arithmetic: residues are < 2^60, split into 30-bit halves v = v0 + v1 2^30
+// (both operands arrive stored as v0 | v1 << 32, see split30);
 // a product then is four 32x32->64-bit multiply-adds into four 64-bit partial
 // sums (S0 = sum a0 b0, S1a = sum a0 b1, S1b = sum a1 b0, S2 = sum a1 b1), each
-// term < 2^60, so 15 terms fit; the sums are folded back to one residue
-// (S0 + (S1a + S1b) 2^30 + S2 2^60 mod q) every 14 terms and at the end.
+// term < 2^60; every 14 terms the sums are renormalised (renorm30) and at
+// the end folded to one residue S0 + (S1a + S1b) 2^30 + S2 2^60 mod q.
 //
 // Work split: one CTA owns limb l = blockIdx.y and X consecutive positions;
 // thread (xi, gs, ct) handles position x0 + xi, giant indices gs*GT ..
@@ -480,6 +562,19 @@ __device__ __forceinline__ u64 fold30(const Acc30& A, const Fold30& f) {
     v += mul_shoup_lazy(A.s1b, f.c30, f.c30s, q);                   // [0, 6q)
     v += mul_shoup_lazy(A.s2, f.c60, f.c60s, q);                    // [0, 8q) < 2^63
     return reduce64(v, f.md);
+}
+
+// Keep the value S0 + (S1a + S1b) 2^30 + S2 2^60 (mod q) while shrinking the
+// sums: carry the bits above 30 of S0 into S1a and of S1a, S1b into S2, then
+// reduce S2 mod q.  Afterwards S0, S1a, S1b < 2^30 and S2 < q < 2^60, so 14
+// more products of 30-bit halves fit into every sum.
+__device__ __forceinline__ void renorm30(Acc30& A, const Mod& md) {
+    A.s1a += A.s0 >> 30;
+    A.s0 &= 0x3fffffffull;
+    const u64 c = (A.s1a >> 30) + (A.s1b >> 30);
+    A.s1a &= 0x3fffffffull;
+    A.s1b &= 0x3fffffffull;
+    A.s2 = reduce64(A.s2 + c, md);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
@@ -586,21 +681,21 @@ __global__ void __launch_bounds__(512) k_diag_mac(const u64* __restrict__ R,
             if (terms == 14) {
 #pragma unroll
                 for (int g = 0; g < GT; ++g) {
-                    A0[g] = Acc30{fold30(A0[g], f), 0, 0, 0};
-                    A1[g] = Acc30{fold30(A1[g], f), 0, 0, 0};
+                    renorm30(A0[g], f.md);
+                    renorm30(A1[g], f.md);
                 }
-                terms = 1;
+                terms = 0;
             }
             ++terms;
+            // operands are stored split: low 30 bits | high 30 bits << 32
             const u64 r0 = Rt0[ai * Xp], r1 = Rt1[ai * Xp];
-            const u32 r00 = (u32)r0 & 0x3fffffffu, r01 = (u32)(r0 >> 30);
-            const u32 r10 = (u32)r1 & 0x3fffffffu, r11 = (u32)(r1 >> 30);
+            const u32 r00 = (u32)r0, r01 = (u32)(r0 >> 32);
+            const u32 r10 = (u32)r1, r11 = (u32)(r1 >> 32);
 #pragma unroll
             for (int g = 0; g < GT; ++g) {
                 const u64 d = D[(ai * GI + g) * Xp];
-                const u32 d0 = (u32)d & 0x3fffffffu, d1 = (u32)(d >> 30);
-                mac30(A0[g], r00, r01, d0, d1);
-                mac30(A1[g], r10, r11, d0, d1);
+                mac30(A0[g], r00, r01, (u32)d, (u32)(d >> 32));
+                mac30(A1[g], r10, r11, (u32)d, (u32)(d >> 32));
             }
         }
         const u32 tt = st / spt;
@@ -622,6 +717,11 @@ __global__ void __launch_bounds__(512) k_diag_mac(const u64* __restrict__ R,
         }
         __syncthreads();                 // buffer `buf` is refilled by the next issue
     }
+}
+
+__global__ void k_split30(u64* __restrict__ data, u64 n) {
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) data[i] = split30(data[i]);
 }
 
 // y[ct] += x[ct] (ciphertexts)
@@ -694,7 +794,11 @@ int build_diagonals(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st)
     k_diag_slots<<<grid2(c.N, count), kBlock, 0, st>>>(out, pl.giants, pl.B, pl.s_prime, c.log_n,
                                                        E, c.d_slot_pos, c.t);
     PDQ_TRY(launched("k_diag_slots"));
-    return encode_finish(c, out, count, E, st);
+    PDQ_TRY(encode_finish(c, out, count, E, st));
+    // stored in the operand layout of the multiply-accumulate
+    const u64 n = (u64)count * E * c.N;
+    k_split30<<<(u32)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(out, n);
+    return launched("k_split30");
 }
 
 int build_group_masks(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st) {
@@ -854,20 +958,61 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
 }
 
 int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, const u64* key,
-                 CtSet out, bool accumulate, cudaStream_t st) {
+                 CtSet out, bool accumulate, bool split, cudaStream_t st) {
     const u64 N = c.N, E = c.L + c.K;
     PDQ_TRY(check_y(cnt, "key switch"));
+    if (accumulate && split) return fail(PDQ_E_PARAM, "ks_apply_ext: cannot accumulate split output");
     k_ks_inner_ext<<<grid2(E * N / 2, cnt), kBlock, 0, st>>>(
         D, key, c.log_n, (u32)E, c.L, c.ndigits, galois, c.d_mods, c0src, c.d_P_mod_q,
-        c.d_P_mod_q_shoup, out, accumulate ? 1u : 0u);
+        c.d_P_mod_q_shoup, out, accumulate ? 1u : 0u, split ? 1u : 0u);
     return launched("k_ks_inner_ext");
 }
 
-int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, cudaStream_t st) {
+int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
+                   const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st) {
+    constexpr u32 T = 64, HC = 16, CPT = 4;
+    if (B > 128) return fail(PDQ_E_PARAM, "baby steps: B <= 128");
+    const size_t tile_bytes = ((size_t)HC * c.ndigits * T + HC * T + c.ndigits * 2 * T) * sizeof(u64);
+    if (c.N < T || tile_bytes > (160u << 10)) {
+        // rings below one tile, or too many digits for the staged tile: one
+        // rotation at a time
+        for (u32 a = 1; a < B; ++a) {
+            const u32 k = (u32)host_powmod(3, a, 2ull * c.N);
+            PDQ_TRY(ks_apply_ext(c, D, u, H, k, keys + key_offsets[a],
+                                 ct_set(Rx + (u64)a * 2 * (c.L + c.K) * c.N,
+                                        (long long)B * 2 * (c.L + c.K) * c.N),
+                                 false, true, st));
+        }
+        return PDQ_OK;
+    }
+    BabyParams bp{};
+    for (u32 a = 1; a < B; ++a) {
+        bp.k[a] = (u32)host_powmod(3, a, 2ull * c.N);
+        bp.kinv[a] = (u32)host_invmod(bp.k[a], 2ull * c.N);
+        bp.koff[a] = key_offsets[a];
+    }
+    const u32 E = c.L + c.K, nd = c.ndigits;
+    const size_t smem = ((size_t)HC * nd * T + HC * T + nd * 2 * T) * sizeof(u64);
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(k_baby_ext<T, HC, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem > (48 << 10) ? (int)smem : (48 << 10)) != cudaSuccess)
+            return cuda_check("k_baby_ext attribute");
+        configured = true;
+    }
+    const dim3 grid(c.N / T, E, (H + HC - 1) / HC);
+    k_baby_ext<T, HC, CPT><<<grid, T * HC / CPT, smem, st>>>(D, u, keys, H, B, c.log_n, E, c.L, nd,
+                                                             c.d_mods, c.d_P_mod_q,
+                                                             c.d_P_mod_q_shoup, Rx, bp);
+    return launched("k_baby_ext");
+}
+
+int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, bool split, cudaStream_t st) {
     const u64 E = c.L + c.K;
     PDQ_TRY(check_y(cnt, "times_P"));
     k_times_P<<<grid2(2 * E * c.N, cnt), kBlock, 0, st>>>(in, c.log_n, c.L, (u32)E, c.d_mods,
-                                                         c.d_P_mod_q, c.d_P_mod_q_shoup, out);
+                                                         c.d_P_mod_q, c.d_P_mod_q_shoup, out,
+                                                         split ? 1u : 0u);
     return launched("k_times_P");
 }
 

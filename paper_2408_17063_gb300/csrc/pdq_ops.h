@@ -59,10 +59,17 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
 
 // Extended-basis rotation (no ModDown): out (+)= (P sigma(c0) + A0, A1) over
 // Q u P, out ciphertexts [2][L+K][N]
+// (`split`: residues stored as v0 | v1 << 32, v = v0 + v1 2^30, the operand
+// layout of diag_mac; not combinable with `accumulate`)
 int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, const u64* key,
-                 CtSet out, bool accumulate, cudaStream_t st);
+                 CtSet out, bool accumulate, bool split, cudaStream_t st);
+// All baby-step rotations a = 1..B-1 of the H ciphertexts u (raised digits
+// D) in one launch, written to Rx[h][a] in the split operand layout; key a at
+// keys + key_offsets[a]
+int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
+                   const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st);
 // (P c0, P c1) over Q u P
-int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, cudaStream_t st);
+int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, bool split, cudaStream_t st);
 // ModDown of cnt extended-basis ciphertexts A ([cnt][2][L+K][N], special limbs
 // clobbered) into out (Q basis)
 size_t mod_down_ws(const Ctx& c, u32 cnt);
@@ -70,6 +77,7 @@ int mod_down_batch(const Ctx& c, u64* A, u32 cnt, CtSet out, u64* ws, cudaStream
 
 int gather_rows(CtSet src, long long src_off, u32 cnt, u64 len, u64* dst, u64 dst_stride,
                 cudaStream_t st);
+// R and Dg in the split operand layout; acc canonical
 int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc,
              cudaStream_t st);
 int ct_add(const Ctx& c, CtSet y, CtSet x, u32 cnt, cudaStream_t st);

@@ -1,0 +1,118 @@
+// Register-only throughput ceilings of the two arithmetic primitives of the
+// library on the current GPU, used as the ALU roofline denominators:
+//   * a modular multiply-accumulate of 60-bit residues in the form the
+//     diagonal multiply-accumulate uses (30-bit halves, four 32x32->64-bit
+//     multiply-adds into 64-bit partial sums), and in the 128-bit carry-chain
+//     form the key-switching inner products use;
+//   * the forward NTT butterfly (Harvey's lazy Cooley-Tukey butterfly with a
+//     Shoup twiddle multiplication).
+// No memory traffic inside the timed loops; CUDA events around each kernel.
+#include <cstdint>
+#include <cstdio>
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+__device__ __forceinline__ void mac128(u64& hi, u64& lo, u64 a, u64 b) {
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(lo), "+l"(hi) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ void mac30(u64* s, u32 a0, u32 a1, u32 b0, u32 b1) {
+    asm("mad.wide.u32 %0, %4, %6, %0;\n\tmad.wide.u32 %1, %4, %7, %1;\n\t"
+        "mad.wide.u32 %2, %5, %6, %2;\n\tmad.wide.u32 %3, %5, %7, %3;"
+        : "+l"(s[0]), "+l"(s[1]), "+l"(s[2]), "+l"(s[3]) : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ u64 csub(u64 x, u64 q) { return x >= q ? x - q : x; }
+__device__ __forceinline__ void bf(u64& x, u64& y, u64 w, u64 wp, u64 q) {
+    const u64 a = csub(x, 2 * q);
+    const u64 t = y * w - __umul64hi(y, wp) * q;
+    x = a + t;
+    y = a - t + 2 * q;
+}
+
+template <int V>
+__global__ void k_mac(const u64* in, u64* out, int iters) {
+    u64 a = in[threadIdx.x & 31], b = in[(threadIdx.x + 7) & 31];
+    u64 acc[8][4] = {};
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const u64 bb = b + g;
+            if (V == 0) mac128(acc[g][0], acc[g][1], a, bb);
+            else mac30(acc[g], (u32)a & 0x3fffffffu, (u32)(a >> 30), (u32)bb & 0x3fffffffu,
+                       (u32)(bb >> 30));
+        }
+        a += 3;
+    }
+    u64 r = 0;
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 4; ++j) r ^= acc[i][j];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+__global__ void k_bf(const u64* in, u64* out, int iters, u64 q) {
+    u64 x[8];
+    for (int i = 0; i < 8; ++i) x[i] = in[(threadIdx.x + i) & 31];
+    u64 w = in[5], wp = in[6];
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) bf(x[i], x[i + 4], w, wp, q);
+#pragma unroll
+        for (int i = 0; i < 8; i += 4) {
+            bf(x[i], x[i + 2], w, wp, q);
+            bf(x[i + 1], x[i + 3], w, wp, q);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) bf(x[i], x[i + 1], w, wp, q);
+        w += 1;
+    }
+    u64 r = 0;
+    for (int i = 0; i < 8; ++i) r ^= x[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+int main() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    u64 *in, *out;
+    cudaMalloc(&in, 32 * sizeof(u64));
+    cudaMalloc(&out, (size_t)blocks * threads * sizeof(u64));
+    const u64 q = 0x0fffffffffc0001ull;
+    u64 h[32];
+    for (int i = 0; i < 32; ++i) h[i] = (q - 977ull * i) % q;
+    h[6] = (u64)(((unsigned __int128)h[5] << 64) / q);
+    cudaMemcpy(in, h, sizeof(h), cudaMemcpyHostToDevice);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const double work = (double)blocks * threads * iters;
+    float ms = 0;
+    for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0);
+        k_mac<1><<<blocks, threads>>>(in, out, iters);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    printf("{\"mac30_per_s\": %.4e, ", work * 8 / (ms * 1e-3));
+    for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0);
+        k_mac<0><<<blocks, threads>>>(in, out, iters);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    printf("\"mac128_per_s\": %.4e, ", work * 8 / (ms * 1e-3));
+    for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0);
+        k_bf<<<blocks, threads>>>(in, out, iters, q);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    printf("\"butterfly_per_s\": %.4e, \"sms\": %d, \"status\": \"%s\"}\n", work * 12 / (ms * 1e-3),
+           sms, cudaGetErrorString(cudaGetLastError()));
+    return 0;
+}
