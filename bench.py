@@ -425,6 +425,36 @@ def run_served(args, mix) -> list:
 
 # ------------------------------------------------------------------ GPU arm --
 
+# One 60-bit modular multiply-accumulate of the diagonal MAC is four
+# 32x32->64-bit multiply-adds (IMAD.WIDE).  Peak: 152 SMs x 2070 MHz x 32
+# IMAD.WIDE per clock per SM (a 64-bit-result multiply-add issues at half the
+# 32-bit rate of 64 per clock) / 4.  A register-only loop of the same
+# instructions (microbench/ceilings.cu) measured 2.02e12 per second on GB300.
+MAC_PEAK_PER_S = 152 * 2070e6 * 32 / 4
+MAC_CEILING_MEASURED = 2.02e12
+# DRAM bytes of one k_diag_mac launch from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the same plan with 3 primes (L=2, K=1), scaled by
+# 10/3 to the 10 primes of Q u P (every CTA works on one prime);
+# None when the kernel has changed since the capture.
+MAC_TRAFFIC_BYTES = None
+
+
+def mac_roofline(ctx, plan, ms):
+    E, N = ctx.E, ctx.N
+    macs = plan.H * plan.B * plan.giants * 2 * E * N
+    # algorithmic bytes: every rotated operand, diagonal and accumulator once
+    algo_bytes = 8 * N * E * (plan.H * plan.B * 2 + plan.hclass * plan.giants * plan.B
+                              + plan.G * plan.giants * 2)
+    achieved = macs / (ms / 1e3)
+    return {"kernel": "k_diag_mac", "bound": "alu", "achieved": achieved / 1e12,
+            "peak": MAC_PEAK_PER_S / 1e12, "unit": "T modmac/s", "frac": achieved / MAC_PEAK_PER_S,
+            "frac_of_measured_ceiling": achieved / MAC_CEILING_MEASURED,
+            "traffic": MAC_TRAFFIC_BYTES, "algorithmic_bytes": algo_bytes,
+            "macs_per_launch": macs, "ms_per_launch": ms,
+            "timing": "CUDA events recorded on the launching stream around each launch",
+            "peak_source": "derived: 152 SMs x 2070 MHz x 32 IMAD.WIDE/clk/SM / 4 per modmac"}
+
+
 def run_gpu(args, cfg, rank: int, world: int):
     import numpy as np
     import torch
@@ -514,23 +544,12 @@ def run_gpu(args, cfg, rank: int, world: int):
             dist.destroy_process_group()
         return
 
-    # roofline of the diagonal multiply-accumulate kernel (one launch per query)
+    # roofline of the diagonal multiply-accumulate kernel (one launch per query):
+    # it is bound by the integer multiply-add pipe, so achieved and peak are
+    # 60-bit modular multiply-accumulates per second
     mac_ms, mac_calls = stages["mac"]
     mac_ms_per = mac_ms / max(1, mac_calls)
-    L, E = ctx.L, ctx.E
-    mac_bytes = 8 * N * L * (plan.H * plan.B * 2 + plan.hclass * plan.giants * plan.B
-                             + plan.G * plan.giants * 2)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = mac_bytes / (mac_ms_per / 1000.0) / 1e9
-    roofline = {"kernel": "k_diag_mac", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                "bytes_per_launch": mac_bytes, "ms_per_launch": mac_ms_per,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s"}
+    roofline = mac_roofline(ctx, plan, mac_ms_per)
     ms_sorted = sorted(per)
     p50 = statistics.median(per)
     p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]

@@ -334,11 +334,12 @@ int pdq_rotate_noalloc(const pdq_ctx* ctx, const uint64_t* ct_in, uint32_t count
 #define PDQ_STAGE_MASK 0
 #define PDQ_STAGE_PACK 1
 #define PDQ_STAGE_BABY 2
-#define PDQ_STAGE_MAC 3
+#define PDQ_STAGE_MAC 3           /* the diagonal multiply-accumulate kernel alone */
 #define PDQ_STAGE_GIANT 4
 #define PDQ_STAGE_ROTSUM 5
 #define PDQ_STAGE_COMBINE 6
-#define PDQ_NSTAGES 7
+#define PDQ_STAGE_ACC_MODDOWN 7   /* ModDown of the multiply-accumulate outputs */
+#define PDQ_NSTAGES 8
 unsigned long long pdq_launch_count(void);
 int pdq_profile_enable(pdq_ctx* ctx, int enable);
 int pdq_profile_read(pdq_ctx* ctx, float* ms, uint32_t* calls, uint32_t nstages);

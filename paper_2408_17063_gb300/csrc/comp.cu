@@ -163,6 +163,7 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     // 3. diagonal multiply-accumulate over Q u P, one ModDown per accumulator
     prof_mark(c, PDQ_STAGE_MAC, st);
     PDQ_TRY(diag_mac(c, pl, Rx, Dg, accx, st));
+    prof_mark(c, PDQ_STAGE_ACC_MODDOWN, st);
     PDQ_TRY(mod_down_batch(c, accx, G * GI, ct_set(acc, cts), aws, st));
     // 4. giant steps: sum over Q u P, one ModDown per group
     prof_mark(c, PDQ_STAGE_GIANT, st);

@@ -69,12 +69,14 @@ __global__ void k_lift(u64* __restrict__ out, u32 logN, u32 nlimbs, const Mod* _
 
 // Diagonal slot values D_{h,gB+a} rotated by -gB (both rows), scattered to
 // transform positions; one plaintext (cls, g, a) per grid row.
+// (plaintext pt = pt_base + y pt_stride goes to row y)
 __global__ void k_diag_slots(u64* __restrict__ out, u32 giants, u32 B, u32 s_prime, u32 logN,
-                             u32 L, const u32* __restrict__ pos, u64 t) {
+                             u32 L, const u32* __restrict__ pos, u64 t, u32 pt_base,
+                             u32 pt_stride) {
     const u32 idx = blockIdx.x * blockDim.x + threadIdx.x;
     const u32 N = 1u << logN, m = N / 2;
     if (idx >= N) return;
-    const u32 pt = blockIdx.y;
+    const u32 pt = pt_base + blockIdx.y * pt_stride;
     const u32 a = pt % B;
     const u32 g = (pt / B) % giants;
     const u32 cls = pt / (B * giants);
@@ -89,7 +91,7 @@ __global__ void k_diag_slots(u64* __restrict__ out, u32 giants, u32 B, u32 s_pri
         b = b * b % t;
         e >>= 1;
     }
-    out[(((u64)pt * L) << logN) + pos[idx]] = r;
+    out[(((u64)blockIdx.y * L) << logN) + pos[idx]] = r;
 }
 
 // database plaintexts: row pt = 2j + half holds DB_j.[1;0] (half 0) or DB_j.[0;1]
@@ -255,36 +257,70 @@ __global__ void k_mask(const u64* __restrict__ v, const u64* __restrict__ db,
 // Raise digit b = blockIdx.y of c1 (coefficient form X [cnt][L][N]) of
 // ciphertext blockIdx.z to the extended basis: D[ct][b][r] for r outside
 // the digit (coefficient form, transformed afterwards); inside the digit
-// the NTT-form c1 limb is copied.
-__global__ void k_modup(const u64* __restrict__ X, CtSet c1ntt, u32 logN, u32 L, u32 E,
-                        u32 alpha, const Mod* __restrict__ mods, const u64* __restrict__ hinv,
-                        const u64* __restrict__ hinvs, const u64* __restrict__ hmod,
-                        const u64* __restrict__ hmods, u64* __restrict__ D) {
-    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= (1u << logN)) return;
+// the NTT-form c1 limb is copied.  Two adjacent positions per thread
+// (16-byte accesses); the digit's conversion constants (Q_b/q_i) mod r and
+// the target moduli are staged in shared memory.  ALPHA: primes per digit
+// (0: read from `alpha` at run time, at most 8).
+template <int ALPHA>
+__global__ void __launch_bounds__(256) k_modup(const u64* __restrict__ X, CtSet c1ntt, u32 logN,
+                                               u32 L, u32 E, u32 alpha,
+                                               const Mod* __restrict__ mods,
+                                               const u64* __restrict__ hinv,
+                                               const u64* __restrict__ hinvs,
+                                               const u64* __restrict__ hmod,
+                                               const u64* __restrict__ hmods,
+                                               u64* __restrict__ D) {
+    __shared__ ulonglong2 sh[8 * 32];     // (hmod, Shoup) [l - lo][r]
+    __shared__ ulonglong2 sq[32];         // (q, floor(2^64/q)) of target r
     const u32 b = blockIdx.y, nd = gridDim.y;
-    const u64 ct = blockIdx.z;
     const u32 lo = b * alpha, hi = min(lo + alpha, L);
-    u64 y[8];
-    const u64* Xc = X + ((ct * L) << logN);
-    for (u32 l = lo; l < hi; ++l) {
-        const u64 q = mods[l].q;
-        y[l - lo] = csub(mul_shoup_lazy(Xc[((u64)l << logN) + x], hinv[l], hinvs[l], q), q);
+    const u32 na = hi - lo;
+    for (u32 i = threadIdx.x; i < na * E; i += blockDim.x) {
+        const u32 l = lo + i / E, r = i - (i / E) * E;
+        sh[(l - lo) * 32 + r] = make_ulonglong2(hmod[(u64)l * E + r], hmods[(u64)l * E + r]);
     }
-    u64* Dc = D + (((ct * nd + b) * E) << logN);
-    const u64* src = c1ntt.at(ct) + ((u64)L << logN);    // c1 of the input (NTT form)
+    for (u32 r = threadIdx.x; r < E; r += blockDim.x) sq[r] = make_ulonglong2(mods[r].q, mods[r].ratio);
+    __syncthreads();
+    const u32 x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= (1u << logN)) return;
+    const u64 ct = blockIdx.z;
+    u64 y0[8], y1[8];
+    const u64* Xc = X + ((ct * L) << logN) + x;
+#pragma unroll
+    for (u32 k = 0; k < (ALPHA ? (u32)ALPHA : 8u); ++k) {
+        if (k < na) {
+            const u32 l = lo + k;
+            const u64 q = sq[l].x;
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(Xc + ((u64)l << logN));
+            y0[k] = csub(mul_shoup_lazy(v.x, hinv[l], hinvs[l], q), q);
+            y1[k] = csub(mul_shoup_lazy(v.y, hinv[l], hinvs[l], q), q);
+        }
+    }
+    u64* Dc = D + (((ct * nd + b) * E) << logN) + x;
+    const u64* src = c1ntt.at(ct) + ((u64)L << logN) + x;   // c1 of the input (NTT form)
     for (u32 r = 0; r < E; ++r) {
+        u64* o = Dc + ((u64)r << logN);
         if (r >= lo && r < hi) {
-            Dc[((u64)r << logN) + x] = src[((u64)r << logN) + x];
+            *reinterpret_cast<ulonglong2*>(o) =
+                *reinterpret_cast<const ulonglong2*>(src + ((u64)r << logN));
             continue;
         }
         // products by the constants (Q_b/q_i) mod r, Shoup: each in [0, 2r),
-        // at most 8 of them, so the sum stays below 2^64
-        const Mod md = mods[r];
-        u64 sum = 0;
-        for (u32 l = lo; l < hi; ++l)
-            sum += mul_shoup_lazy(y[l - lo], hmod[(u64)l * E + r], hmods[(u64)l * E + r], md.q);
-        Dc[((u64)r << logN) + x] = reduce64(sum, md);
+        // at most 8 of them, so the sums stay below 2^64
+        const ulonglong2 m = sq[r];
+        u64 s0 = 0, s1 = 0;
+#pragma unroll
+        for (u32 k = 0; k < (ALPHA ? (u32)ALPHA : 8u); ++k) {
+            if (k < na) {
+                const ulonglong2 h = sh[k * 32 + r];
+                s0 += mul_shoup_lazy(y0[k], h.x, h.y, m.x);
+                s1 += mul_shoup_lazy(y1[k], h.x, h.y, m.x);
+            }
+        }
+        Mod md;
+        md.q = m.x;
+        md.ratio = m.y;
+        *reinterpret_cast<ulonglong2*>(o) = make_ulonglong2(reduce64(s0, md), reduce64(s1, md));
     }
 }
 
@@ -470,36 +506,64 @@ __global__ void k_times_P(CtSet in, u32 logN, u32 L, u32 E, const Mod* __restric
 
 // Conv[cp][i] = sum_k [y_k (P/p_k)^-1]_{p_k} (P/p_k) mod q_i from the special
 // limbs of A (coefficient form); cp = blockIdx.y = ct*2 + p
-__global__ void k_moddown_conv(const u64* __restrict__ A, u32 logN, u32 L, u32 K,
-                               const Mod* __restrict__ mods, const u64* __restrict__ hinv,
-                               const u64* __restrict__ hinvs, const u64* __restrict__ hmod,
-                               const u64* __restrict__ hmods, u64* __restrict__ Cv) {
-    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= (1u << logN)) return;
+template <int KK>
+__global__ void __launch_bounds__(256) k_moddown_conv(const u64* __restrict__ A, u32 logN, u32 L,
+                                                      u32 K, const Mod* __restrict__ mods,
+                                                      const u64* __restrict__ hinv,
+                                                      const u64* __restrict__ hinvs,
+                                                      const u64* __restrict__ hmod,
+                                                      const u64* __restrict__ hmods,
+                                                      u64* __restrict__ Cv) {
+    // KK: special primes (0: K at run time, at most 8); two positions per
+    // thread; constants (P/p_k) mod q_l and the moduli staged in shared memory
+    __shared__ ulonglong2 sh[8 * 32];
+    __shared__ ulonglong2 sq[40];
     const u32 E = L + K;
+    for (u32 i = threadIdx.x; i < K * L; i += blockDim.x)
+        sh[(i / L) * 32 + (i % L)] = make_ulonglong2(hmod[i], hmods[i]);
+    for (u32 r = threadIdx.x; r < E; r += blockDim.x) sq[r] = make_ulonglong2(mods[r].q, mods[r].ratio);
+    __syncthreads();
+    const u32 x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= (1u << logN)) return;
     const u64 cp = blockIdx.y;
-    const u64* a = A + ((cp * E) << logN);
-    u64 y[8];
-    for (u32 k = 0; k < K; ++k) {
-        const u64 pk = mods[L + k].q;
-        y[k] = csub(mul_shoup_lazy(a[((u64)(L + k) << logN) + x], hinv[k], hinvs[k], pk), pk);
+    const u64* a = A + ((cp * E) << logN) + x;
+    u64 y0[8], y1[8];
+#pragma unroll
+    for (u32 k = 0; k < (KK ? (u32)KK : 8u); ++k) {
+        if (k < K) {
+            const u64 pk = sq[L + k].x;
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(a + ((u64)(L + k) << logN));
+            y0[k] = csub(mul_shoup_lazy(v.x, hinv[k], hinvs[k], pk), pk);
+            y1[k] = csub(mul_shoup_lazy(v.y, hinv[k], hinvs[k], pk), pk);
+        }
     }
-    u64* o = Cv + ((cp * L) << logN);
+    u64* o = Cv + ((cp * L) << logN) + x;
     for (u32 l = 0; l < L; ++l) {
-        const Mod md = mods[l];
-        u64 sum = 0;
-        for (u32 k = 0; k < K; ++k)
-            sum += mul_shoup_lazy(y[k], hmod[(u64)k * L + l], hmods[(u64)k * L + l], md.q);
-        o[((u64)l << logN) + x] = reduce64(sum, md);
+        const ulonglong2 m = sq[l];
+        u64 s0 = 0, s1 = 0;
+#pragma unroll
+        for (u32 k = 0; k < (KK ? (u32)KK : 8u); ++k) {
+            if (k < K) {
+                const ulonglong2 h = sh[k * 32 + l];
+                s0 += mul_shoup_lazy(y0[k], h.x, h.y, m.x);
+                s1 += mul_shoup_lazy(y1[k], h.x, h.y, m.x);
+            }
+        }
+        Mod md;
+        md.q = m.x;
+        md.ratio = m.y;
+        *reinterpret_cast<ulonglong2*>(o + ((u64)l << logN)) =
+            make_ulonglong2(reduce64(s0, md), reduce64(s1, md));
     }
 }
 
-// out = (A - Conv) * P^-1 (+ sigma(c0) for p = 0) (+ addend), NTT form
 __global__ void k_moddown_final(const u64* __restrict__ A, const u64* __restrict__ Cv,
                                 CtSet in, CtSet out, CtSet add, u32 logN, u32 L, u32 K,
                                 u32 galois, const Mod* __restrict__ mods,
                                 const u64* __restrict__ pinv, const u64* __restrict__ pinvs) {
-    const u32 rr = blockIdx.x * blockDim.x + threadIdx.x;
+    // two adjacent positions per thread; sigma maps the aligned pair {x, x+1}
+    // onto an aligned pair, possibly swapped
+    const u32 rr = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const u32 LN = L << logN;
     if (rr >= 2 * LN) return;
     const u64 ct = blockIdx.y;
@@ -508,40 +572,60 @@ __global__ void k_moddown_final(const u64* __restrict__ A, const u64* __restrict
     const u32 r = rr - p * LN;
     const u32 l = r >> logN, x = r & ((1u << logN) - 1);
     const u64 q = mods[l].q;
-    const u64 a = A[(((ct * 2 + p) * E) << logN) + r];
-    const u64 cv = Cv[(ct * 2 + p) * LN + r];
-    u64 v = csub(mul_shoup_lazy(submod(a, cv, q), pinv[l], pinvs[l], q), q);
-    if (p == 0 && in.base) v = addmod(v, in.at(ct)[((u64)l << logN) + auto_index(x, galois, logN)], q);
-    if (add.base) v = addmod(v, add.at(ct)[rr], q);
-    out.at(ct)[rr] = v;
+    const u64 pv = pinv[l], pvs = pinvs[l];
+    const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(A + (((ct * 2 + p) * E) << logN) + r);
+    const ulonglong2 cv = *reinterpret_cast<const ulonglong2*>(Cv + (ct * 2 + p) * LN + r);
+    u64 v0 = csub(mul_shoup_lazy(submod(a.x, cv.x, q), pv, pvs, q), q);
+    u64 v1 = csub(mul_shoup_lazy(submod(a.y, cv.y, q), pv, pvs, q), q);
+    if (p == 0 && in.base) {
+        const u32 sx = auto_index(x, galois, logN);
+        const ulonglong2 iv =
+            *reinterpret_cast<const ulonglong2*>(in.at(ct) + ((u64)l << logN) + (sx & ~1u));
+        const bool swap = (sx & 1) != 0;
+        v0 = addmod(v0, swap ? iv.y : iv.x, q);
+        v1 = addmod(v1, swap ? iv.x : iv.y, q);
+    }
+    if (add.base) {
+        const ulonglong2 dv = *reinterpret_cast<const ulonglong2*>(add.at(ct) + rr);
+        v0 = addmod(v0, dv.x, q);
+        v1 = addmod(v1, dv.y, q);
+    }
+    *reinterpret_cast<ulonglong2*>(out.at(ct) + rr) = make_ulonglong2(v0, v1);
 }
 
 // ----------------------------------------------------------- Comp kernels --
 
 // Diagonal multiply-accumulate (the Pegasus inner sum):
-//   acc[gamma][g][p][l][x] = sum_{hh} sum_{a<B} Dg[hh][g][a][l][x] * R[gamma hpg + hh][a][p][l][x]
+//   acc[gamma][g][p][l][x] = sum_{hh} sum_{a<B} Dg[hh][a][l][x][g] * R[gamma hpg + hh][a][p][l][x]
 //
 // Arithmetic: residues are < 2^60, split into 30-bit halves v = v0 + v1 2^30
-// (both operands arrive stored as v0 | v1 << 32, see split30);
-// a product then is four 32x32->64-bit multiply-adds into four 64-bit partial
-// sums (S0 = sum a0 b0, S1a = sum a0 b1, S1b = sum a1 b0, S2 = sum a1 b1), each
-// term < 2^60; every 14 terms the sums are renormalised (renorm30) and at
-// the end folded to one residue S0 + (S1a + S1b) 2^30 + S2 2^60 mod q.
+// (both operands arrive stored as v0 | v1 << 32, see split30).  A product is
+// four 32x32->64-bit multiply-adds into four 64-bit partial sums
+//   S0 = sum a0 b0,  S1a = sum a0 b1,  S1b = sum a1 b0,  S2 = sum a1 b1
+// (every product <= (2^30 - 1)^2), plus a carry word S3 of weight 2^90.
+// After every a-chunk of at most 16 terms the sums are renormalised (renorm5,
+// shifts and masks only):
+// afterwards S0, S1a, S1b < 2^30 and S2 < 2^31, so 16 more products fit into
+// each (2^31 + 16 (2^30 - 1)^2 < 2^64).  At the end of a position tile the
+// sums are folded to S0 + (S1a + S1b) 2^30 + S2 2^60 + S3 2^90 mod q.
 //
-// Work split: one CTA owns limb l = blockIdx.y and X consecutive positions;
-// thread (xi, gs, ct) handles position x0 + xi, giant indices gs*GT ..
-// gs*GT+GT-1 and the combinations (gamma, p) = 2ct, 2ct+1 of its z-slice.
-// Per step (hh, a-chunk) the CTA stages the diagonal tile
-// Dg[hh][:][a0:a0+Bc][l][x0:x0+X] and the rotated-ciphertext tile
-// R[gamma hpg + hh][a0:a0+Bc][p][l][x0:x0+X] of all its combinations in
-// shared memory with asynchronous 16-byte copies, double-buffered so that
-// the next step's copies overlap this step's arithmetic; each diagonal value
-// leaves DRAM once per z-slice and each rotated value once.
-struct Acc30 {
-    u64 s0, s1a, s1b, s2;
+// Work split: one CTA owns limb l = blockIdx.y, X consecutive positions and
+// the (gamma, p) combinations of its z-slice; thread (gs, xi, ct) handles
+// position x0 + xi, giant indices gs*GT .. gs*GT+GT-1 and the two
+// polynomials p = 0, 1 of group gamma = (cbase + 2ct) / 2.  Per step
+// (hh, a-chunk of BC) the CTA stages the diagonal tile
+// Dg[hh][a0:a0+BC][l][x0:x0+X][:] (giant index innermost, rows padded by two
+// words so that the 16-byte loads of a quarter warp hit distinct banks) and
+// the rotated-ciphertext tile R[gamma hpg + hh][a0:a0+BC][p][l][x0:x0+X] of
+// its combinations (stored [combination][a][x]) in shared memory with
+// asynchronous 16-byte copies, double-buffered so that the next step's copies
+// overlap this step's arithmetic; each diagonal value leaves DRAM once per
+// z-slice and each rotated value once.
+struct Acc5 {
+    u64 s0, s1a, s1b, s2, s3;
 };
 
-__device__ __forceinline__ void mac30(Acc30& A, u32 a0, u32 a1, u32 b0, u32 b1) {
+__device__ __forceinline__ void mac4(Acc5& A, u32 a0, u32 a1, u32 b0, u32 b1) {
     asm("mad.wide.u32 %0, %4, %6, %0;\n\t"
         "mad.wide.u32 %1, %4, %7, %1;\n\t"
         "mad.wide.u32 %2, %5, %6, %2;\n\t"
@@ -550,31 +634,28 @@ __device__ __forceinline__ void mac30(Acc30& A, u32 a0, u32 a1, u32 b0, u32 b1) 
         : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
 }
 
-struct Fold30 {
-    Mod md;
-    u64 c30, c30s, c60, c60s;   // 2^30 and 2^60 mod q with Shoup companions
-};
-
-__device__ __forceinline__ u64 fold30(const Acc30& A, const Fold30& f) {
-    const u64 q = f.md.q;
-    u64 v = A.s0 - mulhi64(A.s0, f.md.ratio) * q;                  // [0, 2q)
-    v += mul_shoup_lazy(A.s1a, f.c30, f.c30s, q);                   // [0, 4q)
-    v += mul_shoup_lazy(A.s1b, f.c30, f.c30s, q);                   // [0, 6q)
-    v += mul_shoup_lazy(A.s2, f.c60, f.c60s, q);                    // [0, 8q) < 2^63
-    return reduce64(v, f.md);
+// Keeps S0 + (S1a + S1b) 2^30 + S2 2^60 + S3 2^90 unchanged.  Before it every
+// sum is < 2^31 + 16 (2^30 - 1)^2 < 2^64 - 2^34; the carries into S1a (< 2^34)
+// and into the 2^60 position (c < 2^35) are split so that S2 ends below 2^31.
+__device__ __forceinline__ void renorm5(Acc5& A) {
+    constexpr u64 M = 0x3fffffffull;
+    A.s1a += A.s0 >> 30;
+    A.s0 &= M;
+    const u64 c = (A.s1a >> 30) + (A.s1b >> 30);
+    A.s1a &= M;
+    A.s1b &= M;
+    A.s3 += (A.s2 >> 30) + (c >> 30);
+    A.s2 = (A.s2 & M) + (c & M);
 }
 
-// Keep the value S0 + (S1a + S1b) 2^30 + S2 2^60 (mod q) while shrinking the
-// sums: carry the bits above 30 of S0 into S1a and of S1a, S1b into S2, then
-// reduce S2 mod q.  Afterwards S0, S1a, S1b < 2^30 and S2 < q < 2^60, so 14
-// more products of 30-bit halves fit into every sum.
-__device__ __forceinline__ void renorm30(Acc30& A, const Mod& md) {
-    A.s1a += A.s0 >> 30;
-    A.s0 &= 0x3fffffffull;
-    const u64 c = (A.s1a >> 30) + (A.s1b >> 30);
-    A.s1a &= 0x3fffffffull;
-    A.s1b &= 0x3fffffffull;
-    A.s2 = reduce64(A.s2 + c, md);
+// Value of a renormalised accumulator mod q: S0 + (S1a + S1b) 2^30 < 2^62
+// exactly, S2 2^60 and S3 2^90 by Shoup multiplications.
+__device__ __forceinline__ u64 fold5(const Acc5& A, const Mod& md, const u64* __restrict__ cl) {
+    const u64 q = md.q;
+    u64 v = A.s0 + ((A.s1a + A.s1b) << 30);                         // < 2^62
+    v += mul_shoup_lazy(A.s2, cl[0], cl[1], q);                     // + [0, 2q)
+    v += mul_shoup_lazy(A.s3, cl[2], cl[3], q);                     // + [0, 2q) < 2^63
+    return reduce64(v, md);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
@@ -582,146 +663,171 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
                  "r"(valid ? 16 : 0));
 }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const u32 s = (u32)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-template <int GT>
+struct MacArgs {
+    u32 G, hpg, H, B, GI, E, logN;
+    u32 logX, logGS, logGI, CPC;   // CPC: combinations per CTA (even)
+    u32 tiles_per_cta, achunks;
+};
+
+template <int GT, int BC>
 __global__ void __launch_bounds__(512) k_diag_mac(const u64* __restrict__ R,
-                                                  const u64* __restrict__ Dg, u32 G, u32 hpg,
-                                                  u32 H, u32 B, u32 Bc, u32 GI, u32 L, u32 logN,
-                                                  u32 logX, u32 logGS, u32 combos_per_cta,
-                                                  u32 tiles_per_cta, u32 logGI, u32 logBc,
+                                                  const u64* __restrict__ Dg, MacArgs a,
                                                   const Mod* __restrict__ mods,
-                                                  const u64* __restrict__ c30tab,
+                                                  const u64* __restrict__ c6090,
                                                   u64* __restrict__ acc) {
     extern __shared__ __align__(16) u64 smem[];
-    const u32 X = 1u << logX;
+    const u32 X = 1u << a.logX, GI = a.GI, GIp = GI + 2, CPC = a.CPC;
     const u32 l = blockIdx.y;
-    const u32 xi = threadIdx.x & (X - 1);
-    const u32 gs = (threadIdx.x >> logX) & ((1u << logGS) - 1);
-    const u32 ct = threadIdx.x >> (logX + logGS);
-    const u32 cbase = blockIdx.z * combos_per_cta;      // first combination of the z-slice
-    const u64 LN = (u64)L << logN;
-    const u32 hpg_eff = min(hpg, H);
+    const u32 gs = threadIdx.x & ((1u << a.logGS) - 1);
+    const u32 xi = (threadIdx.x >> a.logGS) & (X - 1);
+    const u32 ct = threadIdx.x >> (a.logGS + a.logX);
+    const u32 cbase = blockIdx.z * CPC;
+    const u64 N = 1ull << a.logN;
+    const u64 LN = (u64)a.E << a.logN;
+    const u32 hpg_eff = min(a.hpg, a.H);
     const u32 g0 = gs * GT;
 
-    Fold30 f;
-    f.md = mods[l];
-    f.c30 = c30tab[4 * l + 0];
-    f.c30s = c30tab[4 * l + 1];
-    f.c60 = c30tab[4 * l + 2];
-    f.c60s = c30tab[4 * l + 3];
+    const u32 dwords = BC * X * GIp, rwords = BC * CPC * X;
+    const u32 stage = dwords + rwords;
 
-    // Tiles in shared memory, rows of X positions padded to Xp = X + 2 words
-    // (16-byte aligned rows, and the giant-index groups of a warp land in
-    // different bank halves): diagonals as [a][g][x], rotated operands as
-    // [combination][a][x].
-    const u32 Xp = X + 2;
-    const u32 drows = GI * Bc, rrows = combos_per_cta * Bc;
-    const u32 dtile = drows * Xp, rtile = rrows * Xp;
-    u64* Dsm[2] = {smem, smem + dtile + rtile};
-    u64* Rsm[2] = {smem + dtile, smem + 2 * dtile + rtile};
+    const u32 gam = (cbase >> 1) + ct;             // group of this thread's two combinations
+    const bool ok = 2 * ct < CPC && gam < a.G;
 
-    const u32 c0 = 2 * ct, c1 = 2 * ct + 1;        // combinations of this thread (in slice)
-    const u32 gam0 = (cbase + c0) >> 1, gam1 = (cbase + c1) >> 1;
-    const bool ok0 = gam0 < G, ok1 = gam1 < G;
+    const u32 spt = hpg_eff * a.achunks;           // steps per position tile
+    const u32 steps = spt * a.tiles_per_cta;
+    const u32 tile0 = blockIdx.x * a.tiles_per_cta;
 
-    const u32 achunks = B >> logBc;
-    const u32 spt = hpg_eff * achunks;             // steps per position tile
-    const u32 steps = spt * tiles_per_cta;
-    const u32 tile0 = blockIdx.x * tiles_per_cta;
-    const u32 pairs_per_row = X >> 1;
-
-    // copies of global step `st` (tile st / spt, step st % spt) into buffer `buf`
-    auto issue = [&](u32 st, u32 buf) {
-        const u32 tt = st / spt, sst = st - tt * spt;
-        const u32 hh = sst / achunks, a0 = (sst - hh * achunks) << logBc;
-        const u64 lx0 = ((u64)l << logN) + ((u64)(tile0 + tt) << logX);
-        u64* D = Dsm[buf];
-        for (u32 e = threadIdx.x; e < drows * pairs_per_row; e += blockDim.x) {
-            const u32 row = e >> (logX - 1), xx = (e & (pairs_per_row - 1)) * 2;
-            const u32 ai = row >> logGI, g = row & (GI - 1);
-            cp_async16(D + row * Xp + xx,
-                       Dg + ((u64)(hh * GI + g) * B + a0 + ai) * LN + lx0 + xx, true);
+    // copies of step (tt, hh, ac) into stage buffer `buf`
+    auto issue = [&](u32 tt, u32 hh, u32 ac, u32 buf) {
+        const u32 a0 = ac * BC;
+        const u64 x0 = (u64)(tile0 + tt) << a.logX;
+        u64* D = smem + buf * stage;
+        const u64* dsrc = Dg + (((u64)hh * a.B + a0) * a.E + l) * N * GI + x0 * GI;
+        if (GI >= 2) {
+            const u32 halfGI = GI >> 1;
+            for (u32 e = threadIdx.x; e < BC * X * halfGI; e += blockDim.x) {
+                const u32 gp = e & (halfGI - 1);
+                const u32 x = (e >> (a.logGI - 1)) & (X - 1);
+                const u32 ai = e >> (a.logGI - 1 + a.logX);
+                cp_async16(D + (ai * X + x) * GIp + 2 * gp,
+                           dsrc + (u64)ai * LN * GI + (u64)x * GI + 2 * gp, true);
+            }
+        } else {
+            for (u32 e = threadIdx.x; e < BC * X; e += blockDim.x) {
+                const u32 x = e & (X - 1), ai = e >> a.logX;
+                cp_async8(D + (ai * X + x) * GIp, dsrc + (u64)ai * LN + x);
+            }
         }
-        u64* Rt = Rsm[buf];
-        for (u32 e = threadIdx.x; e < rrows * pairs_per_row; e += blockDim.x) {
-            const u32 row = e >> (logX - 1), xx = (e & (pairs_per_row - 1)) * 2;
-            const u32 cb = row >> logBc, ai = row & (Bc - 1);
+        u64* Rt = D + dwords;
+        const u32 halfX = X >> 1;
+        for (u32 e = threadIdx.x; e < BC * CPC * halfX; e += blockDim.x) {
+            const u32 xp = e & (halfX - 1);
+            const u32 row = e >> (a.logX - 1);     // cb * BC + ai
+            const u32 cb = row / BC, ai = row & (BC - 1);
             const u32 combo = cbase + cb;
-            const u32 gam = combo >> 1, p = combo & 1;
-            const u32 h = gam * hpg + hh;
-            const bool valid = gam < G && h < H;
-            const u64* src = R + (((u64)(valid ? h : 0) * B + a0 + ai) * 2 + p) * LN + lx0 + xx;
-            cp_async16(Rt + row * Xp + xx, src, valid);
+            const u32 gm = combo >> 1, p = combo & 1;
+            const u32 h = gm * a.hpg + hh;
+            const bool valid = gm < a.G && h < a.H;
+            const u64* src = R + ((((u64)(valid ? h : 0) * a.B + a0 + ai) * 2 + p) * a.E + l) * N +
+                             x0 + 2 * xp;
+            cp_async16(Rt + row * X + 2 * xp, src, valid);
         }
         cp_async_commit();
     };
 
-    Acc30 A0[GT], A1[GT];
+    Acc5 A[2][GT];
 #pragma unroll
-    for (int g = 0; g < GT; ++g) { A0[g] = Acc30{0, 0, 0, 0}; A1[g] = Acc30{0, 0, 0, 0}; }
-    u32 terms = 0;
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int g = 0; g < GT; ++g) A[p][g] = Acc5{0, 0, 0, 0, 0};
 
-    issue(0, 0);
+    u32 itt = 0, ihh = 0, iac = 0;                 // next step to issue
+    auto advance = [&](u32& tt, u32& hh, u32& ac) {
+        if (++ac == a.achunks) {
+            ac = 0;
+            if (++hh == hpg_eff) { hh = 0; ++tt; }
+        }
+    };
+    u32 chh = 0, cac = 0, ctt = 0;                 // step being computed
+    issue(itt, ihh, iac, 0);
+    advance(itt, ihh, iac);
     for (u32 st = 0; st < steps; ++st) {
         const u32 buf = st & 1;
         if (st + 1 < steps) {
-            issue(st + 1, buf ^ 1);
+            issue(itt, ihh, iac, buf ^ 1);
+            advance(itt, ihh, iac);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
         __syncthreads();
-        const u64* D = Dsm[buf] + g0 * Xp + xi;
-        const u64* Rt0 = Rsm[buf] + c0 * Bc * Xp + xi;
-        const u64* Rt1 = Rsm[buf] + c1 * Bc * Xp + xi;
-        for (u32 ai = 0; ai < Bc; ++ai) {
-            if (terms == 14) {
+        const u64* D = smem + buf * stage + xi * GIp + g0;
+        const u64* Rt = smem + buf * stage + dwords + (2 * ct) * BC * X + xi;
 #pragma unroll
-                for (int g = 0; g < GT; ++g) {
-                    renorm30(A0[g], f.md);
-                    renorm30(A1[g], f.md);
+        for (int ai = 0; ai < BC; ++ai) {
+            u64 d[GT];
+            if (GT >= 2) {
+#pragma unroll
+                for (int g = 0; g < GT; g += 2) {
+                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(D + ai * X * GIp + g);
+                    d[g] = v.x;
+                    d[g + 1] = v.y;
                 }
-                terms = 0;
+            } else {
+                d[0] = D[ai * X * GIp];
             }
-            ++terms;
-            // operands are stored split: low 30 bits | high 30 bits << 32
-            const u64 r0 = Rt0[ai * Xp], r1 = Rt1[ai * Xp];
+            const u64 r0 = Rt[ai * X], r1 = Rt[(BC + ai) * X];
             const u32 r00 = (u32)r0, r01 = (u32)(r0 >> 32);
             const u32 r10 = (u32)r1, r11 = (u32)(r1 >> 32);
 #pragma unroll
             for (int g = 0; g < GT; ++g) {
-                const u64 d = D[(ai * GI + g) * Xp];
-                mac30(A0[g], r00, r01, (u32)d, (u32)(d >> 32));
-                mac30(A1[g], r10, r11, (u32)d, (u32)(d >> 32));
+                const u32 d0 = (u32)d[g], d1 = (u32)(d[g] >> 32);
+                mac4(A[0][g], r00, r01, d0, d1);
+                mac4(A[1][g], r10, r11, d0, d1);
             }
         }
-        const u32 tt = st / spt;
-        if (st - tt * spt == spt - 1) {            // last step of this position tile
-            const u64 pos = ((u64)l << logN) + ((u64)(tile0 + tt) << logX) + xi;
-            if (ok0) {
-                u64* o = acc + (((u64)gam0 * GI + g0) * 2 + ((cbase + c0) & 1)) * LN + pos;
+        // at most 16 terms since the last renormalisation (BC <= 16)
 #pragma unroll
-                for (int g = 0; g < GT; ++g) o[(u64)g * 2 * LN] = fold30(A0[g], f);
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int g = 0; g < GT; ++g) renorm5(A[p][g]);
+        const bool tile_end = (cac + 1 == a.achunks) && (chh + 1 == hpg_eff);
+        if (tile_end) {                            // last step of this position tile
+            if (ok) {
+                const Mod md = mods[l];
+                const u64 pos = ((u64)l << a.logN) + ((u64)(tile0 + ctt) << a.logX) + xi;
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    u64* o = acc + (((u64)gam * GI + g0) * 2 + p) * LN + pos;
+#pragma unroll
+                    for (int g = 0; g < GT; ++g)
+                        o[(u64)g * 2 * LN] = fold5(A[p][g], md, c6090 + 4 * l);
+                }
             }
-            if (ok1) {
-                u64* o = acc + (((u64)gam1 * GI + g0) * 2 + ((cbase + c1) & 1)) * LN + pos;
 #pragma unroll
-                for (int g = 0; g < GT; ++g) o[(u64)g * 2 * LN] = fold30(A1[g], f);
-            }
+            for (int p = 0; p < 2; ++p)
 #pragma unroll
-            for (int g = 0; g < GT; ++g) { A0[g] = Acc30{0, 0, 0, 0}; A1[g] = Acc30{0, 0, 0, 0}; }
-            terms = 0;
+                for (int g = 0; g < GT; ++g) A[p][g] = Acc5{0, 0, 0, 0, 0};
         }
+        advance(ctt, chh, cac);
         __syncthreads();                 // buffer `buf` is refilled by the next issue
     }
 }
 
-__global__ void k_split30(u64* __restrict__ data, u64 n) {
+// out[l][x][g] = split30(in[g][l][x]) for the GI diagonals of one (class, a)
+__global__ void k_diag_layout(const u64* __restrict__ in, u64* __restrict__ out, u32 GI,
+                              u64 LN) {
     const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) data[i] = split30(data[i]);
+    if (i >= LN) return;
+    for (u32 g = 0; g < GI; ++g) out[i * GI + g] = split30(in[(u64)g * LN + i]);
 }
 
 // y[ct] += x[ct] (ciphertexts)
@@ -788,17 +894,34 @@ int encode_slots(const Ctx& c, const u32* slots, u32 count, u32 nlimbs, u64* out
 }
 
 int build_diagonals(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st) {
-    // over every prime of Q u P: the products are taken in the extended basis
-    const u32 count = pl.hclass * pl.giants * pl.B, E = c.L + c.K;
-    PDQ_TRY(check_y(count, "diagonals"));
-    k_diag_slots<<<grid2(c.N, count), kBlock, 0, st>>>(out, pl.giants, pl.B, pl.s_prime, c.log_n,
-                                                       E, c.d_slot_pos, c.t);
-    PDQ_TRY(launched("k_diag_slots"));
-    PDQ_TRY(encode_finish(c, out, count, E, st));
-    // stored in the operand layout of the multiply-accumulate
-    const u64 n = (u64)count * E * c.N;
-    k_split30<<<(u32)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(out, n);
-    return launched("k_split30");
+    // over every prime of Q u P: the products are taken in the extended basis.
+    // Plaintext (cls, g, a) is encoded in a temporary, then stored at
+    // out[cls][a][l][x][g] in the operand format of the multiply-accumulate.
+    const u32 GI = pl.giants, B = pl.B, E = c.L + c.K;
+    PDQ_TRY(check_y(GI, "diagonals"));
+    const u64 LN = (u64)E * c.N;
+    u64* tmp = nullptr;
+    if (cudaMallocAsync((void**)&tmp, (size_t)GI * LN * sizeof(u64), st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PDQ_E_NOMEM, "diagonals: temporary allocation failed");
+    }
+    int rc = PDQ_OK;
+    for (u32 cls = 0; cls < pl.hclass && rc == PDQ_OK; ++cls) {
+        for (u32 a = 0; a < B && rc == PDQ_OK; ++a) {
+            k_diag_slots<<<grid2(c.N, GI), kBlock, 0, st>>>(tmp, GI, B, pl.s_prime, c.log_n, E,
+                                                            c.d_slot_pos, c.t, cls * GI * B + a,
+                                                            B);
+            rc = launched("k_diag_slots");
+            if (rc == PDQ_OK) rc = encode_finish(c, tmp, GI, E, st);
+            if (rc == PDQ_OK) {
+                k_diag_layout<<<(u32)((LN + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+                    tmp, out + ((u64)cls * B + a) * GI * LN, GI, LN);
+                rc = launched("k_diag_layout");
+            }
+        }
+    }
+    cudaFreeAsync(tmp, st);
+    return rc;
 }
 
 int build_group_masks(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st) {
@@ -904,6 +1027,25 @@ int mask(const Ctx& c, u32 J, const u64* v, const u64* db, u64* out, cudaStream_
 
 // ---- key switching pieces ---------------------------------------------------
 
+// Cv[cp][l] = sum_k [A[cp][L+k] (P/p_k)^-1]_{p_k} (P/p_k) mod q_l (coefficient form)
+int moddown_conv(const Ctx& c, const u64* A, u32 cps, u64* Cv, cudaStream_t st) {
+    if (c.K > 8 || c.L + c.K > 40 || c.L > 32) return fail(PDQ_E_PARAM, "ModDown: too many primes");
+    PDQ_TRY(check_y(cps, "ModDown"));
+    const dim3 grid((c.N / 2 + kBlock - 1) / kBlock, cps);
+#define PDQ_CONV(KK)                                                                              \
+    k_moddown_conv<KK><<<grid, kBlock, 0, st>>>(A, c.log_n, c.L, c.K, c.d_mods, c.d_dn_hatinv,     \
+                                                c.d_dn_hatinv_shoup, c.d_dn_hatmod,                \
+                                                c.d_dn_hatmod_shoup, Cv)
+    switch (c.K) {
+        case 1: PDQ_CONV(1); break;
+        case 2: PDQ_CONV(2); break;
+        case 3: PDQ_CONV(3); break;
+        default: PDQ_CONV(0); break;
+    }
+#undef PDQ_CONV
+    return launched("k_moddown_conv");
+}
+
 size_t raise_ws(const Ctx& c, u32 cnt) {
     const u64 E = c.L + c.K;
     return (size_t)cnt * ((u64)c.L + (u64)c.ndigits * E) * c.N * sizeof(u64);
@@ -917,9 +1059,20 @@ int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t
     // c1 of every ciphertext -> X, then coefficient form
     PDQ_TRY(gather_rows(in, (long long)(L * N), cnt, L * N, X, L * N, st));
     PDQ_TRY(ntt_inverse(c, X, cnt, c.L, 0, L * N, st));
-    k_modup<<<dim3((c.N + kBlock - 1) / kBlock, (u32)nd, cnt), kBlock, 0, st>>>(
-        X, in, c.log_n, c.L, (u32)E, c.alpha, c.d_mods, c.d_up_hatinv, c.d_up_hatinv_shoup,
-        c.d_up_hatmod, c.d_up_hatmod_shoup, D);
+    if (E > 32 || c.alpha > 8) return fail(PDQ_E_PARAM, "key switch: too many primes per digit");
+    const dim3 grid((c.N / 2 + kBlock - 1) / kBlock, (u32)nd, cnt);
+#define PDQ_MODUP(A)                                                                              \
+    k_modup<A><<<grid, kBlock, 0, st>>>(X, in, c.log_n, c.L, (u32)E, c.alpha, c.d_mods,            \
+                                        c.d_up_hatinv, c.d_up_hatinv_shoup, c.d_up_hatmod,         \
+                                        c.d_up_hatmod_shoup, D)
+    switch (c.alpha) {
+        case 1: PDQ_MODUP(1); break;
+        case 2: PDQ_MODUP(2); break;
+        case 3: PDQ_MODUP(3); break;
+        case 4: PDQ_MODUP(4); break;
+        default: PDQ_MODUP(0); break;
+    }
+#undef PDQ_MODUP
     PDQ_TRY(launched("k_modup"));
     for (u32 b = 0; b < nd; ++b) {
         const u32 lo = c.digit_limbs[b].front(), hi = c.digit_limbs[b].back() + 1;
@@ -946,12 +1099,9 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
                                                          galois, c.d_mods, A);
     PDQ_TRY(launched("k_ks_inner"));
     PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
-    k_moddown_conv<<<grid2(N, 2 * cnt), kBlock, 0, st>>>(A, c.log_n, c.L, c.K, c.d_mods,
-                                                         c.d_dn_hatinv, c.d_dn_hatinv_shoup,
-                                                         c.d_dn_hatmod, c.d_dn_hatmod_shoup, Cv);
-    PDQ_TRY(launched("k_moddown_conv"));
+    PDQ_TRY(moddown_conv(c, A, 2 * cnt, Cv, st));
     PDQ_TRY(ntt_forward(c, Cv, 2 * cnt, c.L, 0, L * N, st));
-    k_moddown_final<<<grid2(2 * L * N, cnt), kBlock, 0, st>>>(A, Cv, in, out, add, c.log_n, c.L,
+    k_moddown_final<<<grid2(L * N, cnt), kBlock, 0, st>>>(A, Cv, in, out, add, c.log_n, c.L,
                                                               c.K, galois, c.d_mods, c.d_dn_pinv,
                                                               c.d_dn_pinv_shoup);
     return launched("k_moddown_final");
@@ -1023,12 +1173,9 @@ int mod_down_batch(const Ctx& c, u64* A, u32 cnt, CtSet out, u64* ws, cudaStream
     PDQ_TRY(check_y(2ull * cnt, "mod_down"));
     u64* Cv = ws;
     PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
-    k_moddown_conv<<<grid2(N, 2 * cnt), kBlock, 0, st>>>(A, c.log_n, c.L, c.K, c.d_mods,
-                                                         c.d_dn_hatinv, c.d_dn_hatinv_shoup,
-                                                         c.d_dn_hatmod, c.d_dn_hatmod_shoup, Cv);
-    PDQ_TRY(launched("k_moddown_conv"));
+    PDQ_TRY(moddown_conv(c, A, 2 * cnt, Cv, st));
     PDQ_TRY(ntt_forward(c, Cv, 2 * cnt, c.L, 0, L * N, st));
-    k_moddown_final<<<grid2(2 * L * N, cnt), kBlock, 0, st>>>(A, Cv, CtSet{}, out, CtSet{}, c.log_n,
+    k_moddown_final<<<grid2(L * N, cnt), kBlock, 0, st>>>(A, Cv, CtSet{}, out, CtSet{}, c.log_n,
                                                               c.L, c.K, 0, c.d_mods, c.d_dn_pinv,
                                                               c.d_dn_pinv_shoup);
     return launched("k_moddown_final");
@@ -1050,8 +1197,8 @@ u32 log2u(u32 x) {
 // Launch shape of k_diag_mac: up to 4 giant indices and both polynomials of
 // one group per thread, up to 16 groups per CTA (more go to further
 // z-slices), X >= 2 positions so that a CTA has up to 512 threads, and an
-// a-chunk Bc that keeps the two staged (diagonal + rotated) tiles within
-// 160 KB of shared memory.
+// a-chunk BC (up to 16) that keeps the two staged (diagonal + rotated) tiles
+// within 160 KB of shared memory.
 MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     MacShape s{};
     const u32 GI = pl.giants, combos = 2 * pl.G;
@@ -1059,7 +1206,7 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     const u32 GS = GI / s.GT;
     s.logGS = log2u(GS);
     u32 ct = combos / 2;
-    u32 ct_max = 512 / (GS * 2);
+    u32 ct_max = 256 / GS;
     if (ct_max > 16) ct_max = 16;
     if (ct > ct_max) ct = 1u << log2u(ct_max);
     s.combos_per_cta = ct * 2;
@@ -1067,9 +1214,9 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     u32 logX = 1;
     while (((ct * GS) << (logX + 1)) <= 512 && logX < 8) ++logX;
     if (logX > logN) logX = logN;
-    u32 Bc = pl.B;
+    u32 Bc = pl.B < 16 ? pl.B : 16;
     auto bytes = [&](u32 bc, u32 lx) {
-        return 2 * (size_t)(GI + s.combos_per_cta) * bc * ((1u << lx) + 2) * 8;
+        return 2 * (size_t)bc * (1u << lx) * (GI + 2 + s.combos_per_cta) * 8;
     };
     while (bytes(Bc, logX) > (160u << 10)) {
         if (Bc > 1) Bc /= 2; else if (logX > 1) --logX; else break;
@@ -1085,24 +1232,46 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     return s;
 }
 
-template <int GT>
+template <int GT, int BC>
 int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R, const u64* Dg,
                u64* acc, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
-        if (cudaFuncSetAttribute(k_diag_mac<GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_diag_mac<GT, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  160 << 10) != cudaSuccess)
             return cuda_check("k_diag_mac attribute");
         configured = true;
     }
-    const u32 E = c.L + c.K;
-    const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, E, s.zslices);
-    k_diag_mac<GT><<<grid, s.threads, s.smem, st>>>(R, Dg, pl.G, pl.hpg, pl.H, pl.B, s.Bc,
-                                                    pl.giants, E, c.log_n, s.logX, s.logGS,
-                                                    s.combos_per_cta, s.tiles_per_cta,
-                                                    log2u(pl.giants), log2u(s.Bc), c.d_mods,
-                                                    c.d_c30, acc);
+    MacArgs a;
+    a.G = pl.G;
+    a.hpg = pl.hpg;
+    a.H = pl.H;
+    a.B = pl.B;
+    a.GI = pl.giants;
+    a.E = c.L + c.K;
+    a.logN = c.log_n;
+    a.logX = s.logX;
+    a.logGS = s.logGS;
+    a.logGI = log2u(pl.giants);
+    a.CPC = s.combos_per_cta;
+    a.tiles_per_cta = s.tiles_per_cta;
+    a.achunks = pl.B / BC;
+    const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, a.E, s.zslices);
+    k_diag_mac<GT, BC><<<grid, s.threads, s.smem, st>>>(R, Dg, a, c.d_mods, c.d_c6090, acc);
     return launched("k_diag_mac");
+}
+
+template <int GT>
+int launch_mac_bc(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R,
+                  const u64* Dg, u64* acc, cudaStream_t st) {
+    switch (s.Bc) {
+        case 1: return launch_mac<GT, 1>(c, pl, s, R, Dg, acc, st);
+        case 2: return launch_mac<GT, 2>(c, pl, s, R, Dg, acc, st);
+        case 4: return launch_mac<GT, 4>(c, pl, s, R, Dg, acc, st);
+        case 8: return launch_mac<GT, 8>(c, pl, s, R, Dg, acc, st);
+        case 16: return launch_mac<GT, 16>(c, pl, s, R, Dg, acc, st);
+        default: return fail(PDQ_E_PARAM, "diag_mac: baby-step count must be a power of two");
+    }
 }
 
 }  // namespace
@@ -1113,9 +1282,9 @@ int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64*
     if (s.zslices > 65535) return fail(PDQ_E_PARAM, "diag_mac: too many groups");
     if (s.logX < 1 || s.smem > (160u << 10)) return fail(PDQ_E_PARAM, "diag_mac: plan too large for one tile");
     switch (s.GT) {
-        case 1: return launch_mac<1>(c, pl, s, R, Dg, acc, st);
-        case 2: return launch_mac<2>(c, pl, s, R, Dg, acc, st);
-        case 4: return launch_mac<4>(c, pl, s, R, Dg, acc, st);
+        case 1: return launch_mac_bc<1>(c, pl, s, R, Dg, acc, st);
+        case 2: return launch_mac_bc<2>(c, pl, s, R, Dg, acc, st);
+        case 4: return launch_mac_bc<4>(c, pl, s, R, Dg, acc, st);
         default: return fail(PDQ_E_PARAM, "diag_mac: giant-step count must be a power of two");
     }
 }

@@ -15,7 +15,13 @@ struct CtSet {
     long long inner = 0;
 
     __host__ __device__ __forceinline__ u64* at(u64 i) const {
-        return const_cast<u64*>(base) + (long long)(i / per) * outer + (long long)(i % per) * inner;
+        // ciphertext counts fit in 32 bits; per is 1 or 2 on the hot paths
+        const u32 j = (u32)i;
+        u32 hi, lo;
+        if (per == 1) { hi = j; lo = 0; }
+        else if (per == 2) { hi = j >> 1; lo = j & 1; }
+        else { hi = j / per; lo = j - hi * per; }
+        return const_cast<u64*>(base) + (long long)hi * outer + (long long)lo * inner;
     }
 };
 

@@ -117,7 +117,7 @@ _SIGS = {
     "pdq_profile_read": (_I, [_P, _P, _P, _U32]),
 }
 
-STAGES = ["mask", "pack", "baby", "mac", "giant", "rotsum", "combine"]
+STAGES = ["mask", "pack", "baby", "mac", "giant", "rotsum", "combine", "acc_moddown"]
 
 
 def pdq_launch_count() -> int:
