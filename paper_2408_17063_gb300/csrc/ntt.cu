@@ -67,97 +67,109 @@ __device__ __forceinline__ u32 smem_index(u32 c, u32 l, u32 logC) {
     return w ^ ((w >> 3) & 15);
 }
 
-template <bool FWD, int S, bool COLS>
+template <bool FWD, int S, bool COLS, bool SINGLE>
 struct Phase {
     static constexpr u32 GS = 1u << S;
+    // sub-transforms per CTA: one whole polynomial in the single-phase case,
+    // else as many as fill a 2048-element tile
+    static constexpr u32 LOGC = SINGLE ? 0 : 11 - S;
+    static constexpr u32 C = 1u << LOGC;
 
     u64* sm;
     const ulonglong2* tw;
     u64 q;
     u64 n0, n0s, n1, n1s;  // N^-1 and psi^-1 N^-1 (with Shoup) for level 0
-    u32 logN, logC, C, sub0, S2;
+    u32 logN, sub0, S2;
 
     // global index of element l of sub-transform c
     __device__ __forceinline__ u32 gidx(u32 c, u32 l) const {
         return COLS ? (l << S2) + sub0 + c : ((sub0 + c) << S) + l;
     }
 
-    // One pass over the R local levels whose pair bits are lb .. lb+R-1:
+    // One pass over the R local levels whose pair bits are LB .. LB+R-1:
     // every thread item holds the 2^R elements that these levels combine.
-    template <int R>
-    __device__ __forceinline__ void pass(u32 lb) const {
+    // All shifts and masks of the local index are compile-time constants.
+    template <int R, int LB>
+    __device__ __forceinline__ void pass() const {
         constexpr u32 NE = 1u << R;
-        const u32 items = (C * GS) >> R;
-        const u32 lowmask = (1u << lb) - 1;
-        const u32 gsh = lb + (COLS ? S2 : 0u);   // global position of pass bit 0
+        constexpr u32 items = (C * GS) >> R;
+        constexpr u32 lowmask = (1u << LB) - 1;
+        const u32 gsh = LB + (COLS ? S2 : 0u);   // global position of pass bit 0
+#pragma unroll 1
         for (u32 w = threadIdx.x; w < items; w += blockDim.x) {
             u32 c, fixed;
             if (COLS) {
                 c = w & (C - 1);
-                fixed = w >> logC;
+                fixed = w >> LOGC;
             } else {
                 fixed = w & ((GS >> R) - 1);
                 c = w >> (S - R);
             }
-            const u32 lbase = (fixed & lowmask) | ((fixed >> lb) << (lb + R));
+            const u32 lbase = (fixed & lowmask) | ((fixed >> LB) << (LB + R));
             const u32 jbase = gidx(c, lbase);
             u64 x[NE];
 #pragma unroll
-            for (u32 k = 0; k < NE; ++k) x[k] = sm[smem_index<S, COLS>(c, lbase | (k << lb), logC)];
+            for (u32 k = 0; k < NE; ++k) x[k] = sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int kb = FWD ? R - 1 - r : r;          // pair bit inside the item
                 const u32 P = gsh + kb;                      // pair bit in the global index
                 const u32 st = logN - 1 - P;                 // radix-2 level
                 const u32 ti0 = (1u << st) + (jbase >> (P + 1));
+                const bool level0 = !FWD && st == 0;
+                ulonglong2 wv[NE / 2];
+                if (!level0) {
+#pragma unroll
+                    for (int id = 0; id < (int)(NE >> (kb + 1)); ++id) wv[id] = __ldg(tw + ti0 + id);
+                }
 #pragma unroll
                 for (int id = 0; id < (int)(NE >> (kb + 1)); ++id) {
-                    if (!FWD && st == 0) {
 #pragma unroll
-                        for (int low = 0; low < (1 << kb); ++low) {
-                            const int k = (id << (kb + 1)) | low;
+                    for (int low = 0; low < (1 << kb); ++low) {
+                        const int k = (id << (kb + 1)) | low;
+                        if (level0) {
                             const u64 xa = x[k], xb = x[k + (1 << kb)];
                             x[k] = mul_shoup_lazy(xa + xb, n0, n0s, q);
                             x[k + (1 << kb)] = mul_shoup_lazy(xa - xb + 2 * q, n1, n1s, q);
-                        }
-                    } else {
-                        const ulonglong2 wv = __ldg(tw + ti0 + id);
-#pragma unroll
-                        for (int low = 0; low < (1 << kb); ++low) {
-                            const int k = (id << (kb + 1)) | low;
-                            if (FWD) bf_fwd(x[k], x[k + (1 << kb)], wv.x, wv.y, q);
-                            else bf_inv(x[k], x[k + (1 << kb)], wv.x, wv.y, q);
+                        } else if (FWD) {
+                            bf_fwd(x[k], x[k + (1 << kb)], wv[id].x, wv[id].y, q);
+                        } else {
+                            bf_inv(x[k], x[k + (1 << kb)], wv[id].x, wv[id].y, q);
                         }
                     }
                 }
             }
 #pragma unroll
-            for (u32 k = 0; k < NE; ++k) sm[smem_index<S, COLS>(c, lbase | (k << lb), logC)] = x[k];
+            for (u32 k = 0; k < NE; ++k) sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)] = x[k];
         }
         __syncthreads();
     }
 
-    __device__ __forceinline__ void run() const {
-        if (FWD) {
-            int top = S;
-            while (top > 0) {
-                const int r = top >= 3 ? 3 : top;
-                const u32 lb = (u32)(top - r);
-                if (r == 3) pass<3>(lb); else if (r == 2) pass<2>(lb); else pass<1>(lb);
-                top -= r;
-            }
-        } else {
-            int lo = 0;
-            while (lo < S) {
-                const int r = (S - lo) >= 3 ? 3 : (S - lo);
-                if (r == 3) pass<3>((u32)lo); else if (r == 2) pass<2>((u32)lo); else pass<1>((u32)lo);
-                lo += r;
-            }
+    // forward: pair bits from the top down, three at a time
+    template <int TOP>
+    __device__ __forceinline__ void run_fwd() const {
+        if constexpr (TOP > 0) {
+            constexpr int R = TOP >= 3 ? 3 : TOP;
+            pass<R, TOP - R>();
+            run_fwd<TOP - R>();
         }
+    }
+    // inverse: pair bits from the bottom up
+    template <int LO>
+    __device__ __forceinline__ void run_inv() const {
+        if constexpr (LO < S) {
+            constexpr int R = (S - LO) >= 3 ? 3 : (S - LO);
+            pass<R, LO>();
+            run_inv<LO + R>();
+        }
+    }
+    __device__ __forceinline__ void run() const {
+        if (FWD) run_fwd<S>();
+        else run_inv<0>();
     }
 };
 
-template <bool FWD, int S, bool COLS>
+template <bool FWD, int S, bool COLS, bool SINGLE>
 __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
     __shared__ __align__(16) u64 sm[kTile];
     const u32 p = blockIdx.x;
@@ -166,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
     const u32 N = 1u << a.logN;
     u64* base = a.data + (u64)grp * a.stride + (u64)limb * N;
 
-    Phase<FWD, S, COLS> ph;
+    Phase<FWD, S, COLS, SINGLE> ph;
     ph.sm = sm;
     ph.q = a.mods[mi].q;
     ph.tw = a.tw + (u64)mi * N;
@@ -175,23 +187,22 @@ __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
     ph.n1 = a.ninv4[4 * mi + 2];
     ph.n1s = a.ninv4[4 * mi + 3];
     ph.logN = a.logN;
-    ph.logC = a.logC;
-    ph.C = 1u << a.logC;
-    ph.sub0 = blockIdx.y << a.logC;
+    ph.sub0 = blockIdx.y << Phase<FWD, S, COLS, SINGLE>::LOGC;
     ph.S2 = a.logN - S;               // column phase: stride of the column elements
 
     constexpr u32 GS = 1u << S;
-    const u32 T = ph.C * GS;
+    constexpr u32 LOGC = Phase<FWD, S, COLS, SINGLE>::LOGC;
+    constexpr u32 T = Phase<FWD, S, COLS, SINGLE>::C * GS;
     // adjacent element pairs are adjacent in global memory (C >= 2 columns,
     // or rows of >= 2 elements) and in shared memory (the row swizzle keeps
     // aligned pairs together, possibly swapped), so tiles move with 16-byte
     // accesses on both sides
     for (u32 e = 2 * threadIdx.x; e < T; e += 2 * blockDim.x) {
         u32 c, l;
-        if (COLS) { l = e >> a.logC; c = e & (ph.C - 1); }
+        if (COLS) { l = e >> LOGC; c = e & ((1u << LOGC) - 1); }
         else { c = e >> S; l = e & (GS - 1); }
         const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(base + ph.gidx(c, l));
-        const u32 w = smem_index<S, COLS>(c, l, a.logC);
+        const u32 w = smem_index<S, COLS>(c, l, LOGC);
         *reinterpret_cast<ulonglong2*>(sm + (w & ~1u)) = (w & 1) ? make_ulonglong2(v.y, v.x) : v;
     }
     __syncthreads();
@@ -199,9 +210,9 @@ __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
     const u64 q = ph.q;
     for (u32 e = 2 * threadIdx.x; e < T; e += 2 * blockDim.x) {
         u32 c, l;
-        if (COLS) { l = e >> a.logC; c = e & (ph.C - 1); }
+        if (COLS) { l = e >> LOGC; c = e & ((1u << LOGC) - 1); }
         else { c = e >> S; l = e & (GS - 1); }
-        const u32 w = smem_index<S, COLS>(c, l, a.logC);
+        const u32 w = smem_index<S, COLS>(c, l, LOGC);
         const ulonglong2 sv = *reinterpret_cast<const ulonglong2*>(sm + (w & ~1u));
         u64 v0 = (w & 1) ? sv.y : sv.x, v1 = (w & 1) ? sv.x : sv.y;
         if (a.last) {
@@ -212,12 +223,13 @@ __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
     }
 }
 
-template <bool FWD, bool COLS>
+template <bool FWD, bool COLS, bool SINGLE>
 int launch_phase(int S, dim3 grid, u32 threads, const NttArgs& a, cudaStream_t st) {
     switch (S) {
-#define PDQ_CASE(s) case s: ntt_phase_kernel<FWD, s, COLS><<<grid, threads, 0, st>>>(a); break;
+#define PDQ_CASE(s) case s: ntt_phase_kernel<FWD, s, COLS, SINGLE><<<grid, threads, 0, st>>>(a); break;
         PDQ_CASE(1) PDQ_CASE(2) PDQ_CASE(3) PDQ_CASE(4) PDQ_CASE(5) PDQ_CASE(6)
         PDQ_CASE(7) PDQ_CASE(8) PDQ_CASE(9) PDQ_CASE(10) PDQ_CASE(11)
+        // (column phases use S = log N - 9 <= 7 for the supported rings)
 #undef PDQ_CASE
         default: return fail(PDQ_E_PARAM, "ntt: unsupported phase size");
     }
@@ -245,7 +257,7 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
         a.logC = 0;
         a.last = 1;
         u32 threads = c.N / 8 < 32 ? 32 : (c.N / 8 > kThreads ? kThreads : c.N / 8);
-        return launch_phase<FWD, false>((int)c.log_n, dim3((u32)polys, 1), threads, a, st);
+        return launch_phase<FWD, false, true>((int)c.log_n, dim3((u32)polys, 1), threads, a, st);
     }
     const u32 S1 = c.log_n - kRowBits;
     a.S1 = S1;
@@ -257,13 +269,15 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
     if (FWD) {
         cols.last = 0;
         rows.last = 1;
-        PDQ_TRY((launch_phase<FWD, true>((int)S1, gcols, kThreads, cols, st)));
-        return launch_phase<FWD, false>((int)kRowBits, grows, kThreads, rows, st);
+        PDQ_TRY((launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cols, st)));
+        ntt_phase_kernel<FWD, kRowBits, false, false><<<grows, kThreads, 0, st>>>(rows);
+        return launched("ntt_phase_kernel");
     }
     rows.last = 0;
     cols.last = 1;
-    PDQ_TRY((launch_phase<FWD, false>((int)kRowBits, grows, kThreads, rows, st)));
-    return launch_phase<FWD, true>((int)S1, gcols, kThreads, cols, st);
+    ntt_phase_kernel<FWD, kRowBits, false, false><<<grows, kThreads, 0, st>>>(rows);
+    PDQ_TRY(launched("ntt_phase_kernel"));
+    return launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cols, st);
 }
 
 }  // namespace
