@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--L", type=int, default=0, help="override the ciphertext primes")
     ap.add_argument("--K", type=int, default=0, help="override the special primes")
     ap.add_argument("--dnum", type=int, default=0, help="override the key-switching digits")
+    ap.add_argument("--B", type=int, default=0, help="baby-step count of the plan (0: the library's choice)")
     ap.add_argument("--s", type=int, default=0, help="override the sparsity")
     ap.add_argument("--mix", type=int, default=64, help="queries of the batched/served mix (0: skip)")
     ap.add_argument("--lanes", type=int, default=4)
@@ -435,8 +436,9 @@ MAC_CEILING_MEASURED = 2.02e12
 # DRAM bytes of one k_diag_mac launch from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the same plan with 3 primes (L=2, K=1), scaled by
 # 10/3 to the 10 primes of Q u P (every CTA works on one prime);
-# None when the kernel has changed since the capture.
-MAC_TRAFFIC_BYTES = None
+# None when the kernel has changed since the capture.  Capture: 2.609 GB read +
+# 0.389 GB written per launch with 3 primes.
+MAC_TRAFFIC_BYTES = round((2.608506e9 + 0.389425e9) * 10 / 3)
 
 
 def mac_roofline(ctx, plan, ms):
@@ -449,7 +451,8 @@ def mac_roofline(ctx, plan, ms):
     return {"kernel": "k_diag_mac", "bound": "alu", "achieved": achieved / 1e12,
             "peak": MAC_PEAK_PER_S / 1e12, "unit": "T modmac/s", "frac": achieved / MAC_PEAK_PER_S,
             "frac_of_measured_ceiling": achieved / MAC_CEILING_MEASURED,
-            "traffic": MAC_TRAFFIC_BYTES, "algorithmic_bytes": algo_bytes,
+            "traffic": MAC_TRAFFIC_BYTES if (N, E, plan.H, plan.B, plan.giants) == (2**15, 10, 64, 16, 16)
+            else None, "algorithmic_bytes": algo_bytes,
             "macs_per_launch": macs, "ms_per_launch": ms,
             "timing": "CUDA events recorded on the launching stream around each launch",
             "peak_source": "derived: 152 SMs x 2070 MHz x 32 IMAD.WIDE/clk/SM / 4 per modmac"}
@@ -471,7 +474,7 @@ def run_gpu(args, cfg, rank: int, world: int):
 
     ctx = pdq.Context.from_config(cfg)
     q = W.draw_query(cfg, cfg.seed + rank)
-    plan = ctx.plan(cfg.n, cfg.s)
+    plan = ctx.plan(cfg.n, cfg.s, args.B)
     galois = ctx.plan_galois(plan)
     sk = ctx.secret_prepare(torch.from_numpy(q.sk))
     N = ctx.N
@@ -557,7 +560,8 @@ def run_gpu(args, cfg, rank: int, world: int):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64 (exact modular integers)", "data": "synthetic",
-            "config": config_dict(cfg, {"parallelism": f"replicas x{world}"}),
+            "config": config_dict(cfg, {"parallelism": f"replicas x{world}",
+                                        "baby_steps_B": plan.B, "giant_steps": plan.giants}),
             "latency_ms": {"p50": p50, "p99": p99, "min": ms_sorted[0], "max": ms_sorted[-1]},
             "stages_ms_per_query": {k: v[0] / max(1, args.steps) for k, v in stages.items()},
             "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps,

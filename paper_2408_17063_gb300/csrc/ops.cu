@@ -42,6 +42,20 @@ __device__ __forceinline__ u32 auto_index(u32 x, u32 k, u32 logN) {
 // v -> v0 | v1 << 32 with v = v0 + v1 2^30 (the operand layout of k_diag_mac)
 __device__ __forceinline__ u64 split30(u64 v) { return (v & 0x3fffffffull) | ((v >> 30) << 32); }
 
+// asynchronous global -> shared copies (valid == false: zero fill)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+    const u32 s = (u32)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
+                 "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const u32 s = (u32)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 // ------------------------------------------------------------- encoding ----
 
 // out[c][0][pos[idx]] = slots[c][idx] mod t
@@ -434,35 +448,54 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
         u32 E, u32 L, u32 nd, const Mod* __restrict__ mods, const u64* __restrict__ Pq,
         const u64* __restrict__ Pqs, u64* __restrict__ Rx, const BabyParams bp) {
     extern __shared__ __align__(16) u64 sm[];
+    const u32 KT = nd * 2 * T;          // words of one key tile
     u64* Ds = sm;                       // [HC][nd][T]
     u64* Cs = Ds + HC * nd * T;         // [HC][T]
-    u64* Ks = Cs + HC * T;              // [nd][2][T]
+    u64* Ks = Cs + HC * T;              // [3][nd][2][T]: key tiles, three rotations in flight
     const u32 y0 = blockIdx.x * T, r = blockIdx.y, h0 = blockIdx.z * HC;
     const u64 EN = (u64)E << logN;
     const u32 nthreads = T * HC / CPT;
-    for (u32 e = threadIdx.x; e < HC * nd * T; e += nthreads) {
-        const u32 yy = e % T, rest = e / T, b = rest % nd, ct = rest / nd;
+    constexpr u32 TP = T / 2;           // 16-byte chunks per row of a tile
+
+    // the digits and c0 of this tile, 16-byte asynchronous copies (zero rows
+    // past the last ciphertext)
+    for (u32 e = threadIdx.x; e < HC * nd * TP; e += nthreads) {
+        const u32 yy = (e % TP) * 2, rest = e / TP, b = rest % nd, ct = rest / nd;
         const u32 h = h0 + ct;
-        Ds[e] = h < H ? D[((u64)h * nd + b) * EN + ((u64)r << logN) + y0 + yy] : 0;
+        cp_async16(Ds + (ct * nd + b) * T + yy,
+                   D + ((u64)(h < H ? h : 0) * nd + b) * EN + ((u64)r << logN) + y0 + yy, h < H);
     }
     if (r < L) {
-        for (u32 e = threadIdx.x; e < HC * T; e += nthreads) {
-            const u32 yy = e % T, ct = e / T, h = h0 + ct;
-            Cs[e] = h < H ? u.at(h)[((u64)r << logN) + y0 + yy] : 0;
+        for (u32 e = threadIdx.x; e < HC * TP; e += nthreads) {
+            const u32 yy = (e % TP) * 2, ct = e / TP, h = h0 + ct;
+            cp_async16(Cs + ct * T + yy, u.at(h < H ? h : 0) + ((u64)r << logN) + y0 + yy, h < H);
         }
     }
+    // key tile of rotation a (the positions x0 .. x0+T-1 whose sources lie in this tile)
+    auto issue_key = [&](u32 a, u32 buf) {
+        const u32 x0 = auto_index(y0, bp.kinv[a], logN) & ~(T - 1);
+        const u64* key = keys + bp.koff[a] + ((u64)r << logN) + x0;
+        u64* dst = Ks + buf * KT;
+        for (u32 e = threadIdx.x; e < nd * 2 * TP; e += nthreads) {
+            const u32 xx = (e % TP) * 2, bp2 = e / TP;    // bp2 = beta * 2 + p
+            cp_async16(dst + bp2 * T + xx, key + (u64)bp2 * EN + xx, true);
+        }
+        cp_async_commit();
+    };
+    issue_key(1, 0);                    // (one group with the tile above)
+    if (B > 2) issue_key(2, 1);
+
     const Mod md = mods[r];
     const u64 P = r < L ? Pq[r] : 0, Ps = r < L ? Pqs[r] : 0;
     const u32 xi = threadIdx.x % T, hg = threadIdx.x / T;
     for (u32 a = 1; a < B; ++a) {
-        const u32 x0 = auto_index(y0, bp.kinv[a], logN) & ~(T - 1);
-        __syncthreads();                // Ds/Cs ready; previous Ks consumed
-        const u64* key = keys + bp.koff[a];
-        for (u32 e = threadIdx.x; e < nd * 2 * T; e += nthreads) {
-            const u32 xx = e % T, bp2 = e / T;            // bp2 = beta * 2 + p
-            Ks[e] = key[(u64)bp2 * EN + ((u64)r << logN) + x0 + xx];
-        }
+        if (a + 1 < B) cp_async_wait<1>(); else cp_async_wait<0>();
+        // key tile a (and the digit tile) visible; every thread is past
+        // rotation a-1, whose buffer (a+1) % 3 is refilled next
         __syncthreads();
+        if (a + 2 < B) issue_key(a + 2, (a + 1) % 3);
+        const u64* Kt = Ks + ((a - 1) % 3) * KT;
+        const u32 x0 = auto_index(y0, bp.kinv[a], logN) & ~(T - 1);
         const u32 x = x0 + xi;
         const u32 y = auto_index(x, bp.k[a], logN) - y0;  // in [0, T)
 #pragma unroll
@@ -472,8 +505,8 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
             u64 h0a = 0, l0a = 0, h1a = 0, l1a = 0;
             for (u32 b = 0; b < nd; ++b) {
                 const u64 d = Ds[(ct * nd + b) * T + y];
-                mac128(h0a, l0a, d, Ks[(b * 2) * T + xi]);
-                mac128(h1a, l1a, d, Ks[(b * 2 + 1) * T + xi]);
+                mac128(h0a, l0a, d, Kt[(b * 2) * T + xi]);
+                mac128(h1a, l1a, d, Kt[(b * 2 + 1) * T + xi]);
             }
             u64 v0 = reduce128(h0a, l0a, md);
             const u64 v1 = reduce128(h1a, l1a, md);
@@ -658,19 +691,6 @@ __device__ __forceinline__ u64 fold5(const Acc5& A, const Mod& md, const u64* __
     return reduce64(v, md);
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
-    const u32 s = (u32)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
-                 "r"(valid ? 16 : 0));
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const u32 s = (u32)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
 struct MacArgs {
     u32 G, hpg, H, B, GI, E, logN;
     u32 logX, logGS, logGI, CPC;   // CPC: combinations per CTA (even)
@@ -678,7 +698,7 @@ struct MacArgs {
 };
 
 template <int GT, int BC>
-__global__ void __launch_bounds__(512) k_diag_mac(const u64* __restrict__ R,
+__global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
                                                   const u64* __restrict__ Dg, MacArgs a,
                                                   const Mod* __restrict__ mods,
                                                   const u64* __restrict__ c6090,
@@ -695,7 +715,8 @@ __global__ void __launch_bounds__(512) k_diag_mac(const u64* __restrict__ R,
     const u32 hpg_eff = min(a.hpg, a.H);
     const u32 g0 = gs * GT;
 
-    const u32 dwords = BC * X * GIp, rwords = BC * CPC * X;
+    const u32 RB = BC * X + 2;                     // words per combination block (padded)
+    const u32 dwords = BC * X * GIp, rwords = CPC * RB;
     const u32 stage = dwords + rwords;
 
     const u32 gam = (cbase >> 1) + ct;             // group of this thread's two combinations
@@ -738,7 +759,7 @@ __global__ void __launch_bounds__(512) k_diag_mac(const u64* __restrict__ R,
             const bool valid = gm < a.G && h < a.H;
             const u64* src = R + ((((u64)(valid ? h : 0) * a.B + a0 + ai) * 2 + p) * a.E + l) * N +
                              x0 + 2 * xp;
-            cp_async16(Rt + row * X + 2 * xp, src, valid);
+            cp_async16(Rt + cb * RB + ai * X + 2 * xp, src, valid);
         }
         cp_async_commit();
     };
@@ -770,7 +791,7 @@ __global__ void __launch_bounds__(512) k_diag_mac(const u64* __restrict__ R,
         }
         __syncthreads();
         const u64* D = smem + buf * stage + xi * GIp + g0;
-        const u64* Rt = smem + buf * stage + dwords + (2 * ct) * BC * X + xi;
+        const u64* Rt = smem + buf * stage + dwords + (2 * ct) * RB + xi;
 #pragma unroll
         for (int ai = 0; ai < BC; ++ai) {
             u64 d[GT];
@@ -784,7 +805,7 @@ __global__ void __launch_bounds__(512) k_diag_mac(const u64* __restrict__ R,
             } else {
                 d[0] = D[ai * X * GIp];
             }
-            const u64 r0 = Rt[ai * X], r1 = Rt[(BC + ai) * X];
+            const u64 r0 = Rt[ai * X], r1 = Rt[RB + ai * X];
             const u32 r00 = (u32)r0, r01 = (u32)(r0 >> 32);
             const u32 r10 = (u32)r1, r11 = (u32)(r1 >> 32);
 #pragma unroll
@@ -1122,7 +1143,7 @@ int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64*
                    const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st) {
     constexpr u32 T = 64, HC = 16, CPT = 4;
     if (B > 128) return fail(PDQ_E_PARAM, "baby steps: B <= 128");
-    const size_t tile_bytes = ((size_t)HC * c.ndigits * T + HC * T + c.ndigits * 2 * T) * sizeof(u64);
+    const size_t tile_bytes = ((size_t)HC * c.ndigits * T + HC * T + 3 * c.ndigits * 2 * T) * sizeof(u64);
     if (c.N < T || tile_bytes > (160u << 10)) {
         // rings below one tile, or too many digits for the staged tile: one
         // rotation at a time
@@ -1142,11 +1163,11 @@ int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64*
         bp.koff[a] = key_offsets[a];
     }
     const u32 E = c.L + c.K, nd = c.ndigits;
-    const size_t smem = ((size_t)HC * nd * T + HC * T + nd * 2 * T) * sizeof(u64);
+    const size_t smem = tile_bytes;
     static bool configured = false;
     if (!configured) {
         if (cudaFuncSetAttribute(k_baby_ext<T, HC, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem > (48 << 10) ? (int)smem : (48 << 10)) != cudaSuccess)
+                                 160 << 10) != cudaSuccess)
             return cuda_check("k_baby_ext attribute");
         configured = true;
     }
@@ -1196,9 +1217,12 @@ u32 log2u(u32 x) {
 
 // Launch shape of k_diag_mac: up to 4 giant indices and both polynomials of
 // one group per thread, up to 16 groups per CTA (more go to further
-// z-slices), X >= 2 positions so that a CTA has up to 512 threads, and an
-// a-chunk BC (up to 16) that keeps the two staged (diagonal + rotated) tiles
-// within 160 KB of shared memory.
+// z-slices), X >= 2 positions so that a CTA has up to 256 threads (two CTAs
+// per SM, whose staging barriers are independent, so one CTA's copy issue
+// and renormalisation overlap the other's products), and an a-chunk BC (up
+// to 16) that keeps the two staged (diagonal + rotated) tiles within 100 KB
+// of shared memory.
+constexpr u32 kMacThreads = 256;
 MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     MacShape s{};
     const u32 GI = pl.giants, combos = 2 * pl.G;
@@ -1206,19 +1230,19 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     const u32 GS = GI / s.GT;
     s.logGS = log2u(GS);
     u32 ct = combos / 2;
-    u32 ct_max = 256 / GS;
+    u32 ct_max = kMacThreads / 2 / GS;
     if (ct_max > 16) ct_max = 16;
     if (ct > ct_max) ct = 1u << log2u(ct_max);
     s.combos_per_cta = ct * 2;
     s.zslices = (combos + s.combos_per_cta - 1) / s.combos_per_cta;
     u32 logX = 1;
-    while (((ct * GS) << (logX + 1)) <= 512 && logX < 8) ++logX;
+    while (((ct * GS) << (logX + 1)) <= kMacThreads && logX < 8) ++logX;
     if (logX > logN) logX = logN;
     u32 Bc = pl.B < 16 ? pl.B : 16;
     auto bytes = [&](u32 bc, u32 lx) {
-        return 2 * (size_t)bc * (1u << lx) * (GI + 2 + s.combos_per_cta) * 8;
+        return 2 * ((size_t)bc * (1u << lx) * (GI + 2 + s.combos_per_cta) + 2 * s.combos_per_cta) * 8;
     };
-    while (bytes(Bc, logX) > (160u << 10)) {
+    while (bytes(Bc, logX) > (100u << 10)) {
         if (Bc > 1) Bc /= 2; else if (logX > 1) --logX; else break;
     }
     s.logX = logX;
@@ -1238,7 +1262,7 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
     static bool configured = false;
     if (!configured) {
         if (cudaFuncSetAttribute(k_diag_mac<GT, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 160 << 10) != cudaSuccess)
+                                 100 << 10) != cudaSuccess)
             return cuda_check("k_diag_mac attribute");
         configured = true;
     }
@@ -1280,7 +1304,7 @@ int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64*
              cudaStream_t st) {
     const MacShape s = mac_shape(pl, c.log_n);
     if (s.zslices > 65535) return fail(PDQ_E_PARAM, "diag_mac: too many groups");
-    if (s.logX < 1 || s.smem > (160u << 10)) return fail(PDQ_E_PARAM, "diag_mac: plan too large for one tile");
+    if (s.logX < 1 || s.smem > (100u << 10)) return fail(PDQ_E_PARAM, "diag_mac: plan too large for one tile");
     switch (s.GT) {
         case 1: return launch_mac_bc<1>(c, pl, s, R, Dg, acc, st);
         case 2: return launch_mac_bc<2>(c, pl, s, R, Dg, acc, st);

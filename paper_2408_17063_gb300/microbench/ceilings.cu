@@ -5,7 +5,10 @@
 //     multiply-adds into 64-bit partial sums), and in the 128-bit carry-chain
 //     form the key-switching inner products use;
 //   * the forward NTT butterfly (Harvey's lazy Cooley-Tukey butterfly with a
-//     Shoup twiddle multiplication).
+//     Shoup twiddle multiplication);
+//   * plain 32x32->32-bit multiply-adds (mad.lo.u32) and 32x32->64-bit
+//     multiply-adds (mad.wide.u32), for the per-SM issue rates of the
+//     integer multiply pipe.
 // No memory traffic inside the timed loops; CUDA events around each kernel.
 #include <cstdint>
 #include <cstdio>
@@ -30,6 +33,7 @@ __device__ __forceinline__ void bf(u64& x, u64& y, u64 w, u64 wp, u64 q) {
     y = a - t + 2 * q;
 }
 
+// V = 0: mac128, 1: mac30 (four 64-bit partial sums), 2: mad.lo.u32 stream
 template <int V>
 __global__ void k_mac(const u64* in, u64* out, int iters) {
     u64 a = in[threadIdx.x & 31], b = in[(threadIdx.x + 7) & 31];
@@ -39,8 +43,16 @@ __global__ void k_mac(const u64* in, u64* out, int iters) {
         for (int g = 0; g < 8; ++g) {
             const u64 bb = b + g;
             if (V == 0) mac128(acc[g][0], acc[g][1], a, bb);
-            else mac30(acc[g], (u32)a & 0x3fffffffu, (u32)(a >> 30), (u32)bb & 0x3fffffffu,
-                       (u32)(bb >> 30));
+            else if (V == 1) mac30(acc[g], (u32)a & 0x3fffffffu, (u32)(a >> 30), (u32)bb & 0x3fffffffu,
+                                   (u32)(bb >> 30));
+            else {
+                u32 x = (u32)acc[g][0];
+                const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)bb, b1 = (u32)(bb >> 32);
+                asm("mad.lo.u32 %0, %1, %2, %0;\n\tmad.lo.u32 %0, %3, %4, %0;\n\t"
+                    "mad.lo.u32 %0, %1, %4, %0;\n\tmad.lo.u32 %0, %3, %2, %0;"
+                    : "+r"(x) : "r"(a0), "r"(b0), "r"(a1), "r"(b1));
+                acc[g][0] = x;
+            }
         }
         a += 3;
     }
@@ -96,7 +108,8 @@ int main() {
         cudaEventSynchronize(e1);
     }
     cudaEventElapsedTime(&ms, e0, e1);
-    printf("{\"mac30_per_s\": %.4e, ", work * 8 / (ms * 1e-3));
+    printf("{\"mac30_per_s\": %.4e, \"imad_wide_per_s\": %.4e, ", work * 8 / (ms * 1e-3),
+           work * 8 * 4 / (ms * 1e-3));
     for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0);
         k_mac<0><<<blocks, threads>>>(in, out, iters);
@@ -105,6 +118,14 @@ int main() {
     }
     cudaEventElapsedTime(&ms, e0, e1);
     printf("\"mac128_per_s\": %.4e, ", work * 8 / (ms * 1e-3));
+    for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0);
+        k_mac<2><<<blocks, threads>>>(in, out, iters);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    printf("\"imad32_per_s\": %.4e, ", work * 8 * 4 / (ms * 1e-3));
     for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0);
         k_bf<<<blocks, threads>>>(in, out, iters, q);
