@@ -43,10 +43,14 @@ def parse():
     ap.add_argument("--K", type=int, default=0, help="override the special primes")
     ap.add_argument("--dnum", type=int, default=0, help="override the key-switching digits")
     ap.add_argument("--B", type=int, default=0, help="baby-step count of the plan (0: the library's choice)")
+    ap.add_argument("--lane-budget-gb", type=float, default=100.0,
+                    help="cap on the batched lanes' workspaces (fewer lanes for the largest ring beyond)")
+    ap.add_argument("--clients", type=int, default=4,
+                    help="second batched run with this many clients sharing key sets (0: skip)")
     ap.add_argument("--s", type=int, default=0, help="override the sparsity")
     ap.add_argument("--mix", type=int, default=64, help="queries of the batched/served mix (0: skip)")
     ap.add_argument("--lanes", type=int, default=4)
-    ap.add_argument("--rates", default="50,200,1000", help="served arrival rates, queries/s")
+    ap.add_argument("--rates", default="50,200,500,1000,2000", help="served arrival rates, queries/s")
     ap.add_argument("--served-requests", type=int, default=192)
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served HBM budget")
     return ap.parse_args()
@@ -57,9 +61,7 @@ def config_dict(cfg, extra=None):
                      f"{cfg.L}x{cfg.prime_bits}-bit + {cfg.K} special primes (dnum={cfg.dnum}), "
                      f"n={cfg.n} records, s={cfg.s} {cfg.pattern} matches",
          "N": cfg.N, "n": cfg.n, "s": cfg.s, "L": cfg.L, "K": cfg.K, "dnum": cfg.dnum,
-         "t": cfg.t, "queries_per_step": 1, "mode": "plain (one query at a time)",
-         "l2": "inputs larger than L2 (2 GiB of diagonals, 128 MiB query, 128 MiB database, "
-               "740 MiB keys read per query)"}
+         "t": cfg.t, "queries_per_step": 1, "mode": "plain (one query at a time)"}
     d.update(extra or {})
     return d
 
@@ -245,11 +247,14 @@ def run_e2e(args, ctx, plan, v_cts, db, keys, galois, consts, ws, stream, dist, 
 
 class Mix:
     """The batched workload: independent queries with mixed ring dimension,
-    record count and sparsity, each with its own key set; one resident
-    database of 2^20 records (values uniform in [0, 2^16)) per ring size;
-    diagonal constants shared by queries with the same plan."""
+    record count and sparsity; one resident database of 2^20 records (values
+    uniform in [0, 2^16)) per ring size; diagonal constants shared by queries
+    with the same plan.  clients = 0: every query has its own secret and key
+    set; clients = c > 0: query i belongs to client i mod c, whose secret and
+    rotation keys (every element its queries of that ring need) all its
+    queries share."""
 
-    def __init__(self, nq: int, lanes: int):
+    def __init__(self, nq: int, lanes: int, clients: int = 0):
         import numpy as np
         import torch
         import workloads as W
@@ -267,22 +272,43 @@ class Mix:
             self.db[ln] = ctx.db_encode(torch.from_numpy(vals.astype(np.int32)).cuda())
         consts = {}
         self.items = []
-        for q in self.specs:
-            ctx = self.ctx[q.log_n]
-            plan = ctx.plan(q.n, q.s)
-            key = (q.log_n, plan.s_prime, plan.B, plan.hclass, plan.G > 1)
-            if key not in consts:
-                consts[key] = ctx.plan_constants(plan)
-            pos = W.draw_matches_uniform(q.n, q.s, W.rng_for(q.seed, 2))
-            sk = ctx.secret_prepare(torch.from_numpy(W.draw_ternary(ctx.N, W.rng_for(q.seed, 3))))
-            galois = ctx.plan_galois(plan)
+        self.clients = clients
+        plans = [self.ctx[q.log_n].plan(q.n, q.s) for q in self.specs]
+
+        def make_keys(ctx, sk, galois, seed):
             keys = ctx._u64(len(galois) * ctx.key_elems)
             kv = keys.view(len(galois), -1)
-            kr = W.rotation_key_randomness(ctx.moduli, ctx.N, ctx.ndigits, galois, q.seed)
+            kr = W.rotation_key_randomness(ctx.moduli, ctx.N, ctx.ndigits, galois, seed)
             for i, k in enumerate(galois):
                 a, e = kr[k]
                 ctx.rotkey_gen(sk, k, torch.from_numpy(a.view(np.int64)).cuda(),
                                torch.from_numpy(e).cuda(), out=kv[i])
+            return keys
+
+        shared = {}
+        if clients:
+            need = {}
+            for i, (q, plan) in enumerate(zip(self.specs, plans)):
+                need.setdefault((i % clients, q.log_n), set()).update(
+                    self.ctx[q.log_n].plan_galois(plan))
+            for (c, ln), ks in sorted(need.items()):
+                ctx = self.ctx[ln]
+                seed = 0xC1E0 + 16 * c + ln
+                sk = ctx.secret_prepare(torch.from_numpy(W.draw_ternary(ctx.N, W.rng_for(seed, 3))))
+                galois = sorted(ks)
+                shared[(c, ln)] = (sk, galois, make_keys(ctx, sk, galois, seed))
+        for qi, (q, plan) in enumerate(zip(self.specs, plans)):
+            ctx = self.ctx[q.log_n]
+            key = (q.log_n, plan.s_prime, plan.B, plan.hclass, plan.G > 1)
+            if key not in consts:
+                consts[key] = ctx.plan_constants(plan)
+            pos = W.draw_matches_uniform(q.n, q.s, W.rng_for(q.seed, 2))
+            if clients:
+                sk, galois, keys = shared[(qi % clients, q.log_n)]
+            else:
+                sk = ctx.secret_prepare(torch.from_numpy(W.draw_ternary(ctx.N, W.rng_for(q.seed, 3))))
+                galois = ctx.plan_galois(plan)
+                keys = make_keys(ctx, sk, galois, q.seed)
             v = np.zeros(plan.J * ctx.N, dtype=np.int32)
             v[pos] = 1
             a, e = W.encryption_randomness(ctx.moduli[:ctx.L], ctx.N, plan.J, q.seed)
@@ -318,12 +344,22 @@ def run_batched(args, mix) -> dict:
     for it in mix.items:
         by_ring.setdefault(it["spec"].log_n, []).append(it)
     handles = {ln: [mix.handle(it) for it in its] for ln, its in by_ring.items()}
-    lane_ws = {}
-    for ln, its in by_ring.items():
-        need = [0] * args.lanes
+    # lanes per ring, fewer where the lanes' workspaces would pass the budget
+    def lane_need(its, lanes):
+        need = [0] * lanes
         for i, it in enumerate(its):
-            need[i % args.lanes] = max(need[i % args.lanes], mix.ws_bytes(it))
-        lane_ws[ln] = [torch.empty(max(b, 8), dtype=torch.uint8, device="cuda") for b in need]
+            need[i % lanes] = max(need[i % lanes], mix.ws_bytes(it))
+        return need
+    lanes = {ln: min(args.lanes, len(its)) for ln, its in by_ring.items()}
+    budget = int(args.lane_budget_gb * (1 << 30))
+    while sum(sum(lane_need(by_ring[ln], k)) for ln, k in lanes.items()) > budget:
+        big = max((ln for ln in lanes if lanes[ln] > 1),
+                  key=lambda ln: max(lane_need(by_ring[ln], lanes[ln])), default=None)
+        if big is None:
+            break
+        lanes[big] -= 1
+    lane_ws = {ln: [torch.empty(max(b, 8), dtype=torch.uint8, device="cuda")
+                    for b in lane_need(by_ring[ln], lanes[ln])] for ln in by_ring}
     streams = {ln: torch.cuda.Stream() for ln in by_ring}
     for ln in by_ring:
         streams[ln].wait_stream(torch.cuda.current_stream())
@@ -358,6 +394,10 @@ def run_batched(args, mix) -> dict:
     torch.cuda.synchronize()
     t_graph = (time.perf_counter() - t0) / reps
     ok = ok and all(mix.check(it, h.out) for ln in by_ring for it, h in zip(by_ring[ln], handles[ln]))
+    # the lanes' workspaces go before the plain run allocates its own
+    del graphs, lane_ws
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     # plain: one query at a time on one stream, no graph
     ws_plain = {ln: torch.empty(max(max(mix.ws_bytes(it) for it in its), 8), dtype=torch.uint8,
                                 device="cuda") for ln, its in by_ring.items()}
@@ -376,10 +416,11 @@ def run_batched(args, mix) -> dict:
     t_plain = time.perf_counter() - t0
     nq = len(mix.items)
     return {"queries": nq, "rings": {str(1 << ln): len(v) for ln, v in by_ring.items()},
-            "lanes_per_ring": args.lanes, "cuda_graph": True, "distinct_plan_constants": mix.n_consts,
+            "lanes_per_ring": {str(1 << ln): k for ln, k in lanes.items()}, "cuda_graph": True, "distinct_plan_constants": mix.n_consts,
             "batched_qps": nq / t_graph, "plain_qps": nq / t_plain,
             "batched_ms_per_batch": 1000 * t_graph, "plain_ms_per_batch": 1000 * t_plain,
             "speedup": t_plain / t_graph, "all_decompress_exactly": bool(ok),
+            "peak_device_gib": torch.cuda.max_memory_allocated() / 2**30,
             "mix": "64 queries, N uniform in {2^13, 2^14, 2^15}, log2 n uniform in 12..20, "
                    "s uniform in [1, min(1024, n/16)], own key set per query"}
 
@@ -561,7 +602,12 @@ def run_gpu(args, cfg, rank: int, world: int):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64 (exact modular integers)", "data": "synthetic",
             "config": config_dict(cfg, {"parallelism": f"replicas x{world}",
-                                        "baby_steps_B": plan.B, "giant_steps": plan.giants}),
+                                        "baby_steps_B": plan.B, "giant_steps": plan.giants,
+                                        "l2": "inputs larger than L2 (per query: "
+                                              f"{consts.numel() * 8 / 2**30:.2f} GiB of plan constants, "
+                                              f"{keys.numel() * 8 / 2**20:.0f} MiB of rotation keys, "
+                                              f"{v_cts.numel() * 8 / 2**20:.0f} MiB query, "
+                                              f"{db.numel() * 8 / 2**20:.0f} MiB database read)"}),
             "latency_ms": {"p50": p50, "p99": p99, "min": ms_sorted[0], "max": ms_sorted[-1]},
             "stages_ms_per_query": {k: v[0] / max(1, args.steps) for k, v in stages.items()},
             "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps,
@@ -572,6 +618,11 @@ def run_gpu(args, cfg, rank: int, world: int):
         mix = Mix(args.mix, args.lanes)
         line["batched"] = run_batched(args, mix)
         line["served"] = run_served(args, mix)
+        if args.clients > 0:
+            del mix
+            torch.cuda.empty_cache()
+            mix = Mix(args.mix, args.lanes, clients=args.clients)
+            line["batched_shared_keys"] = dict(run_batched(args, mix), clients=args.clients)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in oracle_sample(cfg).items()
                                 if k != "seconds_per_query"}

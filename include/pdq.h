@@ -166,9 +166,13 @@ int pdq_rotate(const pdq_ctx* ctx, const uint64_t* ct_in, uint32_t count, uint64
                const uint64_t* key, uint64_t* ct_out, void* ws, size_t ws_bytes, void* stream);
 
 /* ----------------------------------------------------------------- plans
- * Fill the layout for n records and sparsity s; B = 0 picks
- * 2^ceil(log2(s')/2).  Errors: PDQ_E_PARAM if s' > N/2, s' >= t or B does
- * not divide s'. */
+ * Fill the layout for n records and sparsity s (s' = 2^ceil(log2 s), the
+ * Pegasus baby-step/giant-step split k = gB + a of Sec. 5.2).  B = 0 picks
+ * the power of two B <= min(s', 128) with at most 32 giant steps that
+ * minimises H (B - 1) + 8 G (s'/B - 1) + 3 G s'/B (hoisted baby rotations,
+ * giant-step key switches and accumulator ModDowns, weighted by their
+ * measured costs), ties to the smaller B.  Errors: PDQ_E_PARAM if s' > N/2,
+ * s' >= t, B does not divide s', B > 128 or s'/B > 32. */
 int pdq_plan_make(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B, pdq_plan* plan);
 
 /* The Galois elements of every rotation the plan uses, ascending (host
@@ -303,6 +307,36 @@ int pdq_server_destroy(pdq_server* srv);
  * synchronous. */
 int pdq_decomp(const pdq_ctx* ctx, const pdq_plan* plan, const uint32_t* slots,
                uint64_t* idx_out, uint32_t* val_out, uint64_t cap, uint64_t* count);
+
+/* ---------------------------------------------------------- serialise
+ * Exchange format between client and server (Alg. 7 sends the query
+ * ciphertexts to the server and the answer back; the paper fixes no format).
+ * Little-endian bytes: a 64-byte header (u32 magic "PDQC" for ciphertexts or
+ * "PDQS" for a secret key, u32 version 1, u32 N, u32 limbs per polynomial,
+ * u32 level (= limbs), u32 count, u64 t, u64 first ciphertext prime, 24 zero
+ * bytes), then for ciphertexts count x 2 x L x N uint64 in coefficient form
+ * (canonical residues, [ct][poly][limb][coeff]) and for a secret key its N
+ * int8 coefficients in {-1, 0, 1}.  All four calls synchronise `stream`.
+ * pdq_cts_export: cts dev [count][2][L][N] (NTT form, unchanged); out_host
+ *   of at least pdq_cts_serialized_bytes(count) bytes; ws dev, count*2*L*N
+ *   words of scratch.  Too small output -> PDQ_E_NOMEM.
+ * pdq_cts_import: in_host as written by pdq_cts_export; cts_out dev room for
+ *   cap ciphertexts (NTT form on return); *count = the header's count.
+ *   PDQ_E_PARAM for a wrong magic, version, N, L, t or first prime, a short
+ *   buffer or a non-canonical residue; PDQ_E_NOMEM if count > cap.
+ * pdq_sk_export: sk dev [L+K][N] from pdq_secret_prepare; ws dev, N words.
+ *   PDQ_E_PARAM if the secret is not ternary.
+ * pdq_sk_import: sk_out dev [L+K][N], the pdq_secret_prepare form. */
+size_t pdq_cts_serialized_bytes(const pdq_ctx* ctx, uint32_t count);
+int pdq_cts_export(const pdq_ctx* ctx, const uint64_t* cts, uint32_t count, void* out_host,
+                   size_t out_bytes, uint64_t* ws, void* stream);
+int pdq_cts_import(const pdq_ctx* ctx, const void* in_host, size_t in_bytes, uint64_t* cts_out,
+                   uint32_t cap, uint32_t* count, void* stream);
+size_t pdq_sk_serialized_bytes(const pdq_ctx* ctx);
+int pdq_sk_export(const pdq_ctx* ctx, const uint64_t* sk, void* out_host, size_t out_bytes,
+                  uint64_t* ws, void* stream);
+int pdq_sk_import(const pdq_ctx* ctx, const void* in_host, size_t in_bytes, uint64_t* sk_out,
+                  void* stream);
 
 /* ------------------------------------------------- rotation without alloc
  * The paper has no counterpart to this call: it exists for callers that

@@ -71,15 +71,25 @@ def make_plan(par: Params, n: int, s: int, B: int | None = None) -> Plan:
     s_prime = 1 << math.ceil(math.log2(s))
     if s_prime > par.m or s_prime >= par.t:
         raise ValueError("sparsity too large for the ring")
-    if B is None:
-        B = 1 << math.ceil(math.log2(s_prime) / 2)
-    if B < 1 or s_prime % B:
-        raise ValueError("B must divide s'")
     J = -(-n // par.N)
     H = 2 * J
     G_sz = par.N * ((par.t - 1) // par.N)
     hpg = G_sz // par.m
     G = -(-H // hpg)
+    if B is None:
+        # baby/giant split (the paper leaves it open): among the powers of two
+        # B <= min(s', 128) with at most 32 giant steps, the one with the least
+        # work H(B-1) + 8 G(s'/B - 1) + 3 G s'/B (hoisted baby rotations,
+        # giant-step key switches, accumulator ModDowns); ties to the smaller B
+        costs = {}
+        b = 1
+        while b <= min(s_prime, 128):
+            if s_prime // b <= 32:
+                costs[b] = H * (b - 1) + 8 * G * (s_prime // b - 1) + 3 * G * (s_prime // b)
+            b *= 2
+        B = min(costs, key=lambda k: (costs[k], k))
+    if B < 1 or s_prime % B:
+        raise ValueError("B must divide s'")
     per_out = par.m // s_prime
     n_out = -(-G // per_out)
     return Plan(n, s, s_prime, B, J, H, G_sz, hpg, G, per_out, n_out)
@@ -251,9 +261,9 @@ def ring_dot_ext(par: Params, pts, cts) -> np.ndarray:
 
 
 def giant_accumulators(par: Params, R, plan: Plan):
-    """acc[gamma][g] = ModDown( sum_{h in gamma} sum_{a<B} Rot(D_{h,gB+a}; -gB) . R[h][a] ),
-    the products summed over Q u P (diagonals lifted to every prime) and
-    lowered to Q once per accumulator."""
+    """acc[gamma][g] = sum_{h in gamma} sum_{a<B} Rot(D_{h,gB+a}; -gB) . R[h][a],
+    the products summed over Q u P (diagonals lifted to every prime); the
+    accumulators stay in Q u P (giant_steps lowers the ones it rotates)."""
     acc = []
     for gamma in range(plan.G):
         row = []
@@ -265,21 +275,23 @@ def giant_accumulators(par: Params, R, plan: Plan):
                                   -g * plan.B)
                     pts.append(lift(par, encode(par, d), par.ext))
                     cts.append(R[h][a])
-            row.append(ct_mod_down(par, ring_dot_ext(par, pts, cts)))
+            row.append(ring_dot_ext(par, pts, cts))
         acc.append(row)
     return acc
 
 
 def giant_steps(par: Params, acc, keys, plan: Plan):
-    """y_gamma = ModDown( (P acc[gamma][0]) + sum_{g>=1} Rot(acc[gamma][g]; gB) ),
-    each giant rotation kept in Q u P and the sum lowered to Q once."""
+    """y_gamma = ModDown( acc[gamma][0] + sum_{g>=1} Rot(ModDown(acc[gamma][g]); gB) ),
+    acc over Q u P: the unrotated accumulator joins the sum as it is, the
+    others are lowered to Q for their key switch, each giant rotation is kept
+    in Q u P, and the sum is lowered to Q once."""
     el = list(range(par.L + par.K))
     ys = []
     for gamma in range(plan.G):
-        y = ct_times_P(par, acc[gamma][0])
+        y = acc[gamma][0]
         for g in range(1, plan.giants):
             k = par.galois_rot(g * plan.B)
-            ct = acc[gamma][g]
+            ct = ct_mod_down(par, acc[gamma][g])
             r = rotate_ext(par, ct, mod_up_all(par, ct[1]), k, keys[k])
             y = np.stack([poly_add(par, y[0], r[0], el), poly_add(par, y[1], r[1], el)])
         ys.append(ct_mod_down(par, y))

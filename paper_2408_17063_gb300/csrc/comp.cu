@@ -35,14 +35,25 @@ int plan_make(const Ctx& c, u64 n, u32 s, u32 B, pdq_plan* pl) {
     std::memset(pl, 0, sizeof(*pl));
     const u64 sp = 1ull << ceil_log2(s);
     if (sp > c.m || sp >= c.t) return fail(PDQ_E_PARAM, "plan: sparsity too large for the ring");
-    if (B == 0) B = 1u << ((ceil_log2(sp) + 1) / 2);
-    if (sp % B != 0 || B > 128) return fail(PDQ_E_PARAM, "plan: B must divide s' and be at most 128");
     const u64 J = (n + c.N - 1) / c.N;
     if (J > (1u << 20)) return fail(PDQ_E_PARAM, "plan: too many records");
     const u64 G_sz = (u64)c.N * ((c.t - 1) / c.N);
     const u64 hpg = G_sz / c.m;
     const u64 H = 2 * J;
     const u64 G = (H + hpg - 1) / hpg;
+    if (B == 0) {
+        // the power of two minimising the work of the baby/giant split:
+        // H (B-1) hoisted baby rotations, G (s'/B - 1) giant-step key
+        // switches and G s'/B accumulator ModDowns, weighted 1 : 8 : 3
+        u64 best = ~0ull;
+        for (u64 b = 1; b <= sp && b <= 128; b *= 2) {
+            const u64 gi = sp / b;
+            if (gi > 32) continue;
+            const u64 cost = H * (b - 1) + 8 * G * (gi - 1) + 3 * G * gi;
+            if (cost < best) { best = cost; B = (u32)b; }
+        }
+    }
+    if (sp % B != 0 || B > 128) return fail(PDQ_E_PARAM, "plan: B must divide s' and be at most 128");
     const u64 per_out = c.m / sp;
     pl->n = n;
     pl->s = s;
@@ -101,12 +112,12 @@ size_t comp_ws_bytes(const Ctx& c, const pdq_plan& pl) {
     const u64 cts = ct_elems(c), ects = 2ull * (c.L + c.K) * c.N;
     const u64 U = (u64)pl.H * cts;                       // packed u_h over Q
     const u64 Rx = (u64)pl.H * pl.B * ects;              // baby steps over Q u P
-    const u64 accx = (u64)pl.G * pl.giants * ects;       // accumulators over Q u P
-    const u64 acc = (u64)pl.G * pl.giants * cts;         // ... lowered to Q
-    const u64 yx = (u64)pl.G * ects;                     // giant-step sums over Q u P
+    const u64 accx = (u64)pl.G * (pl.giants - 1) * ects; // accumulators g >= 1 over Q u P
+    const u64 acc = (u64)pl.G * (pl.giants - 1) * cts;   // ... lowered to Q
+    const u64 yx = (u64)pl.G * ects;                     // giant-step sums over Q u P (from g = 0)
     const u64 ys = 2ull * pl.G * cts;                    // rotate-and-sum ping-pong
     const u32 cnt = std::max(pl.H, pl.G);
-    const size_t scratch = std::max({apply_ws(c, cnt), mod_down_ws(c, pl.G * pl.giants)});
+    const size_t scratch = std::max({apply_ws(c, cnt), mod_down_ws(c, std::max(1u, pl.G * (pl.giants - 1)))});
     return (U + Rx + accx + acc + yx + ys) * sizeof(u64) + raise_ws(c, cnt) + scratch;
 }
 
@@ -119,8 +130,8 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     u64* U = reinterpret_cast<u64*>(ws);
     u64* Rx = U + (u64)H * cts;
     u64* accx = Rx + (u64)H * B * ects;
-    u64* acc = accx + (u64)G * GI * ects;
-    u64* yx = acc + (u64)G * GI * cts;
+    u64* acc = accx + (u64)G * (GI - 1) * ects;
+    u64* yx = acc + (u64)G * (GI - 1) * cts;
     u64* Y0 = yx + (u64)G * ects;
     u64* Y1 = Y0 + (u64)G * cts;
     u64* rws = Y1 + (u64)G * cts;
@@ -160,19 +171,19 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
         }
         PDQ_TRY(baby_steps_ext(c, D, u, H, B, keys.base, koff, Rx, st));
     }
-    // 3. diagonal multiply-accumulate over Q u P, one ModDown per accumulator
+    // 3. diagonal multiply-accumulate over Q u P: the unrotated accumulators
+    // (g = 0) start the giant-step sums yx, the others get one ModDown each
     prof_mark(c, PDQ_STAGE_MAC, st);
-    PDQ_TRY(diag_mac(c, pl, Rx, Dg, accx, st));
+    PDQ_TRY(diag_mac(c, pl, Rx, Dg, yx, accx, st));
     prof_mark(c, PDQ_STAGE_ACC_MODDOWN, st);
-    PDQ_TRY(mod_down_batch(c, accx, G * GI, ct_set(acc, cts), aws, st));
+    if (GI > 1) PDQ_TRY(mod_down_batch(c, accx, G * (GI - 1), ct_set(acc, cts), aws, st));
     // 4. giant steps: sum over Q u P, one ModDown per group
     prof_mark(c, PDQ_STAGE_GIANT, st);
-    PDQ_TRY(times_P(c, ct_set(acc, (long long)GI * cts), G, ct_set(yx, ects), false, st));
     for (u32 g = 1; g < GI; ++g) {
         const u64 k = galois_rot(c, (long long)g * B);
         const u64* kp;
         PDQ_TRY(key_for(k, &kp));
-        const CtSet in = ct_set(acc + (u64)g * cts, (long long)GI * cts);
+        const CtSet in = ct_set(acc + (u64)(g - 1) * cts, (long long)(GI - 1) * cts);
         PDQ_TRY(ks_raise(c, in, G, rws, &D, st));
         PDQ_TRY(ks_apply_ext(c, D, in, G, (u32)k, kp, ct_set(yx, ects), true, false, st));
     }

@@ -630,6 +630,7 @@ __global__ void k_moddown_final(const u64* __restrict__ A, const u64* __restrict
 
 // Diagonal multiply-accumulate (the Pegasus inner sum):
 //   acc[gamma][g][p][l][x] = sum_{hh} sum_{a<B} Dg[hh][a][l][x][g] * R[gamma hpg + hh][a][p][l][x]
+// (giant index g = 0 is written to acc0[gamma][p], the others to acc[gamma][g-1][p])
 //
 // Arithmetic: residues are < 2^60, split into 30-bit halves v = v0 + v1 2^30
 // (both operands arrive stored as v0 | v1 << 32, see split30).  A product is
@@ -702,6 +703,7 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
                                                   const u64* __restrict__ Dg, MacArgs a,
                                                   const Mod* __restrict__ mods,
                                                   const u64* __restrict__ c6090,
+                                                  u64* __restrict__ acc0,
                                                   u64* __restrict__ acc) {
     extern __shared__ __align__(16) u64 smem[];
     const u32 X = 1u << a.logX, GI = a.GI, GIp = GI + 2, CPC = a.CPC;
@@ -827,10 +829,13 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
                 const u64 pos = ((u64)l << a.logN) + ((u64)(tile0 + ctt) << a.logX) + xi;
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
-                    u64* o = acc + (((u64)gam * GI + g0) * 2 + p) * LN + pos;
 #pragma unroll
-                    for (int g = 0; g < GT; ++g)
-                        o[(u64)g * 2 * LN] = fold5(A[p][g], md, c6090 + 4 * l);
+                    for (int g = 0; g < GT; ++g) {
+                        const u32 gi = g0 + g;
+                        u64* o = gi == 0 ? acc0 + ((u64)gam * 2 + p) * LN + pos
+                                         : acc + (((u64)gam * (GI - 1) + gi - 1) * 2 + p) * LN + pos;
+                        *o = fold5(A[p][g], md, c6090 + 4 * l);
+                    }
                 }
             }
 #pragma unroll
@@ -1258,7 +1263,7 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN) {
 
 template <int GT, int BC>
 int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R, const u64* Dg,
-               u64* acc, cudaStream_t st) {
+               u64* acc0, u64* acc, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
         if (cudaFuncSetAttribute(k_diag_mac<GT, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1281,34 +1286,34 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
     a.tiles_per_cta = s.tiles_per_cta;
     a.achunks = pl.B / BC;
     const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, a.E, s.zslices);
-    k_diag_mac<GT, BC><<<grid, s.threads, s.smem, st>>>(R, Dg, a, c.d_mods, c.d_c6090, acc);
+    k_diag_mac<GT, BC><<<grid, s.threads, s.smem, st>>>(R, Dg, a, c.d_mods, c.d_c6090, acc0, acc);
     return launched("k_diag_mac");
 }
 
 template <int GT>
 int launch_mac_bc(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R,
-                  const u64* Dg, u64* acc, cudaStream_t st) {
+                  const u64* Dg, u64* acc0, u64* acc, cudaStream_t st) {
     switch (s.Bc) {
-        case 1: return launch_mac<GT, 1>(c, pl, s, R, Dg, acc, st);
-        case 2: return launch_mac<GT, 2>(c, pl, s, R, Dg, acc, st);
-        case 4: return launch_mac<GT, 4>(c, pl, s, R, Dg, acc, st);
-        case 8: return launch_mac<GT, 8>(c, pl, s, R, Dg, acc, st);
-        case 16: return launch_mac<GT, 16>(c, pl, s, R, Dg, acc, st);
+        case 1: return launch_mac<GT, 1>(c, pl, s, R, Dg, acc0, acc, st);
+        case 2: return launch_mac<GT, 2>(c, pl, s, R, Dg, acc0, acc, st);
+        case 4: return launch_mac<GT, 4>(c, pl, s, R, Dg, acc0, acc, st);
+        case 8: return launch_mac<GT, 8>(c, pl, s, R, Dg, acc0, acc, st);
+        case 16: return launch_mac<GT, 16>(c, pl, s, R, Dg, acc0, acc, st);
         default: return fail(PDQ_E_PARAM, "diag_mac: baby-step count must be a power of two");
     }
 }
 
 }  // namespace
 
-int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc,
+int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc0, u64* acc,
              cudaStream_t st) {
     const MacShape s = mac_shape(pl, c.log_n);
     if (s.zslices > 65535) return fail(PDQ_E_PARAM, "diag_mac: too many groups");
     if (s.logX < 1 || s.smem > (100u << 10)) return fail(PDQ_E_PARAM, "diag_mac: plan too large for one tile");
     switch (s.GT) {
-        case 1: return launch_mac_bc<1>(c, pl, s, R, Dg, acc, st);
-        case 2: return launch_mac_bc<2>(c, pl, s, R, Dg, acc, st);
-        case 4: return launch_mac_bc<4>(c, pl, s, R, Dg, acc, st);
+        case 1: return launch_mac_bc<1>(c, pl, s, R, Dg, acc0, acc, st);
+        case 2: return launch_mac_bc<2>(c, pl, s, R, Dg, acc0, acc, st);
+        case 4: return launch_mac_bc<4>(c, pl, s, R, Dg, acc0, acc, st);
         default: return fail(PDQ_E_PARAM, "diag_mac: giant-step count must be a power of two");
     }
 }

@@ -83,8 +83,9 @@ int mod_down_batch(const Ctx& c, u64* A, u32 cnt, CtSet out, u64* ws, cudaStream
 
 int gather_rows(CtSet src, long long src_off, u32 cnt, u64 len, u64* dst, u64 dst_stride,
                 cudaStream_t st);
-// R and Dg in the split operand layout; acc canonical
-int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc,
+// R and Dg in the split operand layout; outputs canonical over Q u P:
+// giant index 0 to acc0 [G][2][L+K][N], the others to acc [G][giants-1][2][L+K][N]
+int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc0, u64* acc,
              cudaStream_t st);
 int ct_add(const Ctx& c, CtSet y, CtSet x, u32 cnt, cudaStream_t st);
 int group_combine(const Ctx& c, const pdq_plan& pl, const u64* y, const u64* masks, u64* out,

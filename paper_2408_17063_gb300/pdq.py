@@ -111,6 +111,12 @@ _SIGS = {
     "pdq_server_wait": (_I, [_P, _U64, _U32]),
     "pdq_server_drain": (_I, [_P, _U32]),
     "pdq_server_destroy": (_I, [_P]),
+    "pdq_cts_serialized_bytes": (_SZ, [_P, _U32]),
+    "pdq_cts_export": (_I, [_P, _P, _U32, _P, _SZ, _P, _P]),
+    "pdq_cts_import": (_I, [_P, _P, _SZ, _P, _U32, ctypes.POINTER(_U32), _P]),
+    "pdq_sk_serialized_bytes": (_SZ, [_P]),
+    "pdq_sk_export": (_I, [_P, _P, _P, _SZ, _P, _P]),
+    "pdq_sk_import": (_I, [_P, _P, _SZ, _P, _P]),
     "pdq_rotate_noalloc_max_bytes": (_SZ, []),
     "pdq_rotate_noalloc": (_I, [_P, _P, _U32, _U64, _P, _P, _P]),
     "pdq_profile_enable": (_I, [_P, _I]),
@@ -273,6 +279,38 @@ class Context:
         _check(lib.pdq_decrypt(self.h, _ptr(sk), _ptr(ct), count, _ptr(out), _ptr(ws),
                                ws.numel(), _stream(stream)))
         return out.view(count, self.N)
+
+    # exchange format (host bytes)
+    def cts_export(self, ct, stream=None) -> bytes:
+        count = ct.numel() // self.ct_elems
+        lib = load()
+        nbytes = lib.pdq_cts_serialized_bytes(self.h, count)
+        buf = ctypes.create_string_buffer(nbytes)
+        ws = self._u64(max(count * self.ct_elems, 1))
+        _check(lib.pdq_cts_export(self.h, _ptr(ct), count, buf, nbytes, _ptr(ws), _stream(stream)))
+        return buf.raw
+
+    def cts_import(self, data: bytes, stream=None) -> torch.Tensor:
+        lib = load()
+        hdr_count = int.from_bytes(data[20:24], "little") if len(data) >= 24 else 0
+        out = self._u64(max(hdr_count * self.ct_elems, 1))
+        cnt = _U32()
+        _check(lib.pdq_cts_import(self.h, data, len(data), _ptr(out), hdr_count,
+                                  ctypes.byref(cnt), _stream(stream)))
+        return out[:cnt.value * self.ct_elems].view(cnt.value, 2, self.L, self.N)
+
+    def sk_export(self, sk, stream=None) -> bytes:
+        lib = load()
+        nbytes = lib.pdq_sk_serialized_bytes(self.h)
+        buf = ctypes.create_string_buffer(nbytes)
+        ws = self._u64(self.N)
+        _check(lib.pdq_sk_export(self.h, _ptr(sk), buf, nbytes, _ptr(ws), _stream(stream)))
+        return buf.raw
+
+    def sk_import(self, data: bytes, stream=None) -> torch.Tensor:
+        out = self._u64(self.E * self.N)
+        _check(load().pdq_sk_import(self.h, data, len(data), _ptr(out), _stream(stream)))
+        return out.view(self.E, self.N)
 
     def rotate(self, ct, galois: int, key, stream=None) -> torch.Tensor:
         count = ct.numel() // self.ct_elems
