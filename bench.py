@@ -422,7 +422,9 @@ def run_batched(args, mix) -> dict:
             "speedup": t_plain / t_graph, "all_decompress_exactly": bool(ok),
             "peak_device_gib": torch.cuda.max_memory_allocated() / 2**30,
             "mix": "64 queries, N uniform in {2^13, 2^14, 2^15}, log2 n uniform in 12..20, "
-                   "s uniform in [1, min(1024, n/16)], own key set per query"}
+                   "s uniform in [1, min(1024, n/16)], "
+                   + (f"{mix.clients} clients sharing secret and keys per ring" if mix.clients
+                      else "own key set per query")}
 
 
 def run_served(args, mix) -> list:

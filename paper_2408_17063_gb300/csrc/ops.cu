@@ -698,8 +698,8 @@ struct MacArgs {
     u32 tiles_per_cta, achunks;
 };
 
-template <int GT, int BC>
-__global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
+template <int GT, int BC, int PC>
+__global__ void __launch_bounds__(256, PC == 1 ? 3 : 2) k_diag_mac(const u64* __restrict__ R,
                                                   const u64* __restrict__ Dg, MacArgs a,
                                                   const Mod* __restrict__ mods,
                                                   const u64* __restrict__ c6090,
@@ -721,8 +721,7 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
     const u32 dwords = BC * X * GIp, rwords = CPC * RB;
     const u32 stage = dwords + rwords;
 
-    const u32 gam = (cbase >> 1) + ct;             // group of this thread's two combinations
-    const bool ok = 2 * ct < CPC && gam < a.G;
+    const u32 c0 = PC * ct;                        // first combination of this thread (in slice)
 
     const u32 spt = hpg_eff * a.achunks;           // steps per position tile
     const u32 steps = spt * a.tiles_per_cta;
@@ -766,9 +765,9 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
         cp_async_commit();
     };
 
-    Acc5 A[2][GT];
+    Acc5 A[PC][GT];
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < PC; ++p)
 #pragma unroll
         for (int g = 0; g < GT; ++g) A[p][g] = Acc5{0, 0, 0, 0, 0};
 
@@ -793,7 +792,7 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
         }
         __syncthreads();
         const u64* D = smem + buf * stage + xi * GIp + g0;
-        const u64* Rt = smem + buf * stage + dwords + (2 * ct) * RB + xi;
+        const u64* Rt = smem + buf * stage + dwords + c0 * RB + xi;
 #pragma unroll
         for (int ai = 0; ai < BC; ++ai) {
             u64 d[GT];
@@ -807,39 +806,45 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
             } else {
                 d[0] = D[ai * X * GIp];
             }
-            const u64 r0 = Rt[ai * X], r1 = Rt[RB + ai * X];
-            const u32 r00 = (u32)r0, r01 = (u32)(r0 >> 32);
-            const u32 r10 = (u32)r1, r11 = (u32)(r1 >> 32);
+            u32 rl[PC], rh[PC];
+#pragma unroll
+            for (int p = 0; p < PC; ++p) {
+                const u64 r = Rt[p * RB + ai * X];
+                rl[p] = (u32)r;
+                rh[p] = (u32)(r >> 32);
+            }
 #pragma unroll
             for (int g = 0; g < GT; ++g) {
                 const u32 d0 = (u32)d[g], d1 = (u32)(d[g] >> 32);
-                mac4(A[0][g], r00, r01, d0, d1);
-                mac4(A[1][g], r10, r11, d0, d1);
+#pragma unroll
+                for (int p = 0; p < PC; ++p) mac4(A[p][g], rl[p], rh[p], d0, d1);
             }
         }
         // at most 16 terms since the last renormalisation (BC <= 16)
 #pragma unroll
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < PC; ++p)
 #pragma unroll
             for (int g = 0; g < GT; ++g) renorm5(A[p][g]);
         const bool tile_end = (cac + 1 == a.achunks) && (chh + 1 == hpg_eff);
         if (tile_end) {                            // last step of this position tile
-            if (ok) {
-                const Mod md = mods[l];
-                const u64 pos = ((u64)l << a.logN) + ((u64)(tile0 + ctt) << a.logX) + xi;
 #pragma unroll
-                for (int p = 0; p < 2; ++p) {
+            for (int p = 0; p < PC; ++p) {
+                const u32 combo = cbase + c0 + p;          // (gamma, polynomial)
+                const u32 gam = combo >> 1, poly = combo & 1;
+                if (c0 + p < CPC && gam < a.G) {
+                    const Mod md = mods[l];
+                    const u64 pos = ((u64)l << a.logN) + ((u64)(tile0 + ctt) << a.logX) + xi;
 #pragma unroll
                     for (int g = 0; g < GT; ++g) {
                         const u32 gi = g0 + g;
-                        u64* o = gi == 0 ? acc0 + ((u64)gam * 2 + p) * LN + pos
-                                         : acc + (((u64)gam * (GI - 1) + gi - 1) * 2 + p) * LN + pos;
+                        u64* o = gi == 0 ? acc0 + ((u64)gam * 2 + poly) * LN + pos
+                                         : acc + (((u64)gam * (GI - 1) + gi - 1) * 2 + poly) * LN + pos;
                         *o = fold5(A[p][g], md, c6090 + 4 * l);
                     }
                 }
             }
 #pragma unroll
-            for (int p = 0; p < 2; ++p)
+            for (int p = 0; p < PC; ++p)
 #pragma unroll
                 for (int g = 0; g < GT; ++g) A[p][g] = Acc5{0, 0, 0, 0, 0};
         }
@@ -1220,25 +1225,27 @@ u32 log2u(u32 x) {
     return r;
 }
 
-// Launch shape of k_diag_mac: up to 4 giant indices and both polynomials of
-// one group per thread, up to 16 groups per CTA (more go to further
-// z-slices), X >= 2 positions so that a CTA has up to 256 threads (two CTAs
-// per SM, whose staging barriers are independent, so one CTA's copy issue
-// and renormalisation overlap the other's products), and an a-chunk BC (up
-// to 16) that keeps the two staged (diagonal + rotated) tiles within 100 KB
-// of shared memory.
+// Launch shape of k_diag_mac: up to 4 giant indices and kMacPC polynomials
+// of a group per thread (two: each staged value feeds 8 products; one
+// polynomial per thread, with three CTAs per SM, measured 9% slower), up to
+// 32 combinations per CTA (more go to further z-slices), X >= 2 positions so
+// that a CTA has up to 256 threads (two CTAs per SM), and an a-chunk BC (up
+// to 16) that keeps the two staged (diagonal + rotated) tiles within
+// kMacSmem of shared memory.
 constexpr u32 kMacThreads = 256;
+constexpr u32 kMacPC = 2;                // polynomials (of one group) per thread
+constexpr u32 kMacSmem = 100u << 10;     // two CTAs per SM
 MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     MacShape s{};
     const u32 GI = pl.giants, combos = 2 * pl.G;
     s.GT = GI < 4 ? GI : 4;
     const u32 GS = GI / s.GT;
     s.logGS = log2u(GS);
-    u32 ct = combos / 2;
+    u32 ct = (combos + kMacPC - 1) / kMacPC;       // threads along the combinations
     u32 ct_max = kMacThreads / 2 / GS;
-    if (ct_max > 16) ct_max = 16;
+    if (ct_max > 32) ct_max = 32;
     if (ct > ct_max) ct = 1u << log2u(ct_max);
-    s.combos_per_cta = ct * 2;
+    s.combos_per_cta = ct * kMacPC;
     s.zslices = (combos + s.combos_per_cta - 1) / s.combos_per_cta;
     u32 logX = 1;
     while (((ct * GS) << (logX + 1)) <= kMacThreads && logX < 8) ++logX;
@@ -1247,7 +1254,7 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     auto bytes = [&](u32 bc, u32 lx) {
         return 2 * ((size_t)bc * (1u << lx) * (GI + 2 + s.combos_per_cta) + 2 * s.combos_per_cta) * 8;
     };
-    while (bytes(Bc, logX) > (100u << 10)) {
+    while (bytes(Bc, logX) > kMacSmem) {
         if (Bc > 1) Bc /= 2; else if (logX > 1) --logX; else break;
     }
     s.logX = logX;
@@ -1266,8 +1273,8 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
                u64* acc0, u64* acc, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
-        if (cudaFuncSetAttribute(k_diag_mac<GT, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 100 << 10) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_diag_mac<GT, BC, kMacPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMacSmem) != cudaSuccess)
             return cuda_check("k_diag_mac attribute");
         configured = true;
     }
@@ -1286,7 +1293,8 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
     a.tiles_per_cta = s.tiles_per_cta;
     a.achunks = pl.B / BC;
     const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, a.E, s.zslices);
-    k_diag_mac<GT, BC><<<grid, s.threads, s.smem, st>>>(R, Dg, a, c.d_mods, c.d_c6090, acc0, acc);
+    k_diag_mac<GT, BC, kMacPC><<<grid, s.threads, s.smem, st>>>(R, Dg, a, c.d_mods, c.d_c6090, acc0,
+                                                                 acc);
     return launched("k_diag_mac");
 }
 
@@ -1309,7 +1317,7 @@ int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64*
              cudaStream_t st) {
     const MacShape s = mac_shape(pl, c.log_n);
     if (s.zslices > 65535) return fail(PDQ_E_PARAM, "diag_mac: too many groups");
-    if (s.logX < 1 || s.smem > (100u << 10)) return fail(PDQ_E_PARAM, "diag_mac: plan too large for one tile");
+    if (s.logX < 1 || s.smem > kMacSmem) return fail(PDQ_E_PARAM, "diag_mac: plan too large for one tile");
     switch (s.GT) {
         case 1: return launch_mac_bc<1>(c, pl, s, R, Dg, acc0, acc, st);
         case 2: return launch_mac_bc<2>(c, pl, s, R, Dg, acc0, acc, st);
