@@ -477,11 +477,12 @@ def run_served(args, mix) -> list:
 MAC_PEAK_PER_S = 152 * 2070e6 * 32 / 4
 MAC_CEILING_MEASURED = 2.02e12
 # DRAM bytes of one k_diag_mac launch from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the same plan with 3 primes (L=2, K=1), scaled by
-# 10/3 to the 10 primes of Q u P (every CTA works on one prime);
-# None when the kernel has changed since the capture.  Capture: 2.609 GB read +
-# 0.389 GB written per launch with 3 primes.
-MAC_TRAFFIC_BYTES = round((2.608506e9 + 0.389425e9) * 10 / 3)
+# dram__bytes_write.sum) on the same plan (B=32, 8 giant steps) with 3 primes
+# (L=2, K=1), scaled by 10/3 to the 10 primes of Q u P (every CTA works on
+# one prime); None when the kernel has changed since the capture.  Capture:
+# 4.027 GB read + 0.201 GB written per launch with 3 primes.
+MAC_TRAFFIC_BYTES = round((4.027170e9 + 0.200594e9) * 10 / 3)
+MAC_TRAFFIC_PLAN = (2**15, 10, 64, 32, 8)       # N, primes, H, B, giant steps
 
 
 def mac_roofline(ctx, plan, ms):
@@ -494,7 +495,7 @@ def mac_roofline(ctx, plan, ms):
     return {"kernel": "k_diag_mac", "bound": "alu", "achieved": achieved / 1e12,
             "peak": MAC_PEAK_PER_S / 1e12, "unit": "T modmac/s", "frac": achieved / MAC_PEAK_PER_S,
             "frac_of_measured_ceiling": achieved / MAC_CEILING_MEASURED,
-            "traffic": MAC_TRAFFIC_BYTES if (N, E, plan.H, plan.B, plan.giants) == (2**15, 10, 64, 16, 16)
+            "traffic": MAC_TRAFFIC_BYTES if (N, E, plan.H, plan.B, plan.giants) == MAC_TRAFFIC_PLAN
             else None, "algorithmic_bytes": algo_bytes,
             "macs_per_launch": macs, "ms_per_launch": ms,
             "timing": "CUDA events recorded on the launching stream around each launch",

@@ -84,6 +84,9 @@ Mod make_mod(u64 q) {
     m.ratio = (u64)(((u128)1 << 64) / q);
     m.r64 = (u64)(((u128)1 << 64) % q);
     m.r64_shoup = shoup_of(m.r64, q);
+    u64 inv = q;                                   // q^-1 mod 2^64 by Newton (q odd)
+    for (int i = 0; i < 6; ++i) inv *= 2 - q * inv;
+    m.qinv = (u64)0 - inv;
     return m;
 }
 
@@ -156,7 +159,8 @@ static void free_ctx(Ctx* c) {
                     c->d_up_hatmod, c->d_up_hatmod_shoup, c->d_dn_hatinv,
                     c->d_dn_hatinv_shoup, c->d_dn_hatmod, c->d_dn_hatmod_shoup,
                     c->d_dn_pinv, c->d_dn_pinv_shoup, c->d_P_mod_q, c->d_P_mod_q_shoup, c->d_delta_mod_q,
-                    c->d_dec_omega, c->d_dec_omega_shoup, c->d_c6090};
+                    c->d_dec_omega, c->d_dec_omega_shoup, c->d_c6090,
+                    c->d_up_hatmod_mont, c->d_up_hatmod_mont_shoup, c->d_P_mont};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
@@ -207,6 +211,11 @@ static int build_ctx(const pdq_params& p, Ctx* c) {
     }
     c->ndigits = (u32)c->digit_limbs.size();
     if (c->alpha > 8) return fail(PDQ_E_PARAM, "at most 8 primes per key-switching digit");
+    // key inner products sum ndigits + 1 products below q^2 and end with a
+    // Montgomery reduction, which needs the sum below q 2^64
+    for (u32 i = 0; i < p.L + p.K; ++i)
+        if ((u128)(c->ndigits + 1) * c->mods[i] >= ((u128)1 << 64))
+            return fail(PDQ_E_PARAM, "too many key-switching digits for the prime size");
 
     // slot root
     u64 g = 0;
@@ -314,6 +323,16 @@ static int build_ctx(const pdq_params& p, Ctx* c) {
         for (u32 r = 0; r < E; ++r)
             up_mod_s[(size_t)i * E + r] = shoup_of(up_mod[(size_t)i * E + r], c->mods[r]);
     PDQ_TRY(upload(&c->d_up_hatmod_shoup, up_mod_s));
+    std::vector<u64> up_mont(up_mod.size()), up_mont_s(up_mod.size());
+    for (u32 i = 0; i < L; ++i)
+        for (u32 r = 0; r < E; ++r) {
+            const u64 qr = c->mods[r];
+            const u64 R = (u64)(((u128)1 << 64) % qr);
+            up_mont[(size_t)i * E + r] = mulmod_h(up_mod[(size_t)i * E + r], R, qr);
+            up_mont_s[(size_t)i * E + r] = shoup_of(up_mont[(size_t)i * E + r], qr);
+        }
+    PDQ_TRY(upload(&c->d_up_hatmod_mont, up_mont));
+    PDQ_TRY(upload(&c->d_up_hatmod_mont_shoup, up_mont_s));
 
     // ModDown constants
     std::vector<u64> dn_inv(K), dn_inv_s(K), dn_mod((size_t)K * L), pinv(L), pinv_s(L);
@@ -355,6 +374,10 @@ static int build_ctx(const pdq_params& p, Ctx* c) {
     std::vector<u64> pq_s(L);
     for (u32 i = 0; i < L; ++i) pq_s[i] = shoup_of(c->P_mod_q[i], c->mods[i]);
     PDQ_TRY(upload(&c->d_P_mod_q_shoup, pq_s));
+    std::vector<u64> pm(L);
+    for (u32 i = 0; i < L; ++i)
+        pm[i] = mulmod_h(c->P_mod_q[i], (u64)(((u128)1 << 64) % c->mods[i]), c->mods[i]);
+    PDQ_TRY(upload(&c->d_P_mont, pm));
 
     // Delta = floor(Q/t): Q = t*Delta + (Q mod t) and Q = 0 mod q_i, so
     // Delta = -(Q mod t) * t^{-1} mod q_i.

@@ -269,9 +269,10 @@ __global__ void k_mask(const u64* __restrict__ v, const u64* __restrict__ db,
 // ---------------------------------------------------------- key switching --
 
 // Raise digit b = blockIdx.y of c1 (coefficient form X [cnt][L][N]) of
-// ciphertext blockIdx.z to the extended basis: D[ct][b][r] for r outside
-// the digit (coefficient form, transformed afterwards); inside the digit
-// the NTT-form c1 limb is copied.  Two adjacent positions per thread
+// ciphertext blockIdx.z to the extended basis, multiplied by R = 2^64 mod r
+// (so that the key inner products end with a Montgomery reduction): D[ct][b][r]
+// for r outside the digit (coefficient form, transformed afterwards; hmod
+// carries the factor R); inside the digit the NTT-form c1 limb times R.  Two adjacent positions per thread
 // (16-byte accesses); the digit's conversion constants (Q_b/q_i) mod r and
 // the target moduli are staged in shared memory.  ALPHA: primes per digit
 // (0: read from `alpha` at run time, at most 8).
@@ -315,8 +316,13 @@ __global__ void __launch_bounds__(256) k_modup(const u64* __restrict__ X, CtSet 
     for (u32 r = 0; r < E; ++r) {
         u64* o = Dc + ((u64)r << logN);
         if (r >= lo && r < hi) {
+            // the digit's own limb, multiplied by R = 2^64 mod q_r like the
+            // converted ones (whose constants carry the factor)
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(src + ((u64)r << logN));
+            const Mod mr = mods[r];
             *reinterpret_cast<ulonglong2*>(o) =
-                *reinterpret_cast<const ulonglong2*>(src + ((u64)r << logN));
+                make_ulonglong2(csub(mul_shoup_lazy(v.x, mr.r64, mr.r64_shoup, mr.q), mr.q),
+                                csub(mul_shoup_lazy(v.y, mr.r64, mr.r64_shoup, mr.q), mr.q));
             continue;
         }
         // products by the constants (Q_b/q_i) mod r, Shoup: each in [0, 2r),
@@ -364,11 +370,12 @@ __global__ void k_ks_inner(const u64* __restrict__ D, const u64* __restrict__ ke
         mac128(h1a, l1a, da, k1.x);
         mac128(h1b, l1b, db, k1.y);
     }
+    // the digits carry the factor R: one Montgomery reduction per output
     const Mod md = mods[l];
     *reinterpret_cast<ulonglong2*>(A + ct * 2 * EN + r) =
-        make_ulonglong2(reduce128(h0a, l0a, md), reduce128(h0b, l0b, md));
+        make_ulonglong2(redc128(h0a, l0a, md), redc128(h0b, l0b, md));
     *reinterpret_cast<ulonglong2*>(A + ct * 2 * EN + EN + r) =
-        make_ulonglong2(reduce128(h1a, l1a, md), reduce128(h1b, l1b, md));
+        make_ulonglong2(redc128(h1a, l1a, md), redc128(h1b, l1b, md));
 }
 
 // The rotation before its ModDown, in the extended basis: for output
@@ -378,9 +385,8 @@ __global__ void k_ks_inner(const u64* __restrict__ D, const u64* __restrict__ ke
 // with s = sigma_k; `accumulate` adds into out instead of overwriting it.
 __global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict__ key, u32 logN,
                                u32 E, u32 L, u32 nd, u32 galois, const Mod* __restrict__ mods,
-                               CtSet c0src, const u64* __restrict__ Pq,
-                               const u64* __restrict__ Pqs, CtSet out, u32 accumulate,
-                               u32 split) {
+                               CtSet c0src, const u64* __restrict__ Pm, CtSet out,
+                               u32 accumulate, u32 split) {
     const u32 r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const u64 EN = (u64)E << logN;
     if (r >= EN) return;
@@ -401,15 +407,17 @@ __global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict_
         mac128(h1a, l1a, da, k1.x);
         mac128(h1b, l1b, db, k1.y);
     }
-    const Mod md = mods[l];
-    u64 a0 = reduce128(h0a, l0a, md), b0 = reduce128(h0b, l0b, md);
-    u64 a1 = reduce128(h1a, l1a, md), b1 = reduce128(h1b, l1b, md);
+    // P sigma(c0) joins the sum as c0 times P R (the digits carry R), then one
+    // Montgomery reduction per output
     if (l < L) {
         const ulonglong2 cv = *reinterpret_cast<const ulonglong2*>(c0src.at(ct) + sr);
         const u64 ca = swap ? cv.y : cv.x, cb = swap ? cv.x : cv.y;
-        a0 = addmod(a0, csub(mul_shoup_lazy(ca, Pq[l], Pqs[l], md.q), md.q), md.q);
-        b0 = addmod(b0, csub(mul_shoup_lazy(cb, Pq[l], Pqs[l], md.q), md.q), md.q);
+        mac128(h0a, l0a, ca, Pm[l]);
+        mac128(h0b, l0b, cb, Pm[l]);
     }
+    const Mod md = mods[l];
+    u64 a0 = redc128(h0a, l0a, md), b0 = redc128(h0b, l0b, md);
+    u64 a1 = redc128(h1a, l1a, md), b1 = redc128(h1b, l1b, md);
     ulonglong2* o0 = reinterpret_cast<ulonglong2*>(out.at(ct) + r);
     ulonglong2* o1 = reinterpret_cast<ulonglong2*>(out.at(ct) + EN + r);
     if (accumulate) {
@@ -442,28 +450,28 @@ struct BabyParams {
     u64 koff[128];    // element offset of key a in the key buffer
 };
 
-template <int T, int HC, int CPT>
+template <int T, int HC, int CPT, int ND>
 __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
         const u64* __restrict__ D, CtSet u, const u64* __restrict__ keys, u32 H, u32 B, u32 logN,
-        u32 E, u32 L, u32 nd, const Mod* __restrict__ mods, const u64* __restrict__ Pq,
-        const u64* __restrict__ Pqs, u64* __restrict__ Rx, const BabyParams bp) {
+        u32 E, u32 L, const Mod* __restrict__ mods, const u64* __restrict__ Pm,
+        u64* __restrict__ Rx, const BabyParams bp) {
+    // The digit tile (and c0) of HC ciphertexts is staged in shared memory
+    // once and only read afterwards; every thread keeps the 2 ND key values of
+    // its position in registers, loaded one rotation ahead, so the rotation
+    // loop has no barrier.
     extern __shared__ __align__(16) u64 sm[];
-    const u32 KT = nd * 2 * T;          // words of one key tile
-    u64* Ds = sm;                       // [HC][nd][T]
-    u64* Cs = Ds + HC * nd * T;         // [HC][T]
-    u64* Ks = Cs + HC * T;              // [3][nd][2][T]: key tiles, three rotations in flight
+    u64* Ds = sm;                       // [HC][ND][T]
+    u64* Cs = Ds + HC * ND * T;         // [HC][T]
     const u32 y0 = blockIdx.x * T, r = blockIdx.y, h0 = blockIdx.z * HC;
     const u64 EN = (u64)E << logN;
     const u32 nthreads = T * HC / CPT;
     constexpr u32 TP = T / 2;           // 16-byte chunks per row of a tile
 
-    // the digits and c0 of this tile, 16-byte asynchronous copies (zero rows
-    // past the last ciphertext)
-    for (u32 e = threadIdx.x; e < HC * nd * TP; e += nthreads) {
-        const u32 yy = (e % TP) * 2, rest = e / TP, b = rest % nd, ct = rest / nd;
+    for (u32 e = threadIdx.x; e < HC * ND * TP; e += nthreads) {
+        const u32 yy = (e % TP) * 2, rest = e / TP, b = rest % ND, ct = rest / ND;
         const u32 h = h0 + ct;
-        cp_async16(Ds + (ct * nd + b) * T + yy,
-                   D + ((u64)(h < H ? h : 0) * nd + b) * EN + ((u64)r << logN) + y0 + yy, h < H);
+        cp_async16(Ds + (ct * ND + b) * T + yy,
+                   D + ((u64)(h < H ? h : 0) * ND + b) * EN + ((u64)r << logN) + y0 + yy, h < H);
     }
     if (r < L) {
         for (u32 e = threadIdx.x; e < HC * TP; e += nthreads) {
@@ -471,50 +479,53 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
             cp_async16(Cs + ct * T + yy, u.at(h < H ? h : 0) + ((u64)r << logN) + y0 + yy, h < H);
         }
     }
-    // key tile of rotation a (the positions x0 .. x0+T-1 whose sources lie in this tile)
-    auto issue_key = [&](u32 a, u32 buf) {
-        const u32 x0 = auto_index(y0, bp.kinv[a], logN) & ~(T - 1);
-        const u64* key = keys + bp.koff[a] + ((u64)r << logN) + x0;
-        u64* dst = Ks + buf * KT;
-        for (u32 e = threadIdx.x; e < nd * 2 * TP; e += nthreads) {
-            const u32 xx = (e % TP) * 2, bp2 = e / TP;    // bp2 = beta * 2 + p
-            cp_async16(dst + bp2 * T + xx, key + (u64)bp2 * EN + xx, true);
-        }
-        cp_async_commit();
-    };
-    issue_key(1, 0);                    // (one group with the tile above)
-    if (B > 2) issue_key(2, 1);
+    cp_async_commit();
 
     const Mod md = mods[r];
-    const u64 P = r < L ? Pq[r] : 0, Ps = r < L ? Pqs[r] : 0;
+    const u64 PR = r < L ? Pm[r] : 0;               // P 2^64 mod q_r
     const u32 xi = threadIdx.x % T, hg = threadIdx.x / T;
+    // key values of rotation a at this thread's position (the position whose
+    // source lies in this tile)
+    auto load_keys = [&](u32 a, u64 (&kv)[ND][2], u32& x) {
+        x = (auto_index(y0, bp.kinv[a], logN) & ~(T - 1)) + xi;
+        const u64* key = keys + bp.koff[a] + ((u64)r << logN) + x;
+#pragma unroll
+        for (int b = 0; b < ND; ++b) {
+            kv[b][0] = __ldg(key + (u64)(2 * b) * EN);
+            kv[b][1] = __ldg(key + (u64)(2 * b + 1) * EN);
+        }
+    };
+    u64 kc[ND][2], kn[ND][2];
+    u32 xc, xn = 0;
+    load_keys(1, kc, xc);
+    cp_async_wait<0>();
+    __syncthreads();
     for (u32 a = 1; a < B; ++a) {
-        if (a + 1 < B) cp_async_wait<1>(); else cp_async_wait<0>();
-        // key tile a (and the digit tile) visible; every thread is past
-        // rotation a-1, whose buffer (a+1) % 3 is refilled next
-        __syncthreads();
-        if (a + 2 < B) issue_key(a + 2, (a + 1) % 3);
-        const u64* Kt = Ks + ((a - 1) % 3) * KT;
-        const u32 x0 = auto_index(y0, bp.kinv[a], logN) & ~(T - 1);
-        const u32 x = x0 + xi;
-        const u32 y = auto_index(x, bp.k[a], logN) - y0;  // in [0, T)
+        if (a + 1 < B) load_keys(a + 1, kn, xn);
+        const u32 y = auto_index(xc, bp.k[a], logN) - y0;  // in [0, T)
 #pragma unroll
         for (int i = 0; i < CPT; ++i) {
             const u32 ct = hg * CPT + i, h = h0 + ct;
             if (h >= H) continue;
             u64 h0a = 0, l0a = 0, h1a = 0, l1a = 0;
-            for (u32 b = 0; b < nd; ++b) {
-                const u64 d = Ds[(ct * nd + b) * T + y];
-                mac128(h0a, l0a, d, Kt[(b * 2) * T + xi]);
-                mac128(h1a, l1a, d, Kt[(b * 2 + 1) * T + xi]);
+#pragma unroll
+            for (int b = 0; b < ND; ++b) {
+                const u64 d = Ds[(ct * ND + b) * T + y];
+                mac128(h0a, l0a, d, kc[b][0]);
+                mac128(h1a, l1a, d, kc[b][1]);
             }
-            u64 v0 = reduce128(h0a, l0a, md);
-            const u64 v1 = reduce128(h1a, l1a, md);
-            if (r < L) v0 = addmod(v0, csub(mul_shoup_lazy(Cs[ct * T + y], P, Ps, md.q), md.q), md.q);
-            u64* o = Rx + (((u64)h * B + a) * 2) * EN + ((u64)r << logN) + x;
+            // P sigma(c0) as c0 times P R (the digits carry R); one Montgomery
+            // reduction per output
+            if (r < L) mac128(h0a, l0a, Cs[ct * T + y], PR);
+            const u64 v0 = redc128(h0a, l0a, md);
+            const u64 v1 = redc128(h1a, l1a, md);
+            u64* o = Rx + (((u64)h * B + a) * 2) * EN + ((u64)r << logN) + xc;
             o[0] = split30(v0);
             o[EN] = split30(v1);
         }
+#pragma unroll
+        for (int b = 0; b < ND; ++b) { kc[b][0] = kn[b][0]; kc[b][1] = kn[b][1]; }
+        xc = xn;
     }
 }
 
@@ -699,7 +710,7 @@ struct MacArgs {
 };
 
 template <int GT, int BC, int PC>
-__global__ void __launch_bounds__(256, PC == 1 ? 3 : 2) k_diag_mac(const u64* __restrict__ R,
+__global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
                                                   const u64* __restrict__ Dg, MacArgs a,
                                                   const Mod* __restrict__ mods,
                                                   const u64* __restrict__ c6090,
@@ -725,12 +736,12 @@ __global__ void __launch_bounds__(256, PC == 1 ? 3 : 2) k_diag_mac(const u64* __
 
     const u32 spt = hpg_eff * a.achunks;           // steps per position tile
     const u32 steps = spt * a.tiles_per_cta;
-    const u32 tile0 = blockIdx.x * a.tiles_per_cta;
+    // position tiles blockIdx.x, blockIdx.x + gridDim.x, ... (round robin)
 
     // copies of step (tt, hh, ac) into stage buffer `buf`
     auto issue = [&](u32 tt, u32 hh, u32 ac, u32 buf) {
         const u32 a0 = ac * BC;
-        const u64 x0 = (u64)(tile0 + tt) << a.logX;
+        const u64 x0 = (u64)(blockIdx.x + tt * gridDim.x) << a.logX;
         u64* D = smem + buf * stage;
         const u64* dsrc = Dg + (((u64)hh * a.B + a0) * a.E + l) * N * GI + x0 * GI;
         if (GI >= 2) {
@@ -833,7 +844,7 @@ __global__ void __launch_bounds__(256, PC == 1 ? 3 : 2) k_diag_mac(const u64* __
                 const u32 gam = combo >> 1, poly = combo & 1;
                 if (c0 + p < CPC && gam < a.G) {
                     const Mod md = mods[l];
-                    const u64 pos = ((u64)l << a.logN) + ((u64)(tile0 + ctt) << a.logX) + xi;
+                    const u64 pos = ((u64)l << a.logN) + ((u64)(blockIdx.x + ctt * gridDim.x) << a.logX) + xi;
 #pragma unroll
                     for (int g = 0; g < GT; ++g) {
                         const u32 gi = g0 + g;
@@ -1094,8 +1105,8 @@ int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t
     const dim3 grid((c.N / 2 + kBlock - 1) / kBlock, (u32)nd, cnt);
 #define PDQ_MODUP(A)                                                                              \
     k_modup<A><<<grid, kBlock, 0, st>>>(X, in, c.log_n, c.L, (u32)E, c.alpha, c.d_mods,            \
-                                        c.d_up_hatinv, c.d_up_hatinv_shoup, c.d_up_hatmod,         \
-                                        c.d_up_hatmod_shoup, D)
+                                        c.d_up_hatinv, c.d_up_hatinv_shoup, c.d_up_hatmod_mont,    \
+                                        c.d_up_hatmod_mont_shoup, D)
     switch (c.alpha) {
         case 1: PDQ_MODUP(1); break;
         case 2: PDQ_MODUP(2); break;
@@ -1144,19 +1155,41 @@ int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, c
     PDQ_TRY(check_y(cnt, "key switch"));
     if (accumulate && split) return fail(PDQ_E_PARAM, "ks_apply_ext: cannot accumulate split output");
     k_ks_inner_ext<<<grid2(E * N / 2, cnt), kBlock, 0, st>>>(
-        D, key, c.log_n, (u32)E, c.L, c.ndigits, galois, c.d_mods, c0src, c.d_P_mod_q,
-        c.d_P_mod_q_shoup, out, accumulate ? 1u : 0u, split ? 1u : 0u);
+        D, key, c.log_n, (u32)E, c.L, c.ndigits, galois, c.d_mods, c0src, c.d_P_mont, out,
+        accumulate ? 1u : 0u, split ? 1u : 0u);
     return launched("k_ks_inner_ext");
 }
 
+namespace {
+
+template <int ND>
+int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
+                const BabyParams& bp, u64* Rx, cudaStream_t st) {
+    constexpr u32 T = 64, HC = 16, CPT = 4;
+    const u32 E = c.L + c.K;
+    const size_t smem = ((size_t)HC * ND * T + HC * T) * sizeof(u64);
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(k_baby_ext<T, HC, CPT, ND>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10) != cudaSuccess)
+            return cuda_check("k_baby_ext attribute");
+        configured = true;
+    }
+    const dim3 grid(c.N / T, E, (H + HC - 1) / HC);
+    k_baby_ext<T, HC, CPT, ND><<<grid, T * HC / CPT, smem, st>>>(D, u, keys, H, B, c.log_n, E, c.L,
+                                                                 c.d_mods, c.d_P_mont, Rx, bp);
+    return launched("k_baby_ext");
+}
+
+}  // namespace
+
 int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
                    const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st) {
-    constexpr u32 T = 64, HC = 16, CPT = 4;
+    constexpr u32 T = 64;
     if (B > 128) return fail(PDQ_E_PARAM, "baby steps: B <= 128");
-    const size_t tile_bytes = ((size_t)HC * c.ndigits * T + HC * T + 3 * c.ndigits * 2 * T) * sizeof(u64);
-    if (c.N < T || tile_bytes > (160u << 10)) {
-        // rings below one tile, or too many digits for the staged tile: one
-        // rotation at a time
+    if (c.N < T || c.ndigits > 8) {
+        // rings below one tile, or more digits than the fused kernel keeps
+        // in registers: one rotation at a time
         for (u32 a = 1; a < B; ++a) {
             const u32 k = (u32)host_powmod(3, a, 2ull * c.N);
             PDQ_TRY(ks_apply_ext(c, D, u, H, k, keys + key_offsets[a],
@@ -1172,20 +1205,16 @@ int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64*
         bp.kinv[a] = (u32)host_invmod(bp.k[a], 2ull * c.N);
         bp.koff[a] = key_offsets[a];
     }
-    const u32 E = c.L + c.K, nd = c.ndigits;
-    const size_t smem = tile_bytes;
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(k_baby_ext<T, HC, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 160 << 10) != cudaSuccess)
-            return cuda_check("k_baby_ext attribute");
-        configured = true;
+    switch (c.ndigits) {
+        case 1: return launch_baby<1>(c, D, u, H, B, keys, bp, Rx, st);
+        case 2: return launch_baby<2>(c, D, u, H, B, keys, bp, Rx, st);
+        case 3: return launch_baby<3>(c, D, u, H, B, keys, bp, Rx, st);
+        case 4: return launch_baby<4>(c, D, u, H, B, keys, bp, Rx, st);
+        case 5: return launch_baby<5>(c, D, u, H, B, keys, bp, Rx, st);
+        case 6: return launch_baby<6>(c, D, u, H, B, keys, bp, Rx, st);
+        case 7: return launch_baby<7>(c, D, u, H, B, keys, bp, Rx, st);
+        default: return launch_baby<8>(c, D, u, H, B, keys, bp, Rx, st);
     }
-    const dim3 grid(c.N / T, E, (H + HC - 1) / HC);
-    k_baby_ext<T, HC, CPT><<<grid, T * HC / CPT, smem, st>>>(D, u, keys, H, B, c.log_n, E, c.L, nd,
-                                                             c.d_mods, c.d_P_mod_q,
-                                                             c.d_P_mod_q_shoup, Rx, bp);
-    return launched("k_baby_ext");
 }
 
 int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, bool split, cudaStream_t st) {
@@ -1229,21 +1258,30 @@ u32 log2u(u32 x) {
 // of a group per thread (two: each staged value feeds 8 products; one
 // polynomial per thread, with three CTAs per SM, measured 9% slower), up to
 // 32 combinations per CTA (more go to further z-slices), X >= 2 positions so
-// that a CTA has up to 256 threads (two CTAs per SM), and an a-chunk BC (up
-// to 16) that keeps the two staged (diagonal + rotated) tiles within
-// kMacSmem of shared memory.
+// that a CTA has up to 256 threads (two CTAs per SM; one CTA of 512 threads
+// with 16-position tiles measured 2.5% slower), and an a-chunk BC (up to 16)
+// that keeps the two staged (diagonal + rotated) tiles within kMacSmem of
+// shared memory.  Position tiles are dealt to CTAs round robin, so the two
+// 64-byte halves of a 128-byte line of rotated operands are read by
+// neighbouring CTAs of the same wave (dealt in consecutive runs per CTA,
+// the second half was evicted before use and fetched again: 1.76x the
+// algorithmic DRAM reads).
 constexpr u32 kMacThreads = 256;
 constexpr u32 kMacPC = 2;                // polynomials (of one group) per thread
 constexpr u32 kMacSmem = 100u << 10;     // two CTAs per SM
+constexpr u32 kMacMinX = 2;
+
 MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     MacShape s{};
     const u32 GI = pl.giants, combos = 2 * pl.G;
     s.GT = GI < 4 ? GI : 4;
     const u32 GS = GI / s.GT;
     s.logGS = log2u(GS);
+    const u32 minX = std::min(kMacMinX, 1u << logN);
     u32 ct = (combos + kMacPC - 1) / kMacPC;       // threads along the combinations
-    u32 ct_max = kMacThreads / 2 / GS;
-    if (ct_max > 32) ct_max = 32;
+    u32 ct_max = kMacThreads / minX / GS;
+    if (ct_max < 1) ct_max = 1;
+    if (ct_max > 32 / kMacPC) ct_max = 32 / kMacPC;
     if (ct > ct_max) ct = 1u << log2u(ct_max);
     s.combos_per_cta = ct * kMacPC;
     s.zslices = (combos + s.combos_per_cta - 1) / s.combos_per_cta;

@@ -40,6 +40,7 @@ struct Mod {
     u64 ratio;       // floor(2^64 / q)
     u64 r64;         // 2^64 mod q
     u64 r64_shoup;   // floor(r64 * 2^64 / q)
+    u64 qinv;        // -q^{-1} mod 2^64 (Montgomery reduction)
 };
 
 // ------------------------------------------------------------ device math --
@@ -71,6 +72,15 @@ __host__ __device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const Mod& m) 
     u64 s = a + b;                                            // [0, 4q)
     s = csub(s, 2 * m.q);
     return csub(s, m.q);
+}
+
+// Montgomery reduction of T = hi 2^64 + lo < q 2^64: T 2^-64 mod q, canonical.
+// With m = lo (-q^-1) mod 2^64, T + m q is a multiple of 2^64; its quotient
+// is hi + hi(m q) + [lo != 0] < 2q.
+__host__ __device__ __forceinline__ u64 redc128(u64 hi, u64 lo, const Mod& md) {
+    const u64 m = lo * md.qinv;
+    const u64 t = hi + mulhi64(m, md.q) + (lo != 0 ? 1 : 0);
+    return csub(t, md.q);
 }
 
 __host__ __device__ __forceinline__ u64 mulmod(u64 a, u64 b, const Mod& m) {
@@ -121,6 +131,10 @@ struct Ctx {
     u64* d_up_hatinv_shoup = nullptr;
     u64* d_up_hatmod = nullptr;   // [L][L+K]: (Q_{digit(i)}/q_i) mod r
     u64* d_up_hatmod_shoup = nullptr;
+    // the same scaled by R = 2^64 mod r (raised digits are kept multiplied by
+    // R so that the key inner products end with one Montgomery reduction)
+    u64* d_up_hatmod_mont = nullptr;
+    u64* d_up_hatmod_mont_shoup = nullptr;
     // ModDown: (P/p_k)^-1 mod p_k (+shoup); (P/p_k) mod q_i; P^-1 mod q_i (+shoup)
     u64* d_dn_hatinv = nullptr;   // [K]
     u64* d_dn_hatinv_shoup = nullptr;
@@ -132,6 +146,7 @@ struct Ctx {
     std::vector<u64> P_mod_q, delta_mod_q;
     u64* d_P_mod_q = nullptr;
     u64* d_P_mod_q_shoup = nullptr;
+    u64* d_P_mont = nullptr;      // [L] P 2^64 mod q_i
     u64* d_delta_mod_q = nullptr;
     // decryption: per q_i, omega_i = (Q/q_i)^-1 mod q_i (+shoup), and
     // t * b / q_i split for rounding is done with 128-bit arithmetic.
