@@ -670,11 +670,18 @@ struct Acc5 {
     u64 s0, s1a, s1b, s2, s3;
 };
 
+// each product as a carry chain into the two 32-bit halves of its sum (low
+// half with carry out, high half with carry in; the sums stay below 2^64)
 __device__ __forceinline__ void mac4(Acc5& A, u32 a0, u32 a1, u32 b0, u32 b1) {
-    asm("mad.wide.u32 %0, %4, %6, %0;\n\t"
-        "mad.wide.u32 %1, %4, %7, %1;\n\t"
-        "mad.wide.u32 %2, %5, %6, %2;\n\t"
-        "mad.wide.u32 %3, %5, %7, %3;"
+    asm("{\n\t.reg .u32 l0, h0, l1, h1, l2, h2, l3, h3;\n\t"
+        "mov.b64 {l0, h0}, %0;\n\tmov.b64 {l1, h1}, %1;\n\t"
+        "mov.b64 {l2, h2}, %2;\n\tmov.b64 {l3, h3}, %3;\n\t"
+        "mad.lo.cc.u32 l0, %4, %6, l0;\n\tmadc.hi.u32 h0, %4, %6, h0;\n\t"
+        "mad.lo.cc.u32 l1, %4, %7, l1;\n\tmadc.hi.u32 h1, %4, %7, h1;\n\t"
+        "mad.lo.cc.u32 l2, %5, %6, l2;\n\tmadc.hi.u32 h2, %5, %6, h2;\n\t"
+        "mad.lo.cc.u32 l3, %5, %7, l3;\n\tmadc.hi.u32 h3, %5, %7, h3;\n\t"
+        "mov.b64 %0, {l0, h0};\n\tmov.b64 %1, {l1, h1};\n\t"
+        "mov.b64 %2, {l2, h2};\n\tmov.b64 %3, {l3, h3};\n\t}"
         : "+l"(A.s0), "+l"(A.s1a), "+l"(A.s1b), "+l"(A.s2)
         : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
 }
