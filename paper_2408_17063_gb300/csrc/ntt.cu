@@ -23,9 +23,13 @@ namespace pdq {
 
 namespace {
 
-constexpr u32 kTile = 2048;       // elements per CTA tile
+constexpr u32 kTileBits = 11;
+constexpr u32 kTile = 1u << kTileBits;   // elements per CTA tile
 constexpr u32 kRowBits = 9;       // row length 2^9 in the two-phase split
-constexpr u32 kThreads = 256;
+constexpr u32 kThreads = 256;     // 8 elements per thread and pass
+constexpr int kMaxRadixBits = 3;  // levels per register pass (four, with 128
+                                  // registers and half the resident warps,
+                                  // measured 4-6% slower)
 
 struct NttArgs {
     u64* data;
@@ -39,6 +43,12 @@ struct NttArgs {
     u32 S1;            // levels done by the column phase (0: single phase)
     u32 logC;          // log2(sub-transforms per CTA)
     u32 last;          // 1: this phase writes canonical output
+    // first phase only: read group g from src + (g / per) outer + (g % per)
+    // inner + off (limb l at + l N) instead of data (src == nullptr: in place)
+    const u64* src;
+    long long src_outer, src_inner;
+    u32 src_per;
+    u64 src_off;
 };
 
 __device__ __forceinline__ void bf_fwd(u64& x, u64& y, u64 w, u64 wp, u64 q) {
@@ -71,8 +81,8 @@ template <bool FWD, int S, bool COLS, bool SINGLE>
 struct Phase {
     static constexpr u32 GS = 1u << S;
     // sub-transforms per CTA: one whole polynomial in the single-phase case,
-    // else as many as fill a 2048-element tile
-    static constexpr u32 LOGC = SINGLE ? 0 : 11 - S;
+    // else as many as fill a tile
+    static constexpr u32 LOGC = SINGLE ? 0 : kTileBits - S;
     static constexpr u32 C = 1u << LOGC;
 
     u64* sm;
@@ -145,11 +155,11 @@ struct Phase {
         __syncthreads();
     }
 
-    // forward: pair bits from the top down, three at a time
+    // forward: pair bits from the top down, up to three at a time
     template <int TOP>
     __device__ __forceinline__ void run_fwd() const {
         if constexpr (TOP > 0) {
-            constexpr int R = TOP >= 3 ? 3 : TOP;
+            constexpr int R = TOP >= kMaxRadixBits ? kMaxRadixBits : TOP;
             pass<R, TOP - R>();
             run_fwd<TOP - R>();
         }
@@ -158,7 +168,7 @@ struct Phase {
     template <int LO>
     __device__ __forceinline__ void run_inv() const {
         if constexpr (LO < S) {
-            constexpr int R = (S - LO) >= 3 ? 3 : (S - LO);
+            constexpr int R = (S - LO) >= kMaxRadixBits ? kMaxRadixBits : (S - LO);
             pass<R, LO>();
             run_inv<LO + R>();
         }
@@ -177,6 +187,12 @@ __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
     const u32 mi = a.limb0 + limb;
     const u32 N = 1u << a.logN;
     u64* base = a.data + (u64)grp * a.stride + (u64)limb * N;
+    const u64* inb = base;
+    if (a.src) {
+        const u32 hi = grp / a.src_per, lo = grp - hi * a.src_per;
+        inb = a.src + (long long)hi * a.src_outer + (long long)lo * a.src_inner + a.src_off +
+              (u64)limb * N;
+    }
 
     Phase<FWD, S, COLS, SINGLE> ph;
     ph.sm = sm;
@@ -201,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
         u32 c, l;
         if (COLS) { l = e >> LOGC; c = e & ((1u << LOGC) - 1); }
         else { c = e >> S; l = e & (GS - 1); }
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(base + ph.gidx(c, l));
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(inb + ph.gidx(c, l));
         const u32 w = smem_index<S, COLS>(c, l, LOGC);
         *reinterpret_cast<ulonglong2*>(sm + (w & ~1u)) = (w & 1) ? make_ulonglong2(v.y, v.x) : v;
     }
@@ -238,7 +254,7 @@ int launch_phase(int S, dim3 grid, u32 threads, const NttArgs& a, cudaStream_t s
 
 template <bool FWD>
 int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
-            cudaStream_t st) {
+            cudaStream_t st, const NttArgs* from = nullptr) {
     if (count == 0 || nlimbs == 0) return PDQ_OK;
     if (limb0 + nlimbs > c.nmod) return fail(PDQ_E_PARAM, "ntt: limb range out of bounds");
     const u64 polys = (u64)count * nlimbs;
@@ -252,7 +268,14 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
     a.tw = reinterpret_cast<const ulonglong2*>(FWD ? c.d_fw2 : c.d_iw2);
     a.ninv4 = c.d_ninv;
     a.logN = c.log_n;
-    if (c.log_n <= 11) {
+    if (from) {
+        a.src = from->src;
+        a.src_outer = from->src_outer;
+        a.src_inner = from->src_inner;
+        a.src_per = from->src_per;
+        a.src_off = from->src_off;
+    }
+    if (c.log_n <= kTileBits) {
         a.S1 = 0;
         a.logC = 0;
         a.last = 1;
@@ -262,8 +285,9 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
     const u32 S1 = c.log_n - kRowBits;
     a.S1 = S1;
     NttArgs cols = a, rows = a;
-    cols.logC = 11 - S1;                       // 2^S1 * C = 2048
-    rows.logC = 11 - kRowBits;                 // 4 rows of 512
+    (FWD ? rows : cols).src = nullptr;        // the second phase works in place
+    cols.logC = kTileBits - S1;                // 2^S1 * C = tile
+    rows.logC = kTileBits - kRowBits;          // 4 rows of 512
     const dim3 gcols((u32)polys, (1u << kRowBits) >> cols.logC);
     const dim3 grows((u32)polys, (1u << S1) >> rows.logC);
     if (FWD) {
@@ -290,6 +314,19 @@ int ntt_forward(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 s
 int ntt_inverse(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
                 cudaStream_t st) {
     return ntt_run<false>(c, data, count, nlimbs, limb0, stride, st);
+}
+
+int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_per,
+                     long long src_inner, u64 src_off, u64* data, u32 count, u32 nlimbs,
+                     u64 stride, cudaStream_t st) {
+    if (src_per == 0) return fail(PDQ_E_PARAM, "ntt: bad source set");
+    NttArgs from{};
+    from.src = src;
+    from.src_outer = src_outer;
+    from.src_inner = src_inner;
+    from.src_per = src_per;
+    from.src_off = src_off;
+    return ntt_run<false>(c, data, count, nlimbs, 0, stride, st, &from);
 }
 
 }  // namespace pdq

@@ -1105,9 +1105,10 @@ int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t
     PDQ_TRY(check_y(cnt, "key switch"));
     u64* X = ws;
     u64* D = ws + cnt * L * N;
-    // c1 of every ciphertext -> X, then coefficient form
-    PDQ_TRY(gather_rows(in, (long long)(L * N), cnt, L * N, X, L * N, st));
-    PDQ_TRY(ntt_inverse(c, X, cnt, c.L, 0, L * N, st));
+    // c1 of every ciphertext, coefficient form, into X (the transform reads
+    // the set directly)
+    PDQ_TRY(ntt_inverse_from(c, in.base, in.outer, in.per, in.inner, L * N, X, cnt, c.L, L * N,
+                             st));
     if (E > 32 || c.alpha > 8) return fail(PDQ_E_PARAM, "key switch: too many primes per digit");
     const dim3 grid((c.N / 2 + kBlock - 1) / kBlock, (u32)nd, cnt);
 #define PDQ_MODUP(A)                                                                              \

@@ -36,12 +36,24 @@ def test_prime_chain_matches_oracle(setup):
     assert setup.galois == opdq.galois_elements(par, op)
 
 
-@pytest.mark.parametrize("cfg_name", ["tiny", "c1", "c3"])
+# every transform decomposition: one CTA (N <= 2^12), column + row phases of
+# 5..8 column levels (2^13 .. 2^16)
+RINGS = {"tiny": W.CONFIGS["tiny"], "c1": W.CONFIGS["c1"], "c3": W.CONFIGS["c3"],
+         "n13": (13, 65537, 60, 3, 1, 3), "n14": (14, 65537, 60, 4, 2, 2),
+         "n16": (16, 786433, 60, 2, 1, 2)}
+
+
+@pytest.mark.parametrize("cfg_name", list(RINGS))
 def test_ntt_is_evaluation_in_bit_reversed_order(cfg_name):
     pdq = library()
-    cfg = W.CONFIGS[cfg_name]
-    par = bfv.Params.from_config(cfg)
-    ctx = pdq.Context.from_config(cfg)
+    cfg = RINGS[cfg_name]
+    if isinstance(cfg, tuple):
+        par = bfv.Params(*cfg)
+        ctx = pdq.Context(*cfg)
+        cfg = type("Ring", (), {"log_n": cfg[0]})
+    else:
+        par = bfv.Params.from_config(cfg)
+        ctx = pdq.Context.from_config(cfg)
     rng = np.random.default_rng(1)
     mods = par.ext + [par.t]
     a = np.stack([rng.integers(0, r, size=par.N, dtype=np.uint64) for r in mods])
