@@ -160,8 +160,8 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     // 2. baby steps in the extended basis, the digits of every u_h raised once
     prof_mark(c, PDQ_STAGE_BABY, st);
     const CtSet u = ct_set(U, cts);
-    PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * ects), true, st));
-    if (B > 1) {
+    if (B == 1) PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * ects), true, st));
+    else {
         PDQ_TRY(ks_raise(c, u, H, rws, &D, st));
         std::vector<u64> koff(B, 0);
         for (u32 a = 1; a < B; ++a) {

@@ -461,7 +461,8 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
     // loop has no barrier.
     extern __shared__ __align__(16) u64 sm[];
     u64* Ds = sm;                       // [HC][ND][T]
-    u64* Cs = Ds + HC * ND * T;         // [HC][T]
+    u64* Cs = Ds + HC * ND * T;         // [HC][T]: c0
+    u64* C1s = Cs + HC * T;             // [HC][T]: c1 (for a = 0)
     const u32 y0 = blockIdx.x * T, r = blockIdx.y, h0 = blockIdx.z * HC;
     const u64 EN = (u64)E << logN;
     const u32 nthreads = T * HC / CPT;
@@ -476,7 +477,9 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
     if (r < L) {
         for (u32 e = threadIdx.x; e < HC * TP; e += nthreads) {
             const u32 yy = (e % TP) * 2, ct = e / TP, h = h0 + ct;
-            cp_async16(Cs + ct * T + yy, u.at(h < H ? h : 0) + ((u64)r << logN) + y0 + yy, h < H);
+            const u64* src = u.at(h < H ? h : 0) + ((u64)r << logN) + y0 + yy;
+            cp_async16(Cs + ct * T + yy, src, h < H);
+            cp_async16(C1s + ct * T + yy, src + ((u64)L << logN), h < H);
         }
     }
     cp_async_commit();
@@ -500,6 +503,24 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
     load_keys(1, kc, xc);
     cp_async_wait<0>();
     __syncthreads();
+    // a = 0: (P c0, P c1) over Q u P (zero on the special primes)
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const u32 ct = hg * CPT + i, h = h0 + ct;
+        if (h >= H) continue;
+        u64 v0 = 0, v1 = 0;
+        if (r < L) {
+            u64 hi = 0, lo = 0;
+            mac128(hi, lo, Cs[ct * T + xi], PR);
+            v0 = redc128(hi, lo, md);
+            hi = lo = 0;
+            mac128(hi, lo, C1s[ct * T + xi], PR);
+            v1 = redc128(hi, lo, md);
+        }
+        u64* o = Rx + ((u64)h * B * 2) * EN + ((u64)r << logN) + y0 + xi;
+        o[0] = split30(v0);
+        o[EN] = split30(v1);
+    }
     for (u32 a = 1; a < B; ++a) {
         if (a + 1 < B) load_keys(a + 1, kn, xn);
         const u32 y = auto_index(xc, bp.k[a], logN) - y0;  // in [0, T)
@@ -1175,7 +1196,7 @@ int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* ke
                 const BabyParams& bp, u64* Rx, cudaStream_t st) {
     constexpr u32 T = 64, HC = 16, CPT = 4;
     const u32 E = c.L + c.K;
-    const size_t smem = ((size_t)HC * ND * T + HC * T) * sizeof(u64);
+    const size_t smem = ((size_t)HC * ND * T + 2 * HC * T) * sizeof(u64);
     static bool configured = false;
     if (!configured) {
         if (cudaFuncSetAttribute(k_baby_ext<T, HC, CPT, ND>,
@@ -1198,6 +1219,7 @@ int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64*
     if (c.N < T || c.ndigits > 8) {
         // rings below one tile, or more digits than the fused kernel keeps
         // in registers: one rotation at a time
+        PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * 2 * (c.L + c.K) * c.N), true, st));
         for (u32 a = 1; a < B; ++a) {
             const u32 k = (u32)host_powmod(3, a, 2ull * c.N);
             PDQ_TRY(ks_apply_ext(c, D, u, H, k, keys + key_offsets[a],

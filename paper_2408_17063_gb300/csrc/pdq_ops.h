@@ -69,9 +69,9 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
 // layout of diag_mac; not combinable with `accumulate`)
 int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, const u64* key,
                  CtSet out, bool accumulate, bool split, cudaStream_t st);
-// All baby-step rotations a = 1..B-1 of the H ciphertexts u (raised digits
-// D) in one launch, written to Rx[h][a] in the split operand layout; key a at
-// keys + key_offsets[a]
+// All baby-step rotations a = 0..B-1 of the H ciphertexts u (raised digits
+// D; a = 0 is (P c0, P c1)) written to Rx[h][a] in the split operand layout;
+// key a at keys + key_offsets[a] (B >= 2)
 int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
                    const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st);
 // (P c0, P c1) over Q u P
