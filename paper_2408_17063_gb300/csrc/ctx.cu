@@ -159,7 +159,7 @@ static void free_ctx(Ctx* c) {
                     c->d_up_hatmod, c->d_up_hatmod_shoup, c->d_dn_hatinv,
                     c->d_dn_hatinv_shoup, c->d_dn_hatmod, c->d_dn_hatmod_shoup,
                     c->d_dn_pinv, c->d_dn_pinv_shoup, c->d_P_mod_q, c->d_P_mod_q_shoup, c->d_delta_mod_q,
-                    c->d_dec_omega, c->d_dec_omega_shoup, c->d_c6090,
+                    c->d_dec_omega, c->d_dec_omega_shoup, c->d_ckar,
                     c->d_up_hatmod_mont, c->d_up_hatmod_mont_shoup, c->d_P_mont};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -271,17 +271,17 @@ static int build_ctx(const pdq_params& p, Ctx* c) {
     PDQ_TRY(upload(&c->d_fw2, fw2));
     PDQ_TRY(upload(&c->d_iw2, iw2));
     PDQ_TRY(upload(&c->d_ninv, ninv));
-    std::vector<u64> c6090(nm * 4);
+    std::vector<u64> ckar(nm * 8, 0);
     for (u32 mi = 0; mi < nm; ++mi) {
         const u64 q = c->mods[mi];
-        const u64 a = (u64)(((u128)1 << 60) % q);
-        const u64 b = (u64)((((u128)a << 30)) % q);     // 2^90 mod q
-        c6090[4 * mi + 0] = a;
-        c6090[4 * mi + 1] = shoup_of(a, q);
-        c6090[4 * mi + 2] = b;
-        c6090[4 * mi + 3] = shoup_of(b, q);
+        const u64 p30 = (u64)(((u128)1 << 30) % q), p60 = (u64)(((u128)1 << 60) % q);
+        const u64 k[3] = {(1 % q + q - p30) % q, p30, (p60 + q - p30) % q};
+        for (int j = 0; j < 3; ++j) {
+            ckar[8 * mi + 2 * j] = k[j];
+            ckar[8 * mi + 2 * j + 1] = shoup_of(k[j], q);
+        }
     }
-    PDQ_TRY(upload(&c->d_c6090, c6090));
+    PDQ_TRY(upload(&c->d_ckar, ckar));
 
     // slot position in the transform output: slot (rho, c) is the value at
     // zeta^e with e = (-1)^rho 3^c mod 2N, found at position brv((e-1)/2)

@@ -665,15 +665,15 @@ __global__ void k_moddown_final(const u64* __restrict__ A, const u64* __restrict
 // (giant index g = 0 is written to acc0[gamma][p], the others to acc[gamma][g-1][p])
 //
 // Arithmetic: residues are < 2^60, split into 30-bit halves v = v0 + v1 2^30
-// (both operands arrive stored as v0 | v1 << 32, see split30).  A product is
-// four 32x32->64-bit multiply-adds into four 64-bit partial sums
-//   S0 = sum a0 b0,  S1a = sum a0 b1,  S1b = sum a1 b0,  S2 = sum a1 b1
-// (every product <= (2^30 - 1)^2), plus a carry word S3 of weight 2^90.
-// After every a-chunk of at most 16 terms the sums are renormalised (renorm5,
-// shifts and masks only):
-// afterwards S0, S1a, S1b < 2^30 and S2 < 2^31, so 16 more products fit into
-// each (2^31 + 16 (2^30 - 1)^2 < 2^64).  At the end of a position tile the
-// sums are folded to S0 + (S1a + S1b) 2^30 + S2 2^60 + S3 2^90 mod q.
+// (both operands arrive stored as v0 | v1 << 32, see split30).  A product
+// a b = a0 b0 + (a0 b1 + a1 b0) 2^30 + a1 b1 2^60 takes three 32x32-bit
+// products (Karatsuba): a0 b0, a1 b1 and (a0 + a1)(b0 + b1) < 2^62, whose
+// difference from the other two is the middle term.  Each is accumulated as
+// a carry chain into a 96-bit sum (low and high 32-bit halves, then a
+// count of 64-bit overflows), so no sum needs renormalising within a tile;
+// at the end of a position tile the sums are folded to
+//   S00 + (Smid - S00 - S11) 2^30 + S11 2^60
+//     = S00 (1 - 2^30) + Smid 2^30 + S11 (2^60 - 2^30)   (mod q).
 //
 // Work split: one CTA owns limb l = blockIdx.y, X consecutive positions and
 // the (gamma, p) combinations of its z-slice; thread (gs, xi, ct) handles
@@ -687,47 +687,37 @@ __global__ void k_moddown_final(const u64* __restrict__ A, const u64* __restrict
 // asynchronous 16-byte copies, double-buffered so that the next step's copies
 // overlap this step's arithmetic; each diagonal value leaves DRAM once per
 // z-slice and each rotated value once.
-struct Acc5 {
-    u64 s0, s1a, s1b, s2, s3;
+struct AccK {
+    u32 x0, y0, z0;     // S00 = sum a0 b0
+    u32 x1, y1, z1;     // Smid = sum (a0 + a1)(b0 + b1)
+    u32 x2, y2, z2;     // S11 = sum a1 b1
 };
 
-// each product as a carry chain into the two 32-bit halves of its sum (low
-// half with carry out, high half with carry in; the sums stay below 2^64)
-__device__ __forceinline__ void mac4(Acc5& A, u32 a0, u32 a1, u32 b0, u32 b1) {
-    asm("{\n\t.reg .u32 l0, h0, l1, h1, l2, h2, l3, h3;\n\t"
-        "mov.b64 {l0, h0}, %0;\n\tmov.b64 {l1, h1}, %1;\n\t"
-        "mov.b64 {l2, h2}, %2;\n\tmov.b64 {l3, h3}, %3;\n\t"
-        "mad.lo.cc.u32 l0, %4, %6, l0;\n\tmadc.hi.u32 h0, %4, %6, h0;\n\t"
-        "mad.lo.cc.u32 l1, %4, %7, l1;\n\tmadc.hi.u32 h1, %4, %7, h1;\n\t"
-        "mad.lo.cc.u32 l2, %5, %6, l2;\n\tmadc.hi.u32 h2, %5, %6, h2;\n\t"
-        "mad.lo.cc.u32 l3, %5, %7, l3;\n\tmadc.hi.u32 h3, %5, %7, h3;\n\t"
-        "mov.b64 %0, {l0, h0};\n\tmov.b64 %1, {l1, h1};\n\t"
-        "mov.b64 %2, {l2, h2};\n\tmov.b64 %3, {l3, h3};\n\t}"
-        : "+l"(A.s0), "+l"(A.s1a), "+l"(A.s1b), "+l"(A.s2)
-        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+__device__ __forceinline__ void mack(AccK& A, u32 a0, u32 a1, u32 as, u32 b0, u32 b1, u32 bs) {
+    asm("mad.lo.cc.u32 %0, %9, %12, %0;\n\t"
+        "madc.hi.cc.u32 %1, %9, %12, %1;\n\t"
+        "addc.u32 %2, %2, 0;\n\t"
+        "mad.lo.cc.u32 %3, %11, %14, %3;\n\t"
+        "madc.hi.cc.u32 %4, %11, %14, %4;\n\t"
+        "addc.u32 %5, %5, 0;\n\t"
+        "mad.lo.cc.u32 %6, %10, %13, %6;\n\t"
+        "madc.hi.cc.u32 %7, %10, %13, %7;\n\t"
+        "addc.u32 %8, %8, 0;"
+        : "+r"(A.x0), "+r"(A.y0), "+r"(A.z0), "+r"(A.x1), "+r"(A.y1), "+r"(A.z1), "+r"(A.x2),
+          "+r"(A.y2), "+r"(A.z2)
+        : "r"(a0), "r"(a1), "r"(as), "r"(b0), "r"(b1), "r"(bs));
 }
 
-// Keeps S0 + (S1a + S1b) 2^30 + S2 2^60 + S3 2^90 unchanged.  Before it every
-// sum is < 2^31 + 16 (2^30 - 1)^2 < 2^64 - 2^34; the carries into S1a (< 2^34)
-// and into the 2^60 position (c < 2^35) are split so that S2 ends below 2^31.
-__device__ __forceinline__ void renorm5(Acc5& A) {
-    constexpr u64 M = 0x3fffffffull;
-    A.s1a += A.s0 >> 30;
-    A.s0 &= M;
-    const u64 c = (A.s1a >> 30) + (A.s1b >> 30);
-    A.s1a &= M;
-    A.s1b &= M;
-    A.s3 += (A.s2 >> 30) + (c >> 30);
-    A.s2 = (A.s2 & M) + (c & M);
-}
-
-// Value of a renormalised accumulator mod q: S0 + (S1a + S1b) 2^30 < 2^62
-// exactly, S2 2^60 and S3 2^90 by Shoup multiplications.
-__device__ __forceinline__ u64 fold5(const Acc5& A, const Mod& md, const u64* __restrict__ cl) {
+// The accumulated value mod q; ck = (1 - 2^30, 2^30, 2^60 - 2^30) mod q with
+// Shoup companions.
+__device__ __forceinline__ u64 foldk(const AccK& A, const Mod& md, const u64* __restrict__ ck) {
     const u64 q = md.q;
-    u64 v = A.s0 + ((A.s1a + A.s1b) << 30);                         // < 2^62
-    v += mul_shoup_lazy(A.s2, cl[0], cl[1], q);                     // + [0, 2q)
-    v += mul_shoup_lazy(A.s3, cl[2], cl[3], q);                     // + [0, 2q) < 2^63
+    const u64 v00 = reduce128(A.z0, ((u64)A.y0 << 32) | A.x0, md);
+    const u64 vm = reduce128(A.z1, ((u64)A.y1 << 32) | A.x1, md);
+    const u64 v11 = reduce128(A.z2, ((u64)A.y2 << 32) | A.x2, md);
+    u64 v = mul_shoup_lazy(v00, ck[0], ck[1], q);                  // [0, 2q)
+    v += mul_shoup_lazy(vm, ck[2], ck[3], q);                       // [0, 4q)
+    v += mul_shoup_lazy(v11, ck[4], ck[5], q);                      // [0, 6q) < 2^63
     return reduce64(v, md);
 }
 
@@ -741,7 +731,7 @@ template <int GT, int BC, int PC>
 __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
                                                   const u64* __restrict__ Dg, MacArgs a,
                                                   const Mod* __restrict__ mods,
-                                                  const u64* __restrict__ c6090,
+                                                  const u64* __restrict__ ckar,
                                                   u64* __restrict__ acc0,
                                                   u64* __restrict__ acc) {
     extern __shared__ __align__(16) u64 smem[];
@@ -804,11 +794,11 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
         cp_async_commit();
     };
 
-    Acc5 A[PC][GT];
+    AccK A[PC][GT];
 #pragma unroll
     for (int p = 0; p < PC; ++p)
 #pragma unroll
-        for (int g = 0; g < GT; ++g) A[p][g] = Acc5{0, 0, 0, 0, 0};
+        for (int g = 0; g < GT; ++g) A[p][g] = AccK{0, 0, 0, 0, 0, 0, 0, 0, 0};
 
     u32 itt = 0, ihh = 0, iac = 0;                 // next step to issue
     auto advance = [&](u32& tt, u32& hh, u32& ac) {
@@ -845,25 +835,21 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
             } else {
                 d[0] = D[ai * X * GIp];
             }
-            u32 rl[PC], rh[PC];
+            u32 rl[PC], rh[PC], rs[PC];
 #pragma unroll
             for (int p = 0; p < PC; ++p) {
                 const u64 r = Rt[p * RB + ai * X];
                 rl[p] = (u32)r;
                 rh[p] = (u32)(r >> 32);
+                rs[p] = rl[p] + rh[p];
             }
 #pragma unroll
             for (int g = 0; g < GT; ++g) {
-                const u32 d0 = (u32)d[g], d1 = (u32)(d[g] >> 32);
+                const u32 d0 = (u32)d[g], d1 = (u32)(d[g] >> 32), ds = d0 + d1;
 #pragma unroll
-                for (int p = 0; p < PC; ++p) mac4(A[p][g], rl[p], rh[p], d0, d1);
+                for (int p = 0; p < PC; ++p) mack(A[p][g], rl[p], rh[p], rs[p], d0, d1, ds);
             }
         }
-        // at most 16 terms since the last renormalisation (BC <= 16)
-#pragma unroll
-        for (int p = 0; p < PC; ++p)
-#pragma unroll
-            for (int g = 0; g < GT; ++g) renorm5(A[p][g]);
         const bool tile_end = (cac + 1 == a.achunks) && (chh + 1 == hpg_eff);
         if (tile_end) {                            // last step of this position tile
 #pragma unroll
@@ -878,14 +864,14 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
                         const u32 gi = g0 + g;
                         u64* o = gi == 0 ? acc0 + ((u64)gam * 2 + poly) * LN + pos
                                          : acc + (((u64)gam * (GI - 1) + gi - 1) * 2 + poly) * LN + pos;
-                        *o = fold5(A[p][g], md, c6090 + 4 * l);
+                        *o = foldk(A[p][g], md, ckar + 8 * l);
                     }
                 }
             }
 #pragma unroll
             for (int p = 0; p < PC; ++p)
 #pragma unroll
-                for (int g = 0; g < GT; ++g) A[p][g] = Acc5{0, 0, 0, 0, 0};
+                for (int g = 0; g < GT; ++g) A[p][g] = AccK{0, 0, 0, 0, 0, 0, 0, 0, 0};
         }
         advance(ctt, chh, cac);
         __syncthreads();                 // buffer `buf` is refilled by the next issue
@@ -1361,7 +1347,7 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
     a.tiles_per_cta = s.tiles_per_cta;
     a.achunks = pl.B / BC;
     const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, a.E, s.zslices);
-    k_diag_mac<GT, BC, kMacPC><<<grid, s.threads, s.smem, st>>>(R, Dg, a, c.d_mods, c.d_c6090, acc0,
+    k_diag_mac<GT, BC, kMacPC><<<grid, s.threads, s.smem, st>>>(R, Dg, a, c.d_mods, c.d_ckar, acc0,
                                                                  acc);
     return launched("k_diag_mac");
 }

@@ -150,7 +150,7 @@ struct Ctx {
     u64* d_delta_mod_q = nullptr;
     // decryption: per q_i, omega_i = (Q/q_i)^-1 mod q_i (+shoup), and
     // t * b / q_i split for rounding is done with 128-bit arithmetic.
-    u64* d_c6090 = nullptr;       // [nmod][4]: 2^60, Shoup, 2^90, Shoup (mod q)
+    u64* d_ckar = nullptr;        // [nmod][8]: 1 - 2^30, 2^30, 2^60 - 2^30 (mod q), each + Shoup
     u64* d_dec_omega = nullptr;
     u64* d_dec_omega_shoup = nullptr;
     std::vector<std::vector<u32>> digit_limbs;   // limbs of each digit
