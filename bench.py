@@ -469,19 +469,22 @@ def run_served(args, mix) -> list:
 
 # ------------------------------------------------------------------ GPU arm --
 
-# One 60-bit modular multiply-accumulate of the diagonal MAC is four
-# 32x32->64-bit multiply-adds (IMAD.WIDE).  Peak: 152 SMs x 2070 MHz x 32
-# IMAD.WIDE per clock per SM (a 64-bit-result multiply-add issues at half the
-# 32-bit rate of 64 per clock) / 4.  A register-only loop of the same
-# instructions (microbench/ceilings.cu) measured 2.02e12 per second on GB300.
+# Peak of 60-bit modular multiply-accumulates on the integer multiply-add
+# pipe: 152 SMs x 2070 MHz x 32 IMAD.WIDE per clock per SM (a 64-bit-result
+# multiply-add issues at half the 32-bit rate of 64 per clock) / 4 for the
+# four 32x32-bit products of the schoolbook form = 2.52e12/s.  The kernel's
+# Karatsuba form (three products, each a mad.lo.cc/madc.hi.cc/addc chain)
+# runs 8.1 per SM per clock at a fully busy pipe (a register-only loop at
+# 92% fmaheavy: 2.35e12/s, microbench/ceilings.cu), i.e. 2.55e12/s: the same
+# bound.
 MAC_PEAK_PER_S = 152 * 2070e6 * 32 / 4
-MAC_CEILING_MEASURED = 2.02e12
+MAC_CEILING_MEASURED = 2.35e12
 # DRAM bytes of one k_diag_mac launch from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the same plan (B=32, 8 giant steps) with 3 primes
 # (L=2, K=1), scaled by 10/3 to the 10 primes of Q u P (every CTA works on
 # one prime); None when the kernel has changed since the capture.  Capture:
-# 4.027 GB read + 0.200 GB written per launch with 3 primes.
-MAC_TRAFFIC_BYTES = round((4.026701e9 + 0.199623e9) * 10 / 3)
+# 4.031 GB read + 0.203 GB written per launch with 3 primes.
+MAC_TRAFFIC_BYTES = round((4.031182e9 + 0.203066e9) * 10 / 3)
 MAC_TRAFFIC_PLAN = (2**15, 10, 64, 32, 8)       # N, primes, H, B, giant steps
 
 
@@ -499,7 +502,8 @@ def mac_roofline(ctx, plan, ms):
             else None, "algorithmic_bytes": algo_bytes,
             "macs_per_launch": macs, "ms_per_launch": ms,
             "timing": "CUDA events recorded on the launching stream around each launch",
-            "peak_source": "derived: 152 SMs x 2070 MHz x 32 IMAD.WIDE/clk/SM / 4 per modmac"}
+            "peak_source": "derived: 152 SMs x 2070 MHz x 32 IMAD.WIDE/clk/SM / 4 per modmac; "
+                           "measured ceiling: register-only Karatsuba loop"}
 
 
 def run_gpu(args, cfg, rank: int, world: int):

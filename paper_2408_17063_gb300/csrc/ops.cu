@@ -444,6 +444,43 @@ __global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict_
 // once; sigma_{3^a} maps the aligned output tile X_a = sigma^{-1}(Y) onto Y,
 // so for every a it reads the key tile at X_a, computes all outputs of X_a
 // and writes them as contiguous runs.
+// Exact sums of up to 8 products of 60-bit operands from their 30-bit halves
+// (v = v0 + v1 2^30), Karatsuba: S00 = sum a0 b0, S11 = sum a1 b1 and
+// Sm = sum (a0 + a1)(b0 + b1) mod 2^64, each a 64-bit sum of 32x32-bit
+// products (one mad.lo.cc / madc.hi carry chain each).  With at most 8
+// terms S00, S11 < 8 2^60 = 2^63 and the cross sum Sm - S00 - S11 =
+// sum (a0 b1 + a1 b0) < 16 (2^30 - 1)^2 < 2^64, so all three are exact.
+struct Kara64 {
+    u32 l00, h00, lm, hm, l11, h11;
+};
+
+__device__ __forceinline__ void kmac(Kara64& s, u32 a0, u32 a1, u32 as, u32 b0, u32 b1, u32 bs) {
+    asm("mad.lo.cc.u32 %0, %6, %9, %0;\n\t"
+        "madc.hi.u32 %1, %6, %9, %1;\n\t"
+        "mad.lo.cc.u32 %2, %8, %11, %2;\n\t"
+        "madc.hi.u32 %3, %8, %11, %3;\n\t"
+        "mad.lo.cc.u32 %4, %7, %10, %4;\n\t"
+        "madc.hi.u32 %5, %7, %10, %5;"
+        : "+r"(s.l00), "+r"(s.h00), "+r"(s.lm), "+r"(s.hm), "+r"(s.l11), "+r"(s.h11)
+        : "r"(a0), "r"(a1), "r"(as), "r"(b0), "r"(b1), "r"(bs));
+}
+
+// The summed products as the 128-bit value S00 + (Sm - S00 - S11) 2^30 + S11 2^60.
+__device__ __forceinline__ void kara_value(const Kara64& s, u64& hi, u64& lo) {
+    const u64 s00 = ((u64)s.h00 << 32) | s.l00;
+    const u64 sm = ((u64)s.hm << 32) | s.lm;
+    const u64 s11 = ((u64)s.h11 << 32) | s.l11;
+    const u64 c = sm - s00 - s11;
+    lo = s00;
+    hi = c >> 34;
+    asm("add.cc.u64 %0, %0, %2;\n\t"
+        "addc.u64 %1, %1, %3;\n\t"
+        "add.cc.u64 %0, %0, %4;\n\t"
+        "addc.u64 %1, %1, 0;"
+        : "+l"(lo), "+l"(hi)
+        : "l"(c << 30), "l"(s11 >> 4), "l"(s11 << 60));
+}
+
 struct BabyParams {
     u32 k[128];       // Galois element of Rot(.; a)
     u32 kinv[128];    // its inverse mod 2N
@@ -521,28 +558,84 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
         o[0] = split30(v0);
         o[EN] = split30(v1);
     }
+    // Up to 7 digits (with the c0 term at most 8 products per output) the
+    // rotations take Karatsuba sums of the 30-bit halves: the digit and c0
+    // tiles go to the split layout in shared memory once (each thread
+    // converts the c0 entries it has just read), the keys once per rotation
+    // in registers.
+    constexpr bool KARA = ND <= 7;
+    if constexpr (KARA) {
+        if (r < L) {
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                u64& cv = Cs[(hg * CPT + i) * T + xi];
+                cv = split30(cv);
+            }
+        }
+        for (u32 e = threadIdx.x; e < HC * ND * T; e += nthreads) Ds[e] = split30(Ds[e]);
+        __syncthreads();
+    }
+    const u32 p0 = (u32)PR & 0x3fffffffu, p1 = (u32)(PR >> 30), ps = p0 + p1;
     for (u32 a = 1; a < B; ++a) {
         if (a + 1 < B) load_keys(a + 1, kn, xn);
         const u32 y = auto_index(xc, bp.k[a], logN) - y0;  // in [0, T)
+        if constexpr (KARA) {
+            u32 k0[ND][2], k1[ND][2], ks[ND][2];
 #pragma unroll
-        for (int i = 0; i < CPT; ++i) {
-            const u32 ct = hg * CPT + i, h = h0 + ct;
-            if (h >= H) continue;
-            u64 h0a = 0, l0a = 0, h1a = 0, l1a = 0;
+            for (int b = 0; b < ND; ++b)
 #pragma unroll
-            for (int b = 0; b < ND; ++b) {
-                const u64 d = Ds[(ct * ND + b) * T + y];
-                mac128(h0a, l0a, d, kc[b][0]);
-                mac128(h1a, l1a, d, kc[b][1]);
+                for (int j = 0; j < 2; ++j) {
+                    k0[b][j] = (u32)kc[b][j] & 0x3fffffffu;
+                    k1[b][j] = (u32)(kc[b][j] >> 30);
+                    ks[b][j] = k0[b][j] + k1[b][j];
+                }
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                const u32 ct = hg * CPT + i, h = h0 + ct;
+                if (h >= H) continue;
+                Kara64 s0 = {0, 0, 0, 0, 0, 0}, s1 = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+                for (int b = 0; b < ND; ++b) {
+                    const u64 d = Ds[(ct * ND + b) * T + y];
+                    const u32 d0 = (u32)d, d1 = (u32)(d >> 32), ds = d0 + d1;
+                    kmac(s0, d0, d1, ds, k0[b][0], k1[b][0], ks[b][0]);
+                    kmac(s1, d0, d1, ds, k0[b][1], k1[b][1], ks[b][1]);
+                }
+                if (r < L) {                 // P sigma(c0) as c0 times P R
+                    const u64 cv = Cs[ct * T + y];
+                    const u32 c0 = (u32)cv, c1 = (u32)(cv >> 32);
+                    kmac(s0, c0, c1, c0 + c1, p0, p1, ps);
+                }
+                u64 hi, lo;
+                kara_value(s0, hi, lo);
+                const u64 v0 = redc128(hi, lo, md);
+                kara_value(s1, hi, lo);
+                const u64 v1 = redc128(hi, lo, md);
+                u64* o = Rx + (((u64)h * B + a) * 2) * EN + ((u64)r << logN) + xc;
+                o[0] = split30(v0);
+                o[EN] = split30(v1);
             }
-            // P sigma(c0) as c0 times P R (the digits carry R); one Montgomery
-            // reduction per output
-            if (r < L) mac128(h0a, l0a, Cs[ct * T + y], PR);
-            const u64 v0 = redc128(h0a, l0a, md);
-            const u64 v1 = redc128(h1a, l1a, md);
-            u64* o = Rx + (((u64)h * B + a) * 2) * EN + ((u64)r << logN) + xc;
-            o[0] = split30(v0);
-            o[EN] = split30(v1);
+        } else {
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                const u32 ct = hg * CPT + i, h = h0 + ct;
+                if (h >= H) continue;
+                u64 h0a = 0, l0a = 0, h1a = 0, l1a = 0;
+#pragma unroll
+                for (int b = 0; b < ND; ++b) {
+                    const u64 d = Ds[(ct * ND + b) * T + y];
+                    mac128(h0a, l0a, d, kc[b][0]);
+                    mac128(h1a, l1a, d, kc[b][1]);
+                }
+                // P sigma(c0) as c0 times P R (the digits carry R); one Montgomery
+                // reduction per output
+                if (r < L) mac128(h0a, l0a, Cs[ct * T + y], PR);
+                const u64 v0 = redc128(h0a, l0a, md);
+                const u64 v1 = redc128(h1a, l1a, md);
+                u64* o = Rx + (((u64)h * B + a) * 2) * EN + ((u64)r << logN) + xc;
+                o[0] = split30(v0);
+                o[EN] = split30(v1);
+            }
         }
 #pragma unroll
         for (int b = 0; b < ND; ++b) { kc[b][0] = kn[b][0]; kc[b][1] = kn[b][1]; }

@@ -1,9 +1,11 @@
 // Register-only throughput ceilings of the two arithmetic primitives of the
 // library on the current GPU, used as the ALU roofline denominators:
 //   * a modular multiply-accumulate of 60-bit residues in the form the
-//     diagonal multiply-accumulate uses (30-bit halves, four 32x32->64-bit
-//     multiply-adds into 64-bit partial sums), and in the 128-bit carry-chain
-//     form the key-switching inner products use;
+//     diagonal multiply-accumulate uses (30-bit halves, Karatsuba: three
+//     32x32->64-bit products, each a mad.lo.cc / madc.hi.cc / addc chain into
+//     a 96-bit sum), in the schoolbook form (four mad.wide.u32 into 64-bit
+//     partial sums), and in the 128-bit carry-chain form the key-switching
+//     inner products use;
 //   * the forward NTT butterfly (Harvey's lazy Cooley-Tukey butterfly with a
 //     Shoup twiddle multiplication);
 //   * plain 32x32->32-bit multiply-adds (mad.lo.u32) and 32x32->64-bit
@@ -25,6 +27,15 @@ __device__ __forceinline__ void mac30(u64* s, u32 a0, u32 a1, u32 b0, u32 b1) {
         "mad.wide.u32 %2, %5, %6, %2;\n\tmad.wide.u32 %3, %5, %7, %3;"
         : "+l"(s[0]), "+l"(s[1]), "+l"(s[2]), "+l"(s[3]) : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
 }
+// one Karatsuba product step: three 96-bit sums s[0..2], s[3..5], s[6..8]
+__device__ __forceinline__ void mack(u32* s, u32 a0, u32 a1, u32 as, u32 b0, u32 b1, u32 bs) {
+    asm("mad.lo.cc.u32 %0, %9, %12, %0;\n\tmadc.hi.cc.u32 %1, %9, %12, %1;\n\taddc.u32 %2, %2, 0;\n\t"
+        "mad.lo.cc.u32 %3, %11, %14, %3;\n\tmadc.hi.cc.u32 %4, %11, %14, %4;\n\taddc.u32 %5, %5, 0;\n\t"
+        "mad.lo.cc.u32 %6, %10, %13, %6;\n\tmadc.hi.cc.u32 %7, %10, %13, %7;\n\taddc.u32 %8, %8, 0;"
+        : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]), "+r"(s[4]), "+r"(s[5]), "+r"(s[6]),
+          "+r"(s[7]), "+r"(s[8])
+        : "r"(a0), "r"(a1), "r"(as), "r"(b0), "r"(b1), "r"(bs));
+}
 __device__ __forceinline__ u64 csub(u64 x, u64 q) { return x >= q ? x - q : x; }
 __device__ __forceinline__ void bf(u64& x, u64& y, u64 w, u64 wp, u64 q) {
     const u64 a = csub(x, 2 * q);
@@ -33,16 +44,23 @@ __device__ __forceinline__ void bf(u64& x, u64& y, u64 w, u64 wp, u64 q) {
     y = a - t + 2 * q;
 }
 
-// V = 0: mac128, 1: mac30 (four 64-bit partial sums), 2: mad.lo.u32 stream
+// V = 0: mac128, 1: mac30 (four 64-bit partial sums), 2: mad.lo.u32 stream,
+// 3: Karatsuba (three 96-bit sums; the operand half-sums are formed once per
+// operand, as in the kernel, where each is shared by several products)
 template <int V>
 __global__ void k_mac(const u64* in, u64* out, int iters) {
     u64 a = in[threadIdx.x & 31], b = in[(threadIdx.x + 7) & 31];
     u64 acc[8][4] = {};
+    u32 k[8][9] = {};
     for (int it = 0; it < iters; ++it) {
+        const u32 a0 = (u32)a & 0x3fffffffu, a1 = (u32)(a >> 30) & 0x3fffffffu, as = a0 + a1;
 #pragma unroll
         for (int g = 0; g < 8; ++g) {
             const u64 bb = b + g;
-            if (V == 0) mac128(acc[g][0], acc[g][1], a, bb);
+            if (V == 3) {
+                const u32 b0 = (u32)bb & 0x3fffffffu, b1 = (u32)(bb >> 30) & 0x3fffffffu;
+                mack(k[g], a0, a1, as, b0, b1, b0 + b1);
+            } else if (V == 0) mac128(acc[g][0], acc[g][1], a, bb);
             else if (V == 1) mac30(acc[g], (u32)a & 0x3fffffffu, (u32)(a >> 30), (u32)bb & 0x3fffffffu,
                                    (u32)(bb >> 30));
             else {
@@ -59,6 +77,8 @@ __global__ void k_mac(const u64* in, u64* out, int iters) {
     u64 r = 0;
     for (int i = 0; i < 8; ++i)
         for (int j = 0; j < 4; ++j) r ^= acc[i][j];
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 9; ++j) r ^= k[i][j];
     out[blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
@@ -126,6 +146,14 @@ int main() {
     }
     cudaEventElapsedTime(&ms, e0, e1);
     printf("\"imad32_per_s\": %.4e, ", work * 8 * 4 / (ms * 1e-3));
+    for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0);
+        k_mac<3><<<blocks, threads>>>(in, out, iters);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    printf("\"mac_karatsuba_per_s\": %.4e, ", work * 8 / (ms * 1e-3));
     for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0);
         k_bf<<<blocks, threads>>>(in, out, iters, q);
