@@ -31,6 +31,10 @@ Readings where the paper is silent (all mirrored by the GPU library):
   rotations stay in the extended basis Q u P (no ModDown), the diagonal
   products are summed there and each accumulator is lowered once; the
   giant-step rotations of a group are summed in Q u P and lowered once.
+* Rotate-and-sum (sum of Rot(y; i s') over i < m/s', Sec. 5.2) runs in levels
+  of radix r <= 8 instead of log2(m/s') doublings: each level sums
+  Rot(y; j l), j < r, from one raise of y, in Q u P, lowered once; the slots
+  are the same.
 """
 from __future__ import annotations
 
@@ -95,15 +99,31 @@ def make_plan(par: Params, n: int, s: int, B: int | None = None) -> Plan:
     return Plan(n, s, s_prime, B, J, H, G_sz, hpg, G, per_out, n_out)
 
 
+def rotsum_levels(par: Params, plan: Plan) -> list[tuple[int, int]]:
+    """Levels (l, r) of the rotate-and-sum: level i sums Rot(.; j l) for
+    j < r, l the product of s' and the earlier radices.  The log2(m/s') bits
+    are split into ceil(bits/3) chunks as evenly as possible, larger first,
+    so every radix is at most 8."""
+    bits = int(math.log2(par.m // plan.s_prime))
+    if bits == 0:
+        return []
+    nlev = -(-bits // 3)
+    base, extra = divmod(bits, nlev)
+    levels, l = [], plan.s_prime
+    for i in range(nlev):
+        r = 1 << (base + (1 if i < extra else 0))
+        levels.append((l, r))
+        l *= r
+    return levels
+
+
 def galois_elements(par: Params, plan: Plan) -> list[int]:
     """Every automorphism the schedule uses, ascending."""
     ks = {par.galois_col}
     ks.update(par.galois_rot(a) for a in range(1, plan.B))
     ks.update(par.galois_rot(g * plan.B) for g in range(1, plan.giants))
-    l = plan.s_prime
-    while l < par.m:
-        ks.add(par.galois_rot(l))
-        l *= 2
+    for l, r in rotsum_levels(par, plan):
+        ks.update(par.galois_rot(j * l) for j in range(1, r))
     return sorted(ks)
 
 
@@ -299,13 +319,19 @@ def giant_steps(par: Params, acc, keys, plan: Plan):
 
 
 def rotate_and_sum(par: Params, y, keys, plan: Plan):
-    """y <- y + Rot(y; s' 2^l) for l = 0 .. log2(m/s') - 1 (once, after the
-    blocks were summed, Sec. 5.2)."""
-    l = plan.s_prime
-    while l < par.m:
-        k = par.galois_rot(l)
-        y = ct_add(par, y, rotate(par, y, k, keys[k]))
-        l *= 2
+    """sum_{i < m/s'} Rot(y; i s') (once, after the blocks were summed,
+    Sec. 5.2), level by level: y <- ModDown( sum_{j<r} Rot(y; j l) ) with the
+    rotations hoisted (one raise of y) and kept in Q u P (j = 0: (P c0, P c1)).
+    The levels multiply out to every i < m/s' exactly once."""
+    el = list(range(par.L + par.K))
+    for l, r in rotsum_levels(par, plan):
+        raised = mod_up_all(par, y[1])
+        acc = ct_times_P(par, y)
+        for j in range(1, r):
+            k = par.galois_rot(j * l)
+            rj = rotate_ext(par, y, raised, k, keys[k])
+            acc = np.stack([poly_add(par, acc[0], rj[0], el), poly_add(par, acc[1], rj[1], el)])
+        y = ct_mod_down(par, acc)
     return y
 
 

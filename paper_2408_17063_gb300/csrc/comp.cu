@@ -7,7 +7,8 @@
 //   2. baby   R[h][a] = Rot(u_h; a), a < B, digits of u_h raised once
 //   3. MAC    acc[gamma][g] = sum_{h in gamma} sum_a Rot(D_{h,gB+a}; -gB) . R[h][a]
 //   4. giant  y_gamma = sum_g Rot(acc[gamma][g]; gB)
-//   5. sum    y <- y + Rot(y; s' 2^l), l = 0 .. log2(m/s') - 1
+//   5. sum    y <- sum_{j<r} Rot(y; j l) per level (l, r) of rotsum_levels:
+//             all i s', i < m/s', each once; one raise and one ModDown per level
 //   6. groups out_c = sum_o M_o . y_{c per_out + o}   (one group: out = y)
 #include <algorithm>
 #include <cstring>
@@ -78,12 +79,32 @@ u64 galois_rot(const Ctx& c, long long r) {
     return host_powmod(3, (u64)rr, 2ull * c.N);
 }
 
+// Levels (l, r) of the rotate-and-sum (Sec. 5.2 sums Rot(y; i s') over
+// i < m/s'): level i sums Rot(.; j l), j < r, l = s' times the earlier radices.
+// The log2(m/s') bits are split into ceil(bits/3) chunks as evenly as
+// possible, larger first (radix <= 8: one raise and one ModDown per level
+// instead of per doubling, at most 7 hoisted rotations each).
+std::vector<std::pair<u64, u32>> rotsum_levels(const Ctx& c, const pdq_plan& pl) {
+    std::vector<std::pair<u64, u32>> lv;
+    const u32 bits = ceil_log2(c.m / pl.s_prime);
+    if (bits == 0) return lv;
+    const u32 nlev = (bits + 2) / 3, base = bits / nlev, extra = bits % nlev;
+    u64 l = pl.s_prime;
+    for (u32 i = 0; i < nlev; ++i) {
+        const u32 r = 1u << (base + (i < extra ? 1 : 0));
+        lv.emplace_back(l, r);
+        l *= r;
+    }
+    return lv;
+}
+
 std::vector<u64> plan_galois(const Ctx& c, const pdq_plan& pl) {
     std::vector<u64> ks;
     ks.push_back(2ull * c.N - 1);
     for (u32 a = 1; a < pl.B; ++a) ks.push_back(galois_rot(c, a));
     for (u32 g = 1; g < pl.giants; ++g) ks.push_back(galois_rot(c, (long long)g * pl.B));
-    for (u64 l = pl.s_prime; l < c.m; l *= 2) ks.push_back(galois_rot(c, (long long)l));
+    for (const auto& [l, r] : rotsum_levels(c, pl))
+        for (u32 j = 1; j < r; ++j) ks.push_back(galois_rot(c, (long long)(j * l)));
     std::sort(ks.begin(), ks.end());
     ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
     return ks;
@@ -111,7 +132,8 @@ struct Keys {
 size_t comp_ws_bytes(const Ctx& c, const pdq_plan& pl) {
     const u64 cts = ct_elems(c), ects = 2ull * (c.L + c.K) * c.N;
     const u64 U = (u64)pl.H * cts;                       // packed u_h over Q
-    const u64 Rx = (u64)pl.H * pl.B * ects;              // baby steps over Q u P
+    // baby steps over Q u P; later the rotations of one rotate-and-sum level
+    const u64 Rx = (u64)std::max(pl.H * pl.B, pl.G * 8) * ects;
     const u64 accx = (u64)pl.G * (pl.giants - 1) * ects; // accumulators g >= 1 over Q u P
     const u64 acc = (u64)pl.G * (pl.giants - 1) * cts;   // ... lowered to Q
     const u64 yx = (u64)pl.G * ects;                     // giant-step sums over Q u P (from g = 0)
@@ -188,17 +210,25 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
         PDQ_TRY(ks_apply_ext(c, D, in, G, (u32)k, kp, ct_set(yx, ects), true, false, st));
     }
     PDQ_TRY(mod_down_batch(c, yx, G, ct_set(Y0, cts), aws, st));
-    // 5. rotate-and-sum, ping-pong between Y0 and Y1
+    // 5. rotate-and-sum, ping-pong between Y0 and Y1: per level the r
+    // rotations of every y (hoisted, Q u P) into Rx, summed into yx (free
+    // after the giant steps), lowered once
     prof_mark(c, PDQ_STAGE_ROTSUM, st);
     u64* ycur = Y0;
     u64* ynext = Y1;
-    for (u64 l = pl.s_prime; l < c.m; l *= 2) {
-        const u64 k = galois_rot(c, (long long)l);
-        const u64* kp;
-        PDQ_TRY(key_for(k, &kp));
+    for (const auto& [l, r] : rotsum_levels(c, pl)) {
+        std::vector<u64> gal(r, 1), koff(r, 0);
+        for (u32 j = 1; j < r; ++j) {
+            gal[j] = galois_rot(c, (long long)(j * l));
+            const u64* kp;
+            PDQ_TRY(key_for(gal[j], &kp));
+            koff[j] = (u64)(kp - keys.base);
+        }
         const CtSet yin = ct_set(ycur, cts);
         PDQ_TRY(ks_raise(c, yin, G, rws, &D, st));
-        PDQ_TRY(ks_apply(c, D, yin, G, (u32)k, kp, ct_set(ynext, cts), yin, aws, st));
+        PDQ_TRY(hoisted_rotations_ext(c, D, yin, G, r, gal, keys.base, koff, Rx, st));
+        PDQ_TRY(sum_rotations(c, Rx, G, r, yx, st));
+        PDQ_TRY(mod_down_batch(c, yx, G, ct_set(ynext, cts), aws, st));
         std::swap(ycur, ynext);
     }
     // 6. output

@@ -662,6 +662,28 @@ __global__ void k_times_P(CtSet in, u32 logN, u32 L, u32 E, const Mod* __restric
     out.at(ct)[rr] = split ? split30(v) : v;
 }
 
+// out[h] = sum_{a < R} Rx[h][a] over Q u P, Rx in the split operand layout
+// (v = v0 + v1 2^30 stored as v0 | v1 << 32), out canonical.  Two adjacent
+// positions per thread; R <= 8, so the sum of R residues stays below 2^63.
+__global__ void k_sum_split(const u64* __restrict__ Rx, u32 R, u32 logN, u32 E,
+                            const Mod* __restrict__ mods, u64* __restrict__ out) {
+    const u32 EN = E << logN;
+    const u32 x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);     // over [2][E][N]
+    if (x >= 2 * EN) return;
+    const u64 h = blockIdx.y;
+    const u32 l = (x >= EN ? x - EN : x) >> logN;
+    const u64* src = Rx + h * R * 2 * (u64)EN + x;
+    u64 s0 = 0, s1 = 0;
+    for (u32 a = 0; a < R; ++a) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(src + (u64)a * 2 * EN);
+        s0 += (v.x & 0xffffffffull) + ((v.x >> 32) << 30);
+        s1 += (v.y & 0xffffffffull) + ((v.y >> 32) << 30);
+    }
+    const Mod md = mods[l];
+    *reinterpret_cast<ulonglong2*>(out + h * 2 * (u64)EN + x) =
+        make_ulonglong2(reduce64(s0, md), reduce64(s1, md));
+}
+
 // Conv[cp][i] = sum_k [y_k (P/p_k)^-1]_{p_k} (P/p_k) mod q_i from the special
 // limbs of A (coefficient form); cp = blockIdx.y = ct*2 + p
 template <int KK>
@@ -1293,15 +1315,27 @@ int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* ke
 
 int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
                    const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st) {
+    std::vector<u64> galois(B, 1);
+    for (u32 a = 1; a < B; ++a) galois[a] = host_powmod(3, a, 2ull * c.N);
+    return hoisted_rotations_ext(c, D, u, H, B, galois, keys, key_offsets, Rx, st);
+}
+
+int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
+                          const std::vector<u64>& galois, const u64* keys,
+                          const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st) {
     constexpr u32 T = 64;
-    if (B > 128) return fail(PDQ_E_PARAM, "baby steps: B <= 128");
+    if (B > 128) return fail(PDQ_E_PARAM, "hoisted rotations: at most 128");
+    if (galois.size() < B || key_offsets.size() < B)
+        return fail(PDQ_E_PARAM, "hoisted rotations: one Galois element and key per rotation");
+    for (u32 a = 1; a < B; ++a)
+        if (galois[a] % 2 == 0 || galois[a] >= 2ull * c.N)
+            return fail(PDQ_E_PARAM, "hoisted rotations: bad Galois element");
     if (c.N < T || c.ndigits > 8) {
         // rings below one tile, or more digits than the fused kernel keeps
         // in registers: one rotation at a time
         PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * 2 * (c.L + c.K) * c.N), true, st));
         for (u32 a = 1; a < B; ++a) {
-            const u32 k = (u32)host_powmod(3, a, 2ull * c.N);
-            PDQ_TRY(ks_apply_ext(c, D, u, H, k, keys + key_offsets[a],
+            PDQ_TRY(ks_apply_ext(c, D, u, H, (u32)galois[a], keys + key_offsets[a],
                                  ct_set(Rx + (u64)a * 2 * (c.L + c.K) * c.N,
                                         (long long)B * 2 * (c.L + c.K) * c.N),
                                  false, true, st));
@@ -1310,8 +1344,8 @@ int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64*
     }
     BabyParams bp{};
     for (u32 a = 1; a < B; ++a) {
-        bp.k[a] = (u32)host_powmod(3, a, 2ull * c.N);
-        bp.kinv[a] = (u32)host_invmod(bp.k[a], 2ull * c.N);
+        bp.k[a] = (u32)galois[a];
+        bp.kinv[a] = (u32)host_invmod(galois[a], 2ull * c.N);
         bp.koff[a] = key_offsets[a];
     }
     switch (c.ndigits) {
@@ -1324,6 +1358,14 @@ int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64*
         case 7: return launch_baby<7>(c, D, u, H, B, keys, bp, Rx, st);
         default: return launch_baby<8>(c, D, u, H, B, keys, bp, Rx, st);
     }
+}
+
+int sum_rotations(const Ctx& c, const u64* Rx, u32 cnt, u32 R, u64* out, cudaStream_t st) {
+    const u64 E = c.L + c.K;
+    if (R == 0 || R > 8) return fail(PDQ_E_PARAM, "sum of rotations: 1 to 8 terms");
+    PDQ_TRY(check_y(cnt, "sum of rotations"));
+    k_sum_split<<<grid2(E * c.N, cnt), kBlock, 0, st>>>(Rx, R, c.log_n, (u32)E, c.d_mods, out);
+    return launched("k_sum_split");
 }
 
 int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, bool split, cudaStream_t st) {

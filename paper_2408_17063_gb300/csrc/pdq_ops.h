@@ -74,6 +74,14 @@ int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, c
 // key a at keys + key_offsets[a] (B >= 2)
 int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
                    const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st);
+// The same for any Galois elements: Rx[h][a] = sigma_{galois[a]}(u_h) with
+// key a (a = 1..B-1; a = 0 is (P c0, P c1)), split operand layout
+int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
+                          const std::vector<u64>& galois, const u64* keys,
+                          const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st);
+// out[h] = sum_{a<R} Rx[h][a] (Rx [cnt][R][2][L+K][N] split, out [cnt][2][L+K][N]
+// canonical), R <= 8
+int sum_rotations(const Ctx& c, const u64* Rx, u32 cnt, u32 R, u64* out, cudaStream_t st);
 // (P c0, P c1) over Q u P
 int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, bool split, cudaStream_t st);
 // ModDown of cnt extended-basis ciphertexts A ([cnt][2][L+K][N], special limbs

@@ -39,9 +39,11 @@ def test_plan_shapes_match_cost_model():
     #   c1 (H=2, G=1, s'=16): B=4: 42, B=8: 28, B=16: 33 -> 8
     #   c2 (H=16, G=1, s'=64): B=4: 216, B=8: 192, B=16: 276 -> 8
     #   c3 (H=64, G=16, s'=256): B=16: 3648, B=32: 3264, B=64: 4608 -> 32
-    # #galois = Rot_col + (B-1) baby + (s'/B-1) giant + log2(m/s') sum rotations
-    want = {"c1": (16, 8, 1, 2, 1, 1, 16), "c2": (64, 8, 8, 16, 1, 1, 21),
-            "c3": (256, 32, 32, 64, 16, 1, 45)}
+    # #galois = Rot_col + (B-1) baby + (s'/B-1) giant + sum over the
+    # rotate-and-sum levels of (r-1): c1 m/s' = 2^7 -> radices 8,4,4 (13),
+    # c2 2^6 -> 8,8 (14), c3 2^6 -> 8,8 (14)
+    want = {"c1": (16, 8, 1, 2, 1, 1, 22), "c2": (64, 8, 8, 16, 1, 1, 29),
+            "c3": (256, 32, 32, 64, 16, 1, 53)}
     for name, w in want.items():
         cfg = W.CONFIGS[name]
         par = bfv.Params.from_config(cfg)
@@ -49,6 +51,45 @@ def test_plan_shapes_match_cost_model():
         got = (plan.s_prime, plan.B, plan.J, plan.H, plan.G, plan.n_out,
                len(pdq.galois_elements(par, plan)))
         assert got == w, name
+
+
+def test_rotsum_levels_cover_every_shift_once():
+    """The levels' shifts sum_i j_i l_i (j_i < r_i) are exactly the multiples
+    i s' for i < m/s', each once (brute force), with every radix at most 8 and
+    ceil(log2(m/s')/3) levels."""
+    from types import SimpleNamespace
+    for bits in range(0, 11):
+        for s_prime in (1, 4, 16):
+            par = SimpleNamespace(m=s_prime << bits)
+            plan = SimpleNamespace(s_prime=s_prime)
+            lv = pdq.rotsum_levels(par, plan)
+            assert len(lv) == -(-bits // 3)
+            assert all(2 <= r <= 8 and r & (r - 1) == 0 for _, r in lv)
+            shifts = [0]
+            for l, r in lv:
+                shifts = [x + j * l for x in shifts for j in range(r)]
+            assert sorted(shifts) == [i * s_prime for i in range(1 << bits)]
+
+
+def test_rotate_and_sum_is_the_sum_of_rotations():
+    """Decrypting the hoisted rotate-and-sum gives sum_{i < m/s'} Rot(y; i s')
+    on both rows, computed here from the slots with numpy rolls (two levels:
+    m/s' = 16 on the N = 64 ring)."""
+    par = bfv.Params.from_config(W.CONFIGS["tiny2"])
+    plan = pdq.make_plan(par, 100, 2)
+    assert par.m // plan.s_prime == 16 and len(pdq.rotsum_levels(par, plan)) == 2
+    sk = W.draw_ternary(par.N, W.rng_for(31, 3))
+    a, e = W.encryption_randomness(par.q, par.N, 1, seed=31)
+    slots = W.rng_for(32).integers(0, par.t, size=par.N, dtype=np.uint64)
+    ct = bfv.encrypt(par, sk, bfv.encode(par, slots), a[0], e[0])
+    ks = sorted({par.galois_rot(j * l) for l, r in pdq.rotsum_levels(par, plan)
+                 for j in range(1, r)})
+    kr = W.rotation_key_randomness(par.ext, par.N, len(par.digits), ks, seed=33)
+    keys = {k: bfv.rotation_key(par, sk, k, *kr[k]) for k in ks}
+    got = bfv.decrypt(par, sk, pdq.rotate_and_sum(par, ct, keys, plan)).reshape(2, par.m)
+    rows = slots.reshape(2, par.m).astype(np.int64)
+    want = sum(np.roll(rows, -i * plan.s_prime, axis=1) for i in range(16)) % par.t
+    assert np.array_equal(got.astype(np.int64), want)
 
 
 def test_paper_single_ciphertext_answer():
@@ -100,10 +141,8 @@ def test_diagonal_bsgs_in_the_clear(cfg_name):
                     d = pdq.rot_slots(par, pdq.diagonal_slots(par, plan, h, g * B + a), -g * B)
                     acc = (acc + d * pdq.rot_slots(par, u[h], a)) % t
             y = (y + pdq.rot_slots(par, acc, g * B)) % t
-        l = sp
-        while l < m:
-            y = (y + pdq.rot_slots(par, y, l)) % t
-            l *= 2
+        for l, r in pdq.rotsum_levels(par, plan):
+            y = sum(pdq.rot_slots(par, y, j * l) for j in range(r)) % t
         # explicit product with the group's block of C, both rows
         for rho in range(2):
             want = [0] * sp
