@@ -90,17 +90,38 @@ struct Phase {
     u64 q;
     u64 n0, n0s, n1, n1s;  // N^-1 and psi^-1 N^-1 (with Shoup) for level 0
     u32 logN, sub0, S2;
+    const u64* gin;        // tile input (global), read by a direct first pass
+    u64* gout;             // tile output (global), written by a direct last pass
+    bool canon;            // the last pass writes canonical residues
 
     // global index of element l of sub-transform c
     __device__ __forceinline__ u32 gidx(u32 c, u32 l) const {
         return COLS ? (l << S2) + sub0 + c : ((sub0 + c) << S) + l;
     }
 
+    // pair bits of the first and the last register pass
+    static constexpr int first_lb() { return FWD ? S - (S >= kMaxRadixBits ? kMaxRadixBits : S) : 0; }
+    static constexpr int last_lb() {
+        if (FWD) return 0;
+        int lo = 0;
+        while (S - lo > kMaxRadixBits) lo += kMaxRadixBits;
+        return lo;
+    }
+    // A pass whose items put consecutive threads on consecutive global
+    // elements (every column pass; row passes whose pair bits start at 5 or
+    // above) reads or writes global memory directly when it is the first or
+    // the last pass, instead of staging the tile through shared memory.
+    static constexpr bool direct(int lb) { return COLS || lb >= 5; }
+    static constexpr bool DIRECT_IN = direct(first_lb());
+    static constexpr bool DIRECT_OUT = direct(last_lb());
+
     // One pass over the R local levels whose pair bits are LB .. LB+R-1:
     // every thread item holds the 2^R elements that these levels combine.
     // All shifts and masks of the local index are compile-time constants.
-    template <int R, int LB>
+    template <int R, int LB, bool FIRST, bool LAST>
     __device__ __forceinline__ void pass() const {
+        constexpr bool IN_G = FIRST && DIRECT_IN;
+        constexpr bool OUT_G = LAST && DIRECT_OUT;
         constexpr u32 NE = 1u << R;
         constexpr u32 items = (C * GS) >> R;
         constexpr u32 lowmask = (1u << LB) - 1;
@@ -119,7 +140,10 @@ struct Phase {
             const u32 jbase = gidx(c, lbase);
             u64 x[NE];
 #pragma unroll
-            for (u32 k = 0; k < NE; ++k) x[k] = sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)];
+            for (u32 k = 0; k < NE; ++k) {
+                if constexpr (IN_G) x[k] = gin[gidx(c, lbase | (k << LB))];
+                else x[k] = sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)];
+            }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int kb = FWD ? R - 1 - r : r;          // pair bit inside the item
@@ -150,32 +174,40 @@ struct Phase {
                 }
             }
 #pragma unroll
-            for (u32 k = 0; k < NE; ++k) sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)] = x[k];
+            for (u32 k = 0; k < NE; ++k) {
+                if constexpr (OUT_G) {
+                    u64 v = x[k];
+                    if (canon) v = FWD ? csub(csub(v, 2 * q), q) : csub(v, q);
+                    gout[gidx(c, lbase | (k << LB))] = v;
+                } else {
+                    sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)] = x[k];
+                }
+            }
         }
-        __syncthreads();
+        if constexpr (!OUT_G) __syncthreads();
     }
 
     // forward: pair bits from the top down, up to three at a time
-    template <int TOP>
+    template <int TOP, bool FIRST>
     __device__ __forceinline__ void run_fwd() const {
         if constexpr (TOP > 0) {
             constexpr int R = TOP >= kMaxRadixBits ? kMaxRadixBits : TOP;
-            pass<R, TOP - R>();
-            run_fwd<TOP - R>();
+            pass<R, TOP - R, FIRST, TOP - R == 0>();
+            run_fwd<TOP - R, false>();
         }
     }
     // inverse: pair bits from the bottom up
-    template <int LO>
+    template <int LO, bool FIRST>
     __device__ __forceinline__ void run_inv() const {
         if constexpr (LO < S) {
             constexpr int R = (S - LO) >= kMaxRadixBits ? kMaxRadixBits : (S - LO);
-            pass<R, LO>();
-            run_inv<LO + R>();
+            pass<R, LO, FIRST, LO + R == S>();
+            run_inv<LO + R, false>();
         }
     }
     __device__ __forceinline__ void run() const {
-        if (FWD) run_fwd<S>();
-        else run_inv<0>();
+        if constexpr (FWD) run_fwd<S, true>();
+        else run_inv<0, true>();
     }
 };
 
@@ -205,24 +237,32 @@ __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
     ph.logN = a.logN;
     ph.sub0 = blockIdx.y << Phase<FWD, S, COLS, SINGLE>::LOGC;
     ph.S2 = a.logN - S;               // column phase: stride of the column elements
+    ph.gin = inb;
+    ph.gout = base;
+    ph.canon = a.last != 0;
 
+    using Ph = Phase<FWD, S, COLS, SINGLE>;
     constexpr u32 GS = 1u << S;
-    constexpr u32 LOGC = Phase<FWD, S, COLS, SINGLE>::LOGC;
-    constexpr u32 T = Phase<FWD, S, COLS, SINGLE>::C * GS;
-    // adjacent element pairs are adjacent in global memory (C >= 2 columns,
-    // or rows of >= 2 elements) and in shared memory (the row swizzle keeps
-    // aligned pairs together, possibly swapped), so tiles move with 16-byte
-    // accesses on both sides
-    for (u32 e = 2 * threadIdx.x; e < T; e += 2 * blockDim.x) {
-        u32 c, l;
-        if (COLS) { l = e >> LOGC; c = e & ((1u << LOGC) - 1); }
-        else { c = e >> S; l = e & (GS - 1); }
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(inb + ph.gidx(c, l));
-        const u32 w = smem_index<S, COLS>(c, l, LOGC);
-        *reinterpret_cast<ulonglong2*>(sm + (w & ~1u)) = (w & 1) ? make_ulonglong2(v.y, v.x) : v;
+    constexpr u32 LOGC = Ph::LOGC;
+    constexpr u32 T = Ph::C * GS;
+    // Staging (when the first or the last pass cannot access global memory
+    // directly): adjacent element pairs are adjacent in global memory (C >= 2
+    // columns, or rows of >= 2 elements) and in shared memory (the row
+    // swizzle keeps aligned pairs together, possibly swapped), so tiles move
+    // with 16-byte accesses on both sides.
+    if constexpr (!Ph::DIRECT_IN) {
+        for (u32 e = 2 * threadIdx.x; e < T; e += 2 * blockDim.x) {
+            u32 c, l;
+            if (COLS) { l = e >> LOGC; c = e & ((1u << LOGC) - 1); }
+            else { c = e >> S; l = e & (GS - 1); }
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(inb + ph.gidx(c, l));
+            const u32 w = smem_index<S, COLS>(c, l, LOGC);
+            *reinterpret_cast<ulonglong2*>(sm + (w & ~1u)) = (w & 1) ? make_ulonglong2(v.y, v.x) : v;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     ph.run();
+    if constexpr (Ph::DIRECT_OUT) return;
     const u64 q = ph.q;
     for (u32 e = 2 * threadIdx.x; e < T; e += 2 * blockDim.x) {
         u32 c, l;
