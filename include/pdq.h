@@ -221,8 +221,15 @@ int pdq_comp(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* masked,
              const uint64_t* keys, const uint64_t* galois, uint32_t nkeys,
              const uint64_t* consts, uint64_t* out, void* ws, size_t ws_bytes, void* stream);
 
-/* Answer = Mask then Comp on device buffers (Alg. 7 without Match).
- * Workspace: pdq_answer_workspace_bytes (holds the masked ciphertexts too). */
+/* Answer = Mask then Comp on device buffers (Alg. 7 without Match).  The
+ * pack's column rotation is applied to each index ciphertext before the Mask
+ * products (Rot_col is a ring automorphism: Rot_col(v.P) = Rot_col(v).
+ * sigma_col(P)), so u_{2j} = v_j.[1;0] + Rot_col(v_j).sigma_col(DB_j.[1;0])
+ * and u_{2j+1} = Rot_col(v_j).[1;0] + v_j.(DB_j.[0;1]): one key switch per
+ * index ciphertext instead of two.  The output decrypts to the same slots as
+ * pdq_comp(pdq_mask(...)); the ciphertexts differ (other key-switching
+ * noise).  Workspace: pdq_answer_workspace_bytes (holds J rotated index
+ * ciphertexts too). */
 size_t pdq_answer_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan);
 int pdq_answer(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
                const uint64_t* db, const uint64_t* keys, const uint64_t* galois,

@@ -31,6 +31,10 @@ Readings where the paper is silent (all mirrored by the GPU library):
   rotations stay in the extended basis Q u P (no ModDown), the diagonal
   products are summed there and each accumulator is lowered once; the
   giant-step rotations of a group are summed in Q u P and lowered once.
+* In the Answer (Mask then Comp) the pack's column rotation is applied to
+  each index ciphertext before the Mask products (mask_pack): the same
+  slots, half the pack's key switches.  Comp on its own packs the masked
+  ciphertexts as Sec. 5.2 describes.
 * Rotate-and-sum (sum of Rot(y; i s') over i < m/s', Sec. 5.2) runs in levels
   of radix r <= 8 instead of log2(m/s') doublings: each level sums
   Rot(y; j l), j < r, from one raise of y, in Q u P, lowered once; the slots
@@ -184,6 +188,34 @@ def pack(par: Params, masked, keys, plan: Plan) -> list[np.ndarray]:
         vT, vB, dT, dB = masked[4 * j:4 * j + 4]
         u.append(ct_add(par, vT, rotate(par, dT, kc, keys[kc])))
         u.append(ct_add(par, rotate(par, vB, kc, keys[kc]), dB))
+    return u
+
+
+def swap_rows(par: Params, slots) -> np.ndarray:
+    """The slot permutation of Rot_col: the two rows exchanged (Sec. 5.1)."""
+    return np.asarray(slots).reshape(2, par.m)[::-1].reshape(-1)
+
+
+def mask_pack(par: Params, v_cts, db, keys, plan: Plan) -> list[np.ndarray]:
+    """Mask followed by the pack of Comp, with the column rotation moved in
+    front of the Mask products.  Rot_col is a ring automorphism, so
+    Rot_col(v . P) = Rot_col(v) . sigma_col(P) and, with w_j = Rot_col(v_j),
+      u_{2j}   = v_j . [1;0] + w_j . sigma_col(DB_j . [1;0])
+      u_{2j+1} = w_j . [1;0] + v_j . (DB_j . [0;1])
+    hold the same slots as pack(mask(v)): one key switch per index
+    ciphertext instead of two.  sigma_col of an encoded plaintext is the
+    encoding of its row-swapped slots (t odd, so the centred lift commutes)."""
+    kc = par.galois_col
+    top, bot = row_mask_slots(par, 0), row_mask_slots(par, 1)
+    pt_top = lifted_pt(par, top)
+    u = []
+    for j in range(plan.J):
+        dbs = record_slots(par, db, j)
+        w = rotate(par, v_cts[j], kc, keys[kc])
+        u.append(ct_add(par, pt_mul(par, v_cts[j], pt_top),
+                        pt_mul(par, w, lifted_pt(par, swap_rows(par, dbs * top)))))
+        u.append(ct_add(par, pt_mul(par, w, pt_top),
+                        pt_mul(par, v_cts[j], lifted_pt(par, dbs * bot))))
     return u
 
 
@@ -355,10 +387,9 @@ def combine_groups(par: Params, ys, plan: Plan):
     return outs
 
 
-def comp(par: Params, masked, keys, plan: Plan) -> list[np.ndarray]:
-    """Comp of Alg. 7 in SIMD form: returns the output ciphertexts holding
-    ctxt(Cv) in row 0 and ctxt(Cd) in row 1."""
-    u = pack(par, masked, keys, plan)
+def comp_packed(par: Params, u, keys, plan: Plan) -> list[np.ndarray]:
+    """Comp from the packed u_h on: baby steps, diagonal products, giant
+    steps, rotate-and-sum, group masks."""
     R = baby_steps(par, u, keys, plan)
     acc = giant_accumulators(par, R, plan)
     ys = giant_steps(par, acc, keys, plan)
@@ -366,9 +397,18 @@ def comp(par: Params, masked, keys, plan: Plan) -> list[np.ndarray]:
     return combine_groups(par, ys, plan)
 
 
+def comp(par: Params, masked, keys, plan: Plan) -> list[np.ndarray]:
+    """Comp of Alg. 7 in SIMD form: returns the output ciphertexts holding
+    ctxt(Cv) in row 0 and ctxt(Cd) in row 1."""
+    return comp_packed(par, pack(par, masked, keys, plan), keys, plan)
+
+
 def answer(par: Params, v_cts, db, keys, plan: Plan) -> list[np.ndarray]:
-    """Server side of the query: Mask then Comp (Alg. 7 without Match)."""
-    return comp(par, mask(par, v_cts, db, plan), keys, plan)
+    """Server side of the query: Mask then Comp (Alg. 7 without Match), with
+    the pack's column rotation applied to v before the Mask products
+    (mask_pack): the same slots as comp(mask(v)), one key switch per index
+    ciphertext fewer."""
+    return comp_packed(par, mask_pack(par, v_cts, db, keys, plan), keys, plan)
 
 
 # ------------------------------------------------------- closed form ------

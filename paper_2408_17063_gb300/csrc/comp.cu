@@ -3,7 +3,10 @@
 //
 // Schedule (every key switch raises the digits of c1 before the
 // automorphism; additions are exact, so their order is free):
-//   1. pack   u_{2j} = vT_j + Rot_col(dT_j),  u_{2j+1} = Rot_col(vB_j) + dB_j
+//   1. pack   u_{2j} = vT_j + Rot_col(dT_j),  u_{2j+1} = Rot_col(vB_j) + dB_j;
+//             the Answer rotates v_j instead and masks after:
+//             u_{2j} = v_j.[1;0] + Rot_col(v_j).sigma_col(DB_j.[1;0]),
+//             u_{2j+1} = Rot_col(v_j).[1;0] + v_j.(DB_j.[0;1])
 //   2. baby   R[h][a] = Rot(u_h; a), a < B, digits of u_h raised once
 //   3. MAC    acc[gamma][g] = sum_{h in gamma} sum_a Rot(D_{h,gB+a}; -gB) . R[h][a]
 //   4. giant  y_gamma = sum_g Rot(acc[gamma][g]; gB)
@@ -143,8 +146,13 @@ size_t comp_ws_bytes(const Ctx& c, const pdq_plan& pl) {
     return (U + Rx + accx + acc + yx + ys) * sizeof(u64) + raise_ws(c, cnt) + scratch;
 }
 
+// Comp from the masked ciphertexts (masked != nullptr: [J][4] as pdq_mask
+// writes them), or the Answer from the index ciphertexts v_cts and the
+// database db (masked == nullptr: the Mask fused with the pack, w holding J
+// ciphertexts of scratch).
 int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& keys,
-             const u64* consts, u64* out, void* ws, size_t ws_bytes, cudaStream_t st) {
+             const u64* consts, u64* out, void* ws, size_t ws_bytes, cudaStream_t st,
+             const u64* v_cts = nullptr, const u64* db = nullptr, u64* w = nullptr) {
     if (ws_bytes < comp_ws_bytes(c, pl)) return fail(PDQ_E_NOMEM, "comp: workspace too small");
     const long long cts = (long long)ct_elems(c);
     const long long ects = 2LL * (c.L + c.K) * c.N;
@@ -169,9 +177,20 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     const CtSet none{};
     u64* D = nullptr;
 
-    // 1. pack: i = 2j + which; which 0: dT_j (+vT_j), which 1: vB_j (+dB_j)
+    // 1. pack: i = 2j + which; which 0: dT_j (+vT_j), which 1: vB_j (+dB_j);
+    // in the Answer Rot_col(v_j) once per j and the Mask products after it
     prof_mark(c, PDQ_STAGE_PACK, st);
-    {
+    if (!masked) {
+        if (!v_cts || !db || !w) return fail(PDQ_E_PARAM, "answer: null buffer");
+        const u64 kc = 2ull * c.N - 1;
+        const u64* kp;
+        PDQ_TRY(key_for(kc, &kp));
+        const CtSet vin = ct_set(v_cts, cts);
+        PDQ_TRY(ks_raise(c, vin, pl.J, rws, &D, st));
+        PDQ_TRY(ks_apply(c, D, vin, pl.J, (u32)kc, kp, ct_set(w, cts), none, aws, st));
+        prof_mark(c, PDQ_STAGE_MASK, st);
+        PDQ_TRY(mask_pack(c, pl.J, v_cts, w, db, U, st));
+    } else {
         CtSet in;  in.base = masked + 2 * cts;  in.outer = 4 * cts;  in.per = 2;  in.inner = -cts;
         CtSet add; add.base = masked;           add.outer = 4 * cts; add.per = 2; add.inner = 3 * cts;
         const u64* kp;
@@ -404,7 +423,7 @@ int pdq_comp(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* masked,
 size_t pdq_answer_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {
     if (!ctx || !valid_plan(C(ctx), plan)) return 0;
     const Ctx& c = C(ctx);
-    return (size_t)plan->J * 4 * ct_elems(c) * sizeof(u64) + comp_ws_bytes(c, *plan);
+    return (size_t)plan->J * ct_elems(c) * sizeof(u64) + comp_ws_bytes(c, *plan);
 }
 
 int pdq_answer(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
@@ -415,13 +434,12 @@ int pdq_answer(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
     const Ctx& c = C(ctx);
     if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "answer: invalid plan");
     if (ws_bytes < pdq_answer_workspace_bytes(ctx, plan)) return fail(PDQ_E_NOMEM, "answer: workspace too small");
-    u64* masked = reinterpret_cast<u64*>(ws);
-    const size_t mbytes = (size_t)plan->J * 4 * ct_elems(c) * sizeof(u64);
-    prof_mark(c, PDQ_STAGE_MASK, (cudaStream_t)stream);
-    PDQ_TRY(mask(c, plan->J, v_cts, db, masked, (cudaStream_t)stream));
+    if (!v_cts || !db || !keys || !galois || !consts || !out) return fail(PDQ_E_PARAM, "answer: null buffer");
+    u64* w = reinterpret_cast<u64*>(ws);                  // Rot_col(v_j), J ciphertexts
+    const size_t wbytes = (size_t)plan->J * ct_elems(c) * sizeof(u64);
     Keys k{keys, galois, nkeys, (u64)c.ndigits * 2 * (c.L + c.K) * c.N};
-    return comp_run(c, *plan, masked, k, consts, out, reinterpret_cast<char*>(ws) + mbytes,
-                    ws_bytes - mbytes, (cudaStream_t)stream);
+    return comp_run(c, *plan, nullptr, k, consts, out, reinterpret_cast<char*>(ws) + wbytes,
+                    ws_bytes - wbytes, (cudaStream_t)stream, v_cts, db, w);
 }
 
 size_t pdq_answer_host_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {

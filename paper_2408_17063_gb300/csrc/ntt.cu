@@ -107,11 +107,13 @@ struct Phase {
         while (S - lo > kMaxRadixBits) lo += kMaxRadixBits;
         return lo;
     }
-    // A pass whose items put consecutive threads on consecutive global
-    // elements (every column pass; row passes whose pair bits start at 5 or
-    // above) reads or writes global memory directly when it is the first or
-    // the last pass, instead of staging the tile through shared memory.
-    static constexpr bool direct(int lb) { return COLS || lb >= 5; }
+    // A first or last pass reads or writes global memory directly, instead
+    // of staging the tile through shared memory, where its accesses coalesce:
+    // every column pass and row passes whose pair bits start at 5 or above
+    // (consecutive threads on consecutive elements), and row passes whose
+    // pair bits start at 0 (each thread holds 2^R consecutive elements, moved
+    // as 16-byte pairs).
+    static constexpr bool direct(int lb) { return COLS || lb >= 5 || lb == 0; }
     static constexpr bool DIRECT_IN = direct(first_lb());
     static constexpr bool DIRECT_OUT = direct(last_lb());
 
@@ -139,10 +141,19 @@ struct Phase {
             const u32 lbase = (fixed & lowmask) | ((fixed >> LB) << (LB + R));
             const u32 jbase = gidx(c, lbase);
             u64 x[NE];
+            if constexpr (IN_G && !COLS && LB == 0) {
 #pragma unroll
-            for (u32 k = 0; k < NE; ++k) {
-                if constexpr (IN_G) x[k] = gin[gidx(c, lbase | (k << LB))];
-                else x[k] = sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)];
+                for (u32 k = 0; k < NE; k += 2) {
+                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(gin + gidx(c, lbase + k));
+                    x[k] = v.x;
+                    x[k + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (u32 k = 0; k < NE; ++k) {
+                    if constexpr (IN_G) x[k] = gin[gidx(c, lbase | (k << LB))];
+                    else x[k] = sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)];
+                }
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -173,15 +184,22 @@ struct Phase {
                     }
                 }
             }
+            if constexpr (OUT_G) {
+                if (canon) {
 #pragma unroll
-            for (u32 k = 0; k < NE; ++k) {
-                if constexpr (OUT_G) {
-                    u64 v = x[k];
-                    if (canon) v = FWD ? csub(csub(v, 2 * q), q) : csub(v, q);
-                    gout[gidx(c, lbase | (k << LB))] = v;
-                } else {
-                    sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)] = x[k];
+                    for (u32 k = 0; k < NE; ++k) x[k] = FWD ? csub(csub(x[k], 2 * q), q) : csub(x[k], q);
                 }
+                if constexpr (!COLS && LB == 0) {
+#pragma unroll
+                    for (u32 k = 0; k < NE; k += 2)
+                        *reinterpret_cast<ulonglong2*>(gout + gidx(c, lbase + k)) = make_ulonglong2(x[k], x[k + 1]);
+                } else {
+#pragma unroll
+                    for (u32 k = 0; k < NE; ++k) gout[gidx(c, lbase | (k << LB))] = x[k];
+                }
+            } else {
+#pragma unroll
+                for (u32 k = 0; k < NE; ++k) sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)] = x[k];
             }
         }
         if constexpr (!OUT_G) __syncthreads();

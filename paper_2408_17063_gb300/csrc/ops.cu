@@ -266,6 +266,33 @@ __global__ void k_mask(const u64* __restrict__ v, const u64* __restrict__ db,
     }
 }
 
+// Mask fused with the pack (w_j = Rot_col(v_j), NTT form):
+//   u[2j]   = v_j.[1;0] + w_j.sigma_col(DB_j.[1;0])
+//   u[2j+1] = w_j.[1;0] + v_j.(DB_j.[0;1])
+// sigma_col of the NTT-form plaintext is a gather: position x takes the
+// value at the position that holds the conjugate evaluation point.
+__global__ void k_mask_pack(const u64* __restrict__ v, const u64* __restrict__ w,
+                            const u64* __restrict__ db, const u64* __restrict__ rowmask, u32 L,
+                            u32 logN, const Mod* __restrict__ mods, u64* __restrict__ u) {
+    const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 LN = (u64)L << logN;
+    if (r >= LN) return;
+    const u64 j = blockIdx.y;
+    const u32 N = 1u << logN;
+    const u32 l = r >> logN, x = r & (N - 1);
+    const Mod md = mods[l];
+    const u64 top = rowmask[r];
+    const u64 pb = db[j * 2 * LN + ((u64)l << logN) + auto_index(x, 2 * N - 1, logN)];
+    const u64 pd = db[j * 2 * LN + LN + r];
+    u64* o = u + j * 4 * LN;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const u64 vp = v[j * 2 * LN + p * LN + r], wp = w[j * 2 * LN + p * LN + r];
+        o[p * LN + r] = addmod(mulmod(vp, top, md), mulmod(wp, pb, md), md.q);
+        o[(2 + p) * LN + r] = addmod(mulmod(wp, top, md), mulmod(vp, pd, md), md.q);
+    }
+}
+
 // ---------------------------------------------------------- key switching --
 
 // Raise digit b = blockIdx.y of c1 (coefficient form X [cnt][L][N]) of
@@ -1187,6 +1214,14 @@ int decrypt(const Ctx& c, const u64* sk, const u64* ct, u32 count, u32* slots, u
     PDQ_TRY(ntt_forward(c, m, count, 1, c.nmod - 1, c.N, st));
     k_gather_slots<<<grid2(c.N, count), kBlock, 0, st>>>(m, c.log_n, c.d_slot_pos, slots);
     return launched("k_gather_slots");
+}
+
+int mask_pack(const Ctx& c, u32 J, const u64* v, const u64* w, const u64* db, u64* u,
+              cudaStream_t st) {
+    PDQ_TRY(check_y(J, "mask"));
+    k_mask_pack<<<grid2((u64)c.L * c.N, J), kBlock, 0, st>>>(v, w, db, c.d_rowmask, c.L, c.log_n,
+                                                             c.d_mods, u);
+    return launched("k_mask_pack");
 }
 
 int mask(const Ctx& c, u32 J, const u64* v, const u64* db, u64* out, cudaStream_t st) {

@@ -51,6 +51,11 @@ size_t decrypt_ws(const Ctx& c, u32 count);
 int decrypt(const Ctx& c, const u64* sk, const u64* ct, u32 count, u32* slots, u64* ws,
             cudaStream_t st);
 int mask(const Ctx& c, u32 J, const u64* v, const u64* db, u64* out, cudaStream_t st);
+// u[2j] = v_j.[1;0] + w_j.sigma_col(DB_j.[1;0]), u[2j+1] = w_j.[1;0] + v_j.(DB_j.[0;1])
+// with w_j = Rot_col(v_j): the packed u of Comp straight from the index
+// ciphertexts (u [2J][2][L][N])
+int mask_pack(const Ctx& c, u32 J, const u64* v, const u64* w, const u64* db, u64* u,
+              cudaStream_t st);
 
 // Hybrid key switching, split so that the raised digits of c1 can be shared
 // by every rotation of the same ciphertexts (hoisting):

@@ -132,12 +132,21 @@ def test_answer_bit_exact_and_decompresses(setup):
     assert ctx.decomp(setup.plan, slots) == truth
 
 
-def test_comp_alone_equals_answer(setup):
-    ctx = setup.ctx
+def test_comp_alone_bit_exact(setup):
+    """Comp on the masked ciphertexts (the pack of Sec. 5.2) against the
+    oracle's comp; it decrypts to the same slots as the Answer, whose fused
+    Mask and pack give other ciphertexts."""
+    ctx, par = setup.ctx, setup.par
     masked = ctx.mask(setup.plan, setup.v_cts, setup.db)
     a = ctx.comp(setup.plan, masked, setup.keys, setup.galois, setup.consts)
-    b = setup.answer()
-    assert torch.equal(a, b)
+    o_masked = opdq.mask(par, setup.o_v_cts, setup.q.db, setup.oplan)
+    want = opdq.comp(par, o_masked, setup.o_keys, setup.oplan)
+    got = coeff(ctx, a, par.L)
+    for c, w in enumerate(want):
+        assert np.array_equal(got[c], w), c
+    sa = ctx.decrypt(setup.sk, a).cpu().numpy()
+    sb = ctx.decrypt(setup.sk, setup.answer()).cpu().numpy()
+    assert np.array_equal(sa, sb)
 
 
 def test_answer_host_matches_device(setup):

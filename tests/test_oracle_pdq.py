@@ -180,6 +180,47 @@ def test_mask_and_pack_decrypt(cfg_name):
         assert np.array_equal(bfv.decrypt(par, qi.sk, u[h]), np.concatenate([vh, dh]))
 
 
+@pytest.mark.parametrize("cfg_name", ["tiny", "tiny2", "grouped"])
+def test_mask_pack_decrypts_to_packed_halfblocks(cfg_name):
+    """The fused Mask and pack (column rotation of v first) gives u_h with
+    the slots [v_h; d_h] of the half-block, like pack(mask(v))."""
+    cfg, par, qi, plan, keys, v_cts = build(cfg_name)
+    u = pdq.mask_pack(par, v_cts, qi.db, keys, plan)
+    assert len(u) == plan.H
+    t = par.t
+    for h in range(plan.H):
+        rec = np.arange(h * par.m, (h + 1) * par.m)
+        vh = np.zeros(par.m, dtype=np.uint64)
+        dh = np.zeros(par.m, dtype=np.uint64)
+        ok = rec < cfg.n
+        vh[ok] = qi.v[rec[ok]]
+        dh[ok] = qi.v[rec[ok]].astype(np.uint64) * qi.db[rec[ok]] % t
+        assert np.array_equal(bfv.decrypt(par, qi.sk, u[h]), np.concatenate([vh, dh]))
+
+
+@pytest.mark.parametrize("cfg_name", ["tiny", "grouped"])
+def test_sigma_col_of_a_lifted_plaintext_swaps_its_rows(cfg_name):
+    """sigma_{2N-1} applied limb by limb to a lifted plaintext equals the lift
+    of the row-swapped slots (the identity mask_pack relies on)."""
+    from oracle import ring
+    par = bfv.Params.from_config(W.CONFIGS[cfg_name])
+    slots = W.rng_for(41).integers(0, par.t, size=par.N, dtype=np.uint64)
+    lifted = pdq.lifted_pt(par, slots)
+    want = pdq.lifted_pt(par, pdq.swap_rows(par, slots))
+    for i, q in enumerate(par.q):
+        assert np.array_equal(ring.automorphism(lifted[i], par.galois_col, q), want[i])
+
+
+@pytest.mark.parametrize("cfg_name", ["tiny2", "grouped"])
+def test_comp_of_mask_decrypts_to_closed_form(cfg_name):
+    """Comp on the masked ciphertexts (pack as Sec. 5.2 describes) gives the
+    same slots as the Answer's fused schedule."""
+    cfg, par, qi, plan, keys, v_cts = build(cfg_name)
+    outs = pdq.comp(par, pdq.mask(par, v_cts, qi.db, plan), keys, plan)
+    for ct, want in zip(outs, pdq.expected_slots(par, plan, qi.v, qi.db)):
+        assert np.array_equal(bfv.decrypt(par, qi.sk, ct), want)
+
+
 @pytest.mark.parametrize("cfg_name", ["tiny", "tiny2", "grouped", "small", "c1"])
 def test_answer_decrypts_to_closed_form_and_decompresses(cfg_name):
     cfg, par, qi, plan, keys, v_cts = build(cfg_name)
