@@ -402,6 +402,23 @@ def rotate_ext(par: Params, ct, raised, k: int, key) -> np.ndarray:
     return np.stack([poly_add(par, A0, pc0, el), A1])
 
 
+def rotate_ext_lazy(par: Params, ct_ext, raised, k: int, key) -> np.ndarray:
+    """Rotation of an extended-basis ciphertext (c0, c1) over Q u P whose c1
+    was lowered for its key switch (raised = mod_up_all(mod_down(c1))) while
+    c0 stays in Q u P: (sigma_k(c0) + A0, A1), [2][L+K][N].  Since
+    c0 = P ModDown(c0) + r with |r| < K P, a later ModDown gives the rotation
+    of the lowered ciphertext up to less than K + 1 per coefficient; for
+    c0 = P x (special limbs 0) it is rotate_ext exactly."""
+    el = extlimbs(par)
+    A0 = np.zeros((par.L + par.K, par.N), dtype=np.uint64)
+    A1 = np.zeros_like(A0)
+    for b_idx, _ in enumerate(par.digits):
+        d = poly_automorphism(par, raised[b_idx], k, el)
+        A0 = poly_add(par, A0, poly_mul(par, d, key[b_idx][0], el), el)
+        A1 = poly_add(par, A1, poly_mul(par, d, key[b_idx][1], el), el)
+    return np.stack([poly_add(par, A0, poly_automorphism(par, ct_ext[0], k, el), el), A1])
+
+
 def times_P(par: Params, x) -> np.ndarray:
     """P x over the extended basis for x over Q ([L][N] -> [L+K][N]); the
     special-prime limbs are 0."""

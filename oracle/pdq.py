@@ -37,8 +37,10 @@ Readings where the paper is silent (all mirrored by the GPU library):
   ciphertexts as Sec. 5.2 describes.
 * Rotate-and-sum (sum of Rot(y; i s') over i < m/s', Sec. 5.2) runs in levels
   of radix r <= 8 instead of log2(m/s') doublings: each level sums
-  Rot(y; j l), j < r, from one raise of y, in Q u P, lowered once; the slots
-  are the same.
+  Rot(y; j l), j < r, from one raise of y, in Q u P; the slots are the same.
+* A ciphertext over Q u P that is only rotated next keeps c0 in Q u P: only
+  c1 is lowered for the key switch (giant-step accumulators, giant-step
+  sums, rotate-and-sum levels); the result is lowered once at the end.
 """
 from __future__ import annotations
 
@@ -49,7 +51,7 @@ import numpy as np
 
 from . import ring
 from .bfv import (Params, ct_add, ct_mod_down, ct_times_P, decrypt, encode, encrypt, lift,
-                  mod_up_all, poly_add, pt_mul, rotate, rotate_ext)
+                  mod_down, mod_up_all, poly_add, pt_mul, rotate, rotate_ext, rotate_ext_lazy)
 
 
 # ------------------------------------------------------------------ plan ----
@@ -333,38 +335,40 @@ def giant_accumulators(par: Params, R, plan: Plan):
 
 
 def giant_steps(par: Params, acc, keys, plan: Plan):
-    """y_gamma = ModDown( acc[gamma][0] + sum_{g>=1} Rot(ModDown(acc[gamma][g]); gB) ),
-    acc over Q u P: the unrotated accumulator joins the sum as it is, the
-    others are lowered to Q for their key switch, each giant rotation is kept
-    in Q u P, and the sum is lowered to Q once."""
+    """y_gamma = acc[gamma][0] + sum_{g>=1} Rot(acc[gamma][g]; gB) over Q u P:
+    the unrotated accumulator joins the sum as it is; of the others only c1 is
+    lowered to Q (for its key switch), c0 enters the rotation from Q u P
+    (rotate_ext_lazy).  The sums stay in Q u P for the rotate-and-sum."""
     el = list(range(par.L + par.K))
     ys = []
     for gamma in range(plan.G):
         y = acc[gamma][0]
         for g in range(1, plan.giants):
             k = par.galois_rot(g * plan.B)
-            ct = ct_mod_down(par, acc[gamma][g])
-            r = rotate_ext(par, ct, mod_up_all(par, ct[1]), k, keys[k])
+            raised = mod_up_all(par, mod_down(par, acc[gamma][g][1]))
+            r = rotate_ext_lazy(par, acc[gamma][g], raised, k, keys[k])
             y = np.stack([poly_add(par, y[0], r[0], el), poly_add(par, y[1], r[1], el)])
-        ys.append(ct_mod_down(par, y))
+        ys.append(y)
     return ys
 
 
 def rotate_and_sum(par: Params, y, keys, plan: Plan):
     """sum_{i < m/s'} Rot(y; i s') (once, after the blocks were summed,
-    Sec. 5.2), level by level: y <- ModDown( sum_{j<r} Rot(y; j l) ) with the
-    rotations hoisted (one raise of y) and kept in Q u P (j = 0: (P c0, P c1)).
-    The levels multiply out to every i < m/s' exactly once."""
+    Sec. 5.2) for y over Q u P, level by level: y <- sum_{j<r} Rot(y; j l)
+    with the rotations hoisted (one raise of the lowered c1) and kept in
+    Q u P (j = 0: y itself; c0 enters each rotation from Q u P), lowered to Q
+    after the last level.  The levels multiply out to every i < m/s' exactly
+    once."""
     el = list(range(par.L + par.K))
     for l, r in rotsum_levels(par, plan):
-        raised = mod_up_all(par, y[1])
-        acc = ct_times_P(par, y)
+        raised = mod_up_all(par, mod_down(par, y[1]))
+        acc = y
         for j in range(1, r):
             k = par.galois_rot(j * l)
-            rj = rotate_ext(par, y, raised, k, keys[k])
+            rj = rotate_ext_lazy(par, y, raised, k, keys[k])
             acc = np.stack([poly_add(par, acc[0], rj[0], el), poly_add(par, acc[1], rj[1], el)])
-        y = ct_mod_down(par, acc)
-    return y
+        y = acc
+    return ct_mod_down(par, y)
 
 
 def group_mask_slots(par: Params, plan: Plan, o: int) -> np.ndarray:

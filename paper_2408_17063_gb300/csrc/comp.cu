@@ -11,7 +11,10 @@
 //   3. MAC    acc[gamma][g] = sum_{h in gamma} sum_a Rot(D_{h,gB+a}; -gB) . R[h][a]
 //   4. giant  y_gamma = sum_g Rot(acc[gamma][g]; gB)
 //   5. sum    y <- sum_{j<r} Rot(y; j l) per level (l, r) of rotsum_levels:
-//             all i s', i < m/s', each once; one raise and one ModDown per level
+//             all i s', i < m/s', each once; one raise per level
+// Ciphertexts over Q u P that are only rotated next (accumulators, giant
+// sums, rotate-and-sum levels) lower only c1 for the key switch; c0 joins the
+// rotation from Q u P, and the result is lowered once at the end.
 //   6. groups out_c = sum_o M_o . y_{c per_out + o}   (one group: out = y)
 #include <algorithm>
 #include <cstring>
@@ -132,18 +135,44 @@ struct Keys {
     }
 };
 
-size_t comp_ws_bytes(const Ctx& c, const pdq_plan& pl) {
+// Workspace of Comp, in uint64 elements from its start; the one place that
+// fixes both the size and the placement of every region.
+struct CompLayout {
+    u64 U;      // packed u_h over Q, [H]
+    u64 Rx;     // baby steps over Q u P [H][B], later the rotations of one
+                // rotate-and-sum level (at most 8 per group)
+    u64 accx;   // accumulators g >= 1 over Q u P, [G][giants-1]
+    u64 acc;    // ... their c1 lowered to Q, [G][giants-1][L][N]
+    u64 yx;     // giant-step sums over Q u P (from g = 0), [G]
+    u64 Y0, Y1; // rotate-and-sum: the lowered c1 of a level, the output over Q
+    u64 rws;    // key-switch raise scratch
+    u64 aws;    // key-switch apply / ModDown scratch
+    u64 end;
+};
+
+CompLayout comp_layout(const Ctx& c, const pdq_plan& pl) {
     const u64 cts = ct_elems(c), ects = 2ull * (c.L + c.K) * c.N;
-    const u64 U = (u64)pl.H * cts;                       // packed u_h over Q
-    // baby steps over Q u P; later the rotations of one rotate-and-sum level
-    const u64 Rx = (u64)std::max(pl.H * pl.B, pl.G * 8) * ects;
-    const u64 accx = (u64)pl.G * (pl.giants - 1) * ects; // accumulators g >= 1 over Q u P
-    const u64 acc = (u64)pl.G * (pl.giants - 1) * cts;   // ... lowered to Q
-    const u64 yx = (u64)pl.G * ects;                     // giant-step sums over Q u P (from g = 0)
-    const u64 ys = 2ull * pl.G * cts;                    // rotate-and-sum ping-pong
+    const u64 G = pl.G, GI = pl.giants;
     const u32 cnt = std::max(pl.H, pl.G);
-    const size_t scratch = std::max({apply_ws(c, cnt), mod_down_ws(c, std::max(1u, pl.G * (pl.giants - 1)))});
-    return (U + Rx + accx + acc + yx + ys) * sizeof(u64) + raise_ws(c, cnt) + scratch;
+    const u64 scratch = std::max({apply_ws(c, cnt), mod_down_ws(c, pl.G),
+                                  mod_down_polys_ws(c, std::max(1u, pl.G * (pl.giants - 1))),
+                                  mod_down_polys_ws(c, pl.G)}) / sizeof(u64);
+    CompLayout lo;
+    lo.U = 0;
+    lo.Rx = lo.U + (u64)pl.H * cts;
+    lo.accx = lo.Rx + std::max<u64>((u64)pl.H * pl.B, G * 8) * ects;
+    lo.acc = lo.accx + G * (GI - 1) * ects;
+    lo.yx = lo.acc + G * (GI - 1) * cts;
+    lo.Y0 = lo.yx + G * ects;
+    lo.Y1 = lo.Y0 + G * cts;
+    lo.rws = lo.Y1 + G * cts;
+    lo.aws = lo.rws + raise_ws(c, cnt) / sizeof(u64);
+    lo.end = lo.aws + scratch;
+    return lo;
+}
+
+size_t comp_ws_bytes(const Ctx& c, const pdq_plan& pl) {
+    return comp_layout(c, pl).end * sizeof(u64);
 }
 
 // Comp from the masked ciphertexts (masked != nullptr: [J][4] as pdq_mask
@@ -157,15 +186,17 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     const long long cts = (long long)ct_elems(c);
     const long long ects = 2LL * (c.L + c.K) * c.N;
     const u32 H = pl.H, B = pl.B, G = pl.G, GI = pl.giants;
-    u64* U = reinterpret_cast<u64*>(ws);
-    u64* Rx = U + (u64)H * cts;
-    u64* accx = Rx + (u64)H * B * ects;
-    u64* acc = accx + (u64)G * (GI - 1) * ects;
-    u64* yx = acc + (u64)G * (GI - 1) * cts;
-    u64* Y0 = yx + (u64)G * ects;
-    u64* Y1 = Y0 + (u64)G * cts;
-    u64* rws = Y1 + (u64)G * cts;
-    u64* aws = rws + raise_ws(c, std::max(H, G)) / sizeof(u64);
+    const CompLayout lo = comp_layout(c, pl);
+    u64* const base = reinterpret_cast<u64*>(ws);
+    u64* U = base + lo.U;
+    u64* Rx = base + lo.Rx;
+    u64* accx = base + lo.accx;
+    u64* acc = base + lo.acc;
+    u64* yx = base + lo.yx;
+    u64* Y0 = base + lo.Y0;
+    u64* Y1 = base + lo.Y1;
+    u64* rws = base + lo.rws;
+    u64* aws = base + lo.aws;
     const u64* Dg = consts;
     const u64* masks = consts + (u64)pl.hclass * GI * B * (c.L + c.K) * c.N;
 
@@ -213,28 +244,30 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
         PDQ_TRY(baby_steps_ext(c, D, u, H, B, keys.base, koff, Rx, st));
     }
     // 3. diagonal multiply-accumulate over Q u P: the unrotated accumulators
-    // (g = 0) start the giant-step sums yx, the others get one ModDown each
+    // (g = 0) start the giant-step sums yx; of the others only c1 is lowered
+    // (into acc, [G][GI-1][L][N]), c0 stays in Q u P
     prof_mark(c, PDQ_STAGE_MAC, st);
     PDQ_TRY(diag_mac(c, pl, Rx, Dg, yx, accx, st));
     prof_mark(c, PDQ_STAGE_ACC_MODDOWN, st);
-    if (GI > 1) PDQ_TRY(mod_down_batch(c, accx, G * (GI - 1), ct_set(acc, cts), aws, st));
-    // 4. giant steps: sum over Q u P, one ModDown per group
+    const u64 EN = (u64)(c.L + c.K) * c.N, LN = (u64)c.L * c.N;
+    if (GI > 1) PDQ_TRY(mod_down_polys(c, accx + EN, 2 * EN, G * (GI - 1), acc, LN, aws, st));
+    // 4. giant steps: Rot(acc_g; gB) = (sigma(c0) + A0, A1) over Q u P, the
+    // key switch raising the lowered c1, summed into yx
     prof_mark(c, PDQ_STAGE_GIANT, st);
     for (u32 g = 1; g < GI; ++g) {
         const u64 k = galois_rot(c, (long long)g * B);
         const u64* kp;
         PDQ_TRY(key_for(k, &kp));
-        const CtSet in = ct_set(acc + (u64)(g - 1) * cts, (long long)(GI - 1) * cts);
-        PDQ_TRY(ks_raise(c, in, G, rws, &D, st));
-        PDQ_TRY(ks_apply_ext(c, D, in, G, (u32)k, kp, ct_set(yx, ects), true, false, st));
+        const CtSet c1s = ct_set(acc + (u64)(g - 1) * LN, (long long)(GI - 1) * LN);
+        const CtSet c0s = ct_set(accx + (u64)(g - 1) * ects, (long long)(GI - 1) * ects);
+        PDQ_TRY(ks_raise(c, c1s, G, rws, &D, st, 0));
+        PDQ_TRY(ks_apply_ext(c, D, c0s, G, (u32)k, kp, ct_set(yx, ects), true, false, st, true));
     }
-    PDQ_TRY(mod_down_batch(c, yx, G, ct_set(Y0, cts), aws, st));
-    // 5. rotate-and-sum, ping-pong between Y0 and Y1: per level the r
-    // rotations of every y (hoisted, Q u P) into Rx, summed into yx (free
-    // after the giant steps), lowered once
+    // 5. rotate-and-sum on y over Q u P: per level the lowered c1 of every y
+    // (into Y1) is raised once, the r rotations (a = 0: y itself) go to Rx and
+    // are summed back into yx; the last level's sum is lowered to Y0
     prof_mark(c, PDQ_STAGE_ROTSUM, st);
-    u64* ycur = Y0;
-    u64* ynext = Y1;
+    const CtSet y_ext = ct_set(yx, ects);
     for (const auto& [l, r] : rotsum_levels(c, pl)) {
         std::vector<u64> gal(r, 1), koff(r, 0);
         for (u32 j = 1; j < r; ++j) {
@@ -243,13 +276,13 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
             PDQ_TRY(key_for(gal[j], &kp));
             koff[j] = (u64)(kp - keys.base);
         }
-        const CtSet yin = ct_set(ycur, cts);
-        PDQ_TRY(ks_raise(c, yin, G, rws, &D, st));
-        PDQ_TRY(hoisted_rotations_ext(c, D, yin, G, r, gal, keys.base, koff, Rx, st));
+        PDQ_TRY(mod_down_polys(c, yx + EN, 2 * EN, G, Y1, LN, aws, st));
+        PDQ_TRY(ks_raise(c, ct_set(Y1, (long long)LN), G, rws, &D, st, 0));
+        PDQ_TRY(hoisted_rotations_ext(c, D, y_ext, G, r, gal, keys.base, koff, Rx, st, true));
         PDQ_TRY(sum_rotations(c, Rx, G, r, yx, st));
-        PDQ_TRY(mod_down_batch(c, yx, G, ct_set(ynext, cts), aws, st));
-        std::swap(ycur, ynext);
     }
+    PDQ_TRY(mod_down_batch(c, yx, G, ct_set(Y0, cts), aws, st));
+    u64* ycur = Y0;
     // 6. output
     prof_mark(c, PDQ_STAGE_COMBINE, st);
     if (G == 1) {

@@ -376,7 +376,7 @@ int ntt_inverse(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 s
 
 int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_per,
                      long long src_inner, u64 src_off, u64* data, u32 count, u32 nlimbs,
-                     u64 stride, cudaStream_t st) {
+                     u64 stride, cudaStream_t st, u32 limb0) {
     if (src_per == 0) return fail(PDQ_E_PARAM, "ntt: bad source set");
     NttArgs from{};
     from.src = src;
@@ -384,7 +384,7 @@ int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_
     from.src_inner = src_inner;
     from.src_per = src_per;
     from.src_off = src_off;
-    return ntt_run<false>(c, data, count, nlimbs, 0, stride, st, &from);
+    return ntt_run<false>(c, data, count, nlimbs, limb0, stride, st, &from);
 }
 
 }  // namespace pdq

@@ -304,8 +304,8 @@ __global__ void k_mask_pack(const u64* __restrict__ v, const u64* __restrict__ w
 // the target moduli are staged in shared memory.  ALPHA: primes per digit
 // (0: read from `alpha` at run time, at most 8).
 template <int ALPHA>
-__global__ void __launch_bounds__(256) k_modup(const u64* __restrict__ X, CtSet c1ntt, u32 logN,
-                                               u32 L, u32 E, u32 alpha,
+__global__ void __launch_bounds__(256) k_modup(const u64* __restrict__ X, CtSet c1ntt, u64 c1_off,
+                                               u32 logN, u32 L, u32 E, u32 alpha,
                                                const Mod* __restrict__ mods,
                                                const u64* __restrict__ hinv,
                                                const u64* __restrict__ hinvs,
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(256) k_modup(const u64* __restrict__ X, CtSet 
         }
     }
     u64* Dc = D + (((ct * nd + b) * E) << logN) + x;
-    const u64* src = c1ntt.at(ct) + ((u64)L << logN) + x;   // c1 of the input (NTT form)
+    const u64* src = c1ntt.at(ct) + c1_off + x;             // c1 of the input (NTT form)
     for (u32 r = 0; r < E; ++r) {
         u64* o = Dc + ((u64)r << logN);
         if (r >= lo && r < hi) {
@@ -411,9 +411,9 @@ __global__ void k_ks_inner(const u64* __restrict__ D, const u64* __restrict__ ke
 //   out[ct][1][r] (+)= sum_beta D[ct][beta][r][s(x)] key[beta][1][r][x]
 // with s = sigma_k; `accumulate` adds into out instead of overwriting it.
 __global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict__ key, u32 logN,
-                               u32 E, u32 L, u32 nd, u32 galois, const Mod* __restrict__ mods,
-                               CtSet c0src, const u64* __restrict__ Pm, CtSet out,
-                               u32 accumulate, u32 split) {
+                               u32 E, u32 c0_limbs, u32 nd, u32 galois,
+                               const Mod* __restrict__ mods, CtSet c0src,
+                               const u64* __restrict__ Pm, CtSet out, u32 accumulate, u32 split) {
     const u32 r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const u64 EN = (u64)E << logN;
     if (r >= EN) return;
@@ -435,14 +435,16 @@ __global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict_
         mac128(h1b, l1b, db, k1.y);
     }
     // P sigma(c0) joins the sum as c0 times P R (the digits carry R), then one
-    // Montgomery reduction per output
-    if (l < L) {
+    // Montgomery reduction per output; a c0 over Q u P (Pm == nullptr, all
+    // limbs) joins as c0 times R
+    const Mod md = mods[l];
+    if (l < c0_limbs) {
         const ulonglong2 cv = *reinterpret_cast<const ulonglong2*>(c0src.at(ct) + sr);
         const u64 ca = swap ? cv.y : cv.x, cb = swap ? cv.x : cv.y;
-        mac128(h0a, l0a, ca, Pm[l]);
-        mac128(h0b, l0b, cb, Pm[l]);
+        const u64 cm = Pm ? Pm[l] : md.r64;
+        mac128(h0a, l0a, ca, cm);
+        mac128(h0b, l0b, cb, cm);
     }
-    const Mod md = mods[l];
     u64 a0 = redc128(h0a, l0a, md), b0 = redc128(h0b, l0b, md);
     u64 a1 = redc128(h1a, l1a, md), b1 = redc128(h1b, l1b, md);
     ulonglong2* o0 = reinterpret_cast<ulonglong2*>(out.at(ct) + r);
@@ -517,8 +519,11 @@ struct BabyParams {
 template <int T, int HC, int CPT, int ND>
 __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
         const u64* __restrict__ D, CtSet u, const u64* __restrict__ keys, u32 H, u32 B, u32 logN,
-        u32 E, u32 L, const Mod* __restrict__ mods, const u64* __restrict__ Pm,
+        u32 E, u32 L, u32 c1_limb, const Mod* __restrict__ mods, const u64* __restrict__ Pm,
         u64* __restrict__ Rx, const BabyParams bp) {
+    // L: limbs of c0 (L for ciphertexts over Q, whose c0 joins as P c0 with
+    // Pm = P R; L + K for ciphertexts over Q u P, Pm == nullptr: c0 joins as
+    // c0 R, and a = 0 is the input itself); c1 starts at limb c1_limb
     // The digit tile (and c0) of HC ciphertexts is staged in shared memory
     // once and only read afterwards; every thread keeps the 2 ND key values of
     // its position in registers, loaded one rotation ahead, so the rotation
@@ -543,13 +548,13 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
             const u32 yy = (e % TP) * 2, ct = e / TP, h = h0 + ct;
             const u64* src = u.at(h < H ? h : 0) + ((u64)r << logN) + y0 + yy;
             cp_async16(Cs + ct * T + yy, src, h < H);
-            cp_async16(C1s + ct * T + yy, src + ((u64)L << logN), h < H);
+            cp_async16(C1s + ct * T + yy, src + ((u64)c1_limb << logN), h < H);
         }
     }
     cp_async_commit();
 
     const Mod md = mods[r];
-    const u64 PR = r < L ? Pm[r] : 0;               // P 2^64 mod q_r
+    const u64 PR = r < L ? (Pm ? Pm[r] : md.r64) : 0;   // P 2^64 (or 2^64) mod q_r
     const u32 xi = threadIdx.x % T, hg = threadIdx.x / T;
     // key values of rotation a at this thread's position (the position whose
     // source lies in this tile)
@@ -670,10 +675,11 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
     }
 }
 
-// (P c0, P c1) over Q u P from a ciphertext over Q (special limbs 0)
+// (P c0, P c1) over Q u P from a ciphertext over Q (special limbs 0); with
+// `ext` the input is over Q u P already and is copied
 __global__ void k_times_P(CtSet in, u32 logN, u32 L, u32 E, const Mod* __restrict__ mods,
                           const u64* __restrict__ Pq, const u64* __restrict__ Pqs, CtSet out,
-                          u32 split) {
+                          u32 split, u32 ext) {
     const u32 rr = blockIdx.x * blockDim.x + threadIdx.x;     // over [2][E][N]
     const u32 EN = E << logN;
     if (rr >= 2 * EN) return;
@@ -682,7 +688,9 @@ __global__ void k_times_P(CtSet in, u32 logN, u32 L, u32 E, const Mod* __restric
     const u32 r = rr - p * EN;
     const u32 l = r >> logN;
     u64 v = 0;
-    if (l < L) {
+    if (ext) {
+        v = in.at(ct)[rr];
+    } else if (l < L) {
         const u64 q = mods[l].q;
         v = csub(mul_shoup_lazy(in.at(ct)[(u64)p * (L << logN) + r], Pq[l], Pqs[l], q), q);
     }
@@ -714,7 +722,8 @@ __global__ void k_sum_split(const u64* __restrict__ Rx, u32 R, u32 logN, u32 E,
 // Conv[cp][i] = sum_k [y_k (P/p_k)^-1]_{p_k} (P/p_k) mod q_i from the special
 // limbs of A (coefficient form); cp = blockIdx.y = ct*2 + p
 template <int KK>
-__global__ void __launch_bounds__(256) k_moddown_conv(const u64* __restrict__ A, u32 logN, u32 L,
+__global__ void __launch_bounds__(256) k_moddown_conv(const u64* __restrict__ Asp, u64 sp_stride,
+                                                      u32 logN, u32 L,
                                                       u32 K, const Mod* __restrict__ mods,
                                                       const u64* __restrict__ hinv,
                                                       const u64* __restrict__ hinvs,
@@ -733,13 +742,13 @@ __global__ void __launch_bounds__(256) k_moddown_conv(const u64* __restrict__ A,
     const u32 x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= (1u << logN)) return;
     const u64 cp = blockIdx.y;
-    const u64* a = A + ((cp * E) << logN) + x;
+    const u64* a = Asp + cp * sp_stride + x;     // special limb k at a + k N
     u64 y0[8], y1[8];
 #pragma unroll
     for (u32 k = 0; k < (KK ? (u32)KK : 8u); ++k) {
         if (k < K) {
             const u64 pk = sq[L + k].x;
-            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(a + ((u64)(L + k) << logN));
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(a + ((u64)k << logN));
             y0[k] = csub(mul_shoup_lazy(v.x, hinv[k], hinvs[k], pk), pk);
             y1[k] = csub(mul_shoup_lazy(v.y, hinv[k], hinvs[k], pk), pk);
         }
@@ -798,6 +807,27 @@ __global__ void k_moddown_final(const u64* __restrict__ A, const u64* __restrict
         v1 = addmod(v1, dv.y, q);
     }
     *reinterpret_cast<ulonglong2*>(out.at(ct) + rr) = make_ulonglong2(v0, v1);
+}
+
+// out[i] = (A[i] - Cv[i]) P^-1 over Q for polynomials A[i] = A + i a_stride
+// (NTT form, Q limbs first); two adjacent positions per thread
+__global__ void k_moddown_final_poly(const u64* __restrict__ A, u64 a_stride,
+                                     const u64* __restrict__ Cv, u64* __restrict__ out,
+                                     u64 out_stride, u32 logN, u32 L,
+                                     const Mod* __restrict__ mods, const u64* __restrict__ pinv,
+                                     const u64* __restrict__ pinvs) {
+    const u32 r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const u32 LN = L << logN;
+    if (r >= LN) return;
+    const u64 i = blockIdx.y;
+    const u32 l = r >> logN;
+    const u64 q = mods[l].q;
+    const u64 pv = pinv[l], pvs = pinvs[l];
+    const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(A + i * a_stride + r);
+    const ulonglong2 cv = *reinterpret_cast<const ulonglong2*>(Cv + i * LN + r);
+    *reinterpret_cast<ulonglong2*>(out + i * out_stride + r) =
+        make_ulonglong2(csub(mul_shoup_lazy(submod(a.x, cv.x, q), pv, pvs, q), q),
+                        csub(mul_shoup_lazy(submod(a.y, cv.y, q), pv, pvs, q), q));
 }
 
 // ----------------------------------------------------------- Comp kernels --
@@ -1234,12 +1264,15 @@ int mask(const Ctx& c, u32 J, const u64* v, const u64* db, u64* out, cudaStream_
 // ---- key switching pieces ---------------------------------------------------
 
 // Cv[cp][l] = sum_k [A[cp][L+k] (P/p_k)^-1]_{p_k} (P/p_k) mod q_l (coefficient form)
-int moddown_conv(const Ctx& c, const u64* A, u32 cps, u64* Cv, cudaStream_t st) {
+// Conv of cps polynomials whose special limbs (coefficient form) start at
+// Asp + cp * sp_stride, limb k at + k N
+int moddown_conv(const Ctx& c, const u64* Asp, u64 sp_stride, u32 cps, u64* Cv, cudaStream_t st) {
     if (c.K > 8 || c.L + c.K > 40 || c.L > 32) return fail(PDQ_E_PARAM, "ModDown: too many primes");
     PDQ_TRY(check_y(cps, "ModDown"));
     const dim3 grid((c.N / 2 + kBlock - 1) / kBlock, cps);
 #define PDQ_CONV(KK)                                                                              \
-    k_moddown_conv<KK><<<grid, kBlock, 0, st>>>(A, c.log_n, c.L, c.K, c.d_mods, c.d_dn_hatinv,     \
+    k_moddown_conv<KK><<<grid, kBlock, 0, st>>>(Asp, sp_stride, c.log_n, c.L, c.K, c.d_mods,       \
+                                                c.d_dn_hatinv,                                     \
                                                 c.d_dn_hatinv_shoup, c.d_dn_hatmod,                \
                                                 c.d_dn_hatmod_shoup, Cv)
     switch (c.K) {
@@ -1257,19 +1290,20 @@ size_t raise_ws(const Ctx& c, u32 cnt) {
     return (size_t)cnt * ((u64)c.L + (u64)c.ndigits * E) * c.N * sizeof(u64);
 }
 
-int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t st) {
+int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t st, u64 c1_off) {
     const u64 N = c.N, L = c.L, E = c.L + c.K, nd = c.ndigits;
     PDQ_TRY(check_y(cnt, "key switch"));
+    if (c1_off == ~0ull) c1_off = L * N;
     u64* X = ws;
     u64* D = ws + cnt * L * N;
     // c1 of every ciphertext, coefficient form, into X (the transform reads
     // the set directly)
-    PDQ_TRY(ntt_inverse_from(c, in.base, in.outer, in.per, in.inner, L * N, X, cnt, c.L, L * N,
+    PDQ_TRY(ntt_inverse_from(c, in.base, in.outer, in.per, in.inner, c1_off, X, cnt, c.L, L * N,
                              st));
     if (E > 32 || c.alpha > 8) return fail(PDQ_E_PARAM, "key switch: too many primes per digit");
     const dim3 grid((c.N / 2 + kBlock - 1) / kBlock, (u32)nd, cnt);
 #define PDQ_MODUP(A)                                                                              \
-    k_modup<A><<<grid, kBlock, 0, st>>>(X, in, c.log_n, c.L, (u32)E, c.alpha, c.d_mods,            \
+    k_modup<A><<<grid, kBlock, 0, st>>>(X, in, c1_off, c.log_n, c.L, (u32)E, c.alpha, c.d_mods,    \
                                         c.d_up_hatinv, c.d_up_hatinv_shoup, c.d_up_hatmod_mont,    \
                                         c.d_up_hatmod_mont_shoup, D)
     switch (c.alpha) {
@@ -1306,7 +1340,7 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
                                                          galois, c.d_mods, A);
     PDQ_TRY(launched("k_ks_inner"));
     PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
-    PDQ_TRY(moddown_conv(c, A, 2 * cnt, Cv, st));
+    PDQ_TRY(moddown_conv(c, A + L * N, E * N, 2 * cnt, Cv, st));
     PDQ_TRY(ntt_forward(c, Cv, 2 * cnt, c.L, 0, L * N, st));
     k_moddown_final<<<grid2(L * N, cnt), kBlock, 0, st>>>(A, Cv, in, out, add, c.log_n, c.L,
                                                               c.K, galois, c.d_mods, c.d_dn_pinv,
@@ -1315,13 +1349,13 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
 }
 
 int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, const u64* key,
-                 CtSet out, bool accumulate, bool split, cudaStream_t st) {
+                 CtSet out, bool accumulate, bool split, cudaStream_t st, bool c0_ext) {
     const u64 N = c.N, E = c.L + c.K;
     PDQ_TRY(check_y(cnt, "key switch"));
     if (accumulate && split) return fail(PDQ_E_PARAM, "ks_apply_ext: cannot accumulate split output");
     k_ks_inner_ext<<<grid2(E * N / 2, cnt), kBlock, 0, st>>>(
-        D, key, c.log_n, (u32)E, c.L, c.ndigits, galois, c.d_mods, c0src, c.d_P_mont, out,
-        accumulate ? 1u : 0u, split ? 1u : 0u);
+        D, key, c.log_n, (u32)E, c0_ext ? (u32)E : c.L, c.ndigits, galois, c.d_mods, c0src,
+        c0_ext ? nullptr : c.d_P_mont, out, accumulate ? 1u : 0u, split ? 1u : 0u);
     return launched("k_ks_inner_ext");
 }
 
@@ -1329,7 +1363,7 @@ namespace {
 
 template <int ND>
 int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
-                const BabyParams& bp, u64* Rx, cudaStream_t st) {
+                const BabyParams& bp, u64* Rx, cudaStream_t st, bool ext) {
     constexpr u32 T = 64, HC = 16, CPT = 4;
     const u32 E = c.L + c.K;
     const size_t smem = ((size_t)HC * ND * T + 2 * HC * T) * sizeof(u64);
@@ -1341,8 +1375,9 @@ int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* ke
         configured = true;
     }
     const dim3 grid(c.N / T, E, (H + HC - 1) / HC);
-    k_baby_ext<T, HC, CPT, ND><<<grid, T * HC / CPT, smem, st>>>(D, u, keys, H, B, c.log_n, E, c.L,
-                                                                 c.d_mods, c.d_P_mont, Rx, bp);
+    k_baby_ext<T, HC, CPT, ND><<<grid, T * HC / CPT, smem, st>>>(
+        D, u, keys, H, B, c.log_n, E, ext ? E : c.L, ext ? E : c.L, c.d_mods,
+        ext ? nullptr : c.d_P_mont, Rx, bp);
     return launched("k_baby_ext");
 }
 
@@ -1352,12 +1387,13 @@ int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64*
                    const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st) {
     std::vector<u64> galois(B, 1);
     for (u32 a = 1; a < B; ++a) galois[a] = host_powmod(3, a, 2ull * c.N);
-    return hoisted_rotations_ext(c, D, u, H, B, galois, keys, key_offsets, Rx, st);
+    return hoisted_rotations_ext(c, D, u, H, B, galois, keys, key_offsets, Rx, st, false);
 }
 
 int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
                           const std::vector<u64>& galois, const u64* keys,
-                          const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st) {
+                          const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st,
+                          bool ext) {
     constexpr u32 T = 64;
     if (B > 128) return fail(PDQ_E_PARAM, "hoisted rotations: at most 128");
     if (galois.size() < B || key_offsets.size() < B)
@@ -1368,12 +1404,12 @@ int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
     if (c.N < T || c.ndigits > 8) {
         // rings below one tile, or more digits than the fused kernel keeps
         // in registers: one rotation at a time
-        PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * 2 * (c.L + c.K) * c.N), true, st));
+        PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * 2 * (c.L + c.K) * c.N), true, st, ext));
         for (u32 a = 1; a < B; ++a) {
             PDQ_TRY(ks_apply_ext(c, D, u, H, (u32)galois[a], keys + key_offsets[a],
                                  ct_set(Rx + (u64)a * 2 * (c.L + c.K) * c.N,
                                         (long long)B * 2 * (c.L + c.K) * c.N),
-                                 false, true, st));
+                                 false, true, st, ext));
         }
         return PDQ_OK;
     }
@@ -1384,14 +1420,14 @@ int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
         bp.koff[a] = key_offsets[a];
     }
     switch (c.ndigits) {
-        case 1: return launch_baby<1>(c, D, u, H, B, keys, bp, Rx, st);
-        case 2: return launch_baby<2>(c, D, u, H, B, keys, bp, Rx, st);
-        case 3: return launch_baby<3>(c, D, u, H, B, keys, bp, Rx, st);
-        case 4: return launch_baby<4>(c, D, u, H, B, keys, bp, Rx, st);
-        case 5: return launch_baby<5>(c, D, u, H, B, keys, bp, Rx, st);
-        case 6: return launch_baby<6>(c, D, u, H, B, keys, bp, Rx, st);
-        case 7: return launch_baby<7>(c, D, u, H, B, keys, bp, Rx, st);
-        default: return launch_baby<8>(c, D, u, H, B, keys, bp, Rx, st);
+        case 1: return launch_baby<1>(c, D, u, H, B, keys, bp, Rx, st, ext);
+        case 2: return launch_baby<2>(c, D, u, H, B, keys, bp, Rx, st, ext);
+        case 3: return launch_baby<3>(c, D, u, H, B, keys, bp, Rx, st, ext);
+        case 4: return launch_baby<4>(c, D, u, H, B, keys, bp, Rx, st, ext);
+        case 5: return launch_baby<5>(c, D, u, H, B, keys, bp, Rx, st, ext);
+        case 6: return launch_baby<6>(c, D, u, H, B, keys, bp, Rx, st, ext);
+        case 7: return launch_baby<7>(c, D, u, H, B, keys, bp, Rx, st, ext);
+        default: return launch_baby<8>(c, D, u, H, B, keys, bp, Rx, st, ext);
     }
 }
 
@@ -1403,23 +1439,42 @@ int sum_rotations(const Ctx& c, const u64* Rx, u32 cnt, u32 R, u64* out, cudaStr
     return launched("k_sum_split");
 }
 
-int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, bool split, cudaStream_t st) {
+int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, bool split, cudaStream_t st, bool ext) {
     const u64 E = c.L + c.K;
     PDQ_TRY(check_y(cnt, "times_P"));
     k_times_P<<<grid2(2 * E * c.N, cnt), kBlock, 0, st>>>(in, c.log_n, c.L, (u32)E, c.d_mods,
                                                          c.d_P_mod_q, c.d_P_mod_q_shoup, out,
-                                                         split ? 1u : 0u);
+                                                         split ? 1u : 0u, ext ? 1u : 0u);
     return launched("k_times_P");
 }
 
 size_t mod_down_ws(const Ctx& c, u32 cnt) { return (size_t)cnt * 2 * c.L * c.N * sizeof(u64); }
+
+size_t mod_down_polys_ws(const Ctx& c, u32 npolys) {
+    return (size_t)npolys * (c.L + c.K) * c.N * sizeof(u64);
+}
+
+int mod_down_polys(const Ctx& c, const u64* A, u64 a_stride, u32 npolys, u64* out,
+                   u64 out_stride, u64* ws, cudaStream_t st) {
+    const u64 N = c.N, L = c.L, K = c.K;
+    PDQ_TRY(check_y(npolys, "mod_down"));
+    u64* S = ws;                      // special limbs, coefficient form [npolys][K][N]
+    u64* Cv = ws + (u64)npolys * K * N;
+    PDQ_TRY(ntt_inverse_from(c, A, (long long)a_stride, 1, 0, L * N, S, npolys, c.K, K * N, st,
+                             c.L));
+    PDQ_TRY(moddown_conv(c, S, K * N, npolys, Cv, st));
+    PDQ_TRY(ntt_forward(c, Cv, npolys, c.L, 0, L * N, st));
+    k_moddown_final_poly<<<grid2(L * N / 2, npolys), kBlock, 0, st>>>(
+        A, a_stride, Cv, out, out_stride, c.log_n, c.L, c.d_mods, c.d_dn_pinv, c.d_dn_pinv_shoup);
+    return launched("k_moddown_final_poly");
+}
 
 int mod_down_batch(const Ctx& c, u64* A, u32 cnt, CtSet out, u64* ws, cudaStream_t st) {
     const u64 N = c.N, L = c.L, E = c.L + c.K;
     PDQ_TRY(check_y(2ull * cnt, "mod_down"));
     u64* Cv = ws;
     PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
-    PDQ_TRY(moddown_conv(c, A, 2 * cnt, Cv, st));
+    PDQ_TRY(moddown_conv(c, A + L * N, E * N, 2 * cnt, Cv, st));
     PDQ_TRY(ntt_forward(c, Cv, 2 * cnt, c.L, 0, L * N, st));
     k_moddown_final<<<grid2(L * N, cnt), kBlock, 0, st>>>(A, Cv, CtSet{}, out, CtSet{}, c.log_n,
                                                               c.L, c.K, 0, c.d_mods, c.d_dn_pinv,

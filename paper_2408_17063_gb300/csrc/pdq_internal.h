@@ -193,11 +193,12 @@ int ntt_forward(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 s
                 cudaStream_t st);
 int ntt_inverse(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
                 cudaStream_t st);
-// Inverse transform of limbs 0..nlimbs-1 of `count` groups read from a
-// strided set (group g at src + (g / src_per) src_outer + (g % src_per)
-// src_inner + src_off, limb l at + l N), written to data + g stride.
+// Inverse transform of `count` groups of nlimbs limbs (moduli limb0 ..)
+// read from a strided set (group g at src + (g / src_per) src_outer +
+// (g % src_per) src_inner + src_off, limb l at + l N), written to
+// data + g stride.
 int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_per,
                      long long src_inner, u64 src_off, u64* data, u32 count, u32 nlimbs,
-                     u64 stride, cudaStream_t st);
+                     u64 stride, cudaStream_t st, u32 limb0 = 0);
 
 }  // namespace pdq

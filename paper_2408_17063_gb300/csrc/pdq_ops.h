@@ -64,7 +64,10 @@ int mask_pack(const Ctx& c, u32 J, const u64* v, const u64* w, const u64* db, u6
 //             ModDown(sum_beta sigma_k(D[i][beta]) * key[beta][1])   (+ add[i])
 size_t raise_ws(const Ctx& c, u32 cnt);   // holds D (returned) and a scratch copy of c1
 size_t apply_ws(const Ctx& c, u32 cnt);
-int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t st);
+// (c1 of ciphertext i at in.at(i) + c1_off; default L N, c1 of a ciphertext
+// over Q; 0 raises a set of polynomials)
+int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t st,
+             u64 c1_off = ~0ull);
 int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u64* key,
              CtSet out, CtSet add, u64* ws, cudaStream_t st);
 
@@ -72,27 +75,38 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
 // Q u P, out ciphertexts [2][L+K][N]
 // (`split`: residues stored as v0 | v1 << 32, v = v0 + v1 2^30, the operand
 // layout of diag_mac; not combinable with `accumulate`)
+// (c0_ext: c0src holds ciphertexts over Q u P and sigma(c0) joins on every
+// limb as it is, instead of P sigma(c0) of a c0 over Q)
 int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, const u64* key,
-                 CtSet out, bool accumulate, bool split, cudaStream_t st);
+                 CtSet out, bool accumulate, bool split, cudaStream_t st, bool c0_ext = false);
 // All baby-step rotations a = 0..B-1 of the H ciphertexts u (raised digits
 // D; a = 0 is (P c0, P c1)) written to Rx[h][a] in the split operand layout;
 // key a at keys + key_offsets[a] (B >= 2)
 int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
                    const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st);
 // The same for any Galois elements: Rx[h][a] = sigma_{galois[a]}(u_h) with
-// key a (a = 1..B-1; a = 0 is (P c0, P c1)), split operand layout
+// key a (a = 1..B-1; a = 0 is (P c0, P c1)), split operand layout.  With
+// `ext` the u_h are over Q u P ([2][L+K][N], D raised from their lowered c1):
+// rotation a is (sigma(c0) + A0, A1) and a = 0 is u_h itself.
 int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
                           const std::vector<u64>& galois, const u64* keys,
-                          const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st);
+                          const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st,
+                          bool ext = false);
 // out[h] = sum_{a<R} Rx[h][a] (Rx [cnt][R][2][L+K][N] split, out [cnt][2][L+K][N]
 // canonical), R <= 8
 int sum_rotations(const Ctx& c, const u64* Rx, u32 cnt, u32 R, u64* out, cudaStream_t st);
 // (P c0, P c1) over Q u P
-int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, bool split, cudaStream_t st);
+int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, bool split, cudaStream_t st,
+            bool ext = false);   // ext: copy of a ciphertext over Q u P
 // ModDown of cnt extended-basis ciphertexts A ([cnt][2][L+K][N], special limbs
 // clobbered) into out (Q basis)
 size_t mod_down_ws(const Ctx& c, u32 cnt);
 int mod_down_batch(const Ctx& c, u64* A, u32 cnt, CtSet out, u64* ws, cudaStream_t st);
+// ModDown of npolys polynomials over Q u P (polynomial i at A + i a_stride,
+// [L+K][N], left unchanged) into out + i out_stride ([L][N])
+size_t mod_down_polys_ws(const Ctx& c, u32 npolys);
+int mod_down_polys(const Ctx& c, const u64* A, u64 a_stride, u32 npolys, u64* out,
+                   u64 out_stride, u64* ws, cudaStream_t st);
 
 int gather_rows(CtSet src, long long src_off, u32 cnt, u64 len, u64* dst, u64 dst_stride,
                 cudaStream_t st);

@@ -230,3 +230,29 @@ def test_extended_rotation_lowers_to_the_rotation(cfg):
     ext = bfv.rotate_ext(par, ct, bfv.mod_up_all(par, ct[1]), k, key)
     assert np.array_equal(bfv.ct_mod_down(par, ext), bfv.rotate(par, ct, k, key))
     assert np.array_equal(bfv.ct_mod_down(par, bfv.ct_times_P(par, ct)), ct)
+
+
+@pytest.mark.parametrize("cfg", ["tiny", "tiny2"])
+def test_lazy_extended_rotation(cfg):
+    """rotate_ext_lazy (c0 from Q u P, c1 lowered for the key switch) equals
+    rotate_ext when c0 = P x, and on a genuine extended ciphertext (special
+    limbs of c0 nonzero) lowers to a ciphertext of the rotated slots."""
+    par = bfv.Params.from_config(W.CONFIGS[cfg])
+    sk = _key_material(par, 25)
+    a, e = W.encryption_randomness(par.q, par.N, 1, seed=25)
+    slots = W.rng_for(26).integers(0, par.t, size=par.N, dtype=np.uint64)
+    ct = bfv.encrypt(par, sk, bfv.encode(par, slots), a[0], e[0])
+    ks = [par.galois_rot(1), par.galois_rot(3), par.galois_col]
+    kr = W.rotation_key_randomness(par.ext, par.N, len(par.digits), ks, seed=27)
+    keys = {k: bfv.rotation_key(par, sk, k, *kr[k]) for k in ks}
+    raised = bfv.mod_up_all(par, ct[1])
+    k1 = par.galois_rot(1)
+    x = bfv.rotate_ext_lazy(par, bfv.ct_times_P(par, ct), raised, k1, keys[k1])
+    assert np.array_equal(x, bfv.rotate_ext(par, ct, raised, k1, keys[k1]))
+    assert np.any(x[0][par.L:] != 0)
+    rows = slots.reshape(2, par.m)
+    for k2, want in ((par.galois_rot(3), np.roll(rows, -4, axis=1)),
+                     (par.galois_col, np.roll(rows, -1, axis=1)[::-1])):
+        r2 = bfv.mod_up_all(par, bfv.mod_down(par, x[1]))
+        y = bfv.ct_mod_down(par, bfv.rotate_ext_lazy(par, x, r2, k2, keys[k2]))
+        assert np.array_equal(bfv.decrypt(par, sk, y).reshape(2, par.m), want)

@@ -86,7 +86,8 @@ def test_rotate_and_sum_is_the_sum_of_rotations():
                  for j in range(1, r)})
     kr = W.rotation_key_randomness(par.ext, par.N, len(par.digits), ks, seed=33)
     keys = {k: bfv.rotation_key(par, sk, k, *kr[k]) for k in ks}
-    got = bfv.decrypt(par, sk, pdq.rotate_and_sum(par, ct, keys, plan)).reshape(2, par.m)
+    y = pdq.rotate_and_sum(par, bfv.ct_times_P(par, ct), keys, plan)
+    got = bfv.decrypt(par, sk, y).reshape(2, par.m)
     rows = slots.reshape(2, par.m).astype(np.int64)
     want = sum(np.roll(rows, -i * plan.s_prime, axis=1) for i in range(16)) % par.t
     assert np.array_equal(got.astype(np.int64), want)
