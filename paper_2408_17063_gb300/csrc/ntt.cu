@@ -49,6 +49,9 @@ struct NttArgs {
     long long src_outer, src_inner;
     u32 src_per;
     u64 src_off;
+    // raised digits (skip_alpha > 0): group g is digit g % skip_nd of a
+    // ciphertext, and its limbs skip the digit's own skip_alpha limbs
+    u32 skip_nd, skip_alpha;
 };
 
 __device__ __forceinline__ void bf_fwd(u64& x, u64& y, u64 w, u64 wp, u64 q) {
@@ -233,7 +236,12 @@ template <bool FWD, int S, bool COLS, bool SINGLE>
 __global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
     __shared__ __align__(16) u64 sm[kTile];
     const u32 p = blockIdx.x;
-    const u32 grp = p / a.nlimbs, limb = p - grp * a.nlimbs;
+    const u32 grp = p / a.nlimbs;
+    u32 limb = p - grp * a.nlimbs;
+    if (a.skip_alpha) {
+        const u32 own = (grp % a.skip_nd) * a.skip_alpha;
+        if (limb >= own) limb += a.skip_alpha;
+    }
     const u32 mi = a.limb0 + limb;
     const u32 N = 1u << a.logN;
     u64* base = a.data + (u64)grp * a.stride + (u64)limb * N;
@@ -312,9 +320,9 @@ int launch_phase(int S, dim3 grid, u32 threads, const NttArgs& a, cudaStream_t s
 
 template <bool FWD>
 int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
-            cudaStream_t st, const NttArgs* from = nullptr) {
+            cudaStream_t st, const NttArgs* from = nullptr, u32 skip_nd = 0, u32 skip_alpha = 0) {
     if (count == 0 || nlimbs == 0) return PDQ_OK;
-    if (limb0 + nlimbs > c.nmod) return fail(PDQ_E_PARAM, "ntt: limb range out of bounds");
+    if (limb0 + nlimbs + skip_alpha > c.nmod) return fail(PDQ_E_PARAM, "ntt: limb range out of bounds");
     const u64 polys = (u64)count * nlimbs;
     if (polys > 0x7fffffffULL) return fail(PDQ_E_PARAM, "ntt: too many polynomials");
     NttArgs a{};
@@ -326,6 +334,8 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
     a.tw = reinterpret_cast<const ulonglong2*>(FWD ? c.d_fw2 : c.d_iw2);
     a.ninv4 = c.d_ninv;
     a.logN = c.log_n;
+    a.skip_nd = skip_nd;
+    a.skip_alpha = skip_alpha;
     if (from) {
         a.src = from->src;
         a.src_outer = from->src_outer;
@@ -372,6 +382,13 @@ int ntt_forward(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 s
 int ntt_inverse(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
                 cudaStream_t st) {
     return ntt_run<false>(c, data, count, nlimbs, limb0, stride, st);
+}
+
+int ntt_forward_digits(const Ctx& c, u64* D, u32 count, u32 nd, u32 alpha, u32 nlimbs,
+                       cudaStream_t st) {
+    if (nd == 0 || alpha == 0) return fail(PDQ_E_PARAM, "ntt: bad digit layout");
+    return ntt_run<true>(c, D, count * nd, nlimbs - alpha, 0, (u64)nlimbs * c.N, st, nullptr, nd,
+                         alpha);
 }
 
 int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_per,

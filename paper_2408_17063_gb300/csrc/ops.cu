@@ -572,7 +572,10 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
     load_keys(1, kc, xc);
     cp_async_wait<0>();
     __syncthreads();
-    // a = 0: (P c0, P c1) over Q u P (zero on the special primes)
+    // a = 0: (P c0, P c1) over Q u P (zero on the special primes), or the
+    // input itself when it is over Q u P (PR = R); each thread keeps the
+    // P c0 it computed in the c0 tile, which every rotation adds after its
+    // reduction
 #pragma unroll
     for (int i = 0; i < CPT; ++i) {
         const u32 ct = hg * CPT + i, h = h0 + ct;
@@ -585,89 +588,50 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
             hi = lo = 0;
             mac128(hi, lo, C1s[ct * T + xi], PR);
             v1 = redc128(hi, lo, md);
+            Cs[ct * T + xi] = v0;
         }
         u64* o = Rx + ((u64)h * B * 2) * EN + ((u64)r << logN) + y0 + xi;
         o[0] = split30(v0);
         o[EN] = split30(v1);
     }
-    // Up to 7 digits (with the c0 term at most 8 products per output) the
-    // rotations take Karatsuba sums of the 30-bit halves: the digit and c0
-    // tiles go to the split layout in shared memory once (each thread
-    // converts the c0 entries it has just read), the keys once per rotation
-    // in registers.
-    constexpr bool KARA = ND <= 7;
-    if constexpr (KARA) {
-        if (r < L) {
-#pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                u64& cv = Cs[(hg * CPT + i) * T + xi];
-                cv = split30(cv);
-            }
-        }
-        for (u32 e = threadIdx.x; e < HC * ND * T; e += nthreads) Ds[e] = split30(Ds[e]);
-        __syncthreads();
-    }
-    const u32 p0 = (u32)PR & 0x3fffffffu, p1 = (u32)(PR >> 30), ps = p0 + p1;
+    // The rotations take Karatsuba sums of the 30-bit halves (at most 8
+    // digit-key products per output): the digit tile goes to the split layout
+    // in shared memory once, the keys once per rotation in registers.
+    for (u32 e = threadIdx.x; e < HC * ND * T; e += nthreads) Ds[e] = split30(Ds[e]);
+    __syncthreads();
     for (u32 a = 1; a < B; ++a) {
         if (a + 1 < B) load_keys(a + 1, kn, xn);
         const u32 y = auto_index(xc, bp.k[a], logN) - y0;  // in [0, T)
-        if constexpr (KARA) {
-            u32 k0[ND][2], k1[ND][2], ks[ND][2];
+        u32 k0[ND][2], k1[ND][2], ks[ND][2];
 #pragma unroll
-            for (int b = 0; b < ND; ++b)
+        for (int b = 0; b < ND; ++b)
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    k0[b][j] = (u32)kc[b][j] & 0x3fffffffu;
-                    k1[b][j] = (u32)(kc[b][j] >> 30);
-                    ks[b][j] = k0[b][j] + k1[b][j];
-                }
-#pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                const u32 ct = hg * CPT + i, h = h0 + ct;
-                if (h >= H) continue;
-                Kara64 s0 = {0, 0, 0, 0, 0, 0}, s1 = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-                for (int b = 0; b < ND; ++b) {
-                    const u64 d = Ds[(ct * ND + b) * T + y];
-                    const u32 d0 = (u32)d, d1 = (u32)(d >> 32), ds = d0 + d1;
-                    kmac(s0, d0, d1, ds, k0[b][0], k1[b][0], ks[b][0]);
-                    kmac(s1, d0, d1, ds, k0[b][1], k1[b][1], ks[b][1]);
-                }
-                if (r < L) {                 // P sigma(c0) as c0 times P R
-                    const u64 cv = Cs[ct * T + y];
-                    const u32 c0 = (u32)cv, c1 = (u32)(cv >> 32);
-                    kmac(s0, c0, c1, c0 + c1, p0, p1, ps);
-                }
-                u64 hi, lo;
-                kara_value(s0, hi, lo);
-                const u64 v0 = redc128(hi, lo, md);
-                kara_value(s1, hi, lo);
-                const u64 v1 = redc128(hi, lo, md);
-                u64* o = Rx + (((u64)h * B + a) * 2) * EN + ((u64)r << logN) + xc;
-                o[0] = split30(v0);
-                o[EN] = split30(v1);
+            for (int j = 0; j < 2; ++j) {
+                k0[b][j] = (u32)kc[b][j] & 0x3fffffffu;
+                k1[b][j] = (u32)(kc[b][j] >> 30);
+                ks[b][j] = k0[b][j] + k1[b][j];
             }
-        } else {
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                const u32 ct = hg * CPT + i, h = h0 + ct;
-                if (h >= H) continue;
-                u64 h0a = 0, l0a = 0, h1a = 0, l1a = 0;
+        for (int i = 0; i < CPT; ++i) {
+            const u32 ct = hg * CPT + i, h = h0 + ct;
+            if (h >= H) continue;
+            Kara64 s0 = {0, 0, 0, 0, 0, 0}, s1 = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-                for (int b = 0; b < ND; ++b) {
-                    const u64 d = Ds[(ct * ND + b) * T + y];
-                    mac128(h0a, l0a, d, kc[b][0]);
-                    mac128(h1a, l1a, d, kc[b][1]);
-                }
-                // P sigma(c0) as c0 times P R (the digits carry R); one Montgomery
-                // reduction per output
-                if (r < L) mac128(h0a, l0a, Cs[ct * T + y], PR);
-                const u64 v0 = redc128(h0a, l0a, md);
-                const u64 v1 = redc128(h1a, l1a, md);
-                u64* o = Rx + (((u64)h * B + a) * 2) * EN + ((u64)r << logN) + xc;
-                o[0] = split30(v0);
-                o[EN] = split30(v1);
+            for (int b = 0; b < ND; ++b) {
+                const u64 d = Ds[(ct * ND + b) * T + y];
+                const u32 d0 = (u32)d, d1 = (u32)(d >> 32), ds = d0 + d1;
+                kmac(s0, d0, d1, ds, k0[b][0], k1[b][0], ks[b][0]);
+                kmac(s1, d0, d1, ds, k0[b][1], k1[b][1], ks[b][1]);
             }
+            u64 hi, lo;
+            kara_value(s0, hi, lo);
+            u64 v0 = redc128(hi, lo, md);
+            if (r < L) v0 = addmod(v0, Cs[ct * T + y], md.q);     // + P sigma(c0)
+            kara_value(s1, hi, lo);
+            const u64 v1 = redc128(hi, lo, md);
+            u64* o = Rx + (((u64)h * B + a) * 2) * EN + ((u64)r << logN) + xc;
+            o[0] = split30(v0);
+            o[EN] = split30(v1);
         }
 #pragma unroll
         for (int b = 0; b < ND; ++b) { kc[b][0] = kn[b][0]; kc[b][1] = kn[b][1]; }
@@ -1315,11 +1279,16 @@ int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t
     }
 #undef PDQ_MODUP
     PDQ_TRY(launched("k_modup"));
-    for (u32 b = 0; b < nd; ++b) {
-        const u32 lo = c.digit_limbs[b].front(), hi = c.digit_limbs[b].back() + 1;
-        u64* Db = D + (u64)b * E * N;
-        if (lo > 0) PDQ_TRY(ntt_forward(c, Db, cnt, lo, 0, nd * E * N, st));
-        PDQ_TRY(ntt_forward(c, Db + (u64)hi * N, cnt, (u32)(E - hi), hi, nd * E * N, st));
+    if (c.L % c.alpha == 0) {
+        // every digit alpha primes: one transform over all (ciphertext, digit)
+        PDQ_TRY(ntt_forward_digits(c, D, cnt, (u32)nd, c.alpha, (u32)E, st));
+    } else {
+        for (u32 b = 0; b < nd; ++b) {
+            const u32 lo = c.digit_limbs[b].front(), hi = c.digit_limbs[b].back() + 1;
+            u64* Db = D + (u64)b * E * N;
+            if (lo > 0) PDQ_TRY(ntt_forward(c, Db, cnt, lo, 0, nd * E * N, st));
+            PDQ_TRY(ntt_forward(c, Db + (u64)hi * N, cnt, (u32)(E - hi), hi, nd * E * N, st));
+        }
     }
     *D_out = D;
     return PDQ_OK;

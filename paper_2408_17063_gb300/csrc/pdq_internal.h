@@ -193,6 +193,11 @@ int ntt_forward(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 s
                 cudaStream_t st);
 int ntt_inverse(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
                 cudaStream_t st);
+// Forward transform of raised digits D[count][nd][nlimbs][N] except each
+// digit's own limbs (digit b owns limbs b alpha .. b alpha + alpha - 1; every
+// digit the same size)
+int ntt_forward_digits(const Ctx& c, u64* D, u32 count, u32 nd, u32 alpha, u32 nlimbs,
+                       cudaStream_t st);
 // Inverse transform of `count` groups of nlimbs limbs (moduli limb0 ..)
 // read from a strided set (group g at src + (g / src_per) src_outer +
 // (g % src_per) src_inner + src_off, limb l at + l N), written to
