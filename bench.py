@@ -144,51 +144,61 @@ class ClockSampler:
 
 def oracle_sample(cfg, budget_s: float = 20.0) -> dict:
     """Time the CPU oracle on a bounded sample of the workload and scale it to
-    one query with the schedule's operation counts: one full key switch, one
-    hoisted raise, one hoisted rotation, a plaintext-ciphertext product (Mask)
-    and multiply-accumulate products (diagonal MAC) at full size."""
+    one Answer with the oracle's own operation counts: a raise of c1, a
+    rotation with its ModDown, an extended-basis rotation, a ModDown of one
+    polynomial, a plaintext-ciphertext product and diagonal products over
+    Q u P, each at full size."""
     import numpy as np
     import workloads as W
     from oracle import bfv, pdq as opdq
 
     par = bfv.Params.from_config(cfg)
     plan = opdq.make_plan(par, cfg.n, cfg.s)
+    E = par.L + par.K
     sk = W.draw_ternary(par.N, W.rng_for(cfg.seed, 3))
     a, e = W.encryption_randomness(par.q, par.N, 1, cfg.seed)
     ct = bfv.encrypt(par, sk, bfv.encode(par, np.arange(par.N) % par.t), a[0], e[0])
+    ct_ext = bfv.ct_times_P(par, ct)
     k = par.galois_rot(1)
     kr = W.rotation_key_randomness(par.ext, par.N, len(par.digits), [k], cfg.seed)
     key = bfv.rotation_key(par, sk, k, *kr[k])
     pt = opdq.lifted_pt(par, np.arange(par.N) % par.t)
-    t0 = time.perf_counter()
-    raised = bfv.mod_up_all(par, ct[1])
-    t_raise = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    bfv.rotate_hoisted(par, ct, raised, k, key)
-    t_apply = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    bfv.pt_mul(par, ct, pt)
-    t_ptmul = time.perf_counter() - t0
-    nmac = 4
-    t0 = time.perf_counter()
-    opdq.ring_dot(par, [pt] * nmac, [ct] * nmac)
-    t_mac = (time.perf_counter() - t0) / nmac
-    n_full_ks = plan.H + plan.G * (plan.giants - 1) + plan.G * int(np.log2(par.m // plan.s_prime))
-    n_raise_hoisted = plan.H if plan.B > 1 else 0
-    n_apply_hoisted = plan.H * (plan.B - 1)
+    pt_ext = bfv.lift(par, bfv.encode(par, np.arange(par.N) % par.t), par.ext)
+
+    def timed(f):
+        t0 = time.perf_counter()
+        r = f()
+        return r, time.perf_counter() - t0
+
+    raised, t_raise = timed(lambda: bfv.mod_up_all(par, ct[1]))
+    _, t_apply = timed(lambda: bfv.rotate_hoisted(par, ct, raised, k, key))
+    _, t_ext = timed(lambda: bfv.rotate_ext_lazy(par, ct_ext, raised, k, key))
+    _, t_down = timed(lambda: bfv.mod_down(par, ct_ext[1]))
+    _, t_ptmul = timed(lambda: bfv.pt_mul(par, ct, pt))
+    nmac = 2
+    _, t = timed(lambda: opdq.ring_dot_ext(par, [pt_ext] * nmac, [ct_ext] * nmac))
+    t_mac = t / nmac
+    levels = opdq.rotsum_levels(par, plan)
+    rot_giant = plan.G * (plan.giants - 1)
+    n_full = plan.J                                            # Rot_col of each index ciphertext
+    n_raise = (plan.H if plan.B > 1 else 0) + rot_giant + plan.G * len(levels)
+    n_ext = plan.H * (plan.B - 1) + rot_giant + plan.G * sum(r - 1 for _, r in levels)
+    n_down = rot_giant + plan.G * len(levels) + 2 * plan.G
     n_mac = plan.H * plan.B * plan.giants
-    n_mask = 4 * plan.J
-    per_query = (n_full_ks * (t_raise + t_apply) + n_raise_hoisted * t_raise
-                 + n_apply_hoisted * t_apply + n_mac * t_mac + n_mask * t_ptmul)
-    sampled = t_raise + t_apply + t_ptmul + nmac * t_mac
+    n_ptmul = 4 * plan.J
+    per_query = (n_full * (t_raise + t_apply) + n_raise * t_raise + n_ext * t_ext
+                 + n_down * t_down + n_mac * t_mac + n_ptmul * t_ptmul)
+    sampled = t_raise + t_apply + t_ext + t_down + t_ptmul + nmac * t_mac
     return {"value": 1.0 / per_query, "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle timed on one full-size key-switch raise ({t_raise:.2f} s), one "
-                       f"rotation ({t_apply:.2f} s), one Mask product ({t_ptmul:.2f} s) and "
-                       f"{nmac} diagonal MAC products ({t_mac:.2f} s each), scaled by the "
-                       f"schedule's counts per query ({n_full_ks} full key switches, "
-                       f"{n_raise_hoisted} hoisted raises, {n_apply_hoisted} hoisted rotations, "
-                       f"{n_mac} MAC products, {n_mask} Mask products) = {per_query:.0f} s "
-                       f"per query; {sampled:.1f} s sampled, single thread"),
+            "sample": (f"oracle timed on one full-size raise ({t_raise:.2f} s), one rotation "
+                       f"with ModDown ({t_apply:.2f} s), one extended-basis rotation "
+                       f"({t_ext:.2f} s), one polynomial ModDown ({t_down:.2f} s), one Mask "
+                       f"product ({t_ptmul:.2f} s) and {nmac} diagonal products over Q u P "
+                       f"({t_mac:.2f} s each), scaled by the oracle's counts per Answer "
+                       f"({n_full} rotations with ModDown, {n_raise} raises, {n_ext} "
+                       f"extended-basis rotations, {n_down} polynomial ModDowns, {n_mac} "
+                       f"diagonal products, {n_ptmul} Mask products) = {per_query:.0f} s per "
+                       f"query; {sampled:.1f} s sampled, single thread"),
             "seconds_per_query": per_query}
 
 
