@@ -49,6 +49,9 @@ def parse():
                     help="second batched run with this many clients sharing key sets (0: skip)")
     ap.add_argument("--s", type=int, default=0, help="override the sparsity")
     ap.add_argument("--mix", type=int, default=64, help="queries of the batched/served mix (0: skip)")
+    ap.add_argument("--switch-L", type=int, default=2,
+                    help="also time the Answer with Comp on this many primes after modulus "
+                         "switching (0: skip)")
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="served arrival rates, queries/s")
     ap.add_argument("--served-requests", type=int, default=192)
@@ -516,6 +519,69 @@ def mac_roofline(ctx, plan, ms):
                            "measured ceiling: register-only Karatsuba loop"}
 
 
+def run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank: int) -> dict:
+    """The Answer with Comp on smaller parameters: the resident query (over
+    the configuration's L primes) is switched to the first L' primes
+    (pdq_mod_switch) and answered there with keys, database and diagonals
+    made for L' primes; one step = switch + Answer."""
+    import dataclasses
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2408_17063_gb300 import pdq
+
+    L2 = args.switch_L
+    lcfg = dataclasses.replace(cfg, L=L2, dnum=-(-L2 // cfg.K))
+    lo = pdq.Context.from_config(lcfg)
+    lplan = lo.plan(cfg.n, cfg.s, args.B)
+    galois = lo.plan_galois(lplan)
+    sk = lo.secret_prepare(torch.from_numpy(q.sk))
+    keys = lo._u64(len(galois) * lo.key_elems)
+    kv = keys.view(len(galois), -1)
+    kr = W.rotation_key_randomness(lo.moduli, lo.N, lo.ndigits, galois, cfg.seed + rank + 1)
+    for i, k in enumerate(galois):
+        a, e = kr[k]
+        lo.rotkey_gen(sk, k, torch.from_numpy(a.view(np.int64)).cuda(),
+                      torch.from_numpy(e).cuda(), out=kv[i])
+    db = lo.db_encode(torch.from_numpy(q.db.astype(np.int32)).cuda())
+    consts = lo.plan_constants(lplan)
+    sw = lo._u64(plan.J * lo.ct_elems)
+    sws = ctx._ws(pdq.load().pdq_mod_switch_workspace_bytes(ctx.h, plan.J))
+    ws = lo.answer_workspace(lplan)
+    out = lo._u64(lplan.n_out * lo.ct_elems)
+    torch.cuda.synchronize()
+
+    def step():
+        ctx.mod_switch(lo, v_cts, out=sw, ws=sws, stream=stream)
+        lo.answer(lplan, sw, db, keys, galois, consts, ws=ws, out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    slots = lo.decrypt(sk, out).cpu().numpy()
+    ok = lo.decomp(lplan, slots) == [(int(i), int(q.db[i])) for i in q.positions]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches0 = pdq.pdq_launch_count()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = pdq.pdq_launch_count() - launches0
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total = ev[0].elapsed_time(ev[-1])
+    return {"value": args.steps / (total / 1000.0), "unit": "queries/s",
+            "ms_per_query": total / args.steps, "p50_ms": statistics.median(per),
+            "comp_primes": L2, "special_primes": lcfg.K, "dnum": lcfg.dnum,
+            "query_primes": cfg.L, "answer_bytes": lplan.n_out * lo.ct_elems * 8,
+            "rotation_keys_mib": keys.numel() * 8 / 2**20,
+            "gpu_launches_per_step": int(launches) / args.steps,
+            "all_decompress_exactly": bool(ok),
+            "what": (f"the query over {cfg.L} primes switched to {L2} (pdq_mod_switch) and "
+                     f"answered there (Mask + Comp, keys and diagonals for {L2} primes, "
+                     f"{lcfg.K} special primes, dnum {lcfg.dnum}); one step = switch + Answer")}
+
+
 def run_gpu(args, cfg, rank: int, world: int):
     import numpy as np
     import torch
@@ -629,6 +695,8 @@ def run_gpu(args, cfg, rank: int, world: int):
             "stages_ms_per_query": {k: v[0] / max(1, args.steps) for k, v in stages.items()},
             "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps,
             "clocks": clk, "e2e": e2e, "roofline": roofline}
+    if args.switch_L and 0 < args.switch_L < cfg.L:
+        line["switched"] = run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank)
     if args.mix > 0:
         del v_cts, keys, db, consts, out
         torch.cuda.empty_cache()

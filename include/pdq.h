@@ -165,6 +165,23 @@ size_t pdq_rotate_workspace_bytes(const pdq_ctx* ctx, uint32_t count);
 int pdq_rotate(const pdq_ctx* ctx, const uint64_t* ct_in, uint32_t count, uint64_t galois,
                const uint64_t* key, uint64_t* ct_out, void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------ modulus switching
+ * Comp needs one multiplicative level, so it can run with smaller HE
+ * parameters than the query (Sec. 5.3 switches to a smaller parameter set
+ * after Match and Mask; here the modulus is switched in the same ring).
+ * Ciphertexts over Q = q_0..q_{L-1} of `from` ([count][2][L][N], NTT form)
+ * become ciphertexts over Q' = q_0..q_{L'-1} of `to` ([count][2][L'][N]): the
+ * ModDown formula with the dropped primes D = q_{L'}..q_{L-1} in the role of P,
+ *   c'_i = (c_i - sum_k [c_{d_k} (D/d_k)^-1]_{d_k} (D/d_k)) D^-1  mod q_i,
+ * so c0 + c1 s = Delta m + e becomes Delta' m + e'.  `to` must have the same
+ * N and t and fewer primes, its ciphertext primes the first L' of `from`
+ * (contexts with the same K and prime size have that), else PDQ_E_PARAM; at
+ * most 8 primes dropped.  cts is not modified; out may not overlap it.
+ * Workspace: pdq_mod_switch_workspace_bytes(from, count), else PDQ_E_NOMEM. */
+size_t pdq_mod_switch_workspace_bytes(const pdq_ctx* from, uint32_t count);
+int pdq_mod_switch(const pdq_ctx* from, const pdq_ctx* to, const uint64_t* cts, uint32_t count,
+                   uint64_t* out, void* ws, size_t ws_bytes, void* stream);
+
 /* ----------------------------------------------------------------- plans
  * Fill the layout for n records and sparsity s (s' = 2^ceil(log2 s), the
  * Pegasus baby-step/giant-step split k = gB + a of Sec. 5.2).  B = 0 picks

@@ -363,6 +363,27 @@ def mod_down(par: Params, y) -> np.ndarray:
     return out
 
 
+def mod_switch(par: Params, low: Params, ct) -> np.ndarray:
+    """Modulus switching to smaller parameters (the paper runs Comp with
+    smaller parameters than the query, Sec. 6): a ciphertext over
+    Q = q_0..q_{L-1} ([2][L][N], coefficient form) to Q' = q_0..q_{L'-1}, the
+    ciphertext primes of `low` (the first L' of par's), dividing by the
+    dropped primes D = q_{L'}..q_{L-1} with the ModDown formula (floor-like):
+      c'_i = (c_i - sum_k [c_{d_k} (D/d_k)^{-1}]_{d_k} (D/d_k)) D^{-1}  mod q_i.
+    c0 + c1 s = Delta m + e over Q becomes Delta' m + e' over Q'."""
+    if (low.N, low.t) != (par.N, par.t) or low.L >= par.L or low.q != par.q[:low.L]:
+        raise ValueError("mod_switch: the smaller parameters must keep a prefix of the primes")
+    dropped = par.q[low.L:]
+    D = math.prod(dropped)
+    out = np.empty((2, low.L, par.N), dtype=np.uint64)
+    for p_idx in range(2):
+        yd = np.stack([ct[p_idx][low.L + k] for k in range(len(dropped))])
+        for i, qi in enumerate(low.q):
+            conv = ring.basis_convert(yd, dropped, qi)
+            out[p_idx][i] = ring.vec_scale(ring.vec_sub(ct[p_idx][i], conv, qi), pow(D % qi, -1, qi), qi)
+    return out
+
+
 def mod_up_all(par: Params, c1) -> list[np.ndarray]:
     """The hoistable part of a key switch: one raised polynomial per digit."""
     return [mod_up(par, c1, d) for d in par.digits]

@@ -415,6 +415,14 @@ def answer(par: Params, v_cts, db, keys, plan: Plan) -> list[np.ndarray]:
     return comp_packed(par, mask_pack(par, v_cts, db, keys, plan), keys, plan)
 
 
+def answer_switched(par: Params, low: Params, v_cts, db, keys, plan: Plan) -> list[np.ndarray]:
+    """The Answer with Comp on smaller parameters (Sec. 6): the index
+    ciphertexts are switched from par's modulus to low's (mod_switch), then
+    Mask and Comp run over low's primes with low's keys (plan made for low)."""
+    from .bfv import mod_switch
+    return answer(low, [mod_switch(par, low, v) for v in v_cts], db, keys, plan)
+
+
 # ------------------------------------------------------- closed form ------
 
 def closed_form(par: Params, plan: Plan, v, db):

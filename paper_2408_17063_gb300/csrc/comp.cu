@@ -374,6 +374,26 @@ int pdq_rotate(const pdq_ctx* ctx, const uint64_t* ct_in, uint32_t count, uint64
                     (cudaStream_t)stream);
 }
 
+size_t pdq_mod_switch_workspace_bytes(const pdq_ctx* from, uint32_t count) {
+    return from ? mod_switch_ws(C(from), count) : 0;
+}
+
+int pdq_mod_switch(const pdq_ctx* from, const pdq_ctx* to, const uint64_t* cts, uint32_t count,
+                   uint64_t* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!from || !to) return fail(PDQ_E_PARAM, "mod_switch: null context");
+    const Ctx& a = C(from);
+    const Ctx& b = C(to);
+    if (a.N != b.N || a.t != b.t || b.L >= a.L)
+        return fail(PDQ_E_PARAM, "mod_switch: the target needs the same ring and fewer primes");
+    for (u32 i = 0; i < b.L; ++i)
+        if (a.mods[i] != b.mods[i])
+            return fail(PDQ_E_PARAM, "mod_switch: the target's primes must be a prefix of the source's");
+    if (count == 0) return PDQ_OK;
+    if (!cts || !out || !ws) return fail(PDQ_E_PARAM, "mod_switch: null buffer");
+    if (ws_bytes < mod_switch_ws(a, count)) return fail(PDQ_E_NOMEM, "mod_switch: workspace too small");
+    return mod_switch(a, b.L, cts, count, out, reinterpret_cast<u64*>(ws), (cudaStream_t)stream);
+}
+
 int pdq_plan_make(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B, pdq_plan* plan) {
     PDQ_CHECK_CTX(ctx);
     if (!plan) return fail(PDQ_E_PARAM, "null plan");

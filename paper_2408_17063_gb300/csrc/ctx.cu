@@ -160,7 +160,7 @@ static void free_ctx(Ctx* c) {
                     c->d_dn_hatinv_shoup, c->d_dn_hatmod, c->d_dn_hatmod_shoup,
                     c->d_dn_pinv, c->d_dn_pinv_shoup, c->d_P_mod_q, c->d_P_mod_q_shoup, c->d_delta_mod_q,
                     c->d_dec_omega, c->d_dec_omega_shoup, c->d_ckar,
-                    c->d_up_hatmod_mont, c->d_up_hatmod_mont_shoup, c->d_P_mont};
+                    c->d_up_hatmod_mont, c->d_up_hatmod_mont_shoup, c->d_P_mont, c->d_ms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
@@ -378,6 +378,42 @@ static int build_ctx(const pdq_params& p, Ctx* c) {
     for (u32 i = 0; i < L; ++i)
         pm[i] = mulmod_h(c->P_mod_q[i], (u64)(((u128)1 << 64) % c->mods[i]), c->mods[i]);
     PDQ_TRY(upload(&c->d_P_mont, pm));
+
+    // modulus switching tables, every target level L' < L
+    c->ms_off.assign(L + 1, 0);
+    std::vector<u64> ms;
+    for (u32 L2 = 1; L2 < L; ++L2) {
+        const u32 K2 = L - L2;
+        c->ms_off[L2] = ms.size();
+        std::vector<u64> hinv(K2), hinv_s(K2), hmod((size_t)K2 * L2), hmod_s((size_t)K2 * L2),
+            dinv(L2), dinv_s(L2);
+        for (u32 k = 0; k < K2; ++k) {
+            const u64 dk = c->mods[L2 + k];
+            u64 hat = 1;
+            for (u32 j = 0; j < K2; ++j)
+                if (j != k) hat = mulmod_h(hat, c->mods[L2 + j] % dk, dk);
+            hinv[k] = host_invmod(hat, dk);
+            hinv_s[k] = shoup_of(hinv[k], dk);
+            for (u32 i = 0; i < L2; ++i) {
+                const u64 qi = c->mods[i];
+                u64 h = 1;
+                for (u32 j = 0; j < K2; ++j)
+                    if (j != k) h = mulmod_h(h, c->mods[L2 + j] % qi, qi);
+                hmod[(size_t)k * L2 + i] = h;
+                hmod_s[(size_t)k * L2 + i] = shoup_of(h, qi);
+            }
+        }
+        for (u32 i = 0; i < L2; ++i) {
+            const u64 qi = c->mods[i];
+            u64 D = 1;
+            for (u32 j = 0; j < K2; ++j) D = mulmod_h(D, c->mods[L2 + j] % qi, qi);
+            dinv[i] = host_invmod(D, qi);
+            dinv_s[i] = shoup_of(dinv[i], qi);
+        }
+        for (const auto* v : {&hinv, &hinv_s, &hmod, &hmod_s, &dinv, &dinv_s})
+            ms.insert(ms.end(), v->begin(), v->end());
+    }
+    if (!ms.empty()) PDQ_TRY(upload(&c->d_ms, ms));
 
     // Delta = floor(Q/t): Q = t*Delta + (Q mod t) and Q = 0 mod q_i, so
     // Delta = -(Q mod t) * t^{-1} mod q_i.

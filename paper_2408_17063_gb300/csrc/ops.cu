@@ -1419,6 +1419,43 @@ int times_P(const Ctx& c, CtSet in, u32 cnt, CtSet out, bool split, cudaStream_t
 
 size_t mod_down_ws(const Ctx& c, u32 cnt) { return (size_t)cnt * 2 * c.L * c.N * sizeof(u64); }
 
+size_t mod_switch_ws(const Ctx& c, u32 cnt) { return (size_t)2 * cnt * c.L * c.N * sizeof(u64); }
+
+int mod_switch(const Ctx& c, u32 L2, const u64* cts, u32 cnt, u64* out, u64* ws, cudaStream_t st) {
+    const u64 N = c.N, L = c.L;
+    if (L2 == 0 || L2 >= c.L) return fail(PDQ_E_PARAM, "mod_switch: target level out of range");
+    const u32 K2 = c.L - L2;
+    if (K2 > 8) return fail(PDQ_E_PARAM, "mod_switch: at most 8 dropped primes");
+    PDQ_TRY(check_y(2ull * cnt, "mod_switch"));
+    const u64* T = c.d_ms + c.ms_off[L2];
+    const u64* hinv = T;
+    const u64* hinv_s = hinv + K2;
+    const u64* hmod = hinv_s + K2;
+    const u64* hmod_s = hmod + (u64)K2 * L2;
+    const u64* dinv = hmod_s + (u64)K2 * L2;
+    const u64* dinv_s = dinv + L2;
+    u64* S = ws;                                   // dropped limbs, coefficient form [2cnt][K2][N]
+    u64* Cv = ws + 2ull * cnt * K2 * N;            // [2cnt][L2][N]
+    PDQ_TRY(ntt_inverse_from(c, cts, (long long)(L * N), 1, 0, (u64)L2 * N, S, 2 * cnt, K2,
+                             (u64)K2 * N, st, L2));
+    const dim3 grid((c.N / 2 + kBlock - 1) / kBlock, 2 * cnt);
+#define PDQ_MSCONV(KK)                                                                            \
+    k_moddown_conv<KK><<<grid, kBlock, 0, st>>>(S, (u64)K2 * N, c.log_n, L2, K2, c.d_mods, hinv,   \
+                                                hinv_s, hmod, hmod_s, Cv)
+    switch (K2) {
+        case 1: PDQ_MSCONV(1); break;
+        case 2: PDQ_MSCONV(2); break;
+        case 3: PDQ_MSCONV(3); break;
+        default: PDQ_MSCONV(0); break;
+    }
+#undef PDQ_MSCONV
+    PDQ_TRY(launched("k_moddown_conv"));
+    PDQ_TRY(ntt_forward(c, Cv, 2 * cnt, L2, 0, (u64)L2 * N, st));
+    k_moddown_final_poly<<<grid2((u64)L2 * N / 2, 2 * cnt), kBlock, 0, st>>>(
+        cts, L * N, Cv, out, (u64)L2 * N, c.log_n, L2, c.d_mods, dinv, dinv_s);
+    return launched("k_moddown_final_poly");
+}
+
 size_t mod_down_polys_ws(const Ctx& c, u32 npolys) {
     return (size_t)npolys * (c.L + c.K) * c.N * sizeof(u64);
 }

@@ -154,6 +154,12 @@ struct Ctx {
     u64* d_dec_omega = nullptr;
     u64* d_dec_omega_shoup = nullptr;
     std::vector<std::vector<u32>> digit_limbs;   // limbs of each digit
+    // modulus switching to the first L' ciphertext primes (L' = 1..L-1),
+    // dividing by D = q_{L'} .. q_{L-1} (K' = L - L' primes): one block per
+    // L' at d_ms + ms_off[L']: (D/d_k)^-1 mod d_k [K'] and Shoup [K'],
+    // (D/d_k) mod q_i [K'][L'] and Shoup [K'][L'], D^-1 mod q_i [L'] and Shoup [L']
+    u64* d_ms = nullptr;
+    std::vector<u64> ms_off;
     // stage profiling: events recorded on the caller's stream when enabled
     struct Prof {
         bool on = false;

@@ -104,6 +104,11 @@ size_t mod_down_ws(const Ctx& c, u32 cnt);
 int mod_down_batch(const Ctx& c, u64* A, u32 cnt, CtSet out, u64* ws, cudaStream_t st);
 // ModDown of npolys polynomials over Q u P (polynomial i at A + i a_stride,
 // [L+K][N], left unchanged) into out + i out_stride ([L][N])
+// Modulus switching of cnt ciphertexts [cnt][2][L][N] (NTT form) to the
+// first L2 primes, out [cnt][2][L2][N]: the ModDown formula with the dropped
+// primes q_{L2} .. q_{L-1} in the role of P (input unchanged)
+size_t mod_switch_ws(const Ctx& c, u32 cnt);
+int mod_switch(const Ctx& c, u32 L2, const u64* cts, u32 cnt, u64* out, u64* ws, cudaStream_t st);
 size_t mod_down_polys_ws(const Ctx& c, u32 npolys);
 int mod_down_polys(const Ctx& c, const u64* A, u64 a_stride, u32 npolys, u64* out,
                    u64 out_stride, u64* ws, cudaStream_t st);

@@ -86,6 +86,8 @@ _SIGS = {
     "pdq_rotkey_gen": (_I, [_P, _P, _U64, _P, _P, _P, _P]),
     "pdq_decrypt_workspace_bytes": (_SZ, [_P, _U32]),
     "pdq_decrypt": (_I, [_P, _P, _P, _U32, _P, _P, _SZ, _P]),
+    "pdq_mod_switch_workspace_bytes": (_SZ, [_P, _U32]),
+    "pdq_mod_switch": (_I, [_P, _P, _P, _U32, _P, _P, _SZ, _P]),
     "pdq_rotate_workspace_bytes": (_SZ, [_P, _U32]),
     "pdq_rotate": (_I, [_P, _P, _U32, _U64, _P, _P, _P, _SZ, _P]),
     "pdq_plan_make": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
@@ -320,6 +322,16 @@ class Context:
         _check(lib.pdq_rotate(self.h, _ptr(ct), count, galois, _ptr(key), _ptr(out), _ptr(ws),
                               ws.numel(), _stream(stream)))
         return out
+
+    def mod_switch(self, to: "Context", cts, out=None, ws=None, stream=None) -> torch.Tensor:
+        """pdq_mod_switch: ciphertexts of this context to the first to.L primes."""
+        count = cts.numel() // self.ct_elems
+        lib = load()
+        ws = self._ws(lib.pdq_mod_switch_workspace_bytes(self.h, count)) if ws is None else ws
+        out = to._u64(count * to.ct_elems) if out is None else out
+        _check(lib.pdq_mod_switch(self.h, to.h, _ptr(cts), count, _ptr(out), _ptr(ws), ws.numel(),
+                                  _stream(stream)))
+        return out.view(count, 2, to.L, to.N)
 
     def rotate_noalloc(self, ct, galois: int, key, out=None, stream=None) -> torch.Tensor:
         """pdq_rotate without a workspace: the library's fixed device scratch

@@ -42,13 +42,15 @@ class Setup:
     """Oracle and GPU state for one configuration with identical randomness."""
 
     def __init__(self, cfg_name: str, seed: int | None = None, s: int | None = None,
-                 n: int | None = None, B: int = 0, pattern: str | None = None, ctx=None):
+                 n: int | None = None, B: int = 0, pattern: str | None = None, ctx=None,
+                 L: int | None = None, dnum: int | None = None):
         pdq = library()
         cfg = W.CONFIGS[cfg_name]
-        if s is not None or n is not None or pattern is not None:
+        if any(x is not None for x in (s, n, pattern, L, dnum)):
             import dataclasses
             cfg = dataclasses.replace(cfg, s=s or cfg.s, n=n or cfg.n,
-                                      pattern=pattern or cfg.pattern)
+                                      pattern=pattern or cfg.pattern, L=L or cfg.L,
+                                      dnum=dnum or cfg.dnum)
         self.cfg = cfg
         self.par = bfv.Params.from_config(cfg)
         self.ctx = pdq.Context.from_config(cfg) if ctx is None else ctx

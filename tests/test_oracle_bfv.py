@@ -256,3 +256,31 @@ def test_lazy_extended_rotation(cfg):
         r2 = bfv.mod_up_all(par, bfv.mod_down(par, x[1]))
         y = bfv.ct_mod_down(par, bfv.rotate_ext_lazy(par, x, r2, k2, keys[k2]))
         assert np.array_equal(bfv.decrypt(par, sk, y).reshape(2, par.m), want)
+
+
+@pytest.mark.parametrize("cfg,L2", [("tiny2", 1), ("tiny2", 2), ("small", 1)])
+def test_mod_switch(cfg, L2):
+    """Modulus switching keeps the slots, and every coefficient is
+    floor(X / D) - u mod Q' for the coefficient X over Q, D the product of
+    the dropped primes and 0 <= u < (number of dropped primes) (the
+    base conversion without overflow correction), checked with Python
+    integers."""
+    import dataclasses
+    c = W.CONFIGS[cfg]
+    par = bfv.Params.from_config(c)
+    low = bfv.Params.from_config(dataclasses.replace(c, L=L2, dnum=1))
+    assert low.q == par.q[:L2]
+    sk = _key_material(par, 41)
+    a, e = W.encryption_randomness(par.q, par.N, 1, seed=41)
+    slots = W.rng_for(42).integers(0, par.t, size=par.N, dtype=np.uint64)
+    ct = bfv.encrypt(par, sk, bfv.encode(par, slots), a[0], e[0])
+    sw = bfv.mod_switch(par, low, ct)
+    assert np.array_equal(bfv.decrypt(low, sk, sw), slots)
+    D = math.prod(par.q[L2:])
+    Qp = math.prod(low.q)
+    nd = par.L - L2
+    for p in range(2):
+        X = bfv.crt_compose(par, ct[p])
+        Y = bfv.crt_compose(low, sw[p])
+        for x, y in zip(X, Y):
+            assert any((x // D - u - y) % Qp == 0 for u in range(nd))

@@ -235,6 +235,26 @@ def test_answer_decrypts_to_closed_form_and_decompresses(cfg_name):
     assert got == [(int(i), int(qi.db[i])) for i in qi.positions]
 
 
+@pytest.mark.parametrize("cfg_name", ["tiny2", "small"])
+def test_answer_after_mod_switch(cfg_name):
+    """Comp on smaller parameters: the query switched from 3 primes to 2,
+    keys and plan for the 2-prime parameters (digits no wider than P:
+    dnum = ceil(2 / K)); the answer decrypts to C v, C d and decompresses."""
+    import dataclasses
+    cfg, par, qi, plan, keys, v_cts = build(cfg_name)
+    lcfg = dataclasses.replace(cfg, L=2, dnum=-(-2 // cfg.K))
+    low = bfv.Params.from_config(lcfg)
+    lplan = pdq.make_plan(low, cfg.n, cfg.s)
+    ks = pdq.galois_elements(low, lplan)
+    kr = W.rotation_key_randomness(low.ext, low.N, len(low.digits), ks, cfg.seed + 1)
+    lkeys = {k: bfv.rotation_key(low, qi.sk, k, *kr[k]) for k in ks}
+    outs = pdq.answer_switched(par, low, v_cts, qi.db, lkeys, lplan)
+    for ct, want in zip(outs, pdq.expected_slots(low, lplan, qi.v, qi.db)):
+        assert np.array_equal(bfv.decrypt(low, qi.sk, ct), want)
+        assert bfv.noise_budget_bits(low, qi.sk, ct) > 10
+    assert pdq.decomp(low, qi.sk, lplan, outs) == [(int(i), int(qi.db[i])) for i in qi.positions]
+
+
 def test_newton_against_elementary_symmetric_bruteforce():
     t = 65537
     rnd = random.Random(4)
