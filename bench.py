@@ -549,17 +549,26 @@ def run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank: int) -> dict:
     sws = ctx._ws(pdq.load().pdq_mod_switch_workspace_bytes(ctx.h, plan.J))
     ws = lo.answer_workspace(lplan)
     out = lo._u64(lplan.n_out * lo.ct_elems)
+    # the answer switched once more, to one prime, before it leaves the server
+    one = pdq.Context.from_config(dataclasses.replace(cfg, L=1, dnum=1)) if L2 > 1 else None
+    out1 = one._u64(lplan.n_out * one.ct_elems) if one else None
+    ws1 = lo._ws(pdq.load().pdq_mod_switch_workspace_bytes(lo.h, lplan.n_out)) if one else None
     torch.cuda.synchronize()
 
     def step():
         ctx.mod_switch(lo, v_cts, out=sw, ws=sws, stream=stream)
         lo.answer(lplan, sw, db, keys, galois, consts, ws=ws, out=out, stream=stream)
+        if one:
+            lo.mod_switch(one, out, out=out1, ws=ws1, stream=stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    slots = lo.decrypt(sk, out).cpu().numpy()
-    ok = lo.decomp(lplan, slots) == [(int(i), int(q.db[i])) for i in q.positions]
+    truth = [(int(i), int(q.db[i])) for i in q.positions]
+    ok = lo.decomp(lplan, lo.decrypt(sk, out).cpu().numpy()) == truth
+    if one:
+        sk1 = one.secret_prepare(torch.from_numpy(q.sk))
+        ok = ok and lo.decomp(lplan, one.decrypt(sk1, out1).cpu().numpy()) == truth
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     launches0 = pdq.pdq_launch_count()
     ev[0].record(stream)
@@ -573,13 +582,16 @@ def run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank: int) -> dict:
     return {"value": args.steps / (total / 1000.0), "unit": "queries/s",
             "ms_per_query": total / args.steps, "p50_ms": statistics.median(per),
             "comp_primes": L2, "special_primes": lcfg.K, "dnum": lcfg.dnum,
-            "query_primes": cfg.L, "answer_bytes": lplan.n_out * lo.ct_elems * 8,
+            "query_primes": cfg.L,
+            "answer_bytes": lplan.n_out * (one or lo).ct_elems * 8,
+            "answer_primes": 1 if one else L2,
             "rotation_keys_mib": keys.numel() * 8 / 2**20,
             "gpu_launches_per_step": int(launches) / args.steps,
             "all_decompress_exactly": bool(ok),
             "what": (f"the query over {cfg.L} primes switched to {L2} (pdq_mod_switch) and "
                      f"answered there (Mask + Comp, keys and diagonals for {L2} primes, "
-                     f"{lcfg.K} special primes, dnum {lcfg.dnum}); one step = switch + Answer")}
+                     f"{lcfg.K} special primes, dnum {lcfg.dnum}), the answer switched to "
+                     f"{1 if one else L2} prime(s); one step = the switches + Answer")}
 
 
 def run_gpu(args, cfg, rank: int, world: int):

@@ -44,6 +44,13 @@ def test_switched_answer_bit_exact(cfg_name):
     slots = lo.ctx.decrypt(lo.sk, out).cpu().numpy()
     truth = [(int(i), int(hi.q.db[i])) for i in hi.q.positions]
     assert lo.ctx.decomp(lo.plan, slots) == truth
+    # the answer switched to one prime before it leaves the server
+    one = _low(cfg_name, hi, 1)
+    out1 = lo.ctx.mod_switch(one.ctx, out)
+    got1 = coeff(one.ctx, out1, 1)
+    for c, w in enumerate(want):
+        assert np.array_equal(got1[c], bfv.mod_switch(lo.par, one.par, w)), c
+    assert one.ctx.decomp(one.plan, one.ctx.decrypt(one.sk, out1).cpu().numpy()) == truth
 
 
 def test_mod_switch_refuses_unrelated_contexts():
@@ -70,3 +77,6 @@ def test_c3_switched_answer():
         assert np.array_equal(slots[c].astype(np.uint64), exp[c]), c
     truth = [(int(i), int(lo.q.db[i])) for i in lo.q.positions]
     assert lo.ctx.decomp(lo.plan, slots) == truth
+    one = Setup("c3", L=1, dnum=1)
+    out1 = lo.ctx.mod_switch(one.ctx, out)
+    assert one.ctx.decomp(one.plan, one.ctx.decrypt(one.sk, out1).cpu().numpy()) == truth

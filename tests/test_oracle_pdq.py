@@ -253,6 +253,12 @@ def test_answer_after_mod_switch(cfg_name):
         assert np.array_equal(bfv.decrypt(low, qi.sk, ct), want)
         assert bfv.noise_budget_bits(low, qi.sk, ct) > 10
     assert pdq.decomp(low, qi.sk, lplan, outs) == [(int(i), int(qi.db[i])) for i in qi.positions]
+    # the answer switched to one prime before it leaves the server
+    one = bfv.Params.from_config(dataclasses.replace(cfg, L=1, dnum=1))
+    outs1 = [bfv.mod_switch(low, one, ct) for ct in outs]
+    for ct, want in zip(outs1, pdq.expected_slots(one, lplan, qi.v, qi.db)):
+        assert np.array_equal(bfv.decrypt(one, qi.sk, ct), want)
+    assert pdq.decomp(one, qi.sk, lplan, outs1) == [(int(i), int(qi.db[i])) for i in qi.positions]
 
 
 def test_newton_against_elementary_symmetric_bruteforce():
