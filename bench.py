@@ -49,6 +49,8 @@ def parse():
                     help="second batched run with this many clients sharing key sets (0: skip)")
     ap.add_argument("--s", type=int, default=0, help="override the sparsity")
     ap.add_argument("--mix", type=int, default=64, help="queries of the batched/served mix (0: skip)")
+    ap.add_argument("--paper-shapes", type=int, default=1,
+                    help="also time the paper's Table II/III shapes (N=2^13, 2x54-bit primes; 0: skip)")
     ap.add_argument("--switch-L", type=int, default=2,
                     help="also time the Answer with Comp on this many primes after modulus "
                          "switching (0: skip)")
@@ -594,6 +596,81 @@ def run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank: int) -> dict:
                      f"{1 if one else L2} prime(s); one step = the switches + Answer")}
 
 
+# The paper's Table II (n = 16384, s = 8..128) and Table III (s = 16,
+# n = 2^13..2^17) shapes: ring 2^13, t = 65537, two 54-bit ciphertext primes;
+# its Comp times (single-thread Xeon Silver 4114, seconds) for context.
+PAPER_SHAPES = [(16384, 8, 1.17), (16384, 16, 2.06), (16384, 32, 3.80), (16384, 64, 7.06),
+                (16384, 128, 13.40), (1 << 13, 16, 1.09), (1 << 14, 16, 2.06), (1 << 15, 16, 4.01),
+                (1 << 16, 16, 7.92), (1 << 17, 16, 15.75)]
+
+
+def run_paper_shapes(args, rank: int) -> list:
+    """Comp alone (pdq_comp on the masked ciphertexts), the whole Answer and
+    the client's Decomp for each shape, on the paper's ring and modulus (one
+    54-bit special prime, one prime per key-switching digit: our choice)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2408_17063_gb300 import pdq
+
+    base = W.CONFIGS["paper"]
+    ctx = pdq.Context.from_config(base)
+    stream = torch.cuda.current_stream()
+    out = []
+    for n, s_, paper_s in PAPER_SHAPES:
+        import dataclasses
+        cfg = dataclasses.replace(base, n=n, s=s_)
+        q = W.draw_query(cfg, cfg.seed + rank)
+        plan = ctx.plan(n, s_, 0)
+        galois = ctx.plan_galois(plan)
+        sk = ctx.secret_prepare(torch.from_numpy(q.sk))
+        keys = ctx._u64(len(galois) * ctx.key_elems)
+        kv = keys.view(len(galois), -1)
+        kr = W.rotation_key_randomness(ctx.moduli, ctx.N, ctx.ndigits, galois, cfg.seed + rank)
+        for i, k in enumerate(galois):
+            a, e = kr[k]
+            ctx.rotkey_gen(sk, k, torch.from_numpy(a.view(np.int64)).cuda(),
+                           torch.from_numpy(e).cuda(), out=kv[i])
+        db = ctx.db_encode(torch.from_numpy(q.db.astype(np.int32)).cuda())
+        consts = ctx.plan_constants(plan)
+        a, e = W.encryption_randomness(ctx.moduli[:ctx.L], ctx.N, plan.J, cfg.seed + rank)
+        v = np.zeros(plan.J * ctx.N, dtype=np.int32)
+        v[:n] = q.v
+        v_cts = ctx.encrypt(sk, torch.from_numpy(v).cuda(), torch.from_numpy(a.view(np.int64)).cuda(),
+                            torch.from_numpy(e).cuda())
+        masked = ctx.mask(plan, v_cts, db)
+        cws = ctx.comp_workspace(plan)
+        aws = ctx.answer_workspace(plan)
+        res = ctx._u64(plan.n_out * ctx.ct_elems)
+
+        def timed(f, steps=5):
+            for _ in range(2):
+                f()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for _ in range(steps):
+                f()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / steps
+
+        comp_ms = timed(lambda: ctx.comp(plan, masked, keys, galois, consts, ws=cws, out=res,
+                                         stream=stream))
+        ans_ms = timed(lambda: ctx.answer(plan, v_cts, db, keys, galois, consts, ws=aws, out=res,
+                                          stream=stream))
+        slots = ctx.decrypt(sk, res).cpu().numpy()
+        t0 = time.perf_counter()
+        got = ctx.decomp(plan, slots)
+        dec_ms = (time.perf_counter() - t0) * 1e3
+        out.append({"n": n, "s": s_, "B": plan.B, "giants": plan.giants, "groups": plan.G,
+                    "comp_ms": comp_ms, "answer_ms": ans_ms, "decomp_host_ms": dec_ms,
+                    "decompress_exactly": got == [(int(i), int(q.db[i])) for i in q.positions],
+                    "paper_comp_s": paper_s})
+        del keys, db, consts, v_cts, masked, cws, aws, res
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args, cfg, rank: int, world: int):
     import numpy as np
     import torch
@@ -707,6 +784,13 @@ def run_gpu(args, cfg, rank: int, world: int):
             "stages_ms_per_query": {k: v[0] / max(1, args.steps) for k, v in stages.items()},
             "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps,
             "clocks": clk, "e2e": e2e, "roofline": roofline}
+    if args.paper_shapes:
+        line["paper_shapes"] = {
+            "what": ("the paper's Table II/III shapes (ring 2^13, t=65537, 2x54-bit primes + one "
+                     "54-bit special prime, dnum 2): GPU Comp alone, Answer (Mask + Comp) and "
+                     "host Decomp per query; paper_comp_s is the paper's single-thread Xeon time "
+                     "(context, other hardware and scheme)"),
+            "rows": run_paper_shapes(args, rank)}
     if args.switch_L and 0 < args.switch_L < cfg.L:
         line["switched"] = run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank)
     if args.mix > 0:

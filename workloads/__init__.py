@@ -61,6 +61,9 @@ CONFIGS = {
     "small": Config("small", 10, 12289, 60, 3, 1, 3, 5000, 20, "uniform", 0x73),
     # several record groups (n > t-1) and two output ciphertexts
     "grouped": Config("grouped", 6, 257, 60, 2, 1, 2, 2000, 5, "uniform", 0x74),
+    # the ring and modulus of the paper's experiments (2^13, t = 65537, two
+    # 54-bit primes; one special prime of the same size), Table III's n = 2^13
+    "paper": Config("paper", 13, 65537, 54, 2, 1, 2, 1 << 13, 16, "uniform", 0x2408),
 }
 
 
