@@ -572,17 +572,24 @@ def run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank: int) -> dict:
         sk1 = one.secret_prepare(torch.from_numpy(q.sk))
         ok = ok and lo.decomp(lplan, one.decrypt(sk1, out1).cpu().numpy()) == truth
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    lo.profile_enable(True)
     launches0 = pdq.pdq_launch_count()
+    torch.cuda.nvtx.range_push("switched")
     ev[0].record(stream)
     for i in range(args.steps):
         step()
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = pdq.pdq_launch_count() - launches0
+    stages = {k: v[0] / args.steps for k, v in lo.profile_read().items()}
+    lo.profile_enable(False)
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total = ev[0].elapsed_time(ev[-1])
+    stages["switches"] = total / args.steps - sum(stages.values())
     return {"value": args.steps / (total / 1000.0), "unit": "queries/s",
             "ms_per_query": total / args.steps, "p50_ms": statistics.median(per),
+            "stages_ms_per_query": stages,
             "comp_primes": L2, "special_primes": lcfg.K, "dnum": lcfg.dnum,
             "query_primes": cfg.L,
             "answer_bytes": lplan.n_out * (one or lo).ct_elems * 8,
