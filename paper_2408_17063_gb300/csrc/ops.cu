@@ -1336,13 +1336,12 @@ int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* ke
     constexpr u32 T = 64, HC = 16, CPT = 4;
     const u32 E = c.L + c.K;
     const size_t smem = ((size_t)HC * ND * T + 2 * HC * T) * sizeof(u64);
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(k_baby_ext<T, HC, CPT, ND>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10) != cudaSuccess)
-            return cuda_check("k_baby_ext attribute");
-        configured = true;
-    }
+    // set once per process (thread-safe static initialisation; the server's
+    // workers launch concurrently)
+    static const cudaError_t configured = cudaFuncSetAttribute(
+        k_baby_ext<T, HC, CPT, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10);
+    if (configured != cudaSuccess)
+        return fail(PDQ_E_CUDA, std::string("k_baby_ext attribute: ") + cudaGetErrorString(configured));
     const dim3 grid(c.N / T, E, (H + HC - 1) / HC);
     k_baby_ext<T, HC, CPT, ND><<<grid, T * HC / CPT, smem, st>>>(
         D, u, keys, H, B, c.log_n, E, ext ? E : c.L, ext ? E : c.L, c.d_mods,
@@ -1556,13 +1555,10 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN) {
 template <int GT, int BC>
 int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R, const u64* Dg,
                u64* acc0, u64* acc, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(k_diag_mac<GT, BC, kMacPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kMacSmem) != cudaSuccess)
-            return cuda_check("k_diag_mac attribute");
-        configured = true;
-    }
+    static const cudaError_t configured = cudaFuncSetAttribute(
+        k_diag_mac<GT, BC, kMacPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMacSmem);
+    if (configured != cudaSuccess)
+        return fail(PDQ_E_CUDA, std::string("k_diag_mac attribute: ") + cudaGetErrorString(configured));
     MacArgs a;
     a.G = pl.G;
     a.hpg = pl.hpg;
