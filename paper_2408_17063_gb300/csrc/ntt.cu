@@ -233,7 +233,7 @@ struct Phase {
 };
 
 template <bool FWD, int S, bool COLS, bool SINGLE>
-__global__ void __launch_bounds__(kThreads, 4) ntt_phase_kernel(NttArgs a) {
+__global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
     __shared__ __align__(16) u64 sm[kTile];
     const u32 p = blockIdx.x;
     const u32 grp = p / a.nlimbs;
