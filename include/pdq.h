@@ -217,6 +217,19 @@ size_t pdq_db_bytes(const pdq_ctx* ctx, uint64_t n);
 int pdq_db_encode(const pdq_ctx* ctx, const uint32_t* values, uint64_t n, uint64_t* db_out,
                   void* stream);
 
+/* The u-packing remark's literal order (Sec. 5.2, remark (ii)): the masked
+ * database d = v.DB first, then the row masks, one plaintext product more on
+ * d than pdq_mask (the same slots, more noise).  pdq_db_encode_plain writes
+ * DB_j on both rows without masks, dev [J][L][N] (pdq_db_plain_bytes;
+ * values < t, else reduced mod t); pdq_mask_literal writes, for each index
+ * ciphertext j, (v_j.[1;0], v_j.[0;1], (v_j.DB_j).[1;0], (v_j.DB_j).[0;1]) in
+ * the layout of pdq_mask (dev [J][4][2][L][N]), a valid input of pdq_comp. */
+size_t pdq_db_plain_bytes(const pdq_ctx* ctx, uint64_t n);
+int pdq_db_encode_plain(const pdq_ctx* ctx, const uint32_t* values, uint64_t n, uint64_t* db_out,
+                        void* stream);
+int pdq_mask_literal(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
+                     const uint64_t* db_plain, uint64_t* masked_out, void* stream);
+
 /* ------------------------------------------------------------ hot path
  * Mask (Alg. 7 step 2, with the row split of the u-packing remark): for each
  * index ciphertext j, vT = v_j.[1;0], vB = v_j.[0;1], dT = v_j.(DB_j.[1;0]),

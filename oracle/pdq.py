@@ -179,6 +179,23 @@ def mask(par: Params, v_cts, db, plan: Plan) -> list[np.ndarray]:
     return out
 
 
+def mask_literal(par: Params, v_cts, db, plan: Plan) -> list[np.ndarray]:
+    """Mask as the u-packing remark writes it (Sec. 5.2, remark (ii)): the
+    masked database d = v . DB first, then the row masks on v and on d:
+    vT = v.[1;0], vB = v.[0;1], dT = d.[1;0], dB = d.[0;1] -- one plaintext
+    product more on d than mask(), the same slots."""
+    pt_top = lifted_pt(par, row_mask_slots(par, 0))
+    pt_bot = lifted_pt(par, row_mask_slots(par, 1))
+    out = []
+    for j in range(plan.J):
+        d = pt_mul(par, v_cts[j], lifted_pt(par, record_slots(par, db, j)))
+        out.append(pt_mul(par, v_cts[j], pt_top))
+        out.append(pt_mul(par, v_cts[j], pt_bot))
+        out.append(pt_mul(par, d, pt_top))
+        out.append(pt_mul(par, d, pt_bot))
+    return out
+
+
 # ------------------------------------------------------------------ Comp ----
 
 def pack(par: Params, masked, keys, plan: Plan) -> list[np.ndarray]:

@@ -450,6 +450,29 @@ int pdq_db_encode(const pdq_ctx* ctx, const uint32_t* values, uint64_t n, uint64
     return build_db(c, values, n, (u32)J, db_out, (cudaStream_t)stream);
 }
 
+size_t pdq_db_plain_bytes(const pdq_ctx* ctx, uint64_t n) {
+    if (!ctx) return 0;
+    const Ctx& c = C(ctx);
+    return (n + c.N - 1) / c.N * (u64)c.L * c.N * sizeof(u64);
+}
+
+int pdq_db_encode_plain(const pdq_ctx* ctx, const uint32_t* values, uint64_t n, uint64_t* db_out,
+                        void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    const Ctx& c = C(ctx);
+    if (n == 0) return fail(PDQ_E_PARAM, "db_encode_plain: empty database");
+    if (!values || !db_out) return fail(PDQ_E_PARAM, "db_encode_plain: null buffer");
+    return build_db_plain(c, values, n, (u32)((n + c.N - 1) / c.N), db_out, (cudaStream_t)stream);
+}
+
+int pdq_mask_literal(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
+                     const uint64_t* db_plain, uint64_t* masked_out, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    if (!valid_plan(C(ctx), plan)) return fail(PDQ_E_PARAM, "mask_literal: invalid plan");
+    if (!v_cts || !db_plain || !masked_out) return fail(PDQ_E_PARAM, "mask_literal: null buffer");
+    return mask_literal(C(ctx), plan->J, v_cts, db_plain, masked_out, (cudaStream_t)stream);
+}
+
 int pdq_mask(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts, const uint64_t* db,
              uint64_t* masked_out, void* stream) {
     PDQ_CHECK_CTX(ctx);

@@ -123,6 +123,17 @@ __global__ void k_db_slots(u64* __restrict__ out, const u32* __restrict__ values
     out[(((u64)pt * L) << logN) + pos[idx]] = v;
 }
 
+// database plaintexts without row masks: plaintext j holds DB_j on both rows
+__global__ void k_db_plain_slots(u64* __restrict__ out, const u32* __restrict__ values, u64 n,
+                                 u32 logN, u32 L, const u32* __restrict__ pos, u64 t) {
+    const u32 idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 N = 1u << logN;
+    if (idx >= N) return;
+    const u64 j = blockIdx.y;
+    const u64 rec = (j << logN) + idx;
+    out[((j * L) << logN) + pos[idx]] = rec < n ? (u64)values[rec] % t : 0;
+}
+
 // group mask o: ones at slots [o s', (o+1) s') of both rows
 __global__ void k_groupmask_slots(u64* __restrict__ out, u32 s_prime, u32 logN, u32 L,
                                   const u32* __restrict__ pos) {
@@ -264,6 +275,30 @@ __global__ void k_mask(const u64* __restrict__ v, const u64* __restrict__ db,
         o[(2 * k) * LN + r] = mulmod(v0, pt[k], md);
         o[(2 * k + 1) * LN + r] = mulmod(v1, pt[k], md);
     }
+}
+
+// Mask in the order of the u-packing remark: d = v.DB first, then the row
+// masks: out[j] = (v.[1;0], v.[0;1], d.[1;0], d.[0;1])
+__global__ void k_mask_literal(const u64* __restrict__ v, const u64* __restrict__ dbp,
+                               const u64* __restrict__ rowmask, u32 L, u32 logN,
+                               const Mod* __restrict__ mods, u64* __restrict__ out) {
+    const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 LN = (u64)L << logN;
+    if (r >= LN) return;
+    const u64 j = blockIdx.y;
+    const Mod md = mods[r >> logN];
+    const u64 v0 = v[j * 2 * LN + r], v1 = v[j * 2 * LN + LN + r];
+    const u64 pd = dbp[j * LN + r], top = rowmask[r], bot = rowmask[LN + r];
+    const u64 d0 = mulmod(v0, pd, md), d1 = mulmod(v1, pd, md);
+    u64* o = out + j * 8 * LN;
+    o[0 * LN + r] = mulmod(v0, top, md);
+    o[1 * LN + r] = mulmod(v1, top, md);
+    o[2 * LN + r] = mulmod(v0, bot, md);
+    o[3 * LN + r] = mulmod(v1, bot, md);
+    o[4 * LN + r] = mulmod(d0, top, md);
+    o[5 * LN + r] = mulmod(d1, top, md);
+    o[6 * LN + r] = mulmod(d0, bot, md);
+    o[7 * LN + r] = mulmod(d1, bot, md);
 }
 
 // Mask fused with the pack (w_j = Rot_col(v_j), NTT form):
@@ -1122,6 +1157,21 @@ int build_group_masks(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t s
                                                                  c.d_slot_pos);
     PDQ_TRY(launched("k_groupmask_slots"));
     return encode_finish(c, out, pl.per_out, c.L, st);
+}
+
+int build_db_plain(const Ctx& c, const u32* values, u64 n, u32 J, u64* out, cudaStream_t st) {
+    PDQ_TRY(check_y(J, "database"));
+    k_db_plain_slots<<<grid2(c.N, J), kBlock, 0, st>>>(out, values, n, c.log_n, c.L, c.d_slot_pos,
+                                                       c.t);
+    PDQ_TRY(launched("k_db_plain_slots"));
+    return encode_finish(c, out, J, c.L, st);
+}
+
+int mask_literal(const Ctx& c, u32 J, const u64* v, const u64* dbp, u64* out, cudaStream_t st) {
+    PDQ_TRY(check_y(J, "mask"));
+    k_mask_literal<<<grid2((u64)c.L * c.N, J), kBlock, 0, st>>>(v, dbp, c.d_rowmask, c.L, c.log_n,
+                                                                c.d_mods, out);
+    return launched("k_mask_literal");
 }
 
 int build_db(const Ctx& c, const u32* values, u64 n, u32 J, u64* out, cudaStream_t st) {

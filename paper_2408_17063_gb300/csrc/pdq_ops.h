@@ -51,6 +51,10 @@ size_t decrypt_ws(const Ctx& c, u32 count);
 int decrypt(const Ctx& c, const u64* sk, const u64* ct, u32 count, u32* slots, u64* ws,
             cudaStream_t st);
 int mask(const Ctx& c, u32 J, const u64* v, const u64* db, u64* out, cudaStream_t st);
+// the remark's order: DB_j plaintexts without row masks ([J][L][N]), then
+// out[j] = (v.[1;0], v.[0;1], (v.DB).[1;0], (v.DB).[0;1])
+int build_db_plain(const Ctx& c, const u32* values, u64 n, u32 J, u64* out, cudaStream_t st);
+int mask_literal(const Ctx& c, u32 J, const u64* v, const u64* dbp, u64* out, cudaStream_t st);
 // u[2j] = v_j.[1;0] + w_j.sigma_col(DB_j.[1;0]), u[2j+1] = w_j.[1;0] + v_j.(DB_j.[0;1])
 // with w_j = Rot_col(v_j): the packed u of Comp straight from the index
 // ciphertexts (u [2J][2][L][N])

@@ -97,6 +97,9 @@ _SIGS = {
     "pdq_db_bytes": (_SZ, [_P, _U64]),
     "pdq_db_encode": (_I, [_P, _P, _U64, _P, _P]),
     "pdq_mask": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _P]),
+    "pdq_db_plain_bytes": (_SZ, [_P, _U64]),
+    "pdq_db_encode_plain": (_I, [_P, _P, _U64, _P, _P]),
+    "pdq_mask_literal": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _P]),
     "pdq_comp_workspace_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
     "pdq_comp": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _U32, _P, _P, _P, _SZ, _P]),
     "pdq_answer_workspace_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
@@ -372,6 +375,22 @@ class Context:
         out = self._u64(lib.pdq_db_bytes(self.h, n) // 8)
         _check(lib.pdq_db_encode(self.h, _ptr(values), n, _ptr(out), _stream(stream)))
         return out
+
+    def db_encode_plain(self, values, stream=None) -> torch.Tensor:
+        """pdq_db_encode_plain: DB_j without row masks, [J][L][N]."""
+        values = values.to(device="cuda", dtype=torch.int32).contiguous()
+        n = values.numel()
+        lib = load()
+        out = self._u64(lib.pdq_db_plain_bytes(self.h, n) // 8)
+        _check(lib.pdq_db_encode_plain(self.h, _ptr(values), n, _ptr(out), _stream(stream)))
+        return out
+
+    def mask_literal(self, plan: Plan, v_cts, db_plain, stream=None) -> torch.Tensor:
+        """pdq_mask_literal: d = v.DB first, then the row masks."""
+        out = self._u64(plan.J * 4 * self.ct_elems)
+        _check(load().pdq_mask_literal(self.h, ctypes.byref(plan), _ptr(v_cts), _ptr(db_plain),
+                                       _ptr(out), _stream(stream)))
+        return out.view(plan.J * 4, 2, self.L, self.N)
 
     # hot path
     def mask(self, plan: Plan, v_cts, db, stream=None) -> torch.Tensor:

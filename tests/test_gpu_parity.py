@@ -116,6 +116,23 @@ def test_mask_bit_exact(setup):
         assert np.array_equal(got[i], w), i
 
 
+def test_literal_mask_and_comp_bit_exact(setup):
+    """The remark's literal order (d = v.DB, then the row masks) and Comp on
+    its output, against the oracle's mask_literal and comp."""
+    ctx, par = setup.ctx, setup.par
+    dbp = ctx.db_encode_plain(torch.from_numpy(setup.q.db.astype(np.int32)).cuda())
+    lit = ctx.mask_literal(setup.plan, setup.v_cts, dbp)
+    want = opdq.mask_literal(par, setup.o_v_cts, setup.q.db, setup.oplan)
+    got = coeff(ctx, lit, par.L)
+    for i, w in enumerate(want):
+        assert np.array_equal(got[i], w), i
+    out = ctx.comp(setup.plan, lit, setup.keys, setup.galois, setup.consts)
+    wc = opdq.comp(par, want, setup.o_keys, setup.oplan)
+    gc = coeff(ctx, out, par.L)
+    for c, w in enumerate(wc):
+        assert np.array_equal(gc[c], w), c
+
+
 def test_answer_bit_exact_and_decompresses(setup):
     ctx, par = setup.ctx, setup.par
     out = setup.answer()

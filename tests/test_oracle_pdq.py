@@ -222,6 +222,29 @@ def test_comp_of_mask_decrypts_to_closed_form(cfg_name):
         assert np.array_equal(bfv.decrypt(par, qi.sk, ct), want)
 
 
+@pytest.mark.parametrize("cfg_name", ["tiny2", "grouped", "c1"])
+def test_literal_mask_schedule(cfg_name):
+    """The remark's literal schedule (row masks after d = v . DB): its four
+    products decrypt to v.[1;0], v.[0;1], d.[1;0], d.[0;1], and Comp on them
+    decrypts to the closed form with noise budget to spare (the extra
+    plaintext product costs budget, pinned against the folded masks)."""
+    cfg, par, qi, plan, keys, v_cts = build(cfg_name)
+    lit = pdq.mask_literal(par, v_cts, qi.db, plan)
+    t = par.t
+    top, bot = pdq.row_mask_slots(par, 0), pdq.row_mask_slots(par, 1)
+    for j in range(plan.J):
+        v = pdq.record_slots(par, qi.v, j)
+        d = v * pdq.record_slots(par, qi.db, j) % t
+        for idx, want in enumerate([v * top, v * bot, d * top, d * bot]):
+            assert np.array_equal(bfv.decrypt(par, qi.sk, lit[4 * j + idx]), want)
+    outs = pdq.comp(par, lit, keys, plan)
+    folded = pdq.comp(par, pdq.mask(par, v_cts, qi.db, plan), keys, plan)
+    for ct, ref, want in zip(outs, folded, pdq.expected_slots(par, plan, qi.v, qi.db)):
+        assert np.array_equal(bfv.decrypt(par, qi.sk, ct), want)
+        assert bfv.noise_budget_bits(par, qi.sk, ct) > 5
+        assert bfv.noise_budget_bits(par, qi.sk, ct) <= bfv.noise_budget_bits(par, qi.sk, ref) + 1
+
+
 @pytest.mark.parametrize("cfg_name", ["tiny", "tiny2", "grouped", "small", "c1"])
 def test_answer_decrypts_to_closed_form_and_decompresses(cfg_name):
     cfg, par, qi, plan, keys, v_cts = build(cfg_name)
