@@ -1383,7 +1383,7 @@ namespace {
 template <int ND>
 int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
                 const BabyParams& bp, u64* Rx, cudaStream_t st, bool ext) {
-    constexpr u32 T = 64, HC = 16, CPT = 4;
+    constexpr u32 T = 64, HC = 16, CPT = 8;
     const u32 E = c.L + c.K;
     const size_t smem = ((size_t)HC * ND * T + 2 * HC * T) * sizeof(u64);
     // set once per process (thread-safe static initialisation; the server's
