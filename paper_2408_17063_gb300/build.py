@@ -6,6 +6,7 @@ Every translation unit under csrc/ is compiled in parallel and linked into
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -51,23 +52,33 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
+def _up_to_date() -> bool:
+    return os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime()
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Compile and link libpdq.so if it is missing or older than its sources."""
+    """Compile and link libpdq.so if it is missing or older than its sources.
+    Processes that build at the same time (ranks of one job) take turns on a
+    lock file; the ones that wait find the library up to date."""
     extra = list(extra or [])
     if verbose:
         extra += ["-Xptxas", "-v"]
-    if not force and not extra and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+    if not force and not extra and _up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
+    with open(os.path.join(OUT_DIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not extra and _up_to_date():
+            return LIB
+        os.makedirs(OBJ_DIR, exist_ok=True)
+        with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+            objs = list(ex.map(lambda s: _compile(s, extra), sources()))
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
+        os.replace(tmp, LIB)
     return LIB
 
 
