@@ -36,6 +36,24 @@ def test_prime_chain_matches_oracle(setup):
     assert setup.galois == opdq.galois_elements(par, op)
 
 
+def test_paper_table_shapes_plan_matches_oracle():
+    """The library's plan for every shape of Tables II and III (Sec. 6.2;
+    fixture paper_answer_size.txt) equals the oracle's, one output
+    ciphertext each, with the same rotations."""
+    from tests.test_oracle_pdq import golden_rows
+    cfg = W.CONFIGS["paper"]
+    par = bfv.Params.from_config(cfg)
+    ctx = library().Context.from_config(cfg)
+    for _, n, s, _ in golden_rows("paper_answer_size.txt"):
+        op = opdq.make_plan(par, int(n), int(s))
+        plan = ctx.plan(int(n), int(s))
+        got = plan.as_dict()
+        for f in ("s_prime", "B", "J", "H", "G_sz", "hpg", "G", "per_out", "n_out"):
+            assert got[f] == getattr(op, f), (n, s, f)
+        assert got["n_out"] == 1
+        assert ctx.plan_galois(plan) == opdq.galois_elements(par, op)
+
+
 # every transform decomposition: one CTA (N <= 2^12), column + row phases of
 # 5..8 column levels (2^13 .. 2^16)
 RINGS = {"tiny": W.CONFIGS["tiny"], "c1": W.CONFIGS["c1"], "c3": W.CONFIGS["c3"],

@@ -6,6 +6,7 @@ diagonal (Pegasus) algebra is pinned in the clear against an explicit matrix
 product, Newton's identity against brute-force elementary symmetric
 polynomials, and Decomp by exhaustive enumeration on tiny inputs."""
 import itertools
+import pathlib
 import random
 
 import numpy as np
@@ -93,13 +94,35 @@ def test_rotate_and_sum_is_the_sum_of_rotations():
     assert np.array_equal(got.astype(np.int64), want)
 
 
+def golden_rows(name):
+    """Rows of a fixture under tests/golden/ ('#' starts a comment)."""
+    rows = []
+    for line in (pathlib.Path(__file__).parent / "golden" / name).read_text().splitlines():
+        f = line.split("#", 1)[0].split()
+        if f:
+            rows.append(f)
+    return rows
+
+
 def test_paper_single_ciphertext_answer():
-    """Sec. 6 (footnote on communication): with N = 2^13 and t = 65537 the
-    answer is one ciphertext unless s exceeds N/2 = 4096 slots per row."""
-    par = bfv.Params(13, 65537, 54, 2, 1, 2)
-    for n in (1 << 13, 1 << 14, 1 << 15, 1 << 16):
-        for s in (8, 16, 32, 64, 128):
-            assert pdq.make_plan(par, n, s).n_out == 1
+    """Sec. 6.2, Tables II and III (Size column; fixture paper_answer_size.txt):
+    on the ring and modulus of Sec. 6.1 every answer is one ciphertext of
+    110.6 KB.  The plan has one output ciphertext for every row (both record
+    groups of the 2^17-record row share it), and that ciphertext switched to
+    the first ciphertext prime is 2 polynomials of N coefficients of 54 bits.
+    Footnote of Sec. 6.2: one ciphertext unless s exceeds N/2 = 4096."""
+    par = bfv.Params.from_config(W.CONFIGS["paper"])
+    assert (par.N, par.t, par.L, [q.bit_length() for q in par.q]) == (8192, 65537, 2, [54, 54])
+    low = bfv.Params(par.log_n, par.t, par.bits, 1, par.K, 1)
+    assert low.q == par.q[:1]
+    rows = golden_rows("paper_answer_size.txt")
+    assert len(rows) == 10
+    for table, n, s, kb in rows:
+        plan = pdq.make_plan(par, int(n), int(s))
+        assert plan.n_out == 1, (table, n, s)
+        assert plan.G == (2 if int(n) > 65536 else 1)
+        size = plan.n_out * 2 * low.L * par.N * low.q[0].bit_length() // 8
+        assert size == 110592 and round(size / 1000, 1) == float(kb), (table, n, s)
     assert pdq.make_plan(par, 1 << 14, 4096).n_out == 1
     with pytest.raises(ValueError):
         pdq.make_plan(par, 1 << 14, 4097)
