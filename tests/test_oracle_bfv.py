@@ -121,6 +121,26 @@ def test_decrypt_against_bigint_definition(tiny):
     assert m == bfv.decrypt_coeffs(par, sk, ct).tolist()
 
 
+def test_encryption_scale_is_floor_Q_over_t(tiny, tiny2):
+    """BFV scales the message by Delta = floor(Q/t): a noise-free encryption
+    (e = 0) of the constant plaintext m(X) = 1 has c0 + c1*s = Delta exactly
+    over Z_Q (Python integers, ring product by definition), and that Delta is
+    the largest integer with Delta*t <= Q."""
+    for par in (tiny, tiny2):
+        sk = _key_material(par, 7)
+        a, _ = W.encryption_randomness(par.q, par.N, 1, seed=8)
+        one = np.zeros(par.N, dtype=np.uint64)
+        one[0] = 1
+        ct = bfv.encrypt(par, sk, one, a[0], np.zeros(par.N, dtype=np.int64))
+        Q = math.prod(par.q)
+        crt = [[sum(int(ct[p][i][c]) * (Q // q) * pow(Q // q, -1, q)
+                    for i, q in enumerate(par.q)) % Q for c in range(par.N)] for p in range(2)]
+        s = [int(v) % Q for v in sk]
+        x = [(u + w) % Q for u, w in zip(crt[0], py_negacyclic(crt[1], s, Q))]
+        assert x[1:] == [0] * (par.N - 1)
+        assert x[0] * par.t <= Q < (x[0] + 1) * par.t
+
+
 def test_mod_up_against_crt(tiny2):
     par = tiny2
     rng = np.random.default_rng(3)
@@ -284,3 +304,22 @@ def test_mod_switch(cfg, L2):
         Y = bfv.crt_compose(low, sw[p])
         for x, y in zip(X, Y):
             assert any((x // D - u - y) % Qp == 0 for u in range(nd))
+
+
+def test_mod_switch_needs_a_prefix_of_the_primes(tiny, tiny2):
+    """The smaller parameters must share the ring, the plaintext modulus and
+    a proper prefix of the ciphertext primes; anything else is refused."""
+    import dataclasses
+    c = W.CONFIGS["tiny2"]
+    low = bfv.Params.from_config(dataclasses.replace(c, L=1, dnum=1))
+    ct = np.zeros((2, tiny2.L, tiny2.N), dtype=np.uint64)
+    assert bfv.mod_switch(tiny2, low, ct).shape == (2, 1, tiny2.N)
+    with pytest.raises(ValueError):
+        bfv.mod_switch(low, tiny2, ct[:, :1])             # more primes
+    with pytest.raises(ValueError):
+        bfv.mod_switch(tiny2, tiny2, ct)                  # nothing dropped
+    with pytest.raises(ValueError):
+        bfv.mod_switch(tiny2, tiny, ct)                   # another ring
+    other = bfv.Params(tiny2.log_n, tiny2.t, tiny2.bits - 1, 1, 1, 1)
+    with pytest.raises(ValueError):
+        bfv.mod_switch(tiny2, other, ct)                  # other primes

@@ -56,8 +56,9 @@ def test_plan_shapes_match_cost_model():
 
 def test_rotsum_levels_cover_every_shift_once():
     """The levels' shifts sum_i j_i l_i (j_i < r_i) are exactly the multiples
-    i s' for i < m/s', each once (brute force), with every radix at most 8 and
-    ceil(log2(m/s')/3) levels."""
+    i s' for i < m/s', each once (brute force), with every radix at most 8,
+    ceil(log2(m/s')/3) levels and the larger radices first (the schedule the
+    library runs, so that both use the same rotation keys)."""
     from types import SimpleNamespace
     for bits in range(0, 11):
         for s_prime in (1, 4, 16):
@@ -66,6 +67,7 @@ def test_rotsum_levels_cover_every_shift_once():
             lv = pdq.rotsum_levels(par, plan)
             assert len(lv) == -(-bits // 3)
             assert all(2 <= r <= 8 and r & (r - 1) == 0 for _, r in lv)
+            assert [r for _, r in lv] == sorted((r for _, r in lv), reverse=True)
             shifts = [0]
             for l, r in lv:
                 shifts = [x + j * l for x in shifts for j in range(r)]
@@ -349,6 +351,25 @@ def test_decomp_single_match_closed_form():
         e = [node * val % t]
         assert pdq.reconst_idx(w, t, 65536) == [node]
         assert pdq.reconst(e, [node], t) == [val * 1 % t]
+
+
+def test_decomp_rejects_inconsistent_values():
+    """Alg. 4 solves the square system on the first l rows; the rows l+1..s'
+    of C d must agree with that solution, so a compressed value changed in
+    one of them is reported instead of decoded (brute force over every
+    extra row)."""
+    t, sp = 65537, 8
+    nodes, vals = [3, 10, 4000], [5, 0, 65536]
+    w = [sum(pow(a, j + 1, t) for a in nodes) % t for j in range(sp)]
+    e = [sum(pow(a, j + 1, t) * x for a, x in zip(nodes, vals)) % t for j in range(sp)]
+    got = pdq.reconst_idx(w, t, 65536)
+    assert got == nodes
+    assert pdq.reconst(e, got, t) == vals
+    for j in range(len(nodes), sp):
+        bad = list(e)
+        bad[j] = (bad[j] + 1) % t
+        with pytest.raises(pdq.DecodeError):
+            pdq.reconst(bad, got, t)
 
 
 def test_decomp_detects_overflow():
