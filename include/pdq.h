@@ -269,8 +269,12 @@ int pdq_answer(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
 /* Answer with host buffers, end to end: copies the query ciphertexts (host
  * [J][2][L][N], coefficient form) to the device, transforms them, runs
  * Mask and Comp, transforms the answer back and copies it to out_host
- * ([n_out][2][L][N], coefficient form).  Synchronises `stream` before
- * returning.  Host buffers should be pinned for full copy bandwidth.
+ * ([n_out][2][L][N], coefficient form).  The query goes up in at most four
+ * runs of index ciphertexts on a stream of the call's own, ordered after the
+ * work already queued on `stream`; each run is transformed and packed on
+ * `stream` while the next one is copied.  Synchronises `stream` (and its own
+ * copy stream) before returning, also on errors after the copies started.
+ * Host buffers should be pinned for the copies to overlap.
  * Workspace: pdq_answer_host_workspace_bytes (device). */
 size_t pdq_answer_host_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan);
 int pdq_answer_host(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_host,

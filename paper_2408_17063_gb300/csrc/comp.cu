@@ -175,13 +175,32 @@ size_t comp_ws_bytes(const Ctx& c, const pdq_plan& pl) {
     return comp_layout(c, pl).end * sizeof(u64);
 }
 
+// The Answer's first stage for the jn index ciphertexts at v (NTT form):
+// w_j = Rot_col(v_j), then the Mask products fused with the pack into
+// u_{2j}, u_{2j+1}.  v, db, w and U point at the run's first j; rws and aws
+// are Comp's key-switch scratch.
+int answer_pack(const Ctx& c, const Keys& keys, const u64* v, const u64* db, u64* w, u64* U,
+                u32 jn, u64* rws, u64* aws, cudaStream_t st) {
+    const long long cts = (long long)ct_elems(c);
+    const u64 kc = 2ull * c.N - 1;
+    const u64* kp = keys.find(kc);
+    if (!kp) return fail(PDQ_E_KEY, "answer: missing rotation key for Galois element " + std::to_string(kc));
+    const CtSet vin = ct_set(v, cts);
+    u64* D = nullptr;
+    PDQ_TRY(ks_raise(c, vin, jn, rws, &D, st));
+    PDQ_TRY(ks_apply(c, D, vin, jn, (u32)kc, kp, ct_set(w, cts), CtSet{}, aws, st));
+    prof_mark(c, PDQ_STAGE_MASK, st);
+    return mask_pack(c, jn, v, w, db, U, st);
+}
+
 // Comp from the masked ciphertexts (masked != nullptr: [J][4] as pdq_mask
 // writes them), or the Answer from the index ciphertexts v_cts and the
 // database db (masked == nullptr: the Mask fused with the pack, w holding J
 // ciphertexts of scratch).
 int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& keys,
              const u64* consts, u64* out, void* ws, size_t ws_bytes, cudaStream_t st,
-             const u64* v_cts = nullptr, const u64* db = nullptr, u64* w = nullptr) {
+             const u64* v_cts = nullptr, const u64* db = nullptr, u64* w = nullptr,
+             bool prepacked = false) {
     if (ws_bytes < comp_ws_bytes(c, pl)) return fail(PDQ_E_NOMEM, "comp: workspace too small");
     const long long cts = (long long)ct_elems(c);
     const long long ects = 2LL * (c.L + c.K) * c.N;
@@ -212,15 +231,11 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     // in the Answer Rot_col(v_j) once per j and the Mask products after it
     prof_mark(c, PDQ_STAGE_PACK, st);
     if (!masked) {
-        if (!v_cts || !db || !w) return fail(PDQ_E_PARAM, "answer: null buffer");
-        const u64 kc = 2ull * c.N - 1;
-        const u64* kp;
-        PDQ_TRY(key_for(kc, &kp));
-        const CtSet vin = ct_set(v_cts, cts);
-        PDQ_TRY(ks_raise(c, vin, pl.J, rws, &D, st));
-        PDQ_TRY(ks_apply(c, D, vin, pl.J, (u32)kc, kp, ct_set(w, cts), none, aws, st));
-        prof_mark(c, PDQ_STAGE_MASK, st);
-        PDQ_TRY(mask_pack(c, pl.J, v_cts, w, db, U, st));
+        // prepacked: the caller ran answer_pack into U already
+        if (!prepacked) {
+            if (!v_cts || !db || !w) return fail(PDQ_E_PARAM, "answer: null buffer");
+            PDQ_TRY(answer_pack(c, keys, v_cts, db, w, U, pl.J, rws, aws, st));
+        }
     } else {
         CtSet in;  in.base = masked + 2 * cts;  in.outer = 4 * cts;  in.per = 2;  in.inner = -cts;
         CtSet add; add.base = masked;           add.outer = 4 * cts; add.per = 2; add.inner = 3 * cts;
@@ -533,20 +548,65 @@ int pdq_answer_host(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_
     const Ctx& c = C(ctx);
     if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "answer_host: invalid plan");
     if (!v_host || !out_host) return fail(PDQ_E_PARAM, "answer_host: null host buffer");
+    if (!db || !keys || !galois || !consts || !ws) return fail(PDQ_E_PARAM, "answer_host: null buffer");
     if (ws_bytes < pdq_answer_host_workspace_bytes(ctx, plan)) return fail(PDQ_E_NOMEM, "answer_host: workspace too small");
     cudaStream_t st = (cudaStream_t)stream;
     const u64 cts = ct_elems(c);
+    const u32 J = plan->J;
+    // workspace: v [J] | answer [n_out] | w = Rot_col(v) [J] | Comp
     u64* v = reinterpret_cast<u64*>(ws);
-    u64* o = v + (u64)plan->J * cts;
-    char* rest = reinterpret_cast<char*>(o + (u64)plan->n_out * cts);
-    const size_t vbytes = (size_t)plan->J * cts * sizeof(u64);
-    const size_t obytes = (size_t)plan->n_out * cts * sizeof(u64);
-    if (cudaMemcpyAsync(v, v_host, vbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return fail(PDQ_E_CUDA, "answer_host: upload failed");
-    PDQ_TRY(ntt_forward(c, v, 2 * plan->J, c.L, 0, (u64)c.L * c.N, st));
-    PDQ_TRY(pdq_answer(ctx, plan, v, db, keys, galois, nkeys, consts, o, rest,
-                       ws_bytes - vbytes - obytes, stream));
+    u64* o = v + (u64)J * cts;
+    u64* w = o + (u64)plan->n_out * cts;
+    u64* cws = w + (u64)J * cts;
+    const size_t cws_bytes = ws_bytes - ((size_t)2 * J + plan->n_out) * cts * sizeof(u64);
+    const CompLayout lo = comp_layout(c, *plan);
+    u64* U = cws + lo.U;
+    Keys k{keys, galois, nkeys, (u64)c.ndigits * 2 * (c.L + c.K) * c.N};
+
+    // The index ciphertexts go up in (at most) four runs on a second stream;
+    // each run is transformed and packed on `stream` while the next one is
+    // copied.  The copies start after the work already queued on `stream`.
+    struct Runs {
+        cudaStream_t cs = nullptr;
+        std::vector<cudaEvent_t> ev;
+        ~Runs() {
+            if (cs) cudaStreamSynchronize(cs);   // no copy outlives the call
+            for (cudaEvent_t e : ev) cudaEventDestroy(e);
+            if (cs) cudaStreamDestroy(cs);
+        }
+    } runs;
+    const u32 per = (J + 3) / 4, nrun = (J + per - 1) / per;
+    if (cudaStreamCreateWithFlags(&runs.cs, cudaStreamNonBlocking) != cudaSuccess) {
+        runs.cs = nullptr;
+        return cuda_check("answer_host: copy stream");
+    }
+    for (u32 r = 0; r <= nrun; ++r) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return cuda_check("answer_host: events");
+        runs.ev.push_back(e);
+    }
+    if (cudaEventRecord(runs.ev[nrun], st) != cudaSuccess ||
+        cudaStreamWaitEvent(runs.cs, runs.ev[nrun], 0) != cudaSuccess)
+        return cuda_check("answer_host: stream order");
+    for (u32 r = 0; r < nrun; ++r) {
+        const u64 j0 = (u64)r * per, jn = std::min<u64>(per, J - j0);
+        if (cudaMemcpyAsync(v + j0 * cts, v_host + j0 * cts, jn * cts * sizeof(u64),
+                            cudaMemcpyHostToDevice, runs.cs) != cudaSuccess ||
+            cudaEventRecord(runs.ev[r], runs.cs) != cudaSuccess)
+            return fail(PDQ_E_CUDA, "answer_host: upload failed");
+    }
+    prof_mark(c, PDQ_STAGE_PACK, st);
+    for (u32 r = 0; r < nrun; ++r) {
+        const u64 j0 = (u64)r * per, jn = std::min<u64>(per, J - j0);
+        if (cudaStreamWaitEvent(st, runs.ev[r], 0) != cudaSuccess) return cuda_check("answer_host: wait");
+        PDQ_TRY(ntt_forward(c, v + j0 * cts, 2 * (u32)jn, c.L, 0, (u64)c.L * c.N, st));
+        PDQ_TRY(answer_pack(c, k, v + j0 * cts, db + j0 * cts, w + j0 * cts, U + 2 * j0 * cts,
+                            (u32)jn, cws + lo.rws, cws + lo.aws, st));
+    }
+    PDQ_TRY(comp_run(c, *plan, nullptr, k, consts, o, cws, cws_bytes, st, v, db, w, true));
     PDQ_TRY(ntt_inverse(c, o, 2 * plan->n_out, c.L, 0, (u64)c.L * c.N, st));
+    const size_t obytes = (size_t)plan->n_out * cts * sizeof(u64);
     if (cudaMemcpyAsync(out_host, o, obytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return fail(PDQ_E_CUDA, "answer_host: download failed");
     if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("answer_host");
