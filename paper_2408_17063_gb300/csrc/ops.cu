@@ -892,10 +892,22 @@ __device__ __forceinline__ u64 foldk(const AccK& A, const Mod& md, const u64* __
     return reduce64(v, md);
 }
 
+// The accumulated value mod q when it sums at most 256 products of residues
+// below 2^60: S = S00 + (Smid - S00 - S11) 2^30 + S11 2^60 < 256 (2^60)^2 =
+// 2^128 is formed exactly in 128 bits and reduced once.
+__device__ __forceinline__ u64 fold1(const AccK& A, const Mod& md) {
+    const u128 s00 = ((u128)A.z0 << 64) | ((u128)A.y0 << 32) | A.x0;
+    const u128 sm = ((u128)A.z1 << 64) | ((u128)A.y1 << 32) | A.x1;
+    const u128 s11 = ((u128)A.z2 << 64) | ((u128)A.y2 << 32) | A.x2;
+    const u128 s = s00 + ((sm - s00 - s11) << 30) + (s11 << 60);
+    return reduce128((u64)(s >> 64), (u64)s, md);
+}
+
 struct MacArgs {
     u32 G, hpg, H, B, GI, E, logN;
     u32 logX, logGS, logGI, CPC;   // CPC: combinations per CTA (even)
     u32 tiles_per_cta, achunks;
+    u32 fold_one;                  // at most 256 products per output: fold1
 };
 
 template <int GT, int BC, int PC>
@@ -1035,7 +1047,7 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
                         const u32 gi = g0 + g;
                         u64* o = gi == 0 ? acc0 + ((u64)gam * 2 + poly) * LN + pos
                                          : acc + (((u64)gam * (GI - 1) + gi - 1) * 2 + poly) * LN + pos;
-                        *o = foldk(A[p][g], md, ckar + 8 * l);
+                        *o = a.fold_one ? fold1(A[p][g], md) : foldk(A[p][g], md, ckar + 8 * l);
                     }
                 }
             }
@@ -1623,6 +1635,7 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
     a.CPC = s.combos_per_cta;
     a.tiles_per_cta = s.tiles_per_cta;
     a.achunks = pl.B / BC;
+    a.fold_one = (u64)std::min(pl.hpg, pl.H) * pl.B <= 256 ? 1u : 0u;
     const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, a.E, s.zslices);
     k_diag_mac<GT, BC, kMacPC><<<grid, s.threads, s.smem, st>>>(R, Dg, a, c.d_mods, c.d_ckar, acc0,
                                                                  acc);

@@ -58,6 +58,7 @@ def test_c3_sampled_steps_bit_exact(c3):
     dict(cfg_name="tiny2", s=5, B=1),            # no baby steps
     dict(cfg_name="tiny", n=1, s=1),             # a single record
     dict(cfg_name="grouped", n=257, s=2),        # a second group with one record
+    dict(cfg_name="tiny2", n=300, s=32, B=32),   # 320 products per accumulator (wide fold)
 ])
 def test_edge_cases_bit_exact(kw):
     name = kw.pop("cfg_name")
