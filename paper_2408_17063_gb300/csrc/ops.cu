@@ -920,8 +920,11 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
     extern __shared__ __align__(16) u64 smem[];
     const u32 X = 1u << a.logX, GI = a.GI, GIp = GI + 2, CPC = a.CPC;
     const u32 l = blockIdx.y;
-    const u32 gs = threadIdx.x & ((1u << a.logGS) - 1);
-    const u32 xi = (threadIdx.x >> a.logGS) & (X - 1);
+    // position in the low thread bits: the 8 threads of a quarter-warp read
+    // the diagonal rows of 8 positions (row stride GI + 2 words), whose
+    // 16-byte loads fall in distinct banks, and write 8 consecutive outputs
+    const u32 xi = threadIdx.x & (X - 1);
+    const u32 gs = (threadIdx.x >> a.logX) & ((1u << a.logGS) - 1);
     const u32 ct = threadIdx.x >> (a.logGS + a.logX);
     const u32 cbase = blockIdx.z * CPC;
     const u64 N = 1ull << a.logN;
