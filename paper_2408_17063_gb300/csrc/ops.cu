@@ -844,10 +844,14 @@ __global__ void k_moddown_final_poly(const u64* __restrict__ A, u64 a_stride,
 // count of 64-bit overflows), so no sum needs renormalising within a tile;
 // at the end of a position tile the sums are folded to
 //   S00 + (Smid - S00 - S11) 2^30 + S11 2^60
-//     = S00 (1 - 2^30) + Smid 2^30 + S11 (2^60 - 2^30)   (mod q).
+// formed exactly in 128 bits and reduced once when an output sums at most
+// 256 products (fold1), else as
+//   S00 (1 - 2^30) + Smid 2^30 + S11 (2^60 - 2^30)   (mod q)
+// from the three sums reduced separately (foldk).
 //
 // Work split: one CTA owns limb l = blockIdx.y, X consecutive positions and
-// the (gamma, p) combinations of its z-slice; thread (gs, xi, ct) handles
+// the (gamma, p) combinations of its z-slice; thread (xi, gs, ct) (position
+// in the lowest bits) handles
 // position x0 + xi, giant indices gs*GT .. gs*GT+GT-1 and the two
 // polynomials p = 0, 1 of group gamma = (cbase + 2ct) / 2.  Per step
 // (hh, a-chunk of BC) the CTA stages the diagonal tile
