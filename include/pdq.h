@@ -103,12 +103,21 @@ typedef struct {
 /* ---------------------------------------------------------------- context */
 
 /* Build the prime chain, transform tables, slot permutation and key-switching
- * constants on the current device.  Synchronous.  *out is owned by the
- * caller and released with pdq_ctx_destroy.  Errors: PDQ_E_PARAM for
- * unsupported sizes, PDQ_E_NOMEM / PDQ_E_CUDA on device failures. */
+ * constants of one parameter set on the current device: the ring and the
+ * plaintext prime of Sec. 5.1, the modulus chain of Sec. 6.1 (there: two
+ * 54-bit primes) extended by K special primes for hybrid key switching.
+ * Synchronous.  *out is owned by the caller and released with
+ * pdq_ctx_destroy.  Errors: PDQ_E_PARAM for unsupported sizes, PDQ_E_NOMEM /
+ * PDQ_E_CUDA on device failures. */
 int pdq_ctx_create(const pdq_params* params, pdq_ctx** out);
+/* Release a context and its device tables (no operation of the paper; the
+ * caller's buffers are untouched).  NULL is accepted. */
 int pdq_ctx_destroy(pdq_ctx* ctx);
+/* The parameters a context derived (the primes and roots of Sec. 5.1's ring
+ * and slot structure) into host *info. */
 int pdq_ctx_info(const pdq_ctx* ctx, pdq_info* info);
+/* Message of the calling thread's last error (library bookkeeping; never
+ * NULL, owned by the library until the thread's next failing call). */
 const char* pdq_last_error(void);
 
 /* ------------------------------------------------------------- transforms
@@ -129,8 +138,11 @@ int pdq_ntt_inverse(const pdq_ctx* ctx, uint64_t* data, uint32_t count, uint32_t
 int pdq_encode(const pdq_ctx* ctx, const uint32_t* slots, uint32_t count, uint32_t nlimbs,
                uint64_t* pt_out, void* stream);
 
-/* Ternary secret (dev [N] int8 in {-1,0,1}) -> NTT form over the extended
- * basis (dev sk_out [L+K][N]). */
+/* The secret key s of HE KeyGen (Sec. 2.2), a ternary polynomial: dev [N]
+ * int8 in {-1,0,1} -> NTT form over the extended basis (dev sk_out
+ * [L+K][N]), the form pdq_encrypt, pdq_rotkey_gen and pdq_decrypt take.
+ * PDQ_E_PARAM for a null pointer; coefficients outside {-1,0,1} are not
+ * checked here (pdq_sk_export refuses them). */
 int pdq_secret_prepare(const pdq_ctx* ctx, const int8_t* s, uint64_t* sk_out, void* stream);
 
 /* Symmetric BFV encryption of `count` slot vectors (HE Enc, Sec. 2.2):
@@ -150,7 +162,8 @@ int pdq_rotkey_gen(const pdq_ctx* ctx, const uint64_t* sk, uint64_t galois, cons
 
 /* HE Dec + decode (Sec. 2.2, Alg. 6 first line): m = round(t [c0 + c1 s]_Q / Q)
  * mod t, then the slot values.  ct: dev [count][2][L][N]; slots_out: dev
- * [count][N] uint32.  Needs a workspace of pdq_decrypt_workspace_bytes. */
+ * [count][N] uint32.  pdq_decrypt_workspace_bytes(count) is the dev scratch
+ * this needs (smaller -> PDQ_E_NOMEM). */
 size_t pdq_decrypt_workspace_bytes(const pdq_ctx* ctx, uint32_t count);
 int pdq_decrypt(const pdq_ctx* ctx, const uint64_t* sk, const uint64_t* ct, uint32_t count,
                 uint32_t* slots_out, void* ws, size_t ws_bytes, void* stream);
@@ -159,8 +172,9 @@ int pdq_decrypt(const pdq_ctx* ctx, const uint64_t* sk, const uint64_t* ct, uint
  * ct_out[i] = sigma_k(ct_in[i]) followed by hybrid key switching with `key`
  * (the key for `galois`), for i < count (Rot_row / Rot_col of Sec. 5.1).
  * The raised digits of c1 are computed before the automorphism.  ct_in and
- * ct_out: dev [count][2][L][N], may not overlap.  Workspace:
- * pdq_rotate_workspace_bytes(count). */
+ * ct_out: dev [count][2][L][N], may not overlap.  Workspace (dev):
+ * pdq_rotate_workspace_bytes(count) bytes, the raised digits of Sec. 5.1's
+ * key switching and the inner-product scratch; smaller -> PDQ_E_NOMEM. */
 size_t pdq_rotate_workspace_bytes(const pdq_ctx* ctx, uint32_t count);
 int pdq_rotate(const pdq_ctx* ctx, const uint64_t* ct_in, uint32_t count, uint64_t galois,
                const uint64_t* key, uint64_t* ct_out, void* ws, size_t ws_bytes, void* stream);
@@ -193,8 +207,12 @@ int pdq_mod_switch(const pdq_ctx* from, const pdq_ctx* to, const uint64_t* cts, 
 int pdq_plan_make(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B, pdq_plan* plan);
 
 /* The Galois elements of every rotation the plan uses, ascending (host
- * out[cap]); *count receives how many there are.  The key buffer passed to
- * pdq_comp holds one key per element in this order. */
+ * out[cap]); *count receives how many there are (PDQ_E_NOMEM if cap is
+ * smaller).  These are Rot_col of the u-packing remark (2N-1) and the row
+ * rotations 3^r of Sec. 5.2's baby steps (r = 1..B-1), giant steps (r = gB)
+ * and rotate-and-sum (r = j l per level); the client makes one key per
+ * element (pdq_rotkey_gen).  The key buffer passed to pdq_comp holds one key
+ * per element in this order. */
 int pdq_plan_galois(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out, uint32_t cap,
                     uint32_t* count);
 
@@ -379,6 +397,34 @@ int pdq_sk_export(const pdq_ctx* ctx, const uint64_t* sk, void* out_host, size_t
 int pdq_sk_import(const pdq_ctx* ctx, const void* in_host, size_t in_bytes, uint64_t* sk_out,
                   void* stream);
 
+/* Rotation keys (the hybrid key-switching keys of the rotations of Sec. 5.1
+ * that Comp's baby steps, giant steps and rotate-and-sum use, Sec. 5.2): the
+ * client makes them once per key set and the server keeps them resident.
+ * Header as above with magic "PDQK", limbs = L+K, level = L and the digit
+ * count in the first 4 reserved bytes; then count uint64 Galois elements;
+ * then count x ndigits x 2 x (L+K) x N uint64 in coefficient form,
+ * [key][digit][poly][limb][coeff] (poly 0 = b, 1 = a of pdq_rotkey_gen).
+ * Both calls synchronise `stream`.
+ * pdq_rotkeys_export: keys dev [count][ndigits][2][L+K][N] (NTT form, as
+ *   pdq_rotkey_gen writes them; unchanged), galois host [count]; out_host of
+ *   at least pdq_rotkeys_serialized_bytes(count) bytes (else PDQ_E_NOMEM);
+ *   ws dev, ndigits*2*(L+K)*N words of scratch.  PDQ_E_PARAM for an even or
+ *   out-of-range Galois element.
+ * pdq_rotkeys_import: in_host as written by pdq_rotkeys_export (or by any
+ *   client holding the same prime chain); keys_out dev room for cap keys (NTT
+ *   form on return, the layout pdq_answer takes), galois_out host [cap];
+ *   *count = the header's count.  PDQ_E_PARAM for a wrong magic, version, N,
+ *   L, K, digit count, t or first prime, a truncated buffer, an even,
+ *   out-of-range or repeated Galois element or a non-canonical residue;
+ *   PDQ_E_NOMEM if count > cap. */
+size_t pdq_rotkeys_serialized_bytes(const pdq_ctx* ctx, uint32_t count);
+int pdq_rotkeys_export(const pdq_ctx* ctx, const uint64_t* keys, const uint64_t* galois,
+                       uint32_t count, void* out_host, size_t out_bytes, uint64_t* ws,
+                       void* stream);
+int pdq_rotkeys_import(const pdq_ctx* ctx, const void* in_host, size_t in_bytes,
+                       uint64_t* keys_out, uint64_t* galois_out, uint32_t cap, uint32_t* count,
+                       void* stream);
+
 /* ------------------------------------------------- rotation without alloc
  * The paper has no counterpart to this call: it exists for callers that
  * cannot allocate device memory where they rotate (an external memory
@@ -388,7 +434,9 @@ int pdq_sk_import(const pdq_ctx* ctx, const void* in_host, size_t in_bytes, uint
  * a fixed array of pdq_rotate_noalloc_max_bytes() bytes (32 MiB) that the
  * library reserves on every GPU that loads it, until the process exits; the
  * call itself allocates nothing.  The first call on a device looks up that
- * array's address (once per device), so make it before any stream capture.
+ * array's address (once per device), so make it before any stream capture;
+ * the address stays cached for the life of the process, so do not call this
+ * again on a device after cudaDeviceReset has ended its context.
  * Calls share the array: two calls that overlap on the GPU race.  Every
  * scratch byte is written before it is read, so nothing needs clearing.
  * Errors: PDQ_E_PARAM if `count` ciphertexts need more scratch than the

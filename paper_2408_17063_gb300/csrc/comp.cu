@@ -29,8 +29,6 @@ namespace {
 
 const Ctx& C(const pdq_ctx* p) { return *reinterpret_cast<const Ctx*>(p); }
 
-u64 ct_elems(const Ctx& c) { return 2ull * c.L * c.N; }
-
 u32 ceil_log2(u64 x) {
     u32 r = 0;
     while ((1ull << r) < x) ++r;
@@ -342,6 +340,7 @@ int pdq_encode(const pdq_ctx* ctx, const uint32_t* slots, uint32_t count, uint32
 
 int pdq_secret_prepare(const pdq_ctx* ctx, const int8_t* s, uint64_t* sk_out, void* stream) {
     PDQ_CHECK_CTX(ctx);
+    if (!s || !sk_out) return fail(PDQ_E_PARAM, "secret_prepare: null buffer");
     return secret_prepare(C(ctx), s, sk_out, (cudaStream_t)stream);
 }
 

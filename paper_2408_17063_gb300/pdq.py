@@ -122,6 +122,9 @@ _SIGS = {
     "pdq_sk_serialized_bytes": (_SZ, [_P]),
     "pdq_sk_export": (_I, [_P, _P, _P, _SZ, _P, _P]),
     "pdq_sk_import": (_I, [_P, _P, _SZ, _P, _P]),
+    "pdq_rotkeys_serialized_bytes": (_SZ, [_P, _U32]),
+    "pdq_rotkeys_export": (_I, [_P, _P, _P, _U32, _P, _SZ, _P, _P]),
+    "pdq_rotkeys_import": (_I, [_P, _P, _SZ, _P, _P, _U32, ctypes.POINTER(_U32), _P]),
     "pdq_rotate_noalloc_max_bytes": (_SZ, []),
     "pdq_rotate_noalloc": (_I, [_P, _P, _U32, _U64, _P, _P, _P]),
     "pdq_profile_enable": (_I, [_P, _I]),
@@ -316,6 +319,31 @@ class Context:
         out = self._u64(self.E * self.N)
         _check(load().pdq_sk_import(self.h, data, len(data), _ptr(out), _stream(stream)))
         return out.view(self.E, self.N)
+
+    def rotkeys_export(self, keys, galois, stream=None) -> bytes:
+        """pdq_rotkeys_export: keys [count][ndigits][2][E][N] (NTT form) with
+        their Galois elements -> bytes."""
+        gal = np.ascontiguousarray(galois, dtype=np.uint64)
+        count = len(gal)
+        lib = load()
+        nbytes = lib.pdq_rotkeys_serialized_bytes(self.h, count)
+        buf = ctypes.create_string_buffer(nbytes)
+        ws = self._u64(self.key_elems)
+        _check(lib.pdq_rotkeys_export(self.h, _ptr(keys), _ptr(gal), count, buf, nbytes,
+                                      _ptr(ws), _stream(stream)))
+        return buf.raw
+
+    def rotkeys_import(self, data: bytes, stream=None):
+        """pdq_rotkeys_import: bytes -> (keys [count * key_elems] NTT form on
+        the device, Galois elements as a list)."""
+        lib = load()
+        hdr_count = int.from_bytes(data[20:24], "little") if len(data) >= 24 else 0
+        keys = self._u64(max(hdr_count * self.key_elems, 1))
+        gal = np.zeros(max(hdr_count, 1), dtype=np.uint64)
+        cnt = _U32()
+        _check(lib.pdq_rotkeys_import(self.h, data, len(data), _ptr(keys), _ptr(gal), hdr_count,
+                                      ctypes.byref(cnt), _stream(stream)))
+        return keys[:cnt.value * self.key_elems], [int(g) for g in gal[:cnt.value]]
 
     def rotate(self, ct, galois: int, key, stream=None) -> torch.Tensor:
         count = ct.numel() // self.ct_elems
