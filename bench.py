@@ -9,7 +9,7 @@ resident in HBM.
 Prints one JSON line.  Under torchrun (N > 1) every rank answers its own
 queries (replicas; the method has no cross-GPU exchange), rank 0 prints.
 ``--impl reference`` times the CPU oracle on the host cores instead (a
-bounded sample per step, see ``oracle_sample``).
+bounded sample per step, see ``oracle.baseline``).
 """
 from __future__ import annotations
 
@@ -147,86 +147,30 @@ class ClockSampler:
 
 # ------------------------------------------------------- CPU oracle sample --
 
-def oracle_sample(cfg, budget_s: float = 20.0) -> dict:
-    """Time the CPU oracle on a bounded sample of the workload and scale it to
-    one Answer with the oracle's own operation counts: a raise of c1, a
-    rotation with its ModDown, an extended-basis rotation, a ModDown of one
-    polynomial, a plaintext-ciphertext product and diagonal products over
-    Q u P, each at full size."""
-    import numpy as np
-    import workloads as W
-    from oracle import bfv, pdq as opdq
-
-    par = bfv.Params.from_config(cfg)
-    plan = opdq.make_plan(par, cfg.n, cfg.s)
-    E = par.L + par.K
-    sk = W.draw_ternary(par.N, W.rng_for(cfg.seed, 3))
-    a, e = W.encryption_randomness(par.q, par.N, 1, cfg.seed)
-    ct = bfv.encrypt(par, sk, bfv.encode(par, np.arange(par.N) % par.t), a[0], e[0])
-    ct_ext = bfv.ct_times_P(par, ct)
-    k = par.galois_rot(1)
-    kr = W.rotation_key_randomness(par.ext, par.N, len(par.digits), [k], cfg.seed)
-    key = bfv.rotation_key(par, sk, k, *kr[k])
-    pt = opdq.lifted_pt(par, np.arange(par.N) % par.t)
-    pt_ext = bfv.lift(par, bfv.encode(par, np.arange(par.N) % par.t), par.ext)
-
-    def timed(f):
-        t0 = time.perf_counter()
-        r = f()
-        return r, time.perf_counter() - t0
-
-    raised, t_raise = timed(lambda: bfv.mod_up_all(par, ct[1]))
-    _, t_apply = timed(lambda: bfv.rotate_hoisted(par, ct, raised, k, key))
-    _, t_ext = timed(lambda: bfv.rotate_ext_lazy(par, ct_ext, raised, k, key))
-    _, t_down = timed(lambda: bfv.mod_down(par, ct_ext[1]))
-    _, t_ptmul = timed(lambda: bfv.pt_mul(par, ct, pt))
-    nmac = 2
-    _, t = timed(lambda: opdq.ring_dot_ext(par, [pt_ext] * nmac, [ct_ext] * nmac))
-    t_mac = t / nmac
-    levels = opdq.rotsum_levels(par, plan)
-    rot_giant = plan.G * (plan.giants - 1)
-    n_full = plan.J                                            # Rot_col of each index ciphertext
-    n_raise = (plan.H if plan.B > 1 else 0) + rot_giant + plan.G * len(levels)
-    n_ext = plan.H * (plan.B - 1) + rot_giant + plan.G * sum(r - 1 for _, r in levels)
-    n_down = rot_giant + plan.G * len(levels) + 2 * plan.G
-    n_mac = plan.H * plan.B * plan.giants
-    n_ptmul = 4 * plan.J
-    per_query = (n_full * (t_raise + t_apply) + n_raise * t_raise + n_ext * t_ext
-                 + n_down * t_down + n_mac * t_mac + n_ptmul * t_ptmul)
-    sampled = t_raise + t_apply + t_ext + t_down + t_ptmul + nmac * t_mac
-    return {"value": 1.0 / per_query, "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle timed on one full-size raise ({t_raise:.2f} s), one rotation "
-                       f"with ModDown ({t_apply:.2f} s), one extended-basis rotation "
-                       f"({t_ext:.2f} s), one polynomial ModDown ({t_down:.2f} s), one Mask "
-                       f"product ({t_ptmul:.2f} s) and {nmac} diagonal products over Q u P "
-                       f"({t_mac:.2f} s each), scaled by the oracle's counts per Answer "
-                       f"({n_full} rotations with ModDown, {n_raise} raises, {n_ext} "
-                       f"extended-basis rotations, {n_down} polynomial ModDowns, {n_mac} "
-                       f"diagonal products, {n_ptmul} Mask products) = {per_query:.0f} s per "
-                       f"query; {sampled:.1f} s sampled, single thread"),
-            "seconds_per_query": per_query}
-
-
 def run_reference(args, cfg, rank: int):
+    """The reference arm: the CPU oracle on every host core, one bounded
+    sample of the workload per step (oracle.baseline.all_cores)."""
     if rank != 0:
         return
-    vals = []
-    for _ in range(args.warmup):
-        oracle_sample(cfg)
-    t0 = time.perf_counter()
-    last = None
-    for _ in range(args.steps):
-        last = oracle_sample(cfg)
-        vals.append(last["value"])
-    wall = time.perf_counter() - t0
+    from oracle import baseline
+    procs, rounds = baseline.all_cores(cfg, rounds=args.warmup + args.steps)
+    timed = rounds[args.warmup:]
+    vals = [1.0 / r["seconds_per_query"] for r in timed]
+    wall = sum(r["round_wall_s"] for r in timed)
     v = statistics.median(vals)
+    sample = (f"each step: the oracle (untuned) times one full-size raise, rotation with "
+              f"ModDown, extended-basis rotation, polynomial ModDown, Mask product and two "
+              f"diagonal products over Q u P in each of {procs} processes at once "
+              f"({timed[-1]['sampled_s_per_process']:.1f} s per process), weighted by the "
+              f"oracle's operation counts per Answer and divided over the {procs} cores "
+              f"(the operations are independent across half-blocks, giant steps and groups)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * wall / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 (exact modular integers)",
             "data": "synthetic", "config": config_dict(cfg),
-            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                             "sample": last["sample"]},
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": procs, "kind": "oracle",
+                             "cpu_model": baseline.cpu_model(), "sample": sample},
             "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -812,8 +756,8 @@ def run_gpu(args, cfg, rank: int, world: int):
             mix = Mix(args.mix, args.lanes, clients=args.clients)
             line["batched_shared_keys"] = dict(run_batched(args, mix), clients=args.clients)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in oracle_sample(cfg).items()
-                                if k != "seconds_per_query"}
+        from oracle import baseline
+        line["cpu_baseline"] = baseline.baseline(cfg)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
