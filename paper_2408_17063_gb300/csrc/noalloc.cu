@@ -11,7 +11,10 @@
 // stays reserved until the process exits.  Its device address is looked up
 // once per device (cudaGetSymbolAddress, with that device current) on the
 // first call made on that device, so that first call should come before any
-// stream capture.  All calls share the array: the scratch keeps whatever the
+// stream capture.  The cached address belongs to the device's context at
+// the time of the look-up: after cudaDeviceReset (which ends that context)
+// it is stale, so a process that resets a device must not call this entry
+// point on it again.  All calls share the array: the scratch keeps whatever the
 // previous call left, which is fine because every byte the rotation reads is
 // first written by the same call; but two calls that overlap on the GPU (on
 // different streams, or from different threads) race on it.
@@ -76,7 +79,7 @@ extern "C" int pdq_rotate_noalloc(const pdq_ctx* ctx, const uint64_t* ct_in, uin
     void* base = nullptr;
     PDQ_TRY(scratch_address(&base));
     cudaStream_t st = (cudaStream_t)stream;
-    const long long cts = 2LL * c.L * c.N;
+    const long long cts = (long long)ct_elems(c);
     u64* rws = reinterpret_cast<u64*>(base);
     u64* aws = rws + raise_ws(c, count) / sizeof(u64);
     u64* D = nullptr;

@@ -180,6 +180,9 @@ struct Ctx {
 
 void lanes_release(Ctx* c);
 
+// uint64 elements of one ciphertext over the ciphertext primes, [2][L][N]
+inline u64 ct_elems(const Ctx& c) { return 2ull * c.L * c.N; }
+
 // Record a stage boundary (stage < 0 closes the current stage) when
 // profiling is enabled on the context.
 void prof_mark(const Ctx& c, int stage, cudaStream_t st);
