@@ -110,6 +110,7 @@ class Params:
     L: int
     K: int
     dnum: int
+    chain: tuple | None = None   # (special primes, then ciphertext primes) instead of the search
     N: int = field(init=False)
     m: int = field(init=False)
     q: list = field(init=False)
@@ -127,7 +128,13 @@ class Params:
         self.m = self.N // 2
         if (self.t - 1) % (2 * self.N) or not is_prime(self.t):
             raise ValueError("t must be a prime = 1 mod 2N")
-        chain = ntt_primes(self.N, self.bits, self.K + self.L)
+        if self.chain is None:
+            chain = ntt_primes(self.N, self.bits, self.K + self.L)
+        else:
+            chain = [int(r) for r in self.chain]
+            if len(chain) != self.K + self.L or any(
+                    (r - 1) % (2 * self.N) or r >= 1 << self.bits or not is_prime(r) for r in chain):
+                raise ValueError("chain: need K + L primes = 1 mod 2N below 2^bits")
         self.p = chain[:self.K]
         self.q = chain[self.K:]
         self.ext = self.q + self.p
@@ -145,6 +152,15 @@ class Params:
     @classmethod
     def from_config(cls, cfg) -> "Params":
         return cls(cfg.log_n, cfg.t, cfg.prime_bits, cfg.L, cfg.K, cfg.dnum)
+
+    @classmethod
+    def subring(cls, par: "Params", log_n: int) -> "Params":
+        """The parameters of the subring Z[Y]/(Y^N'+1), Y = X^(N/N'), of
+        par's ring (ring switching, Sec. 5.3): the same t, digits and primes
+        (each = 1 mod 2N, hence 1 mod 2N'), ring dimension N' = 2^log_n."""
+        if not 3 <= log_n < par.log_n:
+            raise ValueError("subring: need a smaller ring dimension")
+        return cls(log_n, par.t, par.bits, par.L, par.K, par.dnum, chain=tuple(par.p + par.q))
 
     # slot (row rho, column c) <-> evaluation exponent (-1)^rho 3^c mod 2N
     def slot_exponents(self) -> np.ndarray:
@@ -463,3 +479,53 @@ def rotate(par: Params, ct, k: int, key) -> np.ndarray:
     """Homomorphic automorphism sigma_k (Rot_row for k = 3^r, Rot_col for
     k = 2N-1), Sec. 5.1."""
     return rotate_hoisted(par, ct, mod_up_all(par, ct[1]), k, key)
+
+
+# ---------------------------------------------------------- ring switching --
+
+def embed_secret(sk_small, R: int) -> np.ndarray:
+    """s'(X) = s_small(X^R): a secret of the subring as an element of the
+    ring of dimension R N' (every R-th coefficient)."""
+    s = np.asarray(sk_small, dtype=np.int64)
+    out = np.zeros(s.size * R, dtype=np.int64)
+    out[::R] = s
+    return out
+
+
+def ring_switch_key(par: Params, sk, sk_small, a, e) -> np.ndarray:
+    """Hybrid key-switching key from s (par's ring) to s'(X) = s_small(X^R),
+    R = N / N' (ring switching, Sec. 5.3, after Gentry-Halevi-Peikert-Smart):
+      b_beta = -a_beta s' + e_beta + [q_i in digit beta] P s  over Q u P,
+    the rotation key's equation with the target secret s' and the source
+    s in place of sigma_k(s).  a: [digits][L+K][N], e: [digits][N];
+    returns [digits][2][L+K][N] holding (b_beta, a_beta)."""
+    el = extlimbs(par)
+    R = par.N // len(sk_small)
+    s_to = signed_to_rns(embed_secret(sk_small, R), par.ext)
+    s_from = signed_to_rns(sk, par.ext)
+    out = []
+    for b_idx, digit in enumerate(par.digits):
+        a_b = np.asarray(a[b_idx], dtype=np.uint64)
+        e_b = signed_to_rns(e[b_idx], par.ext)
+        b = poly_sub(par, e_b, poly_mul(par, a_b, s_to, el), el)
+        for i in digit:
+            qi = par.q[i]
+            b[i] = ring.vec_add(b[i], ring.vec_scale(s_from[i], par.P % qi, qi), qi)
+        out.append(np.stack([b, a_b.copy()]))
+    return np.stack(out)
+
+
+def ring_switch(par: Params, small: Params, ct, key) -> list[np.ndarray]:
+    """Ring switching (Sec. 5.3) of a ciphertext of par's ring to R = N/N'
+    ciphertexts of small's ring over the same primes.  The key switch to
+    s'(X) = s_small(X^R) is the hybrid key switch of rotate() with the
+    identity automorphism; then, with c0 + c1 s' = sum_r X^r
+    (c0_r + c1_r s_small)(X^R) for c_p(X) = sum_r X^r c_{p,r}(X^R), part r
+    = (c0[r::R], c1[r::R]) decrypts under s_small to m_r, where the
+    plaintext is m(X) = sum_r X^r m_r(X^R) (noise split the same way).
+    Returns R ciphertexts [2][L][N'] in coefficient form."""
+    if (small.q, small.p, small.t) != (par.q, par.p, par.t) or par.N % small.N or small.N >= par.N:
+        raise ValueError("ring_switch: small must be a subring with the same primes")
+    R = par.N // small.N
+    sw = rotate(par, ct, 1, key)
+    return [np.ascontiguousarray(sw[:, :, r::R]) for r in range(R)]

@@ -51,7 +51,8 @@ import numpy as np
 
 from . import ring
 from .bfv import (Params, ct_add, ct_mod_down, ct_times_P, decrypt, encode, encrypt, lift,
-                  mod_down, mod_up_all, poly_add, pt_mul, rotate, rotate_ext, rotate_ext_lazy)
+                  mod_down, mod_up_all, poly_add, pt_mul, ring_switch, rotate, rotate_ext,
+                  rotate_ext_lazy)
 
 
 # ------------------------------------------------------------------ plan ----
@@ -86,23 +87,51 @@ def make_plan(par: Params, n: int, s: int, B: int | None = None) -> Plan:
     G_sz = par.N * ((par.t - 1) // par.N)
     hpg = G_sz // par.m
     G = -(-H // hpg)
-    if B is None:
-        # baby/giant split (the paper leaves it open): among the powers of two
-        # B <= min(s', 128) with at most 32 giant steps, the one with the least
-        # work H(B-1) + 8 G(s'/B - 1) + 3 G s'/B (hoisted baby rotations,
-        # giant-step key switches, accumulator ModDowns); ties to the smaller B
-        costs = {}
-        b = 1
-        while b <= min(s_prime, 128):
-            if s_prime // b <= 32:
-                costs[b] = H * (b - 1) + 8 * G * (s_prime // b - 1) + 3 * G * (s_prime // b)
-            b *= 2
-        B = min(costs, key=lambda k: (costs[k], k))
+    B = _baby_steps(H, G, s_prime) if B is None else B
     if B < 1 or s_prime % B:
         raise ValueError("B must divide s'")
     per_out = par.m // s_prime
     n_out = -(-G // per_out)
     return Plan(n, s, s_prime, B, J, H, G_sz, hpg, G, per_out, n_out)
+
+
+def _baby_steps(H: int, G: int, s_prime: int) -> int:
+    """Baby/giant split (the paper leaves it open): among the powers of two
+    B <= min(s', 128) with at most 32 giant steps, the one with the least work
+    H(B-1) + 8 G(s'/B - 1) + 3 G s'/B (hoisted baby rotations, giant-step key
+    switches, accumulator ModDowns); ties to the smaller B."""
+    costs = {}
+    b = 1
+    while b <= min(s_prime, 128):
+        if s_prime // b <= 32:
+            costs[b] = H * (b - 1) + 8 * G * (s_prime // b - 1) + 3 * G * (s_prime // b)
+        b *= 2
+    return min(costs, key=lambda k: (costs[k], k))
+
+
+def make_switched_plan(big: Params, small: Params, n: int, s: int, B: int | None = None) -> Plan:
+    """Plan of Comp in the subring on a ring-switched query (Sec. 5.3): each
+    of the ceil(n/N) ciphertexts of the big ring becomes R = N/N' ciphertexts
+    of the small ring (part r of big ciphertext j at index R j + r, 2R
+    half-blocks), and the records keep the groups of the big ring (G_sz =
+    N floor((t-1)/N) records, nodes alpha(i) = (i mod G_sz) + 1), so
+    hpg = G_sz / m' small half-blocks per group."""
+    if n < 1 or s < 1:
+        raise ValueError("n and s must be positive")
+    R = big.N // small.N
+    s_prime = 1 << math.ceil(math.log2(s))
+    if s_prime > small.m or s_prime >= small.t:
+        raise ValueError("sparsity too large for the ring")
+    J = R * -(-n // big.N)
+    H = 2 * J
+    G_sz = big.N * ((big.t - 1) // big.N)
+    hpg = G_sz // small.m
+    G = -(-H // hpg)
+    B = _baby_steps(H, G, s_prime) if B is None else B
+    if B < 1 or s_prime % B:
+        raise ValueError("B must divide s'")
+    per_out = small.m // s_prime
+    return Plan(n, s, s_prime, B, J, H, G_sz, hpg, G, per_out, -(-G // per_out))
 
 
 def rotsum_levels(par: Params, plan: Plan) -> list[tuple[int, int]]:
@@ -268,6 +297,47 @@ def diagonal_slots(par: Params, plan: Plan, h: int, k: int) -> np.ndarray:
     return np.concatenate([row, row])
 
 
+def switched_nodes(big: Params, small: Params, plan: Plan, h: int):
+    """The records behind half-block h = 2(R j + r) + rho' of a ring-switched
+    query (part r of big ciphertext j, row rho'): small slot (rho', c') with
+    exponent e' = (-1)^rho' 3^c' mod 2N' holds
+      y_r(e') = m_r(zeta'^e') = (1/R) sum_u zeta^(-e_u r) m(zeta^(e_u)),
+    e_u = e' + 2N' u (u < R), zeta' = zeta^R, because m(X) = sum_r X^r
+    m_r(X^R); so the big slots are m(zeta^(e_u)) = sum_r zeta^(e_u r) y_r(e').
+    Returns, per column c' < m' and u < R, the node alpha of the record in
+    big slot e_u of ciphertext j and the factor zeta^(e_u r) mod t."""
+    R = big.N // small.N
+    i, rho = divmod(h, 2)
+    j, r = divmod(i, R)
+    e_small = small.slot_exponents()[rho * small.m:(rho + 1) * small.m].astype(np.int64)
+    e_big = e_small[:, None] + 2 * small.N * np.arange(R, dtype=np.int64)[None, :]
+    slot_of = np.empty(2 * big.N, dtype=np.int64)
+    slot_of[big.slot_exponents()] = np.arange(big.N)
+    rec = j * big.N + slot_of[e_big]
+    alpha = (rec % plan.G_sz + 1).astype(np.uint64)
+    factor = powmod_vec(np.full(e_big.shape, big.zeta, dtype=np.uint64),
+                        (e_big * r) % (2 * big.N), big.t)
+    return alpha, factor
+
+
+def switched_diagonal_slots(big: Params, small: Params, plan: Plan, h: int, k: int) -> np.ndarray:
+    """k-th extended diagonal for half-block h of a ring-switched query.
+    With the fold of switched_nodes, sum over the records of
+    alpha^kk v = sum over (r, e') of y_r(e') W_kk[r][e'],
+    W_kk[r][e'] = sum_u alpha(e_u)^kk zeta^(e_u r): the block of half-block h
+    is M[kk][c'] = W_{kk+1}[r][e'(rho', c')] and, as in diagonal_slots,
+    D_{h,k}[c] = M[c mod s'][(c + k) mod m'] on both rows."""
+    m, t = small.m, small.t
+    alpha, factor = switched_nodes(big, small, plan, h)
+    c = np.arange(m)
+    cc = (c + k) % m
+    kk = (c % plan.s_prime) + 1
+    row = np.zeros(m, dtype=np.uint64)
+    for u in range(alpha.shape[1]):
+        row = (row + powmod_vec(alpha[cc, u], kk, t) * factor[cc, u]) % np.uint64(t)
+    return np.concatenate([row, row])
+
+
 def rot_slots(par: Params, slots, r: int) -> np.ndarray:
     """Rot(.; r) on both rows: [v_1..v_m] -> [v_{1+r}, ..., v_r] (Sec. 5.1)."""
     s = np.asarray(slots).reshape(2, par.m)
@@ -331,10 +401,12 @@ def ring_dot_ext(par: Params, pts, cts) -> np.ndarray:
     return acc
 
 
-def giant_accumulators(par: Params, R, plan: Plan):
+def giant_accumulators(par: Params, R, plan: Plan, diag=None):
     """acc[gamma][g] = sum_{h in gamma} sum_{a<B} Rot(D_{h,gB+a}; -gB) . R[h][a],
     the products summed over Q u P (diagonals lifted to every prime); the
-    accumulators stay in Q u P (giant_steps lowers the ones it rotates)."""
+    accumulators stay in Q u P (giant_steps lowers the ones it rotates).
+    diag(par, plan, h, k) gives D_{h,k} (default: diagonal_slots)."""
+    diag = diag or diagonal_slots
     acc = []
     for gamma in range(plan.G):
         row = []
@@ -342,8 +414,7 @@ def giant_accumulators(par: Params, R, plan: Plan):
             pts, cts = [], []
             for h in group_halfblocks(plan, gamma):
                 for a in range(plan.B):
-                    d = rot_slots(par, diagonal_slots(par, plan, h, g * plan.B + a),
-                                  -g * plan.B)
+                    d = rot_slots(par, diag(par, plan, h, g * plan.B + a), -g * plan.B)
                     pts.append(lift(par, encode(par, d), par.ext))
                     cts.append(R[h][a])
             row.append(ring_dot_ext(par, pts, cts))
@@ -408,20 +479,20 @@ def combine_groups(par: Params, ys, plan: Plan):
     return outs
 
 
-def comp_packed(par: Params, u, keys, plan: Plan) -> list[np.ndarray]:
+def comp_packed(par: Params, u, keys, plan: Plan, diag=None) -> list[np.ndarray]:
     """Comp from the packed u_h on: baby steps, diagonal products, giant
     steps, rotate-and-sum, group masks."""
     R = baby_steps(par, u, keys, plan)
-    acc = giant_accumulators(par, R, plan)
+    acc = giant_accumulators(par, R, plan, diag)
     ys = giant_steps(par, acc, keys, plan)
     ys = [rotate_and_sum(par, y, keys, plan) for y in ys]
     return combine_groups(par, ys, plan)
 
 
-def comp(par: Params, masked, keys, plan: Plan) -> list[np.ndarray]:
+def comp(par: Params, masked, keys, plan: Plan, diag=None) -> list[np.ndarray]:
     """Comp of Alg. 7 in SIMD form: returns the output ciphertexts holding
     ctxt(Cv) in row 0 and ctxt(Cd) in row 1."""
-    return comp_packed(par, pack(par, masked, keys, plan), keys, plan)
+    return comp_packed(par, pack(par, masked, keys, plan), keys, plan, diag)
 
 
 def answer(par: Params, v_cts, db, keys, plan: Plan) -> list[np.ndarray]:
@@ -438,6 +509,37 @@ def answer_switched(par: Params, low: Params, v_cts, db, keys, plan: Plan) -> li
     Mask and Comp run over low's primes with low's keys (plan made for low)."""
     from .bfv import mod_switch
     return answer(low, [mod_switch(par, low, v) for v in v_cts], db, keys, plan)
+
+
+def ring_switch_masked(big: Params, small: Params, masked, rs_key) -> list[np.ndarray]:
+    """The Mask outputs of the big ring (4 per index ciphertext, mask())
+    switched to the subring: part r of masked[4j + q] becomes small
+    ciphertext 4(R j + r) + q.  A small slot of row rho' folds only big slots
+    of row rho' (their exponents agree mod 8), so the row masks survive."""
+    R = big.N // small.N
+    out = [None] * (len(masked) * R)
+    for i, ct in enumerate(masked):
+        j, q = divmod(i, 4)
+        for r, part in enumerate(ring_switch(big, small, ct, rs_key)):
+            out[4 * (R * j + r) + q] = part
+    return out
+
+
+def answer_ring_switched(big: Params, small: Params, v_cts, db, rs_key, keys,
+                         plan: Plan) -> list[np.ndarray]:
+    """The Answer with Comp in a subring (Sec. 5.3: ring switching after Mask,
+    Comp with the smaller parameters): Mask in the big ring (mask()), every
+    masked ciphertext switched to R ciphertexts of small's ring
+    (ring_switch_masked), then Comp there (pack, baby steps, the diagonals of
+    switched_diagonal_slots, giant steps, rotate-and-sum, group masks) with
+    small-ring rotation keys.  plan from make_switched_plan.  The output
+    decrypts under s_small to the same closed form as answer()."""
+    R = big.N // small.N
+    big_plan = Plan(plan.n, plan.s, plan.s_prime, plan.B, plan.J // R, plan.H // R, plan.G_sz,
+                    plan.hpg, plan.G, plan.per_out, plan.n_out)
+    masked = ring_switch_masked(big, small, mask(big, v_cts, db, big_plan), rs_key)
+    return comp(small, masked, keys, plan,
+                lambda par, pl, h, k: switched_diagonal_slots(big, par, pl, h, k))
 
 
 # ------------------------------------------------------- closed form ------
