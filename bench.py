@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--switch-L", type=int, default=2,
                     help="also time the Answer with Comp on this many primes after modulus "
                          "switching (0: skip)")
+    ap.add_argument("--ring-log-n", type=int, default=13,
+                    help="also time the Answer with Comp in the subring of this log2 dimension "
+                         "after ring switching (with --switch-L primes; 0: skip)")
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="served arrival rates, queries/s")
     ap.add_argument("--served-requests", type=int, default=192)
@@ -547,6 +550,111 @@ def run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank: int) -> dict:
                      f"{1 if one else L2} prime(s); one step = the switches + Answer")}
 
 
+def run_ring_switched(args, cfg, ctx, plan, q, v_cts, stream, rank: int) -> dict:
+    """The Answer with Comp in a subring (Sec. 5.3): the resident query over
+    the configuration's primes is switched to L' primes (pdq_mod_switch),
+    masked in the big ring (pdq_mask), switched to R = 2^(log_n - log_small)
+    ciphertexts of the subring each (pdq_ring_switch), compressed there
+    (pdq_comp with a switched plan and subring keys) and the answer switched
+    to one prime.  One step = all of these."""
+    import dataclasses
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2408_17063_gb300 import pdq
+
+    L2, ls = args.switch_L, args.ring_log_n
+    lcfg = dataclasses.replace(cfg, L=L2, dnum=-(-L2 // cfg.K))
+    lo = pdq.Context.from_config(lcfg)
+    small = lo.subring(ls)
+    one = pdq.Context.from_config(dataclasses.replace(cfg, L=1, dnum=1)).subring(ls)
+    bplan = lo.plan(cfg.n, cfg.s)                    # the big-ring Mask only needs J
+    splan = small.plan_switched(cfg.log_n, cfg.n, cfg.s, args.B)
+    seed = cfg.seed + rank + 2
+    sk = lo.secret_prepare(torch.from_numpy(q.sk))
+    s_small = W.draw_ternary(small.N, W.rng_for(seed, 11))
+    ka, ke = W.rotation_key_randomness(lo.moduli, lo.N, lo.ndigits, [1], seed, stream=12)[1]
+    rsk = lo.ring_switch_key_gen(small, sk, torch.from_numpy(s_small),
+                                 torch.from_numpy(ka.view(np.int64)).cuda(), torch.from_numpy(ke))
+    galois = small.plan_galois(splan)
+    ssk = small.secret_prepare(torch.from_numpy(s_small))
+    keys = small._u64(len(galois) * small.key_elems)
+    kv = keys.view(len(galois), -1)
+    kr = W.rotation_key_randomness(small.moduli, small.N, small.ndigits, galois, seed, stream=13)
+    for i, k in enumerate(galois):
+        a, e = kr[k]
+        small.rotkey_gen(ssk, k, torch.from_numpy(a.view(np.int64)).cuda(),
+                         torch.from_numpy(e).cuda(), out=kv[i])
+    db = lo.db_encode(torch.from_numpy(q.db.astype(np.int32)).cuda())
+    consts = small.plan_constants(splan)
+    lib = pdq.load()
+    sw = lo._u64(bplan.J * lo.ct_elems)
+    sws = ctx._ws(lib.pdq_mod_switch_workspace_bytes(ctx.h, bplan.J))
+    masked = lo._u64(4 * bplan.J * lo.ct_elems)
+    R = lo.N // small.N
+    ms = small._u64(4 * bplan.J * R * small.ct_elems)
+    rws = lo._ws(lib.pdq_ring_switch_workspace_bytes(lo.h, 4 * bplan.J))
+    cws = small.comp_workspace(splan)
+    out = small._u64(splan.n_out * small.ct_elems)
+    out1 = one._u64(splan.n_out * one.ct_elems)
+    ws1 = small._ws(lib.pdq_mod_switch_workspace_bytes(small.h, splan.n_out))
+    torch.cuda.synchronize()
+    ev = {}
+
+    def step(mark=False):
+        def rec(name):
+            if mark:
+                ev.setdefault(name, []).append(torch.cuda.Event(enable_timing=True))
+                ev[name][-1].record(stream)
+        rec("start")
+        ctx.mod_switch(lo, v_cts, out=sw, ws=sws, stream=stream)
+        rec("mod_switch")
+        lo.mask(bplan, sw, db, out=masked, stream=stream)
+        rec("mask")
+        lo.ring_switch(small, masked, rsk, group=4, out=ms, ws=rws, stream=stream)
+        rec("ring_switch")
+        small.comp(splan, ms, keys, galois, consts, ws=cws, out=out, stream=stream)
+        rec("comp")
+        small.mod_switch(one, out, out=out1, ws=ws1, stream=stream)
+        rec("answer_mod_switch")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    truth = [(int(i), int(q.db[i])) for i in q.positions]
+    ok = small.decomp(splan, small.decrypt(ssk, out).cpu().numpy()) == truth
+    ssk1 = one.secret_prepare(torch.from_numpy(s_small))
+    ok = ok and one.decomp(splan, one.decrypt(ssk1, out1).cpu().numpy()) == truth
+    launches0 = pdq.pdq_launch_count()
+    for _ in range(args.steps):
+        step(mark=True)
+    torch.cuda.synchronize()
+    launches = pdq.pdq_launch_count() - launches0
+    names = ["mod_switch", "mask", "ring_switch", "comp", "answer_mod_switch"]
+    stages = {}
+    prev = "start"
+    for nm in names:
+        stages[nm] = sum(a.elapsed_time(b) for a, b in zip(ev[prev], ev[nm])) / args.steps
+        prev = nm
+    per = [a.elapsed_time(b) for a, b in zip(ev["start"], ev["answer_mod_switch"])]
+    total = sum(per)
+    return {"value": args.steps / (total / 1000.0), "unit": "queries/s",
+            "ms_per_query": total / args.steps, "p50_ms": statistics.median(per),
+            "stages_ms_per_query": stages, "ring_ratio": R, "small_N": small.N,
+            "comp_primes": L2, "special_primes": lcfg.K, "dnum": lcfg.dnum,
+            "plan": {k: getattr(splan, k) for k in ("B", "giants", "J", "H", "G", "n_out")},
+            "answer_bytes_u64": splan.n_out * one.ct_elems * 8,
+            "answer_bytes_packed_60bit": splan.n_out * 2 * one.N * 60 // 8,
+            "rotation_keys_mib": keys.numel() * 8 / 2**20,
+            "gpu_launches_per_step": int(launches) / args.steps,
+            "all_decompress_exactly": bool(ok),
+            "what": (f"the query over {cfg.L} primes switched to {L2} (pdq_mod_switch), Mask in "
+                     f"the ring 2^{cfg.log_n} (pdq_mask), every masked ciphertext ring-switched to "
+                     f"{R} ciphertexts of the ring 2^{ls} (pdq_ring_switch), Comp there "
+                     f"(pdq_comp, switched plan), the answer switched to one prime; one step = "
+                     f"all of these")}
+
+
 # The paper's Table II (n = 16384, s = 8..128) and Table III (s = 16,
 # n = 2^13..2^17) shapes: ring 2^13, t = 65537, two 54-bit ciphertext primes;
 # its Comp times (single-thread Xeon Silver 4114, seconds) for context.
@@ -744,6 +852,8 @@ def run_gpu(args, cfg, rank: int, world: int):
             "rows": run_paper_shapes(args, rank)}
     if args.switch_L and 0 < args.switch_L < cfg.L:
         line["switched"] = run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank)
+        if args.ring_log_n and args.ring_log_n < cfg.log_n:
+            line["ring_switched"] = run_ring_switched(args, cfg, ctx, plan, q, v_cts, stream, rank)
     if args.mix > 0:
         del v_cts, keys, db, consts, out
         torch.cuda.empty_cache()

@@ -98,6 +98,8 @@ typedef struct {
     uint32_t hclass;     /* distinct diagonal sets = min(hpg, H) */
     uint32_t per_out;    /* groups per output ciphertext = m/s' */
     uint32_t n_out;      /* output ciphertexts */
+    uint32_t ring_ratio; /* 1; R = N_big/N for Comp in a subring after ring
+                            switching (pdq_plan_make_switched) */
 } pdq_plan;
 
 /* ---------------------------------------------------------------- context */
@@ -196,6 +198,40 @@ size_t pdq_mod_switch_workspace_bytes(const pdq_ctx* from, uint32_t count);
 int pdq_mod_switch(const pdq_ctx* from, const pdq_ctx* to, const uint64_t* cts, uint32_t count,
                    uint64_t* out, void* ws, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------- ring switching
+ * Comp needs one multiplicative level, so the paper switches the query to a
+ * ring of smaller dimension after Match and Mask (Sec. 5.3, the ring-switching
+ * technique of Gentry, Halevi, Peikert and Smart): Comp is cheaper there and
+ * the answer shorter.  A big-ring ciphertext under s is key-switched to the
+ * subring secret s'(X) = s_small(X^R), R = N_big/N_small, then split by
+ * coefficient index mod R into R subring ciphertexts over the same primes:
+ * part r decrypts under s_small to m_r, where the plaintext is
+ * m(X) = sum_r X^r m_r(X^R).
+ * pdq_ctx_create_subring: the context of the subring of dimension 2^log_n
+ *   (3 <= log_n < the parent's) with the parent's t, primes and digits.
+ *   Synchronous; released with pdq_ctx_destroy.
+ * pdq_ring_switch_key_gen (client): the key from s (sk: big-ring
+ *   pdq_secret_prepare form) to s_small(X^R) (s_small: dev [N_small] int8
+ *   ternary), b = -a s' + e + [q_i in digit] P s per digit; a: dev
+ *   [ndigits][L+K][N_big] uniform coefficient form, e: dev [ndigits][N_big];
+ *   key_out: dev [ndigits][2][L+K][N_big] NTT form.  Allocates temporaries.
+ * pdq_ring_switch: cts dev [count][2][L][N_big] (NTT form, unchanged); part r
+ *   of ciphertext i is written (NTT form of the subring) to out at index
+ *   (i / group) group R + r group + i mod group, each [2][L][N_small]: group 1
+ *   gives [count][R], group 4 turns pdq_mask's output ([J][4]) into a valid
+ *   pdq_comp input of the subring ([R J][4]; a subring row folds only slots
+ *   of the same big row, so the row masks carry over).  count must be a
+ *   multiple of group.  Workspace: pdq_ring_switch_workspace_bytes(big, count)
+ *   (dev), else PDQ_E_NOMEM.  PDQ_E_PARAM if small is not a subring of big. */
+int pdq_ctx_create_subring(const pdq_ctx* big, uint32_t log_n, pdq_ctx** out);
+int pdq_ring_switch_key_gen(const pdq_ctx* big, const pdq_ctx* small, const uint64_t* sk,
+                            const int8_t* s_small, const uint64_t* a, const int32_t* e,
+                            uint64_t* key_out, void* stream);
+size_t pdq_ring_switch_workspace_bytes(const pdq_ctx* big, uint32_t count);
+int pdq_ring_switch(const pdq_ctx* big, const pdq_ctx* small, const uint64_t* cts, uint32_t count,
+                    uint32_t group, const uint64_t* key, uint64_t* out, void* ws, size_t ws_bytes,
+                    void* stream);
+
 /* ----------------------------------------------------------------- plans
  * Fill the layout for n records and sparsity s (s' = 2^ceil(log2 s), the
  * Pegasus baby-step/giant-step split k = gB + a of Sec. 5.2).  B = 0 picks
@@ -205,6 +241,19 @@ int pdq_mod_switch(const pdq_ctx* from, const pdq_ctx* to, const uint64_t* cts, 
  * measured costs), ties to the smaller B.  Errors: PDQ_E_PARAM if s' > N/2,
  * s' >= t, B does not divide s', B > 128 or s'/B > 32. */
 int pdq_plan_make(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B, pdq_plan* plan);
+
+/* The plan of Comp in the subring `small` on a query ring-switched from the
+ * ring of dimension 2^big_log_n (Sec. 5.3): J = R ceil(n / N_big) subring
+ * ciphertexts (part r of big ciphertext j at R j + r, as pdq_ring_switch
+ * writes them with group 4 after pdq_mask), the big ring's record groups
+ * (G_sz = N_big floor((t-1)/N_big)), the slot layout of the subring, and
+ * ring_ratio = R.  pdq_plan_constants_build then makes the diagonals that
+ * undo the slot fold of the split, so the answer holds the same power sums
+ * of Eq. 1 as pdq_answer's and pdq_decomp (with this plan and the subring
+ * context) recovers the matches.  Errors as pdq_plan_make, and PDQ_E_PARAM
+ * unless N < 2^big_log_n <= 2^16 and t = 1 mod 2^(big_log_n+1). */
+int pdq_plan_make_switched(const pdq_ctx* small, uint32_t big_log_n, uint64_t n, uint32_t s,
+                           uint32_t B, pdq_plan* plan);
 
 /* The Galois elements of every rotation the plan uses, ascending (host
  * out[cap]); *count receives how many there are (PDQ_E_NOMEM if cap is

@@ -35,6 +35,21 @@ u32 ceil_log2(u64 x) {
     return r;
 }
 
+// the power of two minimising the work of the baby/giant split:
+// H (B-1) hoisted baby rotations, G (s'/B - 1) giant-step key switches and
+// G s'/B accumulator ModDowns, weighted 1 : 8 : 3
+u32 default_baby_steps(u64 H, u64 G, u64 sp) {
+    u64 best = ~0ull;
+    u32 B = 1;
+    for (u64 b = 1; b <= sp && b <= 128; b *= 2) {
+        const u64 gi = sp / b;
+        if (gi > 32) continue;
+        const u64 cost = H * (b - 1) + 8 * G * (gi - 1) + 3 * G * gi;
+        if (cost < best) { best = cost; B = (u32)b; }
+    }
+    return B;
+}
+
 int plan_make(const Ctx& c, u64 n, u32 s, u32 B, pdq_plan* pl) {
     if (n == 0 || s == 0) return fail(PDQ_E_PARAM, "plan: n and s must be positive");
     std::memset(pl, 0, sizeof(*pl));
@@ -46,18 +61,7 @@ int plan_make(const Ctx& c, u64 n, u32 s, u32 B, pdq_plan* pl) {
     const u64 hpg = G_sz / c.m;
     const u64 H = 2 * J;
     const u64 G = (H + hpg - 1) / hpg;
-    if (B == 0) {
-        // the power of two minimising the work of the baby/giant split:
-        // H (B-1) hoisted baby rotations, G (s'/B - 1) giant-step key
-        // switches and G s'/B accumulator ModDowns, weighted 1 : 8 : 3
-        u64 best = ~0ull;
-        for (u64 b = 1; b <= sp && b <= 128; b *= 2) {
-            const u64 gi = sp / b;
-            if (gi > 32) continue;
-            const u64 cost = H * (b - 1) + 8 * G * (gi - 1) + 3 * G * gi;
-            if (cost < best) { best = cost; B = (u32)b; }
-        }
-    }
+    if (B == 0) B = default_baby_steps(H, G, sp);
     if (sp % B != 0 || B > 128) return fail(PDQ_E_PARAM, "plan: B must divide s' and be at most 128");
     const u64 per_out = c.m / sp;
     pl->n = n;
@@ -73,9 +77,53 @@ int plan_make(const Ctx& c, u64 n, u32 s, u32 B, pdq_plan* pl) {
     pl->hclass = (u32)std::min(hpg, H);
     pl->per_out = (u32)per_out;
     pl->n_out = (u32)((G + per_out - 1) / per_out);
+    pl->ring_ratio = 1;
     if (pl->giants > 32) return fail(PDQ_E_PARAM, "plan: at most 32 giant steps (choose a larger B)");
     return PDQ_OK;
 }
+
+}  // namespace
+
+// Comp in the subring c (dimension N) of a ring of dimension Nbig = 2^big_log_n
+// after ring switching (Sec. 5.3): big ciphertext j becomes R = Nbig/N small
+// ciphertexts R j + r, and the records keep the big ring's groups of
+// G_sz = Nbig floor((t-1)/Nbig) records, i.e. G_sz/m small half-blocks each.
+int plan_make_switched(const Ctx& c, u32 big_log_n, u64 n, u32 s, u32 B, pdq_plan* pl) {
+    if (big_log_n <= c.log_n || big_log_n > 16) return fail(PDQ_E_PARAM, "plan: the big ring must be larger (at most 2^16)");
+    const u64 Nbig = 1ull << big_log_n, R = Nbig / c.N;
+    if ((c.t - 1) % (2 * Nbig) != 0) return fail(PDQ_E_PARAM, "plan: t must be 1 mod 2 N_big");
+    if (n == 0 || s == 0) return fail(PDQ_E_PARAM, "plan: n and s must be positive");
+    std::memset(pl, 0, sizeof(*pl));
+    const u64 sp = 1ull << ceil_log2(s);
+    if (sp > c.m || sp >= c.t) return fail(PDQ_E_PARAM, "plan: sparsity too large for the ring");
+    const u64 J = R * ((n + Nbig - 1) / Nbig);
+    if (J > (1u << 20)) return fail(PDQ_E_PARAM, "plan: too many records");
+    const u64 G_sz = Nbig * ((c.t - 1) / Nbig);
+    const u64 hpg = G_sz / c.m;
+    const u64 H = 2 * J;
+    const u64 G = (H + hpg - 1) / hpg;
+    if (B == 0) B = default_baby_steps(H, G, sp);
+    if (sp % B != 0 || B > 128) return fail(PDQ_E_PARAM, "plan: B must divide s' and be at most 128");
+    const u64 per_out = c.m / sp;
+    pl->n = n;
+    pl->s = s;
+    pl->s_prime = (u32)sp;
+    pl->B = B;
+    pl->giants = (u32)(sp / B);
+    pl->J = (u32)J;
+    pl->H = (u32)H;
+    pl->G_sz = (u32)G_sz;
+    pl->hpg = (u32)hpg;
+    pl->G = (u32)G;
+    pl->hclass = (u32)std::min(hpg, H);
+    pl->per_out = (u32)per_out;
+    pl->n_out = (u32)((G + per_out - 1) / per_out);
+    pl->ring_ratio = (u32)R;
+    if (pl->giants > 32) return fail(PDQ_E_PARAM, "plan: at most 32 giant steps (choose a larger B)");
+    return PDQ_OK;
+}
+
+namespace {
 
 u64 galois_rot(const Ctx& c, long long r) {
     const long long m = c.m;
@@ -114,12 +162,24 @@ std::vector<u64> plan_galois(const Ctx& c, const pdq_plan& pl) {
     return ks;
 }
 
+}  // namespace
+
 bool valid_plan(const Ctx& c, const pdq_plan* pl) {
     if (!pl) return false;
     pdq_plan chk;
-    if (plan_make(c, pl->n, pl->s, pl->B, &chk) != PDQ_OK) return false;
+    int rc;
+    if (pl->ring_ratio > 1) {
+        const u32 R = pl->ring_ratio;
+        if ((R & (R - 1)) != 0 || R > (1u << 13)) return false;
+        rc = plan_make_switched(c, c.log_n + log2_exact(R), pl->n, pl->s, pl->B, &chk);
+    } else {
+        rc = plan_make(c, pl->n, pl->s, pl->B, &chk);
+    }
+    if (rc != PDQ_OK) return false;
     return std::memcmp(&chk, pl, sizeof(chk)) == 0;
 }
+
+namespace {
 
 struct Keys {
     const u64* base;
@@ -151,7 +211,9 @@ struct CompLayout {
 CompLayout comp_layout(const Ctx& c, const pdq_plan& pl) {
     const u64 cts = ct_elems(c), ects = 2ull * (c.L + c.K) * c.N;
     const u64 G = pl.G, GI = pl.giants;
-    const u32 cnt = std::max(pl.H, pl.G);
+    // raises: every u_h (baby steps), every lowered accumulator at once
+    // (giant steps), every y (rotate-and-sum levels)
+    const u32 cnt = std::max({pl.H, pl.G, pl.G * (pl.giants - 1)});
     const u64 scratch = std::max({apply_ws(c, cnt), mod_down_ws(c, pl.G),
                                   mod_down_polys_ws(c, std::max(1u, pl.G * (pl.giants - 1))),
                                   mod_down_polys_ws(c, pl.G)}) / sizeof(u64);
@@ -265,16 +327,26 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     const u64 EN = (u64)(c.L + c.K) * c.N, LN = (u64)c.L * c.N;
     if (GI > 1) PDQ_TRY(mod_down_polys(c, accx + EN, 2 * EN, G * (GI - 1), acc, LN, aws, st));
     // 4. giant steps: Rot(acc_g; gB) = (sigma(c0) + A0, A1) over Q u P, the
-    // key switch raising the lowered c1, summed into yx
+    // key switch raising the lowered c1, summed into yx.  The lowered c1 of
+    // every (g, gamma) are raised in one call, ordered g-major, so that the
+    // digits of giant step g are the contiguous run g - 1 of G ciphertexts.
     prof_mark(c, PDQ_STAGE_GIANT, st);
+    if (GI > 1) {
+        CtSet c1all;
+        c1all.base = acc;
+        c1all.outer = (long long)LN;                  // g
+        c1all.per = G;
+        c1all.inner = (long long)(GI - 1) * LN;       // gamma
+        PDQ_TRY(ks_raise(c, c1all, G * (GI - 1), rws, &D, st, 0));
+    }
+    const u64 dstride = (u64)c.ndigits * (c.L + c.K) * c.N;
     for (u32 g = 1; g < GI; ++g) {
         const u64 k = galois_rot(c, (long long)g * B);
         const u64* kp;
         PDQ_TRY(key_for(k, &kp));
-        const CtSet c1s = ct_set(acc + (u64)(g - 1) * LN, (long long)(GI - 1) * LN);
         const CtSet c0s = ct_set(accx + (u64)(g - 1) * ects, (long long)(GI - 1) * ects);
-        PDQ_TRY(ks_raise(c, c1s, G, rws, &D, st, 0));
-        PDQ_TRY(ks_apply_ext(c, D, c0s, G, (u32)k, kp, ct_set(yx, ects), true, false, st, true));
+        PDQ_TRY(ks_apply_ext(c, D + (u64)(g - 1) * G * dstride, c0s, G, (u32)k, kp,
+                             ct_set(yx, ects), true, false, st, true));
     }
     // 5. rotate-and-sum on y over Q u P: per level the lowered c1 of every y
     // (into Y1) is raised once, the r rotations (a = 0: y itself) go to Rx and

@@ -171,7 +171,9 @@ static void free_ctx(Ctx* c) {
 int encode_slots(const Ctx& c, const u32* slots, u32 count, u32 nlimbs, u64* out,
                  cudaStream_t st);  // ops.cu
 
-static int build_ctx(const pdq_params& p, Ctx* c) {
+// chain (optional): the K special primes, then the L ciphertext primes, to
+// use instead of the search (a subring shares its parent's primes)
+static int build_ctx(const pdq_params& p, Ctx* c, const std::vector<u64>* given = nullptr) {
     if (p.log_n < 3 || p.log_n > 16) return fail(PDQ_E_PARAM, "log_n must be in [3, 16]");
     if (p.prime_bits < 20 || p.prime_bits > 60) return fail(PDQ_E_PARAM, "prime_bits must be in [20, 60]");
     if (p.L < 1 || p.L > 30 || p.K < 1 || p.K > 8) return fail(PDQ_E_PARAM, "need 1 <= L <= 30, 1 <= K <= 8");
@@ -190,6 +192,13 @@ static int build_ctx(const pdq_params& p, Ctx* c) {
 
     // prime chain: descending candidates = 1 mod 2N below 2^bits
     std::vector<u64> chain;
+    if (given) {
+        chain = *given;
+        if (chain.size() != p.K + p.L) return fail(PDQ_E_PARAM, "prime chain of the wrong length");
+        for (u64 q : chain)
+            if ((q - 1) % twoN != 0 || !host_is_prime(q) || q >= (1ull << p.prime_bits))
+                return fail(PDQ_E_PARAM, "prime chain: every prime must be = 1 mod 2N");
+    }
     u64 cand = ((1ull << p.prime_bits) - 2) / twoN * twoN + 1;
     while (chain.size() < p.K + p.L) {
         if (cand <= twoN) return fail(PDQ_E_PARAM, "not enough NTT-friendly primes");
@@ -228,6 +237,7 @@ static int build_ctx(const pdq_params& p, Ctx* c) {
             if (ok) g = x;
         }
     }
+    c->gen = g;
     c->zeta = host_powmod(g, (p.t - 1) / twoN, p.t);
 
     // twiddles
@@ -473,6 +483,34 @@ int pdq_ctx_create(const pdq_params* params, pdq_ctx** out) {
     *out = nullptr;
     Ctx* c = new Ctx();
     int rc = build_ctx(*params, c);
+    if (rc != PDQ_OK) {
+        std::string msg = g_last_error;
+        free_ctx(c);
+        set_error(msg);
+        return rc;
+    }
+    *out = reinterpret_cast<pdq_ctx*>(c);
+    return PDQ_OK;
+}
+
+int pdq_ctx_create_subring(const pdq_ctx* big, uint32_t log_n, pdq_ctx** out) {
+    if (!big || !out) return fail(PDQ_E_PARAM, "null argument");
+    *out = nullptr;
+    const Ctx& b = *reinterpret_cast<const Ctx*>(big);
+    if (log_n < 3 || log_n >= b.log_n) return fail(PDQ_E_PARAM, "subring: need 3 <= log_n < the parent's");
+    pdq_params p{};
+    p.log_n = log_n;
+    p.prime_bits = b.bits;
+    p.L = b.L;
+    p.K = b.K;
+    p.dnum = b.dnum;
+    p.t = b.t;
+    std::vector<u64> chain;
+    for (u32 k = 0; k < b.K; ++k) chain.push_back(b.mods[b.L + k]);
+    for (u32 i = 0; i < b.L; ++i) chain.push_back(b.mods[i]);
+    Ctx* c = new Ctx();
+    int rc = build_ctx(p, c, &chain);
+    if (rc == PDQ_OK && c->ndigits != b.ndigits) rc = fail(PDQ_E_PARAM, "subring: digit layout differs");
     if (rc != PDQ_OK) {
         std::string msg = g_last_error;
         free_ctx(c);

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "pdq_internal.h"
+#include "pdq_ops.h"
 
 namespace pdq {
 namespace {
@@ -133,10 +134,7 @@ extern "C" int pdq_decomp(const pdq_ctx* ctx, const pdq_plan* plan, const uint32
                           uint64_t* idx_out, uint32_t* val_out, uint64_t cap, uint64_t* count) {
     if (!ctx || !plan || !slots || !count) return fail(PDQ_E_PARAM, "decomp: null argument");
     const Ctx& c = *reinterpret_cast<const Ctx*>(ctx);
-    pdq_plan chk;
-    if (pdq_plan_make(ctx, plan->n, plan->s, plan->B, &chk) != PDQ_OK ||
-        std::memcmp(&chk, plan, sizeof(chk)) != 0)
-        return fail(PDQ_E_PARAM, "decomp: invalid plan");
+    if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "decomp: invalid plan");
     const Zt z{c.t};
     const u32 sp = plan->s_prime;
     u64 total = 0;

@@ -108,6 +108,52 @@ __global__ void k_diag_slots(u64* __restrict__ out, u32 giants, u32 B, u32 s_pri
     out[(((u64)blockIdx.y * L) << logN) + pos[idx]] = r;
 }
 
+// Diagonals of Comp in a subring after ring switching (ring ratio R): the
+// block of half-block class cls = 2(R jj + r) + rho (part r of the jj-th big
+// ciphertext of a group, row rho) is M[kk][c'] = W_{kk+1}[r][e'], with small
+// slot exponent e' = (-1)^rho 3^c' mod 2N, e_u = e' + 2N u (u < R) and
+// W_kk = sum_u alpha(jj Nbig + slot_of[e_u])^kk zeta_big^(e_u r): the power
+// sums of Eq. 1 over the big ring's records, read through the fold
+// m(zeta^e_u) = sum_r zeta^(e_u r) m_r(zeta'^e') of the split.
+// slot_of[e]: big slot index of odd exponent e; zpow[i] = zeta_big^i mod t.
+__global__ void k_diag_slots_sw(u64* __restrict__ out, u32 giants, u32 B, u32 s_prime, u32 logN,
+                                u32 L, const u32* __restrict__ pos, u64 t, u32 pt_base,
+                                u32 pt_stride, u32 R, const u32* __restrict__ slot_of,
+                                const u32* __restrict__ zpow) {
+    const u32 idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 N = 1u << logN, m = N / 2;
+    if (idx >= N) return;
+    const u32 pt = pt_base + blockIdx.y * pt_stride;
+    const u32 a = pt % B;
+    const u32 g = (pt / B) % giants;
+    const u32 cls = pt / (B * giants);
+    const u32 col = idx & (m - 1);
+    const u32 k = g * B + a;
+    const u32 cp = (col + m - (g * B) % m) & (m - 1);        // Rot(.; -gB)
+    const u32 cc = (cp + k) & (m - 1);
+    const u32 kk = (cp & (s_prime - 1)) + 1;
+    const u32 rho = cls & 1, i = cls >> 1, r = i % R, jj = i / R;
+    const u64 twoN = 2ull * N, Nbig = (u64)N * R, twoNbig = 2 * Nbig;
+    u64 e = 1, b3 = 3;
+    for (u32 x = cc; x; x >>= 1) {
+        if (x & 1) e = e * b3 % twoN;
+        b3 = b3 * b3 % twoN;
+    }
+    if (rho) e = twoN - e;
+    u64 acc = 0;
+    for (u32 u = 0; u < R; ++u) {
+        const u64 eu = e + twoN * u;
+        const u64 node = ((u64)jj * Nbig + slot_of[eu] + 1) % t;
+        u64 p = 1, bb = node;
+        for (u32 x = kk; x; x >>= 1) {
+            if (x & 1) p = p * bb % t;
+            bb = bb * bb % t;
+        }
+        acc += p * zpow[(eu * r) % twoNbig] % t;
+    }
+    out[(((u64)blockIdx.y * L) << logN) + pos[idx]] = acc % t;
+}
+
 // database plaintexts: row pt = 2j + half holds DB_j.[1;0] (half 0) or DB_j.[0;1]
 __global__ void k_db_slots(u64* __restrict__ out, const u32* __restrict__ values, u64 n, u32 logN,
                            u32 L, const u32* __restrict__ pos, u64 t) {
@@ -194,8 +240,11 @@ __global__ void k_enc_finish(u64* __restrict__ ct, const u64* __restrict__ sk, u
     c0[r] = submod(c0[r], as, md.q);
 }
 
-// key: b = b(e) - a*s + [l in digit] P sigma_k(s), all NTT form
-__global__ void k_key_finish(u64* __restrict__ key, const u64* __restrict__ sk, u32 E, u32 logN,
+// key: b = b(e) - a*s_to + [l in digit] P sigma_k(s_from), all NTT form
+// (a rotation key: s_to = s_from = s; a ring-switching key: k = 1, s_from = s,
+// s_to the subring's secret embedded)
+__global__ void k_key_finish(u64* __restrict__ key, const u64* __restrict__ sk,
+                             const u64* __restrict__ sk_from, u32 E, u32 logN,
                              u32 galois, const Mod* __restrict__ mods,
                              const u64* __restrict__ Pmodq, DigitBounds db) {
     const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -207,7 +256,7 @@ __global__ void k_key_finish(u64* __restrict__ key, const u64* __restrict__ sk, 
     const u64 av = kb[((u64)E << logN) + r];
     u64 v = submod(kb[r], mulmod(av, sk[r], md), md.q);
     if (l >= db.lo[b] && l < db.hi[b]) {
-        const u64 sv = sk[((u64)l << logN) + auto_index(x, galois, logN)];
+        const u64 sv = sk_from[((u64)l << logN) + auto_index(x, galois, logN)];
         v = addmod(v, mulmod(sv, Pmodq[l], md), md.q);
     }
     kb[r] = v;
@@ -1146,18 +1195,53 @@ int build_diagonals(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st)
     const u32 GI = pl.giants, B = pl.B, E = c.L + c.K;
     PDQ_TRY(check_y(GI, "diagonals"));
     const u64 LN = (u64)E * c.N;
+    const u32 R = pl.ring_ratio;
     u64* tmp = nullptr;
-    if (cudaMallocAsync((void**)&tmp, (size_t)GI * LN * sizeof(u64), st) != cudaSuccess) {
+    u32* sw = nullptr;           // ring-switched plans: slot_of, then zpow ([2 Nbig] each)
+    const u64 twoNbig = 2ull * c.N * R;
+    if (cudaMallocAsync((void**)&tmp, (size_t)GI * LN * sizeof(u64), st) != cudaSuccess ||
+        (R > 1 && cudaMallocAsync((void**)&sw, 2 * twoNbig * sizeof(u32), st) != cudaSuccess)) {
         cudaGetLastError();
+        if (tmp) cudaFreeAsync(tmp, st);
         return fail(PDQ_E_NOMEM, "diagonals: temporary allocation failed");
+    }
+    if (R > 1) {
+        // the big ring's slot index per odd exponent and the powers of its slot root
+        std::vector<u32> tab(2 * twoNbig, 0);
+        const u64 mbig = twoNbig / 4;
+        u64 e = 1;
+        for (u64 col = 0; col < mbig; ++col) {
+            tab[e] = (u32)col;
+            tab[twoNbig - e] = (u32)(mbig + col);
+            e = e * 3 % twoNbig;
+        }
+        const u64 zb = host_powmod(c.gen, (c.t - 1) / twoNbig, c.t);
+        u64 z = 1;
+        for (u64 i = 0; i < twoNbig; ++i) {
+            tab[twoNbig + i] = (u32)z;
+            z = z * zb % c.t;
+        }
+        if (cudaMemcpyAsync(sw, tab.data(), tab.size() * sizeof(u32), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaFreeAsync(tmp, st);
+            cudaFreeAsync(sw, st);
+            return fail(PDQ_E_CUDA, "diagonals: table upload failed");
+        }
     }
     int rc = PDQ_OK;
     for (u32 cls = 0; cls < pl.hclass && rc == PDQ_OK; ++cls) {
         for (u32 a = 0; a < B && rc == PDQ_OK; ++a) {
-            k_diag_slots<<<grid2(c.N, GI), kBlock, 0, st>>>(tmp, GI, B, pl.s_prime, c.log_n, E,
-                                                            c.d_slot_pos, c.t, cls * GI * B + a,
-                                                            B);
-            rc = launched("k_diag_slots");
+            if (R > 1) {
+                k_diag_slots_sw<<<grid2(c.N, GI), kBlock, 0, st>>>(
+                    tmp, GI, B, pl.s_prime, c.log_n, E, c.d_slot_pos, c.t, cls * GI * B + a, B, R,
+                    sw, sw + twoNbig);
+                rc = launched("k_diag_slots_sw");
+            } else {
+                k_diag_slots<<<grid2(c.N, GI), kBlock, 0, st>>>(tmp, GI, B, pl.s_prime, c.log_n, E,
+                                                                c.d_slot_pos, c.t, cls * GI * B + a,
+                                                                B);
+                rc = launched("k_diag_slots");
+            }
             if (rc == PDQ_OK) rc = encode_finish(c, tmp, GI, E, st);
             if (rc == PDQ_OK) {
                 k_diag_layout<<<(u32)((LN + kBlock - 1) / kBlock), kBlock, 0, st>>>(
@@ -1167,6 +1251,7 @@ int build_diagonals(const Ctx& c, const pdq_plan& pl, u64* out, cudaStream_t st)
         }
     }
     cudaFreeAsync(tmp, st);
+    if (sw) cudaFreeAsync(sw, st);
     return rc;
 }
 
@@ -1236,6 +1321,61 @@ int gather_rows(CtSet src, long long src_off, u32 cnt, u64 len, u64* dst, u64 ds
 
 int rotkey_gen(const Ctx& c, const u64* sk, u64 galois, const u64* a, const int32_t* e, u64* key,
                cudaStream_t st) {
+    return keygen(c, sk, sk, galois, a, e, key, st);
+}
+
+// s'(X) = s_small(X^R): out[R i] = s_small[i], zero elsewhere
+__global__ void k_embed_secret(const int8_t* __restrict__ s_small, u32 R, u32 Nbig,
+                               int8_t* __restrict__ out) {
+    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= Nbig) return;
+    out[x] = (x % R == 0) ? s_small[x / R] : (int8_t)0;
+}
+
+int ring_switch_keygen(const Ctx& big, const u64* sk, const int8_t* s_small, u32 R, const u64* a,
+                       const int32_t* e, u64* key, cudaStream_t st) {
+    const u32 E = big.L + big.K;
+    int8_t* emb = nullptr;
+    u64* sk_to = nullptr;
+    if (cudaMallocAsync((void**)&emb, big.N, st) != cudaSuccess ||
+        cudaMallocAsync((void**)&sk_to, (size_t)E * big.N * sizeof(u64), st) != cudaSuccess) {
+        cudaGetLastError();
+        if (emb) cudaFreeAsync(emb, st);
+        return fail(PDQ_E_NOMEM, "ring_switch_keygen: temporary allocation failed");
+    }
+    k_embed_secret<<<(big.N + kBlock - 1) / kBlock, kBlock, 0, st>>>(s_small, R, big.N, emb);
+    int rc = launched("k_embed_secret");
+    if (rc == PDQ_OK) rc = secret_prepare(big, emb, sk_to, st);
+    if (rc == PDQ_OK) rc = keygen(big, sk_to, sk, 1, a, e, key, st);
+    cudaFreeAsync(sk_to, st);
+    cudaFreeAsync(emb, st);
+    return rc;
+}
+
+// small ciphertext (i / group) group R + r group + i mod group, polynomial p,
+// limb l, coefficient y = big ciphertext i, p, l, coefficient R y + r
+__global__ void k_ring_split(const u64* __restrict__ in, u32 R, u32 logNs, u32 L, u32 group,
+                             u64* __restrict__ out) {
+    const u64 Ns = 1ull << logNs, per = 2ull * L * Ns;
+    const u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= per) return;
+    const u32 i = blockIdx.y / R, r = blockIdx.y % R;
+    const u64 pl = idx >> logNs, y = idx & (Ns - 1);
+    const u64 o = (u64)(i / group) * group * R + (u64)r * group + i % group;
+    out[o * per + idx] = in[(u64)i * per * R + pl * Ns * R + y * R + r];
+}
+
+int ring_split(const Ctx& small, const u64* in, u32 count, u32 R, u32 group, u64* out,
+               cudaStream_t st) {
+    if (group == 0 || count % group != 0) return fail(PDQ_E_PARAM, "ring_split: count must be a multiple of group");
+    PDQ_TRY(check_y((u64)count * R, "ring_split"));
+    k_ring_split<<<grid2(2ull * small.L * small.N, count * R), kBlock, 0, st>>>(in, R, small.log_n,
+                                                                               small.L, group, out);
+    return launched("k_ring_split");
+}
+
+int keygen(const Ctx& c, const u64* sk, const u64* sk_from, u64 galois, const u64* a,
+           const int32_t* e, u64* key, cudaStream_t st) {
     const u32 E = c.L + c.K, nd = c.ndigits;
     const u64 EN = (u64)E * c.N;
     if (galois % 2 == 0 || galois >= 2ull * c.N) return fail(PDQ_E_PARAM, "galois element must be odd and < 2N");
@@ -1254,8 +1394,8 @@ int rotkey_gen(const Ctx& c, const u64* sk, u64 galois, const u64* a, const int3
         db.lo[b] = c.digit_limbs[b].front();
         db.hi[b] = c.digit_limbs[b].back() + 1;
     }
-    k_key_finish<<<grid2(EN, nd), kBlock, 0, st>>>(key, sk, E, c.log_n, (u32)galois, c.d_mods,
-                                                   c.d_P_mod_q, db);
+    k_key_finish<<<grid2(EN, nd), kBlock, 0, st>>>(key, sk, sk_from, E, c.log_n, (u32)galois,
+                                                   c.d_mods, c.d_P_mod_q, db);
     return launched("k_key_finish");
 }
 

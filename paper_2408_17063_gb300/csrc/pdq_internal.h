@@ -115,7 +115,8 @@ struct Ctx {
     u32 nmod = 0;                 // L + K + 1 (the last is t)
     std::vector<u64> mods;        // q_0..q_{L-1}, p_0..p_{K-1}, t
     std::vector<Mod> hmods;
-    u64 zeta = 0;                 // slot root mod t
+    u64 gen = 0;                  // smallest generator of Z_t^*
+    u64 zeta = 0;                 // slot root mod t, gen^((t-1)/2N)
     std::vector<u64> psi;         // transform root per modulus
     // device tables, each [nmod][N] unless noted
     Mod* d_mods = nullptr;        // [nmod]

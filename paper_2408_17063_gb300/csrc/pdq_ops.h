@@ -47,6 +47,16 @@ int encrypt(const Ctx& c, const u64* sk, const u32* slots, u32 count, const u64*
             const int32_t* e, u64* ct, cudaStream_t st);
 int rotkey_gen(const Ctx& c, const u64* sk, u64 galois, const u64* a, const int32_t* e, u64* key,
                cudaStream_t st);
+// key-switching key from sigma_galois(s_from) to s (rotation keys: s_from = s)
+int keygen(const Ctx& c, const u64* sk, const u64* sk_from, u64 galois, const u64* a,
+           const int32_t* e, u64* key, cudaStream_t st);
+// key-switching key from s (big's ring) to s_small(X^R) (ring switching)
+int ring_switch_keygen(const Ctx& big, const u64* sk, const int8_t* s_small, u32 R, const u64* a,
+                       const int32_t* e, u64* key, cudaStream_t st);
+// part r of coefficient-form ciphertext i (big ring, [2][L][R N']) into
+// out at index (i / group) group R + r group + i mod group ([2][L][N'])
+int ring_split(const Ctx& small, const u64* in, u32 count, u32 R, u32 group, u64* out,
+               cudaStream_t st);
 size_t decrypt_ws(const Ctx& c, u32 count);
 int decrypt(const Ctx& c, const u64* sk, const u64* ct, u32 count, u32* slots, u64* ws,
             cudaStream_t st);
@@ -60,6 +70,15 @@ int mask_literal(const Ctx& c, u32 J, const u64* v, const u64* dbp, u64* out, cu
 // ciphertexts (u [2J][2][L][N])
 int mask_pack(const Ctx& c, u32 J, const u64* v, const u64* w, const u64* db, u64* u,
               cudaStream_t st);
+
+// plans: valid_plan recomputes a plan (either kind) and compares it
+bool valid_plan(const Ctx& c, const pdq_plan* pl);
+int plan_make_switched(const Ctx& c, u32 big_log_n, u64 n, u32 s, u32 B, pdq_plan* pl);
+inline u32 log2_exact(u32 x) {
+    u32 r = 0;
+    while ((1u << r) < x) ++r;
+    return r;
+}
 
 // Hybrid key switching, split so that the raised digits of c1 can be shared
 // by every rotation of the same ciphertexts (hoisting):

@@ -48,7 +48,7 @@ class Info(ctypes.Structure):
 class Plan(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64)] + [(f, ctypes.c_uint32) for f in (
         "s", "s_prime", "B", "giants", "J", "H", "G_sz", "hpg", "G", "hclass", "per_out",
-        "n_out")]
+        "n_out", "ring_ratio")]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -91,6 +91,11 @@ _SIGS = {
     "pdq_rotate_workspace_bytes": (_SZ, [_P, _U32]),
     "pdq_rotate": (_I, [_P, _P, _U32, _U64, _P, _P, _P, _SZ, _P]),
     "pdq_plan_make": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
+    "pdq_plan_make_switched": (_I, [_P, _U32, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
+    "pdq_ctx_create_subring": (_I, [_P, _U32, ctypes.POINTER(_P)]),
+    "pdq_ring_switch_key_gen": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "pdq_ring_switch_workspace_bytes": (_SZ, [_P, _U32]),
+    "pdq_ring_switch": (_I, [_P, _P, _P, _U32, _U32, _P, _P, _P, _SZ, _P]),
     "pdq_plan_galois": (_I, [_P, ctypes.POINTER(Plan), _P, _U32, ctypes.POINTER(_U32)]),
     "pdq_plan_constants_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
     "pdq_plan_constants_build": (_I, [_P, ctypes.POINTER(Plan), _P, _P]),
@@ -188,11 +193,15 @@ def _stream(stream) -> int:
 class Context:
     """A parameter set on the current CUDA device (owns a pdq_ctx)."""
 
-    def __init__(self, log_n: int, t: int, prime_bits: int, L: int, K: int, dnum: int):
+    def __init__(self, log_n: int, t: int, prime_bits: int, L: int, K: int, dnum: int,
+                 _handle=None):
         lib = load()
-        p = Params(log_n, prime_bits, L, K, dnum, 0, t)
-        h = _P()
-        _check(lib.pdq_ctx_create(ctypes.byref(p), ctypes.byref(h)))
+        if _handle is None:
+            p = Params(log_n, prime_bits, L, K, dnum, 0, t)
+            h = _P()
+            _check(lib.pdq_ctx_create(ctypes.byref(p), ctypes.byref(h)))
+        else:
+            h = _handle
         self.h = h
         info = Info()
         _check(lib.pdq_ctx_info(h, ctypes.byref(info)))
@@ -207,6 +216,45 @@ class Context:
     @classmethod
     def from_config(cls, cfg) -> "Context":
         return cls(cfg.log_n, cfg.t, cfg.prime_bits, cfg.L, cfg.K, cfg.dnum)
+
+    def subring(self, log_n: int) -> "Context":
+        """pdq_ctx_create_subring: the subring of dimension 2^log_n on this
+        context's primes (ring switching)."""
+        h = _P()
+        _check(load().pdq_ctx_create_subring(self.h, log_n, ctypes.byref(h)))
+        return Context(log_n, self.t, 0, self.L, self.K, 0, _handle=h)
+
+    def plan_switched(self, big_log_n: int, n: int, s: int, B: int = 0) -> Plan:
+        """pdq_plan_make_switched: Comp in this subring on a query switched
+        from the ring of dimension 2^big_log_n."""
+        pl = Plan()
+        _check(load().pdq_plan_make_switched(self.h, big_log_n, n, s, B, ctypes.byref(pl)))
+        return pl
+
+    def ring_switch_key_gen(self, small: "Context", sk, s_small, a, e, stream=None) -> torch.Tensor:
+        """pdq_ring_switch_key_gen: key from this ring's s to s_small(X^R)."""
+        s_small = s_small.to(device="cuda", dtype=torch.int8).contiguous()
+        a = a.to(device="cuda").contiguous()
+        e = e.to(device="cuda", dtype=torch.int32).contiguous()
+        out = self._u64(self.key_elems)
+        _check(load().pdq_ring_switch_key_gen(self.h, small.h, _ptr(sk), _ptr(s_small), _ptr(a),
+                                              _ptr(e), _ptr(out), _stream(stream)))
+        return out.view(self.ndigits, 2, self.E, self.N)
+
+    def ring_switch(self, small: "Context", cts, key, group: int = 1, out=None, ws=None,
+                    stream=None) -> torch.Tensor:
+        """pdq_ring_switch: count ciphertexts of this ring -> R count of the
+        subring (part r of ciphertext i at (i/group) group R + r group + i%group)."""
+        count = cts.numel() // self.ct_elems
+        R = self.N // small.N
+        lib = load()
+        if ws is None:
+            ws = self._ws(lib.pdq_ring_switch_workspace_bytes(self.h, count))
+        if out is None:
+            out = small._u64(count * R * small.ct_elems)
+        _check(lib.pdq_ring_switch(self.h, small.h, _ptr(cts), count, group, _ptr(key), _ptr(out),
+                                   _ptr(ws), ws.numel(), _stream(stream)))
+        return out.view(count * R, 2, small.L, small.N)
 
     def close(self):
         if getattr(self, "h", None):
@@ -421,8 +469,8 @@ class Context:
         return out.view(plan.J * 4, 2, self.L, self.N)
 
     # hot path
-    def mask(self, plan: Plan, v_cts, db, stream=None) -> torch.Tensor:
-        out = self._u64(plan.J * 4 * self.ct_elems)
+    def mask(self, plan: Plan, v_cts, db, out=None, stream=None) -> torch.Tensor:
+        out = self._u64(plan.J * 4 * self.ct_elems) if out is None else out
         _check(load().pdq_mask(self.h, ctypes.byref(plan), _ptr(v_cts), _ptr(db), _ptr(out),
                                _stream(stream)))
         return out.view(plan.J * 4, 2, self.L, self.N)
