@@ -542,6 +542,112 @@ def answer_ring_switched(big: Params, small: Params, v_cts, db, rs_key, keys,
                 lambda par, pl, h, k: switched_diagonal_slots(big, par, pl, h, k))
 
 
+# --------------------------------------------------- unencrypted database ---
+#
+# When the database is known in the clear, C (DB . v) = (C diag(DB)) v, so the
+# server can skip Mask and compress v alone with the stacked matrix
+# [C; C diag(DB)] (Sec. 5.2, remark on an unencrypted database).  Here index
+# ciphertext j holds half-block 2j in row 0 and 2j+1 in row 1, and two sets of
+# diagonals put C on one row and C diag(DB) on the other:
+#   set 0: row 0 = C on half-block 2j,        row 1 = C diag(DB) on 2j+1
+#   set 1: row 0 = C diag(DB) on half-block 2j, row 1 = C on 2j+1
+# so after the BSGS products, giant steps and rotate-and-sum set 0 holds
+# (C v_2j, C d_2j+1) and set 1 (C d_2j, C v_2j+1), and set 0 + Rot_col(set 1)
+# = (C v, C d).  Rot_col commutes with the row rotations, so it is folded into
+# the giant steps of set 1 (Galois element 3^(gB) (2N - 1), also for g = 0).
+
+def make_plan_plain_db(par: Params, n: int, s: int, B: int | None = None) -> Plan:
+    """Plan of the Answer on an unencrypted database: the layout of make_plan;
+    by default B is the power of two B <= min(s', 128) with at most 32 giant
+    steps that minimises J(B-1) + 8 G(2 s'/B - 1) + 6 G s'/B (hoisted baby
+    rotations of the J index ciphertexts, giant-step key switches of both
+    sets, accumulator ModDowns), ties to the smaller B."""
+    if B is None:
+        lay = make_plan(par, n, s, 1 << math.ceil(math.log2(s)))
+        costs = {}
+        b = 1
+        while b <= min(lay.s_prime, 128):
+            gi = lay.s_prime // b
+            if gi <= 32:
+                costs[b] = lay.J * (b - 1) + 8 * lay.G * (2 * gi - 1) + 6 * lay.G * gi
+            b *= 2
+        B = min(costs, key=lambda k: (costs[k], k))
+    return make_plan(par, n, s, B)
+
+
+def plain_db_diagonal_slots(par: Params, plan: Plan, db, j: int, sigma: int, k: int) -> np.ndarray:
+    """k-th extended diagonal of set sigma for index ciphertext j: row rho is
+    the diagonal of half-block h = 2j + rho (diagonal_slots), times the
+    database records it meets on the row rho != sigma (row 1 for set 0, row 0
+    for set 1):
+      D[rho][c] = alpha(h m + c')^((c mod s')+1) (DB[h m + c'] if rho != sigma),
+    c' = (c + k) mod m."""
+    m, t = par.m, par.t
+    c = np.arange(m)
+    cc = (c + k) % m
+    rows = []
+    for rho in range(2):
+        h = 2 * j + rho
+        row = diagonal_slots(par, plan, h, k)[:m]
+        if rho != sigma:
+            dbh = np.zeros(m, dtype=np.uint64)
+            chunk = np.asarray(db[h * m:(h + 1) * m], dtype=np.uint64) % np.uint64(t)
+            dbh[:chunk.size] = chunk
+            row = row * dbh[cc] % np.uint64(t)
+        rows.append(row)
+    return np.concatenate(rows)
+
+
+def plain_db_galois_elements(par: Params, plan: Plan) -> list[int]:
+    """Every automorphism of the unencrypted-database Answer, ascending."""
+    col = par.galois_col
+    ks = {col}
+    ks.update(par.galois_rot(a) for a in range(1, plan.B))
+    ks.update(par.galois_rot(g * plan.B) for g in range(1, plan.giants))
+    ks.update(par.galois_rot(g * plan.B) * col % (2 * par.N) for g in range(1, plan.giants))
+    for l, r in rotsum_levels(par, plan):
+        ks.update(par.galois_rot(jj * l) for jj in range(1, r))
+    return sorted(ks)
+
+
+def answer_plain_db(par: Params, v_cts, db, keys, plan: Plan) -> list[np.ndarray]:
+    """The Answer on an unencrypted database (no Mask): baby steps of the J
+    index ciphertexts (baby_steps), per group gamma, set sigma and giant step g
+      acc[sigma][g] = sum_{j in gamma} sum_{a<B} Rot(D^sigma_{j,gB+a}; -gB) . R[j][a]
+    over Q u P, then y = sum_g Rot(acc[0][g]; gB) + sum_g Rot_col(Rot(acc[1][g]; gB))
+    (acc[0][0] as it is; the others rotated from their lowered c1 as in
+    giant_steps, set 1 with Galois element 3^(gB) (2N - 1)), rotate-and-sum,
+    group masks.  Decrypts to the closed form of answer()."""
+    el = list(range(par.L + par.K))
+    R = baby_steps(par, v_cts, keys, plan)
+    jpg = plan.hpg // 2                      # index ciphertexts per group
+    col = par.galois_col
+    ys = []
+    for gamma in range(plan.G):
+        js = range(gamma * jpg, min((gamma + 1) * jpg, plan.J))
+        y = None
+        for sigma in range(2):
+            for g in range(plan.giants):
+                pts, cts = [], []
+                for j in js:
+                    for a in range(plan.B):
+                        d = rot_slots(par, plain_db_diagonal_slots(par, plan, db, j, sigma,
+                                                                   g * plan.B + a), -g * plan.B)
+                        pts.append(lift(par, encode(par, d), par.ext))
+                        cts.append(R[j][a])
+                acc = ring_dot_ext(par, pts, cts)
+                if sigma == 0 and g == 0:
+                    term = acc
+                else:
+                    k = par.galois_rot(g * plan.B) * (col if sigma else 1) % (2 * par.N)
+                    raised = mod_up_all(par, mod_down(par, acc[1]))
+                    term = rotate_ext_lazy(par, acc, raised, k, keys[k])
+                y = term if y is None else np.stack(
+                    [poly_add(par, y[0], term[0], el), poly_add(par, y[1], term[1], el)])
+        ys.append(rotate_and_sum(par, y, keys, plan))
+    return combine_groups(par, ys, plan)
+
+
 # ------------------------------------------------------- closed form ------
 
 def closed_form(par: Params, plan: Plan, v, db):
