@@ -57,9 +57,15 @@ def parse():
     ap.add_argument("--ring-log-n", type=int, default=13,
                     help="also time the Answer with Comp in the subring of this log2 dimension "
                          "after ring switching (with --switch-L primes; 0: skip)")
+    ap.add_argument("--plain-db", type=int, default=1,
+                    help="also time the Answer on an unencrypted database (0: skip)")
+    ap.add_argument("--plain-db-B", type=int, default=0,
+                    help="baby-step count of the unencrypted-database plan (0: its cost rule)")
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="served arrival rates, queries/s")
-    ap.add_argument("--served-requests", type=int, default=192)
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--latency-steps", type=int, default=200,
+                    help="steps of the plain path timed one by one for its p50/p99")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served HBM budget")
     return ap.parse_args()
 
@@ -402,6 +408,18 @@ def run_served(args, mix) -> list:
     arena_bytes = max(budget - resident, 1 << 30)
     arena_bytes = min(arena_bytes, free - (4 << 30))
     arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
+    # every query's answer alone, checked once (decrypts and decompresses to
+    # its matches); a served answer is exact iff it equals it bit for bit
+    # (the Answer is deterministic)
+    reference = []
+    for it in mix.items:
+        h = mix.handle(it)
+        it["ctx"].answer(it["plan"], it["v_cts"], mix.db[it["spec"].log_n], it["keys"],
+                         it["galois"], it["consts"], out=h.out)
+        torch.cuda.synchronize()
+        if not mix.check(it, h.out):
+            raise SystemExit("served reference answer does not decompress")
+        reference.append(h.out)
     out = []
     for r_i, rate in enumerate(float(x) for x in args.rates.split(",") if x):
         nreq = args.served_requests
@@ -422,10 +440,16 @@ def run_served(args, mix) -> list:
         lat = np.array([(i.t_done_ns - i.t_submit_ns) / 1e6 for i in infos])
         span = (max(i.t_done_ns for i in infos) - min(i.t_submit_ns for i in infos)) / 1e9
         ok = all(i.status == 0 for i in infos)
-        exact = all(mix.check(it, h.out) for it, h in list(zip(order, handles))[:16])
+        exact = all(torch.equal(h.out, reference[i % len(mix.items)])
+                    for i, h in enumerate(handles))
         out.append({"rate_qps": rate, "requests": nreq, "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99)), "served_qps": nreq / span,
-                    "all_ok": bool(ok), "first16_decompress_exactly": bool(exact)})
+                    "offered_s": float(arrivals[-1]), "all_ok": bool(ok),
+                    "all_decompress_exactly": bool(exact),
+                    "check": "every result equal bit for bit to its query's answer alone, "
+                             "which decrypts and decompresses to the query's matches"})
+        del handles
+        torch.cuda.empty_cache()
     del arena
     return out
 
@@ -655,6 +679,70 @@ def run_ring_switched(args, cfg, ctx, plan, q, v_cts, stream, rank: int) -> dict
                      f"all of these")}
 
 
+def run_plain_db(args, cfg, ctx, q, v_cts, sk, stream, rank: int) -> dict:
+    """The Answer on an unencrypted database (Sec. 5.2 remark): the resident
+    index ciphertexts compressed with [C; C diag(DB)] (pdq_answer_plain_db),
+    no Mask; the database-specific diagonals resident in HBM."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2408_17063_gb300 import pdq
+
+    plan = ctx.plan_plain_db(cfg.n, cfg.s, args.plain_db_B)
+    galois = ctx.plan_galois(plan)
+    keys = ctx._u64(len(galois) * ctx.key_elems)
+    kv = keys.view(len(galois), -1)
+    kr = W.rotation_key_randomness(ctx.moduli, ctx.N, ctx.ndigits, galois, cfg.seed + rank)
+    for i, k in enumerate(galois):
+        a, e = kr[k]
+        ctx.rotkey_gen(sk, k, torch.from_numpy(a.view(np.int64)).cuda(),
+                       torch.from_numpy(e).cuda(), out=kv[i])
+    t0 = time.perf_counter()
+    consts = ctx.db_diagonals(plan, torch.from_numpy(q.db.astype(np.int32)))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    ws = ctx.answer_plain_db_workspace(plan)
+    out = ctx._u64(plan.n_out * ctx.ct_elems)
+
+    def step():
+        ctx.answer_plain_db(plan, v_cts, keys, galois, consts, ws=ws, out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    truth = [(int(i), int(q.db[i])) for i in q.positions]
+    ok = ctx.decomp(plan, ctx.decrypt(sk, out).cpu().numpy()) == truth
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ctx.profile_enable(True)
+    launches0 = pdq.pdq_launch_count()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = pdq.pdq_launch_count() - launches0
+    stages = {k: v[0] / args.steps for k, v in ctx.profile_read().items() if v[1]}
+    ctx.profile_enable(False)
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total = ev[0].elapsed_time(ev[-1])
+    diag_bytes = consts.numel() * 8
+    mac_ms = stages.get("mac")
+    res = {"value": args.steps / (total / 1000.0), "unit": "queries/s",
+           "ms_per_query": total / args.steps, "p50_ms": statistics.median(per),
+           "stages_ms_per_query": stages,
+           "plan": {k: getattr(plan, k) for k in ("B", "giants", "J", "G", "n_out")},
+           "db_diagonals_gib": diag_bytes / 2**30, "db_diagonals_build_s": build_s,
+           "rotation_keys": len(galois), "gpu_launches_per_step": int(launches) / args.steps,
+           "all_decompress_exactly": bool(ok),
+           "what": "the index ciphertexts compressed with [C; C diag(DB)] (no Mask), "
+                   "database-specific diagonals resident; one step = pdq_answer_plain_db"}
+    if mac_ms:
+        res["mac_dram_gbs"] = diag_bytes / (mac_ms / 1e3) / 1e9
+    del consts, ws, keys
+    torch.cuda.empty_cache()
+    return res
+
+
 # The paper's Table II (n = 16384, s = 8..128) and Table III (s = 16,
 # n = 2^13..2^17) shapes: ring 2^13, t = 65537, two 54-bit ciphertext primes;
 # its Comp times (single-thread Xeon Silver 4114, seconds) for context.
@@ -806,6 +894,15 @@ def run_gpu(args, cfg, rank: int, world: int):
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dist)
     value = job_throughput(total_ms, args.steps, world)
+    # latency distribution of the plain path over more steps (each step timed
+    # by its own pair of events on the stream)
+    lev = [torch.cuda.Event(enable_timing=True) for _ in range(args.latency_steps + 1)]
+    lev[0].record(stream)
+    for i in range(args.latency_steps):
+        step()
+        lev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(lev[i].elapsed_time(lev[i + 1]) for i in range(args.latency_steps))
 
     # end to end through the host-buffer entry point (pinned host buffers,
     # coefficient form, copies inside the timed region)
@@ -825,8 +922,8 @@ def run_gpu(args, cfg, rank: int, world: int):
     mac_ms, mac_calls = stages["mac"]
     mac_ms_per = mac_ms / max(1, mac_calls)
     roofline = mac_roofline(ctx, plan, mac_ms_per)
-    ms_sorted = sorted(per)
-    p50 = statistics.median(per)
+    ms_sorted = lat if lat else sorted(per)
+    p50 = statistics.median(ms_sorted)
     p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -839,7 +936,8 @@ def run_gpu(args, cfg, rank: int, world: int):
                                               f"{keys.numel() * 8 / 2**20:.0f} MiB of rotation keys, "
                                               f"{v_cts.numel() * 8 / 2**20:.0f} MiB query, "
                                               f"{db.numel() * 8 / 2**20:.0f} MiB database read)"}),
-            "latency_ms": {"p50": p50, "p99": p99, "min": ms_sorted[0], "max": ms_sorted[-1]},
+            "latency_ms": {"p50": p50, "p99": p99, "min": ms_sorted[0], "max": ms_sorted[-1],
+                           "steps": len(ms_sorted)},
             "stages_ms_per_query": {k: v[0] / max(1, args.steps) for k, v in stages.items()},
             "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps,
             "clocks": clk, "e2e": e2e, "roofline": roofline}
@@ -850,6 +948,8 @@ def run_gpu(args, cfg, rank: int, world: int):
                      "host Decomp per query; paper_comp_s is the paper's single-thread Xeon time "
                      "(context, other hardware and scheme)"),
             "rows": run_paper_shapes(args, rank)}
+    if args.plain_db:
+        line["plain_db"] = run_plain_db(args, cfg, ctx, q, v_cts, sk, stream, rank)
     if args.switch_L and 0 < args.switch_L < cfg.L:
         line["switched"] = run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank)
         if args.ring_log_n and args.ring_log_n < cfg.log_n:

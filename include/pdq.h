@@ -100,6 +100,8 @@ typedef struct {
     uint32_t n_out;      /* output ciphertexts */
     uint32_t ring_ratio; /* 1; R = N_big/N for Comp in a subring after ring
                             switching (pdq_plan_make_switched) */
+    uint32_t plain_db;   /* 1 for the Answer on an unencrypted database
+                            (pdq_plan_make_plain_db), else 0 */
 } pdq_plan;
 
 /* ---------------------------------------------------------------- context */
@@ -348,6 +350,42 @@ int pdq_answer_host(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_
                     const uint64_t* db, const uint64_t* keys, const uint64_t* galois,
                     uint32_t nkeys, const uint64_t* consts, uint64_t* out_host, void* ws,
                     size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------- unencrypted database
+ * When the server holds the database in the clear, C (DB . v) =
+ * (C diag(DB)) v, so it can skip Mask and compress the index vector alone
+ * with the stacked matrix [C; C diag(DB)] (Sec. 5.2, remark on an
+ * unencrypted database).  Index ciphertext j holds half-block 2j in row 0
+ * and 2j+1 in row 1; two diagonal sets carry C on one row and C diag(DB) on
+ * the other (set 0: C on row 0, C diag(DB) on row 1; set 1 the reverse), so
+ * set 0 + Rot_col(set 1) holds (C v, C d) with d = DB . v, and Rot_col is
+ * folded into the giant steps of set 1 (Galois element 3^(gB) (2N-1)).
+ * pdq_plan_make_plain_db: the layout of pdq_plan_make, plain_db = 1; B = 0
+ *   picks the power of two B <= min(s', 128) with at most 32 giant steps that
+ *   minimises J (B-1) + 8 G (2 s'/B - 1) + 6 G s'/B, ties to the smaller B.
+ *   pdq_plan_galois lists its Galois elements (Rot_col, 3^a, 3^(gB),
+ *   3^(gB) (2N-1), the rotate-and-sum levels).
+ * pdq_db_diagonals_build: the database-specific diagonals of both sets for
+ *   every index ciphertext, over every prime of Q u P, then the group masks
+ *   (dev out of pdq_db_diagonals_bytes; J 2 s' (L+K) N words plus the masks:
+ *   at N = 2^15, n = 2^20, s' = 256, 43 GB).  values: dev [n] uint32 (< t,
+ *   else reduced mod t), n = plan->n.  Allocates temporaries.
+ * pdq_answer_plain_db: v_cts dev [J][2][L][N]; keys, galois, nkeys as for
+ *   pdq_answer with the elements of this plan; consts from
+ *   pdq_db_diagonals_build; out dev [n_out][2][L][N] decrypting to the same
+ *   slots as pdq_answer's.  Workspace: pdq_answer_plain_db_workspace_bytes
+ *   (dev), else PDQ_E_NOMEM; PDQ_E_PARAM for a plan without plain_db,
+ *   PDQ_E_KEY for a missing key. */
+int pdq_plan_make_plain_db(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B,
+                           pdq_plan* plan);
+size_t pdq_db_diagonals_bytes(const pdq_ctx* ctx, const pdq_plan* plan);
+int pdq_db_diagonals_build(const pdq_ctx* ctx, const pdq_plan* plan, const uint32_t* values,
+                           uint64_t* out, void* stream);
+size_t pdq_answer_plain_db_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan);
+int pdq_answer_plain_db(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
+                        const uint64_t* keys, const uint64_t* galois, uint32_t nkeys,
+                        const uint64_t* consts, uint64_t* out, void* ws, size_t ws_bytes,
+                        void* stream);
 
 /* ------------------------------------------------------ batches, serving
  * One query of a batch or of the server: the buffers of pdq_answer.  plan

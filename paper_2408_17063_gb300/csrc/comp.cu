@@ -123,6 +123,27 @@ int plan_make_switched(const Ctx& c, u32 big_log_n, u64 n, u32 s, u32 B, pdq_pla
     return PDQ_OK;
 }
 
+// The Answer on an unencrypted database (Sec. 5.2 remark): the layout of
+// plan_make; B = 0 minimises J (B-1) + 8 G (2 s'/B - 1) + 6 G s'/B (baby
+// rotations of the J index ciphertexts, giant-step key switches of both
+// diagonal sets, accumulator ModDowns).
+int plan_make_plain_db(const Ctx& c, u64 n, u32 s, u32 B, pdq_plan* pl) {
+    PDQ_TRY(plan_make(c, n, s, B, pl));
+    if (B == 0) {
+        u64 best = ~0ull;
+        u32 bb = pl->B;
+        for (u64 b = 1; b <= pl->s_prime && b <= 128; b *= 2) {
+            const u64 gi = pl->s_prime / b;
+            if (gi > 32) continue;
+            const u64 cost = (u64)pl->J * (b - 1) + 8ull * pl->G * (2 * gi - 1) + 6ull * pl->G * gi;
+            if (cost < best) { best = cost; bb = (u32)b; }
+        }
+        PDQ_TRY(plan_make(c, n, s, bb, pl));
+    }
+    pl->plain_db = 1;
+    return PDQ_OK;
+}
+
 namespace {
 
 u64 galois_rot(const Ctx& c, long long r) {
@@ -155,6 +176,9 @@ std::vector<u64> plan_galois(const Ctx& c, const pdq_plan& pl) {
     ks.push_back(2ull * c.N - 1);
     for (u32 a = 1; a < pl.B; ++a) ks.push_back(galois_rot(c, a));
     for (u32 g = 1; g < pl.giants; ++g) ks.push_back(galois_rot(c, (long long)g * pl.B));
+    if (pl.plain_db)           // set 1 of the giant steps goes through Rot_col
+        for (u32 g = 1; g < pl.giants; ++g)
+            ks.push_back(galois_rot(c, (long long)g * pl.B) * (2ull * c.N - 1) % (2ull * c.N));
     for (const auto& [l, r] : rotsum_levels(c, pl))
         for (u32 j = 1; j < r; ++j) ks.push_back(galois_rot(c, (long long)(j * l)));
     std::sort(ks.begin(), ks.end());
@@ -172,6 +196,8 @@ bool valid_plan(const Ctx& c, const pdq_plan* pl) {
         const u32 R = pl->ring_ratio;
         if ((R & (R - 1)) != 0 || R > (1u << 13)) return false;
         rc = plan_make_switched(c, c.log_n + log2_exact(R), pl->n, pl->s, pl->B, &chk);
+    } else if (pl->plain_db) {
+        rc = plan_make_plain_db(c, pl->n, pl->s, pl->B, &chk);
     } else {
         rc = plan_make(c, pl->n, pl->s, pl->B, &chk);
     }
@@ -251,6 +277,44 @@ int answer_pack(const Ctx& c, const Keys& keys, const u64* v, const u64* db, u64
     PDQ_TRY(ks_apply(c, D, vin, jn, (u32)kc, kp, ct_set(w, cts), CtSet{}, aws, st));
     prof_mark(c, PDQ_STAGE_MASK, st);
     return mask_pack(c, jn, v, w, db, U, st);
+}
+
+// Steps 5 and 6 of Comp on the giant-step sums yx ([G][2][L+K][N]): the
+// rotate-and-sum on y over Q u P (per level the lowered c1 of every y, into
+// Y1, is raised once, the r rotations (a = 0: y itself) go to Rx and are
+// summed back into yx; the last level's sum is lowered to Y0), then the group
+// masks (one group: the result as it is).
+int rotsum_and_combine(const Ctx& c, const pdq_plan& pl, const Keys& keys, u64* yx, u64* Rx,
+                       u64* Y0, u64* Y1, u64* rws, u64* aws, const u64* masks, u64* out,
+                       cudaStream_t st) {
+    const long long cts = (long long)ct_elems(c);
+    const long long ects = 2LL * (c.L + c.K) * c.N;
+    const u64 EN = (u64)(c.L + c.K) * c.N, LN = (u64)c.L * c.N;
+    const u32 G = pl.G;
+    u64* D = nullptr;
+    prof_mark(c, PDQ_STAGE_ROTSUM, st);
+    const CtSet y_ext = ct_set(yx, ects);
+    for (const auto& [l, r] : rotsum_levels(c, pl)) {
+        std::vector<u64> gal(r, 1), koff(r, 0);
+        for (u32 j = 1; j < r; ++j) {
+            gal[j] = galois_rot(c, (long long)(j * l));
+            const u64* kp = keys.find(gal[j]);
+            if (!kp) return fail(PDQ_E_KEY, "comp: missing rotation key for Galois element " + std::to_string(gal[j]));
+            koff[j] = (u64)(kp - keys.base);
+        }
+        PDQ_TRY(mod_down_polys(c, yx + EN, 2 * EN, G, Y1, LN, aws, st));
+        PDQ_TRY(ks_raise(c, ct_set(Y1, (long long)LN), G, rws, &D, st, 0));
+        PDQ_TRY(hoisted_rotations_ext(c, D, y_ext, G, r, gal, keys.base, koff, Rx, st, true));
+        PDQ_TRY(sum_rotations(c, Rx, G, r, yx, st));
+    }
+    PDQ_TRY(mod_down_batch(c, yx, G, ct_set(Y0, cts), aws, st));
+    prof_mark(c, PDQ_STAGE_COMBINE, st);
+    if (G == 1) {
+        if (cudaMemcpyAsync(out, Y0, (size_t)cts * sizeof(u64), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return fail(PDQ_E_CUDA, "comp: output copy failed");
+        return PDQ_OK;
+    }
+    return group_combine(c, pl, Y0, masks, out, st);
 }
 
 // Comp from the masked ciphertexts (masked != nullptr: [J][4] as pdq_mask
@@ -348,36 +412,113 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
         PDQ_TRY(ks_apply_ext(c, D + (u64)(g - 1) * G * dstride, c0s, G, (u32)k, kp,
                              ct_set(yx, ects), true, false, st, true));
     }
-    // 5. rotate-and-sum on y over Q u P: per level the lowered c1 of every y
-    // (into Y1) is raised once, the r rotations (a = 0: y itself) go to Rx and
-    // are summed back into yx; the last level's sum is lowered to Y0
-    prof_mark(c, PDQ_STAGE_ROTSUM, st);
-    const CtSet y_ext = ct_set(yx, ects);
-    for (const auto& [l, r] : rotsum_levels(c, pl)) {
-        std::vector<u64> gal(r, 1), koff(r, 0);
-        for (u32 j = 1; j < r; ++j) {
-            gal[j] = galois_rot(c, (long long)(j * l));
-            const u64* kp;
-            PDQ_TRY(key_for(gal[j], &kp));
-            koff[j] = (u64)(kp - keys.base);
-        }
-        PDQ_TRY(mod_down_polys(c, yx + EN, 2 * EN, G, Y1, LN, aws, st));
-        PDQ_TRY(ks_raise(c, ct_set(Y1, (long long)LN), G, rws, &D, st, 0));
-        PDQ_TRY(hoisted_rotations_ext(c, D, y_ext, G, r, gal, keys.base, koff, Rx, st, true));
-        PDQ_TRY(sum_rotations(c, Rx, G, r, yx, st));
-    }
-    PDQ_TRY(mod_down_batch(c, yx, G, ct_set(Y0, cts), aws, st));
-    u64* ycur = Y0;
-    // 6. output
-    prof_mark(c, PDQ_STAGE_COMBINE, st);
-    if (G == 1) {
-        if (cudaMemcpyAsync(out, ycur, (size_t)cts * sizeof(u64), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            return fail(PDQ_E_CUDA, "comp: output copy failed");
-    } else {
-        PDQ_TRY(group_combine(c, pl, ycur, masks, out, st));
-    }
+    PDQ_TRY(rotsum_and_combine(c, pl, keys, yx, Rx, Y0, Y1, rws, aws, masks, out, st));
     prof_mark(c, -1, st);
     (void)none;
+    return PDQ_OK;
+}
+
+// Workspace of the Answer on an unencrypted database, in uint64 elements.
+struct PlainDbLayout {
+    u64 Rx;     // baby steps of the index ciphertexts over Q u P [J][B], later
+                // the rotations of one rotate-and-sum level
+    u64 yx;     // giant-step sums over Q u P (from set 0, giant 0), [G]
+    u64 accx;   // the other accumulators over Q u P, [G][2 giants - 1]
+    u64 acc;    // ... their c1 lowered to Q, [G][2 giants - 1][L][N]
+    u64 Y0, Y1; // rotate-and-sum: the output over Q, the lowered c1 of a level
+    u64 rws;    // key-switch raise scratch
+    u64 aws;    // ModDown scratch
+    u64 end;
+};
+
+PlainDbLayout plain_db_layout(const Ctx& c, const pdq_plan& pl) {
+    const u64 cts = ct_elems(c), ects = 2ull * (c.L + c.K) * c.N;
+    const u64 G = pl.G, NA = 2ull * pl.giants - 1;
+    const u32 cnt = std::max({pl.J, pl.G, (u32)(G * NA)});
+    const u64 scratch = std::max({mod_down_ws(c, pl.G), mod_down_polys_ws(c, (u32)(G * NA)),
+                                  apply_ws(c, pl.G)}) / sizeof(u64);
+    PlainDbLayout lo;
+    lo.Rx = 0;
+    lo.yx = lo.Rx + std::max<u64>((u64)pl.J * pl.B, G * 8) * ects;
+    lo.accx = lo.yx + G * ects;
+    lo.acc = lo.accx + G * NA * ects;
+    lo.Y0 = lo.acc + G * NA * (u64)c.L * c.N;
+    lo.Y1 = lo.Y0 + G * cts;
+    lo.rws = lo.Y1 + G * cts;
+    lo.aws = lo.rws + raise_ws(c, cnt) / sizeof(u64);
+    lo.end = lo.aws + scratch;
+    return lo;
+}
+
+// The Answer on an unencrypted database (Sec. 5.2 remark): no Mask; baby
+// steps of the J index ciphertexts; per group both diagonal sets and every
+// giant step accumulated over Q u P (diag_mac_db); the accumulators other
+// than (set 0, giant 0) rotated from their lowered c1 with Galois element
+// 3^(gB) (set 0) or 3^(gB) (2N - 1) (set 1: Rot_col folded in), summed into
+// yx; then rotate-and-sum and the group masks.
+int answer_plain_db_run(const Ctx& c, const pdq_plan& pl, const u64* v_cts, const Keys& keys,
+                        const u64* consts, u64* out, void* ws, cudaStream_t st) {
+    const long long cts = (long long)ct_elems(c);
+    const long long ects = 2LL * (c.L + c.K) * c.N;
+    const u64 EN = (u64)(c.L + c.K) * c.N, LN = (u64)c.L * c.N;
+    const u32 J = pl.J, B = pl.B, G = pl.G, GI = pl.giants, NA = 2 * GI - 1;
+    const PlainDbLayout lo = plain_db_layout(c, pl);
+    u64* const base = reinterpret_cast<u64*>(ws);
+    u64* Rx = base + lo.Rx;
+    u64* yx = base + lo.yx;
+    u64* accx = base + lo.accx;
+    u64* acc = base + lo.acc;
+    u64* rws = base + lo.rws;
+    u64* aws = base + lo.aws;
+    const u64* Dd = consts;
+    const u64* masks = consts + 2ull * J * B * GI * EN;
+    u64* D = nullptr;
+    // 1. baby steps of the index ciphertexts in the extended basis
+    prof_mark(c, PDQ_STAGE_BABY, st);
+    const CtSet v = ct_set(v_cts, cts);
+    if (B == 1) PDQ_TRY(times_P(c, v, J, ct_set(Rx, (long long)B * ects), true, st));
+    else {
+        PDQ_TRY(ks_raise(c, v, J, rws, &D, st));
+        std::vector<u64> koff(B, 0);
+        for (u32 a = 1; a < B; ++a) {
+            const u64 k = galois_rot(c, a);
+            const u64* kp = keys.find(k);
+            if (!kp) return fail(PDQ_E_KEY, "answer_plain_db: missing rotation key for Galois element " + std::to_string(k));
+            koff[a] = (u64)(kp - keys.base);
+        }
+        PDQ_TRY(baby_steps_ext(c, D, v, J, B, keys.base, koff, Rx, st));
+    }
+    // 2. both diagonal sets, every giant step
+    prof_mark(c, PDQ_STAGE_MAC, st);
+    PDQ_TRY(diag_mac_db(c, pl, Rx, Dd, yx, accx, st));
+    // 3. lower c1 of the accumulators to be rotated, raise them all at once
+    // (ordered by (set, giant) first, so each key's digits are one run of G)
+    prof_mark(c, PDQ_STAGE_ACC_MODDOWN, st);
+    if (NA > 0) PDQ_TRY(mod_down_polys(c, accx + EN, 2 * EN, G * NA, acc, LN, aws, st));
+    prof_mark(c, PDQ_STAGE_GIANT, st);
+    if (NA > 0) {
+        CtSet c1all;
+        c1all.base = acc;
+        c1all.outer = (long long)LN;
+        c1all.per = G;
+        c1all.inner = (long long)NA * LN;
+        PDQ_TRY(ks_raise(c, c1all, G * NA, rws, &D, st, 0));
+    }
+    const u64 dstride = (u64)c.ndigits * (c.L + c.K) * c.N;
+    for (u32 i = 0; i < NA; ++i) {
+        const u32 sigma = (i + 1) / GI, g = (i + 1) % GI;
+        u64 k = galois_rot(c, (long long)g * B);
+        if (sigma) k = k * (2ull * c.N - 1) % (2ull * c.N);
+        const u64* kp = keys.find(k);
+        if (!kp) return fail(PDQ_E_KEY, "answer_plain_db: missing rotation key for Galois element " + std::to_string(k));
+        const CtSet c0s = ct_set(accx + (u64)i * ects, (long long)NA * ects);
+        PDQ_TRY(ks_apply_ext(c, D + (u64)i * G * dstride, c0s, G, (u32)k, kp, ct_set(yx, ects),
+                             true, false, st, true));
+    }
+    // 4. rotate-and-sum and group masks
+    PDQ_TRY(rotsum_and_combine(c, pl, keys, yx, Rx, base + lo.Y0, base + lo.Y1, rws, aws, masks,
+                               out, st));
+    prof_mark(c, -1, st);
     return PDQ_OK;
 }
 
@@ -682,6 +823,55 @@ int pdq_answer_host(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_
         return fail(PDQ_E_CUDA, "answer_host: download failed");
     if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("answer_host");
     return PDQ_OK;
+}
+
+int pdq_plan_make_plain_db(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B,
+                           pdq_plan* plan) {
+    PDQ_CHECK_CTX(ctx);
+    if (!plan) return fail(PDQ_E_PARAM, "null plan");
+    return plan_make_plain_db(C(ctx), n, s, B, plan);
+}
+
+size_t pdq_db_diagonals_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {
+    if (!ctx || !valid_plan(C(ctx), plan) || !plan->plain_db) return 0;
+    const Ctx& c = C(ctx);
+    return ((size_t)2 * plan->J * plan->B * plan->giants * (c.L + c.K) * c.N +
+            (size_t)plan->per_out * c.L * c.N) * sizeof(u64);
+}
+
+int pdq_db_diagonals_build(const pdq_ctx* ctx, const pdq_plan* plan, const uint32_t* values,
+                           uint64_t* out, void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    const Ctx& c = C(ctx);
+    if (!valid_plan(c, plan) || !plan->plain_db) return fail(PDQ_E_PARAM, "db_diagonals_build: invalid plan");
+    if (!values || !out) return fail(PDQ_E_PARAM, "db_diagonals_build: null buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    PDQ_TRY(build_db_diagonals(c, *plan, values, out, st));
+    if (plan->G > 1)
+        PDQ_TRY(build_group_masks(c, *plan,
+                                  out + (u64)2 * plan->J * plan->B * plan->giants * (c.L + c.K) * c.N,
+                                  st));
+    return PDQ_OK;
+}
+
+size_t pdq_answer_plain_db_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {
+    if (!ctx || !valid_plan(C(ctx), plan) || !plan->plain_db) return 0;
+    return plain_db_layout(C(ctx), *plan).end * sizeof(u64);
+}
+
+int pdq_answer_plain_db(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
+                        const uint64_t* keys, const uint64_t* galois, uint32_t nkeys,
+                        const uint64_t* consts, uint64_t* out, void* ws, size_t ws_bytes,
+                        void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    const Ctx& c = C(ctx);
+    if (!valid_plan(c, plan) || !plan->plain_db) return fail(PDQ_E_PARAM, "answer_plain_db: invalid plan");
+    if (!v_cts || !keys || !galois || !consts || !out || !ws)
+        return fail(PDQ_E_PARAM, "answer_plain_db: null buffer");
+    if (ws_bytes < plain_db_layout(c, *plan).end * sizeof(u64))
+        return fail(PDQ_E_NOMEM, "answer_plain_db: workspace too small");
+    const Keys k{keys, galois, nkeys, (u64)c.ndigits * 2 * (c.L + c.K) * c.N};
+    return answer_plain_db_run(c, *plan, v_cts, k, consts, out, ws, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -154,6 +154,40 @@ __global__ void k_diag_slots_sw(u64* __restrict__ out, u32 giants, u32 B, u32 s_
     out[(((u64)blockIdx.y * L) << logN) + pos[idx]] = acc % t;
 }
 
+// Diagonals of the Answer on an unencrypted database, one plaintext (j,
+// sigma, g, a) per grid row (pt = pt_base + y B, pt = ((2j + sigma) giants +
+// g) B + a): row rho is the diagonal of
+// half-block h = 2j + rho rotated by -gB, times the database record it meets
+// on the row rho != sigma:
+//   D[rho][c] = alpha(h m + c')^((cp mod s')+1) (DB[h m + c'] if rho != sigma),
+// cp = (c - gB) mod m, c' = (cp + gB + a) mod m, alpha(i) = (i mod G_sz) + 1.
+__global__ void k_diag_slots_db(u64* __restrict__ out, u32 giants, u32 B, u32 s_prime, u32 logN,
+                                u32 L, const u32* __restrict__ pos, u64 t, u32 G_sz,
+                                const u32* __restrict__ values, u64 n, u64 pt_base) {
+    const u32 idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 N = 1u << logN, m = N / 2;
+    if (idx >= N) return;
+    const u64 pt = pt_base + (u64)blockIdx.y * B;
+    const u32 a = (u32)(pt % B);
+    const u32 g = (u32)((pt / B) % giants);
+    const u32 sigma = (u32)((pt / ((u64)B * giants)) & 1);
+    const u64 j = pt / (2ull * B * giants);
+    const u32 rho = idx >= m ? 1 : 0;
+    const u32 col = idx & (m - 1);
+    const u32 k = g * B + a;
+    const u32 cp = (col + m - (g * B) % m) & (m - 1);
+    const u64 rec = (2 * j + rho) * m + ((cp + k) & (m - 1));
+    u32 e = (cp & (s_prime - 1)) + 1;
+    u64 r = 1, b = (rec % G_sz + 1) % t;
+    while (e) {
+        if (e & 1) r = r * b % t;
+        b = b * b % t;
+        e >>= 1;
+    }
+    if (rho != sigma) r = r * (rec < n ? (u64)values[rec] % t : 0) % t;
+    out[(((u64)blockIdx.y * L) << logN) + pos[idx]] = r;
+}
+
 // database plaintexts: row pt = 2j + half holds DB_j.[1;0] (half 0) or DB_j.[0;1]
 __global__ void k_db_slots(u64* __restrict__ out, const u32* __restrict__ values, u64 n, u32 logN,
                            u32 L, const u32* __restrict__ pos, u64 t) {
@@ -1815,6 +1849,135 @@ int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64*
         case 4: return launch_mac_bc<4>(c, pl, s, R, Dg, acc0, acc, st);
         default: return fail(PDQ_E_PARAM, "diag_mac: giant-step count must be a power of two");
     }
+}
+
+namespace {
+
+// Multiply-accumulate of the Answer on an unencrypted database:
+//   acc[gamma][sigma][g][p] = sum_{j in gamma} sum_{a<B} D[j][sigma][a][l][x][g] * R[j][a][p][l][x]
+// over Q u P.  The diagonals are different for every index ciphertext (the
+// database is in them), so each is used by one thread (for both
+// polynomials) and streamed from DRAM once; the kernel is bound by that
+// stream.  Thread = position x, set sigma and GT giant steps of one group
+// and prime; its GT diagonal values are contiguous (giant index innermost)
+// and the rotated operands R (split layout) are shared through L1 by the
+// threads of the other sets and giant slices at the same position.
+// Output (sigma, g) = (0, 0) goes to y0[gamma][p], the others to
+// acc[gamma][sigma GI + g - 1][p].
+template <int GT>
+__global__ void __launch_bounds__(256) k_diag_mac_db(const u64* __restrict__ R,
+                                                  const u64* __restrict__ Dd, u32 J, u32 jpg,
+                                                  u32 B, u32 GI, u32 GS, u32 E, u32 logN,
+                                                  const Mod* __restrict__ mods,
+                                                  const u64* __restrict__ ckar, u32 fold_one,
+                                                  u64* __restrict__ y0, u64* __restrict__ acc) {
+    const u64 N = 1ull << logN, EN = (u64)E << logN;
+    const u64 x = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 sigma = threadIdx.y / GS, g0 = (threadIdx.y % GS) * GT;
+    const u32 l = blockIdx.y, gamma = blockIdx.z;
+    if (x >= N) return;
+    AccK A[2][GT];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int g = 0; g < GT; ++g) A[p][g] = AccK{0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const u64 loff = ((u64)l << logN) + x;
+    for (u32 jj = 0; jj < jpg; ++jj) {
+        const u64 j = (u64)gamma * jpg + jj;
+        if (j >= J) break;
+        for (u32 a = 0; a < B; ++a) {
+            const u64* rp = R + ((j * B + a) * 2) * EN + loff;
+            const u64 r0 = __ldg(rp), r1 = __ldg(rp + EN);
+            const u32 rl0 = (u32)r0, rh0 = (u32)(r0 >> 32), rs0 = rl0 + rh0;
+            const u32 rl1 = (u32)r1, rh1 = (u32)(r1 >> 32), rs1 = rl1 + rh1;
+            const u64* dp = Dd + ((((j * 2 + sigma) * B + a) * E) << logN) * GI + loff * GI + g0;
+            u64 d[GT];
+            if (GT >= 2) {
+#pragma unroll
+                for (int g = 0; g < GT; g += 2) {
+                    const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(dp + g));
+                    d[g] = v.x;
+                    d[g + 1] = v.y;
+                }
+            } else {
+                d[0] = __ldcs(dp);
+            }
+#pragma unroll
+            for (int g = 0; g < GT; ++g) {
+                const u32 d0 = (u32)d[g], d1 = (u32)(d[g] >> 32), ds = d0 + d1;
+                mack(A[0][g], rl0, rh0, rs0, d0, d1, ds);
+                mack(A[1][g], rl1, rh1, rs1, d0, d1, ds);
+            }
+        }
+    }
+    const Mod md = mods[l];
+#pragma unroll
+    for (int g = 0; g < GT; ++g) {
+        const u32 gi = g0 + g;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const u64 v = fold_one ? fold1(A[p][g], md) : foldk(A[p][g], md, ckar + 8 * l);
+            u64* o = (sigma == 0 && gi == 0)
+                         ? y0 + ((u64)gamma * 2 + p) * EN + loff
+                         : acc + (((u64)gamma * (2 * GI - 1) + sigma * GI + gi - 1) * 2 + p) * EN + loff;
+            *o = v;
+        }
+    }
+}
+
+}  // namespace
+
+int build_db_diagonals(const Ctx& c, const pdq_plan& pl, const u32* values, u64* out,
+                       cudaStream_t st) {
+    const u32 GI = pl.giants, B = pl.B, E = c.L + c.K;
+    PDQ_TRY(check_y(GI, "diagonals"));
+    const u64 LN = (u64)E * c.N;
+    u64* tmp = nullptr;
+    if (cudaMallocAsync((void**)&tmp, (size_t)GI * LN * sizeof(u64), st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PDQ_E_NOMEM, "diagonals: temporary allocation failed");
+    }
+    int rc = PDQ_OK;
+    // plaintext (j, sigma, g, a) is encoded in tmp[g], then stored at
+    // out[j][sigma][a][l][x][g] in the operand layout of the multiply-accumulate
+    for (u64 js = 0; js < 2ull * pl.J && rc == PDQ_OK; ++js) {
+        for (u32 a = 0; a < B && rc == PDQ_OK; ++a) {
+            // row g of tmp: plaintext (js, g, a), pt = (js GI + g) B + a
+            k_diag_slots_db<<<grid2(c.N, GI), kBlock, 0, st>>>(
+                tmp, GI, B, pl.s_prime, c.log_n, E, c.d_slot_pos, c.t, pl.G_sz, values, pl.n,
+                js * GI * B + a);
+            rc = launched("k_diag_slots_db");
+            if (rc == PDQ_OK) rc = encode_finish(c, tmp, GI, E, st);
+            if (rc == PDQ_OK) {
+                k_diag_layout<<<(u32)((LN + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+                    tmp, out + (js * B + a) * GI * LN, GI, LN);
+                rc = launched("k_diag_layout");
+            }
+        }
+    }
+    cudaFreeAsync(tmp, st);
+    return rc;
+}
+
+int diag_mac_db(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dd, u64* y0, u64* acc,
+                cudaStream_t st) {
+    const u32 GI = pl.giants, E = c.L + c.K;
+    const u32 GT = GI < 4 ? GI : 4, GS = GI / GT;
+    if (2 * GS > 256) return fail(PDQ_E_PARAM, "diag_mac_db: too many giant steps");
+    const u32 X = std::max(32u, 256u / (2 * GS));
+    const u32 jpg = pl.hpg / 2;
+    const u32 fold_one = (u64)std::min(jpg, pl.J) * pl.B <= 256 ? 1u : 0u;
+    if (pl.G > 65535) return fail(PDQ_E_PARAM, "diag_mac_db: too many groups");
+    const dim3 block(X, 2 * GS), grid((c.N + X - 1) / X, E, pl.G);
+#define PDQ_MACDB(T)                                                                                  k_diag_mac_db<T><<<grid, block, 0, st>>>(R, Dd, pl.J, jpg, pl.B, GI, GS, E, c.log_n, c.d_mods,                                             c.d_ckar, fold_one, y0, acc)
+    switch (GT) {
+        case 1: PDQ_MACDB(1); break;
+        case 2: PDQ_MACDB(2); break;
+        case 4: PDQ_MACDB(4); break;
+        default: return fail(PDQ_E_PARAM, "diag_mac_db: giant-step count must be a power of two");
+    }
+#undef PDQ_MACDB
+    return launched("k_diag_mac_db");
 }
 
 int ct_add(const Ctx& c, CtSet y, CtSet x, u32 cnt, cudaStream_t st) {

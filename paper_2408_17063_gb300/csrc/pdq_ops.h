@@ -71,7 +71,15 @@ int mask_literal(const Ctx& c, u32 J, const u64* v, const u64* dbp, u64* out, cu
 int mask_pack(const Ctx& c, u32 J, const u64* v, const u64* w, const u64* db, u64* u,
               cudaStream_t st);
 
-// plans: valid_plan recomputes a plan (either kind) and compares it
+// the Answer on an unencrypted database: diagonals [J][2][B][L+K][N][giants]
+// (split layout) and their multiply-accumulate into y0 ([G][2][L+K][N], set 0
+// giant 0) and acc ([G][2 giants - 1][2][L+K][N], the other (set, giant))
+int build_db_diagonals(const Ctx& c, const pdq_plan& pl, const u32* values, u64* out,
+                       cudaStream_t st);
+int diag_mac_db(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dd, u64* y0, u64* acc,
+                cudaStream_t st);
+
+// plans: valid_plan recomputes a plan (any kind) and compares it
 bool valid_plan(const Ctx& c, const pdq_plan* pl);
 int plan_make_switched(const Ctx& c, u32 big_log_n, u64 n, u32 s, u32 B, pdq_plan* pl);
 inline u32 log2_exact(u32 x) {

@@ -48,7 +48,7 @@ class Info(ctypes.Structure):
 class Plan(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64)] + [(f, ctypes.c_uint32) for f in (
         "s", "s_prime", "B", "giants", "J", "H", "G_sz", "hpg", "G", "hclass", "per_out",
-        "n_out", "ring_ratio")]
+        "n_out", "ring_ratio", "plain_db")]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -92,6 +92,12 @@ _SIGS = {
     "pdq_rotate": (_I, [_P, _P, _U32, _U64, _P, _P, _P, _SZ, _P]),
     "pdq_plan_make": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_plan_make_switched": (_I, [_P, _U32, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
+    "pdq_plan_make_plain_db": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
+    "pdq_db_diagonals_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
+    "pdq_db_diagonals_build": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P]),
+    "pdq_answer_plain_db_workspace_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
+    "pdq_answer_plain_db": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _U32, _P, _P, _P, _SZ,
+                                 _P]),
     "pdq_ctx_create_subring": (_I, [_P, _U32, ctypes.POINTER(_P)]),
     "pdq_ring_switch_key_gen": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "pdq_ring_switch_workspace_bytes": (_SZ, [_P, _U32]),
@@ -230,6 +236,35 @@ class Context:
         pl = Plan()
         _check(load().pdq_plan_make_switched(self.h, big_log_n, n, s, B, ctypes.byref(pl)))
         return pl
+
+    def plan_plain_db(self, n: int, s: int, B: int = 0) -> Plan:
+        """pdq_plan_make_plain_db: the Answer on an unencrypted database."""
+        pl = Plan()
+        _check(load().pdq_plan_make_plain_db(self.h, n, s, B, ctypes.byref(pl)))
+        return pl
+
+    def db_diagonals(self, plan: Plan, values, stream=None) -> torch.Tensor:
+        """pdq_db_diagonals_build: database-specific diagonals and group masks."""
+        values = values.to(device="cuda", dtype=torch.int32).contiguous()
+        lib = load()
+        out = self._u64(lib.pdq_db_diagonals_bytes(self.h, ctypes.byref(plan)) // 8)
+        _check(lib.pdq_db_diagonals_build(self.h, ctypes.byref(plan), _ptr(values), _ptr(out),
+                                          _stream(stream)))
+        return out
+
+    def answer_plain_db_workspace(self, plan: Plan) -> torch.Tensor:
+        return self._ws(load().pdq_answer_plain_db_workspace_bytes(self.h, ctypes.byref(plan)))
+
+    def answer_plain_db(self, plan: Plan, v_cts, keys, galois, consts, ws=None, out=None,
+                        stream=None) -> torch.Tensor:
+        """pdq_answer_plain_db: the Answer without Mask, [C; C diag(DB)] v."""
+        ws = self.answer_plain_db_workspace(plan) if ws is None else ws
+        out = self._u64(plan.n_out * self.ct_elems) if out is None else out
+        gal = (ctypes.c_uint64 * len(galois))(*galois)
+        _check(load().pdq_answer_plain_db(self.h, ctypes.byref(plan), _ptr(v_cts), _ptr(keys),
+                                          ctypes.cast(gal, _P), len(galois), _ptr(consts),
+                                          _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+        return out.view(plan.n_out, 2, self.L, self.N)
 
     def ring_switch_key_gen(self, small: "Context", sk, s_small, a, e, stream=None) -> torch.Tensor:
         """pdq_ring_switch_key_gen: key from this ring's s to s_small(X^R)."""

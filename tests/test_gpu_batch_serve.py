@@ -117,3 +117,32 @@ def test_server_admission_limits(mix):
     for t in tickets:
         srv.wait(t)
     srv.close()
+
+
+def test_server_waits_run_out_and_recover(mix):
+    """A wait on a request still queued behind others runs out with
+    PDQ_E_TIMEOUT (the request itself is unaffected), a drain with no time
+    left does too, and a later wait returns the request's result, the same
+    as alone."""
+    pdq = library()
+    sets, alone = mix
+    ctx = sets[0].ctx
+    need = max(pdq.load().pdq_answer_workspace_bytes(ctx.h, st.plan) for st in sets)
+    arena = torch.empty(need + (1 << 20), dtype=torch.uint8, device="cuda")
+    srv = pdq.Server(arena, lanes=1)
+    handles = [(st.handle(), i) for _ in range(8) for i, st in enumerate(sets)]
+    tickets = [srv.submit(h) for h, _ in handles]
+    last = tickets[-1]
+    with pytest.raises(pdq.PdqError) as e:
+        srv.wait(last, timeout_ms=0)
+    assert e.value.code == pdq.PDQ_E_TIMEOUT
+    assert srv.status(last).state != pdq.PDQ_REQ_DONE
+    with pytest.raises(pdq.PdqError) as e:
+        srv.drain(timeout_ms=0)
+    assert e.value.code == pdq.PDQ_E_TIMEOUT
+    srv.wait(last)
+    srv.drain()
+    for t, (h, i) in zip(tickets, handles):
+        assert srv.status(t).status == 0
+        assert torch.equal(h.out.view(alone[i].shape), alone[i])
+    srv.close()
