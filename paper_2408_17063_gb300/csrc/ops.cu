@@ -1859,57 +1859,78 @@ namespace {
 // database is in them), so each is used by one thread (for both
 // polynomials) and streamed from DRAM once; the kernel is bound by that
 // stream.  Thread = position x, set sigma and GT giant steps of one group
-// and prime; its GT diagonal values are contiguous (giant index innermost)
-// and the rotated operands R (split layout) are shared through L1 by the
-// threads of the other sets and giant slices at the same position.
+// and prime; its GT diagonal values are contiguous (giant index innermost,
+// a warp reads one contiguous run) and the rotated operands R (split layout)
+// are shared through L2 with the threads of the other sets and giant slices.
+// Every thread streams its own operands through a private ring of kDbStages
+// shared-memory slots with asynchronous copies, kDbStages - 1 steps ahead
+// of its arithmetic (no block barrier: a thread reads only what it copied).
 // Output (sigma, g) = (0, 0) goes to y0[gamma][p], the others to
 // acc[gamma][sigma GI + g - 1][p].
+constexpr u32 kDbStages = 4;
+constexpr u32 kDbThreads = 256;
+
 template <int GT>
-__global__ void __launch_bounds__(256) k_diag_mac_db(const u64* __restrict__ R,
-                                                  const u64* __restrict__ Dd, u32 J, u32 jpg,
-                                                  u32 B, u32 GI, u32 GS, u32 E, u32 logN,
-                                                  const Mod* __restrict__ mods,
-                                                  const u64* __restrict__ ckar, u32 fold_one,
-                                                  u64* __restrict__ y0, u64* __restrict__ acc) {
+__global__ void __launch_bounds__(kDbThreads, 2) k_diag_mac_db(
+        const u64* __restrict__ R, const u64* __restrict__ Dd, u32 J, u32 jpg, u32 B, u32 GI,
+        u32 GS, u32 E, u32 logN, const Mod* __restrict__ mods, const u64* __restrict__ ckar,
+        u32 fold_one, u64* __restrict__ y0, u64* __restrict__ acc) {
+    constexpr u32 W = GT + 2;                        // words per thread and stage
+    extern __shared__ __align__(16) u64 sring[];     // [kDbStages][threads][W]
     const u64 N = 1ull << logN, EN = (u64)E << logN;
+    const u32 tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     const u64 x = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     const u32 sigma = threadIdx.y / GS, g0 = (threadIdx.y % GS) * GT;
     const u32 l = blockIdx.y, gamma = blockIdx.z;
-    if (x >= N) return;
+    const bool live = x < N;
+    const u64 loff = ((u64)l << logN) + (live ? x : 0);
+    const u64 j0 = (u64)gamma * jpg;
+    const u32 jn = (u32)(j0 >= J ? 0 : (J - j0 < jpg ? J - j0 : jpg));
+    const u32 steps = jn * B;
+    auto slot = [&](u32 st) { return sring + ((u64)(st % kDbStages) * nth + tid) * W; };
+    auto issue = [&](u32 st) {
+        if (st < steps) {
+            const u64 j = j0 + st / B, a = st % B;
+            u64* sl = slot(st);
+            const u64* dp = Dd + ((((j * 2 + sigma) * B + a) * E) << logN) * GI + loff * GI + g0;
+            if (GT >= 2) {
+#pragma unroll
+                for (int g = 0; g < GT; g += 2) cp_async16(sl + g, dp + g, live);
+            } else {
+                cp_async8(sl, dp);
+            }
+            const u64* rp = R + ((j * B + a) * 2) * EN + loff;
+            cp_async8(sl + GT, rp);
+            cp_async8(sl + GT + 1, rp + EN);
+        }
+        cp_async_commit();
+    };
     AccK A[2][GT];
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
         for (int g = 0; g < GT; ++g) A[p][g] = AccK{0, 0, 0, 0, 0, 0, 0, 0, 0};
-    const u64 loff = ((u64)l << logN) + x;
-    for (u32 jj = 0; jj < jpg; ++jj) {
-        const u64 j = (u64)gamma * jpg + jj;
-        if (j >= J) break;
-        for (u32 a = 0; a < B; ++a) {
-            const u64* rp = R + ((j * B + a) * 2) * EN + loff;
-            const u64 r0 = __ldg(rp), r1 = __ldg(rp + EN);
-            const u32 rl0 = (u32)r0, rh0 = (u32)(r0 >> 32), rs0 = rl0 + rh0;
-            const u32 rl1 = (u32)r1, rh1 = (u32)(r1 >> 32), rs1 = rl1 + rh1;
-            const u64* dp = Dd + ((((j * 2 + sigma) * B + a) * E) << logN) * GI + loff * GI + g0;
-            u64 d[GT];
-            if (GT >= 2) {
 #pragma unroll
-                for (int g = 0; g < GT; g += 2) {
-                    const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(dp + g));
-                    d[g] = v.x;
-                    d[g + 1] = v.y;
-                }
-            } else {
-                d[0] = __ldcs(dp);
-            }
+    for (u32 st = 0; st + 1 < kDbStages; ++st) issue(st);
+    for (u32 st = 0; st < steps; ++st) {
+        cp_async_wait<kDbStages - 2>();
+        const u64* sl = slot(st);
+        u64 d[GT];
 #pragma unroll
-            for (int g = 0; g < GT; ++g) {
-                const u32 d0 = (u32)d[g], d1 = (u32)(d[g] >> 32), ds = d0 + d1;
-                mack(A[0][g], rl0, rh0, rs0, d0, d1, ds);
-                mack(A[1][g], rl1, rh1, rs1, d0, d1, ds);
-            }
+        for (int g = 0; g < GT; ++g) d[g] = sl[g];
+        const u64 r0 = sl[GT], r1 = sl[GT + 1];
+        issue(st + kDbStages - 1);                   // refills the slot read last step
+        const u32 rl0 = (u32)r0, rh0 = (u32)(r0 >> 32), rs0 = rl0 + rh0;
+        const u32 rl1 = (u32)r1, rh1 = (u32)(r1 >> 32), rs1 = rl1 + rh1;
+#pragma unroll
+        for (int g = 0; g < GT; ++g) {
+            const u32 d0 = (u32)d[g], d1 = (u32)(d[g] >> 32), ds = d0 + d1;
+            mack(A[0][g], rl0, rh0, rs0, d0, d1, ds);
+            mack(A[1][g], rl1, rh1, rs1, d0, d1, ds);
         }
     }
+    cp_async_wait<0>();
+    if (!live) return;
     const Mod md = mods[l];
 #pragma unroll
     for (int g = 0; g < GT; ++g) {
@@ -1963,20 +1984,28 @@ int diag_mac_db(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dd, u
                 cudaStream_t st) {
     const u32 GI = pl.giants, E = c.L + c.K;
     const u32 GT = GI < 4 ? GI : 4, GS = GI / GT;
-    if (2 * GS > 256) return fail(PDQ_E_PARAM, "diag_mac_db: too many giant steps");
-    const u32 X = std::max(32u, 256u / (2 * GS));
+    if (2 * GS > kDbThreads / 32) return fail(PDQ_E_PARAM, "diag_mac_db: too many giant steps");
+    const u32 X = kDbThreads / (2 * GS);
     const u32 jpg = pl.hpg / 2;
     const u32 fold_one = (u64)std::min(jpg, pl.J) * pl.B <= 256 ? 1u : 0u;
     if (pl.G > 65535) return fail(PDQ_E_PARAM, "diag_mac_db: too many groups");
     const dim3 block(X, 2 * GS), grid((c.N + X - 1) / X, E, pl.G);
-#define PDQ_MACDB(T)                                                                                  k_diag_mac_db<T><<<grid, block, 0, st>>>(R, Dd, pl.J, jpg, pl.B, GI, GS, E, c.log_n, c.d_mods,                                             c.d_ckar, fold_one, y0, acc)
+    const size_t smem = (size_t)kDbStages * kDbThreads * (GT + 2) * sizeof(u64);
     switch (GT) {
-        case 1: PDQ_MACDB(1); break;
-        case 2: PDQ_MACDB(2); break;
-        case 4: PDQ_MACDB(4); break;
+        case 1:
+            k_diag_mac_db<1><<<grid, block, smem, st>>>(R, Dd, pl.J, jpg, pl.B, GI, GS, E, c.log_n,
+                                                        c.d_mods, c.d_ckar, fold_one, y0, acc);
+            break;
+        case 2:
+            k_diag_mac_db<2><<<grid, block, smem, st>>>(R, Dd, pl.J, jpg, pl.B, GI, GS, E, c.log_n,
+                                                        c.d_mods, c.d_ckar, fold_one, y0, acc);
+            break;
+        case 4:
+            k_diag_mac_db<4><<<grid, block, smem, st>>>(R, Dd, pl.J, jpg, pl.B, GI, GS, E, c.log_n,
+                                                        c.d_mods, c.d_ckar, fold_one, y0, acc);
+            break;
         default: return fail(PDQ_E_PARAM, "diag_mac_db: giant-step count must be a power of two");
     }
-#undef PDQ_MACDB
     return launched("k_diag_mac_db");
 }
 
