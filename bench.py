@@ -61,6 +61,9 @@ def parse():
                     help="also time the Answer on an unencrypted database (0: skip)")
     ap.add_argument("--plain-db-B", type=int, default=0,
                     help="baby-step count of the unencrypted-database plan (0: its cost rule)")
+    ap.add_argument("--tune", type=int, default=1,
+                    help="also run the batched mix with autotuned plans (0: skip)")
+    ap.add_argument("--tune-cache", default="", help="JSON file of tuned plans (read and written)")
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="served arrival rates, queries/s")
     ap.add_argument("--served-requests", type=int, default=2000)
@@ -222,7 +225,7 @@ class Mix:
     rotation keys (every element its queries of that ring need) all its
     queries share."""
 
-    def __init__(self, nq: int, lanes: int, clients: int = 0):
+    def __init__(self, nq: int, lanes: int, clients: int = 0, tuner=None):
         import numpy as np
         import torch
         import workloads as W
@@ -241,7 +244,10 @@ class Mix:
         consts = {}
         self.items = []
         self.clients = clients
-        plans = [self.ctx[q.log_n].plan(q.n, q.s) for q in self.specs]
+        # plans: the library's cost model, or the autotuner's timed choice
+        plans = [self.ctx[q.log_n].plan(q.n, q.s, tuner.best(self.ctx[q.log_n], q.n, q.s)
+                                        if tuner else 0) for q in self.specs]
+        self.tuned = tuner is not None
 
         def make_keys(ctx, sk, galois, seed):
             keys = ctx._u64(len(galois) * ctx.key_elems)
@@ -382,6 +388,15 @@ def run_batched(args, mix) -> dict:
     plain()
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
+    # device time of each query alone (events around each call)
+    qev = [torch.cuda.Event(enable_timing=True) for _ in range(len(mix.items) + 1)]
+    qev[0].record()
+    for i, (it, h) in enumerate(zip(mix.items, outs)):
+        it["ctx"].answer(it["plan"], it["v_cts"], mix.db[it["spec"].log_n], it["keys"],
+                         it["galois"], it["consts"], ws=ws_plain[it["spec"].log_n], out=h.out)
+        qev[i + 1].record()
+    torch.cuda.synchronize()
+    per_query = [qev[i].elapsed_time(qev[i + 1]) for i in range(len(mix.items))]
     nq = len(mix.items)
     return {"queries": nq, "rings": {str(1 << ln): len(v) for ln, v in by_ring.items()},
             "lanes_per_ring": {str(1 << ln): k for ln, k in lanes.items()}, "cuda_graph": True, "distinct_plan_constants": mix.n_consts,
@@ -389,6 +404,11 @@ def run_batched(args, mix) -> dict:
             "batched_ms_per_batch": 1000 * t_graph, "plain_ms_per_batch": 1000 * t_plain,
             "speedup": t_plain / t_graph, "all_decompress_exactly": bool(ok),
             "peak_device_gib": torch.cuda.max_memory_allocated() / 2**30,
+            "plans": "autotuned (timed choice of B per shape)" if mix.tuned else
+                     "the library's cost model",
+            "plain_ms_by_ring": {str(1 << ln): sum(per_query[i] for i, it in enumerate(mix.items)
+                                                   if it["spec"].log_n == ln)
+                                 for ln in by_ring},
             "mix": "64 queries, N uniform in {2^13, 2^14, 2^15}, log2 n uniform in 12..20, "
                    "s uniform in [1, min(1024, n/16)], "
                    + (f"{mix.clients} clients sharing secret and keys per ring" if mix.clients
@@ -965,6 +985,19 @@ def run_gpu(args, cfg, rank: int, world: int):
             torch.cuda.empty_cache()
             mix = Mix(args.mix, args.lanes, clients=args.clients)
             line["batched_shared_keys"] = dict(run_batched(args, mix), clients=args.clients)
+        if args.tune:
+            from paper_2408_17063_gb300 import tune
+            del mix
+            torch.cuda.empty_cache()
+            tuner = tune.PlanTuner(args.tune_cache or None, reps=2)
+            t0 = time.perf_counter()
+            mix = Mix(args.mix, args.lanes, tuner=tuner)
+            tune_s = time.perf_counter() - t0
+            res = run_batched(args, mix)
+            changed = {k: {"B": v["B"], "default_B": v["default_B"], "ms": v["ms"]}
+                       for k, v in tuner.cache.items() if v["B"] != v["default_B"]}
+            line["batched_tuned"] = dict(res, tuning_s=tune_s, shapes_tuned=len(tuner.cache),
+                                         shapes_changed=changed)
     if not args.no_cpu_baseline:
         from oracle import baseline
         line["cpu_baseline"] = baseline.baseline(cfg)

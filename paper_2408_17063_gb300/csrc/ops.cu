@@ -650,7 +650,11 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
     u64* Ds = sm;                       // [HC][ND][T]
     u64* Cs = Ds + HC * ND * T;         // [HC][T]: c0
     u64* C1s = Cs + HC * T;             // [HC][T]: c1 (for a = 0)
-    const u32 y0 = blockIdx.x * T, r = blockIdx.y, h0 = blockIdx.z * HC;
+    // the CTAs of one tile and limb (the ciphertext slices, which read the
+    // same key tiles) are consecutive in x, so the later ones find the keys
+    // in L2
+    const u32 zs = (H + HC - 1) / HC;
+    const u32 y0 = (blockIdx.x / zs) * T, r = blockIdx.y, h0 = (blockIdx.x % zs) * HC;
     const u64 EN = (u64)E << logN;
     const u32 nthreads = T * HC / CPT;
     constexpr u32 TP = T / 2;           // 16-byte chunks per row of a tile
@@ -1585,7 +1589,7 @@ int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* ke
         k_baby_ext<T, HC, CPT, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10);
     if (configured != cudaSuccess)
         return fail(PDQ_E_CUDA, std::string("k_baby_ext attribute: ") + cudaGetErrorString(configured));
-    const dim3 grid(c.N / T, E, (H + HC - 1) / HC);
+    const dim3 grid((c.N / T) * ((H + HC - 1) / HC), E);
     k_baby_ext<T, HC, CPT, ND><<<grid, T * HC / CPT, smem, st>>>(
         D, u, keys, H, B, c.log_n, E, ext ? E : c.L, ext ? E : c.L, c.d_mods,
         ext ? nullptr : c.d_P_mont, Rx, bp);
