@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--tune", type=int, default=1,
                     help="also run the batched mix with autotuned plans (0: skip)")
     ap.add_argument("--tune-cache", default="", help="JSON file of tuned plans (read and written)")
+    ap.add_argument("--rotation-budget-gib", type=float, default=2.0,
+                    help="also time the Answer holding at most this many GiB of baby-step "
+                         "rotations (0: skip)")
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="served arrival rates, queries/s")
     ap.add_argument("--served-requests", type=int, default=2000)
@@ -924,6 +927,36 @@ def run_gpu(args, cfg, rank: int, world: int):
     torch.cuda.synchronize()
     lat = sorted(lev[i].elapsed_time(lev[i + 1]) for i in range(args.latency_steps))
 
+    # the same Answer holding at most a budget of baby-step rotations (made and
+    # consumed a chunk of primes at a time): its workspace and time
+    budget_leg = None
+    if args.rotation_budget_gib > 0:
+        lib = pdq.load()
+        full_ws = lib.pdq_answer_workspace_bytes(ctx.h, plan)
+        ctx.set_rotation_budget(int(args.rotation_budget_gib * 2**30))
+        bws = ctx.answer_workspace(plan)
+        bout = ctx._u64(plan.n_out * ctx.ct_elems)
+
+        def bstep():
+            ctx.answer(plan, v_cts, db, keys, galois, consts, ws=bws, out=bout, stream=stream)
+
+        bstep()
+        torch.cuda.synchronize()
+        same = torch.equal(bout, out)
+        bev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        bev[0].record(stream)
+        for _ in range(args.steps):
+            bstep()
+        bev[1].record(stream)
+        torch.cuda.synchronize()
+        ctx.set_rotation_budget(0)
+        budget_leg = {"budget_gib": args.rotation_budget_gib,
+                      "workspace_gib": bws.numel() / 2**30, "full_workspace_gib": full_ws / 2**30,
+                      "ms_per_query": bev[0].elapsed_time(bev[1]) / args.steps,
+                      "same_bits_as_unbudgeted": bool(same)}
+        del bws, bout
+        torch.cuda.empty_cache()
+
     # end to end through the host-buffer entry point (pinned host buffers,
     # coefficient form, copies inside the timed region)
     e2e = None
@@ -961,6 +994,8 @@ def run_gpu(args, cfg, rank: int, world: int):
             "stages_ms_per_query": {k: v[0] / max(1, args.steps) for k, v in stages.items()},
             "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps,
             "clocks": clk, "e2e": e2e, "roofline": roofline}
+    if budget_leg:
+        line["rotation_budget"] = budget_leg
     if args.paper_shapes:
         line["paper_shapes"] = {
             "what": ("the paper's Table II/III shapes (ring 2^13, t=65537, 2x54-bit primes + one "

@@ -124,6 +124,17 @@ int pdq_ctx_info(const pdq_ctx* ctx, pdq_info* info);
  * NULL, owned by the library until the thread's next failing call). */
 const char* pdq_last_error(void);
 
+/* Memory of the baby-step rotations (Sec. 5.2: Rot(u_h; a), a < B, for every
+ * half-block, consumed by the diagonal products).  By default pdq_answer and
+ * pdq_comp hold all of them at once (at N = 2^15, n = 2^20, B = 32: 10 GiB
+ * of the 12.9 GiB workspace).  With a budget of `bytes` > 0 they are made
+ * and consumed a chunk of primes at a time (each prime's rotations and
+ * products are independent), holding at most max(bytes, one prime's
+ * rotations); the results are the same bits, and
+ * pdq_answer_workspace_bytes / pdq_comp_workspace_bytes shrink accordingly.
+ * Set it before sizing workspaces; not while a call on the context runs. */
+int pdq_ctx_set_rotation_budget(pdq_ctx* ctx, uint64_t bytes);
+
 /* ------------------------------------------------------------- transforms
  * Negacyclic transform of polynomials in Z_q[X]/(X^N+1) (the ring of
  * Sec. 5.1), in place on `count` groups of `nlimbs` limbs: group g, limb l is

@@ -234,6 +234,16 @@ struct CompLayout {
     u64 end;
 };
 
+// Primes of the baby-step rotations held at once: all of them, or as many
+// as the context's rotation budget allows (at least one).
+u32 rotation_chunk(const Ctx& c, const pdq_plan& pl) {
+    const u32 E = c.L + c.K;
+    if (c.rotation_budget == 0 || pl.B == 1 || !rotations_chunkable(c)) return E;
+    const u64 per_prime = (u64)pl.H * pl.B * 2 * c.N * sizeof(u64);
+    const u64 k = c.rotation_budget / per_prime;
+    return (u32)std::max<u64>(1, std::min<u64>(E, k));
+}
+
 CompLayout comp_layout(const Ctx& c, const pdq_plan& pl) {
     const u64 cts = ct_elems(c), ects = 2ull * (c.L + c.K) * c.N;
     const u64 G = pl.G, GI = pl.giants;
@@ -246,7 +256,8 @@ CompLayout comp_layout(const Ctx& c, const pdq_plan& pl) {
     CompLayout lo;
     lo.U = 0;
     lo.Rx = lo.U + (u64)pl.H * cts;
-    lo.accx = lo.Rx + std::max<u64>((u64)pl.H * pl.B, G * 8) * ects;
+    const u64 echunk = 2ull * rotation_chunk(c, pl) * c.N;
+    lo.accx = lo.Rx + std::max<u64>((u64)pl.H * pl.B * echunk, G * 8 * ects);
     lo.acc = lo.accx + G * (GI - 1) * ects;
     lo.yx = lo.acc + G * (GI - 1) * cts;
     lo.Y0 = lo.yx + G * ects;
@@ -371,8 +382,16 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     // 2. baby steps in the extended basis, the digits of every u_h raised once
     prof_mark(c, PDQ_STAGE_BABY, st);
     const CtSet u = ct_set(U, cts);
-    if (B == 1) PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * ects), true, st));
-    else {
+    // 3. diagonal multiply-accumulate over Q u P: the unrotated accumulators
+    // (g = 0) start the giant-step sums yx; of the others only c1 is lowered
+    // (into acc, [G][GI-1][L][N]), c0 stays in Q u P.  Steps 2 and 3 work
+    // prime by prime, so under a rotation budget they alternate on chunks of
+    // primes and only one chunk of rotations is held at a time.
+    if (B == 1) {
+        PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * ects), true, st));
+        prof_mark(c, PDQ_STAGE_MAC, st);
+        PDQ_TRY(diag_mac(c, pl, Rx, Dg, yx, accx, st));
+    } else {
         PDQ_TRY(ks_raise(c, u, H, rws, &D, st));
         std::vector<u64> koff(B, 0);
         for (u32 a = 1; a < B; ++a) {
@@ -380,13 +399,15 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
             PDQ_TRY(key_for(galois_rot(c, a), &kp));
             koff[a] = (u64)(kp - keys.base);
         }
-        PDQ_TRY(baby_steps_ext(c, D, u, H, B, keys.base, koff, Rx, st));
+        const u32 E = c.L + c.K, ec = rotation_chunk(c, pl);
+        for (u32 l0 = 0; l0 < E; l0 += ec) {
+            const u32 el = std::min(ec, E - l0);
+            if (l0 > 0) prof_mark(c, PDQ_STAGE_BABY, st);
+            PDQ_TRY(baby_steps_ext(c, D, u, H, B, keys.base, koff, Rx, st, l0, el));
+            prof_mark(c, PDQ_STAGE_MAC, st);
+            PDQ_TRY(diag_mac(c, pl, Rx, Dg, yx, accx, st, l0, el));
+        }
     }
-    // 3. diagonal multiply-accumulate over Q u P: the unrotated accumulators
-    // (g = 0) start the giant-step sums yx; of the others only c1 is lowered
-    // (into acc, [G][GI-1][L][N]), c0 stays in Q u P
-    prof_mark(c, PDQ_STAGE_MAC, st);
-    PDQ_TRY(diag_mac(c, pl, Rx, Dg, yx, accx, st));
     prof_mark(c, PDQ_STAGE_ACC_MODDOWN, st);
     const u64 EN = (u64)(c.L + c.K) * c.N, LN = (u64)c.L * c.N;
     if (GI > 1) PDQ_TRY(mod_down_polys(c, accx + EN, 2 * EN, G * (GI - 1), acc, LN, aws, st));
@@ -619,6 +640,12 @@ int pdq_mod_switch(const pdq_ctx* from, const pdq_ctx* to, const uint64_t* cts, 
     if (!cts || !out || !ws) return fail(PDQ_E_PARAM, "mod_switch: null buffer");
     if (ws_bytes < mod_switch_ws(a, count)) return fail(PDQ_E_NOMEM, "mod_switch: workspace too small");
     return mod_switch(a, b.L, cts, count, out, reinterpret_cast<u64*>(ws), (cudaStream_t)stream);
+}
+
+int pdq_ctx_set_rotation_budget(pdq_ctx* ctx, uint64_t bytes) {
+    if (!ctx) return fail(PDQ_E_PARAM, "null context");
+    reinterpret_cast<Ctx*>(ctx)->rotation_budget = bytes;
+    return PDQ_OK;
 }
 
 int pdq_plan_make(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B, pdq_plan* plan) {

@@ -638,7 +638,9 @@ template <int T, int HC, int CPT, int ND>
 __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
         const u64* __restrict__ D, CtSet u, const u64* __restrict__ keys, u32 H, u32 B, u32 logN,
         u32 E, u32 L, u32 c1_limb, const Mod* __restrict__ mods, const u64* __restrict__ Pm,
-        u64* __restrict__ Rx, const BabyParams bp) {
+        u64* __restrict__ Rx, const BabyParams bp, u32 l0, u32 ER) {
+    // Limbs l0 .. l0 + gridDim.y - 1 of the outputs, written to Rx as limbs
+    // 0 .. of [..][2][ER][N] (a chunk of primes at a time).
     // L: limbs of c0 (L for ciphertexts over Q, whose c0 joins as P c0 with
     // Pm = P R; L + K for ciphertexts over Q u P, Pm == nullptr: c0 joins as
     // c0 R, and a = 0 is the input itself); c1 starts at limb c1_limb
@@ -650,12 +652,8 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
     u64* Ds = sm;                       // [HC][ND][T]
     u64* Cs = Ds + HC * ND * T;         // [HC][T]: c0
     u64* C1s = Cs + HC * T;             // [HC][T]: c1 (for a = 0)
-    // the CTAs of one tile and limb (the ciphertext slices, which read the
-    // same key tiles) are consecutive in x, so the later ones find the keys
-    // in L2
-    const u32 zs = (H + HC - 1) / HC;
-    const u32 y0 = (blockIdx.x / zs) * T, r = blockIdx.y, h0 = (blockIdx.x % zs) * HC;
-    const u64 EN = (u64)E << logN;
+    const u32 y0 = blockIdx.x * T, r = l0 + blockIdx.y, h0 = blockIdx.z * HC;
+    const u64 EN = (u64)E << logN, ERN = (u64)ER << logN;
     const u32 nthreads = T * HC / CPT;
     constexpr u32 TP = T / 2;           // 16-byte chunks per row of a tile
 
@@ -712,9 +710,9 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
             v1 = redc128(hi, lo, md);
             Cs[ct * T + xi] = v0;
         }
-        u64* o = Rx + ((u64)h * B * 2) * EN + ((u64)r << logN) + y0 + xi;
+        u64* o = Rx + ((u64)h * B * 2) * ERN + ((u64)(r - l0) << logN) + y0 + xi;
         o[0] = split30(v0);
-        o[EN] = split30(v1);
+        o[ERN] = split30(v1);
     }
     // The rotations take Karatsuba sums of the 30-bit halves (at most 8
     // digit-key products per output): the digit tile goes to the split layout
@@ -751,9 +749,9 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
             if (r < L) v0 = addmod(v0, Cs[ct * T + y], md.q);     // + P sigma(c0)
             kara_value(s1, hi, lo);
             const u64 v1 = redc128(hi, lo, md);
-            u64* o = Rx + (((u64)h * B + a) * 2) * EN + ((u64)r << logN) + xc;
+            u64* o = Rx + (((u64)h * B + a) * 2) * ERN + ((u64)(r - l0) << logN) + xc;
             o[0] = split30(v0);
-            o[EN] = split30(v1);
+            o[ERN] = split30(v1);
         }
 #pragma unroll
         for (int b = 0; b < ND; ++b) { kc[b][0] = kn[b][0]; kc[b][1] = kn[b][1]; }
@@ -996,6 +994,7 @@ __device__ __forceinline__ u64 fold1(const AccK& A, const Mod& md) {
 
 struct MacArgs {
     u32 G, hpg, H, B, GI, E, logN;
+    u32 l0, ER;                    // primes l0 .. of this launch; R holds ER primes from l0
     u32 logX, logGS, logGI, CPC;   // CPC: combinations per CTA (even)
     u32 tiles_per_cta, achunks;
     u32 fold_one;                  // at most 256 products per output: fold1
@@ -1010,7 +1009,7 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
                                                   u64* __restrict__ acc) {
     extern __shared__ __align__(16) u64 smem[];
     const u32 X = 1u << a.logX, GI = a.GI, GIp = GI + 2, CPC = a.CPC;
-    const u32 l = blockIdx.y;
+    const u32 l = a.l0 + blockIdx.y;
     // position in the low thread bits: the 8 threads of a quarter-warp read
     // the diagonal rows of 8 positions (row stride GI + 2 words), whose
     // 16-byte loads fall in distinct banks, and write 8 consecutive outputs
@@ -1064,7 +1063,7 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
             const u32 gm = combo >> 1, p = combo & 1;
             const u32 h = gm * a.hpg + hh;
             const bool valid = gm < a.G && h < a.H;
-            const u64* src = R + ((((u64)(valid ? h : 0) * a.B + a0 + ai) * 2 + p) * a.E + l) * N +
+            const u64* src = R + ((((u64)(valid ? h : 0) * a.B + a0 + ai) * 2 + p) * a.ER + l - a.l0) * N +
                              x0 + 2 * xp;
             cp_async16(Rt + cb * RB + ai * X + 2 * xp, src, valid);
         }
@@ -1579,7 +1578,7 @@ namespace {
 
 template <int ND>
 int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
-                const BabyParams& bp, u64* Rx, cudaStream_t st, bool ext) {
+                const BabyParams& bp, u64* Rx, cudaStream_t st, bool ext, u32 l0, u32 el) {
     constexpr u32 T = 64, HC = 16, CPT = 8;
     const u32 E = c.L + c.K;
     const size_t smem = ((size_t)HC * ND * T + 2 * HC * T) * sizeof(u64);
@@ -1589,27 +1588,34 @@ int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* ke
         k_baby_ext<T, HC, CPT, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10);
     if (configured != cudaSuccess)
         return fail(PDQ_E_CUDA, std::string("k_baby_ext attribute: ") + cudaGetErrorString(configured));
-    const dim3 grid((c.N / T) * ((H + HC - 1) / HC), E);
+    const dim3 grid(c.N / T, el, (H + HC - 1) / HC);
     k_baby_ext<T, HC, CPT, ND><<<grid, T * HC / CPT, smem, st>>>(
         D, u, keys, H, B, c.log_n, E, ext ? E : c.L, ext ? E : c.L, c.d_mods,
-        ext ? nullptr : c.d_P_mont, Rx, bp);
+        ext ? nullptr : c.d_P_mont, Rx, bp, l0, el);
     return launched("k_baby_ext");
 }
 
 }  // namespace
 
 int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
-                   const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st) {
+                   const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st, u32 l0,
+                   u32 el) {
     std::vector<u64> galois(B, 1);
     for (u32 a = 1; a < B; ++a) galois[a] = host_powmod(3, a, 2ull * c.N);
-    return hoisted_rotations_ext(c, D, u, H, B, galois, keys, key_offsets, Rx, st, false);
+    return hoisted_rotations_ext(c, D, u, H, B, galois, keys, key_offsets, Rx, st, false, l0, el);
 }
+
+bool rotations_chunkable(const Ctx& c) { return c.N >= 64 && c.ndigits <= 8; }
 
 int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
                           const std::vector<u64>& galois, const u64* keys,
                           const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st,
-                          bool ext) {
+                          bool ext, u32 l0, u32 el) {
     constexpr u32 T = 64;
+    const u32 E = c.L + c.K;
+    if (el == 0) el = E - l0;
+    if (l0 + el > E || (el != E && !rotations_chunkable(c)))
+        return fail(PDQ_E_PARAM, "hoisted rotations: bad prime range");
     if (B > 128) return fail(PDQ_E_PARAM, "hoisted rotations: at most 128");
     if (galois.size() < B || key_offsets.size() < B)
         return fail(PDQ_E_PARAM, "hoisted rotations: one Galois element and key per rotation");
@@ -1635,14 +1641,14 @@ int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
         bp.koff[a] = key_offsets[a];
     }
     switch (c.ndigits) {
-        case 1: return launch_baby<1>(c, D, u, H, B, keys, bp, Rx, st, ext);
-        case 2: return launch_baby<2>(c, D, u, H, B, keys, bp, Rx, st, ext);
-        case 3: return launch_baby<3>(c, D, u, H, B, keys, bp, Rx, st, ext);
-        case 4: return launch_baby<4>(c, D, u, H, B, keys, bp, Rx, st, ext);
-        case 5: return launch_baby<5>(c, D, u, H, B, keys, bp, Rx, st, ext);
-        case 6: return launch_baby<6>(c, D, u, H, B, keys, bp, Rx, st, ext);
-        case 7: return launch_baby<7>(c, D, u, H, B, keys, bp, Rx, st, ext);
-        default: return launch_baby<8>(c, D, u, H, B, keys, bp, Rx, st, ext);
+        case 1: return launch_baby<1>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
+        case 2: return launch_baby<2>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
+        case 3: return launch_baby<3>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
+        case 4: return launch_baby<4>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
+        case 5: return launch_baby<5>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
+        case 6: return launch_baby<6>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
+        case 7: return launch_baby<7>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
+        default: return launch_baby<8>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
     }
 }
 
@@ -1801,7 +1807,7 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN) {
 
 template <int GT, int BC>
 int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R, const u64* Dg,
-               u64* acc0, u64* acc, cudaStream_t st) {
+               u64* acc0, u64* acc, cudaStream_t st, u32 l0, u32 el) {
     static const cudaError_t configured = cudaFuncSetAttribute(
         k_diag_mac<GT, BC, kMacPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMacSmem);
     if (configured != cudaSuccess)
@@ -1813,6 +1819,8 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
     a.B = pl.B;
     a.GI = pl.giants;
     a.E = c.L + c.K;
+    a.l0 = l0;
+    a.ER = el;
     a.logN = c.log_n;
     a.logX = s.logX;
     a.logGS = s.logGS;
@@ -1821,7 +1829,7 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
     a.tiles_per_cta = s.tiles_per_cta;
     a.achunks = pl.B / BC;
     a.fold_one = (u64)std::min(pl.hpg, pl.H) * pl.B <= 256 ? 1u : 0u;
-    const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, a.E, s.zslices);
+    const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, el, s.zslices);
     k_diag_mac<GT, BC, kMacPC><<<grid, s.threads, s.smem, st>>>(R, Dg, a, c.d_mods, c.d_ckar, acc0,
                                                                  acc);
     return launched("k_diag_mac");
@@ -1829,13 +1837,13 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
 
 template <int GT>
 int launch_mac_bc(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R,
-                  const u64* Dg, u64* acc0, u64* acc, cudaStream_t st) {
+                  const u64* Dg, u64* acc0, u64* acc, cudaStream_t st, u32 l0, u32 el) {
     switch (s.Bc) {
-        case 1: return launch_mac<GT, 1>(c, pl, s, R, Dg, acc0, acc, st);
-        case 2: return launch_mac<GT, 2>(c, pl, s, R, Dg, acc0, acc, st);
-        case 4: return launch_mac<GT, 4>(c, pl, s, R, Dg, acc0, acc, st);
-        case 8: return launch_mac<GT, 8>(c, pl, s, R, Dg, acc0, acc, st);
-        case 16: return launch_mac<GT, 16>(c, pl, s, R, Dg, acc0, acc, st);
+        case 1: return launch_mac<GT, 1>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
+        case 2: return launch_mac<GT, 2>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
+        case 4: return launch_mac<GT, 4>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
+        case 8: return launch_mac<GT, 8>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
+        case 16: return launch_mac<GT, 16>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
         default: return fail(PDQ_E_PARAM, "diag_mac: baby-step count must be a power of two");
     }
 }
@@ -1843,14 +1851,16 @@ int launch_mac_bc(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64
 }  // namespace
 
 int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc0, u64* acc,
-             cudaStream_t st) {
+             cudaStream_t st, u32 l0, u32 el) {
     const MacShape s = mac_shape(pl, c.log_n);
+    if (el == 0) el = c.L + c.K - l0;
+    if (l0 + el > c.L + c.K) return fail(PDQ_E_PARAM, "diag_mac: bad prime range");
     if (s.zslices > 65535) return fail(PDQ_E_PARAM, "diag_mac: too many groups");
     if (s.logX < 1 || s.smem > kMacSmem) return fail(PDQ_E_PARAM, "diag_mac: plan too large for one tile");
     switch (s.GT) {
-        case 1: return launch_mac_bc<1>(c, pl, s, R, Dg, acc0, acc, st);
-        case 2: return launch_mac_bc<2>(c, pl, s, R, Dg, acc0, acc, st);
-        case 4: return launch_mac_bc<4>(c, pl, s, R, Dg, acc0, acc, st);
+        case 1: return launch_mac_bc<1>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
+        case 2: return launch_mac_bc<2>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
+        case 4: return launch_mac_bc<4>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
         default: return fail(PDQ_E_PARAM, "diag_mac: giant-step count must be a power of two");
     }
 }

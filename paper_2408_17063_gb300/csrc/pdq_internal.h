@@ -177,6 +177,10 @@ struct Ctx {
     };
     mutable Lanes lanes;
     mutable std::mutex lanes_mu;
+    // bytes of baby-step rotations the Answer holds at once (0: all of
+    // them); smaller budgets produce and consume them a chunk of primes at a
+    // time (pdq_ctx_set_rotation_budget)
+    u64 rotation_budget = 0;
 };
 
 void lanes_release(Ctx* c);

@@ -112,9 +112,14 @@ int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, c
                  CtSet out, bool accumulate, bool split, cudaStream_t st, bool c0_ext = false);
 // All baby-step rotations a = 0..B-1 of the H ciphertexts u (raised digits
 // D; a = 0 is (P c0, P c1)) written to Rx[h][a] in the split operand layout;
-// key a at keys + key_offsets[a] (B >= 2)
+// key a at keys + key_offsets[a] (B >= 2).  Only the primes l0 .. l0+el-1
+// (el = 0: to the last), stored as Rx [H][B][2][el][N] (a chunk of primes).
 int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
-                   const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st);
+                   const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st, u32 l0 = 0,
+                   u32 el = 0);
+// whether the hoisted rotations can run on a chunk of primes (their fused
+// kernel applies)
+bool rotations_chunkable(const Ctx& c);
 // The same for any Galois elements: Rx[h][a] = sigma_{galois[a]}(u_h) with
 // key a (a = 1..B-1; a = 0 is (P c0, P c1)), split operand layout.  With
 // `ext` the u_h are over Q u P ([2][L+K][N], D raised from their lowered c1):
@@ -122,7 +127,7 @@ int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64*
 int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
                           const std::vector<u64>& galois, const u64* keys,
                           const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st,
-                          bool ext = false);
+                          bool ext = false, u32 l0 = 0, u32 el = 0);
 // out[h] = sum_{a<R} Rx[h][a] (Rx [cnt][R][2][L+K][N] split, out [cnt][2][L+K][N]
 // canonical), R <= 8
 int sum_rotations(const Ctx& c, const u64* Rx, u32 cnt, u32 R, u64* out, cudaStream_t st);
@@ -147,9 +152,11 @@ int mod_down_polys(const Ctx& c, const u64* A, u64 a_stride, u32 npolys, u64* ou
 int gather_rows(CtSet src, long long src_off, u32 cnt, u64 len, u64* dst, u64 dst_stride,
                 cudaStream_t st);
 // R and Dg in the split operand layout; outputs canonical over Q u P:
-// giant index 0 to acc0 [G][2][L+K][N], the others to acc [G][giants-1][2][L+K][N]
+// giant index 0 to acc0 [G][2][L+K][N], the others to acc [G][giants-1][2][L+K][N].
+// Only the primes l0 .. l0+el-1 (el = 0: to the last); R holds those primes
+// ([H][B][2][el][N]).
 int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc0, u64* acc,
-             cudaStream_t st);
+             cudaStream_t st, u32 l0 = 0, u32 el = 0);
 int ct_add(const Ctx& c, CtSet y, CtSet x, u32 cnt, cudaStream_t st);
 int group_combine(const Ctx& c, const pdq_plan& pl, const u64* y, const u64* masks, u64* out,
                   cudaStream_t st);

@@ -90,6 +90,7 @@ _SIGS = {
     "pdq_mod_switch": (_I, [_P, _P, _P, _U32, _P, _P, _SZ, _P]),
     "pdq_rotate_workspace_bytes": (_SZ, [_P, _U32]),
     "pdq_rotate": (_I, [_P, _P, _U32, _U64, _P, _P, _P, _SZ, _P]),
+    "pdq_ctx_set_rotation_budget": (_I, [_P, _U64]),
     "pdq_plan_make": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_plan_make_switched": (_I, [_P, _U32, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_plan_make_plain_db": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
@@ -222,6 +223,11 @@ class Context:
     @classmethod
     def from_config(cls, cfg) -> "Context":
         return cls(cfg.log_n, cfg.t, cfg.prime_bits, cfg.L, cfg.K, cfg.dnum)
+
+    def set_rotation_budget(self, nbytes: int):
+        """pdq_ctx_set_rotation_budget: hold at most nbytes of baby-step
+        rotations (0: all), made and consumed a chunk of primes at a time."""
+        _check(load().pdq_ctx_set_rotation_budget(self.h, int(nbytes)))
 
     def subring(self, log_n: int) -> "Context":
         """pdq_ctx_create_subring: the subring of dimension 2^log_n on this
