@@ -638,9 +638,9 @@ template <int T, int HC, int CPT, int ND>
 __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
         const u64* __restrict__ D, CtSet u, const u64* __restrict__ keys, u32 H, u32 B, u32 logN,
         u32 E, u32 L, u32 c1_limb, const Mod* __restrict__ mods, const u64* __restrict__ Pm,
-        u64* __restrict__ Rx, const BabyParams bp, u32 l0, u32 ER) {
-    // Limbs l0 .. l0 + gridDim.y - 1 of the outputs, written to Rx as limbs
-    // 0 .. of [..][2][ER][N] (a chunk of primes at a time).
+        u64* __restrict__ Rx, const BabyParams bp, u32 ER) {
+    // Rx holds ER limbs per polynomial ([..][2][ER][N]): a chunk of primes
+    // when the caller advanced every other pointer to the chunk's first prime.
     // L: limbs of c0 (L for ciphertexts over Q, whose c0 joins as P c0 with
     // Pm = P R; L + K for ciphertexts over Q u P, Pm == nullptr: c0 joins as
     // c0 R, and a = 0 is the input itself); c1 starts at limb c1_limb
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
     u64* Ds = sm;                       // [HC][ND][T]
     u64* Cs = Ds + HC * ND * T;         // [HC][T]: c0
     u64* C1s = Cs + HC * T;             // [HC][T]: c1 (for a = 0)
-    const u32 y0 = blockIdx.x * T, r = l0 + blockIdx.y, h0 = blockIdx.z * HC;
+    const u32 y0 = blockIdx.x * T, r = blockIdx.y, h0 = blockIdx.z * HC;
     const u64 EN = (u64)E << logN, ERN = (u64)ER << logN;
     const u32 nthreads = T * HC / CPT;
     constexpr u32 TP = T / 2;           // 16-byte chunks per row of a tile
@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
             v1 = redc128(hi, lo, md);
             Cs[ct * T + xi] = v0;
         }
-        u64* o = Rx + ((u64)h * B * 2) * ERN + ((u64)(r - l0) << logN) + y0 + xi;
+        u64* o = Rx + ((u64)h * B * 2) * ERN + ((u64)r << logN) + y0 + xi;
         o[0] = split30(v0);
         o[ERN] = split30(v1);
     }
@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
             if (r < L) v0 = addmod(v0, Cs[ct * T + y], md.q);     // + P sigma(c0)
             kara_value(s1, hi, lo);
             const u64 v1 = redc128(hi, lo, md);
-            u64* o = Rx + (((u64)h * B + a) * 2) * ERN + ((u64)(r - l0) << logN) + xc;
+            u64* o = Rx + (((u64)h * B + a) * 2) * ERN + ((u64)r << logN) + xc;
             o[0] = split30(v0);
             o[ERN] = split30(v1);
         }
@@ -994,7 +994,7 @@ __device__ __forceinline__ u64 fold1(const AccK& A, const Mod& md) {
 
 struct MacArgs {
     u32 G, hpg, H, B, GI, E, logN;
-    u32 l0, ER;                    // primes l0 .. of this launch; R holds ER primes from l0
+    u32 ER;                        // primes per polynomial in R (a chunk, or E)
     u32 logX, logGS, logGI, CPC;   // CPC: combinations per CTA (even)
     u32 tiles_per_cta, achunks;
     u32 fold_one;                  // at most 256 products per output: fold1
@@ -1009,7 +1009,7 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
                                                   u64* __restrict__ acc) {
     extern __shared__ __align__(16) u64 smem[];
     const u32 X = 1u << a.logX, GI = a.GI, GIp = GI + 2, CPC = a.CPC;
-    const u32 l = a.l0 + blockIdx.y;
+    const u32 l = blockIdx.y;
     // position in the low thread bits: the 8 threads of a quarter-warp read
     // the diagonal rows of 8 positions (row stride GI + 2 words), whose
     // 16-byte loads fall in distinct banks, and write 8 consecutive outputs
@@ -1063,7 +1063,7 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
             const u32 gm = combo >> 1, p = combo & 1;
             const u32 h = gm * a.hpg + hh;
             const bool valid = gm < a.G && h < a.H;
-            const u64* src = R + ((((u64)(valid ? h : 0) * a.B + a0 + ai) * 2 + p) * a.ER + l - a.l0) * N +
+            const u64* src = R + ((((u64)(valid ? h : 0) * a.B + a0 + ai) * 2 + p) * a.ER + l) * N +
                              x0 + 2 * xp;
             cp_async16(Rt + cb * RB + ai * X + 2 * xp, src, valid);
         }
@@ -1588,10 +1588,17 @@ int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* ke
         k_baby_ext<T, HC, CPT, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10);
     if (configured != cudaSuccess)
         return fail(PDQ_E_CUDA, std::string("k_baby_ext attribute: ") + cudaGetErrorString(configured));
+    // the chunk of primes l0 .. l0+el-1: every per-prime pointer advanced to l0
+    const u32 nc0 = ext ? E : c.L;                   // limbs of c0 (from limb 0)
+    const u64 off = (u64)l0 * c.N;
+    CtSet uc = u;
+    uc.base = u.base + off;
+    BabyParams bpc = bp;
+    for (u32 a = 1; a < B; ++a) bpc.koff[a] += off;
     const dim3 grid(c.N / T, el, (H + HC - 1) / HC);
     k_baby_ext<T, HC, CPT, ND><<<grid, T * HC / CPT, smem, st>>>(
-        D, u, keys, H, B, c.log_n, E, ext ? E : c.L, ext ? E : c.L, c.d_mods,
-        ext ? nullptr : c.d_P_mont, Rx, bp, l0, el);
+        D + off, uc, keys, H, B, c.log_n, E, nc0 > l0 ? nc0 - l0 : 0, nc0, c.d_mods + l0,
+        ext ? nullptr : c.d_P_mont + l0, Rx, bpc, el);
     return launched("k_baby_ext");
 }
 
@@ -1819,7 +1826,6 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
     a.B = pl.B;
     a.GI = pl.giants;
     a.E = c.L + c.K;
-    a.l0 = l0;
     a.ER = el;
     a.logN = c.log_n;
     a.logX = s.logX;
@@ -1830,8 +1836,11 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
     a.achunks = pl.B / BC;
     a.fold_one = (u64)std::min(pl.hpg, pl.H) * pl.B <= 256 ? 1u : 0u;
     const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, el, s.zslices);
-    k_diag_mac<GT, BC, kMacPC><<<grid, s.threads, s.smem, st>>>(R, Dg, a, c.d_mods, c.d_ckar, acc0,
-                                                                 acc);
+    // the chunk of primes l0 .. l0+el-1: per-prime pointers advanced to l0
+    const u64 off = (u64)l0 * c.N;
+    k_diag_mac<GT, BC, kMacPC><<<grid, s.threads, s.smem, st>>>(R, Dg + off * pl.giants, a,
+                                                                 c.d_mods + l0, c.d_ckar + 8 * l0,
+                                                                 acc0 + off, acc + off);
     return launched("k_diag_mac");
 }
 
