@@ -18,7 +18,7 @@ def brv(x, bits):
     return int(format(x, f"0{bits}b")[::-1], 2) if bits else 0
 
 
-@pytest.fixture(scope="module", params=SMALL + ["c2", "paper"])
+@pytest.fixture(scope="module", params=SMALL + ["c2", "paper", "tiny40"])
 def setup(request):
     return Setup(request.param)
 

@@ -64,6 +64,8 @@ CONFIGS = {
     # the ring and modulus of the paper's experiments (2^13, t = 65537, two
     # 54-bit primes; one special prime of the same size), Table III's n = 2^13
     "paper": Config("paper", 13, 65537, 54, 2, 1, 2, 1 << 13, 16, "uniform", 0x2408),
+    # 40-bit primes: far from a power of two (the library's generic reduction)
+    "tiny40": Config("tiny40", 6, 12289, 40, 3, 2, 2, 200, 5, "uniform", 0x75),
 }
 
 
