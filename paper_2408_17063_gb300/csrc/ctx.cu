@@ -12,6 +12,8 @@
 #include <atomic>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pdq_internal.h"
 
 namespace pdq {
@@ -39,9 +41,23 @@ int launched(const char* where) {
     return cuda_check(where);
 }
 
+// Stage names of the NVTX ranges (the order of PDQ_STAGE_*).
+static const char* const kStageNames[PDQ_NSTAGES] = {"mask", "pack", "baby", "mac",
+                                                     "giant", "rotsum", "combine", "acc_moddown"};
+
 void prof_mark(const Ctx& c, int stage, cudaStream_t st) {
     Ctx::Prof& p = c.prof;
     if (!p.on) return;
+    // an NVTX range per stage on the calling thread, so that profilers can
+    // select a stage's launches (e.g. ncu --nvtx-include "timed/mac/")
+    if (p.nvtx_open) {
+        nvtxRangePop();
+        p.nvtx_open = false;
+    }
+    if (stage >= 0 && stage < PDQ_NSTAGES) {
+        nvtxRangePushA(kStageNames[stage]);
+        p.nvtx_open = true;
+    }
     if (p.used == p.ev.size()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;

@@ -164,6 +164,7 @@ struct Ctx {
     // stage profiling: events recorded on the caller's stream when enabled
     struct Prof {
         bool on = false;
+        bool nvtx_open = false;
         std::vector<cudaEvent_t> ev;
         std::vector<int> stage;
         size_t used = 0;
