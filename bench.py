@@ -492,8 +492,8 @@ MAC_CEILING_MEASURED = 2.35e12
 # dram__bytes_write.sum) on the same plan (B=32, 8 giant steps) with 3 primes
 # (L=2, K=1), scaled by 10/3 to the 10 primes of Q u P (every CTA works on
 # one prime); None when the kernel has changed since the capture.  Capture:
-# 4.060 GB read + 0.212 GB written per launch with 3 primes.
-MAC_TRAFFIC_BYTES = round((4.059733e9 + 0.212181e9) * 10 / 3)
+# 4.065 GB read + 0.214 GB written per launch with 3 primes.
+MAC_TRAFFIC_BYTES = round((4.064706e9 + 0.213533e9) * 10 / 3)
 MAC_TRAFFIC_PLAN = (2**15, 10, 64, 32, 8)       # N, primes, H, B, giant steps
 
 
