@@ -424,14 +424,18 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
         c1all.inner = (long long)(GI - 1) * LN;       // gamma
         PDQ_TRY(ks_raise(c, c1all, G * (GI - 1), rws, &D, st, 0));
     }
-    const u64 dstride = (u64)c.ndigits * (c.L + c.K) * c.N;
-    for (u32 g = 1; g < GI; ++g) {
-        const u64 k = galois_rot(c, (long long)g * B);
-        const u64* kp;
-        PDQ_TRY(key_for(k, &kp));
-        const CtSet c0s = ct_set(accx + (u64)(g - 1) * ects, (long long)(GI - 1) * ects);
-        PDQ_TRY(ks_apply_ext(c, D + (u64)(g - 1) * G * dstride, c0s, G, (u32)k, kp,
-                             ct_set(yx, ects), true, false, st, true));
+    // all giant steps in one launch: term g - 1 rotates accumulator g of
+    // every group (c0 over Q u P at accx[gamma][g - 1]) into yx[gamma]
+    if (GI > 1) {
+        std::vector<u64> gal(GI - 1), koff(GI - 1);
+        for (u32 g = 1; g < GI; ++g) {
+            gal[g - 1] = galois_rot(c, (long long)g * B);
+            const u64* kp;
+            PDQ_TRY(key_for(gal[g - 1], &kp));
+            koff[g - 1] = (u64)(kp - keys.base);
+        }
+        PDQ_TRY(ks_apply_giants(c, D, G, GI - 1, gal.data(), keys.base, koff.data(), accx,
+                                (u64)ects, (u64)(GI - 1) * ects, yx, (u64)ects, st));
     }
     PDQ_TRY(rotsum_and_combine(c, pl, keys, yx, Rx, Y0, Y1, rws, aws, masks, out, st));
     prof_mark(c, -1, st);
@@ -525,16 +529,20 @@ int answer_plain_db_run(const Ctx& c, const pdq_plan& pl, const u64* v_cts, cons
         c1all.inner = (long long)NA * LN;
         PDQ_TRY(ks_raise(c, c1all, G * NA, rws, &D, st, 0));
     }
-    const u64 dstride = (u64)c.ndigits * (c.L + c.K) * c.N;
-    for (u32 i = 0; i < NA; ++i) {
-        const u32 sigma = (i + 1) / GI, g = (i + 1) % GI;
-        u64 k = galois_rot(c, (long long)g * B);
-        if (sigma) k = k * (2ull * c.N - 1) % (2ull * c.N);
-        const u64* kp = keys.find(k);
-        if (!kp) return fail(PDQ_E_KEY, "answer_plain_db: missing rotation key for Galois element " + std::to_string(k));
-        const CtSet c0s = ct_set(accx + (u64)i * ects, (long long)NA * ects);
-        PDQ_TRY(ks_apply_ext(c, D + (u64)i * G * dstride, c0s, G, (u32)k, kp, ct_set(yx, ects),
-                             true, false, st, true));
+    // every (set, giant) term in one launch
+    if (NA > 0) {
+        std::vector<u64> gal(NA), koff(NA);
+        for (u32 i = 0; i < NA; ++i) {
+            const u32 sigma = (i + 1) / GI, g = (i + 1) % GI;
+            u64 k = galois_rot(c, (long long)g * B);
+            if (sigma) k = k * (2ull * c.N - 1) % (2ull * c.N);
+            const u64* kp = keys.find(k);
+            if (!kp) return fail(PDQ_E_KEY, "answer_plain_db: missing rotation key for Galois element " + std::to_string(k));
+            gal[i] = k;
+            koff[i] = (u64)(kp - keys.base);
+        }
+        PDQ_TRY(ks_apply_giants(c, D, G, NA, gal.data(), keys.base, koff.data(), accx, (u64)ects,
+                                (u64)NA * ects, yx, (u64)ects, st));
     }
     // 4. rotate-and-sum and group masks
     PDQ_TRY(rotsum_and_combine(c, pl, keys, yx, Rx, base + lo.Y0, base + lo.Y1, rws, aws, masks,

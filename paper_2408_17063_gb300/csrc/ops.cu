@@ -581,6 +581,66 @@ __global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict_
     *o1 = make_ulonglong2(a1, b1);
 }
 
+// Galois elements and key offsets of the terms of one giant-step launch
+struct GiantTerms {
+    u64 koff[kMaxGiantTerms];   // element offset of term i's key in the key buffer
+    u32 galois[kMaxGiantTerms];
+};
+
+// Every giant step of the BSGS sum in one launch, in the extended basis: for
+// ciphertext ct (a record group), limb r < E, position x (two per thread)
+//   out[ct][p][r][x] += sum_i ( sum_beta D_i[ct][beta][r][s_i(x)] key_i[beta][p][r][x]
+//                               + [p = 0] c0_i[ct][r][s_i(x)] )
+// with s_i = sigma_{galois_i}, c0 over Q u P and the raised digits carrying R.
+// Each term is reduced once (Montgomery) and the reduced terms added mod q,
+// so the result equals the one-launch-per-term accumulation bit for bit.
+// Record groups are the fastest grid index: the groups at a position run
+// together and read each term's key there once from DRAM.
+__global__ void k_ks_giants(const u64* __restrict__ D, u64 d_term, u64 d_ct,
+                            const u64* __restrict__ keys, GiantTerms tm, u32 T, u32 logN, u32 E,
+                            u32 nd, const Mod* __restrict__ mods, const u64* __restrict__ c0,
+                            u64 c0_term, u64 c0_ct, u64* __restrict__ out, u64 out_ct) {
+    const u32 r = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
+    const u64 EN = (u64)E << logN;
+    if (r >= EN) return;
+    const u64 ct = blockIdx.x;
+    const u32 l = r >> logN, x = r & ((1u << logN) - 1);
+    const Mod md = mods[l];
+    u64 s0a = 0, s0b = 0, s1a = 0, s1b = 0;
+#pragma unroll 2
+    for (u32 i = 0; i < T; ++i) {
+        const u32 sx = auto_index(x, tm.galois[i], logN);
+        const bool swap = (sx & 1) != 0;
+        const u32 sr = (l << logN) + (sx & ~1u);
+        const u64* Dc = D + i * d_term + ct * d_ct;
+        const u64* key = keys + tm.koff[i];
+        u64 h0a = 0, l0a = 0, h1a = 0, l1a = 0, h0b = 0, l0b = 0, h1b = 0, l1b = 0;
+        for (u32 b = 0; b < nd; ++b) {
+            const ulonglong2 dv = *reinterpret_cast<const ulonglong2*>(Dc + b * EN + sr);
+            const u64 da = swap ? dv.y : dv.x, db = swap ? dv.x : dv.y;
+            const ulonglong2 k0 = __ldg(reinterpret_cast<const ulonglong2*>(key + b * 2 * EN + r));
+            const ulonglong2 k1 = __ldg(reinterpret_cast<const ulonglong2*>(key + b * 2 * EN + EN + r));
+            mac128(h0a, l0a, da, k0.x);
+            mac128(h0b, l0b, db, k0.y);
+            mac128(h1a, l1a, da, k1.x);
+            mac128(h1b, l1b, db, k1.y);
+        }
+        const ulonglong2 cv =
+            *reinterpret_cast<const ulonglong2*>(c0 + i * c0_term + ct * c0_ct + sr);
+        mac128(h0a, l0a, swap ? cv.y : cv.x, md.r64);
+        mac128(h0b, l0b, swap ? cv.x : cv.y, md.r64);
+        s0a = addmod(s0a, redc128(h0a, l0a, md), md.q);
+        s0b = addmod(s0b, redc128(h0b, l0b, md), md.q);
+        s1a = addmod(s1a, redc128(h1a, l1a, md), md.q);
+        s1b = addmod(s1b, redc128(h1b, l1b, md), md.q);
+    }
+    ulonglong2* o0 = reinterpret_cast<ulonglong2*>(out + ct * out_ct + r);
+    ulonglong2* o1 = reinterpret_cast<ulonglong2*>(out + ct * out_ct + EN + r);
+    const ulonglong2 p0 = *o0, p1 = *o1;
+    *o0 = make_ulonglong2(addmod(s0a, p0.x, md.q), addmod(s0b, p0.y, md.q));
+    *o1 = make_ulonglong2(addmod(s1a, p1.x, md.q), addmod(s1b, p1.y, md.q));
+}
+
 // All hoisted baby-step rotations a = 1..B-1 of H ciphertexts in one launch,
 // in the extended basis (the rotation before its ModDown), written in the
 // split operand layout of the multiply-accumulate:
@@ -1572,6 +1632,27 @@ int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, c
         D, key, c.log_n, (u32)E, c0_ext ? (u32)E : c.L, c.ndigits, galois, c.d_mods, c0src,
         c0_ext ? nullptr : c.d_P_mont, out, accumulate ? 1u : 0u, split ? 1u : 0u);
     return launched("k_ks_inner_ext");
+}
+
+int ks_apply_giants(const Ctx& c, const u64* D, u32 cnt, u32 terms, const u64* galois,
+                    const u64* keys, const u64* key_offsets, const u64* c0, u64 c0_term,
+                    u64 c0_ct, u64* out, u64 out_ct, cudaStream_t st) {
+    if (terms == 0) return PDQ_OK;
+    if (terms > kMaxGiantTerms) return fail(PDQ_E_PARAM, "giant steps: too many terms");
+    if (cnt == 0 || cnt > 0x7fffffffu) return fail(PDQ_E_PARAM, "giant steps: bad ciphertext count");
+    const u64 N = c.N, E = c.L + c.K;
+    const u64 dstride = (u64)c.ndigits * E * N;
+    if ((E * N / 2 + kBlock - 1) / kBlock > 65535) return fail(PDQ_E_PARAM, "giant steps: ring too large");
+    GiantTerms tm{};
+    for (u32 i = 0; i < terms; ++i) {
+        tm.koff[i] = key_offsets[i];
+        tm.galois[i] = (u32)galois[i];
+    }
+    const dim3 grid(cnt, (u32)((E * N / 2 + kBlock - 1) / kBlock));
+    k_ks_giants<<<grid, kBlock, 0, st>>>(D, (u64)cnt * dstride, dstride, keys, tm, terms, c.log_n,
+                                          (u32)E, c.ndigits, c.d_mods, c0, c0_term, c0_ct, out,
+                                          out_ct);
+    return launched("k_ks_giants");
 }
 
 namespace {

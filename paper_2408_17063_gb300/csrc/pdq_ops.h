@@ -110,6 +110,19 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
 // limb as it is, instead of P sigma(c0) of a c0 over Q)
 int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, const u64* key,
                  CtSet out, bool accumulate, bool split, cudaStream_t st, bool c0_ext = false);
+constexpr u32 kMaxGiantTerms = 64;
+
+// Every giant step in one launch, over Q u P: for ciphertext ct < cnt,
+//   out[ct] += sum_{i < terms} Rot_i(c0_i[ct], c1_i[ct])
+// where Rot_i is the extended-basis rotation with Galois element galois[i]
+// and the key at keys + key_offsets[i], the raised digits of c1_i[ct] are
+// D[i][ct] ([terms][cnt][ndigits][L+K][N], as ks_raise writes them for the
+// c1 ordered term-major) and c0_i[ct] (over Q u P) starts at
+// c0 + i c0_term + ct c0_ct.  out ciphertexts [2][L+K][N], ct-th at
+// out + ct out_ct.  At most kMaxGiantTerms terms.
+int ks_apply_giants(const Ctx& c, const u64* D, u32 cnt, u32 terms, const u64* galois,
+                    const u64* keys, const u64* key_offsets, const u64* c0, u64 c0_term,
+                    u64 c0_ct, u64* out, u64 out_ct, cudaStream_t st);
 // All baby-step rotations a = 0..B-1 of the H ciphertexts u (raised digits
 // D; a = 0 is (P c0, P c1)) written to Rx[h][a] in the split operand layout;
 // key a at keys + key_offsets[a] (B >= 2).  Only the primes l0 .. l0+el-1
