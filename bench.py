@@ -61,6 +61,8 @@ def parse():
                     help="also time the Answer on an unencrypted database (0: skip)")
     ap.add_argument("--plain-db-B", type=int, default=0,
                     help="baby-step count of the unencrypted-database plan (0: its cost rule)")
+    ap.add_argument("--stacked", type=int, default=1,
+                    help="queries of one plan answered together (0: skip)")
     ap.add_argument("--tune", type=int, default=1,
                     help="also run the batched mix with autotuned plans (0: skip)")
     ap.add_argument("--tune-cache", default="", help="JSON file of tuned plans (read and written)")
@@ -841,6 +843,103 @@ def run_paper_shapes(args, rank: int) -> list:
     return out
 
 
+# Queries of one plan answered together: (configuration, records, matches,
+# queries) -- the benchmark's large query, the plain N = 2^13 query and the
+# paper's Table II/III ring at n = 16384, s = 16.
+STACK_SHAPES = [("c3", 1 << 20, 256, 4), ("c2", 1 << 16, 64, 16), ("paper", 16384, 16, 32)]
+
+
+def run_stacked(args, rank: int) -> list:
+    """Clients of one database asking for the same numbers of records and
+    matches (each with its own secret, keys and matches): one
+    pdq_answer_stacked call for all of them against the same queries one
+    pdq_answer at a time, device time (CUDA events); every stacked output is
+    compared bit for bit with the query's answer alone and decompressed."""
+    import dataclasses
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2408_17063_gb300 import pdq
+
+    stream = torch.cuda.current_stream()
+    rows = []
+    for name, n, s_, Q in STACK_SHAPES:
+        cfg = dataclasses.replace(W.CONFIGS[name], n=n, s=s_)
+        ctx = pdq.Context.from_config(cfg)
+        q0 = W.draw_query(cfg, cfg.seed + rank)
+        db = ctx.db_encode(torch.from_numpy(q0.db.astype(np.int32)).cuda())
+        plan = ctx.plan(n, s_, 0)
+        galois = ctx.plan_galois(plan)
+        consts = ctx.plan_constants(plan)
+        v_all = ctx._u64(Q * plan.J * ctx.ct_elems).view(Q, -1)
+        keys, sks, truths = [], [], []
+        for i in range(Q):
+            seed = cfg.seed + 7919 * (i + 1) + rank
+            qi = W.draw_query(cfg, seed)          # own secret and matches; q0's database
+            sk = ctx.secret_prepare(torch.from_numpy(qi.sk))
+            ks = ctx._u64(len(galois) * ctx.key_elems)
+            kv = ks.view(len(galois), -1)
+            kr = W.rotation_key_randomness(ctx.moduli, ctx.N, ctx.ndigits, galois, seed)
+            for j, k in enumerate(galois):
+                a, e = kr[k]
+                ctx.rotkey_gen(sk, k, torch.from_numpy(a.view(np.int64)).cuda(),
+                               torch.from_numpy(e).cuda(), out=kv[j])
+            a, e = W.encryption_randomness(ctx.moduli[:ctx.L], ctx.N, plan.J, seed)
+            v = np.zeros(plan.J * ctx.N, dtype=np.int32)
+            v[:n] = qi.v
+            v_all[i].copy_(ctx.encrypt(sk, torch.from_numpy(v).cuda(),
+                                       torch.from_numpy(a.view(np.int64)).cuda(),
+                                       torch.from_numpy(e).cuda()).reshape(-1))
+            keys.append(ks)
+            sks.append(sk)
+            truths.append([(int(p), int(q0.db[p])) for p in qi.positions])
+        aws = ctx.answer_workspace(plan)
+        sws = ctx.answer_stacked_workspace(plan, Q)
+        alone = ctx._u64(Q * plan.n_out * ctx.ct_elems).view(Q, -1)
+        stacked = ctx._u64(Q * plan.n_out * ctx.ct_elems)
+
+        def plain():
+            for i in range(Q):
+                ctx.answer(plan, v_all[i], db, keys[i], galois, consts, ws=aws, out=alone[i],
+                           stream=stream)
+
+        def together():
+            ctx.answer_stacked(plan, v_all, db, keys, galois, consts, ws=sws, out=stacked,
+                               stream=stream)
+
+        def timed(f, reps):
+            for _ in range(2):
+                f()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for _ in range(reps):
+                f()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / reps
+
+        reps = 3 if name == "c3" else 10
+        t_plain = timed(plain, reps)
+        l0 = pdq.pdq_launch_count()
+        together()
+        launches = pdq.pdq_launch_count() - l0
+        t_stacked = timed(together, reps)
+        torch.cuda.synchronize()
+        out_q = stacked.view(Q, -1)
+        same = all(torch.equal(out_q[i], alone[i]) for i in range(Q))
+        ok = all(ctx.decomp(plan, ctx.decrypt(sks[i], out_q[i]).cpu().numpy()) == truths[i]
+                 for i in range(Q))
+        rows.append({"config": name, "N": ctx.N, "n": n, "s": s_, "queries": Q,
+                     "B": plan.B, "giants": plan.giants, "groups": plan.G,
+                     "plain_ms_per_query": t_plain / Q, "stacked_ms_per_query": t_stacked / Q,
+                     "speedup": t_plain / t_stacked, "launches_per_stacked_call": int(launches),
+                     "bit_identical_to_alone": bool(same), "all_decompress_exactly": bool(ok),
+                     "stacked_workspace_gib": sws.numel() / 2**30})
+        del keys, v_all, db, consts, aws, sws, alone, stacked, ctx
+        torch.cuda.empty_cache()
+    return rows
+
+
 def run_gpu(args, cfg, rank: int, world: int):
     import numpy as np
     import torch
@@ -1005,6 +1104,13 @@ def run_gpu(args, cfg, rank: int, world: int):
             "rows": run_paper_shapes(args, rank)}
     if args.plain_db:
         line["plain_db"] = run_plain_db(args, cfg, ctx, q, v_cts, sk, stream, rank)
+    if args.stacked:
+        line["stacked"] = {
+            "what": ("queries of one plan (one database, the same numbers of records and "
+                     "matches, own secret and keys each) answered by one pdq_answer_stacked "
+                     "call, every step one launch over all of them, against pdq_answer one "
+                     "query at a time; device time per query"),
+            "rows": run_stacked(args, rank)}
     if args.switch_L and 0 < args.switch_L < cfg.L:
         line["switched"] = run_switched(args, cfg, ctx, plan, q, v_cts, stream, rank)
         if args.ring_log_n and args.ring_log_n < cfg.log_n:

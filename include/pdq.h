@@ -346,6 +346,27 @@ int pdq_answer(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
                uint32_t nkeys, const uint64_t* consts, uint64_t* out, void* ws,
                size_t ws_bytes, void* stream);
 
+/* The Answer of Q queries (1 <= Q <= 64) with the same plan, e.g. clients of
+ * one database asking for the same number of records and matches, in one
+ * launch sequence: every step of Mask and Comp (Alg. 7 with the SIMD form of
+ * Sec. 5.2) runs as one launch over the index ciphertexts, half-blocks and
+ * record groups of all Q queries, reading the database plaintexts and the
+ * plan constants once for all of them; each query's rotations use its own
+ * keys.  v_cts: dev [Q][J][2][L][N] (query q's index ciphertexts after
+ * query q-1's); keys: HOST array of Q device pointers, keys[q] = query q's key
+ * set laid out as for pdq_answer (the same galois list and order for every
+ * query); db, galois, nkeys, consts as for pdq_answer; out: dev
+ * [Q][n_out][2][L][N].  Each query's output is bit-identical to its
+ * pdq_answer alone.  Workspace: pdq_answer_stacked_workspace_bytes (about Q
+ * times pdq_answer's); too small -> PDQ_E_NOMEM; Q out of range or a NULL
+ * pointer -> PDQ_E_PARAM; a missing key -> PDQ_E_KEY. */
+size_t pdq_answer_stacked_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan, uint32_t Q);
+int pdq_answer_stacked(const pdq_ctx* ctx, const pdq_plan* plan, uint32_t Q,
+                       const uint64_t* v_cts, const uint64_t* db,
+                       const uint64_t* const* keys, const uint64_t* galois, uint32_t nkeys,
+                       const uint64_t* consts, uint64_t* out, void* ws, size_t ws_bytes,
+                       void* stream);
+
 /* Answer with host buffers, end to end: copies the query ciphertexts (host
  * [J][2][L][N], coefficient form) to the device, transforms them, runs
  * Mask and Comp, transforms the answer back and copies it to out_host

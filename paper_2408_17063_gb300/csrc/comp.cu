@@ -236,28 +236,29 @@ struct CompLayout {
 
 // Primes of the baby-step rotations held at once: all of them, or as many
 // as the context's rotation budget allows (at least one).
-u32 rotation_chunk(const Ctx& c, const pdq_plan& pl) {
+u32 rotation_chunk(const Ctx& c, const pdq_plan& pl, u32 Q = 1) {
     const u32 E = c.L + c.K;
     if (c.rotation_budget == 0 || pl.B == 1 || !rotations_chunkable(c)) return E;
-    const u64 per_prime = (u64)pl.H * pl.B * 2 * c.N * sizeof(u64);
+    const u64 per_prime = (u64)pl.H * Q * pl.B * 2 * c.N * sizeof(u64);
     const u64 k = c.rotation_budget / per_prime;
     return (u32)std::max<u64>(1, std::min<u64>(E, k));
 }
 
-CompLayout comp_layout(const Ctx& c, const pdq_plan& pl) {
+// (Q queries of plan pl answered together: Q times the half-blocks and groups)
+CompLayout comp_layout(const Ctx& c, const pdq_plan& pl, u32 Q = 1) {
     const u64 cts = ct_elems(c), ects = 2ull * (c.L + c.K) * c.N;
-    const u64 G = pl.G, GI = pl.giants;
+    const u64 G = (u64)pl.G * Q, GI = pl.giants, H = (u64)pl.H * Q;
     // raises: every u_h (baby steps), every lowered accumulator at once
     // (giant steps), every y (rotate-and-sum levels)
-    const u32 cnt = std::max({pl.H, pl.G, pl.G * (pl.giants - 1)});
-    const u64 scratch = std::max({apply_ws(c, cnt), mod_down_ws(c, pl.G),
-                                  mod_down_polys_ws(c, std::max(1u, pl.G * (pl.giants - 1))),
-                                  mod_down_polys_ws(c, pl.G)}) / sizeof(u64);
+    const u32 cnt = (u32)std::max({H, G, G * (GI - 1)});
+    const u64 scratch = std::max({apply_ws(c, cnt), mod_down_ws(c, (u32)G),
+                                  mod_down_polys_ws(c, (u32)std::max<u64>(1, G * (GI - 1))),
+                                  mod_down_polys_ws(c, (u32)G)}) / sizeof(u64);
     CompLayout lo;
     lo.U = 0;
-    lo.Rx = lo.U + (u64)pl.H * cts;
-    const u64 echunk = 2ull * rotation_chunk(c, pl) * c.N;
-    lo.accx = lo.Rx + std::max<u64>((u64)pl.H * pl.B * echunk, G * 8 * ects);
+    lo.Rx = lo.U + H * cts;
+    const u64 echunk = 2ull * rotation_chunk(c, pl, Q) * c.N;
+    lo.accx = lo.Rx + std::max<u64>(H * pl.B * echunk, G * 8 * ects);
     lo.acc = lo.accx + G * (GI - 1) * ects;
     lo.yx = lo.acc + G * (GI - 1) * cts;
     lo.Y0 = lo.yx + G * ects;
@@ -268,16 +269,19 @@ CompLayout comp_layout(const Ctx& c, const pdq_plan& pl) {
     return lo;
 }
 
-size_t comp_ws_bytes(const Ctx& c, const pdq_plan& pl) {
-    return comp_layout(c, pl).end * sizeof(u64);
+size_t comp_ws_bytes(const Ctx& c, const pdq_plan& pl, u32 Q = 1) {
+    return comp_layout(c, pl, Q).end * sizeof(u64);
 }
 
 // The Answer's first stage for the jn index ciphertexts at v (NTT form):
 // w_j = Rot_col(v_j), then the Mask products fused with the pack into
 // u_{2j}, u_{2j+1}.  v, db, w and U point at the run's first j; rws and aws
 // are Comp's key-switch scratch.
+// (sk: jn = Q Jq index ciphertexts of the stacked queries, Jq each, every
+// query masked by the same Jq database plaintexts and rotated with its keys)
 int answer_pack(const Ctx& c, const Keys& keys, const u64* v, const u64* db, u64* w, u64* U,
-                u32 jn, u64* rws, u64* aws, cudaStream_t st) {
+                u32 jn, u64* rws, u64* aws, cudaStream_t st, const Stack* sk = nullptr,
+                u32 Jq = 0) {
     const long long cts = (long long)ct_elems(c);
     const u64 kc = 2ull * c.N - 1;
     const u64* kp = keys.find(kc);
@@ -285,9 +289,10 @@ int answer_pack(const Ctx& c, const Keys& keys, const u64* v, const u64* db, u64
     const CtSet vin = ct_set(v, cts);
     u64* D = nullptr;
     PDQ_TRY(ks_raise(c, vin, jn, rws, &D, st));
-    PDQ_TRY(ks_apply(c, D, vin, jn, (u32)kc, kp, ct_set(w, cts), CtSet{}, aws, st));
+    const KeyTable kt = sk ? sk->table(Jq) : single_keys(keys.base);
+    PDQ_TRY(ks_apply(c, D, vin, jn, (u32)kc, kp, ct_set(w, cts), CtSet{}, aws, st, &kt));
     prof_mark(c, PDQ_STAGE_MASK, st);
-    return mask_pack(c, jn, v, w, db, U, st);
+    return mask_pack(c, jn, v, w, db, U, st, Jq);
 }
 
 // Steps 5 and 6 of Comp on the giant-step sums yx ([G][2][L+K][N]): the
@@ -297,11 +302,13 @@ int answer_pack(const Ctx& c, const Keys& keys, const u64* v, const u64* db, u64
 // masks (one group: the result as it is).
 int rotsum_and_combine(const Ctx& c, const pdq_plan& pl, const Keys& keys, u64* yx, u64* Rx,
                        u64* Y0, u64* Y1, u64* rws, u64* aws, const u64* masks, u64* out,
-                       cudaStream_t st) {
+                       cudaStream_t st, const Stack* sk = nullptr) {
     const long long cts = (long long)ct_elems(c);
     const long long ects = 2LL * (c.L + c.K) * c.N;
     const u64 EN = (u64)(c.L + c.K) * c.N, LN = (u64)c.L * c.N;
-    const u32 G = pl.G;
+    const u32 Q = sk ? sk->Q : 1;
+    const u32 G = pl.G * Q;                       // groups of every query
+    const KeyTable kt = sk ? sk->table(pl.G) : single_keys(keys.base);
     u64* D = nullptr;
     prof_mark(c, PDQ_STAGE_ROTSUM, st);
     const CtSet y_ext = ct_set(yx, ects);
@@ -315,32 +322,39 @@ int rotsum_and_combine(const Ctx& c, const pdq_plan& pl, const Keys& keys, u64* 
         }
         PDQ_TRY(mod_down_polys(c, yx + EN, 2 * EN, G, Y1, LN, aws, st));
         PDQ_TRY(ks_raise(c, ct_set(Y1, (long long)LN), G, rws, &D, st, 0));
-        PDQ_TRY(hoisted_rotations_ext(c, D, y_ext, G, r, gal, keys.base, koff, Rx, st, true));
+        PDQ_TRY(hoisted_rotations_ext(c, D, y_ext, G, r, gal, keys.base, koff, Rx, st, true, 0, 0,
+                                      &kt));
         PDQ_TRY(sum_rotations(c, Rx, G, r, yx, st));
     }
     PDQ_TRY(mod_down_batch(c, yx, G, ct_set(Y0, cts), aws, st));
     prof_mark(c, PDQ_STAGE_COMBINE, st);
-    if (G == 1) {
-        if (cudaMemcpyAsync(out, Y0, (size_t)cts * sizeof(u64), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    if (pl.G == 1) {                              // one group per query: y is the output
+        if (cudaMemcpyAsync(out, Y0, (size_t)cts * Q * sizeof(u64), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return fail(PDQ_E_CUDA, "comp: output copy failed");
         return PDQ_OK;
     }
-    return group_combine(c, pl, Y0, masks, out, st);
+    return group_combine(c, pl, Y0, masks, out, st, Q);
 }
 
 // Comp from the masked ciphertexts (masked != nullptr: [J][4] as pdq_mask
 // writes them), or the Answer from the index ciphertexts v_cts and the
 // database db (masked == nullptr: the Mask fused with the pack, w holding J
 // ciphertexts of scratch).
+// (sk: the Answer of sk->Q queries of plan pl together, every step one
+// launch over all of them; their index ciphertexts one after the other in
+// v_cts, w the same size, outputs in out)
 int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& keys,
              const u64* consts, u64* out, void* ws, size_t ws_bytes, cudaStream_t st,
              const u64* v_cts = nullptr, const u64* db = nullptr, u64* w = nullptr,
-             bool prepacked = false) {
-    if (ws_bytes < comp_ws_bytes(c, pl)) return fail(PDQ_E_NOMEM, "comp: workspace too small");
+             bool prepacked = false, const Stack* sk = nullptr) {
+    const u32 Q = sk ? sk->Q : 1;
+    if (Q == 0 || Q > kMaxStack) return fail(PDQ_E_PARAM, "answer: 1 to 64 stacked queries");
+    if (sk && masked) return fail(PDQ_E_PARAM, "comp: stacked queries take index ciphertexts");
+    if (ws_bytes < comp_ws_bytes(c, pl, Q)) return fail(PDQ_E_NOMEM, "comp: workspace too small");
     const long long cts = (long long)ct_elems(c);
     const long long ects = 2LL * (c.L + c.K) * c.N;
-    const u32 H = pl.H, B = pl.B, G = pl.G, GI = pl.giants;
-    const CompLayout lo = comp_layout(c, pl);
+    const u32 H = pl.H * Q, B = pl.B, G = pl.G * Q, GI = pl.giants;
+    const CompLayout lo = comp_layout(c, pl, Q);
     u64* const base = reinterpret_cast<u64*>(ws);
     u64* U = base + lo.U;
     u64* Rx = base + lo.Rx;
@@ -369,7 +383,7 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
         // prepacked: the caller ran answer_pack into U already
         if (!prepacked) {
             if (!v_cts || !db || !w) return fail(PDQ_E_PARAM, "answer: null buffer");
-            PDQ_TRY(answer_pack(c, keys, v_cts, db, w, U, pl.J, rws, aws, st));
+            PDQ_TRY(answer_pack(c, keys, v_cts, db, w, U, pl.J * Q, rws, aws, st, sk, pl.J));
         }
     } else {
         CtSet in;  in.base = masked + 2 * cts;  in.outer = 4 * cts;  in.per = 2;  in.inner = -cts;
@@ -390,7 +404,7 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
     if (B == 1) {
         PDQ_TRY(times_P(c, u, H, ct_set(Rx, (long long)B * ects), true, st));
         prof_mark(c, PDQ_STAGE_MAC, st);
-        PDQ_TRY(diag_mac(c, pl, Rx, Dg, yx, accx, st));
+        PDQ_TRY(diag_mac(c, pl, Rx, Dg, yx, accx, st, 0, 0, Q));
     } else {
         PDQ_TRY(ks_raise(c, u, H, rws, &D, st));
         std::vector<u64> koff(B, 0);
@@ -399,13 +413,14 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
             PDQ_TRY(key_for(galois_rot(c, a), &kp));
             koff[a] = (u64)(kp - keys.base);
         }
-        const u32 E = c.L + c.K, ec = rotation_chunk(c, pl);
+        const u32 E = c.L + c.K, ec = rotation_chunk(c, pl, Q);
+        const KeyTable kth = sk ? sk->table(pl.H) : single_keys(keys.base);
         for (u32 l0 = 0; l0 < E; l0 += ec) {
             const u32 el = std::min(ec, E - l0);
             if (l0 > 0) prof_mark(c, PDQ_STAGE_BABY, st);
-            PDQ_TRY(baby_steps_ext(c, D, u, H, B, keys.base, koff, Rx, st, l0, el));
+            PDQ_TRY(baby_steps_ext(c, D, u, H, B, keys.base, koff, Rx, st, l0, el, &kth));
             prof_mark(c, PDQ_STAGE_MAC, st);
-            PDQ_TRY(diag_mac(c, pl, Rx, Dg, yx, accx, st, l0, el));
+            PDQ_TRY(diag_mac(c, pl, Rx, Dg, yx, accx, st, l0, el, Q));
         }
     }
     prof_mark(c, PDQ_STAGE_ACC_MODDOWN, st);
@@ -434,10 +449,11 @@ int comp_run(const Ctx& c, const pdq_plan& pl, const u64* masked, const Keys& ke
             PDQ_TRY(key_for(gal[g - 1], &kp));
             koff[g - 1] = (u64)(kp - keys.base);
         }
-        PDQ_TRY(ks_apply_giants(c, D, G, GI - 1, gal.data(), keys.base, koff.data(), accx,
+        const KeyTable ktg = sk ? sk->table(pl.G) : single_keys(keys.base);
+        PDQ_TRY(ks_apply_giants(c, D, G, GI - 1, gal.data(), ktg, koff.data(), accx,
                                 (u64)ects, (u64)(GI - 1) * ects, yx, (u64)ects, st));
     }
-    PDQ_TRY(rotsum_and_combine(c, pl, keys, yx, Rx, Y0, Y1, rws, aws, masks, out, st));
+    PDQ_TRY(rotsum_and_combine(c, pl, keys, yx, Rx, Y0, Y1, rws, aws, masks, out, st, sk));
     prof_mark(c, -1, st);
     (void)none;
     return PDQ_OK;
@@ -541,8 +557,8 @@ int answer_plain_db_run(const Ctx& c, const pdq_plan& pl, const u64* v_cts, cons
             gal[i] = k;
             koff[i] = (u64)(kp - keys.base);
         }
-        PDQ_TRY(ks_apply_giants(c, D, G, NA, gal.data(), keys.base, koff.data(), accx, (u64)ects,
-                                (u64)NA * ects, yx, (u64)ects, st));
+        PDQ_TRY(ks_apply_giants(c, D, G, NA, gal.data(), single_keys(keys.base), koff.data(),
+                                accx, (u64)ects, (u64)NA * ects, yx, (u64)ects, st));
     }
     // 4. rotate-and-sum and group masks
     PDQ_TRY(rotsum_and_combine(c, pl, keys, yx, Rx, base + lo.Y0, base + lo.Y1, rws, aws, masks,
@@ -778,6 +794,39 @@ int pdq_answer(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
     Keys k{keys, galois, nkeys, (u64)c.ndigits * 2 * (c.L + c.K) * c.N};
     return comp_run(c, *plan, nullptr, k, consts, out, reinterpret_cast<char*>(ws) + wbytes,
                     ws_bytes - wbytes, (cudaStream_t)stream, v_cts, db, w);
+}
+
+size_t pdq_answer_stacked_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan, uint32_t Q) {
+    if (!ctx || !plan || Q == 0 || Q > kMaxStack) return 0;
+    const Ctx& c = C(ctx);
+    return (size_t)plan->J * Q * ct_elems(c) * sizeof(u64) + comp_ws_bytes(c, *plan, Q);
+}
+
+int pdq_answer_stacked(const pdq_ctx* ctx, const pdq_plan* plan, uint32_t Q,
+                       const uint64_t* v_cts, const uint64_t* db,
+                       const uint64_t* const* keys, const uint64_t* galois, uint32_t nkeys,
+                       const uint64_t* consts, uint64_t* out, void* ws, size_t ws_bytes,
+                       void* stream) {
+    PDQ_CHECK_CTX(ctx);
+    const Ctx& c = C(ctx);
+    if (Q == 0 || Q > kMaxStack) return fail(PDQ_E_PARAM, "answer_stacked: 1 to 64 queries");
+    if (!valid_plan(c, plan) || plan->plain_db || plan->ring_ratio > 1)
+        return fail(PDQ_E_PARAM, "answer_stacked: invalid plan");
+    if (!v_cts || !db || !keys || !galois || !consts || !out || !ws)
+        return fail(PDQ_E_PARAM, "answer_stacked: null buffer");
+    Stack sk;
+    sk.Q = Q;
+    for (u32 q = 0; q < Q; ++q) {
+        if (!keys[q]) return fail(PDQ_E_PARAM, "answer_stacked: null key set");
+        sk.keys[q] = keys[q];
+    }
+    if (ws_bytes < pdq_answer_stacked_workspace_bytes(ctx, plan, Q))
+        return fail(PDQ_E_NOMEM, "answer_stacked: workspace too small");
+    u64* w = reinterpret_cast<u64*>(ws);              // Rot_col(v_j), Q J ciphertexts
+    const size_t wbytes = (size_t)plan->J * Q * ct_elems(c) * sizeof(u64);
+    Keys k{keys[0], galois, nkeys, (u64)c.ndigits * 2 * (c.L + c.K) * c.N};
+    return comp_run(c, *plan, nullptr, k, consts, out, reinterpret_cast<char*>(ws) + wbytes,
+                    ws_bytes - wbytes, (cudaStream_t)stream, v_cts, db, w, false, &sk);
 }
 
 size_t pdq_answer_host_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {

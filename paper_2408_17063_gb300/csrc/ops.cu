@@ -391,17 +391,19 @@ __global__ void k_mask_literal(const u64* __restrict__ v, const u64* __restrict_
 // value at the position that holds the conjugate evaluation point.
 __global__ void k_mask_pack(const u64* __restrict__ v, const u64* __restrict__ w,
                             const u64* __restrict__ db, const u64* __restrict__ rowmask, u32 L,
-                            u32 logN, const Mod* __restrict__ mods, u64* __restrict__ u) {
+                            u32 logN, const Mod* __restrict__ mods, u32 Jq,
+                            u64* __restrict__ u) {
     const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
     const u64 LN = (u64)L << logN;
     if (r >= LN) return;
     const u64 j = blockIdx.y;
+    const u64 jd = Jq == gridDim.y ? j : (u32)j % Jq;   // j's database plaintext in its query
     const u32 N = 1u << logN;
     const u32 l = r >> logN, x = r & (N - 1);
     const Mod md = mods[l];
     const u64 top = rowmask[r];
-    const u64 pb = db[j * 2 * LN + ((u64)l << logN) + auto_index(x, 2 * N - 1, logN)];
-    const u64 pd = db[j * 2 * LN + LN + r];
+    const u64 pb = db[jd * 2 * LN + ((u64)l << logN) + auto_index(x, 2 * N - 1, logN)];
+    const u64 pd = db[jd * 2 * LN + LN + r];
     u64* o = u + j * 4 * LN;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
@@ -492,13 +494,14 @@ __global__ void __launch_bounds__(256) k_modup(const u64* __restrict__ X, CtSet 
 // A[ct][p][r][x] = sum_beta D[ct][beta][r][sigma(x)] * key[beta][p][r][x]
 // Two adjacent positions per thread (16-byte loads and stores): sigma maps
 // the aligned pair {x, x+1} onto an aligned pair, possibly swapped.
-__global__ void k_ks_inner(const u64* __restrict__ D, const u64* __restrict__ key, u32 logN,
+__global__ void k_ks_inner(const u64* __restrict__ D, const KeyTable kt, u64 koff, u32 logN,
                            u32 E, u32 nd, u32 galois, const Mod* __restrict__ mods,
                            u64* __restrict__ A) {
     const u32 r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const u64 EN = (u64)E << logN;
     if (r >= EN) return;
     const u64 ct = blockIdx.y;
+    const u64* __restrict__ key = kt.of((u32)ct) + koff;
     const u32 l = r >> logN, x = r & ((1u << logN) - 1);
     const u32 sx = auto_index(x, galois, logN);
     const bool swap = (sx & 1) != 0;                 // sigma(x) odd -> sigma(x+1) = sigma(x) - 1
@@ -528,7 +531,7 @@ __global__ void k_ks_inner(const u64* __restrict__ D, const u64* __restrict__ ke
 //   out[ct][0][r] (+)= sum_beta D[ct][beta][r][s(x)] key[beta][0][r][x] + [r < L] P c0[ct][r][s(x)]
 //   out[ct][1][r] (+)= sum_beta D[ct][beta][r][s(x)] key[beta][1][r][x]
 // with s = sigma_k; `accumulate` adds into out instead of overwriting it.
-__global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict__ key, u32 logN,
+__global__ void k_ks_inner_ext(const u64* __restrict__ D, const KeyTable kt, u64 koff, u32 logN,
                                u32 E, u32 c0_limbs, u32 nd, u32 galois,
                                const Mod* __restrict__ mods, CtSet c0src,
                                const u64* __restrict__ Pm, CtSet out, u32 accumulate, u32 split) {
@@ -536,6 +539,7 @@ __global__ void k_ks_inner_ext(const u64* __restrict__ D, const u64* __restrict_
     const u64 EN = (u64)E << logN;
     if (r >= EN) return;
     const u64 ct = blockIdx.y;
+    const u64* __restrict__ key = kt.of((u32)ct) + koff;
     const u32 l = r >> logN, x = r & ((1u << logN) - 1);
     const u32 sx = auto_index(x, galois, logN);
     const bool swap = (sx & 1) != 0;
@@ -597,7 +601,7 @@ struct GiantTerms {
 // Record groups are the fastest grid index: the groups at a position run
 // together and read each term's key there once from DRAM.
 __global__ void k_ks_giants(const u64* __restrict__ D, u64 d_term, u64 d_ct,
-                            const u64* __restrict__ keys, GiantTerms tm, u32 T, u32 logN, u32 E,
+                            const KeyTable kt, GiantTerms tm, u32 T, u32 logN, u32 E,
                             u32 nd, const Mod* __restrict__ mods, const u64* __restrict__ c0,
                             u64 c0_term, u64 c0_ct, u64* __restrict__ out, u64 out_ct) {
     const u32 r = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
@@ -606,6 +610,7 @@ __global__ void k_ks_giants(const u64* __restrict__ D, u64 d_term, u64 d_ct,
     const u64 ct = blockIdx.x;
     const u32 l = r >> logN, x = r & ((1u << logN) - 1);
     const Mod md = mods[l];
+    const u64* __restrict__ keys = kt.of((u32)ct);
     u64 s0a = 0, s0b = 0, s1a = 0, s1b = 0;
 #pragma unroll 2
     for (u32 i = 0; i < T; ++i) {
@@ -696,7 +701,8 @@ struct BabyParams {
 
 template <int T, int HC, int CPT, int ND>
 __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
-        const u64* __restrict__ D, CtSet u, const u64* __restrict__ keys, u32 H, u32 B, u32 logN,
+        const u64* __restrict__ D, CtSet u, const KeyTable kt, u32 Hq, u32 zper, u64 zmagic,
+        u32 B, u32 logN,
         u32 E, u32 L, u32 c1_limb, const Mod* __restrict__ mods, const u64* __restrict__ Pm,
         u64* __restrict__ Rx, const BabyParams bp, u32 ER) {
     // Rx holds ER limbs per polynomial ([..][2][ER][N]): a chunk of primes
@@ -712,7 +718,15 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
     u64* Ds = sm;                       // [HC][ND][T]
     u64* Cs = Ds + HC * ND * T;         // [HC][T]: c0
     u64* C1s = Cs + HC * T;             // [HC][T]: c1 (for a = 0)
-    const u32 y0 = blockIdx.x * T, r = blockIdx.y, h0 = blockIdx.z * HC;
+    // blockIdx.z: chunk of HC ciphertexts of one query (queries of Hq
+    // ciphertexts each, zper chunks per query); the chunk's rotations use
+    // that query's keys.  blockIdx.z / zper by the multiplier
+    // zmagic = ceil(2^32 / zper), exact below 2^16 (a hardware division here
+    // costs the kernel half its registers' worth of unrolling)
+    const u32 qz = (u32)(((u64)blockIdx.z * zmagic) >> 32), chunk = blockIdx.z - qz * zper;
+    const u32 y0 = blockIdx.x * T, r = blockIdx.y, h0 = qz * Hq + chunk * HC;
+    const u32 H = qz * Hq + min(Hq, chunk * HC + HC);   // end of the chunk
+    const u64* __restrict__ keys = kt.p[qz];
     const u64 EN = (u64)E << logN, ERN = (u64)ER << logN;
     const u32 nthreads = T * HC / CPT;
     constexpr u32 TP = T / 2;           // 16-byte chunks per row of a tile
@@ -721,12 +735,12 @@ __global__ void __launch_bounds__(T * HC / CPT) k_baby_ext(
         const u32 yy = (e % TP) * 2, rest = e / TP, b = rest % ND, ct = rest / ND;
         const u32 h = h0 + ct;
         cp_async16(Ds + (ct * ND + b) * T + yy,
-                   D + ((u64)(h < H ? h : 0) * ND + b) * EN + ((u64)r << logN) + y0 + yy, h < H);
+                   D + ((u64)(h < H ? h : h0) * ND + b) * EN + ((u64)r << logN) + y0 + yy, h < H);
     }
     if (r < L) {
         for (u32 e = threadIdx.x; e < HC * TP; e += nthreads) {
             const u32 yy = (e % TP) * 2, ct = e / TP, h = h0 + ct;
-            const u64* src = u.at(h < H ? h : 0) + ((u64)r << logN) + y0 + yy;
+            const u64* src = u.at(h < H ? h : h0) + ((u64)r << logN) + y0 + yy;
             cp_async16(Cs + ct * T + yy, src, h < H);
             cp_async16(C1s + ct * T + yy, src + ((u64)c1_limb << logN), h < H);
         }
@@ -1053,14 +1067,18 @@ __device__ __forceinline__ u64 fold1(const AccK& A, const Mod& md) {
 }
 
 struct MacArgs {
-    u32 G, hpg, H, B, GI, E, logN;
+    u32 G, hpg, H, B, GI, E, logN;  // G: groups of the launch; H: half-blocks per query
+    u32 Gq;                        // groups per query (queries answered together)
+    u64 Gq_magic;                  // ceil(2^32 / Gq): gm / Gq = (gm Gq_magic) >> 32
     u32 ER;                        // primes per polynomial in R (a chunk, or E)
     u32 logX, logGS, logGI, CPC;   // CPC: combinations per CTA (even)
     u32 tiles_per_cta, achunks;
     u32 fold_one;                  // at most 256 products per output: fold1
 };
 
-template <int GT, int BC, int PC>
+// STACKED: the groups belong to several queries (of a.Gq groups and a.H
+// half-blocks each); one query's launch keeps the plain index arithmetic.
+template <int GT, int BC, int PC, bool STACKED>
 __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
                                                   const u64* __restrict__ Dg, MacArgs a,
                                                   const Mod* __restrict__ mods,
@@ -1121,8 +1139,18 @@ __global__ void __launch_bounds__(256, 2) k_diag_mac(const u64* __restrict__ R,
             const u32 cb = row / BC, ai = row & (BC - 1);
             const u32 combo = cbase + cb;
             const u32 gm = combo >> 1, p = combo & 1;
-            const u32 h = gm * a.hpg + hh;
-            const bool valid = gm < a.G && h < a.H;
+            // group gm is group gl of query qz, whose half-blocks start at qz H
+            u32 h;
+            bool valid;
+            if constexpr (!STACKED) {
+                h = gm * a.hpg + hh;
+                valid = gm < a.G && h < a.H;
+            } else {
+                const u32 qz = (u32)(((u64)gm * a.Gq_magic) >> 32), gl = gm - qz * a.Gq;
+                const u32 hl = gl * a.hpg + hh;
+                valid = gm < a.G && hl < a.H;
+                h = qz * a.H + hl;
+            }
             const u64* src = R + ((((u64)(valid ? h : 0) * a.B + a0 + ai) * 2 + p) * a.ER + l) * N +
                              x0 + 2 * xp;
             cp_async16(Rt + cb * RB + ai * X + 2 * xp, src, valid);
@@ -1235,18 +1263,21 @@ __global__ void k_ct_add(CtSet y, CtSet x, u32 L, u32 logN, const Mod* __restric
 
 // out[c] = sum_o M_o * y[c per_out + o]
 __global__ void k_group_combine(const u64* __restrict__ y, const u64* __restrict__ masks, u32 G,
-                                u32 per_out, u32 L, u32 logN, const Mod* __restrict__ mods,
-                                u64* __restrict__ out) {
+                                u32 per_out, u32 n_out, u32 L, u32 logN,
+                                const Mod* __restrict__ mods, u64* __restrict__ out) {
+    // output c is output cl of query qz (n_out outputs and G groups per query)
     const u32 rr = blockIdx.x * blockDim.x + threadIdx.x;
     const u32 LN = L << logN;
     if (rr >= 2 * LN) return;
     const u64 c = blockIdx.y;
+    const u64 qz = c / n_out, cl = c - qz * n_out;
     const u32 r = rr >= LN ? rr - LN : rr;
     const Mod md = mods[r >> logN];
     u64 ah = 0, al = 0;
     for (u32 o = 0; o < per_out; ++o) {
-        const u64 gamma = c * per_out + o;
-        if (gamma >= G) break;
+        const u64 gl = cl * per_out + o;
+        if (gl >= G) break;
+        const u64 gamma = qz * G + gl;
         if ((o & 127) == 127) { al = reduce128(ah, al, md); ah = 0; }
         mac128(ah, al, masks[(u64)o * LN + r], y[gamma * 2 * LN + rr]);
     }
@@ -1517,10 +1548,10 @@ int decrypt(const Ctx& c, const u64* sk, const u64* ct, u32 count, u32* slots, u
 }
 
 int mask_pack(const Ctx& c, u32 J, const u64* v, const u64* w, const u64* db, u64* u,
-              cudaStream_t st) {
+              cudaStream_t st, u32 Jq) {
     PDQ_TRY(check_y(J, "mask"));
     k_mask_pack<<<grid2((u64)c.L * c.N, J), kBlock, 0, st>>>(v, w, db, c.d_rowmask, c.L, c.log_n,
-                                                             c.d_mods, u);
+                                                             c.d_mods, Jq ? Jq : J, u);
     return launched("k_mask_pack");
 }
 
@@ -1606,12 +1637,14 @@ size_t apply_ws(const Ctx& c, u32 cnt) {
 }
 
 int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u64* key,
-             CtSet out, CtSet add, u64* ws, cudaStream_t st) {
+             CtSet out, CtSet add, u64* ws, cudaStream_t st, const KeyTable* kt) {
     const u64 N = c.N, L = c.L, K = c.K, E = L + K;
     PDQ_TRY(check_y(2ull * cnt, "key switch"));
     u64* A = ws;
     u64* Cv = ws + cnt * 2 * E * N;
-    k_ks_inner<<<grid2(E * N / 2, cnt), kBlock, 0, st>>>(D, key, c.log_n, (u32)E, c.ndigits,
+    const KeyTable t = kt ? *kt : single_keys(key);
+    const u64 koff = kt ? (u64)(key - kt->p[0]) : 0;
+    k_ks_inner<<<grid2(E * N / 2, cnt), kBlock, 0, st>>>(D, t, koff, c.log_n, (u32)E, c.ndigits,
                                                          galois, c.d_mods, A);
     PDQ_TRY(launched("k_ks_inner"));
     PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
@@ -1624,22 +1657,26 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
 }
 
 int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, const u64* key,
-                 CtSet out, bool accumulate, bool split, cudaStream_t st, bool c0_ext) {
+                 CtSet out, bool accumulate, bool split, cudaStream_t st, bool c0_ext,
+                 const KeyTable* kt) {
     const u64 N = c.N, E = c.L + c.K;
     PDQ_TRY(check_y(cnt, "key switch"));
     if (accumulate && split) return fail(PDQ_E_PARAM, "ks_apply_ext: cannot accumulate split output");
+    const KeyTable t = kt ? *kt : single_keys(key);
+    const u64 koff = kt ? (u64)(key - kt->p[0]) : 0;
     k_ks_inner_ext<<<grid2(E * N / 2, cnt), kBlock, 0, st>>>(
-        D, key, c.log_n, (u32)E, c0_ext ? (u32)E : c.L, c.ndigits, galois, c.d_mods, c0src,
+        D, t, koff, c.log_n, (u32)E, c0_ext ? (u32)E : c.L, c.ndigits, galois, c.d_mods, c0src,
         c0_ext ? nullptr : c.d_P_mont, out, accumulate ? 1u : 0u, split ? 1u : 0u);
     return launched("k_ks_inner_ext");
 }
 
 int ks_apply_giants(const Ctx& c, const u64* D, u32 cnt, u32 terms, const u64* galois,
-                    const u64* keys, const u64* key_offsets, const u64* c0, u64 c0_term,
+                    const KeyTable& kt, const u64* key_offsets, const u64* c0, u64 c0_term,
                     u64 c0_ct, u64* out, u64 out_ct, cudaStream_t st) {
     if (terms == 0) return PDQ_OK;
     if (terms > kMaxGiantTerms) return fail(PDQ_E_PARAM, "giant steps: too many terms");
-    if (cnt == 0 || cnt > 0x7fffffffu) return fail(PDQ_E_PARAM, "giant steps: bad ciphertext count");
+    if (cnt == 0 || cnt > 0x7fffffffu || (kt.per != ~0u && (cnt > 65535 || kt.per > 65535)))
+        return fail(PDQ_E_PARAM, "giant steps: bad ciphertext count");
     const u64 N = c.N, E = c.L + c.K;
     const u64 dstride = (u64)c.ndigits * E * N;
     if ((E * N / 2 + kBlock - 1) / kBlock > 65535) return fail(PDQ_E_PARAM, "giant steps: ring too large");
@@ -1649,7 +1686,7 @@ int ks_apply_giants(const Ctx& c, const u64* D, u32 cnt, u32 terms, const u64* g
         tm.galois[i] = (u32)galois[i];
     }
     const dim3 grid(cnt, (u32)((E * N / 2 + kBlock - 1) / kBlock));
-    k_ks_giants<<<grid, kBlock, 0, st>>>(D, (u64)cnt * dstride, dstride, keys, tm, terms, c.log_n,
+    k_ks_giants<<<grid, kBlock, 0, st>>>(D, (u64)cnt * dstride, dstride, kt, tm, terms, c.log_n,
                                           (u32)E, c.ndigits, c.d_mods, c0, c0_term, c0_ct, out,
                                           out_ct);
     return launched("k_ks_giants");
@@ -1658,7 +1695,7 @@ int ks_apply_giants(const Ctx& c, const u64* D, u32 cnt, u32 terms, const u64* g
 namespace {
 
 template <int ND>
-int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
+int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const KeyTable& kt,
                 const BabyParams& bp, u64* Rx, cudaStream_t st, bool ext, u32 l0, u32 el) {
     constexpr u32 T = 64, HC = 16, CPT = 8;
     const u32 E = c.L + c.K;
@@ -1676,9 +1713,16 @@ int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* ke
     uc.base = u.base + off;
     BabyParams bpc = bp;
     for (u32 a = 1; a < B; ++a) bpc.koff[a] += off;
-    const dim3 grid(c.N / T, el, (H + HC - 1) / HC);
+    // chunks of HC ciphertexts never span two queries (one key set each)
+    const u32 Hq = kt.per == ~0u ? H : kt.per;
+    if (Hq == 0 || H % Hq != 0) return fail(PDQ_E_PARAM, "hoisted rotations: ragged query stack");
+    const u32 zper = (Hq + HC - 1) / HC;
+    const u64 zs = (u64)(H / Hq) * zper;
+    if (zs > 65535) return fail(PDQ_E_PARAM, "hoisted rotations: too many ciphertexts");
+    const u64 zmagic = ((1ull << 32) + zper - 1) / zper;
+    const dim3 grid(c.N / T, el, (u32)zs);
     k_baby_ext<T, HC, CPT, ND><<<grid, T * HC / CPT, smem, st>>>(
-        D + off, uc, keys, H, B, c.log_n, E, nc0 > l0 ? nc0 - l0 : 0, nc0, c.d_mods + l0,
+        D + off, uc, kt, Hq, zper, zmagic, B, c.log_n, E, nc0 > l0 ? nc0 - l0 : 0, nc0, c.d_mods + l0,
         ext ? nullptr : c.d_P_mont + l0, Rx, bpc, el);
     return launched("k_baby_ext");
 }
@@ -1687,10 +1731,11 @@ int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* ke
 
 int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
                    const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st, u32 l0,
-                   u32 el) {
+                   u32 el, const KeyTable* kt) {
     std::vector<u64> galois(B, 1);
     for (u32 a = 1; a < B; ++a) galois[a] = host_powmod(3, a, 2ull * c.N);
-    return hoisted_rotations_ext(c, D, u, H, B, galois, keys, key_offsets, Rx, st, false, l0, el);
+    return hoisted_rotations_ext(c, D, u, H, B, galois, keys, key_offsets, Rx, st, false, l0, el,
+                                 kt);
 }
 
 bool rotations_chunkable(const Ctx& c) { return c.N >= 64 && c.ndigits <= 8; }
@@ -1698,7 +1743,7 @@ bool rotations_chunkable(const Ctx& c) { return c.N >= 64 && c.ndigits <= 8; }
 int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
                           const std::vector<u64>& galois, const u64* keys,
                           const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st,
-                          bool ext, u32 l0, u32 el) {
+                          bool ext, u32 l0, u32 el, const KeyTable* kt) {
     constexpr u32 T = 64;
     const u32 E = c.L + c.K;
     if (el == 0) el = E - l0;
@@ -1718,7 +1763,7 @@ int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
             PDQ_TRY(ks_apply_ext(c, D, u, H, (u32)galois[a], keys + key_offsets[a],
                                  ct_set(Rx + (u64)a * 2 * (c.L + c.K) * c.N,
                                         (long long)B * 2 * (c.L + c.K) * c.N),
-                                 false, true, st, ext));
+                                 false, true, st, ext, kt));
         }
         return PDQ_OK;
     }
@@ -1728,15 +1773,16 @@ int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
         bp.kinv[a] = (u32)host_invmod(galois[a], 2ull * c.N);
         bp.koff[a] = key_offsets[a];
     }
+    const KeyTable t = kt ? *kt : single_keys(keys);
     switch (c.ndigits) {
-        case 1: return launch_baby<1>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
-        case 2: return launch_baby<2>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
-        case 3: return launch_baby<3>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
-        case 4: return launch_baby<4>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
-        case 5: return launch_baby<5>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
-        case 6: return launch_baby<6>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
-        case 7: return launch_baby<7>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
-        default: return launch_baby<8>(c, D, u, H, B, keys, bp, Rx, st, ext, l0, el);
+        case 1: return launch_baby<1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+        case 2: return launch_baby<2>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+        case 3: return launch_baby<3>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+        case 4: return launch_baby<4>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+        case 5: return launch_baby<5>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+        case 6: return launch_baby<6>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+        case 7: return launch_baby<7>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+        default: return launch_baby<8>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
     }
 }
 
@@ -1858,9 +1904,9 @@ constexpr u32 kMacPC = 2;                // polynomials (of one group) per threa
 constexpr u32 kMacSmem = 100u << 10;     // two CTAs per SM
 constexpr u32 kMacMinX = 2;
 
-MacShape mac_shape(const pdq_plan& pl, u32 logN) {
+MacShape mac_shape(const pdq_plan& pl, u32 logN, u32 Q = 1) {
     MacShape s{};
-    const u32 GI = pl.giants, combos = 2 * pl.G;
+    const u32 GI = pl.giants, combos = 2 * pl.G * Q;
     s.GT = GI < 4 ? GI : 4;
     const u32 GS = GI / s.GT;
     s.logGS = log2u(GS);
@@ -1893,15 +1939,18 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN) {
     return s;
 }
 
-template <int GT, int BC>
+template <int GT, int BC, bool STACKED>
 int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R, const u64* Dg,
-               u64* acc0, u64* acc, cudaStream_t st, u32 l0, u32 el) {
+               u64* acc0, u64* acc, cudaStream_t st, u32 l0, u32 el, u32 Q) {
     static const cudaError_t configured = cudaFuncSetAttribute(
-        k_diag_mac<GT, BC, kMacPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMacSmem);
+        k_diag_mac<GT, BC, kMacPC, STACKED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)kMacSmem);
     if (configured != cudaSuccess)
         return fail(PDQ_E_CUDA, std::string("k_diag_mac attribute: ") + cudaGetErrorString(configured));
     MacArgs a;
-    a.G = pl.G;
+    a.G = pl.G * Q;
+    a.Gq = pl.G;
+    a.Gq_magic = ((1ull << 32) + pl.G - 1) / pl.G;
     a.hpg = pl.hpg;
     a.H = pl.H;
     a.B = pl.B;
@@ -1919,7 +1968,7 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
     const dim3 grid((c.N >> s.logX) / s.tiles_per_cta, el, s.zslices);
     // the chunk of primes l0 .. l0+el-1: per-prime pointers advanced to l0
     const u64 off = (u64)l0 * c.N;
-    k_diag_mac<GT, BC, kMacPC><<<grid, s.threads, s.smem, st>>>(R, Dg + off * pl.giants, a,
+    k_diag_mac<GT, BC, kMacPC, STACKED><<<grid, s.threads, s.smem, st>>>(R, Dg + off * pl.giants, a,
                                                                  c.d_mods + l0, c.d_ckar + 8 * l0,
                                                                  acc0 + off, acc + off);
     return launched("k_diag_mac");
@@ -1927,13 +1976,18 @@ int launch_mac(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R
 
 template <int GT>
 int launch_mac_bc(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64* R,
-                  const u64* Dg, u64* acc0, u64* acc, cudaStream_t st, u32 l0, u32 el) {
+                  const u64* Dg, u64* acc0, u64* acc, cudaStream_t st, u32 l0, u32 el, u32 Q) {
     switch (s.Bc) {
-        case 1: return launch_mac<GT, 1>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
-        case 2: return launch_mac<GT, 2>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
-        case 4: return launch_mac<GT, 4>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
-        case 8: return launch_mac<GT, 8>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
-        case 16: return launch_mac<GT, 16>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
+        case 1: return Q > 1 ? launch_mac<GT, 1, true>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q)
+                          : launch_mac<GT, 1, false>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q);
+        case 2: return Q > 1 ? launch_mac<GT, 2, true>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q)
+                          : launch_mac<GT, 2, false>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q);
+        case 4: return Q > 1 ? launch_mac<GT, 4, true>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q)
+                          : launch_mac<GT, 4, false>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q);
+        case 8: return Q > 1 ? launch_mac<GT, 8, true>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q)
+                          : launch_mac<GT, 8, false>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q);
+        case 16: return Q > 1 ? launch_mac<GT, 16, true>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q)
+                          : launch_mac<GT, 16, false>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q);
         default: return fail(PDQ_E_PARAM, "diag_mac: baby-step count must be a power of two");
     }
 }
@@ -1941,16 +1995,20 @@ int launch_mac_bc(const Ctx& c, const pdq_plan& pl, const MacShape& s, const u64
 }  // namespace
 
 int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc0, u64* acc,
-             cudaStream_t st, u32 l0, u32 el) {
-    const MacShape s = mac_shape(pl, c.log_n);
+             cudaStream_t st, u32 l0, u32 el, u32 Q) {
+    // (the kernel divides group indices by pl.G with a multiplier: exact
+    // while every group index times pl.G stays below 2^32)
+    if (Q == 0 || pl.G == 0 || (u64)pl.G * Q * pl.G >= (1ull << 32))
+        return fail(PDQ_E_PARAM, "diag_mac: too many groups for one launch");
+    const MacShape s = mac_shape(pl, c.log_n, Q);
     if (el == 0) el = c.L + c.K - l0;
     if (l0 + el > c.L + c.K) return fail(PDQ_E_PARAM, "diag_mac: bad prime range");
     if (s.zslices > 65535) return fail(PDQ_E_PARAM, "diag_mac: too many groups");
     if (s.logX < 1 || s.smem > kMacSmem) return fail(PDQ_E_PARAM, "diag_mac: plan too large for one tile");
     switch (s.GT) {
-        case 1: return launch_mac_bc<1>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
-        case 2: return launch_mac_bc<2>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
-        case 4: return launch_mac_bc<4>(c, pl, s, R, Dg, acc0, acc, st, l0, el);
+        case 1: return launch_mac_bc<1>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q);
+        case 2: return launch_mac_bc<2>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q);
+        case 4: return launch_mac_bc<4>(c, pl, s, R, Dg, acc0, acc, st, l0, el, Q);
         default: return fail(PDQ_E_PARAM, "diag_mac: giant-step count must be a power of two");
     }
 }
@@ -2120,10 +2178,10 @@ int ct_add(const Ctx& c, CtSet y, CtSet x, u32 cnt, cudaStream_t st) {
 }
 
 int group_combine(const Ctx& c, const pdq_plan& pl, const u64* y, const u64* masks, u64* out,
-                  cudaStream_t st) {
-    PDQ_TRY(check_y(pl.n_out, "group_combine"));
-    k_group_combine<<<grid2(2ull * c.L * c.N, pl.n_out), kBlock, 0, st>>>(
-        y, masks, pl.G, pl.per_out, c.L, c.log_n, c.d_mods, out);
+                  cudaStream_t st, u32 Q) {
+    PDQ_TRY(check_y((u64)pl.n_out * Q, "group_combine"));
+    k_group_combine<<<grid2(2ull * c.L * c.N, pl.n_out * Q), kBlock, 0, st>>>(
+        y, masks, pl.G, pl.per_out, pl.n_out, c.L, c.log_n, c.d_mods, out);
     return launched("k_group_combine");
 }
 

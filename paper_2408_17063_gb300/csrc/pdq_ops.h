@@ -32,6 +32,51 @@ inline CtSet ct_set(const u64* base, long long stride) {
     return s;
 }
 
+// Queries answered together in one launch per step (at most kMaxStack).
+constexpr u32 kMaxStack = 64;
+
+// Key sets of the queries of a launch: the key of ciphertext ct of the
+// launch is read from p[ct / per] plus the key's offset inside a set (every
+// set holds the same Galois elements in the same order).  One query: p[0]
+// and per = ~0u.
+struct KeyTable {
+    const u64* p[kMaxStack];
+    u32 per;
+    u64 magic;      // ceil(2^32 / per): ct / per = (ct magic) >> 32 for ct, per < 2^16
+    // key set of ciphertext ct of the launch (a multiply instead of a
+    // division, which would cost the kernels registers)
+    __host__ __device__ __forceinline__ const u64* of(u32 ct) const {
+        return p[(u32)(((u64)ct * magic) >> 32)];
+    }
+};
+
+inline KeyTable key_table(u32 per) {
+    KeyTable t{};
+    t.per = per;
+    t.magic = ((1ull << 32) + per - 1) / per;
+    return t;
+}
+
+inline KeyTable single_keys(const u64* base) {
+    KeyTable t = key_table(~0u);       // (ct magic) >> 32 = 0 for ct < 2^31
+    t.p[0] = base;
+    return t;
+}
+
+// Q queries with one plan answered together: query q's ciphertexts follow
+// query q-1's in every buffer of the Answer (index ciphertexts, half-blocks,
+// groups, outputs), its key set at keys[q].
+struct Stack {
+    u32 Q = 1;
+    const u64* keys[kMaxStack] = {};
+    // the table for a launch over `per` ciphertexts of each query
+    KeyTable table(u32 per) const {
+        KeyTable t = key_table(Q == 1 ? ~0u : per);
+        for (u32 q = 0; q < Q && q < kMaxStack; ++q) t.p[q] = keys[q];
+        return t;
+    }
+};
+
 struct DigitBounds {
     u32 lo[32];
     u32 hi[32];
@@ -68,8 +113,10 @@ int mask_literal(const Ctx& c, u32 J, const u64* v, const u64* dbp, u64* out, cu
 // u[2j] = v_j.[1;0] + w_j.sigma_col(DB_j.[1;0]), u[2j+1] = w_j.[1;0] + v_j.(DB_j.[0;1])
 // with w_j = Rot_col(v_j): the packed u of Comp straight from the index
 // ciphertexts (u [2J][2][L][N])
+// (Jq > 0: the J index ciphertexts are queries of Jq each, all masked by
+// the same Jq database plaintexts)
 int mask_pack(const Ctx& c, u32 J, const u64* v, const u64* w, const u64* db, u64* u,
-              cudaStream_t st);
+              cudaStream_t st, u32 Jq = 0);
 
 // the Answer on an unencrypted database: diagonals [J][2][B][L+K][N][giants]
 // (split layout) and their multiply-accumulate into y0 ([G][2][L+K][N], set 0
@@ -99,8 +146,10 @@ size_t apply_ws(const Ctx& c, u32 cnt);
 // over Q; 0 raises a set of polynomials)
 int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t st,
              u64 c1_off = ~0ull);
+// (kt: ciphertexts of several queries; `key` points into query 0's set and
+// query q's key is at the same offset in kt->p[q])
 int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u64* key,
-             CtSet out, CtSet add, u64* ws, cudaStream_t st);
+             CtSet out, CtSet add, u64* ws, cudaStream_t st, const KeyTable* kt = nullptr);
 
 // Extended-basis rotation (no ModDown): out (+)= (P sigma(c0) + A0, A1) over
 // Q u P, out ciphertexts [2][L+K][N]
@@ -109,7 +158,8 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
 // (c0_ext: c0src holds ciphertexts over Q u P and sigma(c0) joins on every
 // limb as it is, instead of P sigma(c0) of a c0 over Q)
 int ks_apply_ext(const Ctx& c, const u64* D, CtSet c0src, u32 cnt, u32 galois, const u64* key,
-                 CtSet out, bool accumulate, bool split, cudaStream_t st, bool c0_ext = false);
+                 CtSet out, bool accumulate, bool split, cudaStream_t st, bool c0_ext = false,
+                 const KeyTable* kt = nullptr);
 constexpr u32 kMaxGiantTerms = 64;
 
 // Every giant step in one launch, over Q u P: for ciphertext ct < cnt,
@@ -119,17 +169,19 @@ constexpr u32 kMaxGiantTerms = 64;
 // D[i][ct] ([terms][cnt][ndigits][L+K][N], as ks_raise writes them for the
 // c1 ordered term-major) and c0_i[ct] (over Q u P) starts at
 // c0 + i c0_term + ct c0_ct.  out ciphertexts [2][L+K][N], ct-th at
-// out + ct out_ct.  At most kMaxGiantTerms terms.
+// out + ct out_ct.  At most kMaxGiantTerms terms; ciphertext ct's keys are
+// those of the set kt.p[ct / kt.per].
 int ks_apply_giants(const Ctx& c, const u64* D, u32 cnt, u32 terms, const u64* galois,
-                    const u64* keys, const u64* key_offsets, const u64* c0, u64 c0_term,
+                    const KeyTable& kt, const u64* key_offsets, const u64* c0, u64 c0_term,
                     u64 c0_ct, u64* out, u64 out_ct, cudaStream_t st);
 // All baby-step rotations a = 0..B-1 of the H ciphertexts u (raised digits
 // D; a = 0 is (P c0, P c1)) written to Rx[h][a] in the split operand layout;
 // key a at keys + key_offsets[a] (B >= 2).  Only the primes l0 .. l0+el-1
 // (el = 0: to the last), stored as Rx [H][B][2][el][N] (a chunk of primes).
+// (kt: the H ciphertexts are queries of kt->per each, with their own keys)
 int baby_steps_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const u64* keys,
                    const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st, u32 l0 = 0,
-                   u32 el = 0);
+                   u32 el = 0, const KeyTable* kt = nullptr);
 // whether the hoisted rotations can run on a chunk of primes (their fused
 // kernel applies)
 bool rotations_chunkable(const Ctx& c);
@@ -140,7 +192,8 @@ bool rotations_chunkable(const Ctx& c);
 int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
                           const std::vector<u64>& galois, const u64* keys,
                           const std::vector<u64>& key_offsets, u64* Rx, cudaStream_t st,
-                          bool ext = false, u32 l0 = 0, u32 el = 0);
+                          bool ext = false, u32 l0 = 0, u32 el = 0,
+                          const KeyTable* kt = nullptr);
 // out[h] = sum_{a<R} Rx[h][a] (Rx [cnt][R][2][L+K][N] split, out [cnt][2][L+K][N]
 // canonical), R <= 8
 int sum_rotations(const Ctx& c, const u64* Rx, u32 cnt, u32 R, u64* out, cudaStream_t st);
@@ -168,10 +221,12 @@ int gather_rows(CtSet src, long long src_off, u32 cnt, u64 len, u64* dst, u64 ds
 // giant index 0 to acc0 [G][2][L+K][N], the others to acc [G][giants-1][2][L+K][N].
 // Only the primes l0 .. l0+el-1 (el = 0: to the last); R holds those primes
 // ([H][B][2][el][N]).
+// (Q > 1: Q queries of plan pl, their half-blocks and groups one after the
+// other in R, acc0 and acc)
 int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64* acc0, u64* acc,
-             cudaStream_t st, u32 l0 = 0, u32 el = 0);
+             cudaStream_t st, u32 l0 = 0, u32 el = 0, u32 Q = 1);
 int ct_add(const Ctx& c, CtSet y, CtSet x, u32 cnt, cudaStream_t st);
 int group_combine(const Ctx& c, const pdq_plan& pl, const u64* y, const u64* masks, u64* out,
-                  cudaStream_t st);
+                  cudaStream_t st, u32 Q = 1);
 
 }  // namespace pdq

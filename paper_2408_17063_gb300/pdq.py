@@ -116,6 +116,9 @@ _SIGS = {
     "pdq_comp": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _U32, _P, _P, _P, _SZ, _P]),
     "pdq_answer_workspace_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
     "pdq_answer": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _P, _U32, _P, _P, _P, _SZ, _P]),
+    "pdq_answer_stacked_workspace_bytes": (_SZ, [_P, ctypes.POINTER(Plan), _U32]),
+    "pdq_answer_stacked": (_I, [_P, ctypes.POINTER(Plan), _U32, _P, _P, _P, _P, _U32, _P, _P, _P,
+                                _SZ, _P]),
     "pdq_answer_host_workspace_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
     "pdq_answer_host": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _P, _U32, _P, _P, _P, _SZ,
                              _P]),
@@ -540,6 +543,25 @@ class Context:
                                  ctypes.cast(gal, _P), len(galois), _ptr(consts), _ptr(out),
                                  _ptr(ws), ws.numel(), _stream(stream)))
         return out.view(plan.n_out, 2, self.L, self.N)
+
+    def answer_stacked_workspace(self, plan: Plan, Q: int) -> torch.Tensor:
+        return self._ws(load().pdq_answer_stacked_workspace_bytes(self.h, ctypes.byref(plan), Q))
+
+    def answer_stacked(self, plan: Plan, v_cts, db, key_sets, galois, consts, ws=None, out=None,
+                       stream=None):
+        """Q = len(key_sets) queries of one plan in one launch sequence: v_cts
+        holds their index ciphertexts one query after the other, key_sets[q]
+        is query q's key set; returns [Q][n_out][2][L][N]."""
+        Q = len(key_sets)
+        ws = self.answer_stacked_workspace(plan, Q) if ws is None else ws
+        out = self._u64(Q * plan.n_out * self.ct_elems) if out is None else out
+        gal = (ctypes.c_uint64 * len(galois))(*galois)
+        ptrs = (ctypes.c_uint64 * Q)(*[_ptr(k) or 0 for k in key_sets])
+        _check(load().pdq_answer_stacked(self.h, ctypes.byref(plan), Q, _ptr(v_cts), _ptr(db),
+                                         ctypes.cast(ptrs, _P), ctypes.cast(gal, _P), len(galois),
+                                         _ptr(consts), _ptr(out), _ptr(ws), ws.numel(),
+                                         _stream(stream)))
+        return out.view(Q, plan.n_out, 2, self.L, self.N)
 
     def answer_host_workspace(self, plan: Plan) -> torch.Tensor:
         return self._ws(load().pdq_answer_host_workspace_bytes(self.h, ctypes.byref(plan)))
