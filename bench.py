@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="served arrival rates, queries/s")
     ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--served-stack", type=int, default=16,
+                    help="served again with up to this many requests of one shape stacked (<= 1: skip)")
+    ap.add_argument("--stack-rates", default="2000",
+                    help="arrival rates of the stacked served run, queries/s")
     ap.add_argument("--latency-steps", type=int, default=200,
                     help="steps of the plain path timed one by one for its p50/p99")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served HBM budget")
@@ -420,9 +424,10 @@ def run_batched(args, mix) -> dict:
                       else "own key set per query")}
 
 
-def run_served(args, mix) -> list:
+def run_served(args, mix, stack: int = 1, rates: str = "") -> list:
     """Poisson arrivals of the mix against resident databases and keys; the
-    continuous-batching server admits requests by the HBM budget."""
+    continuous-batching server admits requests by the HBM budget (stack > 1:
+    and answers up to `stack` queued requests of one shape together)."""
     import numpy as np
     import torch
     import workloads as W
@@ -446,12 +451,14 @@ def run_served(args, mix) -> list:
             raise SystemExit("served reference answer does not decompress")
         reference.append(h.out)
     out = []
-    for r_i, rate in enumerate(float(x) for x in args.rates.split(",") if x):
+    for r_i, rate in enumerate(float(x) for x in (rates or args.rates).split(",") if x):
         nreq = args.served_requests
         arrivals = W.poisson_arrivals(rate, nreq, 0x5E + r_i)
         order = [mix.items[i % len(mix.items)] for i in range(nreq)]
         handles = [mix.handle(it) for it in order]
         srv = pdq.Server(arena, lanes=8)
+        if stack > 1:
+            srv.set_stacking(stack)
         tickets = []
         t0 = time.perf_counter()
         for ta, h in zip(arrivals, handles):
@@ -470,6 +477,8 @@ def run_served(args, mix) -> list:
         out.append({"rate_qps": rate, "requests": nreq, "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99)), "served_qps": nreq / span,
                     "offered_s": float(arrivals[-1]), "all_ok": bool(ok),
+                    "stacking": stack,
+                    "mean_requests_per_launch": float(np.mean([i.stacked for i in infos])),
                     "all_decompress_exactly": bool(exact),
                     "check": "every result equal bit for bit to its query's answer alone, "
                              "which decrypts and decompresses to the query's matches"})
@@ -1121,6 +1130,9 @@ def run_gpu(args, cfg, rank: int, world: int):
         mix = Mix(args.mix, args.lanes)
         line["batched"] = run_batched(args, mix)
         line["served"] = run_served(args, mix)
+        if args.served_stack > 1:
+            line["served_stacked"] = run_served(args, mix, stack=args.served_stack,
+                                                rates=args.stack_rates)
         if args.clients > 0:
             del mix
             torch.cuda.empty_cache()

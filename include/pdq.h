@@ -453,8 +453,10 @@ int pdq_answer_batch(const pdq_ctx* ctx, const pdq_query* queries, uint32_t nq,
  * unbounded) caps the number of waiting requests (PDQ_E_BUSY beyond).  A
  * request whose workspace exceeds the whole arena is refused with
  * PDQ_E_NOMEM.  The caller keeps every buffer of a request alive until it is
- * done and must not enable stage profiling while a server runs.  Times are
- * host steady-clock nanoseconds. */
+ * done and must not enable stage profiling while a server runs.  The workers'
+ * streams do not wait on any stream of the caller: the arena and every buffer
+ * of a request must hold no pending work from other streams when they are
+ * handed over.  Times are host steady-clock nanoseconds. */
 typedef struct pdq_server pdq_server;
 #define PDQ_REQ_QUEUED 0
 #define PDQ_REQ_RUNNING 1
@@ -463,12 +465,25 @@ typedef struct {
     int32_t state;           /* PDQ_REQ_* */
     int32_t status;          /* result code once done */
     uint64_t t_submit_ns, t_start_ns, t_done_ns;
+    uint32_t stacked;        /* requests answered in the same launches (1: alone) */
+    uint32_t reserved;
 } pdq_ticket_info;
 int pdq_server_create(void* arena, size_t arena_bytes, uint32_t lanes, uint32_t max_queue,
                       pdq_server** out);
 int pdq_server_submit(pdq_server* srv, const pdq_ctx* ctx, const pdq_query* q,
                       uint64_t* ticket);
 int pdq_server_status(pdq_server* srv, uint64_t ticket, pdq_ticket_info* info);
+/* Stacking (continuous batching of requests of one shape): with max_stack
+ * >= 2, a worker that admits the oldest request also takes up to
+ * max_stack - 1 queued requests of the same context, database, plan
+ * constants, Galois list and plan shape (every plan field but the record and
+ * match counts, which only the client's Decomp reads), as many as the arena
+ * has room for, and answers them with one pdq_answer_stacked call (their
+ * index ciphertexts gathered into the workspace first, the outputs copied to
+ * each request's buffer after); each result is the same bits as the request
+ * alone.  0 or 1 turns it off (the default); at most 64.  Affects requests
+ * admitted after the call. */
+int pdq_server_set_stacking(pdq_server* srv, uint32_t max_stack);
 int pdq_server_wait(pdq_server* srv, uint64_t ticket, uint32_t timeout_ms);
 int pdq_server_drain(pdq_server* srv, uint32_t timeout_ms);
 int pdq_server_destroy(pdq_server* srv);

@@ -10,7 +10,10 @@
 // workspace fits into the free part of the caller's device arena (the
 // admission budget), launches Mask+Comp on its own stream and waits for it,
 // so requests that arrive while others run are admitted as soon as a lane
-// and memory free up, and their kernels overlap on the device.
+// and memory free up, and their kernels overlap on the device.  With
+// stacking on, the worker also takes queued requests of the oldest one's
+// shape and answers them all with one stacked call.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -127,8 +130,35 @@ struct Ticket {
     int state = PDQ_REQ_QUEUED;
     int status = PDQ_OK;
     u64 t_submit = 0, t_start = 0, t_done = 0;
+    u32 stacked = 0;
     std::string error;
 };
+
+// Requests that one stacked call can answer: the same context, database,
+// plan constants and Galois list, and plans equal in every field but the
+// record and match counts (the Answer's kernels never read those; the
+// client's Decomp does).
+bool stackable(const Request& r) { return !r.plan.plain_db && r.plan.ring_ratio <= 1; }
+
+bool same_shape(const Request& a, const Request& b) {
+    if (a.ctx != b.ctx || a.q.db != b.q.db || a.q.consts != b.q.consts || a.galois != b.galois)
+        return false;
+    pdq_plan x = a.plan, y = b.plan;
+    x.n = y.n = 0;
+    x.s = y.s = 0;
+    return std::memcmp(&x, &y, sizeof x) == 0;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// arena bytes of Q stacked requests: the stacked workspace, then the
+// gathered index ciphertexts and the outputs
+size_t stacked_bytes(const Request& r, u32 Q) {
+    const Ctx& c = *reinterpret_cast<const Ctx*>(r.ctx);
+    const size_t cts = ct_elems(c) * sizeof(u64);
+    return align256(pdq_answer_stacked_workspace_bytes(r.ctx, &r.plan, Q)) +
+           align256((size_t)Q * r.plan.J * cts) + align256((size_t)Q * r.plan.n_out * cts);
+}
 
 // first-fit allocator over the caller's arena (offsets aligned to 256 bytes)
 struct Arena {
@@ -187,6 +217,7 @@ struct pdq_server {
     std::vector<cudaStream_t> streams;
     int device = 0;
     u32 max_queue = 0;
+    u32 max_stack = 1;
     u64 next_ticket = 1;
     u64 inflight = 0;
     bool stop = false;
@@ -195,27 +226,53 @@ struct pdq_server {
         cudaSetDevice(device);
         cudaStream_t st = streams[lane];
         for (;;) {
-            Request req;
-            size_t off = 0;
+            std::vector<Request> batch;          // batch[0]: the oldest admitted request
+            size_t off = 0, bytes = 0;
             {
                 std::unique_lock<std::mutex> lock(mu);
                 cv_work.wait(lock, [&] {
                     return stop || (!queue.empty() && arena.alloc(queue.front().ws_bytes, &off));
                 });
                 if (stop) return;
-                req = std::move(queue.front());
+                batch.push_back(std::move(queue.front()));
                 queue.pop_front();
-                Ticket& t = tickets[req.ticket];
-                t.state = PDQ_REQ_RUNNING;
-                t.t_start = now_ns();
-                ++inflight;
+                bytes = batch[0].ws_bytes;
+                if (max_stack > 1 && stackable(batch[0])) {
+                    // queued requests of the same shape, in arrival order, as
+                    // many as a stacked workspace the arena can hold
+                    std::vector<size_t> idx;
+                    for (size_t i = 0; i < queue.size() && idx.size() + 1 < max_stack; ++i)
+                        if (same_shape(batch[0], queue[i])) idx.push_back(i);
+                    if (!idx.empty()) {
+                        arena.release(off, bytes);
+                        bool got = false;
+                        while (!idx.empty() && !got) {
+                            const size_t need = stacked_bytes(batch[0], (u32)idx.size() + 1);
+                            if (arena.alloc(need, &off)) { bytes = need; got = true; }
+                            else idx.pop_back();
+                        }
+                        // alone: the space it was admitted with is free again
+                        if (!got && !arena.alloc(bytes, &off)) {
+                            queue.push_front(std::move(batch[0]));
+                            continue;
+                        }
+                    }
+                    for (auto it = idx.rbegin(); it != idx.rend(); ++it) {
+                        batch.push_back(std::move(queue[*it]));
+                        queue.erase(queue.begin() + (long)*it);
+                    }
+                    std::reverse(batch.begin() + 1, batch.end());
+                }
+                for (const Request& r : batch) {
+                    Ticket& t = tickets[r.ticket];
+                    t.state = PDQ_REQ_RUNNING;
+                    t.t_start = now_ns();
+                    t.stacked = (u32)batch.size();
+                }
+                inflight += batch.size();
             }
             cv_work.notify_all();   // the next request may fit too
-            req.q.plan = &req.plan;
-            req.q.galois = req.galois.data();
-            int rc = pdq_answer(req.ctx, &req.plan, req.q.v_cts, req.q.db, req.q.keys,
-                                req.q.galois, req.q.nkeys, req.q.consts, req.q.out,
-                                arena.base + off, req.ws_bytes, st);
+            int rc = run(batch, arena.base + off, st);
             std::string err = rc == PDQ_OK ? std::string() : std::string(pdq_last_error());
             if (cudaStreamSynchronize(st) != cudaSuccess && rc == PDQ_OK) {
                 rc = PDQ_E_CUDA;
@@ -223,17 +280,55 @@ struct pdq_server {
             }
             {
                 std::lock_guard<std::mutex> lock(mu);
-                Ticket& t = tickets[req.ticket];
-                t.t_done = now_ns();
-                t.state = PDQ_REQ_DONE;
-                t.status = rc;
-                t.error = err;
-                arena.release(off, req.ws_bytes);
-                --inflight;
+                const u64 t_done = now_ns();
+                for (const Request& r : batch) {
+                    Ticket& t = tickets[r.ticket];
+                    t.t_done = t_done;
+                    t.state = PDQ_REQ_DONE;
+                    t.status = rc;
+                    t.error = err;
+                }
+                arena.release(off, bytes);
+                inflight -= batch.size();
             }
             cv_done.notify_all();
             cv_work.notify_all();
         }
+    }
+
+    // Answer the requests of `batch` (one, or several of one shape stacked)
+    // with the workspace at ws on stream st.
+    static int run(std::vector<Request>& batch, char* ws, cudaStream_t st) {
+        Request& r0 = batch[0];
+        for (Request& r : batch) {
+            r.q.plan = &r.plan;
+            r.q.galois = r.galois.data();
+        }
+        if (batch.size() == 1)
+            return pdq_answer(r0.ctx, &r0.plan, r0.q.v_cts, r0.q.db, r0.q.keys, r0.q.galois,
+                              r0.q.nkeys, r0.q.consts, r0.q.out, ws, r0.ws_bytes, st);
+        const u32 Q = (u32)batch.size();
+        const Ctx& c = *reinterpret_cast<const Ctx*>(r0.ctx);
+        const size_t cts = ct_elems(c) * sizeof(u64);
+        const size_t wsb = align256(pdq_answer_stacked_workspace_bytes(r0.ctx, &r0.plan, Q));
+        const size_t vb = (size_t)r0.plan.J * cts, ob = (size_t)r0.plan.n_out * cts;
+        char* vstage = ws + wsb;
+        char* ostage = vstage + align256((size_t)Q * vb);
+        const uint64_t* keys[kMaxStack];
+        for (u32 q = 0; q < Q; ++q) {
+            if (cudaMemcpyAsync(vstage + q * vb, batch[q].q.v_cts, vb, cudaMemcpyDeviceToDevice,
+                                st) != cudaSuccess)
+                return fail(PDQ_E_CUDA, "server: gathering a stacked query failed");
+            keys[q] = batch[q].q.keys;
+        }
+        PDQ_TRY(pdq_answer_stacked(r0.ctx, &r0.plan, Q, reinterpret_cast<const uint64_t*>(vstage),
+                                   r0.q.db, keys, r0.q.galois, r0.q.nkeys, r0.q.consts,
+                                   reinterpret_cast<uint64_t*>(ostage), ws, wsb, st));
+        for (u32 q = 0; q < Q; ++q)
+            if (cudaMemcpyAsync(batch[q].q.out, ostage + q * ob, ob, cudaMemcpyDeviceToDevice,
+                                st) != cudaSuccess)
+                return fail(PDQ_E_CUDA, "server: copying a stacked answer failed");
+        return PDQ_OK;
     }
 };
 
@@ -299,7 +394,17 @@ int pdq_server_status(pdq_server* s, uint64_t ticket, pdq_ticket_info* info) {
     info->t_submit_ns = it->second.t_submit;
     info->t_start_ns = it->second.t_start;
     info->t_done_ns = it->second.t_done;
+    info->stacked = it->second.stacked;
+    info->reserved = 0;
     if (it->second.status != PDQ_OK) set_error(it->second.error);
+    return PDQ_OK;
+}
+
+int pdq_server_set_stacking(pdq_server* s, uint32_t max_stack) {
+    if (!s) return fail(PDQ_E_PARAM, "server_set_stacking: null server");
+    if (max_stack > kMaxStack) return fail(PDQ_E_PARAM, "server_set_stacking: at most 64");
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->max_stack = max_stack < 1 ? 1 : max_stack;
     return PDQ_OK;
 }
 

@@ -64,7 +64,8 @@ class Query(ctypes.Structure):
 class TicketInfo(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("t_submit_ns", ctypes.c_uint64), ("t_start_ns", ctypes.c_uint64),
-                ("t_done_ns", ctypes.c_uint64)]
+                ("t_done_ns", ctypes.c_uint64), ("stacked", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 _P = ctypes.c_void_p
@@ -130,6 +131,7 @@ _SIGS = {
     "pdq_server_status": (_I, [_P, _U64, ctypes.POINTER(TicketInfo)]),
     "pdq_server_wait": (_I, [_P, _U64, _U32]),
     "pdq_server_drain": (_I, [_P, _U32]),
+    "pdq_server_set_stacking": (_I, [_P, _U32]),
     "pdq_server_destroy": (_I, [_P]),
     "pdq_cts_serialized_bytes": (_SZ, [_P, _U32]),
     "pdq_cts_export": (_I, [_P, _P, _U32, _P, _SZ, _P, _P]),
@@ -632,6 +634,10 @@ class Server:
 
     def __init__(self, arena: torch.Tensor, lanes: int = 4, max_queue: int = 0):
         self.arena = arena
+        # the workers' streams do not wait on the caller's: work queued there
+        # (on memory the caching allocator may have just handed to the arena)
+        # must finish before the server starts
+        torch.cuda.current_stream().synchronize()
         h = _P()
         _check(load().pdq_server_create(_ptr(arena), arena.numel() * arena.element_size(), lanes,
                                         max_queue, ctypes.byref(h)))
@@ -649,6 +655,10 @@ class Server:
         info = TicketInfo()
         _check(load().pdq_server_status(self.h, ticket, ctypes.byref(info)))
         return info
+
+    def set_stacking(self, max_stack: int):
+        """Answer up to max_stack queued requests of one shape together."""
+        _check(load().pdq_server_set_stacking(self.h, max_stack))
 
     def wait(self, ticket: int, timeout_ms: int = 600000):
         _check(load().pdq_server_wait(self.h, ticket, timeout_ms))

@@ -146,3 +146,48 @@ def test_server_waits_run_out_and_recover(mix):
         assert srv.status(t).status == 0
         assert torch.equal(h.out.view(alone[i].shape), alone[i])
     srv.close()
+
+
+def test_server_stacks_requests_of_one_shape(mix):
+    """With stacking on, queued requests of one shape (other clients of the
+    same database with the same record and match counts, each with its own
+    keys) are answered together; every result is still the request's answer
+    alone, and requests of other shapes in the same stream are unaffected."""
+    pdq = library()
+    sets, alone = mix
+    base = sets[0]
+    ctx, plan = base.ctx, base.plan
+    clients = [Setup("small", seed=50 + i, n=MIX[0][0], s=MIX[0][1], ctx=ctx) for i in range(4)]
+
+    def handle(st):
+        out = ctx._u64(plan.n_out * ctx.ct_elems)
+        return ctx.query(plan, st.v_cts, base.db, st.keys, base.galois, base.consts, out)
+
+    want = [ctx.answer(plan, st.v_cts, base.db, st.keys, base.galois, base.consts).clone()
+            for st in clients]
+    # the server's streams do not order after this one: its arena must not be
+    # memory that the answers above still use
+    torch.cuda.synchronize()
+    arena = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    srv = pdq.Server(arena, lanes=1)
+    srv.set_stacking(8)
+    subs = []
+    for _ in range(3):
+        for i, st in enumerate(clients):
+            h = handle(st)
+            subs.append((srv.submit(h), h, want[i]))
+        for j, st in enumerate(sets):
+            h = st.handle()
+            subs.append((srv.submit(h), h, alone[j]))
+    srv.drain()
+    infos = [srv.status(t) for t, _, _ in subs]
+    assert max(i.stacked for i in infos) > 1, "no requests were stacked"
+    bad = [(k, info.stacked) for k, (info, (_, h, w)) in enumerate(zip(infos, subs))
+           if not torch.equal(h.out.view(w.shape), w)]
+    for info in infos:
+        assert info.state == pdq.PDQ_REQ_DONE and info.status == 0 and info.stacked >= 1
+    assert not bad, f"(request, stack size) differing from alone: {bad}"
+    with pytest.raises(pdq.PdqError):
+        srv.set_stacking(65)
+    srv.close()

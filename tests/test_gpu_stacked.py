@@ -27,6 +27,7 @@ def _queries(cfg_name, Q, **kw):
     ("c1", 2, {}),
     ("grouped", 3, {}),                   # 8 record groups, two outputs per query
     ("grouped", 2, {"n": 1700}),          # a partial last group and a partial output
+    ("small", 8, {}),
 ])
 def test_stacked_answers_equal_alone(cfg_name, Q, kw):
     base, sets = _queries(cfg_name, Q, **kw)
