@@ -63,6 +63,8 @@ def parse():
                     help="baby-step count of the unencrypted-database plan (0: its cost rule)")
     ap.add_argument("--stacked", type=int, default=1,
                     help="queries of one plan answered together (0: skip)")
+    ap.add_argument("--stacked-configs", default="",
+                    help="comma-separated configurations of the stacked leg (default: all)")
     ap.add_argument("--tune", type=int, default=1,
                     help="also run the batched mix with autotuned plans (0: skip)")
     ap.add_argument("--tune-cache", default="", help="JSON file of tuned plans (read and written)")
@@ -872,7 +874,10 @@ def run_stacked(args, rank: int) -> list:
 
     stream = torch.cuda.current_stream()
     rows = []
+    only = {x for x in args.stacked_configs.split(",") if x}
     for name, n, s_, Q in STACK_SHAPES:
+        if only and name not in only:
+            continue
         cfg = dataclasses.replace(W.CONFIGS[name], n=n, s=s_)
         ctx = pdq.Context.from_config(cfg)
         q0 = W.draw_query(cfg, cfg.seed + rank)
@@ -930,8 +935,15 @@ def run_stacked(args, rank: int) -> list:
         reps = 3 if name == "c3" else 10
         t_plain = timed(plain, reps)
         l0 = pdq.pdq_launch_count()
+        # (NVTX ranges let a profiler select one stacked call and one alone)
+        torch.cuda.nvtx.range_push(f"stacked_{name}")
         together()
+        torch.cuda.nvtx.range_pop()
         launches = pdq.pdq_launch_count() - l0
+        torch.cuda.nvtx.range_push(f"alone_{name}")
+        ctx.answer(plan, v_all[0], db, keys[0], galois, consts, ws=aws, out=alone[0],
+                   stream=stream)
+        torch.cuda.nvtx.range_pop()
         t_stacked = timed(together, reps)
         torch.cuda.synchronize()
         out_q = stacked.view(Q, -1)
