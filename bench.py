@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--tune", type=int, default=1,
                     help="also run the batched mix with autotuned plans (0: skip)")
     ap.add_argument("--tune-cache", default="", help="JSON file of tuned plans (read and written)")
+    ap.add_argument("--tune-schedule", type=int, default=1,
+                    help="autotune the context's launch schedule on the benchmark's shape first")
     ap.add_argument("--rotation-budget-gib", type=float, default=2.0,
                     help="also time the Answer holding at most this many GiB of baby-step "
                          "rotations (0: skip)")
@@ -978,6 +980,16 @@ def run_gpu(args, cfg, rank: int, world: int):
     ctx = pdq.Context.from_config(cfg)
     q = W.draw_query(cfg, cfg.seed + rank)
     plan = ctx.plan(cfg.n, cfg.s, args.B)
+    sched_tuning = None
+    if args.tune_schedule:
+        # the launch schedule of the context (transform phase split,
+        # multiply-accumulate tiles): timed on a synthetic query of this shape,
+        # the fastest kept; every schedule gives the same bits
+        from paper_2408_17063_gb300 import tune
+        t0 = time.perf_counter()
+        hit = tune.ScheduleTuner(args.tune_cache or None, reps=2).best(ctx, cfg.n, cfg.s, args.B)
+        sched_tuning = dict(hit, tuning_s=time.perf_counter() - t0)
+        torch.cuda.empty_cache()
     galois = ctx.plan_galois(plan)
     sk = ctx.secret_prepare(torch.from_numpy(q.sk))
     N = ctx.N
@@ -1095,6 +1107,8 @@ def run_gpu(args, cfg, rank: int, world: int):
     mac_ms, mac_calls = stages["mac"]
     mac_ms_per = mac_ms / max(1, mac_calls)
     roofline = mac_roofline(ctx, plan, mac_ms_per)
+    if ctx.schedule()["mac_tiles"] or ctx.schedule()["mac_bc"]:
+        roofline["traffic"] = None        # captured under the default tiles
     ms_sorted = lat if lat else sorted(per)
     p50 = statistics.median(ms_sorted)
     p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]
@@ -1114,6 +1128,9 @@ def run_gpu(args, cfg, rank: int, world: int):
             "stages_ms_per_query": {k: v[0] / max(1, args.steps) for k, v in stages.items()},
             "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps,
             "clocks": clk, "e2e": e2e, "roofline": roofline}
+    line["config"]["schedule"] = ctx.schedule()
+    if sched_tuning:
+        line["schedule_tuning"] = sched_tuning
     if budget_leg:
         line["rotation_budget"] = budget_leg
     if args.paper_shapes:

@@ -135,6 +135,25 @@ const char* pdq_last_error(void);
  * Set it before sizing workspaces; not while a call on the context runs. */
 int pdq_ctx_set_rotation_budget(pdq_ctx* ctx, uint64_t bytes);
 
+/* Launch schedule of the transforms and of the diagonal multiply-accumulate
+ * (Sec. 5.2's products): the knobs an autotuner searches; every schedule
+ * gives the same bits.  ntt_row_bits: levels in the row phase of a transform
+ * of N > 2^11, 7..11 and below log N (the column phase takes the other
+ * levels); mac_tiles: position tiles per multiply-accumulate CTA, 1, 2, 4 or
+ * 8; mac_bc: baby steps staged per copy step, 1, 2, 4, 8 or 16 (fewer where
+ * shared memory requires).  0 keeps the library's rule for a knob (9 row
+ * levels; 8 tiles while 64 CTAs per prime remain; 16 baby steps).  Errors:
+ * PDQ_E_PARAM for other values.  Set it before the calls it should affect,
+ * not while a call on the context runs. */
+typedef struct {
+    uint32_t ntt_row_bits;
+    uint32_t mac_tiles;
+    uint32_t mac_bc;
+    uint32_t reserved;
+} pdq_schedule;
+int pdq_ctx_set_schedule(pdq_ctx* ctx, const pdq_schedule* sched);
+int pdq_ctx_get_schedule(const pdq_ctx* ctx, pdq_schedule* sched);
+
 /* ------------------------------------------------------------- transforms
  * Negacyclic transform of polynomials in Z_q[X]/(X^N+1) (the ring of
  * Sec. 5.1), in place on `count` groups of `nlimbs` limbs: group g, limb l is

@@ -666,6 +666,27 @@ int pdq_mod_switch(const pdq_ctx* from, const pdq_ctx* to, const uint64_t* cts, 
     return mod_switch(a, b.L, cts, count, out, reinterpret_cast<u64*>(ws), (cudaStream_t)stream);
 }
 
+int pdq_ctx_set_schedule(pdq_ctx* ctx, const pdq_schedule* sched) {
+    PDQ_CHECK_CTX(ctx);
+    if (!sched) return fail(PDQ_E_PARAM, "schedule: null");
+    Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+    const u32 rb = sched->ntt_row_bits, mt = sched->mac_tiles, bc = sched->mac_bc;
+    if (rb && (rb < 7 || rb > 11 || rb >= c.log_n))
+        return fail(PDQ_E_PARAM, "schedule: row levels must be 7..11 and below log N");
+    if (mt && (mt > 8 || (mt & (mt - 1)))) return fail(PDQ_E_PARAM, "schedule: 1, 2, 4 or 8 tiles");
+    if (bc && (bc > 16 || (bc & (bc - 1)))) return fail(PDQ_E_PARAM, "schedule: 1..16 baby steps, a power of two");
+    c.sched = *sched;
+    c.sched.reserved = 0;
+    return PDQ_OK;
+}
+
+int pdq_ctx_get_schedule(const pdq_ctx* ctx, pdq_schedule* sched) {
+    PDQ_CHECK_CTX(ctx);
+    if (!sched) return fail(PDQ_E_PARAM, "schedule: null");
+    *sched = C(ctx).sched;
+    return PDQ_OK;
+}
+
 int pdq_ctx_set_rotation_budget(pdq_ctx* ctx, uint64_t bytes) {
     if (!ctx) return fail(PDQ_E_PARAM, "null context");
     reinterpret_cast<Ctx*>(ctx)->rotation_budget = bytes;

@@ -318,6 +318,20 @@ int launch_phase(int S, dim3 grid, u32 threads, const NttArgs& a, cudaStream_t s
     return launched("ntt_phase_kernel");
 }
 
+// the row phase of a two-phase transform, R = 7..11 levels
+template <bool FWD>
+int launch_rows(u32 R, dim3 grid, const NttArgs& a, cudaStream_t st) {
+    switch (R) {
+        case 7: ntt_phase_kernel<FWD, 7, false, false><<<grid, kThreads, 0, st>>>(a); break;
+        case 8: ntt_phase_kernel<FWD, 8, false, false><<<grid, kThreads, 0, st>>>(a); break;
+        case 9: ntt_phase_kernel<FWD, 9, false, false><<<grid, kThreads, 0, st>>>(a); break;
+        case 10: ntt_phase_kernel<FWD, 10, false, false><<<grid, kThreads, 0, st>>>(a); break;
+        case 11: ntt_phase_kernel<FWD, 11, false, false><<<grid, kThreads, 0, st>>>(a); break;
+        default: return fail(PDQ_E_PARAM, "ntt: unsupported row phase");
+    }
+    return launched("ntt_phase_kernel");
+}
+
 template <bool FWD>
 int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
             cudaStream_t st, const NttArgs* from = nullptr, u32 skip_nd = 0, u32 skip_alpha = 0) {
@@ -350,25 +364,27 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
         u32 threads = c.N / 8 < 32 ? 32 : (c.N / 8 > kThreads ? kThreads : c.N / 8);
         return launch_phase<FWD, false, true>((int)c.log_n, dim3((u32)polys, 1), threads, a, st);
     }
-    const u32 S1 = c.log_n - kRowBits;
+    // row phase: R levels (the schedule's, else kRowBits), column phase the rest
+    const u32 R = c.sched.ntt_row_bits ? c.sched.ntt_row_bits : kRowBits;
+    if (R < 7 || R > kTileBits || R >= c.log_n || c.log_n - R > kTileBits)
+        return fail(PDQ_E_PARAM, "ntt: unsupported phase split");
+    const u32 S1 = c.log_n - R;
     a.S1 = S1;
     NttArgs cols = a, rows = a;
     (FWD ? rows : cols).src = nullptr;        // the second phase works in place
     cols.logC = kTileBits - S1;                // 2^S1 * C = tile
-    rows.logC = kTileBits - kRowBits;          // 4 rows of 512
-    const dim3 gcols((u32)polys, (1u << kRowBits) >> cols.logC);
+    rows.logC = kTileBits - R;                 // 2^(11-R) rows of 2^R
+    const dim3 gcols((u32)polys, (1u << R) >> cols.logC);
     const dim3 grows((u32)polys, (1u << S1) >> rows.logC);
     if (FWD) {
         cols.last = 0;
         rows.last = 1;
         PDQ_TRY((launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cols, st)));
-        ntt_phase_kernel<FWD, kRowBits, false, false><<<grows, kThreads, 0, st>>>(rows);
-        return launched("ntt_phase_kernel");
+        return launch_rows<FWD>(R, grows, rows, st);
     }
     rows.last = 0;
     cols.last = 1;
-    ntt_phase_kernel<FWD, kRowBits, false, false><<<grows, kThreads, 0, st>>>(rows);
-    PDQ_TRY(launched("ntt_phase_kernel"));
+    PDQ_TRY(launch_rows<FWD>(R, grows, rows, st));
     return launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cols, st);
 }
 

@@ -1907,7 +1907,7 @@ constexpr u32 kMacPC = 2;                // polynomials (of one group) per threa
 constexpr u32 kMacSmem = 100u << 10;     // two CTAs per SM
 constexpr u32 kMacMinX = 2;
 
-MacShape mac_shape(const pdq_plan& pl, u32 logN, u32 Q = 1) {
+MacShape mac_shape(const pdq_plan& pl, u32 logN, u32 Q = 1, const pdq_schedule* sc = nullptr) {
     MacShape s{};
     const u32 GI = pl.giants, combos = 2 * pl.G * Q;
     s.GT = GI < 4 ? GI : 4;
@@ -1925,6 +1925,7 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN, u32 Q = 1) {
     while (((ct * GS) << (logX + 1)) <= kMacThreads && logX < 8) ++logX;
     if (logX > logN) logX = logN;
     u32 Bc = pl.B < 16 ? pl.B : 16;
+    if (sc && sc->mac_bc && sc->mac_bc < Bc) Bc = sc->mac_bc;
     auto bytes = [&](u32 bc, u32 lx) {
         return 2 * ((size_t)bc * (1u << lx) * (GI + 2 + s.combos_per_cta) + 2 * s.combos_per_cta) * 8;
     };
@@ -1938,7 +1939,12 @@ MacShape mac_shape(const pdq_plan& pl, u32 logN, u32 Q = 1) {
     // several position tiles per CTA so that the copy pipeline runs long
     const u32 tiles = 1u << (logN - logX);
     s.tiles_per_cta = 1;
-    while (s.tiles_per_cta < 8 && tiles / (s.tiles_per_cta * 2) >= 64) s.tiles_per_cta *= 2;
+    if (sc && sc->mac_tiles) {
+        while (s.tiles_per_cta < sc->mac_tiles && tiles / (s.tiles_per_cta * 2) >= 1)
+            s.tiles_per_cta *= 2;
+    } else {
+        while (s.tiles_per_cta < 8 && tiles / (s.tiles_per_cta * 2) >= 64) s.tiles_per_cta *= 2;
+    }
     return s;
 }
 
@@ -2003,7 +2009,7 @@ int diag_mac(const Ctx& c, const pdq_plan& pl, const u64* R, const u64* Dg, u64*
     // while every group index times pl.G stays below 2^32)
     if (Q == 0 || pl.G == 0 || (u64)pl.G * Q * pl.G >= (1ull << 32))
         return fail(PDQ_E_PARAM, "diag_mac: too many groups for one launch");
-    const MacShape s = mac_shape(pl, c.log_n, Q);
+    const MacShape s = mac_shape(pl, c.log_n, Q, &c.sched);
     if (el == 0) el = c.L + c.K - l0;
     if (l0 + el > c.L + c.K) return fail(PDQ_E_PARAM, "diag_mac: bad prime range");
     if (s.zslices > 65535) return fail(PDQ_E_PARAM, "diag_mac: too many groups");

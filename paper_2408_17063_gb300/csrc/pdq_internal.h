@@ -182,6 +182,8 @@ struct Ctx {
     // them); smaller budgets produce and consume them a chunk of primes at a
     // time (pdq_ctx_set_rotation_budget)
     u64 rotation_budget = 0;
+    // launch schedule knobs (pdq_ctx_set_schedule; 0: the library's rule)
+    pdq_schedule sched{};
 };
 
 void lanes_release(Ctx* c);

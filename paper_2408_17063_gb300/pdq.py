@@ -45,6 +45,15 @@ class Info(ctypes.Structure):
                 ("moduli", ctypes.c_uint64 * MAX_MODULI), ("psi", ctypes.c_uint64 * MAX_MODULI)]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("ntt_row_bits", ctypes.c_uint32), ("mac_tiles", ctypes.c_uint32),
+                ("mac_bc", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {"ntt_row_bits": self.ntt_row_bits, "mac_tiles": self.mac_tiles,
+                "mac_bc": self.mac_bc}
+
+
 class Plan(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64)] + [(f, ctypes.c_uint32) for f in (
         "s", "s_prime", "B", "giants", "J", "H", "G_sz", "hpg", "G", "hclass", "per_out",
@@ -92,6 +101,8 @@ _SIGS = {
     "pdq_rotate_workspace_bytes": (_SZ, [_P, _U32]),
     "pdq_rotate": (_I, [_P, _P, _U32, _U64, _P, _P, _P, _SZ, _P]),
     "pdq_ctx_set_rotation_budget": (_I, [_P, _U64]),
+    "pdq_ctx_set_schedule": (_I, [_P, ctypes.POINTER(Schedule)]),
+    "pdq_ctx_get_schedule": (_I, [_P, ctypes.POINTER(Schedule)]),
     "pdq_plan_make": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_plan_make_switched": (_I, [_P, _U32, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_plan_make_plain_db": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
@@ -233,6 +244,17 @@ class Context:
         """pdq_ctx_set_rotation_budget: hold at most nbytes of baby-step
         rotations (0: all), made and consumed a chunk of primes at a time."""
         _check(load().pdq_ctx_set_rotation_budget(self.h, int(nbytes)))
+
+    def set_schedule(self, ntt_row_bits: int = 0, mac_tiles: int = 0, mac_bc: int = 0):
+        """pdq_ctx_set_schedule: launch-schedule knobs (0: the library's rule);
+        results are the same bits under every schedule."""
+        sc = Schedule(ntt_row_bits, mac_tiles, mac_bc, 0)
+        _check(load().pdq_ctx_set_schedule(self.h, ctypes.byref(sc)))
+
+    def schedule(self) -> dict:
+        sc = Schedule()
+        _check(load().pdq_ctx_get_schedule(self.h, ctypes.byref(sc)))
+        return sc.as_dict()
 
     def subring(self, log_n: int) -> "Context":
         """pdq_ctx_create_subring: the subring of dimension 2^log_n on this

@@ -14,6 +14,12 @@ Choices persist in a JSON file keyed by the parameter set and the plan shape
 (ring dimension, primes, digits, t, records, s', and the Answer kind), so a
 server tunes each shape once.  Tuning allocates the keys, plan constants and
 workspace of each candidate in turn (at N = 2^15, n = 2^20: about 17 GB).
+
+ScheduleTuner does the same for the launch schedule of a context
+(pdq_ctx_set_schedule: the phase split of the transforms, the position tiles
+per CTA and the baby steps per copy step of the multiply-accumulate), by
+coordinate descent over the knobs on one query shape; every schedule gives
+the same bits, so only the time decides.
 """
 from __future__ import annotations
 
@@ -80,7 +86,19 @@ class PlanTuner:
 
     def time_answer(self, ctx: pdq.Context, n: int, s: int, B: int, stream=None) -> float:
         """Milliseconds per Answer with plan B on synthetic inputs."""
+        rig = AnswerRig(ctx, n, s, B, stream)
+        ms = rig.time(self.reps)
+        rig.close()
+        return ms
+
+
+class AnswerRig:
+    """One synthetic Answer of a shape (random secret, keys, database and index
+    vector: the timing does not depend on the values), ready to be timed."""
+
+    def __init__(self, ctx: pdq.Context, n: int, s: int, B: int = 0, stream=None):
         stream = stream or torch.cuda.current_stream()
+        self.ctx, self.stream = ctx, stream
         gen = torch.Generator(device="cpu").manual_seed(B * 1_000_003 + n)
         plan = ctx.plan(n, s, B)
         galois = ctx.plan_galois(plan)
@@ -102,23 +120,86 @@ class PlanTuner:
                                        dtype=torch.int64) % q for q in ctx.moduli[:ctx.L]], dim=1)
         e = torch.randint(-3, 4, (plan.J, ctx.N), generator=gen, dtype=torch.int32)
         v_cts = ctx.encrypt(sk, slots, a.contiguous(), e, stream=stream)
-        ws = ctx.answer_workspace(plan)
-        out = ctx._u64(plan.n_out * ctx.ct_elems)
+        self.plan = plan
+        self.bufs = dict(v_cts=v_cts, db=db, keys=keys, galois=galois, consts=consts,
+                         ws=ctx.answer_workspace(plan), out=ctx._u64(plan.n_out * ctx.ct_elems))
 
-        def run():
-            ctx.answer(plan, v_cts, db, keys, galois, consts, ws=ws, out=out, stream=stream)
+    def run(self):
+        b = self.bufs
+        self.ctx.answer(self.plan, b["v_cts"], b["db"], b["keys"], b["galois"], b["consts"],
+                        ws=b["ws"], out=b["out"], stream=self.stream)
 
-        run()
+    def time(self, reps: int = 3) -> float:
+        """Milliseconds per Answer (CUDA events on the stream, after one warm-up)."""
+        self.run()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record(stream)
-        for _ in range(self.reps):
-            run()
-        ev[1].record(stream)
+        ev[0].record(self.stream)
+        for _ in range(reps):
+            self.run()
+        ev[1].record(self.stream)
         ev[1].synchronize()
-        ms = ev[0].elapsed_time(ev[1]) / self.reps
-        del keys, consts, ws, out, v_cts, db, sk
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    def close(self):
+        self.bufs = {}
         torch.cuda.empty_cache()
-        return ms
+
+
+# knob -> candidate values (0: the library's rule)
+SCHEDULE_KNOBS = {"ntt_row_bits": [8, 9, 10], "mac_tiles": [2, 4, 8], "mac_bc": [8, 16]}
+
+
+def schedule_candidates(ctx: pdq.Context, knob: str) -> list[int]:
+    vals = SCHEDULE_KNOBS[knob]
+    if knob == "ntt_row_bits":       # two-phase transforms only, both phases <= 2^11
+        vals = [r for r in vals if r < ctx.log_n and ctx.log_n - r <= 11]
+    return [0] + vals
+
+
+class ScheduleTuner:
+    """Coordinate descent over the launch-schedule knobs of a context, timed on
+    one Answer shape; persisted like PlanTuner's choices."""
+
+    def __init__(self, path: str | None = None, reps: int = 3):
+        self.path = path
+        self.reps = reps
+        self.cache: dict = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                self.cache = json.load(f)
+
+    save = PlanTuner.save
+
+    def best(self, ctx: pdq.Context, n: int, s: int, B: int = 0, stream=None) -> dict:
+        """The fastest schedule for Answers of n records and sparsity s (plan
+        B) on ctx; the context is left on it."""
+        key = "schedule:" + shape_key(ctx, n, s) + f":B{B}"
+        with _LOCK:
+            hit = self.cache.get(key)
+        if hit is None:
+            rig = AnswerRig(ctx, n, s, B, stream)
+            cur = {k: 0 for k in SCHEDULE_KNOBS}
+            ctx.set_schedule(**cur)
+            default_ms = rig.time(self.reps)
+            tried = {json.dumps(cur, sort_keys=True): default_ms}
+            best_ms = default_ms
+            for knob in SCHEDULE_KNOBS:
+                for v in schedule_candidates(ctx, knob):
+                    cand = dict(cur, **{knob: v})
+                    tag = json.dumps(cand, sort_keys=True)
+                    if tag not in tried:
+                        ctx.set_schedule(**cand)
+                        tried[tag] = rig.time(self.reps)
+                    if tried[tag] < best_ms:
+                        best_ms, cur = tried[tag], cand
+            rig.close()
+            hit = {"schedule": cur, "ms": best_ms, "default_ms": default_ms,
+                   "tried": {k: v for k, v in sorted(tried.items())}}
+            with _LOCK:
+                self.cache[key] = hit
+                self.save()
+        ctx.set_schedule(**hit["schedule"])
+        return hit
 
 
 def tune_plan(ctx: pdq.Context, n: int, s: int, tuner: PlanTuner | None = None, stream=None):
@@ -127,4 +208,5 @@ def tune_plan(ctx: pdq.Context, n: int, s: int, tuner: PlanTuner | None = None, 
     return ctx.plan(n, s, tuner.best(ctx, n, s, stream))
 
 
-__all__ = ["PlanTuner", "tune_plan", "candidates", "shape_key"]
+__all__ = ["PlanTuner", "ScheduleTuner", "AnswerRig", "tune_plan", "candidates",
+           "schedule_candidates", "shape_key"]

@@ -31,3 +31,47 @@ def test_tuner_picks_the_fastest_admissible_split_and_persists_it(tmp_path):
     slots = tuned.ctx.decrypt(tuned.sk, tuned.answer()).cpu().numpy()
     assert tuned.ctx.decomp(tuned.plan, slots) == [(int(i), int(tuned.q.db[i]))
                                                    for i in tuned.q.positions]
+
+
+@pytest.mark.parametrize("cfg_name", ["c1", "grouped"])
+def test_every_schedule_gives_the_same_bits(cfg_name):
+    """The schedule knobs (transform phase split, multiply-accumulate tiles and
+    staged baby steps) change launches, never results."""
+    st = Setup(cfg_name)
+    ctx = st.ctx
+    ctx.set_schedule()
+    want = st.answer().clone()
+    rows = [r for r in tune.schedule_candidates(ctx, "ntt_row_bits") if r] or [0]
+    for rb in rows:
+        for mt in (1, 2, 8):
+            for bc in (1, 4, 16):
+                ctx.set_schedule(ntt_row_bits=rb, mac_tiles=mt, mac_bc=bc)
+                assert ctx.schedule() == {"ntt_row_bits": rb, "mac_tiles": mt, "mac_bc": bc}
+                assert st.answer().equal(want), (rb, mt, bc)
+    ctx.set_schedule()
+
+
+def test_schedule_refuses_bad_knobs():
+    from paper_2408_17063_gb300 import pdq
+    ctx = Setup("c1").ctx
+    for kw in ({"ntt_row_bits": 6}, {"ntt_row_bits": 12}, {"mac_tiles": 3}, {"mac_bc": 32}):
+        with pytest.raises(pdq.PdqError):
+            ctx.set_schedule(**kw)
+    ctx.set_schedule()
+
+
+def test_schedule_tuner_keeps_the_fastest_and_persists_it(tmp_path):
+    st = Setup("c1")
+    ctx, cfg = st.ctx, st.cfg
+    path = tmp_path / "sched.json"
+    tuner = tune.ScheduleTuner(str(path), reps=2)
+    hit = tuner.best(ctx, cfg.n, cfg.s)
+    assert hit["ms"] == min(hit["tried"].values()) and hit["ms"] <= hit["default_ms"]
+    assert ctx.schedule() == hit["schedule"]
+    saved = json.loads(path.read_text())
+    assert [v["schedule"] for v in saved.values()] == [hit["schedule"]]
+    ctx.set_schedule()
+    again = tune.ScheduleTuner(str(path))
+    assert again.best(ctx, cfg.n, cfg.s)["schedule"] == hit["schedule"]
+    assert ctx.schedule() == hit["schedule"]
+    ctx.set_schedule()
