@@ -1697,10 +1697,12 @@ int ks_apply_giants(const Ctx& c, const u64* D, u32 cnt, u32 terms, const u64* g
 
 namespace {
 
-template <int ND>
+// HC ciphertexts per CTA, CPT per thread: 16 and 8, or 2 and 1 for queries
+// of at most 2 ciphertexts (a CTA holds one query's, which share a key set)
+template <int ND, u32 HC = 16, u32 CPT = 8>
 int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const KeyTable& kt,
                 const BabyParams& bp, u64* Rx, cudaStream_t st, bool ext, u32 l0, u32 el) {
-    constexpr u32 T = 64, HC = 16, CPT = 8;
+    constexpr u32 T = 64;
     const u32 E = c.L + c.K;
     const size_t smem = ((size_t)HC * ND * T + 2 * HC * T) * sizeof(u64);
     // set once per process (thread-safe static initialisation; the server's
@@ -1777,6 +1779,19 @@ int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
         bp.koff[a] = key_offsets[a];
     }
     const KeyTable t = kt ? *kt : single_keys(keys);
+    const u32 Hq = t.per == ~0u ? H : t.per;
+    if (Hq <= 2) {
+        switch (c.ndigits) {
+            case 1: return launch_baby<1, 2, 1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            case 2: return launch_baby<2, 2, 1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            case 3: return launch_baby<3, 2, 1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            case 4: return launch_baby<4, 2, 1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            case 5: return launch_baby<5, 2, 1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            case 6: return launch_baby<6, 2, 1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            case 7: return launch_baby<7, 2, 1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            default: return launch_baby<8, 2, 1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+        }
+    }
     switch (c.ndigits) {
         case 1: return launch_baby<1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
         case 2: return launch_baby<2>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
