@@ -18,8 +18,8 @@ workspace of each candidate in turn (at N = 2^15, n = 2^20: about 17 GB).
 ScheduleTuner does the same for the launch schedule of a context
 (pdq_ctx_set_schedule: the phase split of the transforms, the position tiles
 per CTA and the baby steps per copy step of the multiply-accumulate), by
-coordinate descent over the knobs on one query shape; every schedule gives
-the same bits, so only the time decides.
+coordinate descent over the knobs on one query shape (a knob moves only for a
+gain above 1%); every schedule gives the same bits, so only the time decides.
 """
 from __future__ import annotations
 
@@ -160,9 +160,12 @@ class ScheduleTuner:
     """Coordinate descent over the launch-schedule knobs of a context, timed on
     one Answer shape; persisted like PlanTuner's choices."""
 
-    def __init__(self, path: str | None = None, reps: int = 3):
+    def __init__(self, path: str | None = None, reps: int = 3, min_gain: float = 0.01):
         self.path = path
         self.reps = reps
+        # a knob leaves the library's rule only for a gain above this fraction
+        # (smaller differences are run-to-run noise)
+        self.min_gain = min_gain
         self.cache: dict = {}
         if path and os.path.exists(path):
             with open(path) as f:
@@ -190,7 +193,7 @@ class ScheduleTuner:
                     if tag not in tried:
                         ctx.set_schedule(**cand)
                         tried[tag] = rig.time(self.reps)
-                    if tried[tag] < best_ms:
+                    if tried[tag] < best_ms * (1 - self.min_gain):
                         best_ms, cur = tried[tag], cand
             rig.close()
             hit = {"schedule": cur, "ms": best_ms, "default_ms": default_ms,
