@@ -85,3 +85,24 @@ def test_stacked_refuses_bad_arguments():
     small = ctx.answer_stacked_workspace(plan, 1)
     with pytest.raises(pdq.PdqError, match="workspace"):
         ctx.answer_stacked(plan, v, base.db, keys, base.galois, base.consts, ws=small)
+
+
+def test_stacked_under_rotation_budget_and_schedule():
+    """Stacked queries with the baby-step rotations made a prime at a time (a
+    rotation budget) and a non-default launch schedule: still each query's
+    answer alone (taken with the defaults)."""
+    base, sets = _queries("c1", 3)
+    ctx, plan = base.ctx, base.plan
+    want = [ctx.answer(plan, st.v_cts, base.db, st.keys, base.galois, base.consts).clone()
+            for st in sets]
+    v = torch.cat([st.v_cts.reshape(-1) for st in sets])
+    try:
+        ctx.set_rotation_budget(1)            # one prime's rotations at a time
+        ctx.set_schedule(ntt_row_bits=8, mac_tiles=1, mac_bc=4)
+        got = ctx.answer_stacked(plan, v, base.db, [st.keys for st in sets], base.galois,
+                                 base.consts)
+        for i in range(len(sets)):
+            assert torch.equal(got[i], want[i]), f"query {i}"
+    finally:
+        ctx.set_rotation_budget(0)
+        ctx.set_schedule()
