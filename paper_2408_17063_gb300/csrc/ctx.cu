@@ -176,7 +176,8 @@ static void free_ctx(Ctx* c) {
                     c->d_dn_hatinv_shoup, c->d_dn_hatmod, c->d_dn_hatmod_shoup,
                     c->d_dn_pinv, c->d_dn_pinv_shoup, c->d_P_mod_q, c->d_P_mod_q_shoup, c->d_delta_mod_q,
                     c->d_dec_omega, c->d_dec_omega_shoup, c->d_ckar,
-                    c->d_up_hatmod_mont, c->d_up_hatmod_mont_shoup, c->d_P_mont, c->d_ms};
+                    c->d_up_hatmod_mont, c->d_up_hatmod_mont_shoup, c->d_P_mont, c->d_ms,
+                    c->d_ninv_up, c->d_up_mont2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
@@ -359,6 +360,23 @@ static int build_ctx(const pdq_params& p, Ctx* c, const std::vector<u64>* given 
         }
     PDQ_TRY(upload(&c->d_up_hatmod_mont, up_mont));
     PDQ_TRY(upload(&c->d_up_hatmod_mont_shoup, up_mont_s));
+    // the raise with the conversion folded into the transforms: limb i's
+    // inverse transform ends scaled by hat_inv_i, the forward transform of a
+    // raised digit reads (hatmod R, Shoup) pairs
+    std::vector<u64> ninv_up(ninv), up_mont2(2 * up_mont.size());
+    for (u32 i = 0; i < L; ++i) {
+        const u64 q = c->mods[i];
+        ninv_up[4 * i + 0] = mulmod_h(ninv[4 * i + 0], up_inv[i], q);
+        ninv_up[4 * i + 1] = shoup_of(ninv_up[4 * i + 0], q);
+        ninv_up[4 * i + 2] = mulmod_h(ninv[4 * i + 2], up_inv[i], q);
+        ninv_up[4 * i + 3] = shoup_of(ninv_up[4 * i + 2], q);
+    }
+    for (size_t k = 0; k < up_mont.size(); ++k) {
+        up_mont2[2 * k] = up_mont[k];
+        up_mont2[2 * k + 1] = up_mont_s[k];
+    }
+    PDQ_TRY(upload(&c->d_ninv_up, ninv_up));
+    PDQ_TRY(upload(&c->d_up_mont2, up_mont2));
 
     // ModDown constants
     std::vector<u64> dn_inv(K), dn_inv_s(K), dn_mod((size_t)K * L), pinv(L), pinv_s(L);

@@ -52,6 +52,13 @@ struct NttArgs {
     // raised digits (skip_alpha > 0): group g is digit g % skip_nd of a
     // ciphertext, and its limbs skip the digit's own skip_alpha limbs
     u32 skip_nd, skip_alpha;
+    // the raise's basis conversion in the first (column) phase of the forward
+    // transform of raised digits: element = sum_{k < skip_alpha} y_k * hm_k
+    // (Shoup), y_k = up_src[ct][b skip_alpha + k] ([.][up_L][N]), hm_k =
+    // up_hm[(b skip_alpha + k) * up_E + prime]
+    const u64* up_src;
+    const ulonglong2* up_hm;
+    u32 up_L, up_E;
 };
 
 __device__ __forceinline__ void bf_fwd(u64& x, u64& y, u64 w, u64 wp, u64 q) {
@@ -80,7 +87,7 @@ __device__ __forceinline__ u32 smem_index(u32 c, u32 l, u32 logC) {
     return w ^ ((w >> 3) & 15);
 }
 
-template <bool FWD, int S, bool COLS, bool SINGLE>
+template <bool FWD, int S, bool COLS, bool SINGLE, bool MODUP = false>
 struct Phase {
     static constexpr u32 GS = 1u << S;
     // sub-transforms per CTA: one whole polynomial in the single-phase case,
@@ -96,6 +103,11 @@ struct Phase {
     const u64* gin;        // tile input (global), read by a direct first pass
     u64* gout;             // tile output (global), written by a direct last pass
     bool canon;            // the last pass writes canonical residues
+    // MODUP: the first pass converts from these sources (at most 2 limbs)
+    const u64* ysrc0;
+    const u64* ysrc1;
+    u64 hm0, hm0s, hm1, hm1s;
+    bool two;
 
     // global index of element l of sub-transform c
     __device__ __forceinline__ u32 gidx(u32 c, u32 l) const {
@@ -154,8 +166,18 @@ struct Phase {
             } else {
 #pragma unroll
                 for (u32 k = 0; k < NE; ++k) {
-                    if constexpr (IN_G) x[k] = gin[gidx(c, lbase | (k << LB))];
-                    else x[k] = sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)];
+                    if constexpr (IN_G && MODUP) {
+                        // each Shoup product in [0, 2q): the sum within the
+                        // forward transform's input range [0, 4q)
+                        const u32 pos = gidx(c, lbase | (k << LB));
+                        u64 v = mul_shoup_lazy(ysrc0[pos], hm0, hm0s, q);
+                        if (two) v += mul_shoup_lazy(ysrc1[pos], hm1, hm1s, q);
+                        x[k] = v;
+                    } else if constexpr (IN_G) {
+                        x[k] = gin[gidx(c, lbase | (k << LB))];
+                    } else {
+                        x[k] = sm[smem_index<S, COLS>(c, lbase | (k << LB), LOGC)];
+                    }
                 }
             }
 #pragma unroll
@@ -232,7 +254,7 @@ struct Phase {
     }
 };
 
-template <bool FWD, int S, bool COLS, bool SINGLE>
+template <bool FWD, int S, bool COLS, bool SINGLE, bool MODUP = false>
 __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
     __shared__ __align__(16) u64 sm[kTile];
     const u32 p = blockIdx.x;
@@ -252,7 +274,25 @@ __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
               (u64)limb * N;
     }
 
-    Phase<FWD, S, COLS, SINGLE> ph;
+    Phase<FWD, S, COLS, SINGLE, MODUP> ph;
+    if constexpr (MODUP) {
+        // group grp is digit b of ciphertext ct; its sources are limbs
+        // b alpha .. of the ciphertext's y, the constants those of prime mi
+        const u32 ct = grp / a.skip_nd, b = grp - ct * a.skip_nd;
+        const u32 i0 = b * a.skip_alpha;
+        const u64 N2 = 1ull << a.logN;
+        ph.ysrc0 = a.up_src + ((u64)ct * a.up_L + i0) * N2;
+        ph.ysrc1 = ph.ysrc0 + N2;
+        const ulonglong2 h0 = a.up_hm[(u64)i0 * a.up_E + mi];
+        ph.hm0 = h0.x;
+        ph.hm0s = h0.y;
+        ph.two = a.skip_alpha > 1;
+        if (ph.two) {
+            const ulonglong2 h1 = a.up_hm[(u64)(i0 + 1) * a.up_E + mi];
+            ph.hm1 = h1.x;
+            ph.hm1s = h1.y;
+        }
+    }
     ph.sm = sm;
     ph.q = a.mods[mi].q;
     ph.tw = a.tw + (u64)mi * N;
@@ -267,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
     ph.gout = base;
     ph.canon = a.last != 0;
 
-    using Ph = Phase<FWD, S, COLS, SINGLE>;
+    using Ph = Phase<FWD, S, COLS, SINGLE, MODUP>;
     constexpr u32 GS = 1u << S;
     constexpr u32 LOGC = Ph::LOGC;
     constexpr u32 T = Ph::C * GS;
@@ -305,10 +345,10 @@ __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
     }
 }
 
-template <bool FWD, bool COLS, bool SINGLE>
+template <bool FWD, bool COLS, bool SINGLE, bool MODUP = false>
 int launch_phase(int S, dim3 grid, u32 threads, const NttArgs& a, cudaStream_t st) {
     switch (S) {
-#define PDQ_CASE(s) case s: ntt_phase_kernel<FWD, s, COLS, SINGLE><<<grid, threads, 0, st>>>(a); break;
+#define PDQ_CASE(s) case s: ntt_phase_kernel<FWD, s, COLS, SINGLE, MODUP><<<grid, threads, 0, st>>>(a); break;
         PDQ_CASE(1) PDQ_CASE(2) PDQ_CASE(3) PDQ_CASE(4) PDQ_CASE(5) PDQ_CASE(6)
         PDQ_CASE(7) PDQ_CASE(8) PDQ_CASE(9) PDQ_CASE(10) PDQ_CASE(11)
         // (column phases use S = log N - 9 <= 7 for the supported rings)
@@ -334,7 +374,8 @@ int launch_rows(u32 R, dim3 grid, const NttArgs& a, cudaStream_t st) {
 
 template <bool FWD>
 int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
-            cudaStream_t st, const NttArgs* from = nullptr, u32 skip_nd = 0, u32 skip_alpha = 0) {
+            cudaStream_t st, const NttArgs* from = nullptr, u32 skip_nd = 0, u32 skip_alpha = 0,
+            const u64* ninv_tab = nullptr, const u64* up_src = nullptr) {
     if (count == 0 || nlimbs == 0) return PDQ_OK;
     if (limb0 + nlimbs + skip_alpha > c.nmod) return fail(PDQ_E_PARAM, "ntt: limb range out of bounds");
     const u64 polys = (u64)count * nlimbs;
@@ -346,10 +387,19 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
     a.limb0 = limb0;
     a.mods = c.d_mods;
     a.tw = reinterpret_cast<const ulonglong2*>(FWD ? c.d_fw2 : c.d_iw2);
-    a.ninv4 = c.d_ninv;
+    a.ninv4 = ninv_tab ? ninv_tab : c.d_ninv;
     a.logN = c.log_n;
     a.skip_nd = skip_nd;
     a.skip_alpha = skip_alpha;
+    if (up_src) {
+        // the conversion rides on the forward column phase of raised digits
+        if (!FWD || c.log_n <= kTileBits || skip_alpha == 0 || skip_alpha > 2 || skip_nd == 0)
+            return fail(PDQ_E_PARAM, "ntt: the fused conversion needs a two-phase forward transform of raised digits");
+        a.up_src = up_src;
+        a.up_hm = reinterpret_cast<const ulonglong2*>(c.d_up_mont2);
+        a.up_L = c.L;
+        a.up_E = c.L + c.K;
+    }
     if (from) {
         a.src = from->src;
         a.src_outer = from->src_outer;
@@ -379,7 +429,8 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
     if (FWD) {
         cols.last = 0;
         rows.last = 1;
-        PDQ_TRY((launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cols, st)));
+        if (up_src) PDQ_TRY((launch_phase<true, true, false, true>((int)S1, gcols, kThreads, cols, st)));
+        else PDQ_TRY((launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cols, st)));
         return launch_rows<FWD>(R, grows, rows, st);
     }
     rows.last = 0;
@@ -407,9 +458,16 @@ int ntt_forward_digits(const Ctx& c, u64* D, u32 count, u32 nd, u32 alpha, u32 n
                          alpha);
 }
 
+int ntt_forward_digits_modup(const Ctx& c, u64* D, const u64* Y, u32 count, u32 nd, u32 alpha,
+                             u32 nlimbs, cudaStream_t st) {
+    if (nd == 0 || alpha == 0 || !Y) return fail(PDQ_E_PARAM, "ntt: bad digit layout");
+    return ntt_run<true>(c, D, count * nd, nlimbs - alpha, 0, (u64)nlimbs * c.N, st, nullptr, nd,
+                         alpha, nullptr, Y);
+}
+
 int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_per,
                      long long src_inner, u64 src_off, u64* data, u32 count, u32 nlimbs,
-                     u64 stride, cudaStream_t st, u32 limb0) {
+                     u64 stride, cudaStream_t st, u32 limb0, const u64* ninv_tab) {
     if (src_per == 0) return fail(PDQ_E_PARAM, "ntt: bad source set");
     NttArgs from{};
     from.src = src;
@@ -417,7 +475,7 @@ int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_
     from.src_inner = src_inner;
     from.src_per = src_per;
     from.src_off = src_off;
-    return ntt_run<false>(c, data, count, nlimbs, limb0, stride, st, &from);
+    return ntt_run<false>(c, data, count, nlimbs, limb0, stride, st, &from, 0, 0, ninv_tab);
 }
 
 }  // namespace pdq

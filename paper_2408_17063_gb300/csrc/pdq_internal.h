@@ -136,6 +136,11 @@ struct Ctx {
     // R so that the key inner products end with one Montgomery reduction)
     u64* d_up_hatmod_mont = nullptr;
     u64* d_up_hatmod_mont_shoup = nullptr;
+    // the raise with the conversion folded into the transforms: the inverse
+    // transform's last-level constants times hat_inv_i ([nmod][4], as d_ninv),
+    // and (hatmod R, Shoup) pairs [L][L+K][2]
+    u64* d_ninv_up = nullptr;
+    u64* d_up_mont2 = nullptr;
     // ModDown: (P/p_k)^-1 mod p_k (+shoup); (P/p_k) mod q_i; P^-1 mod q_i (+shoup)
     u64* d_dn_hatinv = nullptr;   // [K]
     u64* d_dn_hatinv_shoup = nullptr;
@@ -219,8 +224,17 @@ int ntt_forward_digits(const Ctx& c, u64* D, u32 count, u32 nd, u32 alpha, u32 n
 // read from a strided set (group g at src + (g / src_per) src_outer +
 // (g % src_per) src_inner + src_off, limb l at + l N), written to
 // data + g stride.
+// (ninv_tab: the last level's constants [nmod][4] instead of N^-1's, e.g.
+// c.d_ninv_up, which leaves limb i scaled by hat_inv_i)
 int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_per,
                      long long src_inner, u64 src_off, u64* data, u32 count, u32 nlimbs,
-                     u64 stride, cudaStream_t st, u32 limb0 = 0);
+                     u64 stride, cudaStream_t st, u32 limb0 = 0, const u64* ninv_tab = nullptr);
+// The raised digits' forward transform with the basis conversion folded into
+// its first phase: D[ct][b][r] (r outside digit b's alpha <= 2 limbs) =
+// NTT(sum_{k < alpha} y[ct][b alpha + k] (Q_b/q_{b alpha+k}) R mod q_r), where
+// Y [count][L][N] holds y_i = c1_i hat_inv_i (coefficient form); the digits'
+// own limbs are left as they are.
+int ntt_forward_digits_modup(const Ctx& c, u64* D, const u64* Y, u32 count, u32 nd, u32 alpha,
+                             u32 nlimbs, cudaStream_t st);
 
 }  // namespace pdq
