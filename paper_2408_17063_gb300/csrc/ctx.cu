@@ -177,7 +177,7 @@ static void free_ctx(Ctx* c) {
                     c->d_dn_pinv, c->d_dn_pinv_shoup, c->d_P_mod_q, c->d_P_mod_q_shoup, c->d_delta_mod_q,
                     c->d_dec_omega, c->d_dec_omega_shoup, c->d_ckar,
                     c->d_up_hatmod_mont, c->d_up_hatmod_mont_shoup, c->d_P_mont, c->d_ms,
-                    c->d_ninv_up, c->d_up_mont2};
+                    c->d_ninv_up, c->d_up_mont2, c->d_ninv_dn, c->d_dn_pair};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
@@ -412,6 +412,26 @@ static int build_ctx(const pdq_params& p, Ctx* c, const std::vector<u64>* given 
         for (u32 i = 0; i < L; ++i)
             dn_mod_s[(size_t)k * L + i] = shoup_of(dn_mod[(size_t)k * L + i], c->mods[i]);
     PDQ_TRY(upload(&c->d_dn_hatmod_shoup, dn_mod_s));
+    // ModDown with the conversion folded into the transforms: special limb
+    // k's inverse transform ends scaled by (P/p_k)^-1, the forward transform
+    // of the converted limbs reads ((P/p_k) mod q_i, Shoup) pairs [K][L]
+    {
+        std::vector<u64> ninv_dn(ninv), dn_pair(2 * dn_mod.size());
+        for (u32 k = 0; k < K; ++k) {
+            const u32 mi = L + k;
+            const u64 pk = c->mods[mi];
+            ninv_dn[4 * mi + 0] = mulmod_h(ninv[4 * mi + 0], dn_inv[k], pk);
+            ninv_dn[4 * mi + 1] = shoup_of(ninv_dn[4 * mi + 0], pk);
+            ninv_dn[4 * mi + 2] = mulmod_h(ninv[4 * mi + 2], dn_inv[k], pk);
+            ninv_dn[4 * mi + 3] = shoup_of(ninv_dn[4 * mi + 2], pk);
+        }
+        for (size_t i = 0; i < dn_mod.size(); ++i) {
+            dn_pair[2 * i] = dn_mod[i];
+            dn_pair[2 * i + 1] = dn_mod_s[i];
+        }
+        PDQ_TRY(upload(&c->d_ninv_dn, ninv_dn));
+        PDQ_TRY(upload(&c->d_dn_pair, dn_pair));
+    }
     PDQ_TRY(upload(&c->d_dn_pinv, pinv));
     PDQ_TRY(upload(&c->d_dn_pinv_shoup, pinv_s));
     PDQ_TRY(upload(&c->d_P_mod_q, c->P_mod_q));

@@ -52,13 +52,15 @@ struct NttArgs {
     // raised digits (skip_alpha > 0): group g is digit g % skip_nd of a
     // ciphertext, and its limbs skip the digit's own skip_alpha limbs
     u32 skip_nd, skip_alpha;
-    // the raise's basis conversion in the first (column) phase of the forward
-    // transform of raised digits: element = sum_{k < skip_alpha} y_k * hm_k
-    // (Shoup), y_k = up_src[ct][b skip_alpha + k] ([.][up_L][N]), hm_k =
-    // up_hm[(b skip_alpha + k) * up_E + prime]
+    // a basis conversion in the first (column) phase of a forward transform
+    // (the raise's and ModDown's): transform group g takes source group
+    // s = g / up_div and first source limb i0 = (g % up_div) up_i0_step;
+    // element = sum_{k < up_n} y_k hm_k (Shoup), y_k at up_src + s
+    // up_src_stride + (i0 + k) N, hm_k = up_hm[(i0 + k) up_E + prime]
     const u64* up_src;
     const ulonglong2* up_hm;
-    u32 up_L, up_E;
+    u64 up_src_stride;
+    u32 up_div, up_i0_step, up_n, up_E;
 };
 
 __device__ __forceinline__ void bf_fwd(u64& x, u64& y, u64 w, u64 wp, u64 q) {
@@ -276,17 +278,17 @@ __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
 
     Phase<FWD, S, COLS, SINGLE, MODUP> ph;
     if constexpr (MODUP) {
-        // group grp is digit b of ciphertext ct; its sources are limbs
-        // b alpha .. of the ciphertext's y, the constants those of prime mi
-        const u32 ct = grp / a.skip_nd, b = grp - ct * a.skip_nd;
-        const u32 i0 = b * a.skip_alpha;
+        // group grp takes source group sg from its first source limb i0 (a
+        // raised digit: its ciphertext and the digit's limbs); the constants
+        // are those of prime mi
+        const u32 sg = grp / a.up_div, i0 = (grp - sg * a.up_div) * a.up_i0_step;
         const u64 N2 = 1ull << a.logN;
-        ph.ysrc0 = a.up_src + ((u64)ct * a.up_L + i0) * N2;
+        ph.ysrc0 = a.up_src + (u64)sg * a.up_src_stride + (u64)i0 * N2;
         ph.ysrc1 = ph.ysrc0 + N2;
         const ulonglong2 h0 = a.up_hm[(u64)i0 * a.up_E + mi];
         ph.hm0 = h0.x;
         ph.hm0s = h0.y;
-        ph.two = a.skip_alpha > 1;
+        ph.two = a.up_n > 1;
         if (ph.two) {
             const ulonglong2 h1 = a.up_hm[(u64)(i0 + 1) * a.up_E + mi];
             ph.hm1 = h1.x;
@@ -375,7 +377,7 @@ int launch_rows(u32 R, dim3 grid, const NttArgs& a, cudaStream_t st) {
 template <bool FWD>
 int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
             cudaStream_t st, const NttArgs* from = nullptr, u32 skip_nd = 0, u32 skip_alpha = 0,
-            const u64* ninv_tab = nullptr, const u64* up_src = nullptr) {
+            const u64* ninv_tab = nullptr, const NttArgs* conv = nullptr) {
     if (count == 0 || nlimbs == 0) return PDQ_OK;
     if (limb0 + nlimbs + skip_alpha > c.nmod) return fail(PDQ_E_PARAM, "ntt: limb range out of bounds");
     const u64 polys = (u64)count * nlimbs;
@@ -391,14 +393,18 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
     a.logN = c.log_n;
     a.skip_nd = skip_nd;
     a.skip_alpha = skip_alpha;
-    if (up_src) {
-        // the conversion rides on the forward column phase of raised digits
-        if (!FWD || c.log_n <= kTileBits || skip_alpha == 0 || skip_alpha > 2 || skip_nd == 0)
-            return fail(PDQ_E_PARAM, "ntt: the fused conversion needs a two-phase forward transform of raised digits");
-        a.up_src = up_src;
-        a.up_hm = reinterpret_cast<const ulonglong2*>(c.d_up_mont2);
-        a.up_L = c.L;
-        a.up_E = c.L + c.K;
+    const u64* up_src = conv ? conv->up_src : nullptr;
+    if (conv) {
+        // the conversion rides on the forward column phase
+        if (!FWD || c.log_n <= kTileBits || conv->up_n == 0 || conv->up_n > 2 || conv->up_div == 0)
+            return fail(PDQ_E_PARAM, "ntt: the fused conversion needs a two-phase forward transform of at most 2 sources");
+        a.up_src = conv->up_src;
+        a.up_hm = conv->up_hm;
+        a.up_src_stride = conv->up_src_stride;
+        a.up_div = conv->up_div;
+        a.up_i0_step = conv->up_i0_step;
+        a.up_n = conv->up_n;
+        a.up_E = conv->up_E;
     }
     if (from) {
         a.src = from->src;
@@ -447,8 +453,8 @@ int ntt_forward(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 s
 }
 
 int ntt_inverse(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
-                cudaStream_t st) {
-    return ntt_run<false>(c, data, count, nlimbs, limb0, stride, st);
+                cudaStream_t st, const u64* ninv_tab) {
+    return ntt_run<false>(c, data, count, nlimbs, limb0, stride, st, nullptr, 0, 0, ninv_tab);
 }
 
 int ntt_forward_digits(const Ctx& c, u64* D, u32 count, u32 nd, u32 alpha, u32 nlimbs,
@@ -461,8 +467,30 @@ int ntt_forward_digits(const Ctx& c, u64* D, u32 count, u32 nd, u32 alpha, u32 n
 int ntt_forward_digits_modup(const Ctx& c, u64* D, const u64* Y, u32 count, u32 nd, u32 alpha,
                              u32 nlimbs, cudaStream_t st) {
     if (nd == 0 || alpha == 0 || !Y) return fail(PDQ_E_PARAM, "ntt: bad digit layout");
+    NttArgs cv{};
+    cv.up_src = Y;
+    cv.up_hm = reinterpret_cast<const ulonglong2*>(c.d_up_mont2);
+    cv.up_src_stride = (u64)c.L * c.N;     // y of one ciphertext, [L][N]
+    cv.up_div = nd;                        // digits per ciphertext
+    cv.up_i0_step = alpha;                 // digit b's limbs start at b alpha
+    cv.up_n = alpha;
+    cv.up_E = c.L + c.K;
     return ntt_run<true>(c, D, count * nd, nlimbs - alpha, 0, (u64)nlimbs * c.N, st, nullptr, nd,
-                         alpha, nullptr, Y);
+                         alpha, nullptr, &cv);
+}
+
+int ntt_forward_moddown(const Ctx& c, u64* Cv, const u64* S, u64 s_stride, u32 count,
+                        cudaStream_t st) {
+    if (!S || c.K == 0 || c.K > 2) return fail(PDQ_E_PARAM, "ntt: the fused ModDown takes 1 or 2 special primes");
+    NttArgs cv{};
+    cv.up_src = S;
+    cv.up_hm = reinterpret_cast<const ulonglong2*>(c.d_dn_pair);
+    cv.up_src_stride = s_stride;
+    cv.up_div = 1;
+    cv.up_i0_step = 0;
+    cv.up_n = c.K;
+    cv.up_E = c.L;                         // pairs [K][L]
+    return ntt_run<true>(c, Cv, count, c.L, 0, (u64)c.L * c.N, st, nullptr, 0, 0, nullptr, &cv);
 }
 
 int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_per,

@@ -1584,6 +1584,27 @@ int mask(const Ctx& c, u32 J, const u64* v, const u64* db, u64* out, cudaStream_
 // Cv[cp][l] = sum_k [A[cp][L+k] (P/p_k)^-1]_{p_k} (P/p_k) mod q_l (coefficient form)
 // Conv of cps polynomials whose special limbs (coefficient form) start at
 // Asp + cp * sp_stride, limb k at + k N
+int moddown_conv(const Ctx& c, const u64* Asp, u64 sp_stride, u32 cps, u64* Cv, cudaStream_t st);
+
+// whether ModDown's conversion rides on the forward transform (large rings,
+// at most 2 special primes; at N = 2^13 the separate kernel measured faster)
+bool moddown_fused(const Ctx& c) { return c.log_n >= 14 && c.K >= 1 && c.K <= 2; }
+
+// Cv [cps][L][N] (NTT form) = the conversion of the special limbs of cps
+// polynomials (limb k of polynomial g at Sp + g sp_stride + k N) to the
+// ciphertext primes.  inverse: Sp holds the special limbs in NTT form and
+// is transformed in place first (else: coefficient form already, from an
+// inverse transform with c.d_ninv_dn when moddown_fused(c)).
+int moddown_to_ntt(const Ctx& c, u64* Sp, u64 sp_stride, u32 cps, u64* Cv, bool inverse,
+                   cudaStream_t st) {
+    const bool fuse = moddown_fused(c);
+    if (inverse)
+        PDQ_TRY(ntt_inverse(c, Sp, cps, c.K, c.L, sp_stride, st, fuse ? c.d_ninv_dn : nullptr));
+    if (fuse) return ntt_forward_moddown(c, Cv, Sp, sp_stride, cps, st);
+    PDQ_TRY(moddown_conv(c, Sp, sp_stride, cps, Cv, st));
+    return ntt_forward(c, Cv, cps, c.L, 0, (u64)c.L * c.N, st);
+}
+
 int moddown_conv(const Ctx& c, const u64* Asp, u64 sp_stride, u32 cps, u64* Cv, cudaStream_t st) {
     if (c.K > 8 || c.L + c.K > 40 || c.L > 32) return fail(PDQ_E_PARAM, "ModDown: too many primes");
     PDQ_TRY(check_y(cps, "ModDown"));
@@ -1681,9 +1702,7 @@ int ks_apply(const Ctx& c, const u64* D, CtSet in, u32 cnt, u32 galois, const u6
     k_ks_inner<<<grid2(E * N / 2, cnt), kBlock, 0, st>>>(D, t, koff, c.log_n, (u32)E, c.ndigits,
                                                          galois, c.d_mods, A);
     PDQ_TRY(launched("k_ks_inner"));
-    PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
-    PDQ_TRY(moddown_conv(c, A + L * N, E * N, 2 * cnt, Cv, st));
-    PDQ_TRY(ntt_forward(c, Cv, 2 * cnt, c.L, 0, L * N, st));
+    PDQ_TRY(moddown_to_ntt(c, A + L * N, E * N, 2 * cnt, Cv, true, st));
     k_moddown_final<<<grid2(L * N, cnt), kBlock, 0, st>>>(A, Cv, in, out, add, c.log_n, c.L,
                                                               c.K, galois, c.d_mods, c.d_dn_pinv,
                                                               c.d_dn_pinv_shoup);
@@ -1904,10 +1923,10 @@ int mod_down_polys(const Ctx& c, const u64* A, u64 a_stride, u32 npolys, u64* ou
     PDQ_TRY(check_y(npolys, "mod_down"));
     u64* S = ws;                      // special limbs, coefficient form [npolys][K][N]
     u64* Cv = ws + (u64)npolys * K * N;
+    const bool fuse = moddown_fused(c);
     PDQ_TRY(ntt_inverse_from(c, A, (long long)a_stride, 1, 0, L * N, S, npolys, c.K, K * N, st,
-                             c.L));
-    PDQ_TRY(moddown_conv(c, S, K * N, npolys, Cv, st));
-    PDQ_TRY(ntt_forward(c, Cv, npolys, c.L, 0, L * N, st));
+                             c.L, fuse ? c.d_ninv_dn : nullptr));
+    PDQ_TRY(moddown_to_ntt(c, S, K * N, npolys, Cv, false, st));
     k_moddown_final_poly<<<grid2(L * N / 2, npolys), kBlock, 0, st>>>(
         A, a_stride, Cv, out, out_stride, c.log_n, c.L, c.d_mods, c.d_dn_pinv, c.d_dn_pinv_shoup);
     return launched("k_moddown_final_poly");
@@ -1917,9 +1936,7 @@ int mod_down_batch(const Ctx& c, u64* A, u32 cnt, CtSet out, u64* ws, cudaStream
     const u64 N = c.N, L = c.L, E = c.L + c.K;
     PDQ_TRY(check_y(2ull * cnt, "mod_down"));
     u64* Cv = ws;
-    PDQ_TRY(ntt_inverse(c, A + L * N, 2 * cnt, c.K, c.L, E * N, st));
-    PDQ_TRY(moddown_conv(c, A + L * N, E * N, 2 * cnt, Cv, st));
-    PDQ_TRY(ntt_forward(c, Cv, 2 * cnt, c.L, 0, L * N, st));
+    PDQ_TRY(moddown_to_ntt(c, A + L * N, E * N, 2 * cnt, Cv, true, st));
     k_moddown_final<<<grid2(L * N, cnt), kBlock, 0, st>>>(A, Cv, CtSet{}, out, CtSet{}, c.log_n,
                                                               c.L, c.K, 0, c.d_mods, c.d_dn_pinv,
                                                               c.d_dn_pinv_shoup);

@@ -141,6 +141,10 @@ struct Ctx {
     // and (hatmod R, Shoup) pairs [L][L+K][2]
     u64* d_ninv_up = nullptr;
     u64* d_up_mont2 = nullptr;
+    // ModDown likewise: last-level constants times (P/p_k)^-1 on the special
+    // primes ([nmod][4]) and ((P/p_k) mod q_i, Shoup) pairs [K][L][2]
+    u64* d_ninv_dn = nullptr;
+    u64* d_dn_pair = nullptr;
     // ModDown: (P/p_k)^-1 mod p_k (+shoup); (P/p_k) mod q_i; P^-1 mod q_i (+shoup)
     u64* d_dn_hatinv = nullptr;   // [K]
     u64* d_dn_hatinv_shoup = nullptr;
@@ -214,7 +218,7 @@ u32 bitrev(u32 x, u32 bits);
 int ntt_forward(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
                 cudaStream_t st);
 int ntt_inverse(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
-                cudaStream_t st);
+                cudaStream_t st, const u64* ninv_tab = nullptr);
 // Forward transform of raised digits D[count][nd][nlimbs][N] except each
 // digit's own limbs (digit b owns limbs b alpha .. b alpha + alpha - 1; every
 // digit the same size)
@@ -236,5 +240,11 @@ int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_
 // own limbs are left as they are.
 int ntt_forward_digits_modup(const Ctx& c, u64* D, const u64* Y, u32 count, u32 nd, u32 alpha,
                              u32 nlimbs, cudaStream_t st);
+// ModDown's conversion folded into a forward transform: Cv[g][i] (i < L) =
+// NTT(sum_{k < K} y_k(g) (P/p_k) mod q_i) for the K <= 2 special limbs y_k(g)
+// at S + g s_stride + k N, coefficient form scaled by (P/p_k)^-1 (an inverse
+// transform with c.d_ninv_dn); Cv [count][L][N].
+int ntt_forward_moddown(const Ctx& c, u64* Cv, const u64* S, u64 s_stride, u32 count,
+                        cudaStream_t st);
 
 }  // namespace pdq
