@@ -141,15 +141,18 @@ int pdq_ctx_set_rotation_budget(pdq_ctx* ctx, uint64_t bytes);
  * of N > 2^11, 7..11 and below log N (the column phase takes the other
  * levels); mac_tiles: position tiles per multiply-accumulate CTA, 1, 2, 4 or
  * 8; mac_bc: baby steps staged per copy step, 1, 2, 4, 8 or 16 (fewer where
- * shared memory requires).  0 keeps the library's rule for a knob (9 row
- * levels; 8 tiles while 64 CTAs per prime remain; 16 baby steps).  Errors:
- * PDQ_E_PARAM for other values.  Set it before the calls it should affect,
- * not while a call on the context runs. */
+ * shared memory requires); ntt_chunk: polynomials per launch pair of a
+ * two-phase transform (a call over more runs in chunks, so that a chunk's
+ * intermediate between the phases can stay in L2; rounded to whole
+ * ciphertexts), 0 or 64..2^20.  0 keeps the library's rule for a knob (9 row
+ * levels; 8 tiles while 64 CTAs per prime remain; 16 baby steps; no chunks).
+ * Errors: PDQ_E_PARAM for other values.  Set it before the calls it should
+ * affect, not while a call on the context runs. */
 typedef struct {
     uint32_t ntt_row_bits;
     uint32_t mac_tiles;
     uint32_t mac_bc;
-    uint32_t reserved;
+    uint32_t ntt_chunk;
 } pdq_schedule;
 int pdq_ctx_set_schedule(pdq_ctx* ctx, const pdq_schedule* sched);
 int pdq_ctx_get_schedule(const pdq_ctx* ctx, pdq_schedule* sched);

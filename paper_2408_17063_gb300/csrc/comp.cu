@@ -675,8 +675,9 @@ int pdq_ctx_set_schedule(pdq_ctx* ctx, const pdq_schedule* sched) {
         return fail(PDQ_E_PARAM, "schedule: row levels must be 7..11 and below log N");
     if (mt && (mt > 8 || (mt & (mt - 1)))) return fail(PDQ_E_PARAM, "schedule: 1, 2, 4 or 8 tiles");
     if (bc && (bc > 16 || (bc & (bc - 1)))) return fail(PDQ_E_PARAM, "schedule: 1..16 baby steps, a power of two");
+    if (sched->ntt_chunk && (sched->ntt_chunk < 64 || sched->ntt_chunk > (1u << 20)))
+        return fail(PDQ_E_PARAM, "schedule: 64..2^20 polynomials per transform launch");
     c.sched = *sched;
-    c.sched.reserved = 0;
     return PDQ_OK;
 }
 

@@ -430,19 +430,45 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
     (FWD ? rows : cols).src = nullptr;        // the second phase works in place
     cols.logC = kTileBits - S1;                // 2^S1 * C = tile
     rows.logC = kTileBits - R;                 // 2^(11-R) rows of 2^R
-    const dim3 gcols((u32)polys, (1u << R) >> cols.logC);
-    const dim3 grows((u32)polys, (1u << S1) >> rows.logC);
-    if (FWD) {
-        cols.last = 0;
-        rows.last = 1;
-        if (up_src) PDQ_TRY((launch_phase<true, true, false, true>((int)S1, gcols, kThreads, cols, st)));
-        else PDQ_TRY((launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cols, st)));
-        return launch_rows<FWD>(R, grows, rows, st);
+    // (first phase: FWD columns, else rows; its `src` is the strided set)
+    cols.last = FWD ? 0 : 1;
+    rows.last = FWD ? 1 : 0;
+    // Groups go in chunks of the schedule's polynomials per launch pair (0:
+    // all at once), so that a chunk's intermediate between the two phases
+    // can stay in L2.  A chunk starts on a whole ciphertext (digits,
+    // conversion sources, strided input set).
+    u32 unit = 1;
+    if (skip_alpha) unit = skip_nd;
+    if (conv) unit = std::max(unit, conv->up_div);
+    if (from) unit = std::max(unit, from->src_per);
+    u64 chunk = count;
+    if (c.sched.ntt_chunk) {
+        chunk = std::max<u64>(1, c.sched.ntt_chunk / nlimbs) / unit * unit;
+        if (chunk == 0) chunk = unit;
     }
-    rows.last = 0;
-    cols.last = 1;
-    PDQ_TRY(launch_rows<FWD>(R, grows, rows, st));
-    return launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cols, st);
+    for (u64 g0 = 0; g0 < count; g0 += chunk) {
+        const u64 gn = std::min<u64>(chunk, count - g0);
+        NttArgs cc = cols, rr = rows;
+        cc.data = rr.data = data + g0 * stride;
+        if (from) {
+            // (the first phase of an inverse transform reads the set)
+            const u64 hi = g0 / from->src_per;
+            (FWD ? cc : rr).src = from->src + (long long)hi * from->src_outer;
+        }
+        if (conv) cc.up_src = conv->up_src + (g0 / conv->up_div) * conv->up_src_stride;
+        const u32 pc = (u32)(gn * nlimbs);
+        const dim3 gcols(pc, (1u << R) >> cols.logC);
+        const dim3 grows(pc, (1u << S1) >> rows.logC);
+        if (FWD) {
+            if (up_src) PDQ_TRY((launch_phase<true, true, false, true>((int)S1, gcols, kThreads, cc, st)));
+            else PDQ_TRY((launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cc, st)));
+            PDQ_TRY(launch_rows<FWD>(R, grows, rr, st));
+        } else {
+            PDQ_TRY(launch_rows<FWD>(R, grows, rr, st));
+            PDQ_TRY((launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cc, st)));
+        }
+    }
+    return PDQ_OK;
 }
 
 }  // namespace

@@ -47,11 +47,11 @@ class Info(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("ntt_row_bits", ctypes.c_uint32), ("mac_tiles", ctypes.c_uint32),
-                ("mac_bc", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("mac_bc", ctypes.c_uint32), ("ntt_chunk", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {"ntt_row_bits": self.ntt_row_bits, "mac_tiles": self.mac_tiles,
-                "mac_bc": self.mac_bc}
+                "mac_bc": self.mac_bc, "ntt_chunk": self.ntt_chunk}
 
 
 class Plan(ctypes.Structure):
@@ -245,10 +245,11 @@ class Context:
         rotations (0: all), made and consumed a chunk of primes at a time."""
         _check(load().pdq_ctx_set_rotation_budget(self.h, int(nbytes)))
 
-    def set_schedule(self, ntt_row_bits: int = 0, mac_tiles: int = 0, mac_bc: int = 0):
+    def set_schedule(self, ntt_row_bits: int = 0, mac_tiles: int = 0, mac_bc: int = 0,
+                     ntt_chunk: int = 0):
         """pdq_ctx_set_schedule: launch-schedule knobs (0: the library's rule);
         results are the same bits under every schedule."""
-        sc = Schedule(ntt_row_bits, mac_tiles, mac_bc, 0)
+        sc = Schedule(ntt_row_bits, mac_tiles, mac_bc, ntt_chunk)
         _check(load().pdq_ctx_set_schedule(self.h, ctypes.byref(sc)))
 
     def schedule(self) -> dict:

@@ -16,8 +16,9 @@ server tunes each shape once.  Tuning allocates the keys, plan constants and
 workspace of each candidate in turn (at N = 2^15, n = 2^20: about 17 GB).
 
 ScheduleTuner does the same for the launch schedule of a context
-(pdq_ctx_set_schedule: the phase split of the transforms, the position tiles
-per CTA and the baby steps per copy step of the multiply-accumulate), by
+(pdq_ctx_set_schedule: the phase split of the transforms and their
+polynomials per launch, the position tiles per CTA and the baby steps per
+copy step of the multiply-accumulate), by
 coordinate descent over the knobs on one query shape (a knob moves only for a
 gain above 1%); every schedule gives the same bits, so only the time decides.
 """
@@ -146,7 +147,8 @@ class AnswerRig:
 
 
 # knob -> candidate values (0: the library's rule)
-SCHEDULE_KNOBS = {"ntt_row_bits": [8, 9, 10], "mac_tiles": [2, 4, 8], "mac_bc": [8, 16]}
+SCHEDULE_KNOBS = {"ntt_row_bits": [8, 9, 10], "mac_tiles": [2, 4, 8], "mac_bc": [8, 16],
+                  "ntt_chunk": [256, 1024]}
 
 
 def schedule_candidates(ctx: pdq.Context, knob: str) -> list[int]:

@@ -46,15 +46,34 @@ def test_every_schedule_gives_the_same_bits(cfg_name):
         for mt in (1, 2, 8):
             for bc in (1, 4, 16):
                 ctx.set_schedule(ntt_row_bits=rb, mac_tiles=mt, mac_bc=bc)
-                assert ctx.schedule() == {"ntt_row_bits": rb, "mac_tiles": mt, "mac_bc": bc}
+                assert ctx.schedule() == {"ntt_row_bits": rb, "mac_tiles": mt, "mac_bc": bc,
+                                          "ntt_chunk": 0}
                 assert st.answer().equal(want), (rb, mt, bc)
+    for ch in (64, 100, 4096):                 # transforms in chunks (ragged last one)
+        ctx.set_schedule(ntt_chunk=ch)
+        assert st.answer().equal(want), ch
+    ctx.set_schedule()
+
+
+def test_schedules_at_the_large_ring_give_the_same_bits():
+    """At N = 2^15 (8 + 2 primes, 4 digits) the raise and ModDown conversions
+    ride on the transforms; chunked transforms and other splits keep the bits."""
+    st = Setup("c3", n=1 << 16, s=64)
+    ctx = st.ctx
+    ctx.set_schedule()
+    want = st.answer().clone()
+    for kw in ({"ntt_chunk": 64}, {"ntt_chunk": 300}, {"ntt_row_bits": 8, "ntt_chunk": 1024},
+               {"ntt_row_bits": 10}, {"mac_tiles": 1, "mac_bc": 2}):
+        ctx.set_schedule(**kw)
+        assert st.answer().equal(want), kw
     ctx.set_schedule()
 
 
 def test_schedule_refuses_bad_knobs():
     from paper_2408_17063_gb300 import pdq
     ctx = Setup("c1").ctx
-    for kw in ({"ntt_row_bits": 6}, {"ntt_row_bits": 12}, {"mac_tiles": 3}, {"mac_bc": 32}):
+    for kw in ({"ntt_row_bits": 6}, {"ntt_row_bits": 12}, {"mac_tiles": 3}, {"mac_bc": 32},
+               {"ntt_chunk": 8}):
         with pytest.raises(pdq.PdqError):
             ctx.set_schedule(**kw)
     ctx.set_schedule()
