@@ -153,8 +153,8 @@ SCHEDULE_KNOBS = {"ntt_row_bits": [8, 9, 10], "mac_tiles": [2, 4, 8], "mac_bc": 
 
 def schedule_candidates(ctx: pdq.Context, knob: str) -> list[int]:
     vals = SCHEDULE_KNOBS[knob]
-    if knob == "ntt_row_bits":       # two-phase transforms only, both phases <= 2^11
-        vals = [r for r in vals if r < ctx.log_n and ctx.log_n - r <= 11]
+    if knob == "ntt_row_bits":       # two-phase transforms (N > 2^11), both phases <= 2^11
+        vals = [r for r in vals if ctx.log_n > 11 and r < ctx.log_n and ctx.log_n - r <= 11]
     return [0] + vals
 
 
