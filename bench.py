@@ -688,9 +688,11 @@ def run_ring_switched(args, cfg, ctx, plan, q, v_cts, stream, rank: int) -> dict
     ssk1 = one.secret_prepare(torch.from_numpy(s_small))
     ok = ok and one.decomp(splan, one.decrypt(ssk1, out1).cpu().numpy()) == truth
     launches0 = pdq.pdq_launch_count()
+    torch.cuda.nvtx.range_push("ring_switched")
     for _ in range(args.steps):
         step(mark=True)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = pdq.pdq_launch_count() - launches0
     names = ["mod_switch", "mask", "ring_switch", "comp", "answer_mod_switch"]
     stages = {}
