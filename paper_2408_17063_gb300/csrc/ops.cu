@@ -1586,9 +1586,9 @@ int mask(const Ctx& c, u32 J, const u64* v, const u64* db, u64* out, cudaStream_
 // Asp + cp * sp_stride, limb k at + k N
 int moddown_conv(const Ctx& c, const u64* Asp, u64 sp_stride, u32 cps, u64* Cv, cudaStream_t st);
 
-// whether ModDown's conversion rides on the forward transform (large rings,
-// at most 2 special primes; at N = 2^13 the separate kernel measured faster)
-bool moddown_fused(const Ctx& c) { return c.log_n >= 14 && c.K >= 1 && c.K <= 2; }
+// whether ModDown's conversion rides on the forward transform (two-phase
+// transforms, N > 2^11; at most 2 special primes)
+bool moddown_fused(const Ctx& c) { return c.log_n > 11 && c.K >= 1 && c.K <= 2; }
 
 // Cv [cps][L][N] (NTT form) = the conversion of the special limbs of cps
 // polynomials (limb k of polynomial g at Sp + g sp_stride + k N) to the
@@ -1635,13 +1635,11 @@ int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t
     if (c1_off == ~0ull) c1_off = L * N;
     u64* X = ws;
     u64* D = ws + cnt * L * N;
-    if (c.log_n >= 14 && c.alpha <= 2 && c.L % c.alpha == 0) {
+    if (c.log_n > 11 && c.alpha <= 2 && c.L % c.alpha == 0) {
         // the conversion folded into the transforms: the inverse transform of
         // c1 ends scaled by hat_inv_i (y_i into X), the digits' own limbs are
         // c1 R, and the forward transform of the other limbs converts from y
-        // in its first phase (no converted copy of the digits is written).
-        // (At N = 2^13 the separate conversion measured faster: its copies
-        // are small and the extra launch is not.)
+        // in its first phase (no converted copy of the digits is written)
         PDQ_TRY(ntt_inverse_from(c, in.base, in.outer, in.per, in.inner, c1_off, X, cnt, c.L,
                                  L * N, st, 0, c.d_ninv_up));
         const dim3 g((c.N / 2 + kBlock - 1) / kBlock, c.L, cnt);
