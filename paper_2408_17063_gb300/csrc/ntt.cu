@@ -61,6 +61,15 @@ struct NttArgs {
     const ulonglong2* up_hm;
     u64 up_src_stride;
     u32 up_div, up_i0_step, up_n, up_E;
+    // ModDown's last step in the last (row) phase of a forward transform of
+    // converted limbs: instead of the transform, group g limb l writes
+    // (A - NTT(conv)) P^-1 mod q to epi_out + g epi_out_stride + l N, A read at
+    // epi_a + g epi_a_stride + l N
+    const u64* epi_a;
+    u64* epi_out;
+    u64 epi_a_stride, epi_out_stride;
+    const u64* epi_pinv;
+    const u64* epi_pinvs;
 };
 
 __device__ __forceinline__ void bf_fwd(u64& x, u64& y, u64 w, u64 wp, u64 q) {
@@ -89,7 +98,7 @@ __device__ __forceinline__ u32 smem_index(u32 c, u32 l, u32 logC) {
     return w ^ ((w >> 3) & 15);
 }
 
-template <bool FWD, int S, bool COLS, bool SINGLE, bool MODUP = false>
+template <bool FWD, int S, bool COLS, bool SINGLE, bool MODUP = false, bool EPI = false>
 struct Phase {
     static constexpr u32 GS = 1u << S;
     // sub-transforms per CTA: one whole polynomial in the single-phase case,
@@ -110,6 +119,10 @@ struct Phase {
     const u64* ysrc1;
     u64 hm0, hm0s, hm1, hm1s;
     bool two;
+    // EPI: the last pass writes (A - x) P^-1 to eout instead of x to gout
+    const u64* ea;
+    u64* eout;
+    u64 pv, pvs;
 
     // global index of element l of sub-transform c
     __device__ __forceinline__ u32 gidx(u32 c, u32 l) const {
@@ -216,7 +229,22 @@ struct Phase {
 #pragma unroll
                     for (u32 k = 0; k < NE; ++k) x[k] = FWD ? csub(csub(x[k], 2 * q), q) : csub(x[k], q);
                 }
-                if constexpr (!COLS && LB == 0) {
+                if constexpr (EPI && !COLS && LB == 0) {
+#pragma unroll
+                    for (u32 k = 0; k < NE; k += 2) {
+                        const u32 pos = gidx(c, lbase + k);
+                        const ulonglong2 av = *reinterpret_cast<const ulonglong2*>(ea + pos);
+                        *reinterpret_cast<ulonglong2*>(eout + pos) = make_ulonglong2(
+                            csub(mul_shoup_lazy(submod(av.x, x[k], q), pv, pvs, q), q),
+                            csub(mul_shoup_lazy(submod(av.y, x[k + 1], q), pv, pvs, q), q));
+                    }
+                } else if constexpr (EPI) {
+#pragma unroll
+                    for (u32 k = 0; k < NE; ++k) {
+                        const u32 pos = gidx(c, lbase | (k << LB));
+                        eout[pos] = csub(mul_shoup_lazy(submod(ea[pos], x[k], q), pv, pvs, q), q);
+                    }
+                } else if constexpr (!COLS && LB == 0) {
 #pragma unroll
                     for (u32 k = 0; k < NE; k += 2)
                         *reinterpret_cast<ulonglong2*>(gout + gidx(c, lbase + k)) = make_ulonglong2(x[k], x[k + 1]);
@@ -256,7 +284,7 @@ struct Phase {
     }
 };
 
-template <bool FWD, int S, bool COLS, bool SINGLE, bool MODUP = false>
+template <bool FWD, int S, bool COLS, bool SINGLE, bool MODUP = false, bool EPI = false>
 __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
     __shared__ __align__(16) u64 sm[kTile];
     const u32 p = blockIdx.x;
@@ -276,7 +304,13 @@ __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
               (u64)limb * N;
     }
 
-    Phase<FWD, S, COLS, SINGLE, MODUP> ph;
+    Phase<FWD, S, COLS, SINGLE, MODUP, EPI> ph;
+    if constexpr (EPI) {
+        ph.ea = a.epi_a + (u64)grp * a.epi_a_stride + (u64)limb * N;
+        ph.eout = a.epi_out + (u64)grp * a.epi_out_stride + (u64)limb * N;
+        ph.pv = a.epi_pinv[mi];
+        ph.pvs = a.epi_pinvs[mi];
+    }
     if constexpr (MODUP) {
         // group grp takes source group sg from its first source limb i0 (a
         // raised digit: its ciphertext and the digit's limbs); the constants
@@ -309,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
     ph.gout = base;
     ph.canon = a.last != 0;
 
-    using Ph = Phase<FWD, S, COLS, SINGLE, MODUP>;
+    using Ph = Phase<FWD, S, COLS, SINGLE, MODUP, EPI>;
     constexpr u32 GS = 1u << S;
     constexpr u32 LOGC = Ph::LOGC;
     constexpr u32 T = Ph::C * GS;
@@ -360,15 +394,16 @@ int launch_phase(int S, dim3 grid, u32 threads, const NttArgs& a, cudaStream_t s
     return launched("ntt_phase_kernel");
 }
 
-// the row phase of a two-phase transform, R = 7..11 levels
-template <bool FWD>
+// the row phase of a two-phase transform, R = 7..11 levels (EPI: ModDown's
+// last step in its output)
+template <bool FWD, bool EPI = false>
 int launch_rows(u32 R, dim3 grid, const NttArgs& a, cudaStream_t st) {
     switch (R) {
-        case 7: ntt_phase_kernel<FWD, 7, false, false><<<grid, kThreads, 0, st>>>(a); break;
-        case 8: ntt_phase_kernel<FWD, 8, false, false><<<grid, kThreads, 0, st>>>(a); break;
-        case 9: ntt_phase_kernel<FWD, 9, false, false><<<grid, kThreads, 0, st>>>(a); break;
-        case 10: ntt_phase_kernel<FWD, 10, false, false><<<grid, kThreads, 0, st>>>(a); break;
-        case 11: ntt_phase_kernel<FWD, 11, false, false><<<grid, kThreads, 0, st>>>(a); break;
+        case 7: ntt_phase_kernel<FWD, 7, false, false, false, EPI><<<grid, kThreads, 0, st>>>(a); break;
+        case 8: ntt_phase_kernel<FWD, 8, false, false, false, EPI><<<grid, kThreads, 0, st>>>(a); break;
+        case 9: ntt_phase_kernel<FWD, 9, false, false, false, EPI><<<grid, kThreads, 0, st>>>(a); break;
+        case 10: ntt_phase_kernel<FWD, 10, false, false, false, EPI><<<grid, kThreads, 0, st>>>(a); break;
+        case 11: ntt_phase_kernel<FWD, 11, false, false, false, EPI><<<grid, kThreads, 0, st>>>(a); break;
         default: return fail(PDQ_E_PARAM, "ntt: unsupported row phase");
     }
     return launched("ntt_phase_kernel");
@@ -377,7 +412,8 @@ int launch_rows(u32 R, dim3 grid, const NttArgs& a, cudaStream_t st) {
 template <bool FWD>
 int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
             cudaStream_t st, const NttArgs* from = nullptr, u32 skip_nd = 0, u32 skip_alpha = 0,
-            const u64* ninv_tab = nullptr, const NttArgs* conv = nullptr) {
+            const u64* ninv_tab = nullptr, const NttArgs* conv = nullptr,
+            const NttArgs* epi = nullptr) {
     if (count == 0 || nlimbs == 0) return PDQ_OK;
     if (limb0 + nlimbs + skip_alpha > c.nmod) return fail(PDQ_E_PARAM, "ntt: limb range out of bounds");
     const u64 polys = (u64)count * nlimbs;
@@ -405,6 +441,15 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
         a.up_i0_step = conv->up_i0_step;
         a.up_n = conv->up_n;
         a.up_E = conv->up_E;
+    }
+    if (epi) {
+        if (!FWD || c.log_n <= kTileBits) return fail(PDQ_E_PARAM, "ntt: the fused ModDown needs a two-phase forward transform");
+        a.epi_a = epi->epi_a;
+        a.epi_out = epi->epi_out;
+        a.epi_a_stride = epi->epi_a_stride;
+        a.epi_out_stride = epi->epi_out_stride;
+        a.epi_pinv = epi->epi_pinv;
+        a.epi_pinvs = epi->epi_pinvs;
     }
     if (from) {
         a.src = from->src;
@@ -456,13 +501,18 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
             (FWD ? cc : rr).src = from->src + (long long)hi * from->src_outer;
         }
         if (conv) cc.up_src = conv->up_src + (g0 / conv->up_div) * conv->up_src_stride;
+        if (epi) {
+            rr.epi_a = epi->epi_a + g0 * epi->epi_a_stride;
+            rr.epi_out = epi->epi_out + g0 * epi->epi_out_stride;
+        }
         const u32 pc = (u32)(gn * nlimbs);
         const dim3 gcols(pc, (1u << R) >> cols.logC);
         const dim3 grows(pc, (1u << S1) >> rows.logC);
         if (FWD) {
             if (up_src) PDQ_TRY((launch_phase<true, true, false, true>((int)S1, gcols, kThreads, cc, st)));
             else PDQ_TRY((launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cc, st)));
-            PDQ_TRY(launch_rows<FWD>(R, grows, rr, st));
+            if (epi) PDQ_TRY((launch_rows<true, true>(R, grows, rr, st)));
+            else PDQ_TRY(launch_rows<FWD>(R, grows, rr, st));
         } else {
             PDQ_TRY(launch_rows<FWD>(R, grows, rr, st));
             PDQ_TRY((launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cc, st)));
@@ -506,7 +556,7 @@ int ntt_forward_digits_modup(const Ctx& c, u64* D, const u64* Y, u32 count, u32 
 }
 
 int ntt_forward_moddown(const Ctx& c, u64* Cv, const u64* S, u64 s_stride, u32 count,
-                        cudaStream_t st) {
+                        cudaStream_t st, const u64* A, u64 a_stride, u64* out, u64 out_stride) {
     if (!S || c.K == 0 || c.K > 2) return fail(PDQ_E_PARAM, "ntt: the fused ModDown takes 1 or 2 special primes");
     NttArgs cv{};
     cv.up_src = S;
@@ -516,7 +566,15 @@ int ntt_forward_moddown(const Ctx& c, u64* Cv, const u64* S, u64 s_stride, u32 c
     cv.up_i0_step = 0;
     cv.up_n = c.K;
     cv.up_E = c.L;                         // pairs [K][L]
-    return ntt_run<true>(c, Cv, count, c.L, 0, (u64)c.L * c.N, st, nullptr, 0, 0, nullptr, &cv);
+    if (!A) return ntt_run<true>(c, Cv, count, c.L, 0, (u64)c.L * c.N, st, nullptr, 0, 0, nullptr, &cv);
+    NttArgs ep{};
+    ep.epi_a = A;
+    ep.epi_a_stride = a_stride;
+    ep.epi_out = out;
+    ep.epi_out_stride = out_stride;
+    ep.epi_pinv = c.d_dn_pinv;
+    ep.epi_pinvs = c.d_dn_pinv_shoup;
+    return ntt_run<true>(c, Cv, count, c.L, 0, (u64)c.L * c.N, st, nullptr, 0, 0, nullptr, &cv, &ep);
 }
 
 int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_per,

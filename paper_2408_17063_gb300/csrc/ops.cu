@@ -1924,6 +1924,9 @@ int mod_down_polys(const Ctx& c, const u64* A, u64 a_stride, u32 npolys, u64* ou
     const bool fuse = moddown_fused(c);
     PDQ_TRY(ntt_inverse_from(c, A, (long long)a_stride, 1, 0, L * N, S, npolys, c.K, K * N, st,
                              c.L, fuse ? c.d_ninv_dn : nullptr));
+    // fused: the conversion in the forward transform's first phase and the
+    // final (A - Cv) P^-1 in its last
+    if (fuse) return ntt_forward_moddown(c, Cv, S, K * N, npolys, st, A, a_stride, out, out_stride);
     PDQ_TRY(moddown_to_ntt(c, S, K * N, npolys, Cv, false, st));
     k_moddown_final_poly<<<grid2(L * N / 2, npolys), kBlock, 0, st>>>(
         A, a_stride, Cv, out, out_stride, c.log_n, c.L, c.d_mods, c.d_dn_pinv, c.d_dn_pinv_shoup);

@@ -244,7 +244,11 @@ int ntt_forward_digits_modup(const Ctx& c, u64* D, const u64* Y, u32 count, u32 
 // NTT(sum_{k < K} y_k(g) (P/p_k) mod q_i) for the K <= 2 special limbs y_k(g)
 // at S + g s_stride + k N, coefficient form scaled by (P/p_k)^-1 (an inverse
 // transform with c.d_ninv_dn); Cv [count][L][N].
+// With A: ModDown's last step in the transform's output, out[g][i] = (A[g][i]
+// - Cv[g][i]) P^-1 mod q_i (A at A + g a_stride, out at out + g out_stride,
+// limb i at + i N); Cv then only holds the intermediate of the two phases.
 int ntt_forward_moddown(const Ctx& c, u64* Cv, const u64* S, u64 s_stride, u32 count,
-                        cudaStream_t st);
+                        cudaStream_t st, const u64* A = nullptr, u64 a_stride = 0,
+                        u64* out = nullptr, u64 out_stride = 0);
 
 }  // namespace pdq
