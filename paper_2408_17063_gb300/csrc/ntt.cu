@@ -70,6 +70,11 @@ struct NttArgs {
     u64 epi_a_stride, epi_out_stride;
     const u64* epi_pinv;
     const u64* epi_pinvs;
+    // the raise's own limbs from the first (row) phase of the inverse
+    // transform of c1: as it reads limb r (NTT form) of ciphertext g it also
+    // writes c1_r R mod q_r to own_out + ((g own_nd + r / own_alpha) own_E + r) N
+    u64* own_out;
+    u32 own_nd, own_alpha, own_E;
 };
 
 __device__ __forceinline__ void bf_fwd(u64& x, u64& y, u64 w, u64 wp, u64 q) {
@@ -98,7 +103,8 @@ __device__ __forceinline__ u32 smem_index(u32 c, u32 l, u32 logC) {
     return w ^ ((w >> 3) & 15);
 }
 
-template <bool FWD, int S, bool COLS, bool SINGLE, bool MODUP = false, bool EPI = false>
+template <bool FWD, int S, bool COLS, bool SINGLE, bool MODUP = false, bool EPI = false,
+          bool OWN = false>
 struct Phase {
     static constexpr u32 GS = 1u << S;
     // sub-transforms per CTA: one whole polynomial in the single-phase case,
@@ -123,6 +129,9 @@ struct Phase {
     const u64* ea;
     u64* eout;
     u64 pv, pvs;
+    // OWN: the first pass also writes the loaded values times R to own
+    u64* own;
+    u64 rv, rvs;
 
     // global index of element l of sub-transform c
     __device__ __forceinline__ u32 gidx(u32 c, u32 l) const {
@@ -174,9 +183,14 @@ struct Phase {
             if constexpr (IN_G && !COLS && LB == 0) {
 #pragma unroll
                 for (u32 k = 0; k < NE; k += 2) {
-                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(gin + gidx(c, lbase + k));
+                    const u32 pos = gidx(c, lbase + k);
+                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(gin + pos);
                     x[k] = v.x;
                     x[k + 1] = v.y;
+                    if constexpr (OWN)
+                        *reinterpret_cast<ulonglong2*>(own + pos) =
+                            make_ulonglong2(csub(mul_shoup_lazy(v.x, rv, rvs, q), q),
+                                            csub(mul_shoup_lazy(v.y, rv, rvs, q), q));
                 }
             } else {
 #pragma unroll
@@ -284,7 +298,8 @@ struct Phase {
     }
 };
 
-template <bool FWD, int S, bool COLS, bool SINGLE, bool MODUP = false, bool EPI = false>
+template <bool FWD, int S, bool COLS, bool SINGLE, bool MODUP = false, bool EPI = false,
+          bool OWN = false>
 __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
     __shared__ __align__(16) u64 sm[kTile];
     const u32 p = blockIdx.x;
@@ -304,7 +319,13 @@ __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
               (u64)limb * N;
     }
 
-    Phase<FWD, S, COLS, SINGLE, MODUP, EPI> ph;
+    Phase<FWD, S, COLS, SINGLE, MODUP, EPI, OWN> ph;
+    if constexpr (OWN) {
+        const u32 b = mi / a.own_alpha;
+        ph.own = a.own_out + (((u64)grp * a.own_nd + b) * a.own_E + mi) * N;
+        ph.rv = a.mods[mi].r64;
+        ph.rvs = a.mods[mi].r64_shoup;
+    }
     if constexpr (EPI) {
         ph.ea = a.epi_a + (u64)grp * a.epi_a_stride + (u64)limb * N;
         ph.eout = a.epi_out + (u64)grp * a.epi_out_stride + (u64)limb * N;
@@ -343,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 5) ntt_phase_kernel(NttArgs a) {
     ph.gout = base;
     ph.canon = a.last != 0;
 
-    using Ph = Phase<FWD, S, COLS, SINGLE, MODUP, EPI>;
+    using Ph = Phase<FWD, S, COLS, SINGLE, MODUP, EPI, OWN>;
     constexpr u32 GS = 1u << S;
     constexpr u32 LOGC = Ph::LOGC;
     constexpr u32 T = Ph::C * GS;
@@ -395,15 +416,15 @@ int launch_phase(int S, dim3 grid, u32 threads, const NttArgs& a, cudaStream_t s
 }
 
 // the row phase of a two-phase transform, R = 7..11 levels (EPI: ModDown's
-// last step in its output)
-template <bool FWD, bool EPI = false>
+// last step in its output; OWN: the raise's own limbs from its input)
+template <bool FWD, bool EPI = false, bool OWN = false>
 int launch_rows(u32 R, dim3 grid, const NttArgs& a, cudaStream_t st) {
     switch (R) {
-        case 7: ntt_phase_kernel<FWD, 7, false, false, false, EPI><<<grid, kThreads, 0, st>>>(a); break;
-        case 8: ntt_phase_kernel<FWD, 8, false, false, false, EPI><<<grid, kThreads, 0, st>>>(a); break;
-        case 9: ntt_phase_kernel<FWD, 9, false, false, false, EPI><<<grid, kThreads, 0, st>>>(a); break;
-        case 10: ntt_phase_kernel<FWD, 10, false, false, false, EPI><<<grid, kThreads, 0, st>>>(a); break;
-        case 11: ntt_phase_kernel<FWD, 11, false, false, false, EPI><<<grid, kThreads, 0, st>>>(a); break;
+        case 7: ntt_phase_kernel<FWD, 7, false, false, false, EPI, OWN><<<grid, kThreads, 0, st>>>(a); break;
+        case 8: ntt_phase_kernel<FWD, 8, false, false, false, EPI, OWN><<<grid, kThreads, 0, st>>>(a); break;
+        case 9: ntt_phase_kernel<FWD, 9, false, false, false, EPI, OWN><<<grid, kThreads, 0, st>>>(a); break;
+        case 10: ntt_phase_kernel<FWD, 10, false, false, false, EPI, OWN><<<grid, kThreads, 0, st>>>(a); break;
+        case 11: ntt_phase_kernel<FWD, 11, false, false, false, EPI, OWN><<<grid, kThreads, 0, st>>>(a); break;
         default: return fail(PDQ_E_PARAM, "ntt: unsupported row phase");
     }
     return launched("ntt_phase_kernel");
@@ -413,7 +434,7 @@ template <bool FWD>
 int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 stride,
             cudaStream_t st, const NttArgs* from = nullptr, u32 skip_nd = 0, u32 skip_alpha = 0,
             const u64* ninv_tab = nullptr, const NttArgs* conv = nullptr,
-            const NttArgs* epi = nullptr) {
+            const NttArgs* epi = nullptr, const NttArgs* own = nullptr) {
     if (count == 0 || nlimbs == 0) return PDQ_OK;
     if (limb0 + nlimbs + skip_alpha > c.nmod) return fail(PDQ_E_PARAM, "ntt: limb range out of bounds");
     const u64 polys = (u64)count * nlimbs;
@@ -450,6 +471,14 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
         a.epi_out_stride = epi->epi_out_stride;
         a.epi_pinv = epi->epi_pinv;
         a.epi_pinvs = epi->epi_pinvs;
+    }
+    if (own) {
+        if (FWD || c.log_n <= kTileBits || limb0 != 0 || own->own_alpha == 0)
+            return fail(PDQ_E_PARAM, "ntt: own limbs need a two-phase inverse transform of c1");
+        a.own_out = own->own_out;
+        a.own_nd = own->own_nd;
+        a.own_alpha = own->own_alpha;
+        a.own_E = own->own_E;
     }
     if (from) {
         a.src = from->src;
@@ -505,6 +534,7 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
             rr.epi_a = epi->epi_a + g0 * epi->epi_a_stride;
             rr.epi_out = epi->epi_out + g0 * epi->epi_out_stride;
         }
+        if (own) rr.own_out = own->own_out + g0 * own->own_nd * own->own_E * c.N;
         const u32 pc = (u32)(gn * nlimbs);
         const dim3 gcols(pc, (1u << R) >> cols.logC);
         const dim3 grows(pc, (1u << S1) >> rows.logC);
@@ -514,7 +544,8 @@ int ntt_run(const Ctx& c, u64* data, u32 count, u32 nlimbs, u32 limb0, u64 strid
             if (epi) PDQ_TRY((launch_rows<true, true>(R, grows, rr, st)));
             else PDQ_TRY(launch_rows<FWD>(R, grows, rr, st));
         } else {
-            PDQ_TRY(launch_rows<FWD>(R, grows, rr, st));
+            if (own) PDQ_TRY((launch_rows<false, false, true>(R, grows, rr, st)));
+            else PDQ_TRY(launch_rows<FWD>(R, grows, rr, st));
             PDQ_TRY((launch_phase<FWD, true, false>((int)S1, gcols, kThreads, cc, st)));
         }
     }
@@ -579,7 +610,7 @@ int ntt_forward_moddown(const Ctx& c, u64* Cv, const u64* S, u64 s_stride, u32 c
 
 int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_per,
                      long long src_inner, u64 src_off, u64* data, u32 count, u32 nlimbs,
-                     u64 stride, cudaStream_t st, u32 limb0, const u64* ninv_tab) {
+                     u64 stride, cudaStream_t st, u32 limb0, const u64* ninv_tab, u64* own_out) {
     if (src_per == 0) return fail(PDQ_E_PARAM, "ntt: bad source set");
     NttArgs from{};
     from.src = src;
@@ -587,6 +618,15 @@ int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_
     from.src_inner = src_inner;
     from.src_per = src_per;
     from.src_off = src_off;
+    if (own_out) {
+        NttArgs ow{};
+        ow.own_out = own_out;
+        ow.own_nd = c.ndigits;
+        ow.own_alpha = c.alpha;
+        ow.own_E = c.L + c.K;
+        return ntt_run<false>(c, data, count, nlimbs, limb0, stride, st, &from, 0, 0, ninv_tab,
+                              nullptr, nullptr, &ow);
+    }
     return ntt_run<false>(c, data, count, nlimbs, limb0, stride, st, &from, 0, 0, ninv_tab);
 }
 

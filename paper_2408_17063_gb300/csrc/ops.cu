@@ -491,23 +491,6 @@ __global__ void __launch_bounds__(256) k_modup(const u64* __restrict__ X, CtSet 
     }
 }
 
-// The digits' own limbs of the raise (when the conversion rides on the
-// forward transform): D[ct][b][r] = c1_r R mod q_r for r in digit b (NTT form,
-// canonical), two positions per thread.
-__global__ void k_own_limbs(CtSet c1ntt, u64 c1_off, u32 logN, u32 E, u32 nd, u32 alpha,
-                            const Mod* __restrict__ mods, u64* __restrict__ D) {
-    const u32 x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (x >= (1u << logN)) return;
-    const u32 r = blockIdx.y, b = r / alpha;
-    const u64 ct = blockIdx.z;
-    const Mod mr = mods[r];
-    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(c1ntt.at(ct) + c1_off +
-                                                              ((u64)r << logN) + x);
-    *reinterpret_cast<ulonglong2*>(D + ((((ct * nd + b) * E) + r) << logN) + x) =
-        make_ulonglong2(csub(mul_shoup_lazy(v.x, mr.r64, mr.r64_shoup, mr.q), mr.q),
-                        csub(mul_shoup_lazy(v.y, mr.r64, mr.r64_shoup, mr.q), mr.q));
-}
-
 // A[ct][p][r][x] = sum_beta D[ct][beta][r][sigma(x)] * key[beta][p][r][x]
 // Two adjacent positions per thread (16-byte loads and stores): sigma maps
 // the aligned pair {x, x+1} onto an aligned pair, possibly swapped.
@@ -1640,12 +1623,9 @@ int ks_raise(const Ctx& c, CtSet in, u32 cnt, u64* ws, u64** D_out, cudaStream_t
         // c1 ends scaled by hat_inv_i (y_i into X), the digits' own limbs are
         // c1 R, and the forward transform of the other limbs converts from y
         // in its first phase (no converted copy of the digits is written)
+        // (the own limbs, c1 R, written by the inverse transform as it reads c1)
         PDQ_TRY(ntt_inverse_from(c, in.base, in.outer, in.per, in.inner, c1_off, X, cnt, c.L,
-                                 L * N, st, 0, c.d_ninv_up));
-        const dim3 g((c.N / 2 + kBlock - 1) / kBlock, c.L, cnt);
-        k_own_limbs<<<g, kBlock, 0, st>>>(in, c1_off, c.log_n, (u32)E, (u32)nd, c.alpha, c.d_mods,
-                                           D);
-        PDQ_TRY(launched("k_own_limbs"));
+                                 L * N, st, 0, c.d_ninv_up, D));
         PDQ_TRY(ntt_forward_digits_modup(c, D, X, cnt, (u32)nd, c.alpha, (u32)E, st));
         *D_out = D;
         return PDQ_OK;

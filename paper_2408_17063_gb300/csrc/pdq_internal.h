@@ -230,9 +230,13 @@ int ntt_forward_digits(const Ctx& c, u64* D, u32 count, u32 nd, u32 alpha, u32 n
 // data + g stride.
 // (ninv_tab: the last level's constants [nmod][4] instead of N^-1's, e.g.
 // c.d_ninv_up, which leaves limb i scaled by hat_inv_i)
+// (own_out: also write the raise's own limbs, c1_r R for r in digit r /
+// alpha, into raised digits [count][ndigits][L+K][N], as the first phase reads
+// c1; two-phase rings, nlimbs = L, limb0 = 0)
 int ntt_inverse_from(const Ctx& c, const u64* src, long long src_outer, u32 src_per,
                      long long src_inner, u64 src_off, u64* data, u32 count, u32 nlimbs,
-                     u64 stride, cudaStream_t st, u32 limb0 = 0, const u64* ninv_tab = nullptr);
+                     u64 stride, cudaStream_t st, u32 limb0 = 0, const u64* ninv_tab = nullptr,
+                     u64* own_out = nullptr);
 // The raised digits' forward transform with the basis conversion folded into
 // its first phase: D[ct][b][r] (r outside digit b's alpha <= 2 limbs) =
 // NTT(sum_{k < alpha} y[ct][b alpha + k] (Q_b/q_{b alpha+k}) R mod q_r), where
