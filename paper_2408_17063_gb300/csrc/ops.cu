@@ -1728,8 +1728,9 @@ int ks_apply_giants(const Ctx& c, const u64* D, u32 cnt, u32 terms, const u64* g
 
 namespace {
 
-// HC ciphertexts per CTA, CPT per thread: 16 and 8, or 2 and 1 for queries
-// of at most 2 ciphertexts (a CTA holds one query's, which share a key set)
+// HC ciphertexts per CTA, CPT per thread: 16 and 8, or 2/4/8 and 1/2/4 for
+// queries of at most that many ciphertexts (a CTA holds one query's, which
+// share a key set)
 template <int ND, u32 HC = 16, u32 CPT = 8>
 int launch_baby(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B, const KeyTable& kt,
                 const BabyParams& bp, u64* Rx, cudaStream_t st, bool ext, u32 l0, u32 el) {
@@ -1811,6 +1812,23 @@ int hoisted_rotations_ext(const Ctx& c, const u64* D, CtSet u, u32 H, u32 B,
     }
     const KeyTable t = kt ? *kt : single_keys(keys);
     const u32 Hq = t.per == ~0u ? H : t.per;
+    // CTAs of 4 or 8 ciphertexts for queries of that many (up to 4 digits)
+    if (Hq > 2 && Hq <= 8 && c.ndigits <= 4) {
+        if (Hq <= 4) {
+            switch (c.ndigits) {
+                case 1: return launch_baby<1, 4, 2>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+                case 2: return launch_baby<2, 4, 2>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+                case 3: return launch_baby<3, 4, 2>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+                default: return launch_baby<4, 4, 2>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            }
+        }
+        switch (c.ndigits) {
+            case 1: return launch_baby<1, 8, 4>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            case 2: return launch_baby<2, 8, 4>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            case 3: return launch_baby<3, 8, 4>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+            default: return launch_baby<4, 8, 4>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);
+        }
+    }
     if (Hq <= 2) {
         switch (c.ndigits) {
             case 1: return launch_baby<1, 2, 1>(c, D, u, H, B, t, bp, Rx, st, ext, l0, el);

@@ -59,6 +59,9 @@ def test_c3_sampled_steps_bit_exact(c3):
     dict(cfg_name="tiny", n=1, s=1),             # a single record
     dict(cfg_name="grouped", n=257, s=2),        # a second group with one record
     dict(cfg_name="tiny2", n=300, s=32, B=32),   # 320 products per accumulator (wide fold)
+    dict(cfg_name="small", n=2000, s=9),         # 4 half-blocks: rotation CTAs of 4
+    dict(cfg_name="small", n=3500, s=9),         # 8 half-blocks: rotation CTAs of 8
+    dict(cfg_name="c1", n=8000, s=20),           # 4 half-blocks at a two-phase ring
 ])
 def test_edge_cases_bit_exact(kw):
     name = kw.pop("cfg_name")
