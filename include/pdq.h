@@ -189,7 +189,8 @@ int pdq_secret_prepare(const pdq_ctx* ctx, const int8_t* s, uint64_t* sk_out, vo
 int pdq_encrypt(const pdq_ctx* ctx, const uint64_t* sk, const uint32_t* slots, uint32_t count,
                 const uint64_t* a, const int32_t* e, uint64_t* ct_out, void* stream);
 
-/* Hybrid key-switching key from sigma_k(s) to s for the Galois element
+/* Hybrid key-switching key from sigma_k(s) to s (an evaluation key of HE
+ * KeyGen, Sec. 2.2, for the rotations of Sec. 5.1) for the Galois element
  * `galois` (k odd, < 2N; Rot_row(.; r) is k = 3^r, Rot_col is k = 2N-1):
  * per digit beta, b = -a*s + e + [q_i in beta] * P * sigma_k(s).  a: dev
  * [ndigits][L+K][N] uniform coefficient form, e: dev [ndigits][N].
@@ -389,16 +390,16 @@ int pdq_answer_stacked(const pdq_ctx* ctx, const pdq_plan* plan, uint32_t Q,
                        const uint64_t* consts, uint64_t* out, void* ws, size_t ws_bytes,
                        void* stream);
 
-/* Answer with host buffers, end to end: copies the query ciphertexts (host
- * [J][2][L][N], coefficient form) to the device, transforms them, runs
- * Mask and Comp, transforms the answer back and copies it to out_host
- * ([n_out][2][L][N], coefficient form).  The query goes up in at most four
- * runs of index ciphertexts on a stream of the call's own, ordered after the
- * work already queued on `stream`; each run is transformed and packed on
- * `stream` while the next one is copied.  Synchronises `stream` (and its own
- * copy stream) before returning, also on errors after the copies started.
- * Host buffers should be pinned for the copies to overlap.
- * Workspace: pdq_answer_host_workspace_bytes (device). */
+/* Answer (Alg. 7 without Match, as pdq_answer) with host buffers, end to
+ * end: copies the query ciphertexts (host [J][2][L][N], coefficient form) to
+ * the device, transforms them, runs Mask and Comp, transforms the answer
+ * back and copies it to out_host ([n_out][2][L][N], coefficient form).  The
+ * query goes up in at most four runs of index ciphertexts on a stream of the
+ * call's own, ordered after the work already queued on `stream`; each run is
+ * transformed and packed on `stream` while the next one is copied.
+ * Synchronises `stream` (and its own copy stream) before returning, also on
+ * errors after the copies started.  Host buffers should be pinned for the
+ * copies to overlap.  Workspace: pdq_answer_host_workspace_bytes (device). */
 size_t pdq_answer_host_workspace_bytes(const pdq_ctx* ctx, const pdq_plan* plan);
 int pdq_answer_host(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_host,
                     const uint64_t* db, const uint64_t* keys, const uint64_t* galois,
@@ -467,18 +468,20 @@ int pdq_answer_batch(const pdq_ctx* ctx, const pdq_query* queries, uint32_t nq,
                      void* const* lane_ws, const size_t* lane_ws_bytes, uint32_t lanes,
                      void* stream);
 
-/* Continuous-batching server.  `arena` (dev, arena_bytes) is the device
- * memory the server may use for workspaces: a request is admitted when one
- * of the `lanes` worker threads is idle and the arena has room for its
- * workspace (first fit), in arrival order; it then runs on that worker's
- * stream, concurrently with the other admitted requests.  max_queue (0 =
- * unbounded) caps the number of waiting requests (PDQ_E_BUSY beyond).  A
- * request whose workspace exceeds the whole arena is refused with
- * PDQ_E_NOMEM.  The caller keeps every buffer of a request alive until it is
- * done and must not enable stage profiling while a server runs.  The workers'
- * streams do not wait on any stream of the caller: the arena and every buffer
- * of a request must hold no pending work from other streams when they are
- * handed over.  Times are host steady-clock nanoseconds. */
+/* Continuous-batching server of Answer requests (each one Alg. 7 without
+ * Match, as pdq_answer; the serving loop itself is not part of the paper's
+ * method).  `arena` (dev, arena_bytes) is the device memory the server may
+ * use for workspaces: a request is admitted when one of the `lanes` worker
+ * threads is idle and the arena has room for its workspace (first fit), in
+ * arrival order; it then runs on that worker's stream, concurrently with the
+ * other admitted requests.  max_queue (0 = unbounded) caps the number of
+ * waiting requests (PDQ_E_BUSY beyond).  A request whose workspace exceeds
+ * the whole arena is refused with PDQ_E_NOMEM.  The caller keeps every
+ * buffer of a request alive until it is done and must not enable stage
+ * profiling while a server runs.  The workers' streams do not wait on any
+ * stream of the caller: the arena and every buffer of a request must hold no
+ * pending work from other streams when they are handed over.  Times are host
+ * steady-clock nanoseconds. */
 typedef struct pdq_server pdq_server;
 #define PDQ_REQ_QUEUED 0
 #define PDQ_REQ_RUNNING 1
@@ -495,16 +498,17 @@ int pdq_server_create(void* arena, size_t arena_bytes, uint32_t lanes, uint32_t 
 int pdq_server_submit(pdq_server* srv, const pdq_ctx* ctx, const pdq_query* q,
                       uint64_t* ticket);
 int pdq_server_status(pdq_server* srv, uint64_t ticket, pdq_ticket_info* info);
-/* Stacking (continuous batching of requests of one shape): with max_stack
- * >= 2, a worker that admits the oldest request also takes up to
- * max_stack - 1 queued requests of the same context, database, plan
- * constants, Galois list and plan shape (every plan field but the record and
- * match counts, which only the client's Decomp reads), as many as the arena
- * has room for, and answers them with one pdq_answer_stacked call (their
- * index ciphertexts gathered into the workspace first, the outputs copied to
- * each request's buffer after); each result is the same bits as the request
- * alone.  0 or 1 turns it off (the default); at most 64.  Affects requests
- * admitted after the call. */
+/* Stacking (continuous batching of requests of one shape; each request is
+ * still Alg. 7's Answer, and stacking is a launch schedule that is not part
+ * of the paper's method): with max_stack >= 2, a worker that admits the
+ * oldest request also takes up to max_stack - 1 queued requests of the same
+ * context, database, plan constants, Galois list and plan shape (every plan
+ * field but the record and match counts, which only the client's Decomp
+ * reads), as many as the arena has room for, and answers them with one
+ * pdq_answer_stacked call (their index ciphertexts gathered into the
+ * workspace first, the outputs copied to each request's buffer after); each
+ * result is the same bits as the request alone.  0 or 1 turns it off (the
+ * default); at most 64.  Affects requests admitted after the call. */
 int pdq_server_set_stacking(pdq_server* srv, uint32_t max_stack);
 int pdq_server_wait(pdq_server* srv, uint64_t ticket, uint32_t timeout_ms);
 int pdq_server_drain(pdq_server* srv, uint32_t timeout_ms);

@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads without a GPU and exports every
-entry point declared in include/pdq.h (no compute calls)."""
+entry point declared in include/pdq.h, each citing its passage; a plain C99
+client compiles and links against it (no compute calls)."""
 import ctypes
 import re
 
@@ -18,10 +19,96 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert sorted(pdq._SIGS) == declared
 
 
-def test_header_documents_every_entry_point():
-    text = open(build.os.path.join(build.INCLUDE, "pdq.h")).read()
-    for name in re.findall(r"\b(pdq_[a-z0-9_]+)\s*\(", text):
-        assert f"{name}(" in text
+_DECL = re.compile(r"^\s*(?:const\s+)?(?:int|size_t|void|unsigned long long|uint\d+_t|const char\*)"
+                   r"\s*\*?\s*(pdq_[a-z0-9_]+)\s*\(")
+_CITES = re.compile(r"(Sec\.|Alg\.|Eq\.|Def\.|Table|[Rr]emark)")
+_NO_COUNTERPART = re.compile(r"(no operation of the paper|not part of the paper|[Nn]ot part of the "
+                             r"paper's method|no counterpart|library bookkeeping)")
+
+
+def _declarations_with_comments():
+    """(name, the comment block that precedes its declaration group) for every
+    function declared in include/pdq.h."""
+    lines = open(build.os.path.join(build.INCLUDE, "pdq.h")).read().splitlines()
+    out, last, cur, in_comment = [], "", [], False
+    for ln in lines:
+        s = ln.strip()
+        if in_comment:
+            cur.append(s)
+            if "*/" in s:
+                in_comment, last = False, " ".join(cur)
+            continue
+        if s.startswith("/*"):
+            cur = [s]
+            if "*/" in s:
+                last = s
+            else:
+                in_comment = True
+            continue
+        m = _DECL.match(ln)
+        if m:
+            out.append((m.group(1), last))
+    return out
+
+
+def test_header_cites_the_passage_of_every_entry_point():
+    """Each entry point's comment names the passage of the paper it follows
+    (section, algorithm, equation, definition, table or remark), or says that
+    the paper has no counterpart (bookkeeping, workspaces, instrumentation)."""
+    decls = _declarations_with_comments()
+    from paper_2408_17063_gb300 import pdq
+    assert sorted(n for n, _ in decls) == pdq.header_symbols()
+    bare = [n for n, c in decls if not (_CITES.search(c) or _NO_COUNTERPART.search(c))]
+    assert bare == [], f"entry points without a cited passage: {bare}"
+
+
+_C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "pdq.h"
+
+int main(void) {
+    pdq_ctx* ctx = NULL;
+    pdq_schedule sched;
+    int rc;
+    if (pdq_launch_count() != 0) return 10;
+    if (pdq_rotate_noalloc_max_bytes() != (size_t)32 << 20) return 11;
+    /* refusals come back as codes with a message, never as a crash */
+    rc = pdq_ctx_create(NULL, &ctx);
+    if (rc != PDQ_E_PARAM || ctx != NULL) return 12;
+    if (strlen(pdq_last_error()) == 0) return 13;
+    if (pdq_ctx_destroy(NULL) != PDQ_OK) return 14;
+    memset(&sched, 0, sizeof sched);
+    if (pdq_ctx_set_schedule(NULL, &sched) != PDQ_E_PARAM) return 15;
+    printf("ok %s\n", pdq_last_error());
+    return 0;
+}
+"""
+
+
+def test_c_client_compiles_links_and_gets_error_codes(tmp_path):
+    """The boundary is a C ABI: a C99 program (no C++ and no Python) compiles
+    against include/pdq.h with -pedantic -Werror, links libpdq.so and gets
+    error codes and messages back from refused calls (no GPU is touched)."""
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    path = build.build()
+    src = tmp_path / "client.c"
+    src.write_text(_C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = build.os.path.dirname(path)
+    cmd = [cc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", build.INCLUDE,
+           str(src), "-o", str(exe), f"-L{libdir}", f"-l:{build.os.path.basename(path)}",
+           f"-Wl,-rpath,{libdir}"]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0, (run.returncode, run.stdout, run.stderr)
+    assert run.stdout.startswith("ok ")
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
