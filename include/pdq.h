@@ -277,6 +277,14 @@ int pdq_ring_switch(const pdq_ctx* big, const pdq_ctx* small, const uint64_t* ct
  * measured costs), ties to the smaller B.  Errors: PDQ_E_PARAM if s' > N/2,
  * s' >= t, B does not divide s', B > 128 or s'/B > 32. */
 int pdq_plan_make(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B, pdq_plan* plan);
+/* The same plan without a context, from the plaintext prime t and the ring
+ * X^N + 1, N = 2^log_n, alone (the layout of Sec. 5.2 depends on nothing
+ * else): for a client that computes the answer's layout on a machine with no
+ * GPU.  Host only, synchronous; nothing is allocated.  Errors as
+ * pdq_plan_make's, and PDQ_E_PARAM unless 3 <= log_n <= 16 and t is a prime
+ * < 2^31 with t = 1 mod 2N (the checks of pdq_ctx_create). */
+int pdq_plan_make_client(uint64_t t, uint32_t log_n, uint64_t n, uint32_t s, uint32_t B,
+                         pdq_plan* plan);
 
 /* The plan of Comp in the subring `small` on a query ring-switched from the
  * ring of dimension 2^big_log_n (Sec. 5.3): J = R ceil(n / N_big) subring
@@ -526,6 +534,15 @@ int pdq_server_destroy(pdq_server* srv);
  * synchronous. */
 int pdq_decomp(const pdq_ctx* ctx, const pdq_plan* plan, const uint32_t* slots,
                uint64_t* idx_out, uint32_t* val_out, uint64_t cap, uint64_t* count);
+/* Decomp (Alg. 6) without a context: the client decrypts and decompresses
+ * on its own machine, which needs no GPU.  t and log_n give the plaintext
+ * prime and the answer's ring (for a ring-switched answer, the subring's);
+ * the plan is checked against a fresh plan of its kind for that ring, as
+ * pdq_decomp checks it against its context's.  Same results and errors as
+ * pdq_decomp, and PDQ_E_PARAM for a ring or prime that pdq_ctx_create would
+ * refuse.  Host only, synchronous. */
+int pdq_decomp_client(uint64_t t, uint32_t log_n, const pdq_plan* plan, const uint32_t* slots,
+                      uint64_t* idx_out, uint32_t* val_out, uint64_t cap, uint64_t* count);
 
 /* ---------------------------------------------------------- serialise
  * Exchange format between client and server (Alg. 7 sends the query

@@ -700,6 +700,14 @@ int pdq_plan_make(const pdq_ctx* ctx, uint64_t n, uint32_t s, uint32_t B, pdq_pl
     return plan_make(C(ctx), n, s, B, plan);
 }
 
+int pdq_plan_make_client(uint64_t t, uint32_t log_n, uint64_t n, uint32_t s, uint32_t B,
+                         pdq_plan* plan) {
+    if (!plan) return fail(PDQ_E_PARAM, "null plan");
+    Ctx c;
+    PDQ_TRY(host_ring(t, log_n, &c));
+    return plan_make(c, n, s, B, plan);
+}
+
 int pdq_plan_galois(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out, uint32_t cap,
                     uint32_t* count) {
     PDQ_CHECK_CTX(ctx);

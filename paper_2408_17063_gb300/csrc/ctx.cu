@@ -159,6 +159,18 @@ static u64 root_2n(u64 q, u64 N) {
     return 0;
 }
 
+int host_ring(u64 t, u32 log_n, Ctx* c) {
+    if (log_n < 3 || log_n > 16) return fail(PDQ_E_PARAM, "log_n must be in [3, 16]");
+    const u64 twoN = 2ull << log_n;
+    if (t < 3 || t >= (1ull << 31) || (t - 1) % twoN != 0 || !host_is_prime(t))
+        return fail(PDQ_E_PARAM, "t must be a prime < 2^31 with t = 1 mod 2N");
+    c->log_n = log_n;
+    c->N = 1u << log_n;
+    c->m = c->N / 2;
+    c->t = t;
+    return PDQ_OK;
+}
+
 template <class T>
 static int upload(T** dst, const std::vector<T>& src) {
     if (cudaMalloc((void**)dst, src.size() * sizeof(T)) != cudaSuccess)

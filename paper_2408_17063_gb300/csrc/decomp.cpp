@@ -125,15 +125,11 @@ int decode_group(const u32* w, const u32* e, u32 sp, u64 G_sz, const Zt& z,
     return PDQ_OK;
 }
 
-}  // namespace
-}  // namespace pdq
-
-using namespace pdq;
-
-extern "C" int pdq_decomp(const pdq_ctx* ctx, const pdq_plan* plan, const uint32_t* slots,
-                          uint64_t* idx_out, uint32_t* val_out, uint64_t cap, uint64_t* count) {
-    if (!ctx || !plan || !slots || !count) return fail(PDQ_E_PARAM, "decomp: null argument");
-    const Ctx& c = *reinterpret_cast<const Ctx*>(ctx);
+// Decomp over every record group of the plan's output ciphertexts; only the
+// ring and t of c are read (c may be a host ring without device tables).
+int decomp_run(const Ctx& c, const pdq_plan* plan, const uint32_t* slots, uint64_t* idx_out,
+               uint32_t* val_out, uint64_t cap, uint64_t* count) {
+    if (!plan || !slots || !count) return fail(PDQ_E_PARAM, "decomp: null argument");
     if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "decomp: invalid plan");
     const Zt z{c.t};
     const u32 sp = plan->s_prime;
@@ -155,4 +151,24 @@ extern "C" int pdq_decomp(const pdq_ctx* ctx, const pdq_plan* plan, const uint32
     *count = total;
     if (total > cap) return fail(PDQ_E_NOMEM, "decomp: output capacity too small");
     return PDQ_OK;
+}
+
+}  // namespace
+}  // namespace pdq
+
+using namespace pdq;
+
+extern "C" int pdq_decomp(const pdq_ctx* ctx, const pdq_plan* plan, const uint32_t* slots,
+                          uint64_t* idx_out, uint32_t* val_out, uint64_t cap, uint64_t* count) {
+    if (!ctx) return fail(PDQ_E_PARAM, "decomp: null argument");
+    return decomp_run(*reinterpret_cast<const Ctx*>(ctx), plan, slots, idx_out, val_out, cap,
+                      count);
+}
+
+extern "C" int pdq_decomp_client(uint64_t t, uint32_t log_n, const pdq_plan* plan,
+                                 const uint32_t* slots, uint64_t* idx_out, uint32_t* val_out,
+                                 uint64_t cap, uint64_t* count) {
+    Ctx c;
+    PDQ_TRY(host_ring(t, log_n, &c));
+    return decomp_run(c, plan, slots, idx_out, val_out, cap, count);
 }

@@ -210,6 +210,10 @@ u64 host_invmod(u64 a, u64 q);
 u64 shoup_of(u64 w, u64 q);
 Mod make_mod(u64 q);
 bool host_is_prime(u64 n);
+// The ring X^N + 1 (N = 2^log_n) and the plaintext prime t alone, checked as
+// a context checks them, into c: no primes, tables or device memory.  Enough
+// for the plan arithmetic and Decomp, which a client runs without a GPU.
+int host_ring(u64 t, u32 log_n, Ctx* c);
 u32 bitrev(u32 x, u32 bits);
 
 // ------------------------------------------------------------- transforms --

@@ -104,6 +104,7 @@ _SIGS = {
     "pdq_ctx_set_schedule": (_I, [_P, ctypes.POINTER(Schedule)]),
     "pdq_ctx_get_schedule": (_I, [_P, ctypes.POINTER(Schedule)]),
     "pdq_plan_make": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
+    "pdq_plan_make_client": (_I, [_U64, _U32, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_plan_make_switched": (_I, [_P, _U32, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_plan_make_plain_db": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_db_diagonals_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
@@ -135,6 +136,8 @@ _SIGS = {
     "pdq_answer_host": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _P, _U32, _P, _P, _P, _SZ,
                              _P]),
     "pdq_decomp": (_I, [_P, ctypes.POINTER(Plan), _P, _P, _P, _U64, ctypes.POINTER(_U64)]),
+    "pdq_decomp_client": (_I, [_U64, _U32, ctypes.POINTER(Plan), _P, _P, _P, _U64,
+                               ctypes.POINTER(_U64)]),
     "pdq_launch_count": (ctypes.c_ulonglong, []),
     "pdq_answer_batch": (_I, [_P, ctypes.POINTER(Query), _U32, _P, _P, _U32, _P]),
     "pdq_server_create": (_I, [_P, _SZ, _U32, _U32, ctypes.POINTER(_P)]),
@@ -211,6 +214,32 @@ def _stream(stream) -> int:
     if stream is None:
         return torch.cuda.current_stream().cuda_stream
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _decomp(call, plan: Plan, slots) -> list[tuple[int, int]]:
+    """Marshals one Decomp call: call(plan, slots, idx, val, cap, count)."""
+    s = np.ascontiguousarray(torch.as_tensor(slots).cpu().numpy().astype(np.uint32))
+    cap = max(1, plan.G * plan.s_prime)
+    idx = np.zeros(cap, dtype=np.uint64)
+    val = np.zeros(cap, dtype=np.uint32)
+    cnt = _U64()
+    _check(call(ctypes.byref(plan), _ptr(s), _ptr(idx), _ptr(val), cap, ctypes.byref(cnt)))
+    n = cnt.value
+    return [(int(i), int(v)) for i, v in zip(idx[:n], val[:n])]
+
+
+def plan_make_client(t: int, log_n: int, n: int, s: int, B: int = 0) -> Plan:
+    """pdq_plan_make_client: the Answer's layout from t and the ring alone."""
+    pl = Plan()
+    _check(load().pdq_plan_make_client(t, log_n, n, s, B, ctypes.byref(pl)))
+    return pl
+
+
+def decomp_client(t: int, log_n: int, plan: Plan, slots) -> list[tuple[int, int]]:
+    """pdq_decomp_client: Decomp on the host with no context or GPU; slots
+    [n_out][N] decrypted answer; returns sorted (record index, value) pairs."""
+    lib = load()
+    return _decomp(lambda *a: lib.pdq_decomp_client(t, log_n, *a), plan, slots)
 
 
 class Context:
@@ -627,15 +656,8 @@ class Context:
     def decomp(self, plan: Plan, slots) -> list[tuple[int, int]]:
         """slots: [n_out][N] decrypted answer (host or device); returns sorted
         (record index, value) pairs."""
-        s = np.ascontiguousarray(torch.as_tensor(slots).cpu().numpy().astype(np.uint32))
-        cap = max(1, plan.G * plan.s_prime)
-        idx = np.zeros(cap, dtype=np.uint64)
-        val = np.zeros(cap, dtype=np.uint32)
-        cnt = _U64()
-        _check(load().pdq_decomp(self.h, ctypes.byref(plan), _ptr(s), _ptr(idx), _ptr(val), cap,
-                                 ctypes.byref(cnt)))
-        n = cnt.value
-        return [(int(i), int(v)) for i, v in zip(idx[:n], val[:n])]
+        lib = load()
+        return _decomp(lambda *a: lib.pdq_decomp(self.h, *a), plan, slots)
 
 
 class QueryHandle:
