@@ -308,6 +308,14 @@ int pdq_plan_make_switched(const pdq_ctx* small, uint32_t big_log_n, uint64_t n,
  * per element in this order. */
 int pdq_plan_galois(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out, uint32_t cap,
                     uint32_t* count);
+/* The same list without a context, from t and the ring X^N + 1, N = 2^log_n
+ * (the plan's ring: the subring for a ring-switched plan), as
+ * pdq_plan_make_client: the client learns which rotation keys (Sec. 5.2) to
+ * make and send on a machine with no GPU.  Host only; errors as
+ * pdq_plan_galois's, and PDQ_E_PARAM for a ring or prime that
+ * pdq_ctx_create would refuse. */
+int pdq_plan_galois_client(uint64_t t, uint32_t log_n, const pdq_plan* plan, uint64_t* out,
+                           uint32_t cap, uint32_t* count);
 
 /* Query-independent constants of a plan: the extended diagonals
  *   D_{h,k}[c] = alpha(h m + ((c+k) mod m))^{(c mod s')+1} mod t,

@@ -721,6 +721,20 @@ int pdq_plan_galois(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t* out, uin
     return PDQ_OK;
 }
 
+int pdq_plan_galois_client(uint64_t t, uint32_t log_n, const pdq_plan* plan, uint64_t* out,
+                           uint32_t cap, uint32_t* count) {
+    Ctx c;
+    PDQ_TRY(host_ring(t, log_n, &c));
+    if (!valid_plan(c, plan) || !count) return fail(PDQ_E_PARAM, "plan_galois: invalid plan");
+    auto ks = plan_galois(c, *plan);
+    *count = (uint32_t)ks.size();
+    if (out) {
+        if (cap < ks.size()) return fail(PDQ_E_NOMEM, "plan_galois: output too small");
+        std::copy(ks.begin(), ks.end(), out);
+    }
+    return PDQ_OK;
+}
+
 size_t pdq_plan_constants_bytes(const pdq_ctx* ctx, const pdq_plan* plan) {
     if (!ctx || !valid_plan(C(ctx), plan)) return 0;
     const Ctx& c = C(ctx);

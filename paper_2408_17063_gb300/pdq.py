@@ -105,6 +105,8 @@ _SIGS = {
     "pdq_ctx_get_schedule": (_I, [_P, ctypes.POINTER(Schedule)]),
     "pdq_plan_make": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_plan_make_client": (_I, [_U64, _U32, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
+    "pdq_plan_galois_client": (_I, [_U64, _U32, ctypes.POINTER(Plan), _P, _U32,
+                                    ctypes.POINTER(_U32)]),
     "pdq_plan_make_switched": (_I, [_P, _U32, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_plan_make_plain_db": (_I, [_P, _U64, _U32, _U32, ctypes.POINTER(Plan)]),
     "pdq_db_diagonals_bytes": (_SZ, [_P, ctypes.POINTER(Plan)]),
@@ -233,6 +235,17 @@ def plan_make_client(t: int, log_n: int, n: int, s: int, B: int = 0) -> Plan:
     pl = Plan()
     _check(load().pdq_plan_make_client(t, log_n, n, s, B, ctypes.byref(pl)))
     return pl
+
+
+def plan_galois_client(t: int, log_n: int, plan: Plan) -> list[int]:
+    """pdq_plan_galois_client: the plan's Galois elements from t and the ring."""
+    lib = load()
+    cnt = _U32()
+    _check(lib.pdq_plan_galois_client(t, log_n, ctypes.byref(plan), None, 0, ctypes.byref(cnt)))
+    arr = (ctypes.c_uint64 * max(1, cnt.value))()
+    _check(lib.pdq_plan_galois_client(t, log_n, ctypes.byref(plan), ctypes.cast(arr, _P),
+                                      cnt.value, ctypes.byref(cnt)))
+    return [int(x) for x in arr[:cnt.value]]
 
 
 def decomp_client(t: int, log_n: int, plan: Plan, slots) -> list[tuple[int, int]]:

@@ -1,23 +1,27 @@
-"""Client-side layout and Decomp of the library without a context or a GPU
-(pdq_plan_make_client, pdq_decomp_client: host code of libpdq.so): the
-library's plans equal the oracle's for every kind of plan, and its Decomp
-recovers exactly the matching records from the closed-form answer slots of
-Eq. 1 (Alg. 6), as the oracle's Decomp does, with the same refusals."""
+"""Client-side layout, rotation list and Decomp of the library without a
+context or a GPU (pdq_plan_make_client, pdq_plan_galois_client,
+pdq_decomp_client: host code of libpdq.so): the library's plans and Galois
+elements equal the oracle's for every kind of plan, and its Decomp recovers
+exactly the matching records from the closed-form answer slots of Eq. 1
+(Alg. 6), as the oracle's Decomp does, with the same refusals."""
 import ctypes
-from types import SimpleNamespace
+import functools
 
 import numpy as np
 import pytest
 
+from oracle import bfv
 from oracle import pdq as opdq
 from paper_2408_17063_gb300 import pdq
 
 FIELDS = ("n", "s", "s_prime", "B", "J", "H", "G_sz", "hpg", "G", "per_out", "n_out")
 
 
+@functools.lru_cache(maxsize=None)
 def ring(t, log_n):
-    # the oracle's layout and closed form read only N, m and t
-    return SimpleNamespace(t=t, log_n=log_n, N=1 << log_n, m=1 << (log_n - 1))
+    # an oracle parameter set with a short chain: the layout, the Galois
+    # elements and the closed form read only its ring and t
+    return bfv.Params(log_n=log_n, t=t, bits=40, L=1, K=1, dnum=1)
 
 
 def to_struct(op, kind="answer", R=1):
@@ -50,6 +54,36 @@ SHAPES = [  # (t, log_n, n, s, B)
 def test_client_plan_equals_oracle_plan(t, log_n, n, s, B):
     op = opdq.make_plan(ring(t, log_n), n, s, B or None)
     assert same_plan(pdq.plan_make_client(t, log_n, n, s, B), op)
+
+
+@pytest.mark.parametrize("t,log_n,n,s,B", SHAPES)
+def test_client_galois_elements_equal_the_oracle(t, log_n, n, s, B):
+    """The rotations the schedule of Sec. 5.2 uses (Rot_col, baby and giant
+    steps, the rotate-and-sum levels): the keys the client must send."""
+    par = ring(t, log_n)
+    op = opdq.make_plan(par, n, s, B or None)
+    pl = pdq.plan_make_client(t, log_n, n, s, B)
+    assert pdq.plan_galois_client(t, log_n, pl) == opdq.galois_elements(par, op)
+    db = opdq.make_plan_plain_db(par, n, s, B or None)
+    assert pdq.plan_galois_client(t, log_n, to_struct(db, kind="plain_db")) == \
+        opdq.plain_db_galois_elements(par, db)
+
+
+def test_client_galois_elements_of_a_switched_plan_and_refusals():
+    big, small = ring(65537, 15), ring(65537, 13)
+    op = opdq.make_switched_plan(big, small, 2 ** 17, 256)
+    pl = to_struct(op, R=4)
+    assert pdq.plan_galois_client(65537, 13, pl) == opdq.galois_elements(small, op)
+    lib = pdq.load()
+    cnt = ctypes.c_uint32()
+    out = np.zeros(2, dtype=np.uint64)
+    rc = lib.pdq_plan_galois_client(65537, 13, ctypes.byref(pl), out.ctypes.data, 2,
+                                    ctypes.byref(cnt))
+    assert rc == pdq.PDQ_E_NOMEM and cnt.value == len(opdq.galois_elements(small, op))
+    pl.hpg += 1
+    with pytest.raises(pdq.PdqError) as e:
+        pdq.plan_galois_client(65537, 13, pl)
+    assert e.value.code == pdq.PDQ_E_PARAM
 
 
 def test_client_plan_refusals():
