@@ -118,3 +118,24 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     import pytest
     with pytest.raises(ImportError):
         pdq.load()
+
+
+def test_context_refuses_bad_parameters_before_any_device_work():
+    """pdq_ctx_create checks the parameter set of Sec. 5.1 (ring, prime t =
+    1 mod 2N, chain and digit counts) on the host and returns PDQ_E_PARAM with
+    a message, leaving *out NULL, before it touches a device."""
+    from paper_2408_17063_gb300 import pdq
+    lib = pdq.load()
+    good = dict(log_n=10, prime_bits=40, L=2, K=1, dnum=2, t=65537)
+    bad = [dict(log_n=2), dict(log_n=17), dict(prime_bits=19), dict(prime_bits=61),
+           dict(L=0), dict(L=31), dict(K=0), dict(K=9), dict(dnum=0), dict(dnum=3),
+           dict(t=65539), dict(t=12289 * 2 + 1), dict(t=7681), dict(t=2),
+           dict(log_n=16, t=65537),              # 65536 is not a multiple of 2^17
+           dict(prime_bits=20, L=30, K=8)]       # too few primes = 1 mod 2N below 2^20
+    for change in bad:
+        p = pdq.Params(**{**good, **change})
+        out = ctypes.c_void_p(1234)
+        rc = lib.pdq_ctx_create(ctypes.byref(p), ctypes.byref(out))
+        assert rc == pdq.PDQ_E_PARAM, (change, rc, lib.pdq_last_error())
+        assert out.value is None
+        assert lib.pdq_last_error()
