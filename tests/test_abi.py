@@ -139,3 +139,27 @@ def test_context_refuses_bad_parameters_before_any_device_work():
         assert rc == pdq.PDQ_E_PARAM, (change, rc, lib.pdq_last_error())
         assert out.value is None
         assert lib.pdq_last_error()
+
+
+def test_every_entry_point_refuses_null_arguments():
+    """Called with every pointer NULL and every number 0, each entry point
+    returns an error code with a message (an int call), or 0 (a size query),
+    without touching memory or a device: NULL is never dereferenced across
+    the ABI.  Destroying NULL is a no-op that succeeds."""
+    from paper_2408_17063_gb300 import pdq
+    lib = pdq.load()
+    no_error = {"pdq_ctx_destroy", "pdq_server_destroy"}
+    not_calls = {"pdq_last_error", "pdq_launch_count", "pdq_rotate_noalloc_max_bytes"}
+    for name, (res, args) in sorted(pdq._SIGS.items()):
+        if name in not_calls:
+            continue
+        vals = [None if (a is pdq._P or (isinstance(a, type) and issubclass(a, ctypes._Pointer)))
+                else 0 for a in args]
+        rc = getattr(lib, name)(*vals)
+        if res is pdq._SZ:
+            assert rc == 0, name
+        elif name in no_error:
+            assert rc == pdq.PDQ_OK, name
+        else:
+            assert rc == pdq.PDQ_E_PARAM, (name, rc)
+            assert lib.pdq_last_error(), name
