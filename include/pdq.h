@@ -127,7 +127,7 @@ const char* pdq_last_error(void);
 /* Memory of the baby-step rotations (Sec. 5.2: Rot(u_h; a), a < B, for every
  * half-block, consumed by the diagonal products).  By default pdq_answer and
  * pdq_comp hold all of them at once (at N = 2^15, n = 2^20, B = 32: 10 GiB
- * of the 12.9 GiB workspace).  With a budget of `bytes` > 0 they are made
+ * of the 13.9 GiB workspace).  With a budget of `bytes` > 0 they are made
  * and consumed a chunk of primes at a time (each prime's rotations and
  * products are independent), holding at most max(bytes, one prime's
  * rotations); the results are the same bits, and
