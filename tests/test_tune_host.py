@@ -1,6 +1,7 @@
-"""Host logic of the schedule autotuner, without a GPU: a fake context and a
-fake timing rig stand in for the library, so the coordinate descent, the
-noise margin and the persisted choice are checked on the CPU."""
+"""Host logic of the autotuners, without a GPU: a fake context and a fake
+timing rig stand in for the library, so the schedule tuner's coordinate
+descent, noise margin and persisted choice, and the plan tuner's search over
+the library's admissible baby-step splits, are checked on the CPU."""
 import json
 
 import pytest
@@ -68,3 +69,49 @@ def test_row_split_candidates_follow_the_ring():
     assert tune.schedule_candidates(ctx, "ntt_row_bits") == [0, 8, 9, 10]
     ctx.log_n = 9                       # one-phase transforms: no split to tune
     assert tune.schedule_candidates(ctx, "ntt_row_bits") == [0]
+
+
+class FakePlanCtx(FakeCtx):
+    def plan(self, n, s, B=0):
+        from paper_2408_17063_gb300 import pdq
+        return pdq.plan_make_client(self.t, self.log_n, n, s, B)
+
+
+def test_plan_candidates_are_the_library_admissible_splits():
+    """The tuner searches exactly the B the library accepts for a shape: the
+    powers of two that divide s', at most 128, with at most 32 giant steps."""
+    from paper_2408_17063_gb300 import pdq
+    ctx = FakePlanCtx()
+    for s in (1, 3, 16, 100, 256, 1024, 4096, 16384):
+        sp = 1 << (s - 1).bit_length()
+        accepted = []
+        for b in (1 << i for i in range(sp.bit_length())):
+            try:
+                pdq.plan_make_client(ctx.t, ctx.log_n, 1 << 20, s, b)
+                accepted.append(b)
+            except pdq.PdqError:
+                pass
+        assert tune.candidates(ctx, 1 << 20, s) == accepted, s
+
+
+def test_plan_tuner_keeps_the_fastest_split_and_persists(tmp_path, monkeypatch):
+    ms = {1: 9.0, 2: 7.0, 4: 5.0, 8: 5.0, 16: 6.0, 32: 8.0}   # a tie: the smaller B wins
+    timed = []
+
+    def fake_time(self, ctx, n, s, B, stream=None):
+        timed.append(B)
+        return ms[B]
+
+    monkeypatch.setattr(tune.PlanTuner, "time_answer", fake_time)
+    ctx = FakePlanCtx()
+    path = tmp_path / "plans.json"
+    tuner = tune.PlanTuner(str(path))
+    assert tuner.best(ctx, 1 << 16, 32) == 4
+    assert sorted(timed) == tune.candidates(ctx, 1 << 16, 32) == [1, 2, 4, 8, 16, 32]
+    entry = json.loads(path.read_text())[tune.shape_key(ctx, 1 << 16, 32)]
+    assert entry["B"] == 4 and entry["default_B"] == ctx.plan(1 << 16, 32).B
+    # a new tuner on the same file answers without timing
+    timed.clear()
+    assert tune.PlanTuner(str(path)).best(ctx, 1 << 16, 32) == 4 and timed == []
+    # another sparsity with the same padded s' is the same shape
+    assert tune.PlanTuner(str(path)).best(ctx, 1 << 16, 20) == 4 and timed == []
