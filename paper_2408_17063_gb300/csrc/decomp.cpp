@@ -3,13 +3,16 @@
 // Per record group: the power sums w_1..w_s' (row 0) give, by Newton's
 // identity (Lem. 1, Alg. 1 step 1), the coefficients of
 // f(X) = prod_{nodes}(X - node) * X^{s' - #nodes}; the factors of X are
-// stripped and the roots among the nodes 1..G_sz are found by evaluating the
-// stripped polynomial at every node (Alg. 1 step 2; the paper suggests
-// Cantor-Zassenhaus, any exact root finder gives the same set).  The values
+// stripped and the roots among the nodes 1..G_sz are found (Alg. 1 step 2):
+// by evaluating the stripped polynomial at every node where that is the
+// cheaper, else by Cantor-Zassenhaus root finding as the paper suggests
+// (Sec. 3.1), whose cost grows with log t instead of t; the root set is
+// unique, so both give the same nodes.  The values
 // solve sum_l node_l^{j} x_l = e_j, j = 1..l (Alg. 4); this system is
 // node-scaled transposed Vandermonde, solved in O(l^2) through the Lagrange
 // basis of the nodes, and rows l+1..s' must agree.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -60,6 +63,148 @@ std::vector<u64> roots_among(const std::vector<u64>& g, u64 hi, const Zt& z) {
     return r;
 }
 
+// Polynomials over Z_t, coefficients low to high, trimmed (no zero leading
+// coefficient; the zero polynomial is empty).
+using Poly = std::vector<u64>;
+
+void trim(Poly& a) {
+    while (!a.empty() && a.back() == 0) a.pop_back();
+}
+
+// a mod m (m trimmed, nonzero)
+void poly_rem(Poly& a, const Poly& m, const Zt& z) {
+    trim(a);
+    const size_t dm = m.size() - 1;
+    const u64 il = z.inv(m.back());
+    while (a.size() > dm) {
+        const u64 c = z.mul(a.back(), il);
+        const size_t sh = a.size() - 1 - dm;
+        for (size_t i = 0; i < dm; ++i) a[sh + i] = z.sub(a[sh + i], z.mul(c, m[i]));
+        a.pop_back();                    // its coefficient is now zero
+    }
+    trim(a);
+}
+
+// a / m for m dividing a
+Poly poly_div_exact(Poly a, const Poly& m, const Zt& z) {
+    trim(a);
+    const size_t dm = m.size() - 1;
+    if (a.size() < m.size()) return {};
+    Poly q(a.size() - dm, 0);
+    const u64 il = z.inv(m.back());
+    while (a.size() > dm) {
+        const u64 c = z.mul(a.back(), il);
+        const size_t sh = a.size() - 1 - dm;
+        q[sh] = c;
+        for (size_t i = 0; i < dm; ++i) a[sh + i] = z.sub(a[sh + i], z.mul(c, m[i]));
+        a.pop_back();
+    }
+    trim(q);
+    return q;
+}
+
+Poly mul_mod(const Poly& a, const Poly& b, const Poly& m, const Zt& z) {
+    if (a.empty() || b.empty()) return {};
+    Poly r(a.size() + b.size() - 1, 0);
+    for (size_t i = 0; i < a.size(); ++i) {
+        if (a[i] == 0) continue;
+        for (size_t j = 0; j < b.size(); ++j) r[i + j] = (r[i + j] + a[i] * b[j]) % z.t;
+    }
+    poly_rem(r, m, z);
+    return r;
+}
+
+// (X + a)^e mod m
+Poly pow_linear(u64 a, u64 e, const Poly& m, const Zt& z) {
+    Poly base{a % z.t, 1}, r{1};
+    poly_rem(base, m, z);
+    poly_rem(r, m, z);
+    while (e) {
+        if (e & 1) r = mul_mod(r, base, m, z);
+        e >>= 1;
+        if (e) base = mul_mod(base, base, m, z);
+    }
+    return r;
+}
+
+// monic gcd
+Poly poly_gcd(Poly a, Poly b, const Zt& z) {
+    trim(a);
+    trim(b);
+    while (!b.empty()) {
+        poly_rem(a, b, z);
+        std::swap(a, b);
+    }
+    if (!a.empty()) {
+        const u64 il = z.inv(a.back());
+        for (u64& c : a) c = z.mul(c, il);
+    }
+    return a;
+}
+
+// Roots of f, a product of distinct linear factors over Z_t with f(0) != 0,
+// by equal-degree splitting (Cantor and Zassenhaus, 1981): for a = 0, 1, ...
+// gcd(g, (X + a)^((t-1)/2) - 1) keeps the roots r of g with r + a a nonzero
+// square, which splits g as soon as g has roots on both sides.
+int split_roots(const Poly& f, const Zt& z, std::vector<u64>& out) {
+    std::vector<Poly> work{f};
+    u64 a = 0, tries = 0;
+    while (!work.empty()) {
+        Poly g = std::move(work.back());
+        work.pop_back();
+        trim(g);
+        if (g.size() <= 1) continue;
+        if (g.size() == 2) {
+            out.push_back(z.mul(z.sub(0, g[0]), z.inv(g[1])));
+            continue;
+        }
+        const size_t d = g.size() - 1;
+        for (;;) {
+            if (++tries > 4 * z.t) return fail(PDQ_E_DECODE, "decomp: root splitting did not converge");
+            Poly h = pow_linear(a, (z.t - 1) / 2, g, z);
+            a = (a + 1) % z.t;
+            if (h.empty()) h.push_back(0);
+            h[0] = z.sub(h[0], 1);
+            Poly c = poly_gcd(g, h, z);
+            if (c.size() > 1 && c.size() - 1 < d) {
+                work.push_back(poly_div_exact(g, c, z));
+                work.push_back(std::move(c));
+                break;
+            }
+        }
+    }
+    std::sort(out.begin(), out.end());
+    return PDQ_OK;
+}
+
+// The roots of g (g(0) != 0) among the nodes 1..hi: every node evaluated
+// (Horner, on all host cores) when that is the cheaper, else the distinct
+// roots of g in Z_t as gcd(g, X^t - X), split into linear factors (the
+// Cantor-Zassenhaus root finding of Sec. 3.1), at a cost that grows with
+// log t instead of t.  Both give the same set.
+int find_roots(const Poly& g, u64 hi, const Zt& z, std::vector<u64>& roots) {
+    const double d = (double)(g.size() - 1);
+    const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const double by_nodes = (double)hi * (d + 1) / nt;
+    const double by_gcd = 2.0 * d * d * std::log2((double)z.t) * (std::log2(d) + 2);
+    if (by_nodes <= by_gcd) {
+        roots = roots_among(g, hi, z);
+        return PDQ_OK;
+    }
+    Poly xt = pow_linear(0, z.t, g, z);          // X^t mod g
+    if (xt.size() < 2) xt.resize(2, 0);
+    xt[1] = z.sub(xt[1], 1);
+    const Poly f = poly_gcd(g, xt, z);           // the distinct roots of g in Z_t
+    roots.clear();
+    if (f.size() != g.size()) return PDQ_OK;     // fewer roots than the degree: the caller refuses
+    PDQ_TRY(split_roots(f, z, roots));
+    std::vector<u64> in;
+    for (u64 r : roots)
+        if (r >= 1 && r <= hi) in.push_back(r);
+    roots.swap(in);
+    return PDQ_OK;
+}
+
 int decode_group(const u32* w, const u32* e, u32 sp, u64 G_sz, const Zt& z,
                  std::vector<u64>& nodes, std::vector<u64>& vals) {
     // Newton's identity
@@ -87,7 +232,7 @@ int decode_group(const u32* w, const u32* e, u32 sp, u64 G_sz, const Zt& z,
             if (e[j] % z.t) return fail(PDQ_E_DECODE, "decomp: values without indices");
         return PDQ_OK;
     }
-    nodes = roots_among(g, G_sz, z);
+    PDQ_TRY(find_roots(g, G_sz, z, nodes));
     if (nodes.size() != deg) return fail(PDQ_E_DECODE, "decomp: root count differs from the degree");
     const u32 l = deg;
     // M(X) = prod (X - node)

@@ -251,3 +251,29 @@ def test_client_decomp_of_unencrypted_database_answers():
     with pytest.raises(pdq.PdqError) as e:
         pdq.decomp_client(t, log_n, other, slots)
     assert e.value.code == pdq.PDQ_E_PARAM
+
+
+BIG_T = 2013265921          # 15 * 2^27 + 1: a prime = 1 mod 2N for every ring up to 2^16
+
+
+@pytest.mark.parametrize("log_n,n,s,seed", [(4, 16, 8, 21), (10, 5000, 64, 22), (13, 70000, 16, 23),
+                                            (15, 2 ** 17, 128, 24)])
+def test_client_decomp_with_a_large_plaintext_prime(log_n, n, s, seed):
+    """With t near 2^31 a group holds t - 1 records, far too many nodes to try
+    one by one: the roots come from gcd(g, X^t - X) and its splitting (the
+    Cantor-Zassenhaus route of Sec. 3.1), and the matches are recovered
+    exactly, as the closed form of Eq. 1 lays them out."""
+    par, op, v, db, truth = _case(BIG_T, log_n, n, s, seed, per_group=s)
+    assert op.G == 1 and op.G_sz == BIG_T - 1
+    pl = pdq.plan_make_client(BIG_T, log_n, n, s)
+    slots = np.stack(opdq.expected_slots(par, op, v, db)).astype(np.uint32)
+    assert pdq.decomp_client(BIG_T, log_n, pl, slots) == truth
+    # one match more than s' power sums can hold is refused
+    if s < n:
+        v2 = v.copy()
+        v2[np.flatnonzero(v2 == 0)[:1]] = 1
+        if int(v2.sum()) > op.s_prime:
+            over = np.stack(opdq.expected_slots(par, op, v2, db)).astype(np.uint32)
+            with pytest.raises(pdq.PdqError) as e:
+                pdq.decomp_client(BIG_T, log_n, pl, over)
+            assert e.value.code == pdq.PDQ_E_DECODE
