@@ -41,9 +41,21 @@ struct Zt {
     u64 inv(u64 a) const { return pow(a, t - 2); }
 };
 
-// roots of g (coefficients low to high) among 1..hi, evaluated in parallel
-std::vector<u64> roots_among(const std::vector<u64>& g, u64 hi, const Zt& z) {
-    const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+unsigned host_threads() {
+    return std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+}
+
+// roots of g (coefficients low to high) among 1..hi, evaluated on nt threads
+std::vector<u64> roots_among(const std::vector<u64>& g, u64 hi, const Zt& z, unsigned nt) {
+    if (nt <= 1) {
+        std::vector<u64> r;
+        for (u64 x = 1; x <= hi; ++x) {
+            u64 acc = 0;
+            for (size_t i = g.size(); i-- > 0;) acc = (acc * x + g[i]) % z.t;
+            if (acc == 0) r.push_back(x);
+        }
+        return r;
+    }
     std::vector<std::vector<u64>> part(nt);
     std::vector<std::thread> th;
     const u64 chunk = (hi + nt - 1) / nt;
@@ -182,13 +194,16 @@ int split_roots(const Poly& f, const Zt& z, std::vector<u64>& out) {
 // roots of g in Z_t as gcd(g, X^t - X), split into linear factors (the
 // Cantor-Zassenhaus root finding of Sec. 3.1), at a cost that grows with
 // log t instead of t.  Both give the same set.
-int find_roots(const Poly& g, u64 hi, const Zt& z, std::vector<u64>& roots) {
+// (nt: threads for the node evaluation.  The two costs in the same unit:
+// one node evaluation per Horner step, and for the gcd route about d^2 log t
+// products per polynomial power, log d + 2 powers, each product about an
+// eighth of a Horner step's cost, as measured on the host.)
+int find_roots(const Poly& g, u64 hi, const Zt& z, unsigned nt, std::vector<u64>& roots) {
     const double d = (double)(g.size() - 1);
-    const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     const double by_nodes = (double)hi * (d + 1) / nt;
-    const double by_gcd = 2.0 * d * d * std::log2((double)z.t) * (std::log2(d) + 2);
+    const double by_gcd = d * d * std::log2((double)z.t) * (std::log2(d) + 2) / 8;
     if (by_nodes <= by_gcd) {
-        roots = roots_among(g, hi, z);
+        roots = roots_among(g, hi, z, nt);
         return PDQ_OK;
     }
     Poly xt = pow_linear(0, z.t, g, z);          // X^t mod g
@@ -205,7 +220,7 @@ int find_roots(const Poly& g, u64 hi, const Zt& z, std::vector<u64>& roots) {
     return PDQ_OK;
 }
 
-int decode_group(const u32* w, const u32* e, u32 sp, u64 G_sz, const Zt& z,
+int decode_group(const u32* w, const u32* e, u32 sp, u64 G_sz, const Zt& z, unsigned nt,
                  std::vector<u64>& nodes, std::vector<u64>& vals) {
     // Newton's identity
     std::vector<u64> a(sp + 1, 0);
@@ -232,7 +247,7 @@ int decode_group(const u32* w, const u32* e, u32 sp, u64 G_sz, const Zt& z,
             if (e[j] % z.t) return fail(PDQ_E_DECODE, "decomp: values without indices");
         return PDQ_OK;
     }
-    PDQ_TRY(find_roots(g, G_sz, z, nodes));
+    PDQ_TRY(find_roots(g, G_sz, z, nt, nodes));
     if (nodes.size() != deg) return fail(PDQ_E_DECODE, "decomp: root count differs from the degree");
     const u32 l = deg;
     // M(X) = prod (X - node)
@@ -272,23 +287,47 @@ int decode_group(const u32* w, const u32* e, u32 sp, u64 G_sz, const Zt& z,
 
 // Decomp over every record group of the plan's output ciphertexts; only the
 // ring and t of c are read (c may be a host ring without device tables).
+// The groups are independent: with several, each host thread decodes every
+// nt-th group (its node evaluation single-threaded); with one, the group's
+// node evaluation runs on every thread.  An error is reported as the first
+// failing group (in group order) raised it.
 int decomp_run(const Ctx& c, const pdq_plan* plan, const uint32_t* slots, uint64_t* idx_out,
                uint32_t* val_out, uint64_t cap, uint64_t* count) {
     if (!plan || !slots || !count) return fail(PDQ_E_PARAM, "decomp: null argument");
     if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "decomp: invalid plan");
     const Zt z{c.t};
-    const u32 sp = plan->s_prime;
-    u64 total = 0;
-    std::vector<u64> nodes, vals;
-    for (u32 gamma = 0; gamma < plan->G; ++gamma) {
-        const u32 cidx = plan->G > 1 ? gamma / plan->per_out : 0;
-        const u32 o = plan->G > 1 ? gamma % plan->per_out : 0;
+    const u32 sp = plan->s_prime, G = plan->G;
+    std::vector<std::vector<u64>> nodes(G), vals(G);
+    std::vector<int> rc(G, PDQ_OK);
+    std::vector<std::string> err(G);
+    auto one = [&](u32 gamma, unsigned nt) {
+        const u32 cidx = G > 1 ? gamma / plan->per_out : 0;
+        const u32 o = G > 1 ? gamma % plan->per_out : 0;
         const u32* s = slots + (u64)cidx * c.N;
-        PDQ_TRY(decode_group(s + (u64)o * sp, s + c.m + (u64)o * sp, sp, plan->G_sz, z, nodes, vals));
-        for (size_t k = 0; k < nodes.size(); ++k) {
+        rc[gamma] = decode_group(s + (u64)o * sp, s + c.m + (u64)o * sp, sp, plan->G_sz, z, nt,
+                                 nodes[gamma], vals[gamma]);
+        if (rc[gamma] != PDQ_OK) err[gamma] = pdq_last_error();   // this thread's message
+    };
+    const unsigned hw = host_threads();
+    if (G == 1 || hw == 1) {
+        for (u32 gamma = 0; gamma < G; ++gamma) one(gamma, hw);
+    } else {
+        const unsigned nw = std::min<unsigned>(hw, G);
+        std::vector<std::thread> th;
+        for (unsigned w = 0; w < nw; ++w)
+            th.emplace_back([&, w] {
+                for (u32 gamma = w; gamma < G; gamma += nw) one(gamma, 1);
+            });
+        for (auto& t : th) t.join();
+    }
+    for (u32 gamma = 0; gamma < G; ++gamma)
+        if (rc[gamma] != PDQ_OK) return fail(rc[gamma], err[gamma]);
+    u64 total = 0;
+    for (u32 gamma = 0; gamma < G; ++gamma) {
+        for (size_t k = 0; k < nodes[gamma].size(); ++k) {
             if (total < cap) {
-                if (idx_out) idx_out[total] = (u64)gamma * plan->G_sz + nodes[k] - 1;
-                if (val_out) val_out[total] = (u32)vals[k];
+                if (idx_out) idx_out[total] = (u64)gamma * plan->G_sz + nodes[gamma][k] - 1;
+                if (val_out) val_out[total] = (u32)vals[gamma][k];
             }
             ++total;
         }

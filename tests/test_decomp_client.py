@@ -277,3 +277,50 @@ def test_client_decomp_with_a_large_plaintext_prime(log_n, n, s, seed):
             with pytest.raises(pdq.PdqError) as e:
                 pdq.decomp_client(BIG_T, log_n, pl, over)
             assert e.value.code == pdq.PDQ_E_DECODE
+
+
+def test_client_decomp_of_many_groups_and_the_first_failing_group():
+    """Groups decode independently (on several host threads): 40 groups give
+    the oracle's answer; an overflow planted in group 7 and values without
+    indices in group 23 are reported as group 7's error, the first in group
+    order, with its own message."""
+    t, log_n = 257, 5                     # G_sz = 256 records per group, 16 slots per row
+    n = 40 * 256 - 3
+    par, op, v, db, truth = _case(t, log_n, n, 2, 31)
+    assert op.G == 40 and op.n_out == 5
+    pl = pdq.plan_make_client(t, log_n, n, 2)
+    slots = np.stack(opdq.expected_slots(par, op, v, db)).astype(np.uint32)
+    assert pdq.decomp_client(t, log_n, pl, slots) == truth == opdq.decomp_slots(par, op, slots)
+    v2 = v.copy()
+    lo = 7 * op.G_sz
+    v2[lo:lo + op.G_sz] = 0
+    v2[[lo + 3, lo + 40, lo + 99]] = 1    # three matches, s' = 2
+    bad = np.stack(opdq.expected_slots(par, op, v2, db)).astype(np.uint32)
+    with pytest.raises(opdq.DecodeError):
+        opdq.decomp_slots(par, op, bad)
+    c, o = divmod(23, op.per_out)
+    bad[c, par.m + o * op.s_prime] = 5     # group 23: an e-row value, its w-rows zeroed
+    bad[c, o * op.s_prime:(o + 1) * op.s_prime] = 0
+    with pytest.raises(pdq.PdqError) as e:
+        pdq.decomp_client(t, log_n, pl, bad)
+    assert e.value.code == pdq.PDQ_E_DECODE
+    assert "values without indices" not in str(e.value)
+    # group 23's error alone is its own
+    only23 = slots.copy()
+    only23[c, par.m + o * op.s_prime] = 5
+    only23[c, o * op.s_prime:(o + 1) * op.s_prime] = 0
+    with pytest.raises(pdq.PdqError) as e:
+        pdq.decomp_client(t, log_n, pl, only23)
+    assert e.value.code == pdq.PDQ_E_DECODE and "values without indices" in str(e.value)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_client_decomp_repeats_exactly(seed):
+    """The same answer decoded again and again (threads racing on shared
+    state would show here) gives the same records every time."""
+    t, log_n, n, s = 65537, 9, 65536 * 3 + 700, 16
+    par, op, v, db, truth = _case(t, log_n, n, s, 40 + seed, pattern="clustered")
+    pl = pdq.plan_make_client(t, log_n, n, s)
+    slots = np.stack(opdq.expected_slots(par, op, v, db)).astype(np.uint32)
+    for _ in range(5):
+        assert pdq.decomp_client(t, log_n, pl, slots) == truth
