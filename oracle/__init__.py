@@ -13,6 +13,8 @@ holds none of the method's arithmetic).
   integers), hybrid key switching, rotations (Sec. 5.1).
 * ``pdq``       — Mask, Comp (Alg. 7 in the SIMD form of Sec. 5.2), the
   plaintext closed form C v / C d (Eq. 1) and Decomp (Alg. 1, 4, 6).
+* ``mutants``   — planted mistakes in the modules above, each of which the
+  pins must catch (``python -m oracle.mutants``).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against definitions,
 brute force and invariants that do not reuse the oracle's own code path.

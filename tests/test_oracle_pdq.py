@@ -225,6 +225,28 @@ def test_mask_pack_decrypts_to_packed_halfblocks(cfg_name):
 
 
 @pytest.mark.parametrize("cfg_name", ["tiny", "grouped"])
+def test_mask_pack_with_every_record_matching(cfg_name):
+    """Every record a match (v = 1 everywhere): each slot of every half-block
+    must come through Mask and the pack, so a row split that drops or moves a
+    column shows.  The expected slots are read off the records directly."""
+    cfg, par, qi, plan, keys, _ = build(cfg_name)
+    v = np.ones(cfg.n, dtype=np.uint32)
+    a, e = W.encryption_randomness(par.q, par.N, plan.J, cfg.seed + 7)
+    v_cts = pdq.encrypt_index(par, qi.sk, v, plan, a, e)
+    t = par.t
+    for name, u in (("pack(mask)", pdq.pack(par, pdq.mask(par, v_cts, qi.db, plan), keys, plan)),
+                    ("mask_pack", pdq.mask_pack(par, v_cts, qi.db, keys, plan))):
+        for h in range(plan.H):
+            rec = np.arange(h * par.m, (h + 1) * par.m)
+            ok = rec < cfg.n
+            vh = ok.astype(np.uint64)
+            dh = np.zeros(par.m, dtype=np.uint64)
+            dh[ok] = qi.db[rec[ok]].astype(np.uint64) % t
+            got = bfv.decrypt(par, qi.sk, u[h])
+            assert np.array_equal(got, np.concatenate([vh, dh])), (name, h)
+
+
+@pytest.mark.parametrize("cfg_name", ["tiny", "grouped"])
 def test_sigma_col_of_a_lifted_plaintext_swaps_its_rows(cfg_name):
     """sigma_{2N-1} applied limb by limb to a lifted plaintext equals the lift
     of the row-swapped slots (the identity mask_pack relies on)."""
