@@ -7,10 +7,11 @@
 // by evaluating the stripped polynomial at every node where that is the
 // cheaper, else by Cantor-Zassenhaus root finding as the paper suggests
 // (Sec. 3.1), whose cost grows with log t instead of t; the root set is
-// unique, so both give the same nodes.  The values
-// solve sum_l node_l^{j} x_l = e_j, j = 1..l (Alg. 4); this system is
-// node-scaled transposed Vandermonde, solved in O(l^2) through the Lagrange
-// basis of the nodes, and rows l+1..s' must agree.
+// unique, so both give the same nodes.  The values solve
+// sum_l node_l^{j} x_l = e_j, j = 1..l (Alg. 4); this system is node-scaled
+// transposed Vandermonde, solved in O(l^2) through the Lagrange basis of the
+// nodes, and rows l+1..s' must agree.  Record groups are independent and
+// decoded in parallel on the host cores.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
