@@ -288,10 +288,11 @@ int decode_group(const u32* w, const u32* e, u32 sp, u64 G_sz, const Zt& z, unsi
 
 // Decomp over every record group of the plan's output ciphertexts; only the
 // ring and t of c are read (c may be a host ring without device tables).
-// The groups are independent: with several, each host thread decodes every
-// nt-th group (its node evaluation single-threaded); with one, the group's
-// node evaluation runs on every thread.  An error is reported as the first
-// failing group (in group order) raised it.
+// The groups are independent: with several, min(G, threads) workers each
+// decode every nw-th group, a group's node evaluation (where chosen) on the
+// threads left over per worker; with one, that evaluation runs on every
+// thread.  An error is reported as the first failing group (in group order)
+// raised it.
 int decomp_run(const Ctx& c, const pdq_plan* plan, const uint32_t* slots, uint64_t* idx_out,
                uint32_t* val_out, uint64_t cap, uint64_t* count) {
     if (!plan || !slots || !count) return fail(PDQ_E_PARAM, "decomp: null argument");
@@ -313,11 +314,11 @@ int decomp_run(const Ctx& c, const pdq_plan* plan, const uint32_t* slots, uint64
     if (G == 1 || hw == 1) {
         for (u32 gamma = 0; gamma < G; ++gamma) one(gamma, hw);
     } else {
-        const unsigned nw = std::min<unsigned>(hw, G);
+        const unsigned nw = std::min<unsigned>(hw, G), per = std::max(1u, hw / nw);
         std::vector<std::thread> th;
         for (unsigned w = 0; w < nw; ++w)
             th.emplace_back([&, w] {
-                for (u32 gamma = w; gamma < G; gamma += nw) one(gamma, 1);
+                for (u32 gamma = w; gamma < G; gamma += nw) one(gamma, per);
             });
         for (auto& t : th) t.join();
     }
