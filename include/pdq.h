@@ -21,6 +21,8 @@
  *    message for the calling thread.  No call throws across the ABI.
  *  - "dev" pointers are CUDA device pointers, "host" pointers host memory.
  *    The caller owns every buffer it passes; the library never frees them.
+ *    A NULL buffer that a call would touch is refused with PDQ_E_PARAM
+ *    before any work is queued (a zero count touches none).
  *    The context owns only its own tables (allocated in pdq_ctx_create).
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
  *    enqueued asynchronously on it unless a call says otherwise; buffers must

@@ -581,18 +581,21 @@ extern "C" {
 int pdq_ntt_forward(const pdq_ctx* ctx, uint64_t* data, uint32_t count, uint32_t nlimbs,
                     uint32_t limb0, uint64_t stride, void* stream) {
     PDQ_CHECK_CTX(ctx);
+    if (count && !data) return fail(PDQ_E_PARAM, "ntt_forward: null buffer");
     return ntt_forward(C(ctx), data, count, nlimbs, limb0, stride, (cudaStream_t)stream);
 }
 
 int pdq_ntt_inverse(const pdq_ctx* ctx, uint64_t* data, uint32_t count, uint32_t nlimbs,
                     uint32_t limb0, uint64_t stride, void* stream) {
     PDQ_CHECK_CTX(ctx);
+    if (count && !data) return fail(PDQ_E_PARAM, "ntt_inverse: null buffer");
     return ntt_inverse(C(ctx), data, count, nlimbs, limb0, stride, (cudaStream_t)stream);
 }
 
 int pdq_encode(const pdq_ctx* ctx, const uint32_t* slots, uint32_t count, uint32_t nlimbs,
                uint64_t* pt_out, void* stream) {
     PDQ_CHECK_CTX(ctx);
+    if (count && (!slots || !pt_out)) return fail(PDQ_E_PARAM, "encode: null buffer");
     return encode_slots(C(ctx), slots, count, nlimbs, pt_out, (cudaStream_t)stream);
 }
 
@@ -605,12 +608,15 @@ int pdq_secret_prepare(const pdq_ctx* ctx, const int8_t* s, uint64_t* sk_out, vo
 int pdq_encrypt(const pdq_ctx* ctx, const uint64_t* sk, const uint32_t* slots, uint32_t count,
                 const uint64_t* a, const int32_t* e, uint64_t* ct_out, void* stream) {
     PDQ_CHECK_CTX(ctx);
+    if (count && (!sk || !slots || !a || !e || !ct_out))
+        return fail(PDQ_E_PARAM, "encrypt: null buffer");
     return encrypt(C(ctx), sk, slots, count, a, e, ct_out, (cudaStream_t)stream);
 }
 
 int pdq_rotkey_gen(const pdq_ctx* ctx, const uint64_t* sk, uint64_t galois, const uint64_t* a,
                    const int32_t* e, uint64_t* key_out, void* stream) {
     PDQ_CHECK_CTX(ctx);
+    if (!sk || !a || !e || !key_out) return fail(PDQ_E_PARAM, "rotkey_gen: null buffer");
     return rotkey_gen(C(ctx), sk, galois, a, e, key_out, (cudaStream_t)stream);
 }
 
@@ -622,6 +628,7 @@ int pdq_decrypt(const pdq_ctx* ctx, const uint64_t* sk, const uint64_t* ct, uint
                 uint32_t* slots_out, void* ws, size_t ws_bytes, void* stream) {
     PDQ_CHECK_CTX(ctx);
     if (ws_bytes < decrypt_ws(C(ctx), count)) return fail(PDQ_E_NOMEM, "decrypt: workspace too small");
+    if (count && (!sk || !ct || !slots_out || !ws)) return fail(PDQ_E_PARAM, "decrypt: null buffer");
     return decrypt(C(ctx), sk, ct, count, slots_out, reinterpret_cast<u64*>(ws), (cudaStream_t)stream);
 }
 
@@ -634,6 +641,7 @@ int pdq_rotate(const pdq_ctx* ctx, const uint64_t* ct_in, uint32_t count, uint64
     PDQ_CHECK_CTX(ctx);
     const Ctx& c = C(ctx);
     if (count == 0) return PDQ_OK;
+    if (!ct_in || !key || !ct_out || !ws) return fail(PDQ_E_PARAM, "rotate: null buffer");
     if (galois % 2 == 0 || galois >= 2ull * c.N) return fail(PDQ_E_PARAM, "rotate: bad Galois element");
     if (ws_bytes < pdq_rotate_workspace_bytes(ctx, count)) return fail(PDQ_E_NOMEM, "rotate: workspace too small");
     const long long cts = (long long)ct_elems(c);
@@ -748,6 +756,7 @@ int pdq_plan_constants_build(const pdq_ctx* ctx, const pdq_plan* plan, uint64_t*
     PDQ_CHECK_CTX(ctx);
     const Ctx& c = C(ctx);
     if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "plan_constants_build: invalid plan");
+    if (!out) return fail(PDQ_E_PARAM, "plan_constants_build: null buffer");
     PDQ_TRY(build_diagonals(c, *plan, out, (cudaStream_t)stream));
     if (plan->G > 1) {
         u64* masks = out + (u64)plan->hclass * plan->giants * plan->B * (c.L + c.K) * c.N;
@@ -768,6 +777,7 @@ int pdq_db_encode(const pdq_ctx* ctx, const uint32_t* values, uint64_t n, uint64
     PDQ_CHECK_CTX(ctx);
     const Ctx& c = C(ctx);
     if (n == 0) return fail(PDQ_E_PARAM, "db_encode: empty database");
+    if (!values || !db_out) return fail(PDQ_E_PARAM, "db_encode: null buffer");
     const u64 J = (n + c.N - 1) / c.N;
     return build_db(c, values, n, (u32)J, db_out, (cudaStream_t)stream);
 }
@@ -799,6 +809,7 @@ int pdq_mask(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts, co
              uint64_t* masked_out, void* stream) {
     PDQ_CHECK_CTX(ctx);
     if (!valid_plan(C(ctx), plan)) return fail(PDQ_E_PARAM, "mask: invalid plan");
+    if (!v_cts || !db || !masked_out) return fail(PDQ_E_PARAM, "mask: null buffer");
     return mask(C(ctx), plan->J, v_cts, db, masked_out, (cudaStream_t)stream);
 }
 
@@ -832,7 +843,8 @@ int pdq_answer(const pdq_ctx* ctx, const pdq_plan* plan, const uint64_t* v_cts,
     const Ctx& c = C(ctx);
     if (!valid_plan(c, plan)) return fail(PDQ_E_PARAM, "answer: invalid plan");
     if (ws_bytes < pdq_answer_workspace_bytes(ctx, plan)) return fail(PDQ_E_NOMEM, "answer: workspace too small");
-    if (!v_cts || !db || !keys || !galois || !consts || !out) return fail(PDQ_E_PARAM, "answer: null buffer");
+    if (!v_cts || !db || !keys || !galois || !consts || !out || !ws)
+        return fail(PDQ_E_PARAM, "answer: null buffer");
     u64* w = reinterpret_cast<u64*>(ws);                  // Rot_col(v_j), J ciphertexts
     const size_t wbytes = (size_t)plan->J * ct_elems(c) * sizeof(u64);
     Keys k{keys, galois, nkeys, (u64)c.ndigits * 2 * (c.L + c.K) * c.N};
